@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the wave-equation hot path on the batched 64-shot workload.
+
+Workload (default): 400 x 1200 seeded layered-fault model, dx 12.5 m,
+dt 1 ms, 20-cell sponge, 8 Hz Ricker, 64 surface shots with 200-600
+receivers and 3000-4000 samples each, all shots in one batched pass.
+
+One step = one FWI iteration's wave-equation work in the order of the paper:
+  1. fwi_gradient: forward modelling + misfit + adjoint-state gradient
+     (forward pass with checkpoints, segment recomputation, adjoint pass);
+  2. born_demig of the gradient (background + scattered fields jointly);
+  3. rtm_mig of those Born data -> the doubly migrated image (Eq. 15).
+value = algorithmic cell updates per second, Gcell-updates/s: per step
+6 U (forward U + adjoint U for the gradient, 2 U for Born, forward U +
+adjoint U for migration), U = sum over shots of nt_s x padded window cells.
+Checkpoint recomputation (2 U more per step) is overhead and not counted.
+
+--impl reference times the FP64 CPU oracle (the only other implementation
+of this path) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FD Gcell-updates/s & HBM roofline %; model error vs GPU-s, deblurred vs plain"
+UNIT = "Gcell-updates/s"
+FWD_BYTES_PER_CELL = 12  # read u^n, read u^{n-1}, write u^{n+1} (kappa is an L2-resident shared model)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="config2", choices=["config2", "config1"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    return p.parse_args()
+
+
+def make_case(name):
+    import synth
+
+    return synth.config2_case() if name == "config2" else synth.config1_case()
+
+
+def algorithmic_cells(case) -> int:
+    return 6 * case.geom.cell_updates(case.nz, case.nb)
+
+
+# ---------------------------------------------------------------------------
+# Distributed plumbing (replicas: every rank runs the whole workload)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            backend = "nccl"
+            try:
+                import torch
+
+                if not torch.cuda.is_available():
+                    backend = "gloo"
+            except Exception:
+                backend = "gloo"
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            import torch
+
+            if torch.cuda.is_available():
+                self.pg.barrier(device_ids=[self.local])
+            else:
+                self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        dev = torch.device("cuda", self.local) if torch.cuda.is_available() else torch.device("cpu")
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# ncu traffic from the committed profile (null when the kernel has changed)
+# ---------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_2403_17518_gb300", "csrc", "fd_kernels.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(cells_per_launch: float):
+    """DRAM bytes per launch of the forward step kernel from profiles/, scaled
+    to this launch size, or None if absent or taken on another kernel source."""
+    path = os.path.join(ROOT, "profiles", "fwd_step_kernel_config2.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_hash = re.search(r"kernel source sha256\[:16\]:\s*`?([0-9a-f]{16})", txt)
+    m_bpc = re.search(r"DRAM bytes per cell update:\s*([0-9.]+)", txt)
+    if not m_hash or not m_bpc or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bpc.group(1)) * cells_per_launch
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(case, n_shots: int, nt: int):
+    import numpy as np
+
+    g = case.geom.subset(list(range(min(n_shots, case.geom.n_shots))))
+    g.nt = np.minimum(g.nt, nt).astype(np.int32)
+    g.wavelet = np.ascontiguousarray(g.wavelet[:nt])
+    return g
+
+
+def run_oracle_step(case, g, d_obs):
+    import oracle
+
+    J, grad, _ = oracle.fwi_gradient(case.v_init, g, d_obs, case.h, case.dt, case.nb)
+    db = oracle.born_demig(case.v_init, g, grad, case.h, case.dt, case.nb)
+    oracle.rtm_mig(case.v_init, g, db, case.h, case.dt, case.nb)
+
+
+def oracle_measure(case, n_shots, nt, steps, warmup):
+    import oracle
+
+    oracle.build()
+    g = oracle_sample(case, n_shots, nt)
+    d_obs = oracle.model_shots(case.v_true, g, case.h, case.dt, case.nb)
+    for _ in range(warmup):
+        run_oracle_step(case, g, d_obs)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        run_oracle_step(case, g, d_obs)
+    el = time.perf_counter() - t0
+    cells = 6 * g.cell_updates(case.nz, case.nb) * steps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = min(cores, os.cpu_count() or 1)
+    sample = (f"{g.n_shots} of {case.geom.n_shots} shots (first ones), each truncated to nt={nt} "
+              f"samples, full {case.nz}x{case.nx} grid; gradient + Born + migration, FP64, OpenMP over shots")
+    return cells / el / 1e9, el / steps, cores, sample
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    case = make_case(args.workload)
+    cores = cpu_cores()
+    n_shots = min(cores, case.geom.n_shots)
+    val, sec, used, sample = oracle_measure(case, n_shots, 150, max(args.steps, 1), args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(case, args),
+        "cpu_baseline": {"value": round(val, 6), "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(val, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(case, args):
+    return {
+        "workload": f"{case.name}: batched forward modelling + adjoint-state gradient + Born demigration + "
+                    f"migration (doubly migrated image)",
+        "grid": [case.nz, case.nx], "h_m": case.h, "dt_s": case.dt, "sponge": case.nb,
+        "shots": case.geom.n_shots, "nt_range": [int(case.geom.nt.min()), int(case.geom.nt.max())],
+        "receivers_range": [int(min(case.geom.nrec(s) for s in range(case.geom.n_shots))),
+                            int(max(case.geom.nrec(s) for s in range(case.geom.n_shots)))],
+        "cell_updates_per_step": algorithmic_cells(case),
+        "l2": "inputs larger than L2 (wavefield pools + checkpoints ~15 GB per step)",
+        "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
+    }
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+        dist.close()
+        return
+    import numpy as np
+    import torch
+
+    from paper_2403_17518_gb300 import build
+    from paper_2403_17518_gb300.ops import Context, GeomArgs
+
+    torch.cuda.set_device(dist.local)
+    build()
+    case = make_case(args.workload)
+    dev = torch.device("cuda", dist.local)
+    ctx = Context(case.nz, case.nx, case.h, case.dt, case.nb, device=dist.local)
+    geom = GeomArgs(case.geom)
+    v_true = torch.tensor(case.v_true, dtype=torch.float32, device=dev)
+    v0 = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
+    d_obs = ctx.model_shots(v_true, geom)
+    grad = ctx.new_model()
+    dm1 = ctx.new_model()
+    d_born = ctx.new_data(geom)
+    ctx.set_timing(True)
+    phase = {"ms": 0.0, "launches": 0, "cells": 0}
+    launches = [0]
+
+    def step(collect=False):
+        J, _ = ctx.fwi_gradient(v0, geom, d_obs, grad=grad)
+        st = ctx.stats()
+        launches[0] += st["kernel_launches"]
+        if collect:
+            phase["ms"] += st["phase_ms"][0]
+            phase["launches"] += st["phase_launches"][0]
+            phase["cells"] += st["phase_cells"][0]
+        ctx.born_demig(v0, geom, grad, out=d_born)
+        launches[0] += ctx.stats()["kernel_launches"]
+        ctx.rtm_mig(v0, geom, d_born, out=dm1)
+        st = ctx.stats()
+        launches[0] += st["kernel_launches"]
+        if collect:
+            phase["ms"] += st["phase_ms"][0]
+            phase["launches"] += st["phase_launches"][0]
+            phase["cells"] += st["phase_cells"][0]
+        return J
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches[0] = 0
+    clocks = ClockSampler(dist.local) if dist.rank == 0 else None
+    if clocks:
+        clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(collect=True)
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    ms_max = dist.max(ms)
+    cells_step = algorithmic_cells(case)
+    value = dist.world * cells_step * args.steps / (ms_max / 1e3) / 1e9
+
+    # Roofline of the forward step kernel (pure forward passes of the step).
+    peak, peak_kind = peaks()
+    fwd_ms_per_launch = phase["ms"] / max(phase["launches"], 1)
+    cells_per_launch = phase["cells"] / max(phase["launches"], 1)
+    achieved = FWD_BYTES_PER_CELL * phase["cells"] / (phase["ms"] / 1e3) / 1e9 if phase["ms"] > 0 else None
+    traffic = profiled_traffic(cells_per_launch)
+
+    # End to end through the public API with host buffers.
+    e2e = None
+    if not args.no_e2e:
+        h_v0 = torch.tensor(case.v_init, dtype=torch.float32).pin_memory()
+        h_dobs = d_obs.cpu().pin_memory()
+        h_grad = torch.empty((case.nz, case.nx), dtype=torch.float32).pin_memory()
+        h_dm1 = torch.empty((case.nz, case.nx), dtype=torch.float32).pin_memory()
+        dv0 = torch.empty_like(v0)
+        ddobs = torch.empty_like(d_obs)
+
+        def e2e_step():
+            dv0.copy_(h_v0, non_blocking=True)
+            ddobs.copy_(h_dobs, non_blocking=True)
+            ctx.fwi_gradient(dv0, geom, ddobs, grad=grad)
+            ctx.born_demig(dv0, geom, grad, out=d_born)
+            ctx.rtm_mig(dv0, geom, d_born, out=dm1)
+            h_grad.copy_(grad, non_blocking=True)
+            h_dm1.copy_(dm1, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        el = dist.max(time.perf_counter() - t0)
+        e2e = {"value": round(dist.world * cells_step * args.e2e_steps / el / 1e9, 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(h_v0.numel() * 4 + h_dobs.numel() * 4),
+               "d2h_bytes_per_step": int(h_grad.numel() * 4 + h_dm1.numel() * 4 + 8)}
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        n_sh = min(cpu_cores(), case.geom.n_shots)
+        val, sec, used, sample = oracle_measure(case, n_sh, 300, 1, 0)
+        cpu = {"value": round(val, 6), "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample}
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(case, args),
+            "roofline": {
+                "kernel": "fwd_step_kernel (forward passes of fwi_gradient and rtm_mig)",
+                "bound": "hbm", "achieved": round(achieved, 2) if achieved else None, "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+                "traffic": round(traffic) if traffic else None,
+                "algorithmic_bytes_per_launch": round(FWD_BYTES_PER_CELL * cells_per_launch),
+                "avg_launch_ms": round(fwd_ms_per_launch, 6), "peak_kind": f"{peak_kind} (hbm_gbs)",
+            },
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches[0]),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * dhfwi.h - C ABI of the GB300 (sm_103a) implementation of the wave-equation
+ * hot path of "Robust Full Waveform Inversion with deep Hessian deblurring"
+ * (Alfarhan, Ravasi, Chen, Alkhalifah; arXiv 2403.17518).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Model arrays (velocity v, perturbation dv, gradient, image) are float32,
+ *   row-major [nz][nx] with x fastest, in device memory owned by the caller.
+ *   Velocity is in m/s (the paper's m(x) is the medium velocity, Section 2.1,
+ *   Eq. 1).
+ * - Data arrays are float32 device memory owned by the caller, packed shot
+ *   after shot in shot order; shot s occupies nt[s] * nrec_s values laid out
+ *   [nt_s][nrec_s] (time slow, receiver fast), nrec_s = rec_off[s+1]-rec_off[s].
+ *   Sample n of a shot is the wavefield produced by time step n, i.e. at time
+ *   (n+1)*dt.
+ * - Geometry arrays (dhfwi_geom) are HOST memory owned by the caller; they are
+ *   read during the call and cached on the device by content.
+ * - `stream` is a cudaStream_t (0 = the legacy default stream).  Work is
+ *   enqueued on it.  Every call first validates the model on the device and
+ *   waits for that check (one stream synchronisation); calls that return host
+ *   scalars (misfit_out, loss_hist) synchronise the stream again before
+ *   returning.  Calls on one context must not run concurrently from several
+ *   host threads.
+ * - Every call returns DHFWI_OK (0) or a negative DHFWI_ERR_* code; a message
+ *   is then available from dhfwi_last_error().  No C++ exception crosses this
+ *   boundary.  On error, output buffers hold unspecified values.
+ *
+ * Discretisation (what every propagator computes)
+ * -----------------------------------------------
+ * Eq. 1 (Section 2.1), constant-density acoustic: m^-2 u_tt - lap(u) = f.
+ * Per shot, the padded domain is the physical column window
+ * [win_x0, win_x1) extended by nb cells on all four sides (velocity there is
+ * the model's, indices clamped to the model).  With kappa = v^2 dt^2/h^2,
+ * D the unscaled 8th-order Laplacian (zero outside the padded domain) and w
+ * the Cerjan sponge factor exp(-(0.015 (nb - d))^2) per axis (d = cells from
+ * the domain's outer edge, 1 inside):
+ *     a^n     = D u^n + q^n          (q^n = wavelet[n] at the source node)
+ *     u^{n+1} = w (2 u^n + kappa a^n) - w^2 u^{n-1},   u^0 = u^{-1} = 0
+ *     d[n][r] = u^{n+1} at receiver r,                 n = 0 .. nt_s-1
+ */
+#ifndef DHFWI_H
+#define DHFWI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define DHFWI_OK 0
+#define DHFWI_ERR_ARG (-1)        /* null pointer, bad size or bad config value */
+#define DHFWI_ERR_GEOM (-2)       /* source, receiver or window outside the grid */
+#define DHFWI_ERR_CFL (-3)        /* kappa_max * 13.0032 > 4: the scheme is unstable */
+#define DHFWI_ERR_NONFINITE (-4)  /* non-finite or non-positive velocity, or non-finite result */
+#define DHFWI_ERR_OOM (-5)        /* device allocation failed */
+#define DHFWI_ERR_TIMEOUT (-6)    /* a bounded device-side wait ran out */
+#define DHFWI_ERR_CUDA (-7)       /* any other CUDA runtime error */
+#define DHFWI_ERR_STATE (-8)      /* call made in the wrong state (e.g. apply before train) */
+
+/* Born/migration parameterisation flags (born_demig / rtm_mig `flags`). */
+#define DHFWI_ABS 0  /* dv is an absolute velocity perturbation in m/s */
+#define DHFWI_REL 1  /* dv is relative, dv_abs = v0 * dv (Section 2.2, after Eq. 12) */
+
+typedef struct dhfwi_ctx dhfwi_ctx;
+
+/* Physical grid: nz rows (depth, row 0 at the surface) by nx columns, spacing
+ * h metres in both directions, time step dt seconds, sponge width nb cells
+ * (0 <= nb <= 64). */
+typedef struct {
+    int nz, nx, nb;
+    float h, dt;
+} dhfwi_grid;
+
+/* Acquisition geometry, all HOST pointers.
+ *   src_iz, src_ix [n_shots]  source node (physical row, column)
+ *   nt             [n_shots]  record length of each shot (samples), 0..nt_max
+ *   rec_off        [n_shots+1] CSR offsets into rec_iz / rec_ix
+ *   rec_iz, rec_ix [rec_off[n_shots]] receiver nodes
+ *   win_x0, win_x1 [n_shots]  physical column window [x0, x1) of each shot;
+ *                             its source and receivers must lie inside it
+ *   wavelet        [nt_max] if wavelet_shared, else [n_shots][nt_max]
+ */
+typedef struct {
+    int n_shots;
+    const int *src_iz, *src_ix, *nt;
+    const int *rec_off;
+    const int *rec_iz, *rec_ix;
+    const int *win_x0, *win_x1;
+    const float *wavelet;
+    int nt_max;
+    int wavelet_shared;
+} dhfwi_geom;
+
+/* Per-context counters of the last call (host struct filled by dhfwi_stats). */
+typedef struct {
+    long long cell_updates;   /* stencil cell updates of the last call (all wavefields) */
+    long long kernel_launches;/* kernels this library launched in the last call */
+    int checkpoint_every;     /* forward checkpoint interval used (steps) */
+    int shot_groups;          /* number of shot groups the memory planner used */
+    double workspace_bytes;   /* device workspace held by the context */
+    /* Device time of the phases of the last call, from CUDA events recorded on
+     * the call's stream around each phase (0 unless timing is on, see
+     * dhfwi_set_timing).  Phase 0: forward passes (forward step kernel only);
+     * 1: backward sweeps (segment recompute + adjoint step kernels); 2: Born
+     * joint passes. */
+    double phase_ms[3];
+    long long phase_launches[3];
+    long long phase_cells[3];  /* cell updates in that phase (Born counts 2 per cell) */
+} dhfwi_stats_t;
+
+/* Create a context on CUDA device `device` for grid `g`.  The context owns all
+ * device workspace (wavefields, checkpoints, network weights and Adam state);
+ * the caller owns every argument buffer.  Returns DHFWI_OK and *out, or an
+ * error code (*out is then NULL). */
+int dhfwi_create(dhfwi_ctx **out, const dhfwi_grid *g, int device);
+
+/* Release the context and its device workspace.  Accepts NULL. */
+void dhfwi_destroy(dhfwi_ctx *ctx);
+
+/* Message of the last error on this context (never NULL; "" after success).
+ * With ctx == NULL, the message of the last failed dhfwi_create. */
+const char *dhfwi_last_error(const dhfwi_ctx *ctx);
+
+/* Counters of the last call on this context.  With timing on, waits for the
+ * phase events of the last call to complete. */
+int dhfwi_stats(const dhfwi_ctx *ctx, dhfwi_stats_t *out);
+
+/* Turn per-phase CUDA-event timing on (1) or off (0) for later calls. */
+int dhfwi_set_timing(dhfwi_ctx *ctx, int on);
+
+/* Forward shot modelling (Section 2.1: "the wave equation is solved using a
+ * forward modeling scheme such as the finite difference method to obtain the
+ * simulated data d_s").  All shots run in one batched pass.
+ *   v_dev  [nz][nx] velocity (m/s), device
+ *   d_dev  packed records (see above), device, written */
+int model_shots(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, float *d_dev,
+                void *stream);
+
+/* Misfit and adjoint-state gradient (Section 2.1 Eq. 2; Section 2.3.1 Eq. 13).
+ *   misfit_out (host, may be NULL)  J = 1/2 sum (d_s - d_o)^2
+ *   grad_dev   [nz][nx] device, written with dJ/dv (m/s)^-1 scaled units.
+ *              The paper's g = L~^T (d_o - d_s) equals -grad.
+ *   d_syn_dev  optional (may be NULL) packed synthetic records d_s.
+ * Uses forward checkpoints and segment recomputation; synchronises the stream
+ * when misfit_out is not NULL. */
+int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom,
+                 const float *d_obs_dev, float *grad_dev, double *misfit_out, float *d_syn_dev,
+                 void *stream);
+
+/* Born demigration d = L~ dv (Section 2.2 Eqs. 9-12b): the background field
+ * (Eq. 9) and the scattered field (Eq. 11) advance together in one kernel, so
+ * the background wavefield is never stored.  This is the exact tangent of
+ * model_shots at v0.
+ *   dv_dev [nz][nx] device: perturbation (absolute m/s, or relative with
+ *          flags = DHFWI_REL)
+ *   d_dev  packed Born records, device, written */
+int born_demig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const float *dv_dev,
+               float *d_dev, int flags, void *stream);
+
+/* Migration img = L~^T d (Section 2.3.1 Eq. 13 applied to arbitrary data; the
+ * exact transpose of born_demig with the same flags).  The doubly migrated
+ * image of Eq. 15 is rtm_mig(born_demig(g)).
+ *   d_dev   packed records, device
+ *   img_dev [nz][nx] device, written */
+int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const float *d_dev,
+            float *img_dev, int flags, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DHFWI_H */

@@ -1,0 +1,711 @@
+// Host side of the C ABI declared in include/dhfwi.h: context, geometry
+// plans (cached by content), validation, workspace and the batched time loops
+// for model_shots, fwi_gradient, born_demig and rtm_mig.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dhfwi.h"
+#include "fd_internal.h"
+#include "nn_api.h"
+
+using namespace dhfwi;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Plan {
+    unsigned long long hash = 0;
+    int n_shots = 0, nt_max = 0;
+    std::vector<ShotDesc> shots;       // by slot
+    std::vector<int> slot_of_shot;
+    std::vector<int> nt_sorted;        // nt by slot (non-increasing)
+    std::vector<Tile> tiles;           // with a sentinel at the end
+    std::vector<TileRec> recs;
+    std::vector<int> tiles_prefix;     // tiles of the first m slots
+    long long pool_floats = 0;
+    long long n_data = 0;
+    long long cells_per_step_all = 0;  // padded cells of all shots
+    DevBuf d_shots, d_tiles, d_recs, d_slot_of, d_wav;
+};
+
+}  // namespace
+
+struct dhfwi_ctx {
+    int device = 0;
+    dhfwi_grid g{};
+    std::string err;
+    int pf = 0;             // pitch of padded model arrays
+    int NZ = 0, NXF = 0;
+    Plan plan;
+    DevBuf kap, vpad, dkap, status, partial;
+    DevBuf fields;          // general wavefield pools
+    DevBuf ck;              // checkpoints
+    DevBuf abuf;            // segment buffer of a^n
+    DevBuf dtmp, rtmp;      // data-sized temporaries
+    unsigned *h_status = nullptr;   // pinned
+    double *h_partial = nullptr;    // pinned
+    int ck_every = 50;
+    dhfwi_stats_t stats{};
+    dhfwi::NetState *net = nullptr;
+    bool timing = false;
+    cudaEvent_t ev[3][2] = {};
+    bool ev_used[3] = {};
+};
+
+namespace {
+
+constexpr int RESID_BLOCKS = 1024;
+
+int fail(dhfwi_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(dhfwi_ctx *ctx, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? DHFWI_ERR_OOM : DHFWI_ERR_CUDA, m);
+}
+
+#define CK(call)                                           \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+int ensure(dhfwi_ctx *ctx, DevBuf &b, size_t bytes, const char *what) {
+    if (b.bytes >= bytes && b.p) return DHFWI_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char msg[256];
+        snprintf(msg, sizeof msg, "allocating %s (%.3f GB): %s", what, bytes / 1e9, cudaGetErrorString(e));
+        return fail(ctx, e == cudaErrorMemoryAllocation ? DHFWI_ERR_OOM : DHFWI_ERR_CUDA, msg);
+    }
+    b.bytes = bytes;
+    return DHFWI_OK;
+}
+
+void release(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+unsigned long long fnv(unsigned long long h, const void *p, size_t n) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; i++) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+int round_up(int a, int m) { return (a + m - 1) / m * m; }
+
+// Host validation of the geometry against the grid.
+int validate_geom(dhfwi_ctx *ctx, const dhfwi_geom *G) {
+    const dhfwi_grid &g = ctx->g;
+    if (!G) return fail(ctx, DHFWI_ERR_ARG, "geometry is NULL");
+    if (G->n_shots < 1) return fail(ctx, DHFWI_ERR_ARG, "n_shots must be >= 1");
+    if (!G->src_iz || !G->src_ix || !G->nt || !G->rec_off || !G->win_x0 || !G->win_x1 || !G->wavelet)
+        return fail(ctx, DHFWI_ERR_ARG, "geometry has a NULL array");
+    if (G->nt_max < 1) return fail(ctx, DHFWI_ERR_ARG, "nt_max must be >= 1");
+    if (G->rec_off[0] != 0) return fail(ctx, DHFWI_ERR_ARG, "rec_off[0] must be 0");
+    if (G->rec_off[G->n_shots] > 0 && (!G->rec_iz || !G->rec_ix))
+        return fail(ctx, DHFWI_ERR_ARG, "receiver arrays are NULL");
+    char msg[256];
+    for (int s = 0; s < G->n_shots; s++) {
+        if (G->nt[s] < 1 || G->nt[s] > G->nt_max) {
+            snprintf(msg, sizeof msg, "shot %d: nt=%d outside [1, nt_max=%d]", s, G->nt[s], G->nt_max);
+            return fail(ctx, DHFWI_ERR_ARG, msg);
+        }
+        if (G->rec_off[s + 1] < G->rec_off[s]) return fail(ctx, DHFWI_ERR_ARG, "rec_off not monotone");
+        int x0 = G->win_x0[s], x1 = G->win_x1[s];
+        if (x0 < 0 || x1 > g.nx || x1 <= x0) {
+            snprintf(msg, sizeof msg, "shot %d: window [%d,%d) outside [0,%d)", s, x0, x1, g.nx);
+            return fail(ctx, DHFWI_ERR_GEOM, msg);
+        }
+        auto inside = [&](int iz, int ix) { return iz >= 0 && iz < g.nz && ix >= x0 && ix < x1; };
+        if (!inside(G->src_iz[s], G->src_ix[s])) {
+            snprintf(msg, sizeof msg, "shot %d: source (%d,%d) outside its window", s, G->src_iz[s], G->src_ix[s]);
+            return fail(ctx, DHFWI_ERR_GEOM, msg);
+        }
+        for (int r = G->rec_off[s]; r < G->rec_off[s + 1]; r++) {
+            if (!inside(G->rec_iz[r], G->rec_ix[r])) {
+                snprintf(msg, sizeof msg, "shot %d: receiver %d (%d,%d) outside its window", s, r - G->rec_off[s],
+                         G->rec_iz[r], G->rec_ix[r]);
+                return fail(ctx, DHFWI_ERR_GEOM, msg);
+            }
+        }
+    }
+    return DHFWI_OK;
+}
+
+unsigned long long geom_hash(const dhfwi_grid &g, const dhfwi_geom *G) {
+    unsigned long long h = 1469598103934665603ull;
+    h = fnv(h, &g, sizeof g);
+    h = fnv(h, &G->n_shots, sizeof(int));
+    h = fnv(h, &G->nt_max, sizeof(int));
+    h = fnv(h, &G->wavelet_shared, sizeof(int));
+    const int ns = G->n_shots;
+    h = fnv(h, G->src_iz, sizeof(int) * ns);
+    h = fnv(h, G->src_ix, sizeof(int) * ns);
+    h = fnv(h, G->nt, sizeof(int) * ns);
+    h = fnv(h, G->rec_off, sizeof(int) * (ns + 1));
+    const int nr = G->rec_off[ns];
+    if (nr > 0) {
+        h = fnv(h, G->rec_iz, sizeof(int) * nr);
+        h = fnv(h, G->rec_ix, sizeof(int) * nr);
+    }
+    h = fnv(h, G->win_x0, sizeof(int) * ns);
+    h = fnv(h, G->win_x1, sizeof(int) * ns);
+    size_t nw = (size_t)G->nt_max * (G->wavelet_shared ? 1 : ns);
+    h = fnv(h, G->wavelet, sizeof(float) * nw);
+    return h;
+}
+
+template <typename T>
+int upload(dhfwi_ctx *ctx, DevBuf &b, const std::vector<T> &v, const char *what) {
+    int rc = ensure(ctx, b, std::max<size_t>(sizeof(T) * v.size(), 16), what);
+    if (rc) return rc;
+    if (!v.empty()) CK(cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return DHFWI_OK;
+}
+
+// Builds (or reuses) the plan for this geometry.
+int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
+    int rc = validate_geom(ctx, G);
+    if (rc) return rc;
+    unsigned long long h = geom_hash(ctx->g, G);
+    Plan &P = ctx->plan;
+    if (P.hash == h && P.n_shots == G->n_shots) return DHFWI_OK;
+    const int nb = ctx->g.nb, NZ = ctx->NZ, ns = G->n_shots;
+    // The plan's device tables may still be read by earlier work on any stream.
+    CK(cudaDeviceSynchronize());
+    P.hash = 0;
+    P.n_shots = ns;
+    P.nt_max = G->nt_max;
+    std::vector<int> order(ns);
+    for (int s = 0; s < ns; s++) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return G->nt[a] > G->nt[b]; });
+    std::vector<long long> doff(ns + 1, 0);
+    for (int s = 0; s < ns; s++)
+        doff[s + 1] = doff[s] + (long long)G->nt[s] * (G->rec_off[s + 1] - G->rec_off[s]);
+    P.n_data = doff[ns];
+    P.shots.assign(ns, ShotDesc{});
+    P.slot_of_shot.assign(ns, 0);
+    P.nt_sorted.assign(ns, 0);
+    P.tiles.clear();
+    P.recs.clear();
+    P.tiles_prefix.assign(ns + 1, 0);
+    long long foff = 0;
+    P.cells_per_step_all = 0;
+    for (int k = 0; k < ns; k++) {
+        const int s = order[k];
+        ShotDesc &sd = P.shots[k];
+        const int x0 = G->win_x0[s], x1 = G->win_x1[s];
+        sd.nxw = x1 - x0 + 2 * nb;
+        sd.pitch = round_up(sd.nxw, 32);
+        sd.foff = foff;
+        foff += (long long)sd.pitch * NZ;
+        sd.doff = doff[s];
+        sd.x0 = x0;
+        sd.sz = G->src_iz[s] + nb;
+        sd.sx = G->src_ix[s] - x0 + nb;
+        sd.nt = G->nt[s];
+        sd.nrec = G->rec_off[s + 1] - G->rec_off[s];
+        sd.wav_off = G->wavelet_shared ? 0 : s * G->nt_max;
+        sd.shot = s;
+        P.slot_of_shot[s] = k;
+        P.nt_sorted[k] = sd.nt;
+        P.cells_per_step_all += (long long)sd.nxw * NZ;
+        // Tiles of this shot, and its receivers bucketed per tile.
+        const int ntz = (NZ + TZ - 1) / TZ, ntx = (sd.nxw + TX - 1) / TX;
+        std::vector<std::vector<TileRec>> bucket((size_t)ntz * ntx);
+        for (int r = 0; r < sd.nrec; r++) {
+            const int rz = G->rec_iz[G->rec_off[s] + r] + nb;
+            const int rx = G->rec_ix[G->rec_off[s] + r] - x0 + nb;
+            bucket[(size_t)(rz / TZ) * ntx + rx / TX].push_back(TileRec{(rz % TZ) * TX + rx % TX, r});
+        }
+        for (int tz = 0; tz < ntz; tz++)
+            for (int tx = 0; tx < ntx; tx++) {
+                P.tiles.push_back(Tile{k, tz * TZ, tx * TX, (int)P.recs.size()});
+                for (const TileRec &e : bucket[(size_t)tz * ntx + tx]) P.recs.push_back(e);
+            }
+        P.tiles_prefix[k + 1] = (int)P.tiles.size();
+    }
+    P.tiles.push_back(Tile{0, 0, 0, (int)P.recs.size()});  // sentinel
+    P.pool_floats = foff;
+    std::vector<float> wav((size_t)G->nt_max * (G->wavelet_shared ? 1 : ns));
+    std::memcpy(wav.data(), G->wavelet, sizeof(float) * wav.size());
+    if ((rc = upload(ctx, P.d_shots, P.shots, "shot table"))) return rc;
+    if ((rc = upload(ctx, P.d_tiles, P.tiles, "tile table"))) return rc;
+    if ((rc = upload(ctx, P.d_recs, P.recs, "receiver table"))) return rc;
+    if ((rc = upload(ctx, P.d_slot_of, P.slot_of_shot, "slot table"))) return rc;
+    if ((rc = upload(ctx, P.d_wav, wav, "wavelets"))) return rc;
+    P.hash = h;
+    return DHFWI_OK;
+}
+
+// Number of active tiles at forward step n (shots with nt > n).
+inline int active_tiles(const Plan &P, int n) {
+    // nt_sorted is non-increasing; count slots with nt > n.
+    int lo = 0, hi = P.n_shots;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (P.nt_sorted[mid] > n) lo = mid + 1;
+        else hi = mid;
+    }
+    return P.tiles_prefix[lo];
+}
+
+long long active_cells(const Plan &P, int n, int NZ) {
+    long long c = 0;
+    for (int k = 0; k < P.n_shots && P.nt_sorted[k] > n; k++) c += (long long)P.shots[k].nxw * NZ;
+    return c;
+}
+
+StepCommon common(dhfwi_ctx *ctx) {
+    StepCommon c;
+    c.shots = (const ShotDesc *)ctx->plan.d_shots.p;
+    c.tiles = (const Tile *)ctx->plan.d_tiles.p;
+    c.recs = (const TileRec *)ctx->plan.d_recs.p;
+    c.kap = (const float *)ctx->kap.p;
+    c.vpad = (const float *)ctx->vpad.p;
+    c.wav = (const float *)ctx->plan.d_wav.p;
+    c.pf = ctx->pf;
+    c.NZ = ctx->NZ;
+    c.nb = ctx->g.nb;
+    return c;
+}
+
+// Padded model arrays from v (and dv), with the velocity / CFL check.
+int prep_model(dhfwi_ctx *ctx, const float *v, const float *dv, int rel, cudaStream_t st) {
+    if (!v) return fail(ctx, DHFWI_ERR_ARG, "velocity pointer is NULL");
+    size_t mb = sizeof(float) * (size_t)ctx->NZ * ctx->pf;
+    int rc;
+    if ((rc = ensure(ctx, ctx->kap, mb, "kappa"))) return rc;
+    if ((rc = ensure(ctx, ctx->vpad, mb, "padded velocity"))) return rc;
+    if (dv && (rc = ensure(ctx, ctx->dkap, mb, "d kappa"))) return rc;
+    CK(cudaMemsetAsync(ctx->status.p, 0, 2 * sizeof(unsigned), st));
+    const float c = (ctx->g.dt * ctx->g.dt) / (ctx->g.h * ctx->g.h);
+    launch_prep_model(v, dv, rel, ctx->g.nz, ctx->g.nx, ctx->g.nb, c, (float *)ctx->kap.p,
+                      (float *)ctx->vpad.p, dv ? (float *)ctx->dkap.p : nullptr, ctx->pf,
+                      (unsigned *)ctx->status.p, st);
+    ctx->stats.kernel_launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ctx->h_status[0])
+        return fail(ctx, DHFWI_ERR_NONFINITE, "velocity must be finite and > 0 (and dv finite)");
+    float kmax;
+    std::memcpy(&kmax, &ctx->h_status[1], sizeof kmax);
+    // Leapfrog stability: kappa * (spectral radius of -D) <= 4, where the 2D
+    // radius of the 8th-order stencil is 2 (|c0| + 2 sum |c_k|).
+    const double S = 2.0 * (205.0 / 72.0 + 2.0 * (8.0 / 5.0 + 1.0 / 5.0 + 8.0 / 315.0 + 1.0 / 560.0));
+    if ((double)kmax * S > 4.0) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "CFL violated: v_max dt/h = %.4f > %.4f", std::sqrt((double)kmax),
+                 std::sqrt(4.0 / S));
+        return fail(ctx, DHFWI_ERR_CFL, msg);
+    }
+    return DHFWI_OK;
+}
+
+int begin_call(dhfwi_ctx *ctx) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx->err.clear();
+    ctx->stats.cell_updates = 0;
+    ctx->stats.kernel_launches = 0;
+    ctx->stats.shot_groups = 1;
+    for (int i = 0; i < 3; i++) {
+        ctx->stats.phase_ms[i] = 0.0;
+        ctx->stats.phase_launches[i] = 0;
+        ctx->stats.phase_cells[i] = 0;
+        ctx->ev_used[i] = false;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return DHFWI_OK;
+}
+
+void phase_begin(dhfwi_ctx *ctx, int ph, cudaStream_t st) {
+    if (!ctx->timing) return;
+    if (!ctx->ev[ph][0]) {
+        cudaEventCreate(&ctx->ev[ph][0]);
+        cudaEventCreate(&ctx->ev[ph][1]);
+    }
+    cudaEventRecord(ctx->ev[ph][0], st);
+}
+
+void phase_end(dhfwi_ctx *ctx, int ph, cudaStream_t st, long long launches, long long cells) {
+    ctx->stats.phase_launches[ph] += launches;
+    ctx->stats.phase_cells[ph] += cells;
+    if (!ctx->timing) return;
+    cudaEventRecord(ctx->ev[ph][1], st);
+    ctx->ev_used[ph] = true;
+}
+
+int end_call(dhfwi_ctx *ctx) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    ctx->stats.checkpoint_every = ctx->ck_every;
+    double ws = ctx->kap.bytes + ctx->vpad.bytes + ctx->dkap.bytes + ctx->fields.bytes + ctx->ck.bytes +
+                ctx->abuf.bytes + ctx->dtmp.bytes + ctx->rtmp.bytes;
+    ctx->stats.workspace_bytes = ws;
+    return DHFWI_OK;
+}
+
+// Forward pass over all steps.  u pools A/B must be zeroed by the caller.
+// d (nullable) receives samples; ck (nullable) receives checkpoints every K.
+int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *d, float *ck, int K, cudaStream_t st) {
+    const Plan &P = ctx->plan;
+    FwdArgs a{};
+    a.c = common(ctx);
+    float *cur = uA, *old = uB;
+    const long long pool = P.pool_floats;
+    const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
+    phase_begin(ctx, 0, st);
+    for (int n = 0; n < P.nt_max; n++) {
+        const int nt = active_tiles(P, n);
+        a.u = cur;
+        a.uo = old;
+        a.d = d;
+        a.a_out = nullptr;
+        if (ck && n % K == 0) {
+            const long long j = n / K;
+            a.ck_old = ck + (2 * j) * pool;
+            a.ck_cur = ck + (2 * j + 1) * pool;
+        } else {
+            a.ck_old = a.ck_cur = nullptr;
+        }
+        a.n = n;
+        launch_fwd_step(a, nt, st);
+        ctx->stats.kernel_launches++;
+        ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
+        std::swap(cur, old);
+    }
+    phase_end(ctx, 0, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
+    CK(cudaGetLastError());
+    return DHFWI_OK;
+}
+
+// Backward sweep: recompute each segment from its checkpoint, then the
+// adjoint steps over it with the data r injected; image accumulated in gpool.
+int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *nuA, float *nuB, float *gpool,
+                 const float *r, cudaStream_t st) {
+    const Plan &P = ctx->plan;
+    const long long pool = P.pool_floats;
+    const int nseg = (P.nt_max + K - 1) / K;
+    FwdArgs f{};
+    f.c = common(ctx);
+    AdjArgs b{};
+    b.c = f.c;
+    b.r = r;
+    b.g = gpool;
+    float *ncur = nuA, *nold = nuB;
+    const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
+    phase_begin(ctx, 1, st);
+    for (int js = nseg - 1; js >= 0; js--) {
+        const int n0 = js * K, n1 = std::min(n0 + K, P.nt_max);
+        float *cur = ck + (2 * (long long)js + 1) * pool;
+        float *old = ck + (2 * (long long)js) * pool;
+        for (int n = n0; n < n1; n++) {
+            f.u = cur;
+            f.uo = old;
+            f.a_out = abuf + (long long)(n - n0) * pool;
+            f.d = nullptr;
+            f.ck_old = f.ck_cur = nullptr;
+            f.n = n;
+            launch_fwd_step(f, active_tiles(P, n), st);
+            ctx->stats.kernel_launches++;
+            ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
+            std::swap(cur, old);
+        }
+        for (int k = n1; k >= n0 + 1; k--) {
+            b.nu = ncur;
+            b.nuo = nold;
+            b.a = abuf + (long long)(k - 1 - n0) * pool;
+            b.k = k;
+            launch_adj_step(b, active_tiles(P, k - 1), st);
+            ctx->stats.kernel_launches++;
+            ctx->stats.cell_updates += active_cells(P, k - 1, ctx->NZ);
+            std::swap(ncur, nold);
+        }
+        CK(cudaGetLastError());
+    }
+    phase_end(ctx, 1, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
+    return DHFWI_OK;
+}
+
+// Workspace for a backward-capable pass: 2 field pools + image pool + 2 adjoint
+// pools, nseg checkpoint pairs, K segment slots.
+int ensure_backward_ws(dhfwi_ctx *ctx, int *K_out) {
+    const Plan &P = ctx->plan;
+    const size_t pool = sizeof(float) * (size_t)P.pool_floats;
+    int K = ctx->ck_every;
+    int rc = ensure(ctx, ctx->fields, 5 * pool, "wavefield pools");
+    if (rc) return rc;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        const int nseg = (P.nt_max + K - 1) / K;
+        rc = ensure(ctx, ctx->ck, 2 * (size_t)nseg * pool, "checkpoints");
+        if (!rc) rc = ensure(ctx, ctx->abuf, (size_t)std::min(K, P.nt_max) * pool, "segment buffer");
+        if (!rc) break;
+        if (rc != DHFWI_ERR_OOM) return rc;
+        // Fall back to ~sqrt(2 nt) segments, which minimises 2 nt/K + K.
+        release(ctx->ck);
+        release(ctx->abuf);
+        K = std::max(K, (int)std::ceil(std::sqrt(2.0 * P.nt_max)));
+    }
+    if (rc) return rc;
+    *K_out = K;
+    ctx->ck_every = K;
+    return DHFWI_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int dhfwi_create(dhfwi_ctx **out, const dhfwi_grid *g, int device) {
+    g_create_error.clear();
+    if (!out || !g) {
+        g_create_error = "out and g must not be NULL";
+        return DHFWI_ERR_ARG;
+    }
+    *out = nullptr;
+    if (g->nz < 1 || g->nx < 1 || g->nb < 0 || g->nb > 64 || !(g->h > 0.f) || !(g->dt > 0.f) ||
+        !std::isfinite(g->h) || !std::isfinite(g->dt)) {
+        g_create_error = "bad grid: need nz, nx >= 1, 0 <= nb <= 64, finite h, dt > 0";
+        return DHFWI_ERR_ARG;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        g_create_error = std::string("no such CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "index");
+        cudaGetLastError();
+        return DHFWI_ERR_CUDA;
+    }
+    if ((e = cudaSetDevice(device)) != cudaSuccess) {
+        g_create_error = cudaGetErrorString(e);
+        return DHFWI_ERR_CUDA;
+    }
+    dhfwi_ctx *ctx = new (std::nothrow) dhfwi_ctx();
+    if (!ctx) {
+        g_create_error = "host allocation failed";
+        return DHFWI_ERR_OOM;
+    }
+    ctx->device = device;
+    ctx->g = *g;
+    ctx->NZ = g->nz + 2 * g->nb;
+    ctx->NXF = g->nx + 2 * g->nb;
+    ctx->pf = round_up(ctx->NXF, 32);
+    if (ensure(ctx, ctx->status, 64, "status") || ensure(ctx, ctx->partial, sizeof(double) * RESID_BLOCKS, "partials") ||
+        cudaMallocHost(&ctx->h_status, 64) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_partial, sizeof(double) * RESID_BLOCKS) != cudaSuccess) {
+        g_create_error = ctx->err.empty() ? "pinned allocation failed" : ctx->err;
+        dhfwi_destroy(ctx);
+        return DHFWI_ERR_OOM;
+    }
+    *out = ctx;
+    return DHFWI_OK;
+}
+
+void dhfwi_destroy(dhfwi_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    DevBuf *bufs[] = {&ctx->kap, &ctx->vpad, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
+                      &ctx->ck, &ctx->abuf, &ctx->dtmp, &ctx->rtmp, &ctx->plan.d_shots, &ctx->plan.d_tiles,
+                      &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav};
+    for (DevBuf *b : bufs) release(*b);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->h_partial) cudaFreeHost(ctx->h_partial);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 2; j++)
+            if (ctx->ev[i][j]) cudaEventDestroy(ctx->ev[i][j]);
+    dhfwi::net_destroy(ctx->net);
+    delete ctx;
+}
+
+const char *dhfwi_last_error(const dhfwi_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+int dhfwi_stats(const dhfwi_ctx *ctx, dhfwi_stats_t *out) {
+    if (!ctx || !out) return DHFWI_ERR_ARG;
+    *out = ctx->stats;
+    for (int i = 0; i < 3; i++) {
+        out->phase_ms[i] = 0.0;
+        if (ctx->timing && ctx->ev_used[i]) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(ctx->ev[i][1]) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]) == cudaSuccess)
+                out->phase_ms[i] = ms;
+            cudaGetLastError();
+        }
+    }
+    return DHFWI_OK;
+}
+
+int dhfwi_set_timing(dhfwi_ctx *ctx, int on) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx->timing = on != 0;
+    return DHFWI_OK;
+}
+
+int model_shots(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, float *d_dev, void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!d_dev) return fail(ctx, DHFWI_ERR_ARG, "d_dev is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = get_plan(ctx, geom))) return rc;
+    if ((rc = prep_model(ctx, v_dev, nullptr, 0, st))) return rc;
+    const size_t pool = sizeof(float) * (size_t)ctx->plan.pool_floats;
+    if ((rc = ensure(ctx, ctx->fields, 5 * pool, "wavefield pools"))) return rc;
+    float *uA = (float *)ctx->fields.p, *uB = uA + ctx->plan.pool_floats;
+    CK(cudaMemsetAsync(uA, 0, 2 * pool, st));
+    if ((rc = run_forward(ctx, uA, uB, d_dev, nullptr, 1, st))) return rc;
+    return end_call(ctx);
+}
+
+int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, const float *d_obs_dev,
+                 float *grad_dev, double *misfit_out, float *d_syn_dev, void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!d_obs_dev || !grad_dev) return fail(ctx, DHFWI_ERR_ARG, "d_obs_dev and grad_dev must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = get_plan(ctx, geom))) return rc;
+    if ((rc = prep_model(ctx, v_dev, nullptr, 0, st))) return rc;
+    const Plan &P = ctx->plan;
+    int K = 0;
+    if ((rc = ensure_backward_ws(ctx, &K))) return rc;
+    const size_t nd = (size_t)P.n_data;
+    if ((rc = ensure(ctx, ctx->rtmp, sizeof(float) * std::max<size_t>(nd, 1), "residual"))) return rc;
+    float *dsyn = d_syn_dev;
+    if (!dsyn) {
+        if ((rc = ensure(ctx, ctx->dtmp, sizeof(float) * std::max<size_t>(nd, 1), "synthetic data"))) return rc;
+        dsyn = (float *)ctx->dtmp.p;
+    }
+    const long long pool = P.pool_floats;
+    float *F = (float *)ctx->fields.p;
+    float *uA = F, *uB = F + pool, *nuA = F + 2 * pool, *nuB = F + 3 * pool, *gp = F + 4 * pool;
+    CK(cudaMemsetAsync(F, 0, sizeof(float) * 5 * (size_t)pool, st));
+    if ((rc = run_forward(ctx, uA, uB, dsyn, (float *)ctx->ck.p, K, st))) return rc;
+    float *r = (float *)ctx->rtmp.p;
+    launch_residual(dsyn, d_obs_dev, r, (long long)nd, (double *)ctx->partial.p, RESID_BLOCKS, st);
+    ctx->stats.kernel_launches++;
+    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, nuA, nuB, gp, r, st))) return rc;
+    launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
+                        ctx->g.nx, ctx->g.nb, v_dev, 0, grad_dev, st);
+    ctx->stats.kernel_launches++;
+    CK(cudaGetLastError());
+    if (misfit_out) {
+        CK(cudaMemcpyAsync(ctx->h_partial, ctx->partial.p, sizeof(double) * RESID_BLOCKS, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double J = 0.0;
+        for (int i = 0; i < RESID_BLOCKS; i++) J += ctx->h_partial[i];
+        J *= 0.5;
+        if (!std::isfinite(J)) return fail(ctx, DHFWI_ERR_NONFINITE, "misfit is not finite");
+        *misfit_out = J;
+    }
+    return end_call(ctx);
+}
+
+int born_demig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const float *dv_dev, float *d_dev,
+               int flags, void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!dv_dev || !d_dev) return fail(ctx, DHFWI_ERR_ARG, "dv_dev and d_dev must not be NULL");
+    if (flags != DHFWI_ABS && flags != DHFWI_REL) return fail(ctx, DHFWI_ERR_ARG, "flags must be DHFWI_ABS or DHFWI_REL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = get_plan(ctx, geom))) return rc;
+    if ((rc = prep_model(ctx, v0_dev, dv_dev, flags == DHFWI_REL, st))) return rc;
+    const Plan &P = ctx->plan;
+    const long long pool = P.pool_floats;
+    if ((rc = ensure(ctx, ctx->fields, 5 * sizeof(float) * (size_t)pool, "wavefield pools"))) return rc;
+    float *F = (float *)ctx->fields.p;
+    CK(cudaMemsetAsync(F, 0, sizeof(float) * 4 * (size_t)pool, st));
+    BornArgs a{};
+    a.c = common(ctx);
+    a.dkap = (const float *)ctx->dkap.p;
+    a.d = d_dev;
+    float *u = F, *uo = F + pool, *p = F + 2 * pool, *po = F + 3 * pool;
+    const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
+    phase_begin(ctx, 2, st);
+    for (int n = 0; n < P.nt_max; n++) {
+        a.u = u;
+        a.uo = uo;
+        a.p = p;
+        a.po = po;
+        a.n = n;
+        launch_born_step(a, active_tiles(P, n), st);
+        ctx->stats.kernel_launches++;
+        ctx->stats.cell_updates += 2 * active_cells(P, n, ctx->NZ);
+        std::swap(u, uo);
+        std::swap(p, po);
+    }
+    phase_end(ctx, 2, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
+    return end_call(ctx);
+}
+
+int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const float *d_dev, float *img_dev,
+            int flags, void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!d_dev || !img_dev) return fail(ctx, DHFWI_ERR_ARG, "d_dev and img_dev must not be NULL");
+    if (flags != DHFWI_ABS && flags != DHFWI_REL) return fail(ctx, DHFWI_ERR_ARG, "flags must be DHFWI_ABS or DHFWI_REL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = get_plan(ctx, geom))) return rc;
+    if ((rc = prep_model(ctx, v0_dev, nullptr, 0, st))) return rc;
+    const Plan &P = ctx->plan;
+    int K = 0;
+    if ((rc = ensure_backward_ws(ctx, &K))) return rc;
+    const long long pool = P.pool_floats;
+    float *F = (float *)ctx->fields.p;
+    float *uA = F, *uB = F + pool, *nuA = F + 2 * pool, *nuB = F + 3 * pool, *gp = F + 4 * pool;
+    CK(cudaMemsetAsync(F, 0, sizeof(float) * 5 * (size_t)pool, st));
+    if ((rc = run_forward(ctx, uA, uB, nullptr, (float *)ctx->ck.p, K, st))) return rc;
+    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, nuA, nuB, gp, d_dev, st))) return rc;
+    launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
+                        ctx->g.nx, ctx->g.nb, v0_dev, flags == DHFWI_REL, img_dev, st);
+    ctx->stats.kernel_launches++;
+    return end_call(ctx);
+}
+
+}  // extern "C"
+
+// Accessors used by the network code in the same library.
+namespace dhfwi {
+NetState *&ctx_net(dhfwi_ctx *ctx) { return ctx->net; }
+int ctx_device(dhfwi_ctx *ctx) { return ctx->device; }
+void ctx_set_error(dhfwi_ctx *ctx, const char *msg) { ctx->err = msg; }
+void ctx_begin(dhfwi_ctx *ctx) {
+    ctx->err.clear();
+    ctx->stats.kernel_launches = 0;
+    ctx->stats.cell_updates = 0;
+}
+void ctx_count_launches(dhfwi_ctx *ctx, long long n) { ctx->stats.kernel_launches += n; }
+}  // namespace dhfwi

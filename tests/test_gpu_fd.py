@@ -1,0 +1,189 @@
+"""GPU parity of the finite-difference path against the FP64 oracle.
+
+Tolerances: wavefields, records and gradients relative L2 <= 1e-5; the
+FP32 dot-product test <= 1e-4.  All calls go through the C ABI
+(libdhfwi.so) via the ctypes binding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import f32, f32_geom, gpu_ctx, rel_l2, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _cases():
+    tiny = synth.tiny_case()
+    tiny2 = synth.tiny_case(nz=37, nx=141, nt=150, nb=20, n_shots=3, seed=8)
+    one = synth.tiny_case(nz=9, nx=11, nt=40, nb=4, n_shots=1, seed=2, windows=False)
+    return {"tiny": tiny, "ragged": tiny2, "single": one, "config1": synth.config1_case()}
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_model_shots_parity(name):
+    c = CASES[name]
+    ctx = gpu_ctx(c)
+    v, geom = f32(c.v_true), f32_geom(c.geom)
+    d_ref = oracle.model_shots(v, geom, c.h, c.dt, c.nb)
+    d = to_host(ctx.model_shots(to_dev(v), geom))
+    assert rel_l2(d, d_ref) <= TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fwi_gradient_parity(name):
+    c = CASES[name]
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom)
+    v0 = f32(c.v_init)
+    d_obs = f32(oracle.model_shots(f32(c.v_true), geom, c.h, c.dt, c.nb))
+    J_ref, g_ref, ds_ref = oracle.fwi_gradient(v0, geom, d_obs, c.h, c.dt, c.nb)
+    import torch
+
+    ds = torch.empty(geom.n_data, dtype=torch.float32, device="cuda")
+    J, g = ctx.fwi_gradient(to_dev(v0), geom, to_dev(d_obs), d_syn=ds)
+    assert rel_l2(to_host(ds), ds_ref) <= TOL
+    assert abs(J - J_ref) <= TOL * abs(J_ref)
+    assert rel_l2(to_host(g), g_ref) <= TOL
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged", "config1"])
+@pytest.mark.parametrize("rel", [False, True])
+def test_born_parity(name, rel):
+    c = CASES[name]
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom)
+    v0 = f32(c.v_init)
+    dv = f32(synth.smooth_random_field(c.nz, c.nx, 5) * (0.05 if rel else 100.0))
+    dv_abs = v0 * dv if rel else dv
+    d_ref = oracle.born_demig(v0, geom, dv_abs, c.h, c.dt, c.nb)
+    d = to_host(ctx.born_demig(to_dev(v0), geom, to_dev(dv), rel=rel))
+    assert rel_l2(d, d_ref) <= TOL
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged", "config1"])
+@pytest.mark.parametrize("rel", [False, True])
+def test_rtm_parity(name, rel):
+    c = CASES[name]
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom)
+    v0 = f32(c.v_init)
+    d = f32(synth.gaussian_field(geom.n_data, 11))
+    img_ref = oracle.rtm_mig(v0, geom, d, c.h, c.dt, c.nb)
+    if rel:
+        img_ref = img_ref * v0
+    img = to_host(ctx.rtm_mig(to_dev(v0), geom, to_dev(d), rel=rel))
+    assert rel_l2(img, img_ref) <= TOL
+
+
+@pytest.mark.parametrize("name", ["tiny", "config1"])
+def test_dot_product_fp32(name):
+    c = CASES[name]
+    ctx = gpu_ctx(c)
+    v0 = to_dev(c.v_init)
+    x = synth.gaussian_field((c.nz, c.nx), 23)
+    y = synth.gaussian_field(c.geom.n_data, 24)
+    Lx = to_host(ctx.born_demig(v0, c.geom, to_dev(x)))
+    LTy = to_host(ctx.rtm_mig(v0, c.geom, to_dev(y)))
+    a, b = float(np.dot(Lx, f32(y))), float(np.sum(f32(x) * LTy))
+    assert abs(a - b) <= 1e-4 * max(abs(a), abs(b))
+
+
+def test_gradient_equals_migration_of_residual():
+    c = CASES["tiny"]
+    ctx = gpu_ctx(c)
+    import torch
+
+    v0 = to_dev(c.v_init)
+    d_obs = ctx.model_shots(to_dev(c.v_true), c.geom)
+    ds = torch.empty_like(d_obs)
+    _, g = ctx.fwi_gradient(v0, c.geom, d_obs, d_syn=ds)
+    img = ctx.rtm_mig(v0, c.geom, ds - d_obs)
+    assert rel_l2(to_host(g), to_host(img)) <= 1e-6
+
+
+def test_deterministic():
+    c = CASES["ragged"]
+    ctx = gpu_ctx(c)
+    v0 = to_dev(c.v_init)
+    d_obs = ctx.model_shots(to_dev(c.v_true), c.geom)
+    J1, g1 = ctx.fwi_gradient(v0, c.geom, d_obs)
+    J2, g2 = ctx.fwi_gradient(v0, c.geom, d_obs)
+    assert J1 == J2
+    assert np.array_equal(to_host(g1), to_host(g2))
+
+
+def test_autograd_function():
+    c = CASES["tiny"]
+    ctx = gpu_ctx(c)
+    import torch
+
+    from paper_2403_17518_gb300.ops import FWIMisfit
+
+    d_obs = ctx.model_shots(to_dev(c.v_true), c.geom)
+    v = to_dev(c.v_init).requires_grad_(True)
+    J = FWIMisfit.apply(v, ctx, c.geom, d_obs)
+    (3.0 * J).backward()
+    _, g = ctx.fwi_gradient(to_dev(c.v_init), c.geom, d_obs)
+    assert torch.allclose(v.grad, 3.0 * g)
+
+
+def test_errors_are_reported():
+    c = CASES["tiny"]
+    ctx = gpu_ctx(c)
+    from paper_2403_17518_gb300.ops import DhfwiError
+
+    v = c.v_true.copy()
+    v[3, 4] = np.nan
+    with pytest.raises(DhfwiError, match="NONFINITE"):
+        ctx.model_shots(to_dev(v), c.geom)
+    with pytest.raises(DhfwiError, match="CFL"):
+        ctx.model_shots(to_dev(c.v_true * 40.0), c.geom)
+    bad = f32_geom(c.geom)
+    bad.src_ix = bad.src_ix.copy()
+    bad.src_ix[0] = c.nx + 5
+    with pytest.raises(DhfwiError, match="GEOM"):
+        ctx.model_shots(to_dev(c.v_true), bad)
+    # The context stays usable after errors.
+    d = ctx.model_shots(to_dev(c.v_true), c.geom)
+    assert np.isfinite(to_host(d)).all()
+
+
+# ---------------------------------------------------------------------------
+# Full-size workload (400 x 1200, 64 shots, nt 3000-4000): the batched launch
+# the benchmark times, checked on shots the oracle computes one by one.
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def config2():
+    return synth.config2_case()
+
+
+def test_config2_model_shots_sampled(config2):
+    c = config2
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom)
+    v = f32(c.v_true)
+    d = to_host(ctx.model_shots(to_dev(v), geom))
+    off = geom.data_offsets()
+    for s in (0, 37):  # shots run inside the full 64-shot batch
+        sub = geom.subset([s])
+        ref = oracle.model_shots(v, sub, c.h, c.dt, c.nb)
+        assert rel_l2(d[off[s]:off[s + 1]], ref) <= TOL, s
+
+
+def test_config2_gradient_two_shots(config2):
+    c = config2
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom).subset([5, 50])
+    v0 = f32(c.v_init)
+    d_obs = f32(oracle.model_shots(f32(c.v_true), geom, c.h, c.dt, c.nb))
+    J_ref, g_ref, _ = oracle.fwi_gradient(v0, geom, d_obs, c.h, c.dt, c.nb)
+    J, g = ctx.fwi_gradient(to_dev(v0), geom, to_dev(d_obs))
+    assert abs(J - J_ref) <= TOL * J_ref
+    assert rel_l2(to_host(g), g_ref) <= TOL
