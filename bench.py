@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 
 METRIC = "FD Gcell-updates/s & HBM roofline %; model error vs GPU-s, deblurred vs plain"
 UNIT = "Gcell-updates/s"
-FWD_BYTES_PER_CELL = 12  # read u^n, read u^{n-1}, write u^{n+1} (kappa is an L2-resident shared model)
+FWD_BYTES_PER_CELL = 16  # read u^n and D^n, write u^{n+1} and D^{n+1} (kappa: L2-resident shared model)
 
 
 def parse():
@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--only", default="", choices=["", "fwd"],
+                   help="fwd: time batched forward modelling (model_shots) alone; used for profiling")
     return p.parse_args()
 
 
@@ -275,6 +277,30 @@ def workload_config(case, args):
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
+def run_forward_only(args, dist, ctx, case, geom, v0, d_out):
+    """Batched forward modelling alone (model_shots), for kernel profiling."""
+    import torch
+
+    for _ in range(args.warmup):
+        ctx.model_shots(v0, geom, out=d_out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.model_shots(v0, geom, out=d_out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    U = case.geom.cell_updates(case.nz, case.nb)
+    st = ctx.stats()
+    if dist.rank == 0:
+        print(json.dumps({"only": "fwd", "workload": case.name, "ms_per_pass": round(ms, 3),
+                          "step_variants": st["step_variant"],
+                          "gcell_per_s": round(U / ms / 1e6, 3), "launches_per_pass": st["kernel_launches"],
+                          "bytes_per_cell": 16, "effective_GBps": round(16 * U / ms / 1e6, 1)}), flush=True)
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -297,6 +323,11 @@ def main():
     v_true = torch.tensor(case.v_true, dtype=torch.float32, device=dev)
     v0 = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
     d_obs = ctx.model_shots(v_true, geom)
+    if args.only == "fwd":
+        run_forward_only(args, dist, ctx, case, geom, v0, d_obs)
+        ctx.close()
+        dist.close()
+        return
     grad = ctx.new_model()
     dm1 = ctx.new_model()
     d_born = ctx.new_data(geom)
@@ -407,6 +438,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches[0]),
+            "step_variants": ctx.stats()["step_variant"],
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

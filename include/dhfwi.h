@@ -108,6 +108,9 @@ typedef struct {
     double phase_ms[3];
     long long phase_launches[3];
     long long phase_cells[3];  /* cell updates in that phase (Born counts 2 per cell) */
+    /* Step-kernel variant chosen by the autotuner for: forward, forward with
+     * segment store, adjoint, Born (index into the library's variant table). */
+    int step_variant[4];
 } dhfwi_stats_t;
 
 /* Create a context on CUDA device `device` for grid `g`.  The context owns all

@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("cell_updates", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
                 ("checkpoint_every", ctypes.c_int), ("shot_groups", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_double), ("phase_ms", ctypes.c_double * 3),
-                ("phase_launches", ctypes.c_longlong * 3), ("phase_cells", ctypes.c_longlong * 3)]
+                ("phase_launches", ctypes.c_longlong * 3), ("phase_cells", ctypes.c_longlong * 3),
+                ("step_variant", ctypes.c_int * 4)]
 
 
 class TrainCfg(ctypes.Structure):

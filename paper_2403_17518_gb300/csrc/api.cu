@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -50,7 +51,7 @@ struct dhfwi_ctx {
     int pf = 0;             // pitch of padded model arrays
     int NZ = 0, NXF = 0;
     Plan plan;
-    DevBuf kap, vpad, dkap, status, partial;
+    DevBuf kap, vpad, g2v, dkap, status, partial;
     DevBuf fields;          // general wavefield pools
     DevBuf ck;              // checkpoints
     DevBuf abuf;            // segment buffer of a^n
@@ -61,6 +62,11 @@ struct dhfwi_ctx {
     dhfwi_stats_t stats{};
     dhfwi::NetState *net = nullptr;
     bool timing = false;
+    // Step-kernel launch choice per kind: forward, forward+segment store,
+    // adjoint, Born.  Picked by autotune() for the current plan.
+    StepLaunch launch[4];
+    unsigned long long tuned_hash = 0;
+    int nsm = 1;
     cudaEvent_t ev[3][2] = {};
     bool ev_used[3] = {};
 };
@@ -68,6 +74,7 @@ struct dhfwi_ctx {
 namespace {
 
 constexpr int RESID_BLOCKS = 1024;
+constexpr int NPOOLS = 7;  // field pools: u (2) + D, nu (2) + D_nu, image
 
 int fail(dhfwi_ctx *ctx, int code, const std::string &msg) {
     if (ctx) ctx->err = msg;
@@ -224,7 +231,7 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
         ShotDesc &sd = P.shots[k];
         const int x0 = G->win_x0[s], x1 = G->win_x1[s];
         sd.nxw = x1 - x0 + 2 * nb;
-        sd.pitch = round_up(sd.nxw, 32);
+        sd.pitch = round_up(sd.nxw, POOL_ALIGN);
         sd.foff = foff;
         foff += (long long)sd.pitch * NZ;
         sd.doff = doff[s];
@@ -291,6 +298,8 @@ StepCommon common(dhfwi_ctx *ctx) {
     c.recs = (const TileRec *)ctx->plan.d_recs.p;
     c.kap = (const float *)ctx->kap.p;
     c.vpad = (const float *)ctx->vpad.p;
+    c.g2v = (const float *)ctx->g2v.p;
+    c.mstride = (long long)ctx->NZ * ctx->pf;
     c.wav = (const float *)ctx->plan.d_wav.p;
     c.pf = ctx->pf;
     c.NZ = ctx->NZ;
@@ -303,13 +312,15 @@ int prep_model(dhfwi_ctx *ctx, const float *v, const float *dv, int rel, cudaStr
     if (!v) return fail(ctx, DHFWI_ERR_ARG, "velocity pointer is NULL");
     size_t mb = sizeof(float) * (size_t)ctx->NZ * ctx->pf;
     int rc;
-    if ((rc = ensure(ctx, ctx->kap, mb, "kappa"))) return rc;
+    if ((rc = ensure(ctx, ctx->kap, 4 * mb, "kappa"))) return rc;
     if ((rc = ensure(ctx, ctx->vpad, mb, "padded velocity"))) return rc;
-    if (dv && (rc = ensure(ctx, ctx->dkap, mb, "d kappa"))) return rc;
+    if ((rc = ensure(ctx, ctx->g2v, 4 * mb, "padded 2/v"))) return rc;
+    if (dv && (rc = ensure(ctx, ctx->dkap, 4 * mb, "d kappa"))) return rc;
     CK(cudaMemsetAsync(ctx->status.p, 0, 2 * sizeof(unsigned), st));
-    const float c = (ctx->g.dt * ctx->g.dt) / (ctx->g.h * ctx->g.h);
+    const double c = ((double)ctx->g.dt * ctx->g.dt) / ((double)ctx->g.h * ctx->g.h);
     launch_prep_model(v, dv, rel, ctx->g.nz, ctx->g.nx, ctx->g.nb, c, (float *)ctx->kap.p,
-                      (float *)ctx->vpad.p, dv ? (float *)ctx->dkap.p : nullptr, ctx->pf,
+                      (float *)ctx->vpad.p, (float *)ctx->g2v.p, dv ? (float *)ctx->dkap.p : nullptr, ctx->pf,
+                      (long long)ctx->NZ * ctx->pf,
                       (unsigned *)ctx->status.p, st);
     ctx->stats.kernel_launches++;
     CK(cudaGetLastError());
@@ -369,50 +380,158 @@ int end_call(dhfwi_ctx *ctx) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
     ctx->stats.checkpoint_every = ctx->ck_every;
+    for (int k = 0; k < 4; k++) ctx->stats.step_variant[k] = ctx->launch[k].variant;
     double ws = ctx->kap.bytes + ctx->vpad.bytes + ctx->dkap.bytes + ctx->fields.bytes + ctx->ck.bytes +
                 ctx->abuf.bytes + ctx->dtmp.bytes + ctx->rtmp.bytes;
     ctx->stats.workspace_bytes = ws;
     return DHFWI_OK;
 }
 
-// Forward pass over all steps.  u pools A/B must be zeroed by the caller.
-// d (nullable) receives samples; ck (nullable) receives checkpoints every K.
-int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *d, float *ck, int K, cudaStream_t st) {
+void set_variant(dhfwi_ctx *ctx, int kind, int v) {
+    static const int kernel_kind[4] = {0, 0, 1, 2};
+    ctx->launch[kind].variant = v;
+    ctx->launch[kind].max_ctas = step_occupancy(kernel_kind[kind], v, kind == 1) * ctx->nsm;
+    cudaGetLastError();
+}
+
+// Autotuner: for the current plan, time every step-kernel variant of each
+// kind on the plan's full tile list (all shots active) using the scratch
+// field pools, and keep the fastest.  The pools are zeroed again by the call
+// that follows, so tuning leaves no trace in the results.  Runs once per
+// geometry; DHFWI_STEP_VARIANT=<0..2> pins a variant instead.
+int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
+    const Plan &P = ctx->plan;
+    if (ctx->tuned_hash == P.hash) return DHFWI_OK;
+    const char *pin = getenv("DHFWI_STEP_VARIANT");
+    if (pin && *pin) {
+        const int v = atoi(pin);
+        for (int k = 0; k < 4; k++) set_variant(ctx, k, v < 0 || v >= N_STEP_VARIANTS ? 1 : v);
+        ctx->tuned_hash = P.hash;
+        return DHFWI_OK;
+    }
+    const long long pool = P.pool_floats;
+    int rc = ensure(ctx, ctx->fields, NPOOLS * sizeof(float) * (size_t)pool, "wavefield pools");
+    if (rc) return rc;
+    if ((rc = ensure(ctx, ctx->rtmp, sizeof(float) * std::max<long long>(P.n_data, 1), "residual"))) return rc;
+    if ((rc = ensure(ctx, ctx->dtmp, sizeof(float) * std::max<long long>(P.n_data, 1), "synthetic data")))
+        return rc;
+    float *F = (float *)ctx->fields.p;
+    CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
+    CK(cudaMemsetAsync(ctx->rtmp.p, 0, sizeof(float) * std::max<long long>(P.n_data, 1), st));
+    const int ntiles = active_tiles(P, 0);
+    const int reps = 4;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int kind = 0; kind < 4; kind++) {
+        float best = 1e30f;
+        int best_v = 1;
+        for (int v = 0; v < N_STEP_VARIANTS; v++) {
+            set_variant(ctx, kind, v);
+            float ms = 0.f;
+            for (int rep = -1; rep < reps; rep++) {
+                if (rep == 0) cudaEventRecord(e0, st);
+                if (kind <= 1) {
+                    FwdArgs a{};
+                    a.c = common(ctx);
+                    a.u = F;
+                    a.un = F + pool;
+                    a.dd = F + 2 * pool;
+                    a.a_out = kind == 1 ? F + 3 * pool : nullptr;
+                    a.d = kind == 0 ? (float *)ctx->dtmp.p : nullptr;
+                    a.n = 0;
+                    launch_fwd_step(a, ntiles, ctx->launch[kind], st);
+                } else if (kind == 2) {
+                    AdjArgs b{};
+                    b.c = common(ctx);
+                    b.nu = F;
+                    b.nun = F + pool;
+                    b.dd = F + 2 * pool;
+                    b.a = F + 3 * pool;
+                    b.g = F + 4 * pool;
+                    b.r = (const float *)ctx->rtmp.p;
+                    b.k = 1;
+                    launch_adj_step(b, ntiles, ctx->launch[kind], st);
+                } else {
+                    BornArgs b{};
+                    b.c = common(ctx);
+                    b.u = F;
+                    b.un = F + pool;
+                    b.du = F + 2 * pool;
+                    b.p = F + 3 * pool;
+                    b.pn = F + 4 * pool;
+                    b.dp = F + 5 * pool;
+                    b.dkap = (const float *)ctx->kap.p;
+                    b.d = (float *)ctx->dtmp.p;
+                    b.n = 0;
+                    launch_born_step(b, ntiles, ctx->launch[kind], st);
+                }
+            }
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(ctx, e, "autotune");
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        set_variant(ctx, kind, best_v);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->stats.kernel_launches += 4LL * N_STEP_VARIANTS * (reps + 1);
+    ctx->tuned_hash = P.hash;
+    CK(cudaGetLastError());
+    return DHFWI_OK;
+}
+
+// Forward pass over all steps.  State pools uA (u^0), uB (scratch) and dd
+// (D^0) must be zeroed by the caller.  d (nullable) receives samples; ck
+// (nullable) receives (u^n, D^n) every K steps, two pools per checkpoint.
+int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *d, float *ck, int K, cudaStream_t st) {
     const Plan &P = ctx->plan;
     FwdArgs a{};
     a.c = common(ctx);
-    float *cur = uA, *old = uB;
+    float *cur = uA, *nxt = uB;
     const long long pool = P.pool_floats;
     const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
     phase_begin(ctx, 0, st);
     for (int n = 0; n < P.nt_max; n++) {
         const int nt = active_tiles(P, n);
         a.u = cur;
-        a.uo = old;
+        a.un = nxt;
+        a.dd = dd;
         a.d = d;
         a.a_out = nullptr;
         if (ck && n % K == 0) {
             const long long j = n / K;
-            a.ck_old = ck + (2 * j) * pool;
-            a.ck_cur = ck + (2 * j + 1) * pool;
+            a.ck_u = ck + (2 * j) * pool;
+            a.ck_d = ck + (2 * j + 1) * pool;
         } else {
-            a.ck_old = a.ck_cur = nullptr;
+            a.ck_u = a.ck_d = nullptr;
         }
         a.n = n;
-        launch_fwd_step(a, nt, st);
+        launch_fwd_step(a, nt, ctx->launch[0], st);
         ctx->stats.kernel_launches++;
         ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
-        std::swap(cur, old);
+        std::swap(cur, nxt);
     }
     phase_end(ctx, 0, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
     CK(cudaGetLastError());
     return DHFWI_OK;
 }
 
-// Backward sweep: recompute each segment from its checkpoint, then the
+// Backward sweep: recompute each segment from its checkpoint (u in the
+// checkpoint and the work pool w, D in place in the checkpoint), then the
 // adjoint steps over it with the data r injected; image accumulated in gpool.
-int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *nuA, float *nuB, float *gpool,
-                 const float *r, cudaStream_t st) {
+// Adjoint state pools nuA, nuB, nud must be zeroed by the caller.
+int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float *nuA, float *nuB, float *nud,
+                 float *gpool, const float *r, cudaStream_t st) {
     const Plan &P = ctx->plan;
     const long long pool = P.pool_floats;
     const int nseg = (P.nt_max + K - 1) / K;
@@ -422,34 +541,36 @@ int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *nuA, floa
     b.c = f.c;
     b.r = r;
     b.g = gpool;
-    float *ncur = nuA, *nold = nuB;
+    b.dd = nud;
+    float *ncur = nuA, *nnxt = nuB;
     const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
     phase_begin(ctx, 1, st);
     for (int js = nseg - 1; js >= 0; js--) {
         const int n0 = js * K, n1 = std::min(n0 + K, P.nt_max);
-        float *cur = ck + (2 * (long long)js + 1) * pool;
-        float *old = ck + (2 * (long long)js) * pool;
+        float *cur = ck + (2 * (long long)js) * pool;
+        float *nxt = w;
+        f.dd = ck + (2 * (long long)js + 1) * pool;
         for (int n = n0; n < n1; n++) {
             f.u = cur;
-            f.uo = old;
+            f.un = nxt;
             f.a_out = abuf + (long long)(n - n0) * pool;
             f.d = nullptr;
-            f.ck_old = f.ck_cur = nullptr;
+            f.ck_u = f.ck_d = nullptr;
             f.n = n;
-            launch_fwd_step(f, active_tiles(P, n), st);
+            launch_fwd_step(f, active_tiles(P, n), ctx->launch[1], st);
             ctx->stats.kernel_launches++;
             ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
-            std::swap(cur, old);
+            std::swap(cur, nxt);
         }
         for (int k = n1; k >= n0 + 1; k--) {
             b.nu = ncur;
-            b.nuo = nold;
+            b.nun = nnxt;
             b.a = abuf + (long long)(k - 1 - n0) * pool;
             b.k = k;
-            launch_adj_step(b, active_tiles(P, k - 1), st);
+            launch_adj_step(b, active_tiles(P, k - 1), ctx->launch[2], st);
             ctx->stats.kernel_launches++;
             ctx->stats.cell_updates += active_cells(P, k - 1, ctx->NZ);
-            std::swap(ncur, nold);
+            std::swap(ncur, nnxt);
         }
         CK(cudaGetLastError());
     }
@@ -463,7 +584,7 @@ int ensure_backward_ws(dhfwi_ctx *ctx, int *K_out) {
     const Plan &P = ctx->plan;
     const size_t pool = sizeof(float) * (size_t)P.pool_floats;
     int K = ctx->ck_every;
-    int rc = ensure(ctx, ctx->fields, 5 * pool, "wavefield pools");
+    int rc = ensure(ctx, ctx->fields, NPOOLS * pool, "wavefield pools");
     if (rc) return rc;
     for (int attempt = 0; attempt < 2; attempt++) {
         const int nseg = (P.nt_max + K - 1) / K;
@@ -521,7 +642,10 @@ int dhfwi_create(dhfwi_ctx **out, const dhfwi_grid *g, int device) {
     ctx->g = *g;
     ctx->NZ = g->nz + 2 * g->nb;
     ctx->NXF = g->nx + 2 * g->nb;
-    ctx->pf = round_up(ctx->NXF, 32);
+    ctx->pf = round_up(ctx->NXF + 4, 32);
+    cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
+    cudaGetLastError();
+    for (int k = 0; k < 4; k++) set_variant(ctx, k, 1);
     if (ensure(ctx, ctx->status, 64, "status") || ensure(ctx, ctx->partial, sizeof(double) * RESID_BLOCKS, "partials") ||
         cudaMallocHost(&ctx->h_status, 64) != cudaSuccess ||
         cudaMallocHost(&ctx->h_partial, sizeof(double) * RESID_BLOCKS) != cudaSuccess) {
@@ -536,7 +660,7 @@ int dhfwi_create(dhfwi_ctx **out, const dhfwi_grid *g, int device) {
 void dhfwi_destroy(dhfwi_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
-    DevBuf *bufs[] = {&ctx->kap, &ctx->vpad, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
+    DevBuf *bufs[] = {&ctx->kap, &ctx->vpad, &ctx->g2v, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
                       &ctx->ck, &ctx->abuf, &ctx->dtmp, &ctx->rtmp, &ctx->plan.d_shots, &ctx->plan.d_tiles,
                       &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav};
     for (DevBuf *b : bufs) release(*b);
@@ -583,11 +707,12 @@ int model_shots(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, floa
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = get_plan(ctx, geom))) return rc;
     if ((rc = prep_model(ctx, v_dev, nullptr, 0, st))) return rc;
+    if ((rc = autotune(ctx, st))) return rc;
     const size_t pool = sizeof(float) * (size_t)ctx->plan.pool_floats;
-    if ((rc = ensure(ctx, ctx->fields, 5 * pool, "wavefield pools"))) return rc;
-    float *uA = (float *)ctx->fields.p, *uB = uA + ctx->plan.pool_floats;
-    CK(cudaMemsetAsync(uA, 0, 2 * pool, st));
-    if ((rc = run_forward(ctx, uA, uB, d_dev, nullptr, 1, st))) return rc;
+    if ((rc = ensure(ctx, ctx->fields, NPOOLS * pool, "wavefield pools"))) return rc;
+    float *uA = (float *)ctx->fields.p, *uB = uA + ctx->plan.pool_floats, *ud = uB + ctx->plan.pool_floats;
+    CK(cudaMemsetAsync(uA, 0, 3 * pool, st));
+    if ((rc = run_forward(ctx, uA, uB, ud, d_dev, nullptr, 1, st))) return rc;
     return end_call(ctx);
 }
 
@@ -599,6 +724,7 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = get_plan(ctx, geom))) return rc;
     if ((rc = prep_model(ctx, v_dev, nullptr, 0, st))) return rc;
+    if ((rc = autotune(ctx, st))) return rc;
     const Plan &P = ctx->plan;
     int K = 0;
     if ((rc = ensure_backward_ws(ctx, &K))) return rc;
@@ -611,13 +737,15 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     }
     const long long pool = P.pool_floats;
     float *F = (float *)ctx->fields.p;
-    float *uA = F, *uB = F + pool, *nuA = F + 2 * pool, *nuB = F + 3 * pool, *gp = F + 4 * pool;
-    CK(cudaMemsetAsync(F, 0, sizeof(float) * 5 * (size_t)pool, st));
-    if ((rc = run_forward(ctx, uA, uB, dsyn, (float *)ctx->ck.p, K, st))) return rc;
+    float *uA = F, *uB = F + pool, *ud = F + 2 * pool;
+    float *nuA = F + 3 * pool, *nuB = F + 4 * pool, *nud = F + 5 * pool, *gp = F + 6 * pool;
+    CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
+    if ((rc = run_forward(ctx, uA, uB, ud, dsyn, (float *)ctx->ck.p, K, st))) return rc;
     float *r = (float *)ctx->rtmp.p;
     launch_residual(dsyn, d_obs_dev, r, (long long)nd, (double *)ctx->partial.p, RESID_BLOCKS, st);
     ctx->stats.kernel_launches++;
-    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, nuA, nuB, gp, r, st))) return rc;
+    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, nuA, nuB, nud, gp, r, st)))
+        return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v_dev, 0, grad_dev, st);
     ctx->stats.kernel_launches++;
@@ -643,29 +771,32 @@ int born_demig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, cons
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = get_plan(ctx, geom))) return rc;
     if ((rc = prep_model(ctx, v0_dev, dv_dev, flags == DHFWI_REL, st))) return rc;
+    if ((rc = autotune(ctx, st))) return rc;
     const Plan &P = ctx->plan;
     const long long pool = P.pool_floats;
-    if ((rc = ensure(ctx, ctx->fields, 5 * sizeof(float) * (size_t)pool, "wavefield pools"))) return rc;
+    if ((rc = ensure(ctx, ctx->fields, NPOOLS * sizeof(float) * (size_t)pool, "wavefield pools"))) return rc;
     float *F = (float *)ctx->fields.p;
-    CK(cudaMemsetAsync(F, 0, sizeof(float) * 4 * (size_t)pool, st));
+    CK(cudaMemsetAsync(F, 0, sizeof(float) * 6 * (size_t)pool, st));
     BornArgs a{};
     a.c = common(ctx);
     a.dkap = (const float *)ctx->dkap.p;
     a.d = d_dev;
-    float *u = F, *uo = F + pool, *p = F + 2 * pool, *po = F + 3 * pool;
+    float *u = F, *un = F + pool, *p = F + 2 * pool, *pn = F + 3 * pool;
+    a.du = F + 4 * pool;
+    a.dp = F + 5 * pool;
     const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
     phase_begin(ctx, 2, st);
     for (int n = 0; n < P.nt_max; n++) {
         a.u = u;
-        a.uo = uo;
+        a.un = un;
         a.p = p;
-        a.po = po;
+        a.pn = pn;
         a.n = n;
-        launch_born_step(a, active_tiles(P, n), st);
+        launch_born_step(a, active_tiles(P, n), ctx->launch[3], st);
         ctx->stats.kernel_launches++;
         ctx->stats.cell_updates += 2 * active_cells(P, n, ctx->NZ);
-        std::swap(u, uo);
-        std::swap(p, po);
+        std::swap(u, un);
+        std::swap(p, pn);
     }
     phase_end(ctx, 2, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
     return end_call(ctx);
@@ -680,15 +811,18 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = get_plan(ctx, geom))) return rc;
     if ((rc = prep_model(ctx, v0_dev, nullptr, 0, st))) return rc;
+    if ((rc = autotune(ctx, st))) return rc;
     const Plan &P = ctx->plan;
     int K = 0;
     if ((rc = ensure_backward_ws(ctx, &K))) return rc;
     const long long pool = P.pool_floats;
     float *F = (float *)ctx->fields.p;
-    float *uA = F, *uB = F + pool, *nuA = F + 2 * pool, *nuB = F + 3 * pool, *gp = F + 4 * pool;
-    CK(cudaMemsetAsync(F, 0, sizeof(float) * 5 * (size_t)pool, st));
-    if ((rc = run_forward(ctx, uA, uB, nullptr, (float *)ctx->ck.p, K, st))) return rc;
-    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, nuA, nuB, gp, d_dev, st))) return rc;
+    float *uA = F, *uB = F + pool, *ud = F + 2 * pool;
+    float *nuA = F + 3 * pool, *nuB = F + 4 * pool, *nud = F + 5 * pool, *gp = F + 6 * pool;
+    CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
+    if ((rc = run_forward(ctx, uA, uB, ud, nullptr, (float *)ctx->ck.p, K, st))) return rc;
+    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, nuA, nuB, nud, gp, d_dev, st)))
+        return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v0_dev, flags == DHFWI_REL, img_dev, st);
     ctx->stats.kernel_launches++;

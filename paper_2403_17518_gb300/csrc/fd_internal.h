@@ -8,14 +8,15 @@
 namespace dhfwi {
 
 // Stencil tile handled by one CTA: TZ rows x TX columns of one shot window.
+// A CTA has 32 x (TZ/R) threads; each thread owns two adjacent columns and
+// R consecutive rows (R is a property of the kernel variant).  Tiles are
+// staged through double-buffered shared memory with cp.async.
 constexpr int TX = 64;
-constexpr int TZ = 32;
+constexpr int TZ = 64;
 constexpr int HALO = 4;          // radius of the 8th-order stencil
-constexpr int NTHR_X = 64;       // threads per CTA along x (one column each)
-constexpr int NTHR_Z = 4;        // threads per CTA along z
-constexpr int ROWS_PER_THR = TZ / NTHR_Z;
 constexpr int SROW = TX + 2 * HALO;   // shared-memory row length (floats)
 constexpr int SROWS = TZ + 2 * HALO;
+constexpr int POOL_ALIGN = TX;   // row pitch of a window is a multiple of this
 
 // Per-shot descriptor, indexed by "slot" (shots sorted by record length,
 // longest first, so that the shots still running at step n are a prefix).
@@ -23,7 +24,7 @@ struct ShotDesc {
     long long foff;   // offset (floats) of this shot's window inside a field pool
     long long doff;   // offset of this shot's block in the packed data vector
     int nxw;          // padded window width (cells) = win_x1 - win_x0 + 2 nb
-    int pitch;        // row pitch of the window in a field pool (floats)
+    int pitch;        // row pitch of the window in a field pool (floats, multiple of TX)
     int x0;           // padded-model column of the window's column 0 (= win_x0)
     int sz, sx;       // source node, padded window coordinates
     int nt;           // record length
@@ -49,34 +50,49 @@ struct StepCommon {
     const ShotDesc *shots;
     const Tile *tiles;
     const TileRec *recs;
-    const float *kap;     // [NZ][pf] padded model, kappa = v^2 dt^2/h^2
-    const float *vpad;    // [NZ][pf] padded model velocity
+    // Padded model arrays [NZ][pf]; kap, g2v and dkap hold four copies
+    // (mstride floats apart): copy r is copy 0 shifted left by r columns.
+    const float *kap;     // kappa = v^2 dt^2/h^2
+    const float *vpad;    // velocity (one copy)
+    const float *g2v;     // 2 / v (imaging-condition factor)
+    long long mstride;    // floats between consecutive copies
     const float *wav;     // wavelets
     int pf;               // pitch of the padded model arrays
     int NZ;               // padded rows = nz + 2 nb
     int nb;
 };
 
+// Every propagated field is kept in "summed" form: the field u^n and its
+// damped time difference D^n = u^n - w u^{n-1}.  The recurrence
+//   u^{n+1} = w (2 u^n + kappa a^n) - w^2 u^{n-1}
+// is then, exactly,
+//   D^{n+1} = w (D^n + kappa a^n),   u^{n+1} = w u^n + D^{n+1}.
+// u is double buffered (neighbours read u^n while u^{n+1} is written); D is
+// updated in place.
+
 // Forward step n over the active tiles (grid = number of active tiles).
 struct FwdArgs {
     StepCommon c;
     const float *u;   // pool: u^n
-    float *uo;        // pool: u^{n-1}, overwritten with u^{n+1}
-    float *ck_old;    // nullable: store u^{n-1} here (checkpoint)
-    float *ck_cur;    // nullable: store u^n here (checkpoint)
-    float *a_out;     // nullable: store a^n = D u^n + q^n here (segment buffer slot)
+    float *un;        // pool: u^{n+1} (written)
+    float *dd;        // pool: D^n, overwritten with D^{n+1}
+    float *ck_u;      // nullable: store u^n here (checkpoint)
+    float *ck_d;      // nullable: store D^n here (checkpoint)
+    float *a_out;     // nullable: store (2/v) a^n, a^n = D u^n + q^n (segment buffer slot)
     float *d;         // nullable: packed records, sample n written from u^{n+1}
     int n;
 };
 
-// Adjoint step k (scaled field nu = kappa w lambda, which obeys the forward
-// recurrence with the data injected like the source).
+// Adjoint step k for the scaled multiplier nu = kappa w lambda, which obeys
+// the forward recurrence with the data injected like the source, in the same
+// summed form.
 struct AdjArgs {
     StepCommon c;
     const float *nu;      // pool: nu^{k+1}
-    float *nuo;           // pool: nu^{k+2}, overwritten with nu^k
+    float *nun;           // pool: nu^k (written)
+    float *dd;            // pool: D_nu^{k+1}, overwritten with D_nu^k
     const float *r;       // packed data injected at the receivers (sample k-1)
-    const float *a;       // pool: a^{k-1} of the background forward field
+    const float *a;       // pool: (2/v) a^{k-1} of the background forward field
     float *g;             // pool: per-shot image accumulator, += (2/v) a^{k-1} nu^k
     int k;
 };
@@ -84,23 +100,38 @@ struct AdjArgs {
 // Born joint step n: background u0 and scattered p advance together.
 struct BornArgs {
     StepCommon c;
-    const float *u;   float *uo;     // background pools (u0^n, u0^{n-1} -> u0^{n+1})
-    const float *p;   float *po;     // scattered pools
-    const float *dkap;               // [NZ][pf] padded d kappa = 2 kappa dv / v
-    float *d;                        // packed Born records (sample n from p^{n+1})
+    const float *u;  float *un;  float *du;   // background: u0^n, u0^{n+1}, D_u0 in place
+    const float *p;  float *pn;  float *dp;   // scattered:  p^n,  p^{n+1},  D_p in place
+    const float *dkap;                         // padded d kappa = 2 kappa dv / v (four copies)
+    float *d;                                  // packed Born records (sample n from p^{n+1})
     int n;
 };
 
-void launch_fwd_step(const FwdArgs &a, int ntiles, cudaStream_t s);
-void launch_adj_step(const AdjArgs &a, int ntiles, cudaStream_t s);
-void launch_born_step(const BornArgs &a, int ntiles, cudaStream_t s);
+// Step-kernel variants: rows per thread (2, 4 or 8; CTA = 32 x 64/R
+// threads).  The autotuner in api.cu times them per geometry.
+constexpr int N_STEP_VARIANTS = 3;
+int step_variant_rows(int v);
+// Resident CTAs per SM of a step kernel; kind 0 forward, 1 adjoint, 2 Born.
+int step_occupancy(int kind, int variant, int store_a);
+
+struct StepLaunch {
+    int variant = 1;     // index into the variant table
+    int max_ctas = 152;  // persistent grid cap = resident CTAs per SM x SMs
+};
+
+// Persistent launches: grid = min(ntiles, max_ctas); each CTA walks the tile
+// list with a stride of gridDim.x.
+void launch_fwd_step(const FwdArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s);
+void launch_adj_step(const AdjArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s);
+void launch_born_step(const BornArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s);
 
 // Padded model preparation: kap, vpad (and dkap when dv != nullptr) from the
-// physical [nz][nx] model; also checks v (finite, > 0) and records max kappa.
+// physical [nz][nx] model, columns [0, pf) (clamped beyond the model); also
+// checks v (finite, > 0) and records max kappa.
 // status[0] |= 1 for a bad velocity; status[1] = bits of max kappa (float).
-void launch_prep_model(const float *v, const float *dv, int rel, int nz, int nx, int nb, float c,
-                       float *kap, float *vpad, float *dkap, int pf, unsigned *status,
-                       cudaStream_t s);
+void launch_prep_model(const float *v, const float *dv, int rel, int nz, int nx, int nb, double c,
+                       float *kap, float *vpad, float *g2v, float *dkap, int pf, long long mstride,
+                       unsigned *status, cudaStream_t s);
 
 // r = d_syn - d_obs, and per-block partial sums of r^2 (double).
 void launch_residual(const float *ds, const float *dobs, float *r, long long n, double *partial,

@@ -7,8 +7,16 @@
 // acoustic): with kappa = v^2 dt^2/h^2, D the unscaled 8th-order Laplacian,
 // q^n the source sample at the source node and w the Cerjan sponge factor,
 //     a^n = D u^n + q^n,  u^{n+1} = w (2u^n + kappa a^n) - w^2 u^{n-1}.
+// Computed in FP32 in two algebraically exact rearrangements that keep the
+// rounding error of long records small:
+//  * summed form: D^{n+1} = w (D^n + kappa a^n), u^{n+1} = w u^n + D^{n+1},
+//    with D^n = u^n - w u^{n-1} stored instead of u^{n-1} (the small time
+//    difference is never recovered from two nearly equal fields);
+//  * difference-form Laplacian: since c0 + 2 sum c_k = 0 on each axis,
+//    D u = sum_k c_k [(u_{+k} - u) + (u_{-k} - u)] over both axes, a sum of
+//    small terms for smooth fields instead of large cancelling ones.
 //
-// Adjoint: the exact transpose of that recurrence, written for the scaled
+// Adjoint: the exact transpose of the recurrence, written for the scaled
 // field nu = kappa w lambda, obeys the same recurrence with the data injected
 // where the source is, and gives the velocity gradient (Eq. 13 with the sign
 // of dJ/dv) as sum_k (2/v) a^{k-1} nu^k.
@@ -22,221 +30,524 @@
 
 namespace dhfwi {
 
-// 8th-order central second-difference weights for unit spacing.
-#define FD_C0 (-205.0f / 72.0f)
+// 8th-order central second-difference weights for unit spacing (c0 is
+// implied by c0 = -2 (c1 + c2 + c3 + c4)).
 #define FD_C1 (8.0f / 5.0f)
 #define FD_C2 (-1.0f / 5.0f)
 #define FD_C3 (8.0f / 315.0f)
 #define FD_C4 (-1.0f / 560.0f)
 
-constexpr int NTHREADS = NTHR_X * NTHR_Z;
-
 typedef float STile[SROWS][SROW];
+typedef float CTile[TZ][TX];
 
-__device__ __forceinline__ void load_tile(STile &s, const float *__restrict__ f, const ShotDesc &sd,
-                                          int NZ, int z0, int x0) {
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (16 bytes, zero-filled past src_bytes)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// Field tile with halo: rows [z0-4, z0+TZ+4) x columns [x0-4, x0+TX+4) of a
+// shot window, zero outside [0,NZ) x [0,nxw).  x0 and the pitch are
+// multiples of TX, so every 16-byte chunk is aligned.
+template <int NT>
+__device__ __forceinline__ void issue_halo_tile(STile &s, const float *__restrict__ f, const ShotDesc &sd,
+                                                int NZ, int z0, int x0) {
     const float *base = f + sd.foff;
-    const int tid = threadIdx.x + threadIdx.y * NTHR_X;
-    for (int idx = tid; idx < SROWS * SROW; idx += NTHREADS) {
-        const int r = idx / SROW;
-        const int cc = idx - r * SROW;
+    const int tid = threadIdx.x + threadIdx.y * 32;
+    constexpr int Q = SROW / 4;
+    for (int idx = tid; idx < SROWS * Q; idx += NT) {
+        const int r = idx / Q;
+        const int q = idx - r * Q;
         const int gz = z0 - HALO + r;
-        const int gx = x0 - HALO + cc;
-        float val = 0.f;
-        if (gz >= 0 && gz < NZ && gx >= 0 && gx < sd.nxw) val = base[(long long)gz * sd.pitch + gx];
-        s[r][cc] = val;
+        const int gx = x0 - HALO + 4 * q;
+        const bool in = gz >= 0 && gz < NZ && gx >= 0 && gx < sd.nxw;
+        const int bytes = in ? min(16, 4 * (sd.nxw - gx)) : 0;
+        cp_async16(&s[r][4 * q], in ? base + gz * sd.pitch + gx : f, bytes);
     }
 }
 
-// D u at tile-local (lz, lx).
-__device__ __forceinline__ float lap8(const STile &s, int lz, int lx) {
-    const int z = lz + HALO, x = lx + HALO;
-    float acc = (2.0f * FD_C0) * s[z][x];
-    acc = fmaf(FD_C1, (s[z][x - 1] + s[z][x + 1]) + (s[z - 1][x] + s[z + 1][x]), acc);
-    acc = fmaf(FD_C2, (s[z][x - 2] + s[z][x + 2]) + (s[z - 2][x] + s[z + 2][x]), acc);
-    acc = fmaf(FD_C3, (s[z][x - 3] + s[z][x + 3]) + (s[z - 3][x] + s[z + 3][x]), acc);
-    acc = fmaf(FD_C4, (s[z][x - 4] + s[z][x + 4]) + (s[z - 4][x] + s[z + 4][x]), acc);
-    return acc;
+// Interior tile (rows [z0, z0+TZ), columns [x0, x0+TX)) of a per-shot pool
+// (window layout) or of a padded-model array (mcol0 = first model column of
+// the window rounded down to a multiple of 4, in the copy shifted by the rest).
+template <int NT>
+__device__ __forceinline__ void issue_cell_tile(CTile &s, const float *__restrict__ base, int pitch, int NZ,
+                                                int nxw, int z0, int x0) {
+    const int tid = threadIdx.x + threadIdx.y * 32;
+    constexpr int Q = TX / 4;
+    for (int idx = tid; idx < TZ * Q; idx += NT) {
+        const int r = idx / Q;
+        const int q = idx - r * Q;
+        const int gz = z0 + r;
+        const int gx = x0 + 4 * q;
+        const bool in = gz < NZ && gx < nxw;
+        const int bytes = in ? min(16, 4 * (nxw - gx)) : 0;
+        cp_async16(&s[r][4 * q], in ? base + (long long)gz * pitch + gx : base, bytes);
+    }
 }
 
-// Cerjan sponge: exp(-(0.015 (nb - d))^2) per axis, d = cells from the outer edge.
-__device__ __forceinline__ float sponge(int i, int NZ, int j, int NXW, int nb) {
-    const int dz = min(i, NZ - 1 - i), dx = min(j, NXW - 1 - j);
-    const int pz = max(nb - dz, 0), px = max(nb - dx, 0);
-    if ((pz | px) == 0) return 1.0f;
-    return expf(-2.25e-4f * (float)(pz * pz + px * px));
+// Difference-form D u for the two cells (row lzr, columns lxp, lxp+1) of a
+// thread.  zc holds the two columns for rows lzr-4 .. lzr+4 (index 4 = cell).
+__device__ __forceinline__ float2 lap8x2(const STile &s, const float2 *zc, int lzr, int lxp) {
+    // Row segment: columns lxp .. lxp+9 (the cells sit at lxp+4, lxp+5).
+    const float2 *rp = reinterpret_cast<const float2 *>(&s[lzr + HALO][lxp]);
+    const float2 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4];
+    // r0=(x-4,x-3) r1=(x-2,x-1) r2=(x,x+1) r3=(x+2,x+3) r4=(x+4,x+5), x = lxp+4
+    const float u0 = r2.x, u1 = r2.y;
+    float a0 = FD_C4 * (((r4.x - u0) + (r0.x - u0)) + ((zc[8].x - u0) + (zc[0].x - u0)));
+    float a1 = FD_C4 * (((r4.y - u1) + (r0.y - u1)) + ((zc[8].y - u1) + (zc[0].y - u1)));
+    a0 = fmaf(FD_C3, ((r3.y - u0) + (r0.y - u0)) + ((zc[7].x - u0) + (zc[1].x - u0)), a0);
+    a1 = fmaf(FD_C3, ((r4.x - u1) + (r1.x - u1)) + ((zc[7].y - u1) + (zc[1].y - u1)), a1);
+    a0 = fmaf(FD_C2, ((r3.x - u0) + (r1.x - u0)) + ((zc[6].x - u0) + (zc[2].x - u0)), a0);
+    a1 = fmaf(FD_C2, ((r3.y - u1) + (r1.y - u1)) + ((zc[6].y - u1) + (zc[2].y - u1)), a1);
+    a0 = fmaf(FD_C1, ((r2.y - u0) + (r1.y - u0)) + ((zc[5].x - u0) + (zc[3].x - u0)), a0);
+    a1 = fmaf(FD_C1, ((r3.x - u1) + (r2.x - u1)) + ((zc[5].y - u1) + (zc[3].y - u1)), a1);
+    return make_float2(a0, a1);
 }
 
-__global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs A) {
-    __shared__ STile s;
-    __shared__ float so[TZ][TX];
-    const Tile t = A.c.tiles[blockIdx.x];
-    const ShotDesc sd = A.c.shots[t.slot];
+// Cerjan sponge factor along one axis: exp(-(0.015 (nb - d))^2), d = cells
+// from the outer edge; 1 inside.
+__device__ __forceinline__ float sponge1(int i, int N, int nb) {
+    const int d = min(i, N - 1 - i);
+    const int p = nb - d;
+    return p > 0 ? expf(-2.25e-4f * (float)(p * p)) : 1.0f;
+}
+
+template <int NT>
+__device__ __forceinline__ void sample_receivers(const STile &so, const Tile &t, const Tile &tn,
+                                                 const TileRec *__restrict__ recs, const ShotDesc &sd,
+                                                 float *__restrict__ d, int n) {
+    const int tid = threadIdx.x + threadIdx.y * 32;
+    for (int e = t.rec_begin + tid; e < tn.rec_begin; e += NT) {
+        const TileRec tr = recs[e];
+        d[sd.doff + (long long)n * sd.nrec + tr.r] = so[tr.cell / TX + HALO][tr.cell % TX + HALO];
+    }
+}
+
+// Model arrays are stored as 4 copies, copy r shifted left by r columns, so
+// the model row of a window starting at model column x0 is 16-byte aligned in
+// copy (x0 & 3) at column (x0 & ~3).
+__device__ __forceinline__ const float *model_base(const float *arr, const StepCommon &c, int x0) {
+    return arr + (long long)(x0 & 3) * c.mstride + (x0 & ~3);
+}
+
+template <typename T>
+__device__ __forceinline__ T &sm2(float *p) { return *reinterpret_cast<T *>(p); }
+
+// ---------------------------------------------------------------------------
+// Step kernels.  Persistent CTAs walk tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...; the shared-memory stages are double buffered so that the
+// asynchronous copies of the next tile overlap the arithmetic of the current
+// one.  A warp covers the 64 columns of a tile (two per thread, float2
+// shared/global accesses); each thread owns R rows.
+// ---------------------------------------------------------------------------
+template <bool STORE_A>
+struct FwdStage {
+    STile u;
+    CTile d, k, g;  // g: 2/v, for the segment store
+};
+template <>
+struct FwdStage<false> {
+    STile u;
+    CTile d, k;
+};
+
+template <int R, bool STORE_A>
+__global__ void __launch_bounds__(32 * (TZ / R), 1) fwd_step_kernel(FwdArgs A, int ntiles) {
+    constexpr int NT = 32 * (TZ / R);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FwdStage<STORE_A> *st = reinterpret_cast<FwdStage<STORE_A> *>(smem_raw);
     const int NZ = A.c.NZ;
-    load_tile(s, A.u, sd, NZ, t.z0, t.x0);
-    __syncthreads();
-    const int lx = threadIdx.x;
-    const int j = t.x0 + lx;
-    const float q = A.c.wav[sd.wav_off + A.n];
-#pragma unroll 4
-    for (int rr = 0; rr < ROWS_PER_THR; rr++) {
-        const int lz = threadIdx.y + rr * NTHR_Z;
-        const int i = t.z0 + lz;
-        if (i < NZ && j < sd.nxw) {
-            const long long c = sd.foff + (long long)i * sd.pitch + j;
-            float a = lap8(s, lz, lx);
-            if (i == sd.sz && j == sd.sx) a += q;
-            const float kap = __ldg(A.c.kap + (long long)i * A.c.pf + sd.x0 + j);
-            const float w = sponge(i, NZ, j, sd.nxw, A.c.nb);
-            const float uc = s[lz + HALO][lx + HALO];
-            const float uold = A.uo[c];
-            const float un = w * (2.0f * uc + kap * a) - (w * w) * uold;
-            A.uo[c] = un;
-            if (A.ck_old) {
-                A.ck_old[c] = uold;
-                A.ck_cur[c] = uc;
+    const int lxp = 2 * threadIdx.x;
+    const int lz0 = threadIdx.y * R;
+
+    auto issue = [&](FwdStage<STORE_A> &S, int tix) {
+        const Tile t = A.c.tiles[tix];
+        const ShotDesc sd = A.c.shots[t.slot];
+        issue_halo_tile<NT>(S.u, A.u, sd, NZ, t.z0, t.x0);
+        issue_cell_tile<NT>(S.d, A.dd + sd.foff, sd.pitch, NZ, sd.nxw, t.z0, t.x0);
+        issue_cell_tile<NT>(S.k, model_base(A.c.kap, A.c, sd.x0), A.c.pf, NZ, sd.nxw, t.z0, t.x0);
+        if constexpr (STORE_A)
+            issue_cell_tile<NT>(S.g, model_base(A.c.g2v, A.c, sd.x0), A.c.pf, NZ, sd.nxw, t.z0, t.x0);
+    };
+
+    int k = 0;
+    if (blockIdx.x < ntiles) issue(st[0], blockIdx.x);
+    cp_async_commit();
+    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
+        if (tix + (int)gridDim.x < ntiles) issue(st[k ^ 1], tix + gridDim.x);
+        cp_async_commit();
+        cp_async_wait_prev();
+        __syncthreads();
+        FwdStage<STORE_A> &S = st[k];
+        const Tile t = A.c.tiles[tix];
+        const ShotDesc sd = A.c.shots[t.slot];
+        const int j = t.x0 + lxp;
+        const int i0 = t.z0 + lz0;
+        const int nrow = min(R, NZ - i0);
+        const bool ok = j < sd.nxw;
+        const float q = A.c.wav[sd.wav_off + A.n];
+        const float wx0 = sponge1(j, sd.nxw, A.c.nb), wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
+        float2 zc[R + 2 * HALO];
+#pragma unroll
+        for (int r = 0; r < R + 2 * HALO; r++) zc[r] = sm2<float2>(&S.u[lz0 + r][lxp + HALO]);
+        const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+        float2 out[R];
+#pragma unroll
+        for (int rr = 0; rr < R; rr++) {
+            out[rr] = make_float2(0.f, 0.f);
+            if (ok && rr < nrow) {
+                const int i = i0 + rr;
+                float2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
+                if (i == sd.sz) {
+                    if (j == sd.sx) a.x += q;
+                    if (j + 1 == sd.sx) a.y += q;
+                }
+                const float wz = sponge1(i, NZ, A.c.nb);
+                const float w0 = wz * wx0, w1 = wz * wx1;
+                const float2 u = zc[rr + HALO];
+                const float2 dv = sm2<float2>(&S.d[lz0 + rr][lxp]);
+                const float2 kv = sm2<float2>(&S.k[lz0 + rr][lxp]);
+                float2 dn, un;
+                dn.x = w0 * fmaf(kv.x, a.x, dv.x);
+                dn.y = w1 * fmaf(kv.y, a.y, dv.y);
+                un.x = fmaf(w0, u.x, dn.x);
+                un.y = fmaf(w1, u.y, dn.y);
+                const long long c = cbase + (long long)rr * sd.pitch;
+                *reinterpret_cast<float2 *>(A.dd + c) = dn;
+                *reinterpret_cast<float2 *>(A.un + c) = un;
+                if (!STORE_A && A.ck_u) {
+                    *reinterpret_cast<float2 *>(A.ck_u + c) = u;
+                    *reinterpret_cast<float2 *>(A.ck_d + c) = dv;
+                }
+                if constexpr (STORE_A) {
+                    const float2 gv = sm2<float2>(&S.g[lz0 + rr][lxp]);
+                    *reinterpret_cast<float2 *>(A.a_out + c) = make_float2(gv.x * a.x, gv.y * a.y);
+                }
+                out[rr] = un;
             }
-            if (A.a_out) A.a_out[c] = a;
-            so[lz][lx] = un;
         }
-    }
-    if (A.d) {
-        const int rb = t.rec_begin, re = A.c.tiles[blockIdx.x + 1].rec_begin;
-        if (re > rb) {
+        const Tile tn = A.c.tiles[tix + 1];
+        __syncthreads();
+        if (!STORE_A && A.d && tn.rec_begin > t.rec_begin) {
+#pragma unroll
+            for (int rr = 0; rr < R; rr++) sm2<float2>(&S.u[lz0 + rr + HALO][lxp + HALO]) = out[rr];
             __syncthreads();
-            const int tid = threadIdx.x + threadIdx.y * NTHR_X;
-            for (int e = rb + tid; e < re; e += NTHREADS) {
+            sample_receivers<NT>(S.u, t, tn, A.c.recs, sd, A.d, A.n);
+            __syncthreads();
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+}
+
+struct AdjStage {
+    STile u;
+    CTile d, k, a, g;
+};
+
+template <int R>
+__global__ void __launch_bounds__(32 * (TZ / R), 1) adj_step_kernel(AdjArgs A, int ntiles) {
+    constexpr int NT = 32 * (TZ / R);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AdjStage *st = reinterpret_cast<AdjStage *>(smem_raw);
+    CTile &inj = *reinterpret_cast<CTile *>(smem_raw + 2 * sizeof(AdjStage));
+    const int NZ = A.c.NZ;
+    const int tid = threadIdx.x + threadIdx.y * 32;
+    const int lxp = 2 * threadIdx.x;
+    const int lz0 = threadIdx.y * R;
+
+    auto issue = [&](AdjStage &S, int tix) {
+        const Tile t = A.c.tiles[tix];
+        const ShotDesc sd = A.c.shots[t.slot];
+        issue_halo_tile<NT>(S.u, A.nu, sd, NZ, t.z0, t.x0);
+        issue_cell_tile<NT>(S.d, A.dd + sd.foff, sd.pitch, NZ, sd.nxw, t.z0, t.x0);
+        issue_cell_tile<NT>(S.a, A.a + sd.foff, sd.pitch, NZ, sd.nxw, t.z0, t.x0);
+        issue_cell_tile<NT>(S.g, A.g + sd.foff, sd.pitch, NZ, sd.nxw, t.z0, t.x0);
+        issue_cell_tile<NT>(S.k, model_base(A.c.kap, A.c, sd.x0), A.c.pf, NZ, sd.nxw, t.z0, t.x0);
+    };
+
+    int k = 0;
+    if (blockIdx.x < ntiles) issue(st[0], blockIdx.x);
+    cp_async_commit();
+    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
+        if (tix + (int)gridDim.x < ntiles) issue(st[k ^ 1], tix + gridDim.x);
+        cp_async_commit();
+        const Tile t = A.c.tiles[tix];
+        const Tile tn = A.c.tiles[tix + 1];
+        const ShotDesc sd = A.c.shots[t.slot];
+        const bool has_rec = tn.rec_begin > t.rec_begin;
+        if (has_rec) {
+            for (int e = tid; e < TZ * TX; e += NT) (&inj[0][0])[e] = 0.f;
+            __syncthreads();
+            const float *rk = A.r + sd.doff + (long long)(A.k - 1) * sd.nrec;
+            for (int e = t.rec_begin + tid; e < tn.rec_begin; e += NT) {
                 const TileRec tr = A.c.recs[e];
-                A.d[sd.doff + (long long)A.n * sd.nrec + tr.r] = so[tr.cell / TX][tr.cell % TX];
+                atomicAdd(&inj[tr.cell / TX][tr.cell % TX], rk[tr.r]);
             }
         }
-    }
-}
-
-__global__ void __launch_bounds__(NTHREADS) adj_step_kernel(AdjArgs A) {
-    __shared__ STile s;
-    __shared__ float inj[TZ][TX];
-    const Tile t = A.c.tiles[blockIdx.x];
-    const ShotDesc sd = A.c.shots[t.slot];
-    const int NZ = A.c.NZ;
-    const int tid = threadIdx.x + threadIdx.y * NTHR_X;
-    const int rb = t.rec_begin, re = A.c.tiles[blockIdx.x + 1].rec_begin;
-    const bool has_rec = re > rb;
-    load_tile(s, A.nu, sd, NZ, t.z0, t.x0);
-    if (has_rec) {
-        for (int e = tid; e < TZ * TX; e += NTHREADS) (&inj[0][0])[e] = 0.f;
+        cp_async_wait_prev();
         __syncthreads();
-        const float *rk = A.r + sd.doff + (long long)(A.k - 1) * sd.nrec;
-        for (int e = rb + tid; e < re; e += NTHREADS) {
-            const TileRec tr = A.c.recs[e];
-            atomicAdd(&inj[tr.cell / TX][tr.cell % TX], rk[tr.r]);
+        AdjStage &S = st[k];
+        const int j = t.x0 + lxp;
+        const int i0 = t.z0 + lz0;
+        const int nrow = min(R, NZ - i0);
+        const bool ok = j < sd.nxw;
+        const float wx0 = sponge1(j, sd.nxw, A.c.nb), wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
+        float2 zc[R + 2 * HALO];
+#pragma unroll
+        for (int r = 0; r < R + 2 * HALO; r++) zc[r] = sm2<float2>(&S.u[lz0 + r][lxp + HALO]);
+        const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+#pragma unroll
+        for (int rr = 0; rr < R; rr++) {
+            if (ok && rr < nrow) {
+                const int i = i0 + rr;
+                float2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
+                if (has_rec) {
+                    const float2 in = sm2<float2>(&inj[lz0 + rr][lxp]);
+                    a.x += in.x;
+                    a.y += in.y;
+                }
+                const float wz = sponge1(i, NZ, A.c.nb);
+                const float w0 = wz * wx0, w1 = wz * wx1;
+                const float2 nu = zc[rr + HALO];
+                const float2 dv = sm2<float2>(&S.d[lz0 + rr][lxp]);
+                const float2 kv = sm2<float2>(&S.k[lz0 + rr][lxp]);
+                const float2 av = sm2<float2>(&S.a[lz0 + rr][lxp]);
+                const float2 gv = sm2<float2>(&S.g[lz0 + rr][lxp]);
+                float2 dn, nn, gn;
+                dn.x = w0 * fmaf(kv.x, a.x, dv.x);
+                dn.y = w1 * fmaf(kv.y, a.y, dv.y);
+                nn.x = fmaf(w0, nu.x, dn.x);
+                nn.y = fmaf(w1, nu.y, dn.y);
+                gn.x = fmaf(av.x, nn.x, gv.x);
+                gn.y = fmaf(av.y, nn.y, gv.y);
+                const long long c = cbase + (long long)rr * sd.pitch;
+                *reinterpret_cast<float2 *>(A.dd + c) = dn;
+                *reinterpret_cast<float2 *>(A.nun + c) = nn;
+                *reinterpret_cast<float2 *>(A.g + c) = gn;
+            }
         }
-    }
-    __syncthreads();
-    const int lx = threadIdx.x;
-    const int j = t.x0 + lx;
-#pragma unroll 4
-    for (int rr = 0; rr < ROWS_PER_THR; rr++) {
-        const int lz = threadIdx.y + rr * NTHR_Z;
-        const int i = t.z0 + lz;
-        if (i < NZ && j < sd.nxw) {
-            const long long c = sd.foff + (long long)i * sd.pitch + j;
-            float a = lap8(s, lz, lx);
-            if (has_rec) a += inj[lz][lx];
-            const long long mc = (long long)i * A.c.pf + sd.x0 + j;
-            const float kap = __ldg(A.c.kap + mc);
-            const float v = __ldg(A.c.vpad + mc);
-            const float w = sponge(i, NZ, j, sd.nxw, A.c.nb);
-            const float nc = s[lz + HALO][lx + HALO];
-            const float nold = A.nuo[c];
-            const float nn = w * (2.0f * nc + kap * a) - (w * w) * nold;
-            A.nuo[c] = nn;
-            A.g[c] += (2.0f / v) * A.a[c] * nn;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(NTHREADS) born_step_kernel(BornArgs A) {
-    __shared__ STile su;
-    __shared__ STile sp;
-    __shared__ float so[TZ][TX];
-    const Tile t = A.c.tiles[blockIdx.x];
-    const ShotDesc sd = A.c.shots[t.slot];
-    const int NZ = A.c.NZ;
-    load_tile(su, A.u, sd, NZ, t.z0, t.x0);
-    load_tile(sp, A.p, sd, NZ, t.z0, t.x0);
-    __syncthreads();
-    const int lx = threadIdx.x;
-    const int j = t.x0 + lx;
-    const float q = A.c.wav[sd.wav_off + A.n];
-#pragma unroll 4
-    for (int rr = 0; rr < ROWS_PER_THR; rr++) {
-        const int lz = threadIdx.y + rr * NTHR_Z;
-        const int i = t.z0 + lz;
-        if (i < NZ && j < sd.nxw) {
-            const long long c = sd.foff + (long long)i * sd.pitch + j;
-            const long long mc = (long long)i * A.c.pf + sd.x0 + j;
-            float a0 = lap8(su, lz, lx);
-            if (i == sd.sz && j == sd.sx) a0 += q;
-            const float kap = __ldg(A.c.kap + mc);
-            const float dk = __ldg(A.dkap + mc);
-            const float w = sponge(i, NZ, j, sd.nxw, A.c.nb);
-            const float ww = w * w;
-            const float un = w * (2.0f * su[lz + HALO][lx + HALO] + kap * a0) - ww * A.uo[c];
-            const float pn =
-                w * (2.0f * sp[lz + HALO][lx + HALO] + kap * lap8(sp, lz, lx) + dk * a0) - ww * A.po[c];
-            A.uo[c] = un;
-            A.po[c] = pn;
-            so[lz][lx] = pn;
-        }
-    }
-    const int rb = t.rec_begin, re = A.c.tiles[blockIdx.x + 1].rec_begin;
-    if (re > rb) {
         __syncthreads();
-        const int tid = threadIdx.x + threadIdx.y * NTHR_X;
-        for (int e = rb + tid; e < re; e += NTHREADS) {
-            const TileRec tr = A.c.recs[e];
-            A.d[sd.doff + (long long)A.n * sd.nrec + tr.r] = so[tr.cell / TX][tr.cell % TX];
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+}
+
+struct BornStage {
+    STile u, p;
+    CTile du, dp, k, dk;
+};
+
+template <int R>
+__global__ void __launch_bounds__(32 * (TZ / R), 1) born_step_kernel(BornArgs A, int ntiles) {
+    constexpr int NT = 32 * (TZ / R);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BornStage *st = reinterpret_cast<BornStage *>(smem_raw);
+    const int NZ = A.c.NZ;
+    const int lxp = 2 * threadIdx.x;
+    const int lz0 = threadIdx.y * R;
+
+    auto issue = [&](BornStage &S, int tix) {
+        const Tile t = A.c.tiles[tix];
+        const ShotDesc sd = A.c.shots[t.slot];
+        issue_halo_tile<NT>(S.u, A.u, sd, NZ, t.z0, t.x0);
+        issue_halo_tile<NT>(S.p, A.p, sd, NZ, t.z0, t.x0);
+        issue_cell_tile<NT>(S.du, A.du + sd.foff, sd.pitch, NZ, sd.nxw, t.z0, t.x0);
+        issue_cell_tile<NT>(S.dp, A.dp + sd.foff, sd.pitch, NZ, sd.nxw, t.z0, t.x0);
+        issue_cell_tile<NT>(S.k, model_base(A.c.kap, A.c, sd.x0), A.c.pf, NZ, sd.nxw, t.z0, t.x0);
+        issue_cell_tile<NT>(S.dk, model_base(A.dkap, A.c, sd.x0), A.c.pf, NZ, sd.nxw, t.z0, t.x0);
+    };
+
+    int k = 0;
+    if (blockIdx.x < ntiles) issue(st[0], blockIdx.x);
+    cp_async_commit();
+    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
+        if (tix + (int)gridDim.x < ntiles) issue(st[k ^ 1], tix + gridDim.x);
+        cp_async_commit();
+        cp_async_wait_prev();
+        __syncthreads();
+        BornStage &S = st[k];
+        const Tile t = A.c.tiles[tix];
+        const ShotDesc sd = A.c.shots[t.slot];
+        const int j = t.x0 + lxp;
+        const int i0 = t.z0 + lz0;
+        const int nrow = min(R, NZ - i0);
+        const bool ok = j < sd.nxw;
+        const float q = A.c.wav[sd.wav_off + A.n];
+        const float wx0 = sponge1(j, sd.nxw, A.c.nb), wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
+        float2 zu[R + 2 * HALO], zp[R + 2 * HALO];
+#pragma unroll
+        for (int r = 0; r < R + 2 * HALO; r++) {
+            zu[r] = sm2<float2>(&S.u[lz0 + r][lxp + HALO]);
+            zp[r] = sm2<float2>(&S.p[lz0 + r][lxp + HALO]);
         }
+        const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+        float2 out[R];
+#pragma unroll
+        for (int rr = 0; rr < R; rr++) {
+            out[rr] = make_float2(0.f, 0.f);
+            if (ok && rr < nrow) {
+                const int i = i0 + rr;
+                float2 a0 = lap8x2(S.u, zu + rr, lz0 + rr, lxp);
+                if (i == sd.sz) {
+                    if (j == sd.sx) a0.x += q;
+                    if (j + 1 == sd.sx) a0.y += q;
+                }
+                const float2 ap = lap8x2(S.p, zp + rr, lz0 + rr, lxp);
+                const float wz = sponge1(i, NZ, A.c.nb);
+                const float w0 = wz * wx0, w1 = wz * wx1;
+                const float2 duv = sm2<float2>(&S.du[lz0 + rr][lxp]);
+                const float2 dpv = sm2<float2>(&S.dp[lz0 + rr][lxp]);
+                const float2 kv = sm2<float2>(&S.k[lz0 + rr][lxp]);
+                const float2 dkv = sm2<float2>(&S.dk[lz0 + rr][lxp]);
+                float2 du, dp, un, pn;
+                du.x = w0 * fmaf(kv.x, a0.x, duv.x);
+                du.y = w1 * fmaf(kv.y, a0.y, duv.y);
+                dp.x = w0 * fmaf(dkv.x, a0.x, fmaf(kv.x, ap.x, dpv.x));
+                dp.y = w1 * fmaf(dkv.y, a0.y, fmaf(kv.y, ap.y, dpv.y));
+                un.x = fmaf(w0, zu[rr + HALO].x, du.x);
+                un.y = fmaf(w1, zu[rr + HALO].y, du.y);
+                pn.x = fmaf(w0, zp[rr + HALO].x, dp.x);
+                pn.y = fmaf(w1, zp[rr + HALO].y, dp.y);
+                const long long c = cbase + (long long)rr * sd.pitch;
+                *reinterpret_cast<float2 *>(A.du + c) = du;
+                *reinterpret_cast<float2 *>(A.dp + c) = dp;
+                *reinterpret_cast<float2 *>(A.un + c) = un;
+                *reinterpret_cast<float2 *>(A.pn + c) = pn;
+                out[rr] = pn;
+            }
+        }
+        const Tile tn = A.c.tiles[tix + 1];
+        __syncthreads();
+        if (tn.rec_begin > t.rec_begin) {
+#pragma unroll
+            for (int rr = 0; rr < R; rr++) sm2<float2>(&S.p[lz0 + rr + HALO][lxp + HALO]) = out[rr];
+            __syncthreads();
+            sample_receivers<NT>(S.p, t, tn, A.c.recs, sd, A.d, A.n);
+            __syncthreads();
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+}
+
+// ---------------------------------------------------------------------------
+// Variants (rows per thread) and their launchers.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kRows[N_STEP_VARIANTS] = {2, 4, 8};
+
+template <int R, bool SA>
+constexpr size_t fwd_smem() { return 2 * sizeof(FwdStage<SA>); }
+constexpr size_t adj_smem() { return 2 * sizeof(AdjStage) + sizeof(CTile); }
+constexpr size_t born_smem() { return 2 * sizeof(BornStage); }
+
+template <int R>
+void fwd_launch(const FwdArgs &a, int ntiles, int grid, cudaStream_t s) {
+    if (a.a_out)
+        fwd_step_kernel<R, true><<<grid, dim3(32, TZ / R), fwd_smem<R, true>(), s>>>(a, ntiles);
+    else
+        fwd_step_kernel<R, false><<<grid, dim3(32, TZ / R), fwd_smem<R, false>(), s>>>(a, ntiles);
+}
+template <int R>
+void adj_launch(const AdjArgs &a, int ntiles, int grid, cudaStream_t s) {
+    adj_step_kernel<R><<<grid, dim3(32, TZ / R), adj_smem(), s>>>(a, ntiles);
+}
+template <int R>
+void born_launch(const BornArgs &a, int ntiles, int grid, cudaStream_t s) {
+    born_step_kernel<R><<<grid, dim3(32, TZ / R), born_smem(), s>>>(a, ntiles);
+}
+
+#define DHFWI_DISPATCH(fn, v, ...)        \
+    switch (v) {                          \
+    case 0: fn<2>(__VA_ARGS__); break;    \
+    case 1: fn<4>(__VA_ARGS__); break;    \
+    default: fn<8>(__VA_ARGS__); break;   \
+    }
+
+template <int R>
+int occ_of(int kind, int store_a) {
+    int n = 0;
+    const int nt = 32 * (TZ / R);
+    const void *fn;
+    size_t sm;
+    if (kind == 0) {
+        fn = store_a ? (const void *)fwd_step_kernel<R, true> : (const void *)fwd_step_kernel<R, false>;
+        sm = store_a ? fwd_smem<R, true>() : fwd_smem<R, false>();
+    } else if (kind == 1) {
+        fn = (const void *)adj_step_kernel<R>;
+        sm = adj_smem();
+    } else {
+        fn = (const void *)born_step_kernel<R>;
+        sm = born_smem();
+    }
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, nt, sm);
+    return n < 1 ? 1 : n;
+}
+}  // namespace
+
+int step_variant_rows(int v) { return kRows[v]; }
+
+int step_occupancy(int kind, int variant, int store_a) {
+    switch (variant) {
+    case 0: return occ_of<2>(kind, store_a);
+    case 1: return occ_of<4>(kind, store_a);
+    default: return occ_of<8>(kind, store_a);
     }
 }
 
-void launch_fwd_step(const FwdArgs &a, int ntiles, cudaStream_t s) {
-    if (ntiles > 0) fwd_step_kernel<<<ntiles, dim3(NTHR_X, NTHR_Z), 0, s>>>(a);
+void launch_fwd_step(const FwdArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    const int grid = ntiles < L.max_ctas ? ntiles : L.max_ctas;
+    DHFWI_DISPATCH(fwd_launch, L.variant, a, ntiles, grid, s);
 }
-void launch_adj_step(const AdjArgs &a, int ntiles, cudaStream_t s) {
-    if (ntiles > 0) adj_step_kernel<<<ntiles, dim3(NTHR_X, NTHR_Z), 0, s>>>(a);
+void launch_adj_step(const AdjArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    const int grid = ntiles < L.max_ctas ? ntiles : L.max_ctas;
+    DHFWI_DISPATCH(adj_launch, L.variant, a, ntiles, grid, s);
 }
-void launch_born_step(const BornArgs &a, int ntiles, cudaStream_t s) {
-    if (ntiles > 0) born_step_kernel<<<ntiles, dim3(NTHR_X, NTHR_Z), 0, s>>>(a);
+void launch_born_step(const BornArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    const int grid = ntiles < L.max_ctas ? ntiles : L.max_ctas;
+    DHFWI_DISPATCH(born_launch, L.variant, a, ntiles, grid, s);
 }
 
 // ---------------------------------------------------------------------------
 // Model preparation
 // ---------------------------------------------------------------------------
 __global__ void prep_model_kernel(const float *__restrict__ v, const float *__restrict__ dv, int rel,
-                                  int nz, int nx, int nb, float c, float *kap, float *vpad,
-                                  float *dkap, int pf, unsigned *status) {
+                                  int nz, int nx, int nb, double c, float *kap, float *vpad,
+                                  float *g2v, float *dkap, int pf, long long mstride, unsigned *status) {
     const int NZ = nz + 2 * nb, NXF = nx + 2 * nb;
     const int pc = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     float kmax = 0.f;
     bool bad = false;
-    if (pc < NXF && i < NZ) {
+    if (pc < pf && i < NZ) {
         const int iz = min(max(i - nb, 0), nz - 1);
-        const int ix = min(max(pc - nb, 0), nx - 1);
-        const float vv = v[(long long)iz * nx + ix];
-        bad = !(vv > 0.f) || !isfinite(vv);
-        const float k = vv * vv * c;
-        const long long o = (long long)i * pf + pc;
-        kap[o] = k;
-        vpad[o] = vv;
-        if (dkap) {
-            const float dd = dv[(long long)iz * nx + ix];
-            bad = bad || !isfinite(dd);
-            dkap[o] = rel ? 2.0f * k * dd : (2.0f * k / vv) * dd;
+        // Copy r holds padded-model column pc + r, so that a window starting
+        // at any model column reads 16-byte aligned rows from one copy.
+        for (int copy = 0; copy < 4; copy++) {
+            const int ix = min(max(pc + copy - nb, 0), nx - 1);
+            const float vv = v[(long long)iz * nx + ix];
+            const bool inside = copy == 0 && pc < NXF;
+            bad = bad || (inside && (!(vv > 0.f) || !isfinite(vv)));
+            // kappa rounded once from a double product.
+            const float k = (float)((double)vv * (double)vv * c);
+            const long long o = copy * mstride + (long long)i * pf + pc;
+            kap[o] = k;
+            g2v[o] = (float)(2.0 / (double)vv);
+            if (copy == 0) vpad[(long long)i * pf + pc] = vv;
+            if (dkap) {
+                const float dd = dv[(long long)iz * nx + ix];
+                bad = bad || (inside && !isfinite(dd));
+                dkap[o] = rel ? (float)(2.0 * (double)k * (double)dd)
+                              : (float)(2.0 * (double)vv * c * (double)dd);
+            }
+            if (inside && !bad) kmax = k;
         }
-        kmax = bad ? 0.f : k;
     }
     // Warp reduction of the max and of the bad flag, one atomic per warp.
     for (int off = 16; off > 0; off >>= 1) {
@@ -249,12 +560,13 @@ __global__ void prep_model_kernel(const float *__restrict__ v, const float *__re
     }
 }
 
-void launch_prep_model(const float *v, const float *dv, int rel, int nz, int nx, int nb, float c,
-                       float *kap, float *vpad, float *dkap, int pf, unsigned *status,
-                       cudaStream_t s) {
-    const int NZ = nz + 2 * nb, NXF = nx + 2 * nb;
-    dim3 grid((NXF + 127) / 128, NZ);
-    prep_model_kernel<<<grid, 128, 0, s>>>(v, dv, rel, nz, nx, nb, c, kap, vpad, dkap, pf, status);
+void launch_prep_model(const float *v, const float *dv, int rel, int nz, int nx, int nb, double c,
+                       float *kap, float *vpad, float *g2v, float *dkap, int pf, long long mstride,
+                       unsigned *status, cudaStream_t s) {
+    const int NZ = nz + 2 * nb;
+    dim3 grid((pf + 127) / 128, NZ);
+    prep_model_kernel<<<grid, 128, 0, s>>>(v, dv, rel, nz, nx, nb, c, kap, vpad, g2v, dkap, pf, mstride,
+                                           status);
 }
 
 // ---------------------------------------------------------------------------
