@@ -333,25 +333,25 @@ def main():
     d_born = ctx.new_data(geom)
     ctx.set_timing(True)
     phase = {"ms": 0.0, "launches": 0, "cells": 0}
+    breakdown = {"forward_ms": 0.0, "backward_ms": 0.0, "born_ms": 0.0}
     launches = [0]
 
     def step(collect=False):
         J, _ = ctx.fwi_gradient(v0, geom, d_obs, grad=grad)
-        st = ctx.stats()
-        launches[0] += st["kernel_launches"]
-        if collect:
-            phase["ms"] += st["phase_ms"][0]
-            phase["launches"] += st["phase_launches"][0]
-            phase["cells"] += st["phase_cells"][0]
+        stats = [ctx.stats()]
         ctx.born_demig(v0, geom, grad, out=d_born)
-        launches[0] += ctx.stats()["kernel_launches"]
+        stats.append(ctx.stats())
         ctx.rtm_mig(v0, geom, d_born, out=dm1)
-        st = ctx.stats()
-        launches[0] += st["kernel_launches"]
-        if collect:
-            phase["ms"] += st["phase_ms"][0]
-            phase["launches"] += st["phase_launches"][0]
-            phase["cells"] += st["phase_cells"][0]
+        stats.append(ctx.stats())
+        for st in stats:
+            launches[0] += st["kernel_launches"]
+            if collect:
+                phase["ms"] += st["phase_ms"][0]
+                phase["launches"] += st["phase_launches"][0]
+                phase["cells"] += st["phase_cells"][0]
+                breakdown["forward_ms"] += st["phase_ms"][0]
+                breakdown["backward_ms"] += st["phase_ms"][1]
+                breakdown["born_ms"] += st["phase_ms"][2]
         return J
 
     for _ in range(args.warmup):
@@ -439,6 +439,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(launches[0]),
             "step_variants": ctx.stats()["step_variant"],
+            "phase_ms_per_step": {k: round(v / args.steps, 2) for k, v in breakdown.items()},
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

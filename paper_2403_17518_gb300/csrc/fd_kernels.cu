@@ -89,23 +89,69 @@ __device__ __forceinline__ void issue_cell_tile(CTile &s, const float *__restric
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed two-lane FP32 arithmetic (sm_100+ add/sub/mul/fma .f32x2): lane 0 is
+// the low word (float2.x).  Each lane is rounded exactly like the scalar op.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float2 a) { return *reinterpret_cast<f2 *>(&a); }
+__device__ __forceinline__ float2 upk(f2 a) { return *reinterpret_cast<float2 *>(&a); }
+__device__ __forceinline__ f2 pk2(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Difference-form D u for the two cells (row lzr, columns lxp, lxp+1) of a
-// thread.  zc holds the two columns for rows lzr-4 .. lzr+4 (index 4 = cell).
-__device__ __forceinline__ float2 lap8x2(const STile &s, const float2 *zc, int lzr, int lxp) {
+// thread, both lanes at once.  zc holds the two columns for rows lzr-4 ..
+// lzr+4 (index 4 = the cells).
+__device__ __forceinline__ f2 lap8x2(const STile &s, const float2 *zc, int lzr, int lxp) {
     // Row segment: columns lxp .. lxp+9 (the cells sit at lxp+4, lxp+5).
     const float2 *rp = reinterpret_cast<const float2 *>(&s[lzr + HALO][lxp]);
     const float2 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4];
     // r0=(x-4,x-3) r1=(x-2,x-1) r2=(x,x+1) r3=(x+2,x+3) r4=(x+4,x+5), x = lxp+4
-    const float u0 = r2.x, u1 = r2.y;
-    float a0 = FD_C4 * (((r4.x - u0) + (r0.x - u0)) + ((zc[8].x - u0) + (zc[0].x - u0)));
-    float a1 = FD_C4 * (((r4.y - u1) + (r0.y - u1)) + ((zc[8].y - u1) + (zc[0].y - u1)));
-    a0 = fmaf(FD_C3, ((r3.y - u0) + (r0.y - u0)) + ((zc[7].x - u0) + (zc[1].x - u0)), a0);
-    a1 = fmaf(FD_C3, ((r4.x - u1) + (r1.x - u1)) + ((zc[7].y - u1) + (zc[1].y - u1)), a1);
-    a0 = fmaf(FD_C2, ((r3.x - u0) + (r1.x - u0)) + ((zc[6].x - u0) + (zc[2].x - u0)), a0);
-    a1 = fmaf(FD_C2, ((r3.y - u1) + (r1.y - u1)) + ((zc[6].y - u1) + (zc[2].y - u1)), a1);
-    a0 = fmaf(FD_C1, ((r2.y - u0) + (r1.y - u0)) + ((zc[5].x - u0) + (zc[3].x - u0)), a0);
-    a1 = fmaf(FD_C1, ((r3.x - u1) + (r2.x - u1)) + ((zc[5].y - u1) + (zc[3].y - u1)), a1);
-    return make_float2(a0, a1);
+    const f2 u = pk(r2);
+    const f2 m4 = pk(r0), p4 = pk(r4);
+    const f2 m3 = pk2(r0.y, r1.x), p3 = pk2(r3.y, r4.x);
+    const f2 m2 = pk(r1), p2 = pk(r3);
+    const f2 m1 = pk2(r1.y, r2.x), p1 = pk2(r2.y, r3.x);
+    const f2 c1 = pk2(FD_C1, FD_C1), c2 = pk2(FD_C2, FD_C2), c3 = pk2(FD_C3, FD_C3), c4 = pk2(FD_C4, FD_C4);
+    f2 a = mul2(c4, add2(add2(sub2(p4, u), sub2(m4, u)), add2(sub2(pk(zc[8]), u), sub2(pk(zc[0]), u))));
+    a = fma2(c3, add2(add2(sub2(p3, u), sub2(m3, u)), add2(sub2(pk(zc[7]), u), sub2(pk(zc[1]), u))), a);
+    a = fma2(c2, add2(add2(sub2(p2, u), sub2(m2, u)), add2(sub2(pk(zc[6]), u), sub2(pk(zc[2]), u))), a);
+    a = fma2(c1, add2(add2(sub2(p1, u), sub2(m1, u)), add2(sub2(pk(zc[5]), u), sub2(pk(zc[3]), u))), a);
+    return a;
+}
+
+// Source injection into lane 0 / 1 of a when the cell is the source node.
+__device__ __forceinline__ f2 inject(f2 a, int i, int j, int sz, int sx, float q) {
+    if (i == sz && (j == sx || j + 1 == sx)) {
+        float2 v = upk(a);
+        if (j == sx) v.x += q;
+        else v.y += q;
+        a = pk(v);
+    }
+    return a;
 }
 
 // Cerjan sponge factor along one axis: exp(-(0.015 (nb - d))^2), d = cells
@@ -201,33 +247,26 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) fwd_step_kernel(FwdArgs A, i
             out[rr] = make_float2(0.f, 0.f);
             if (ok && rr < nrow) {
                 const int i = i0 + rr;
-                float2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
-                if (i == sd.sz) {
-                    if (j == sd.sx) a.x += q;
-                    if (j + 1 == sd.sx) a.y += q;
-                }
+                const f2 a = inject(lap8x2(S.u, zc + rr, lz0 + rr, lxp), i, j, sd.sz, sd.sx, q);
                 const float wz = sponge1(i, NZ, A.c.nb);
-                const float w0 = wz * wx0, w1 = wz * wx1;
-                const float2 u = zc[rr + HALO];
-                const float2 dv = sm2<float2>(&S.d[lz0 + rr][lxp]);
-                const float2 kv = sm2<float2>(&S.k[lz0 + rr][lxp]);
-                float2 dn, un;
-                dn.x = w0 * fmaf(kv.x, a.x, dv.x);
-                dn.y = w1 * fmaf(kv.y, a.y, dv.y);
-                un.x = fmaf(w0, u.x, dn.x);
-                un.y = fmaf(w1, u.y, dn.y);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                const f2 u = pk(zc[rr + HALO]);
+                const f2 dv = pk(sm2<float2>(&S.d[lz0 + rr][lxp]));
+                const f2 kv = pk(sm2<float2>(&S.k[lz0 + rr][lxp]));
+                const f2 dn = mul2(w, fma2(kv, a, dv));
+                const f2 un = fma2(w, u, dn);
                 const long long c = cbase + (long long)rr * sd.pitch;
-                *reinterpret_cast<float2 *>(A.dd + c) = dn;
-                *reinterpret_cast<float2 *>(A.un + c) = un;
+                *reinterpret_cast<f2 *>(A.dd + c) = dn;
+                *reinterpret_cast<f2 *>(A.un + c) = un;
                 if (!STORE_A && A.ck_u) {
-                    *reinterpret_cast<float2 *>(A.ck_u + c) = u;
-                    *reinterpret_cast<float2 *>(A.ck_d + c) = dv;
+                    *reinterpret_cast<f2 *>(A.ck_u + c) = u;
+                    *reinterpret_cast<f2 *>(A.ck_d + c) = dv;
                 }
                 if constexpr (STORE_A) {
-                    const float2 gv = sm2<float2>(&S.g[lz0 + rr][lxp]);
-                    *reinterpret_cast<float2 *>(A.a_out + c) = make_float2(gv.x * a.x, gv.y * a.y);
+                    const f2 gv = pk(sm2<float2>(&S.g[lz0 + rr][lxp]));
+                    *reinterpret_cast<f2 *>(A.a_out + c) = mul2(gv, a);
                 }
-                out[rr] = un;
+                out[rr] = upk(un);
             }
         }
         const Tile tn = A.c.tiles[tix + 1];
@@ -304,30 +343,21 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) adj_step_kernel(AdjArgs A, i
         for (int rr = 0; rr < R; rr++) {
             if (ok && rr < nrow) {
                 const int i = i0 + rr;
-                float2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
-                if (has_rec) {
-                    const float2 in = sm2<float2>(&inj[lz0 + rr][lxp]);
-                    a.x += in.x;
-                    a.y += in.y;
-                }
+                f2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
+                if (has_rec) a = add2(a, pk(sm2<float2>(&inj[lz0 + rr][lxp])));
                 const float wz = sponge1(i, NZ, A.c.nb);
-                const float w0 = wz * wx0, w1 = wz * wx1;
-                const float2 nu = zc[rr + HALO];
-                const float2 dv = sm2<float2>(&S.d[lz0 + rr][lxp]);
-                const float2 kv = sm2<float2>(&S.k[lz0 + rr][lxp]);
-                const float2 av = sm2<float2>(&S.a[lz0 + rr][lxp]);
-                const float2 gv = sm2<float2>(&S.g[lz0 + rr][lxp]);
-                float2 dn, nn, gn;
-                dn.x = w0 * fmaf(kv.x, a.x, dv.x);
-                dn.y = w1 * fmaf(kv.y, a.y, dv.y);
-                nn.x = fmaf(w0, nu.x, dn.x);
-                nn.y = fmaf(w1, nu.y, dn.y);
-                gn.x = fmaf(av.x, nn.x, gv.x);
-                gn.y = fmaf(av.y, nn.y, gv.y);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                const f2 nu = pk(zc[rr + HALO]);
+                const f2 dv = pk(sm2<float2>(&S.d[lz0 + rr][lxp]));
+                const f2 kv = pk(sm2<float2>(&S.k[lz0 + rr][lxp]));
+                const f2 av = pk(sm2<float2>(&S.a[lz0 + rr][lxp]));
+                const f2 gv = pk(sm2<float2>(&S.g[lz0 + rr][lxp]));
+                const f2 dn = mul2(w, fma2(kv, a, dv));
+                const f2 nn = fma2(w, nu, dn);
                 const long long c = cbase + (long long)rr * sd.pitch;
-                *reinterpret_cast<float2 *>(A.dd + c) = dn;
-                *reinterpret_cast<float2 *>(A.nun + c) = nn;
-                *reinterpret_cast<float2 *>(A.g + c) = gn;
+                *reinterpret_cast<f2 *>(A.dd + c) = dn;
+                *reinterpret_cast<f2 *>(A.nun + c) = nn;
+                *reinterpret_cast<f2 *>(A.g + c) = fma2(av, nn, gv);
             }
         }
         __syncthreads();
@@ -390,33 +420,23 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) born_step_kernel(BornArgs A,
             out[rr] = make_float2(0.f, 0.f);
             if (ok && rr < nrow) {
                 const int i = i0 + rr;
-                float2 a0 = lap8x2(S.u, zu + rr, lz0 + rr, lxp);
-                if (i == sd.sz) {
-                    if (j == sd.sx) a0.x += q;
-                    if (j + 1 == sd.sx) a0.y += q;
-                }
-                const float2 ap = lap8x2(S.p, zp + rr, lz0 + rr, lxp);
+                const f2 a0 = inject(lap8x2(S.u, zu + rr, lz0 + rr, lxp), i, j, sd.sz, sd.sx, q);
+                const f2 ap = lap8x2(S.p, zp + rr, lz0 + rr, lxp);
                 const float wz = sponge1(i, NZ, A.c.nb);
-                const float w0 = wz * wx0, w1 = wz * wx1;
-                const float2 duv = sm2<float2>(&S.du[lz0 + rr][lxp]);
-                const float2 dpv = sm2<float2>(&S.dp[lz0 + rr][lxp]);
-                const float2 kv = sm2<float2>(&S.k[lz0 + rr][lxp]);
-                const float2 dkv = sm2<float2>(&S.dk[lz0 + rr][lxp]);
-                float2 du, dp, un, pn;
-                du.x = w0 * fmaf(kv.x, a0.x, duv.x);
-                du.y = w1 * fmaf(kv.y, a0.y, duv.y);
-                dp.x = w0 * fmaf(dkv.x, a0.x, fmaf(kv.x, ap.x, dpv.x));
-                dp.y = w1 * fmaf(dkv.y, a0.y, fmaf(kv.y, ap.y, dpv.y));
-                un.x = fmaf(w0, zu[rr + HALO].x, du.x);
-                un.y = fmaf(w1, zu[rr + HALO].y, du.y);
-                pn.x = fmaf(w0, zp[rr + HALO].x, dp.x);
-                pn.y = fmaf(w1, zp[rr + HALO].y, dp.y);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                const f2 duv = pk(sm2<float2>(&S.du[lz0 + rr][lxp]));
+                const f2 dpv = pk(sm2<float2>(&S.dp[lz0 + rr][lxp]));
+                const f2 kv = pk(sm2<float2>(&S.k[lz0 + rr][lxp]));
+                const f2 dkv = pk(sm2<float2>(&S.dk[lz0 + rr][lxp]));
+                const f2 du = mul2(w, fma2(kv, a0, duv));
+                const f2 dp = mul2(w, fma2(dkv, a0, fma2(kv, ap, dpv)));
+                const f2 pn = fma2(w, pk(zp[rr + HALO]), dp);
                 const long long c = cbase + (long long)rr * sd.pitch;
-                *reinterpret_cast<float2 *>(A.du + c) = du;
-                *reinterpret_cast<float2 *>(A.dp + c) = dp;
-                *reinterpret_cast<float2 *>(A.un + c) = un;
-                *reinterpret_cast<float2 *>(A.pn + c) = pn;
-                out[rr] = pn;
+                *reinterpret_cast<f2 *>(A.du + c) = du;
+                *reinterpret_cast<f2 *>(A.dp + c) = dp;
+                *reinterpret_cast<f2 *>(A.un + c) = fma2(w, pk(zu[rr + HALO]), du);
+                *reinterpret_cast<f2 *>(A.pn + c) = pn;
+                out[rr] = upk(pn);
             }
         }
         const Tile tn = A.c.tiles[tix + 1];
