@@ -5,11 +5,15 @@ Workload (default): 400 x 1200 seeded layered-fault model, dx 12.5 m,
 dt 1 ms, 20-cell sponge, 8 Hz Ricker, 64 surface shots with 200-600
 receivers and 3000-4000 samples each, all shots in one batched pass.
 
-One step = one FWI iteration's wave-equation work in the order of the paper:
+One step = one deblurred FWI iteration, in the order of the paper:
   1. fwi_gradient: forward modelling + misfit + adjoint-state gradient
      (forward pass with checkpoints, segment recomputation, adjoint pass);
   2. born_demig of the gradient (background + scattered fields jointly);
-  3. rtm_mig of those Born data -> the doubly migrated image (Eq. 15).
+  3. rtm_mig of those Born data -> the doubly migrated image (Eq. 15);
+  4. deblur_train: warm-started U-Net training on the (doubly migrated
+     image -> gradient) pair, 20 epochs of 108 patches of 128 x 128, batch 32
+     (the 200-epoch cold start runs once before the timed region);
+  5. deblur_apply to the full gradient, 6. fwi_update of the model.
 value = algorithmic cell updates per second, Gcell-updates/s: per step
 6 U (forward U + adjoint U for the gradient, 2 U for Born, forward U +
 adjoint U for migration), U = sum over shots of nt_s x padded window cells.
@@ -63,6 +67,34 @@ def make_case(name):
 
 def algorithmic_cells(case) -> int:
     return 6 * case.geom.cell_updates(case.nz, case.nb)
+
+
+NET = dict(base_channels=32, levels=4, patch=128, stride=64, batch=32, lr=1e-3, seed=29)
+WARM_EPOCHS, COLD_EPOCHS = 20, 200
+
+
+def conv_flops(base, levels, H, W):
+    """Multiply-add FLOPs (2 per MAC) of one forward pass of the U-Net on H x W."""
+    f = 0
+    C = lambda l: base << l
+    f += 2 * H * W * 9 * (1 * C(0) + C(0) * C(0))
+    for l in range(1, levels + 1):
+        h, w = H >> l, W >> l
+        f += 2 * h * w * 9 * (C(l - 1) * C(l) + C(l) * C(l))
+    for l in range(1, levels + 1):
+        r = levels - l
+        h, w = H >> r, W >> r
+        f += 2 * (h // 2) * (w // 2) * C(r + 1) * 4 * C(r)          # transposed conv
+        f += 2 * h * w * 9 * (2 * C(r) * C(r) + C(r) * C(r))
+    f += 2 * H * W * C(0)
+    return f
+
+
+def n_patches(n, p, s):
+    o = list(range(0, n - p + 1, s))
+    if o[-1] != n - p:
+        o.append(n - p)
+    return len(o)
 
 
 # ---------------------------------------------------------------------------
@@ -262,8 +294,8 @@ def run_reference(args, dist):
 
 def workload_config(case, args):
     return {
-        "workload": f"{case.name}: batched forward modelling + adjoint-state gradient + Born demigration + "
-                    f"migration (doubly migrated image)",
+        "workload": f"{case.name}: one deblurred FWI iteration (forward modelling + adjoint-state gradient + "
+                    f"Born demigration + migration + warm-started U-Net training + apply + model update)",
         "grid": [case.nz, case.nx], "h_m": case.h, "dt_s": case.dt, "sponge": case.nb,
         "shots": case.geom.n_shots, "nt_range": [int(case.geom.nt.min()), int(case.geom.nt.max())],
         "receivers_range": [int(min(case.geom.nrec(s) for s in range(case.geom.n_shots))),
@@ -330,8 +362,17 @@ def main():
         return
     grad = ctx.new_model()
     dm1 = ctx.new_model()
+    direction = ctx.new_model()
+    v1 = ctx.new_model()
     d_born = ctx.new_data(geom)
     ctx.set_timing(True)
+    alpha = 0.01 * float(np.mean(case.v_init))
+    # Cold start of the network (first FWI iteration), outside the timed region.
+    ctx.fwi_gradient(v0, geom, d_obs, grad=grad)
+    ctx.born_demig(v0, geom, grad, out=d_born)
+    ctx.rtm_mig(v0, geom, d_born, out=dm1)
+    ctx.deblur_train(dm1, grad, warm_start=False, epochs=COLD_EPOCHS, **NET)
+    nn_ev = []
     phase = {"ms": 0.0, "launches": 0, "cells": 0}
     breakdown = {"forward_ms": 0.0, "backward_ms": 0.0, "born_ms": 0.0}
     launches = [0]
@@ -343,6 +384,18 @@ def main():
         stats.append(ctx.stats())
         ctx.rtm_mig(v0, geom, d_born, out=dm1)
         stats.append(ctx.stats())
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        ctx.deblur_train(dm1, grad, warm_start=True, epochs=WARM_EPOCHS, **NET)
+        launches[0] += ctx.stats()["kernel_launches"]
+        ctx.deblur_apply(grad, out=direction)
+        launches[0] += ctx.stats()["kernel_launches"]
+        ev1.record()
+        if collect:
+            nn_ev.append((ev0, ev1))
+        ctx.fwi_update(v0, direction, alpha, 1500.0, 4500.0, 5, out=v1)
+        launches[0] += ctx.stats()["kernel_launches"]
         for st in stats:
             launches[0] += st["kernel_launches"]
             if collect:
@@ -400,8 +453,11 @@ def main():
             ctx.fwi_gradient(dv0, geom, ddobs, grad=grad)
             ctx.born_demig(dv0, geom, grad, out=d_born)
             ctx.rtm_mig(dv0, geom, d_born, out=dm1)
-            h_grad.copy_(grad, non_blocking=True)
-            h_dm1.copy_(dm1, non_blocking=True)
+            ctx.deblur_train(dm1, grad, warm_start=True, epochs=WARM_EPOCHS, **NET)
+            ctx.deblur_apply(grad, out=direction)
+            ctx.fwi_update(dv0, direction, alpha, 1500.0, 4500.0, 5, out=v1)
+            h_grad.copy_(v1, non_blocking=True)
+            h_dm1.copy_(direction, non_blocking=True)
             torch.cuda.synchronize()
 
         e2e_step()
@@ -414,6 +470,15 @@ def main():
         e2e = {"value": round(dist.world * cells_step * args.e2e_steps / el / 1e9, 4), "unit": UNIT,
                "h2d_bytes_per_step": int(h_v0.numel() * 4 + h_dobs.numel() * 4),
                "d2h_bytes_per_step": int(h_grad.numel() * 4 + h_dm1.numel() * 4 + 8)}
+
+    nn_ms = sum(a.elapsed_time(b) for a, b in nn_ev) / max(len(nn_ev), 1)
+    npatch = n_patches(case.nz, NET["patch"], NET["stride"]) * n_patches(case.nx, NET["patch"], NET["stride"])
+    f_patch = conv_flops(NET["base_channels"], NET["levels"], NET["patch"], NET["patch"])
+    f_apply = conv_flops(NET["base_channels"], NET["levels"], case.nz, case.nx)
+    nn_flops = WARM_EPOCHS * npatch * 3 * f_patch + f_apply  # training = forward + two gradient GEMMs
+    bf16_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1700.0
+    nn_tflops = nn_flops / (nn_ms / 1e3) / 1e12 if nn_ms > 0 else None
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -439,7 +504,14 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(launches[0]),
             "step_variants": ctx.stats()["step_variant"],
-            "phase_ms_per_step": {k: round(v / args.steps, 2) for k, v in breakdown.items()},
+            "phase_ms_per_step": dict({k: round(v / args.steps, 2) for k, v in breakdown.items()},
+                                      network_ms=round(nn_ms, 2)),
+            "roofline_network": {
+                "kernel": "U-Net training (20 warm epochs, 108 patches, batch 32) + full-image apply",
+                "bound": "tensor", "achieved": round(nn_tflops, 2) if nn_tflops else None, "peak": bf16_peak,
+                "unit": "TFLOP/s", "frac": round(nn_tflops / bf16_peak, 4) if nn_tflops else None,
+                "flops_per_step": nn_flops, "peak_kind": "measured (bf16_tflops_sustained)",
+            },
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

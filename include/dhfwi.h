@@ -170,6 +170,87 @@ int born_demig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, cons
 int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const float *d_dev,
             float *img_dev, int flags, void *stream);
 
+/* Model update along a direction (Section 2.1 Eq. 4 with the inverse Hessian
+ * replaced by a scalar step, or by the network for the deblurred direction):
+ *   v_out = clamp(v - alpha * dir / max|dir|, vmin, vmax),
+ * with dir taken as 0 in the first mute_rows rows (source/receiver footprint;
+ * those rows are also left out of the max).  v_dev, dir_dev, v_out_dev
+ * [nz][nx] float32 device (v_out may equal v).  Asynchronous. */
+int fwi_update(dhfwi_ctx *ctx, const float *v_dev, const float *dir_dev, float alpha, float vmin, float vmax,
+               int mute_rows, float *v_out_dev, void *stream);
+
+/* Data misfit J = 1/2 sum (a - b)^2 (Section 2.1 Eq. 2) of two device
+ * vectors of n float32 values, accumulated in float64.  Synchronises. */
+int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long long n, double *misfit_out,
+                void *stream);
+
+/* ------------------------------------------------------------------------
+ * Deblurring network: an approximate inverse Hessian (Section 2.3.1 and
+ * Section 2.4, architecture in Appendix A).  A UNet-like network is trained to
+ * map the doubly migrated image delta m_1 (Eq. 15) to the gradient g
+ * (Eq. 13), then applied to g to obtain the update direction; weights carry
+ * over between training calls (transfer learning).  Convolutions run with
+ * bfloat16 operands and float32 accumulation; master weights, Adam moments,
+ * loss and schedule are float32.
+ *
+ * Parameters are one flat float32 vector, tensor after tensor: input block
+ * (conv 1->B, conv B->B), `levels` down blocks (conv, conv), `levels` up blocks
+ * (transposed conv, conv on [skip, up], conv), output 1x1 conv B->1.  A 3x3
+ * conv stores weight [Cout][3][3][Cin] then bias [Cout]; the 2x2 stride-2
+ * transposed conv weight [Cout][2][2][Cin] (output pixel (2h+a, 2w+b) gets
+ * W[co][a][b][:] . x[h][w]) then bias; the 1x1 conv [Cout][Cin] then bias.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int base_channels;  /* channels of the input block (multiple of 8); 32 here, 128 in the paper */
+    int levels;         /* down/up blocks (4 in the paper) */
+    int patch;          /* square patch size (multiple of 2^levels) */
+    int stride;         /* patch stride; the last patch of each axis touches the edge */
+    int batch;          /* patches per optimiser step */
+    int epochs;         /* passes over the patches (<= 4096) */
+    float lr;           /* initial learning rate of the cosine schedule */
+    float beta1, beta2, eps;     /* Adam */
+    unsigned long long seed;     /* initialisation (cold start) and shuffling */
+} dhfwi_train_cfg;
+
+/* Fix the architecture and initialise the weights from `seed` (SplitMix64,
+ * uniform in +-1/sqrt(fan_in)).  Synchronous. */
+int dhfwi_net_init(dhfwi_ctx *ctx, int base_channels, int levels, unsigned long long seed);
+
+/* Number of float32 parameters of the current network (0 if none). */
+long long dhfwi_net_size(const dhfwi_ctx *ctx);
+
+/* Copy the float32 master weights to / from HOST memory (n = dhfwi_net_size).
+ * Synchronous.  net_set requires a prior dhfwi_net_init (architecture). */
+int dhfwi_net_get(dhfwi_ctx *ctx, float *host, size_t n);
+int dhfwi_net_set(dhfwi_ctx *ctx, const float *host, size_t n);
+
+/* Network output for a batch: x_dev [n][h][w] float32 (one channel, device),
+ * out_dev [n][h][w] float32 (device); h, w multiples of 2^levels.  No
+ * normalisation.  Asynchronous on `stream`. */
+int deblur_forward(dhfwi_ctx *ctx, const float *x_dev, int n, int h, int w, float *out_dev, void *stream);
+
+/* One forward + MSE + backward on a batch: grad_dev (device, float32,
+ * dhfwi_net_size values) receives dL/dtheta of L = mean((net(x) - y)^2);
+ * loss_out (host, may be NULL) receives L and synchronises the stream. */
+int deblur_grad(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int n, int h, int w, float *grad_dev,
+                double *loss_out, void *stream);
+
+/* Train on the pair (x = doubly migrated image, y = gradient), both [nz][nx]
+ * float32 device images, each normalised by its max |.|, cut into patches.
+ * Adam with lr_t = lr (1 + cos(pi t / T)) / 2 over the T steps of this call,
+ * moments reset at the start of each call; warm_start != 0 keeps the current
+ * weights (transfer learning), 0 re-initialises them from cfg->seed.
+ * loss_hist (host, may be NULL): cfg->epochs per-epoch mean MSE; when given,
+ * the stream is synchronised.  Errors: DHFWI_ERR_ARG for a bad cfg. */
+int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz, int nx,
+                 const dhfwi_train_cfg *cfg, int warm_start, float *loss_hist, void *stream);
+
+/* Update direction from the gradient (Section 2.3.1): out = net(g / max|g|)
+ * * max|g| on the full image, zero padded to a multiple of 2^levels and
+ * cropped.  g_dev, out_dev [nz][nx] float32 device.  DHFWI_ERR_STATE before
+ * the network has weights. */
+int deblur_apply(dhfwi_ctx *ctx, const float *g_dev, int nz, int nx, float *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,11 +51,10 @@ class Stats(ctypes.Structure):
 
 
 class TrainCfg(ctypes.Structure):
-    _fields_ = [("patch", ctypes.c_int), ("stride", ctypes.c_int), ("batch", ctypes.c_int),
-                ("epochs", ctypes.c_int), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
-                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("cosine_steps", ctypes.c_int),
-                ("seed", ctypes.c_ulonglong), ("base_channels", ctypes.c_int), ("levels", ctypes.c_int),
-                ("normalize", ctypes.c_int)]
+    _fields_ = [("base_channels", ctypes.c_int), ("levels", ctypes.c_int), ("patch", ctypes.c_int),
+                ("stride", ctypes.c_int), ("batch", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
 
 
 _lock = threading.Lock()
@@ -73,6 +72,19 @@ SIGNATURES = [
                                     ctypes.POINTER(ctypes.c_double), _VP, _VP]),
     ("born_demig", ctypes.c_int, [_VP, _VP, ctypes.POINTER(Geom), _VP, _VP, ctypes.c_int, _VP]),
     ("rtm_mig", ctypes.c_int, [_VP, _VP, ctypes.POINTER(Geom), _VP, _VP, ctypes.c_int, _VP]),
+    ("fwi_update", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                                  _VP, _VP]),
+    ("data_misfit", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _VP]),
+    ("dhfwi_net_init", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong]),
+    ("dhfwi_net_size", ctypes.c_longlong, [_VP]),
+    ("dhfwi_net_get", ctypes.c_int, [_VP, _FP, ctypes.c_size_t]),
+    ("dhfwi_net_set", ctypes.c_int, [_VP, _FP, ctypes.c_size_t]),
+    ("deblur_forward", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    ("deblur_grad", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                   ctypes.POINTER(ctypes.c_double), _VP]),
+    ("deblur_train", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TrainCfg),
+                                    ctypes.c_int, _FP, _VP]),
+    ("deblur_apply", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
 ]
 OPTIONAL = {}
 

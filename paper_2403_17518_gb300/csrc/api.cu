@@ -829,6 +829,36 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
     return end_call(ctx);
 }
 
+int fwi_update(dhfwi_ctx *ctx, const float *v_dev, const float *dir_dev, float alpha, float vmin, float vmax,
+               int mute_rows, float *v_out_dev, void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!v_dev || !dir_dev || !v_out_dev) return fail(ctx, DHFWI_ERR_ARG, "NULL model pointer");
+    if (!(vmin > 0.f) || !(vmax >= vmin) || !std::isfinite(alpha) || mute_rows < 0)
+        return fail(ctx, DHFWI_ERR_ARG, "need 0 < vmin <= vmax, finite alpha, mute_rows >= 0");
+    launch_update_model(v_dev, dir_dev, ctx->g.nz, ctx->g.nx, std::min(mute_rows, ctx->g.nz), alpha, vmin, vmax,
+                        (unsigned *)ctx->status.p + 2, v_out_dev, (cudaStream_t)stream);
+    ctx->stats.kernel_launches += 2;
+    return end_call(ctx);
+}
+
+int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long long n, double *misfit_out,
+                void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!a_dev || !b_dev || !misfit_out || n < 0) return fail(ctx, DHFWI_ERR_ARG, "bad misfit arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure(ctx, ctx->rtmp, sizeof(float) * std::max<long long>(n, 1), "residual"))) return rc;
+    launch_residual(a_dev, b_dev, (float *)ctx->rtmp.p, n, (double *)ctx->partial.p, RESID_BLOCKS, st);
+    ctx->stats.kernel_launches++;
+    CK(cudaMemcpyAsync(ctx->h_partial, ctx->partial.p, sizeof(double) * RESID_BLOCKS, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double J = 0.0;
+    for (int i = 0; i < RESID_BLOCKS; i++) J += ctx->h_partial[i];
+    *misfit_out = 0.5 * J;
+    return end_call(ctx);
+}
+
 }  // extern "C"
 
 // Accessors used by the network code in the same library.

@@ -137,6 +137,11 @@ void launch_prep_model(const float *v, const float *dv, int rel, int nz, int nx,
 void launch_residual(const float *ds, const float *dobs, float *r, long long n, double *partial,
                      int nblocks, cudaStream_t s);
 
+// vout = clamp(v - alpha * dir / max|dir|, vmin, vmax), dir taken as 0 in the
+// first mute_rows rows (also excluded from the max); mxbits: 1 word scratch.
+void launch_update_model(const float *v, const float *dir, int nz, int nx, int mute_rows, float alpha, float vmin,
+                         float vmax, unsigned *mxbits, float *vout, cudaStream_t s);
+
 // Sum of the per-shot image accumulators into the physical [nz][nx] grid,
 // folding the sponge cells onto the edge cells they copy (transpose of the
 // extension), shots in original order; rel != 0 multiplies by v.

@@ -618,6 +618,40 @@ void launch_residual(const float *ds, const float *dobs, float *r, long long n, 
 }
 
 // ---------------------------------------------------------------------------
+// Model update along a direction normalised by its max |.|
+// ---------------------------------------------------------------------------
+__global__ void absmax_bits_kernel(const float *__restrict__ x, long long n, unsigned *out) {
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+__global__ void update_model_kernel(const float *__restrict__ v, const float *__restrict__ dir, int nz, int nx,
+                                    int mute_rows, float alpha, float vmin, float vmax, const unsigned *mxbits,
+                                    float *__restrict__ vout) {
+    const long long n = (long long)nz * nx;
+    const float mx = __uint_as_float(*mxbits);
+    const float sc = mx > 0.f ? alpha / mx : 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int iz = (int)(i / nx);
+        const float d = iz < mute_rows ? 0.f : dir[i];
+        vout[i] = fminf(fmaxf(v[i] - sc * d, vmin), vmax);
+    }
+}
+
+void launch_update_model(const float *v, const float *dir, int nz, int nx, int mute_rows, float alpha, float vmin,
+                         float vmax, unsigned *mxbits, float *vout, cudaStream_t s) {
+    const long long n = (long long)nz * nx;
+    cudaMemsetAsync(mxbits, 0, sizeof(unsigned), s);
+    // The normalisation ignores the muted rows.
+    const long long off = (long long)mute_rows * nx;
+    if (n > off) absmax_bits_kernel<<<512, 256, 0, s>>>(dir + off, n - off, mxbits);
+    update_model_kernel<<<512, 256, 0, s>>>(v, dir, nz, nx, mute_rows, alpha, vmin, vmax, mxbits, vout);
+}
+
+// ---------------------------------------------------------------------------
 // Image reduction: shots in original order, sponge folded onto edge cells.
 // ---------------------------------------------------------------------------
 __global__ void reduce_image_kernel(const ShotDesc *__restrict__ shots, const int *__restrict__ slot_of,

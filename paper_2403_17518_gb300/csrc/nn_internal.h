@@ -1,0 +1,80 @@
+// Internal declarations of the deblurring-network kernels (nn_kernels.cu)
+// used by the network host code (nn_net.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace dhfwi {
+namespace nn {
+
+enum { EPI_BF16_LEAKY = 0, EPI_BF16 = 1, EPI_BF16_CONVT = 2, EPI_F32 = 3, EPI_F32_ADD = 4 };
+enum { WG_CONV = 0, WG_CONVT = 1 };
+
+// Implicit GEMM C[m][n] = sum_k A[m][k] B^T[n][k]; see igemm_fprop_kernel.
+struct FpropArgs {
+    const __nv_bfloat16 *src;   // NHWC source, channel stride src_stride, offset src_off
+    int src_stride, src_off;
+    int Hs, Ws;                 // source grid
+    int C;                      // channels per tap (multiple of 8)
+    int ntaps, scale;
+    int dh[9], dw[9];
+    int Ho, Wo;                 // output grid (m = img*Ho*Wo + ho*Wo + wo)
+    int M, N;
+    const __nv_bfloat16 *bt;    // [N][ntaps*C]
+    const float *bias;          // [N] (or [N/4] for the transposed conv)
+    float slope;
+    __nv_bfloat16 *dst_bf16;
+    float *dst_f32;
+    int dst_stride, dst_off;
+};
+
+// Split-k weight-gradient GEMM; see igemm_wgrad_kernel.
+struct WgradArgs {
+    int mode;
+    const __nv_bfloat16 *g;     // output gradient (NHWC, stride g_stride)
+    int g_stride;
+    const __nv_bfloat16 *x;     // layer input (NHWC, stride x_stride, offset x_off)
+    int x_stride, x_off;
+    int nimg, H, W;             // grid of the summed pixels (coarse grid for WG_CONVT)
+    int co, ci;                 // channels (co used by WG_CONVT, ci by WG_CONV)
+    int M, N;
+    float *part;                // [splits][M][N]
+};
+
+void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s);
+int wgrad_splits(long long kpix, int M, int N);
+void launch_wgrad(const WgradArgs &a, int splits, float *dw, cudaStream_t s);
+void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, float *part, int max_blocks, float *db,
+                      cudaStream_t s);
+void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H, int W, int C, __nv_bfloat16 *y,
+                        cudaStream_t s);
+void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *dx, int accumulate, cudaStream_t s);
+void launch_leaky_bwd(const float *dA, const __nv_bfloat16 *a, int as, int ao, long long P, int C, float slope,
+                      __nv_bfloat16 *g, cudaStream_t s);
+void launch_f32_to_bf16_slice(const float *x, int xs, int xo, long long P, int C, __nv_bfloat16 *y, cudaStream_t s);
+void launch_add_slice(const float *src, int ss, int so, long long P, int C, float *dst, cudaStream_t s);
+void launch_conv1x1_fwd(const __nv_bfloat16 *a, int C, long long P, const __nv_bfloat16 *w, const float *b, float *out,
+                        cudaStream_t s);
+void launch_mse(const float *out, const float *y, long long P, __nv_bfloat16 *g, double *partial, int nblocks,
+                cudaStream_t s);
+void launch_conv1x1_bwd(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long long P, int C, const __nv_bfloat16 *w,
+                        float *dA, float *part, int max_blocks, float *dw_db, cudaStream_t s);
+void launch_adam(float *theta, const float *grad, float *m, float *v, long long n, float lr, float b1, float b2,
+                 float eps, int t, __nv_bfloat16 *shadow, cudaStream_t s);
+void launch_to_bf16(const float *x, long long n, __nv_bfloat16 *y, cudaStream_t s);
+void launch_transpose_w(const __nv_bfloat16 *w, int co, int taps, int ci, __nv_bfloat16 *wt, cudaStream_t s);
+void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cudaStream_t s);
+void launch_gather_patches(const float *img, int nx, const int *oz, const int *ox, const int *sel, int nb, int p,
+                           const float *scale, float *dst, cudaStream_t s);
+void launch_pad_image(const float *img, int nz, int nx, int Hp, int Wp, const float *scale, float *dst,
+                      cudaStream_t s);
+void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const float *scale, float *dst,
+                       cudaStream_t s);
+void launch_absmax(const float *x, long long n, unsigned *mx, float *scale_out, cudaStream_t s);
+void launch_pad_first_w(const __nv_bfloat16 *w, int co, int cpad, __nv_bfloat16 *wp, cudaStream_t s);
+void launch_unpad_first_grad(const float *gp, int co, int cpad, float *g, cudaStream_t s);
+void launch_loss_accum(const double *partial, int nblocks, double weight, double *acc, cudaStream_t s);
+
+}  // namespace nn
+}  // namespace dhfwi

@@ -1,0 +1,808 @@
+// Kernels of the deblurring network (Section 2.4 / Appendix A of arXiv
+// 2403.17518): BF16 implicit-GEMM convolutions on the tensor cores with FP32
+// accumulation (forward, input gradient, weight gradient; 3x3 and 2x2-stride-2
+// transposed), average pooling, LeakyReLU backward, MSE, Adam with cosine
+// annealing, and the image <-> patch plumbing.  Activations are NHWC bf16.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "nn_internal.h"
+
+namespace dhfwi {
+namespace nn {
+
+// ---------------------------------------------------------------------------
+// PTX helpers: asynchronous copies, ldmatrix, mma.sync m16n8k16 bf16
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp16(void *smem, const void *gmem, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(pred ? 16 : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void mma16816(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------------------
+// Implicit GEMM "fprop" form: C[m][n] = sum_k A[m][k] B[k][n].
+//   m: output pixel (img, ho, wo) of an Ho x Wo grid;
+//   k = tap * C + c: source pixel (img, scale*ho + dh[tap], scale*wo + dw[tap]),
+//     channel c of a NHWC bf16 tensor (zero outside the source grid);
+//   B^T[n][k] dense bf16 row-major (k contiguous).
+// Covers: conv 3x3 forward (taps dh,dw in -1..1), conv 3x3 input gradient
+// (taps 1-dh), transposed-conv forward (1 tap, n = (co,a,b)) and transposed-
+// conv input gradient (scale 2, taps (a,b)).
+// Tile 128 x BN x 32, 4 warps along m, 3-stage cp.async pipeline.
+// ---------------------------------------------------------------------------
+constexpr int BM = 128, BK = 32, STAGES = 3, SK = BK + 8;  // +8 halves: conflict-free ldmatrix
+
+template <int BN>
+struct FpropSmem {
+    __nv_bfloat16 a[STAGES][BM][SK];
+    __nv_bfloat16 b[STAGES][BN][SK];
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    FpropSmem<BN> &S = *reinterpret_cast<FpropSmem<BN> *>(smraw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int K = P.ntaps * P.C;
+    const int nk = (K + BK - 1) / BK;
+    const int HWo = P.Ho * P.Wo;
+
+    // Each thread loads fixed 16-byte chunks of the A and B tiles.
+    // A: 128 rows x 4 chunks = 512 chunks -> 4 per thread; B: BN x 4.
+    int a_img[4], a_ho[4], a_wo[4];
+    bool a_ok[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int row = (tid + i * 128) >> 2;
+        const int m = m0 + row;
+        a_ok[i] = m < P.M;
+        const int mm = a_ok[i] ? m : 0;
+        a_img[i] = mm / HWo;
+        const int r = mm - a_img[i] * HWo;
+        a_ho[i] = r / P.Wo;
+        a_wo[i] = r - a_ho[i] * P.Wo;
+    }
+    auto load_stage = [&](int st, int kt) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int idx = tid + i * 128;
+            const int row = idx >> 2, ch = idx & 3;
+            const int k = kt * BK + ch * 8;
+            bool ok = a_ok[i] && k < K;
+            const __nv_bfloat16 *src = P.src;
+            if (ok) {
+                const int tap = k / P.C, c = k - tap * P.C;
+                const int hs = P.scale * a_ho[i] + P.dh[tap], ws = P.scale * a_wo[i] + P.dw[tap];
+                ok = hs >= 0 && hs < P.Hs && ws >= 0 && ws < P.Ws;
+                if (ok) src = P.src + (((long long)a_img[i] * P.Hs + hs) * P.Ws + ws) * P.src_stride + P.src_off + c;
+            }
+            cp16(&S.a[st][row][ch * 8], src, ok);
+        }
+#pragma unroll
+        for (int i = 0; i < (BN * 4 + 127) / 128; i++) {
+            const int idx = tid + i * 128;
+            if (idx < BN * 4) {
+                const int row = idx >> 2, ch = idx & 3;
+                const int n = n0 + row, k = kt * BK + ch * 8;
+                const bool ok = n < P.N && k < K;
+                cp16(&S.b[st][row][ch * 8], ok ? P.bt + (long long)n * K + k : P.bt, ok);
+            }
+        }
+    };
+
+    float acc[2][BN / 8][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < BN / 8; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
+
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; s++) {
+        if (s < nk) load_stage(s, s);
+        cp_commit();
+    }
+    for (int kt = 0; kt < nk; kt++) {
+        cp_wait<STAGES - 2>();
+        __syncthreads();
+        {
+            const int nxt = kt + STAGES - 1;
+            if (nxt < nk) load_stage(nxt % STAGES, nxt);
+            cp_commit();
+        }
+        const int st = kt % STAGES;
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            unsigned af[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int r = warp * 32 + i * 16 + (lane & 15);
+                ldsm_x4(af[i], &S.a[st][r][kk + (lane >> 4) * 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < BN / 8; j += 2) {
+                unsigned bf[4];
+                const int r = j * 8 + (lane & 7) + ((lane >> 4) << 3);
+                ldsm_x4(bf, &S.b[st][r][kk + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    mma16816(acc[i][j], af[i], bf[0], bf[1]);
+                    mma16816(acc[i][j + 1], af[i], bf[2], bf[3]);
+                }
+            }
+        }
+    }
+    cp_wait<0>();
+
+    // Epilogue.
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            const int m = m0 + warp * 32 + i * 16 + g + half * 8;
+            if (m >= P.M) continue;
+            const int img = m / HWo;
+            const int r = m - img * HWo;
+            const int ho = r / P.Wo, wo = r - ho * P.Wo;
+#pragma unroll
+            for (int j = 0; j < BN / 8; j++) {
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int n = n0 + j * 8 + 2 * t + e;
+                    if (n >= P.N) continue;
+                    float v = acc[i][j][half * 2 + e];
+                    if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
+                        v += P.bias[n];
+                        if (EPI == EPI_BF16_LEAKY) v = v > 0.f ? v : P.slope * v;
+                        const long long o = (long long)m * P.dst_stride + P.dst_off + n;
+                        P.dst_bf16[o] = __float2bfloat16_rn(v);
+                    } else if (EPI == EPI_BF16_CONVT) {
+                        // n = co*4 + a*2 + b -> output pixel (2ho+a, 2wo+b), channel co.
+                        const int co = n >> 2, a = (n >> 1) & 1, b = n & 1;
+                        v += P.bias[co];
+                        const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
+                        P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v);
+                    } else {  // EPI_F32 / EPI_F32_ADD
+                        const long long o = (long long)m * P.dst_stride + P.dst_off + n;
+                        if (EPI == EPI_F32_ADD) v += P.dst_f32[o];
+                        P.dst_f32[o] = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Implicit GEMM "wgrad" form (split over k): C[m][n] = sum_k A[m][k] B[k][n]
+//   k: pixel (img, h, w) of an H x W grid (range [k_begin, k_end) per CTA);
+//   A[m][k] = G[pixel'(k, m)][m-channel], B[k][n] = X[pixel''(k, n)][n-channel].
+// Conv 3x3 weight gradient: m = co (G = output gradient at pixel k),
+//   n = tap*Ci + ci (X = input at pixel k shifted by tap).
+// Transposed conv weight gradient: m = (a*2+b)*Co + co (G at the fine pixel
+//   (2h+a, 2w+b)), n = ci (X at the coarse pixel k).
+// Tiles are stored k-major in shared memory and read with ldmatrix.trans.
+// Each CTA writes its partial C tile to part[blockIdx.z][M][N].
+// ---------------------------------------------------------------------------
+constexpr int WBM = 64, WBN = 64, WBK = 32, WSM = WBM + 8, WSN = WBN + 8;
+
+struct WgradSmem {
+    __nv_bfloat16 a[STAGES][WBK][WSM];
+    __nv_bfloat16 b[STAGES][WBK][WSN];
+};
+
+__global__ void __launch_bounds__(128) igemm_wgrad_kernel(WgradArgs P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    WgradSmem &S = *reinterpret_cast<WgradSmem *>(smraw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.x * WBM, n0 = blockIdx.y * WBN;
+    const long long HW = (long long)P.H * P.W;
+    const long long KP = (long long)P.nimg * HW;
+    const long long per = (KP + gridDim.z - 1) / gridDim.z;
+    const long long kb = (long long)blockIdx.z * per;
+    const long long ke = kb + per < KP ? kb + per : KP;
+    const int nk = ke > kb ? (int)((ke - kb + WBK - 1) / WBK) : 0;
+
+    // A tile: 32 k-rows x 64 m = 32 x 8 chunks = 256 chunks -> 2 per thread.
+    // B tile: 32 k-rows x 64 n = 256 chunks -> 2 per thread.
+    auto load_stage = [&](int st, int kt) {
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int idx = tid + i * 128;
+            const int kr = idx >> 3, ch = idx & 7;
+            const long long k = kb + (long long)kt * WBK + kr;
+            // A chunk: 8 consecutive m.
+            {
+                const int m = m0 + ch * 8;
+                bool ok = k < ke && m < P.M;
+                const __nv_bfloat16 *src = P.g;
+                if (ok) {
+                    const int img = (int)(k / HW);
+                    const int r = (int)(k - img * HW);
+                    const int h = r / P.W, w = r - h * P.W;
+                    if (P.mode == WG_CONV) {
+                        src = P.g + k * P.g_stride + m;
+                    } else {  // WG_CONVT: m = ab*Co + co
+                        const int ab = m / P.co, co = m - ab * P.co;
+                        const long long pix = ((long long)img * (2 * P.H) + 2 * h + (ab >> 1)) * (2 * P.W) + 2 * w + (ab & 1);
+                        src = P.g + pix * P.g_stride + co;
+                    }
+                }
+                cp16(&S.a[st][kr][ch * 8], src, ok);
+            }
+            // B chunk: 8 consecutive n.
+            {
+                const int n = n0 + ch * 8;
+                bool ok = k < ke && n < P.N;
+                const __nv_bfloat16 *src = P.x;
+                if (ok) {
+                    const int img = (int)(k / HW);
+                    const int r = (int)(k - img * HW);
+                    const int h = r / P.W, w = r - h * P.W;
+                    if (P.mode == WG_CONV) {
+                        const int tap = n / P.ci, c = n - tap * P.ci;
+                        const int hs = h + tap / 3 - 1, ws = w + tap % 3 - 1;
+                        ok = hs >= 0 && hs < P.H && ws >= 0 && ws < P.W;
+                        if (ok) src = P.x + (((long long)img * P.H + hs) * P.W + ws) * P.x_stride + P.x_off + c;
+                    } else {
+                        src = P.x + k * P.x_stride + P.x_off + n;
+                    }
+                }
+                cp16(&S.b[st][kr][ch * 8], src, ok);
+            }
+        }
+    };
+
+    // Warps: 2 x 2 over the 64 x 64 tile, each 32 x 32.
+    const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
+
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; s++) {
+        if (s < nk) load_stage(s, s);
+        cp_commit();
+    }
+    for (int kt = 0; kt < nk; kt++) {
+        cp_wait<STAGES - 2>();
+        __syncthreads();
+        {
+            const int nxt = kt + STAGES - 1;
+            if (nxt < nk) load_stage(nxt % STAGES, nxt);
+            cp_commit();
+        }
+        const int st = kt % STAGES;
+#pragma unroll
+        for (int kk = 0; kk < WBK; kk += 16) {
+            unsigned af[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                // matrices (m0-7,k0-7) (m8-15,k0-7) (m0-7,k8-15) (m8-15,k8-15), stored k-major
+                const int mat = lane >> 3;
+                const int krow = kk + (lane & 7) + ((mat >> 1) << 3);
+                const int mcol = wm + i * 16 + ((mat & 1) << 3);
+                ldsm_x4_t(af[i], &S.a[st][krow][mcol]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j += 2) {
+                unsigned bf[4];
+                // matrices (k0-7,n0-7) (k8-15,n0-7) (k0-7,n8-15) (k8-15,n8-15), stored k-major
+                const int mat = lane >> 3;
+                const int krow = kk + (lane & 7) + ((mat & 1) << 3);
+                const int ncol = wn + j * 8 + ((mat >> 1) << 3);
+                ldsm_x4_t(bf, &S.b[st][krow][ncol]);
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    mma16816(acc[i][j], af[i], bf[0], bf[1]);
+                    mma16816(acc[i][j + 1], af[i], bf[2], bf[3]);
+                }
+            }
+        }
+    }
+    cp_wait<0>();
+    float *out = P.part + (long long)blockIdx.z * P.M * P.N;
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            const int m = m0 + wm + i * 16 + g + half * 8;
+            if (m >= P.M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int n = n0 + wn + j * 8 + 2 * t + e;
+                    if (n < P.N) out[(long long)m * P.N + n] = acc[i][j][half * 2 + e];
+                }
+        }
+}
+
+// Sum of the split partials in split order; writes the weight gradient in
+// the parameter layout (conv: [co][tap][ci] = C[co][n]; transposed conv:
+// [co][a][b][ci] = C[(a*2+b)*Co + co][ci]).
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, int M, int N, int mode, int co_n,
+                                    float *__restrict__ dw) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)M * N) return;
+    float s = 0.f;
+    for (int z = 0; z < splits; z++) s += part[(long long)z * M * N + idx];
+    const int m = (int)(idx / N), n = (int)(idx - (long long)m * N);
+    long long o;
+    if (mode == WG_CONV) {
+        o = idx;
+    } else {
+        const int ab = m / co_n, co = m - ab * co_n;
+        o = ((long long)co * 4 + ab) * N + n;
+    }
+    dw[o] = s;
+}
+
+// Bias gradient: db[c] = sum over pixels of g[p][c] (bf16 in, fixed order:
+// per-block partial sums then a second pass).
+__global__ void bias_grad_partial_kernel(const __nv_bfloat16 *__restrict__ g, int stride, int C, long long P,
+                                         int rows_per_block, float *__restrict__ part) {
+    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const long long p0 = (long long)blockIdx.x * rows_per_block;
+    const long long p1 = p0 + rows_per_block < P ? p0 + rows_per_block : P;
+    float s = 0.f;
+    for (long long p = p0; p < p1; p++) s += __bfloat162float(g[p * stride + c]);
+    part[(long long)blockIdx.x * C + c] = s;
+}
+
+__global__ void bias_grad_final_kernel(const float *__restrict__ part, int nblk, int C, float *__restrict__ db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int b = 0; b < nblk; b++) s += part[(long long)b * C + c];
+    db[c] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise and small kernels
+// ---------------------------------------------------------------------------
+// Average pool 3x3, stride 2, zero padding 1 counted (divide by 9); output bf16.
+__global__ void avgpool_fwd_kernel(const __nv_bfloat16 *__restrict__ x, int xs, int xo, int nimg, int H, int W, int C,
+                                   __nv_bfloat16 *__restrict__ y) {
+    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
+    const long long n = (long long)nimg * Ho * Wo * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long r = i / C;
+        const int wo = (int)(r % Wo);
+        r /= Wo;
+        const int ho = (int)(r % Ho);
+        const int img = (int)(r / Ho);
+        float s = 0.f;
+        for (int a = 0; a < 3; a++) {
+            const int h = 2 * ho + a - 1;
+            if (h < 0 || h >= H) continue;
+            for (int b = 0; b < 3; b++) {
+                const int w = 2 * wo + b - 1;
+                if (w < 0 || w >= W) continue;
+                s += __bfloat162float(x[(((long long)img * H + h) * W + w) * xs + xo + c]);
+            }
+        }
+        y[i] = __float2bfloat16_rn(s * (1.0f / 9.0f));
+    }
+}
+
+// dx[h][w] (+)= sum of dy/9 over the pooling windows containing (h, w).
+__global__ void avgpool_bwd_kernel(const float *__restrict__ dy, int nimg, int H, int W, int C, float *__restrict__ dx,
+                                   int accumulate) {
+    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
+    const long long n = (long long)nimg * H * W * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long r = i / C;
+        const int w = (int)(r % W);
+        r /= W;
+        const int h = (int)(r % H);
+        const int img = (int)(r / H);
+        float s = 0.f;
+        // Windows (ho, wo) with 2ho-1 <= h <= 2ho+1.
+        for (int ho = (h > 0 ? (h) / 2 : 0); ho <= (h + 1) / 2 && ho < Ho; ho++) {
+            if (2 * ho - 1 > h || 2 * ho + 1 < h) continue;
+            for (int wo = (w > 0 ? (w) / 2 : 0); wo <= (w + 1) / 2 && wo < Wo; wo++) {
+                if (2 * wo - 1 > w || 2 * wo + 1 < w) continue;
+                s += dy[(((long long)img * Ho + ho) * Wo + wo) * C + c];
+            }
+        }
+        s *= (1.0f / 9.0f);
+        dx[i] = accumulate ? dx[i] + s : s;
+    }
+}
+
+// g = bf16(dA * (a > 0 ? 1 : slope)) for a LeakyReLU output a (bf16, with
+// channel stride/offset), dA float32 dense [P][C].
+__global__ void leaky_bwd_kernel(const float *__restrict__ dA, const __nv_bfloat16 *__restrict__ a, int as, int ao,
+                                 long long P, int C, float slope, __nv_bfloat16 *__restrict__ g) {
+    const long long n = P * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C;
+        const int c = (int)(i - p * C);
+        const float av = __bfloat162float(a[p * as + ao + c]);
+        g[i] = __float2bfloat16_rn(dA[i] * (av > 0.f ? 1.0f : slope));
+    }
+}
+
+// Copy channels [off, off+C) of a float32 [P][Ct] tensor into bf16 [P][C].
+__global__ void f32_to_bf16_slice_kernel(const float *__restrict__ x, int xs, int xo, long long P, int C,
+                                         __nv_bfloat16 *__restrict__ y) {
+    const long long n = P * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C;
+        const int c = (int)(i - p * C);
+        y[i] = __float2bfloat16_rn(x[p * xs + xo + c]);
+    }
+}
+
+// dst[P][C] += src[P][Cs] channels [off, off+C)  (float32)
+__global__ void add_slice_kernel(const float *__restrict__ src, int ss, int so, long long P, int C,
+                                 float *__restrict__ dst) {
+    const long long n = P * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C;
+        const int c = (int)(i - p * C);
+        dst[i] += src[p * ss + so + c];
+    }
+}
+
+// Output layer 1x1 conv (Cin -> 1), fp32 out: out[p] = b + sum_c bf16(W[c]) a[p][c].
+__global__ void conv1x1_fwd_kernel(const __nv_bfloat16 *__restrict__ a, int C, long long P,
+                                   const __nv_bfloat16 *__restrict__ w, const float *__restrict__ b,
+                                   float *__restrict__ out) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int c = 0; c < C; c++) s = fmaf(__bfloat162float(w[c]), __bfloat162float(a[p * C + c]), s);
+        out[p] = s + b[0];
+    }
+}
+
+// MSE over P outputs: loss partials (double) and g = bf16(2 (out - y) / P).
+__global__ void mse_kernel(const float *__restrict__ out, const float *__restrict__ y, long long P,
+                           __nv_bfloat16 *__restrict__ g, double *__restrict__ partial) {
+    double acc = 0.0;
+    const float sc = 2.0f / (float)P;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+        const float r = out[i] - y[i];
+        acc += (double)r * r;
+        g[i] = __float2bfloat16_rn(sc * r);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = v;
+    }
+}
+
+// Output layer backward: dW[c] = sum_p g[p] a[p][c] (per-block partials),
+// db = sum_p g[p], dA[p][c] = bf16(W[c]) g[p].
+__global__ void conv1x1_bwd_data_kernel(const __nv_bfloat16 *__restrict__ g, long long P, int C,
+                                        const __nv_bfloat16 *__restrict__ w, float *__restrict__ dA) {
+    const long long n = P * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C;
+        const int c = (int)(i - p * C);
+        dA[i] = __bfloat162float(w[c]) * __bfloat162float(g[p]);
+    }
+}
+
+__global__ void conv1x1_wgrad_partial_kernel(const __nv_bfloat16 *__restrict__ g, const __nv_bfloat16 *__restrict__ a,
+                                             long long P, int C, int rows, float *__restrict__ part) {
+    // part[blk][c] for c < C, part[blk][C] = sum g
+    const int c = threadIdx.x;
+    const long long p0 = (long long)blockIdx.x * rows;
+    const long long p1 = p0 + rows < P ? p0 + rows : P;
+    if (c > C) return;
+    float s = 0.f;
+    for (long long p = p0; p < p1; p++) {
+        const float gv = __bfloat162float(g[p]);
+        s += c < C ? gv * __bfloat162float(a[p * C + c]) : gv;
+    }
+    part[(long long)blockIdx.x * (C + 1) + c] = s;
+}
+
+// Adam with bias correction (Adam's step t is 1-based), master weights fp32,
+// and the bf16 shadow copy refreshed.
+__global__ void adam_kernel(float *__restrict__ theta, const float *__restrict__ grad, float *__restrict__ m,
+                            float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2, __nv_bfloat16 *__restrict__ shadow) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float g = grad[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * g;
+        const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float mh = mi / bc1, vh = vi / bc2;
+        const float th = theta[i] - lr * mh / (sqrtf(vh) + eps);
+        theta[i] = th;
+        shadow[i] = __float2bfloat16_rn(th);
+    }
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ x, long long n, __nv_bfloat16 *__restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// Transposed weights for the input-gradient GEMM:
+// wt[ci][tap][co] = w[co][tap][ci] (bf16), taps = 9 (conv) or 4 (transposed conv).
+__global__ void transpose_w_kernel(const __nv_bfloat16 *__restrict__ w, int co, int taps, int ci,
+                                   __nv_bfloat16 *__restrict__ wt) {
+    const long long n = (long long)co * taps * ci;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % ci);
+        long long r = i / ci;
+        const int t = (int)(r % taps);
+        const int o = (int)(r / taps);
+        wt[((long long)c * taps + t) * co + o] = w[i];
+    }
+}
+
+// Input image (float32 [img][H][W]) into a bf16 NHWC tensor of Cp channels
+// (channel 0 = the image, others 0).
+__global__ void input_pack_kernel(const float *__restrict__ x, long long P, int Cp, __nv_bfloat16 *__restrict__ y) {
+    const long long n = P * Cp;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % Cp);
+        y[i] = __float2bfloat16_rn(c == 0 ? x[i / Cp] : 0.f);
+    }
+}
+
+// Patches: dst[b][i][j] = img[oz + i][ox + j] * scale for patch b = sel[b].
+__global__ void gather_patches_kernel(const float *__restrict__ img, int nx, const int *__restrict__ oz,
+                                      const int *__restrict__ ox, const int *__restrict__ sel, int nb, int p,
+                                      const float *__restrict__ scale, float *__restrict__ dst) {
+    const long long n = (long long)nb * p * p;
+    const float sc = *scale;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(i % p);
+        long long r = i / p;
+        const int ii = (int)(r % p);
+        const int b = (int)(r / p);
+        const int pi = sel[b];
+        dst[i] = img[(long long)(oz[pi] + ii) * nx + ox[pi] + j] * sc;
+    }
+}
+
+// Full-image input: zero padded to Hp x Wp, scaled.
+__global__ void pad_image_kernel(const float *__restrict__ img, int nz, int nx, int Hp, int Wp,
+                                 const float *__restrict__ scale, float *__restrict__ dst) {
+    const long long n = (long long)Hp * Wp;
+    const float sc = *scale;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(i % Wp), h = (int)(i / Wp);
+        dst[i] = (h < nz && w < nx) ? img[(long long)h * nx + w] * sc : 0.f;
+    }
+}
+
+__global__ void crop_image_kernel(const float *__restrict__ src, int Hp, int Wp, int nz, int nx,
+                                  const float *__restrict__ scale, float *__restrict__ dst) {
+    const long long n = (long long)nz * nx;
+    const float sc = *scale;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(i % nx), h = (int)(i / nx);
+        dst[i] = src[(long long)h * Wp + w] * sc;
+    }
+}
+
+// max |x| over n values -> *out as float bits via atomicMax (values >= 0).
+__global__ void absmax_kernel(const float *__restrict__ x, long long n, unsigned *out) {
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// scale_out[0] = 1 / max (or 1 if max == 0); scale_out[1] = max.
+__global__ void absmax_finish_kernel(const unsigned *mx, float *scale_out) {
+    const float m = __uint_as_float(*mx);
+    scale_out[0] = m > 0.f ? 1.0f / m : 1.0f;
+    scale_out[1] = m > 0.f ? m : 1.0f;
+}
+
+// First layer (one input channel) padded to cpad channels: wp[co][tap][c] =
+// w[co][tap] for c == 0, else 0; and the gradient taken back from channel 0.
+__global__ void pad_first_w_kernel(const __nv_bfloat16 *__restrict__ w, int co, int cpad,
+                                   __nv_bfloat16 *__restrict__ wp) {
+    const int n = co * 9 * cpad;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = i % cpad;
+        wp[i] = c == 0 ? w[i / cpad] : __float2bfloat16_rn(0.f);
+    }
+}
+
+__global__ void unpad_first_grad_kernel(const float *__restrict__ gp, int co, int cpad, float *__restrict__ g) {
+    const int n = co * 9;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) g[i] = gp[i * cpad];
+}
+
+// acc[0] += weight * sum(partial) (single thread, fixed order).
+__global__ void loss_accum_kernel(const double *__restrict__ partial, int nblocks, double weight, double *acc) {
+    double s = 0.0;
+    for (int i = 0; i < nblocks; i++) s += partial[i];
+    acc[0] += weight * s;
+}
+
+// ===========================================================================
+// Host launchers
+// ===========================================================================
+static int grid_for(long long n, int block = 256) {
+    long long g = (n + block - 1) / block;
+    return (int)(g < 152 * 16 ? (g < 1 ? 1 : g) : 152 * 16);
+}
+
+template <int BN, int EPI>
+static void fprop_launch(const FpropArgs &a, cudaStream_t s) {
+    const size_t sm = sizeof(FpropSmem<BN>);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(igemm_fprop_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN);
+    igemm_fprop_kernel<BN, EPI><<<grid, 128, sm, s>>>(a);
+}
+
+void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
+    const bool small = a.N <= 32;
+    switch (epi) {
+    case EPI_BF16_LEAKY: small ? fprop_launch<32, EPI_BF16_LEAKY>(a, s) : fprop_launch<64, EPI_BF16_LEAKY>(a, s); break;
+    case EPI_BF16: small ? fprop_launch<32, EPI_BF16>(a, s) : fprop_launch<64, EPI_BF16>(a, s); break;
+    case EPI_BF16_CONVT: small ? fprop_launch<32, EPI_BF16_CONVT>(a, s) : fprop_launch<64, EPI_BF16_CONVT>(a, s); break;
+    case EPI_F32: small ? fprop_launch<32, EPI_F32>(a, s) : fprop_launch<64, EPI_F32>(a, s); break;
+    default: small ? fprop_launch<32, EPI_F32_ADD>(a, s) : fprop_launch<64, EPI_F32_ADD>(a, s); break;
+    }
+}
+
+int wgrad_splits(long long kpix, int M, int N) {
+    const int tiles = ((M + WBM - 1) / WBM) * ((N + WBN - 1) / WBN);
+    long long want = (152LL * 4 + tiles - 1) / tiles;
+    long long maxs = (kpix + 255) / 256;  // at least 256 pixels per split
+    if (want > maxs) want = maxs;
+    if (want < 1) want = 1;
+    if (want > 512) want = 512;
+    return (int)want;
+}
+
+void launch_wgrad(const WgradArgs &a, int splits, float *dw, cudaStream_t s) {
+    const size_t sm = sizeof(WgradSmem);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(igemm_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    dim3 grid((a.M + WBM - 1) / WBM, (a.N + WBN - 1) / WBN, splits);
+    igemm_wgrad_kernel<<<grid, 128, sm, s>>>(a);
+    const long long mn = (long long)a.M * a.N;
+    wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, splits, a.M, a.N, a.mode, a.co, dw);
+}
+
+void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, float *part, int max_blocks,
+                      float *db, cudaStream_t s) {
+    int rows = (int)((P + max_blocks - 1) / max_blocks);
+    if (rows < 64) rows = 64;
+    const int nblk = (int)((P + rows - 1) / rows);
+    dim3 grid(nblk, (C + 127) / 128);
+    bias_grad_partial_kernel<<<grid, 128, 0, s>>>(g, stride, C, P, rows, part);
+    bias_grad_final_kernel<<<(C + 127) / 128, 128, 0, s>>>(part, nblk, C, db);
+}
+
+void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H, int W, int C, __nv_bfloat16 *y,
+                        cudaStream_t s) {
+    const long long n = (long long)nimg * ((H - 1) / 2 + 1) * ((W - 1) / 2 + 1) * C;
+    avgpool_fwd_kernel<<<grid_for(n), 256, 0, s>>>(x, xs, xo, nimg, H, W, C, y);
+}
+void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *dx, int accumulate, cudaStream_t s) {
+    const long long n = (long long)nimg * H * W * C;
+    avgpool_bwd_kernel<<<grid_for(n), 256, 0, s>>>(dy, nimg, H, W, C, dx, accumulate);
+}
+void launch_leaky_bwd(const float *dA, const __nv_bfloat16 *a, int as, int ao, long long P, int C, float slope,
+                      __nv_bfloat16 *g, cudaStream_t s) {
+    leaky_bwd_kernel<<<grid_for(P * C), 256, 0, s>>>(dA, a, as, ao, P, C, slope, g);
+}
+void launch_f32_to_bf16_slice(const float *x, int xs, int xo, long long P, int C, __nv_bfloat16 *y, cudaStream_t s) {
+    f32_to_bf16_slice_kernel<<<grid_for(P * C), 256, 0, s>>>(x, xs, xo, P, C, y);
+}
+void launch_add_slice(const float *src, int ss, int so, long long P, int C, float *dst, cudaStream_t s) {
+    add_slice_kernel<<<grid_for(P * C), 256, 0, s>>>(src, ss, so, P, C, dst);
+}
+void launch_conv1x1_fwd(const __nv_bfloat16 *a, int C, long long P, const __nv_bfloat16 *w, const float *b, float *out,
+                        cudaStream_t s) {
+    conv1x1_fwd_kernel<<<grid_for(P), 256, 0, s>>>(a, C, P, w, b, out);
+}
+void launch_mse(const float *out, const float *y, long long P, __nv_bfloat16 *g, double *partial, int nblocks,
+                cudaStream_t s) {
+    mse_kernel<<<nblocks, 256, 0, s>>>(out, y, P, g, partial);
+}
+void launch_conv1x1_bwd(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long long P, int C, const __nv_bfloat16 *w,
+                        float *dA, float *part, int max_blocks, float *dw_db, cudaStream_t s) {
+    conv1x1_bwd_data_kernel<<<grid_for(P * C), 256, 0, s>>>(g, P, C, w, dA);
+    int rows = (int)((P + max_blocks - 1) / max_blocks);
+    if (rows < 64) rows = 64;
+    const int nblk = (int)((P + rows - 1) / rows);
+    conv1x1_wgrad_partial_kernel<<<nblk, ((C + 1 + 31) / 32) * 32, 0, s>>>(g, a, P, C, rows, part);
+    // dw_db[0..C) = dW, dw_db[C] = db: reuse the bias-final reduction over C+1 columns.
+    bias_grad_final_kernel<<<(C + 1 + 127) / 128, 128, 0, s>>>(part, nblk, C + 1, dw_db);
+}
+void launch_adam(float *theta, const float *grad, float *m, float *v, long long n, float lr, float b1, float b2,
+                 float eps, int t, __nv_bfloat16 *shadow, cudaStream_t s) {
+    const float bc1 = 1.0f - powf(b1, (float)t), bc2 = 1.0f - powf(b2, (float)t);
+    adam_kernel<<<grid_for(n), 256, 0, s>>>(theta, grad, m, v, n, lr, b1, b2, eps, bc1, bc2, shadow);
+}
+void launch_to_bf16(const float *x, long long n, __nv_bfloat16 *y, cudaStream_t s) {
+    to_bf16_kernel<<<grid_for(n), 256, 0, s>>>(x, n, y);
+}
+void launch_transpose_w(const __nv_bfloat16 *w, int co, int taps, int ci, __nv_bfloat16 *wt, cudaStream_t s) {
+    transpose_w_kernel<<<grid_for((long long)co * taps * ci), 256, 0, s>>>(w, co, taps, ci, wt);
+}
+void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cudaStream_t s) {
+    input_pack_kernel<<<grid_for(P * Cp), 256, 0, s>>>(x, P, Cp, y);
+}
+void launch_gather_patches(const float *img, int nx, const int *oz, const int *ox, const int *sel, int nb, int p,
+                           const float *scale, float *dst, cudaStream_t s) {
+    gather_patches_kernel<<<grid_for((long long)nb * p * p), 256, 0, s>>>(img, nx, oz, ox, sel, nb, p, scale, dst);
+}
+void launch_pad_image(const float *img, int nz, int nx, int Hp, int Wp, const float *scale, float *dst,
+                      cudaStream_t s) {
+    pad_image_kernel<<<grid_for((long long)Hp * Wp), 256, 0, s>>>(img, nz, nx, Hp, Wp, scale, dst);
+}
+void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const float *scale, float *dst,
+                       cudaStream_t s) {
+    crop_image_kernel<<<grid_for((long long)nz * nx), 256, 0, s>>>(src, Hp, Wp, nz, nx, scale, dst);
+}
+void launch_pad_first_w(const __nv_bfloat16 *w, int co, int cpad, __nv_bfloat16 *wp, cudaStream_t s) {
+    pad_first_w_kernel<<<grid_for((long long)co * 9 * cpad), 256, 0, s>>>(w, co, cpad, wp);
+}
+void launch_unpad_first_grad(const float *gp, int co, int cpad, float *g, cudaStream_t s) {
+    unpad_first_grad_kernel<<<grid_for((long long)co * 9), 256, 0, s>>>(gp, co, cpad, g);
+}
+void launch_loss_accum(const double *partial, int nblocks, double weight, double *acc, cudaStream_t s) {
+    loss_accum_kernel<<<1, 1, 0, s>>>(partial, nblocks, weight, acc);
+}
+void launch_absmax(const float *x, long long n, unsigned *mx, float *scale_out, cudaStream_t s) {
+    cudaMemsetAsync(mx, 0, sizeof(unsigned), s);
+    absmax_kernel<<<grid_for(n), 256, 0, s>>>(x, n, mx);
+    absmax_finish_kernel<<<1, 1, 0, s>>>(mx, scale_out);
+}
+
+}  // namespace nn
+}  // namespace dhfwi

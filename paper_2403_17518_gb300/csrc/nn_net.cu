@@ -1,12 +1,873 @@
-// Deblurring network state (Section 2.4): owned by the context.
+// Deblurring network (Section 2.4 / Appendix A of arXiv 2403.17518) on the
+// GPU: parameter state, activation workspace, forward, backward, Adam
+// training with cosine annealing on image patches, and full-image apply.
+//
+// Per FWI iteration the network learns the map from the doubly migrated
+// image (Eq. 15) to the gradient (Eq. 13) and is then applied to the
+// gradient (Section 2.3.1); weights carry over between calls when
+// warm_start is set (transfer learning, Section 2.3.1).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dhfwi.h"
 #include "nn_api.h"
+#include "nn_internal.h"
 
 namespace dhfwi {
+using namespace nn;
 
-struct NetState {
-    int placeholder = 0;
+namespace {
+
+constexpr int CPAD = 8;          // first-layer input channels after padding
+constexpr int MSE_BLOCKS = 256;
+constexpr int RED_BLOCKS = 512;  // max blocks of the bias reductions
+
+enum { K_C3 = 0, K_CT = 1, K_C1 = 2 };
+
+struct LayerDesc {
+    int kind, ci, co;
+    long long off;   // offset of the weight in the flat parameter vector (bias follows)
+    long long nw;    // number of weight values
 };
 
-void net_destroy(NetState *net) { delete net; }
+int ilog_mult(int v, int levels) { return (v >> levels) << levels == v; }
+
+}  // namespace
+
+struct NetState {
+    int base = 0, levels = 0;
+    std::vector<LayerDesc> L;
+    long long nparams = 0;
+    bool have_weights = false;
+    // Parameter state (device).
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *w16 = nullptr, *wt16 = nullptr, *w0pad = nullptr;
+    float *g0pad = nullptr;
+    // Workspace (device arena) sized for (wsN, wsH, wsW).
+    int wsN = 0, wsH = 0, wsW = 0;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    // Small buffers.
+    double *mse_part = nullptr, *loss_acc = nullptr;
+    float *red_part = nullptr;
+    size_t red_part_floats = 0;
+    float *wg_part = nullptr;
+    size_t wg_part_floats = 0;
+    unsigned *mx = nullptr;
+    float *scales = nullptr;  // [0..1] x scale, [2..3] y scale
+    int *oz = nullptr, *ox = nullptr, *perm = nullptr;
+    size_t oz_cap = 0, perm_cap = 0;
+    float *patch_x = nullptr, *patch_y = nullptr;
+    size_t patch_floats = 0;
+    long long launches = 0;
+
+    // Workspace views (filled by layout()).
+    struct Views {
+        __nv_bfloat16 *xin, *a_inc0;
+        std::vector<__nv_bfloat16 *> cat, pool, tmp, dec0, dec1;
+        __nv_bfloat16 *bottom, *gbuf;
+        float *xf, *yf, *out, *dA, *dB;
+        std::vector<float *> dskip;
+    } V;
+};
+
+namespace {
+
+int layer_index_down(const NetState &N, int l, int j) { return 2 + 2 * (l - 1) + j; }
+int layer_index_up(const NetState &N, int l, int j) { return 2 + 2 * N.levels + 3 * (l - 1) + j; }  // j: 0 t, 1 c0, 2 c1
+int layer_index_out(const NetState &N) { return (int)N.L.size() - 1; }
+
+void build_layers(NetState &N, int base, int levels) {
+    N.base = base;
+    N.levels = levels;
+    N.L.clear();
+    long long off = 0;
+    auto add = [&](int kind, int ci, int co) {
+        LayerDesc d;
+        d.kind = kind;
+        d.ci = ci;
+        d.co = co;
+        d.off = off;
+        d.nw = kind == K_C3 ? 9LL * ci * co : kind == K_CT ? 4LL * ci * co : (long long)ci * co;
+        off += d.nw + co;
+        N.L.push_back(d);
+    };
+    auto C = [&](int l) { return base << l; };
+    add(K_C3, 1, base);
+    add(K_C3, base, base);
+    for (int l = 1; l <= levels; l++) {
+        add(K_C3, C(l - 1), C(l));
+        add(K_C3, C(l), C(l));
+    }
+    for (int l = 1; l <= levels; l++) {
+        const int hi = C(levels - l + 1), lo = C(levels - l);
+        add(K_CT, hi, lo);
+        add(K_C3, 2 * lo, lo);
+        add(K_C3, lo, lo);
+    }
+    add(K_C1, base, 1);
+    N.nparams = off;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): state = seed + (counter+1) * golden.
+unsigned long long splitmix(unsigned long long seed, unsigned long long counter) {
+    unsigned long long z = seed + (counter + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void init_host(const NetState &N, unsigned long long seed, std::vector<float> &out) {
+    out.assign((size_t)N.nparams, 0.f);
+    for (const LayerDesc &d : N.L) {
+        const int fan = d.kind == K_C3 ? 9 * d.ci : d.ci;
+        const float bound = (float)(1.0 / std::sqrt((double)fan));
+        const long long cnt = d.nw + d.co;
+        for (long long i = 0; i < cnt; i++) {
+            const unsigned long long k = (unsigned long long)(d.off + i);
+            const float u = (float)(splitmix(seed, k) >> 40) * (1.0f / 16777216.0f);
+            const float two_u = 2.0f * u;
+            const float c = two_u - 1.0f;
+            out[(size_t)(d.off + i)] = bound * c;
+        }
+    }
+}
+
+void permutation_host(int n, unsigned long long seed, int epoch, std::vector<int> &perm) {
+    const unsigned long long key = seed ^ ((unsigned long long)(epoch + 1) * 0xD1B54A32D192ED03ull);
+    perm.resize(n);
+    for (int i = 0; i < n; i++) perm[i] = i;
+    for (int i = n - 1; i > 0; i--) {
+        const int j = (int)(splitmix(key, (unsigned long long)i) % (unsigned long long)(i + 1));
+        std::swap(perm[i], perm[j]);
+    }
+}
+
+std::vector<int> patch_origins(int n, int p, int stride) {
+    std::vector<int> o;
+    for (int v = 0; v + p <= n; v += stride) o.push_back(v);
+    if (o.empty() || o.back() != n - p) o.push_back(n - p);
+    return o;
+}
+
+int fail(dhfwi_ctx *ctx, int code, const char *msg) {
+    ctx_set_error(ctx, msg);
+    return code;
+}
+
+#define NCK(call)                                                              \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            char b_[256];                                                      \
+            snprintf(b_, sizeof b_, "%s: %s", #call, cudaGetErrorString(e_));  \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? DHFWI_ERR_OOM : DHFWI_ERR_CUDA, b_); \
+        }                                                                      \
+    } while (0)
+
+int dev_alloc(dhfwi_ctx *ctx, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char b[200];
+        snprintf(b, sizeof b, "network allocation of %.3f GB failed: %s", bytes / 1e9, cudaGetErrorString(e));
+        *p = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? DHFWI_ERR_OOM : DHFWI_ERR_CUDA, b);
+    }
+    return DHFWI_OK;
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+void free_params(NetState &N) {
+    dev_free(N.theta);
+    dev_free(N.grad);
+    dev_free(N.m);
+    dev_free(N.v);
+    dev_free(N.w16);
+    dev_free(N.wt16);
+    dev_free(N.w0pad);
+    dev_free(N.g0pad);
+    N.theta = N.grad = N.m = N.v = nullptr;
+    N.w16 = N.wt16 = N.w0pad = nullptr;
+    N.g0pad = nullptr;
+}
+
+int alloc_params(dhfwi_ctx *ctx, NetState &N) {
+    free_params(N);
+    const size_t n = (size_t)N.nparams;
+    int rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.theta, 4 * n))) return rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.grad, 4 * n))) return rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.m, 4 * n))) return rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.v, 4 * n))) return rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.w16, 2 * n))) return rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.wt16, 2 * n))) return rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.w0pad, 2 * 9 * CPAD * (size_t)N.base))) return rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.g0pad, 4 * 9 * CPAD * (size_t)N.base))) return rc;
+    return DHFWI_OK;
+}
+
+// bf16 shadow, transposed copies and the padded first layer from theta.
+void refresh_weights(NetState &N, cudaStream_t s, bool shadow_from_theta) {
+    if (shadow_from_theta) {
+        launch_to_bf16(N.theta, N.nparams, N.w16, s);
+        N.launches++;
+    }
+    for (size_t i = 0; i < N.L.size(); i++) {
+        const LayerDesc &d = N.L[i];
+        if (d.kind == K_C3 && i != 0) {
+            launch_transpose_w(N.w16 + d.off, d.co, 9, d.ci, N.wt16 + d.off, s);
+            N.launches++;
+        } else if (d.kind == K_CT) {
+            launch_transpose_w(N.w16 + d.off, d.co, 4, d.ci, N.wt16 + d.off, s);
+            N.launches++;
+        }
+    }
+    launch_pad_first_w(N.w16 + N.L[0].off, N.base, CPAD, N.w0pad, s);
+    N.launches++;
+}
+
+// Activation / gradient workspace for batches of up to (n, H, W).
+int layout(dhfwi_ctx *ctx, NetState &N, int n, int H, int W) {
+    if (N.arena && N.wsN >= n && N.wsH == H && N.wsW == W) return DHFWI_OK;
+    const int Lv = N.levels;
+    auto P = [&](int r) { return (size_t)n * (size_t)(H >> r) * (size_t)(W >> r); };
+    auto C = [&](int r) { return (size_t)N.base << r; };
+    size_t off = 0;
+    std::vector<std::pair<void **, size_t>> plan;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    // Offsets first, pointers after allocation.
+    std::vector<size_t> o_cat(Lv), o_pool(Lv + 1), o_tmp(Lv + 1), o_dec0(Lv), o_dec1(Lv), o_dskip(Lv);
+    const size_t o_xin = take(2 * P(0) * CPAD);
+    const size_t o_inc0 = take(2 * P(0) * C(0));
+    size_t max_pc2 = 0;
+    for (int r = 0; r < Lv; r++) {
+        o_cat[r] = take(2 * P(r) * 2 * C(r));
+        o_dec0[r] = take(2 * P(r) * C(r));
+        o_dec1[r] = take(2 * P(r) * C(r));
+        o_dskip[r] = take(4 * P(r) * C(r));
+        max_pc2 = std::max(max_pc2, P(r) * 2 * C(r));
+    }
+    for (int r = 1; r <= Lv; r++) {
+        o_pool[r] = take(2 * P(r) * C(r - 1));
+        o_tmp[r] = take(2 * P(r) * C(r));
+        max_pc2 = std::max(max_pc2, P(r) * 2 * C(r));
+    }
+    const size_t o_bottom = take(2 * P(Lv) * C(Lv));
+    const size_t o_gbuf = take(2 * max_pc2);
+    const size_t o_xf = take(4 * P(0));
+    const size_t o_yf = take(4 * P(0));
+    const size_t o_out = take(4 * P(0));
+    const size_t o_dA = take(4 * max_pc2);
+    const size_t o_dB = take(4 * max_pc2);
+    if (N.arena) cudaFree(N.arena);
+    N.arena = nullptr;
+    int rc = dev_alloc(ctx, (void **)&N.arena, off);
+    if (rc) return rc;
+    N.arena_bytes = off;
+    char *A = N.arena;
+    auto bf = [&](size_t o) { return reinterpret_cast<__nv_bfloat16 *>(A + o); };
+    auto fl = [&](size_t o) { return reinterpret_cast<float *>(A + o); };
+    N.V.xin = bf(o_xin);
+    N.V.a_inc0 = bf(o_inc0);
+    N.V.cat.assign(Lv, nullptr);
+    N.V.dec0.assign(Lv, nullptr);
+    N.V.dec1.assign(Lv, nullptr);
+    N.V.dskip.assign(Lv, nullptr);
+    N.V.pool.assign(Lv + 1, nullptr);
+    N.V.tmp.assign(Lv + 1, nullptr);
+    for (int r = 0; r < Lv; r++) {
+        N.V.cat[r] = bf(o_cat[r]);
+        N.V.dec0[r] = bf(o_dec0[r]);
+        N.V.dec1[r] = bf(o_dec1[r]);
+        N.V.dskip[r] = fl(o_dskip[r]);
+    }
+    for (int r = 1; r <= Lv; r++) {
+        N.V.pool[r] = bf(o_pool[r]);
+        N.V.tmp[r] = bf(o_tmp[r]);
+    }
+    N.V.bottom = bf(o_bottom);
+    N.V.gbuf = bf(o_gbuf);
+    N.V.xf = fl(o_xf);
+    N.V.yf = fl(o_yf);
+    N.V.out = fl(o_out);
+    N.V.dA = fl(o_dA);
+    N.V.dB = fl(o_dB);
+    N.wsN = n;
+    N.wsH = H;
+    N.wsW = W;
+    // Weight-gradient partials: splits x M x N over every weight-gradient call.
+    size_t need = 0;
+    auto consider = [&](long long kpix, int M, int Nn) {
+        need = std::max(need, (size_t)wgrad_splits(kpix, M, Nn) * M * Nn);
+    };
+    consider((long long)P(0), (int)C(0), 9 * CPAD);  // first layer (padded input)
+    consider((long long)P(0), (int)C(0), 9 * (int)C(0));
+    for (int l = 1; l <= Lv; l++) {
+        consider((long long)P(l), (int)C(l), 9 * (int)C(l - 1));
+        consider((long long)P(l), (int)C(l), 9 * (int)C(l));
+    }
+    for (int r = 0; r < Lv; r++) {
+        consider((long long)P(r + 1), 4 * (int)C(r), (int)C(r + 1));  // transposed conv
+        consider((long long)P(r), (int)C(r), 9 * 2 * (int)C(r));
+        consider((long long)P(r), (int)C(r), 9 * (int)C(r));
+    }
+    if (N.wg_part_floats < need) {
+        dev_free(N.wg_part);
+        N.wg_part = nullptr;
+        if ((rc = dev_alloc(ctx, (void **)&N.wg_part, 4 * need))) return rc;
+        N.wg_part_floats = need;
+    }
+    const size_t rneed = (size_t)RED_BLOCKS * (2 * C(Lv) + 2);
+    if (N.red_part_floats < rneed) {
+        dev_free(N.red_part);
+        N.red_part = nullptr;
+        if ((rc = dev_alloc(ctx, (void **)&N.red_part, 4 * rneed))) return rc;
+        N.red_part_floats = rneed;
+    }
+    return DHFWI_OK;
+}
+
+// 3x3 conv forward with epilogue; src channel stride/offset, dst stride/offset.
+void conv3_fwd(NetState &N, const LayerDesc &d, const __nv_bfloat16 *w, int nimg, int H, int W,
+               const __nv_bfloat16 *src, int ss, int so, int C, void *dst, int ds, int dof, int epi, cudaStream_t s) {
+    FpropArgs a{};
+    a.src = src;
+    a.src_stride = ss;
+    a.src_off = so;
+    a.Hs = H;
+    a.Ws = W;
+    a.C = C;
+    a.ntaps = 9;
+    a.scale = 1;
+    for (int t = 0; t < 9; t++) {
+        a.dh[t] = t / 3 - 1;
+        a.dw[t] = t % 3 - 1;
+    }
+    a.Ho = H;
+    a.Wo = W;
+    a.M = nimg * H * W;
+    a.N = d.co;
+    a.bt = w;
+    a.bias = N.theta + d.off + d.nw;
+    a.slope = 0.2f;
+    if (epi == EPI_F32 || epi == EPI_F32_ADD)
+        a.dst_f32 = (float *)dst;
+    else
+        a.dst_bf16 = (__nv_bfloat16 *)dst;
+    a.dst_stride = ds;
+    a.dst_off = dof;
+    launch_fprop(a, epi, s);
+    N.launches++;
+}
+
+void forward(NetState &N, int n, int H, int W, cudaStream_t s) {
+    const int Lv = N.levels;
+    auto C = [&](int r) { return N.base << r; };
+    NetState::Views &V = N.V;
+    launch_input_pack(V.xf, (long long)n * H * W, CPAD, V.xin, s);
+    N.launches++;
+    conv3_fwd(N, N.L[0], N.w0pad, n, H, W, V.xin, CPAD, 0, CPAD, V.a_inc0, C(0), 0, EPI_BF16_LEAKY, s);
+    conv3_fwd(N, N.L[1], N.w16 + N.L[1].off, n, H, W, V.a_inc0, C(0), 0, C(0), V.cat[0], 2 * C(0), 0,
+              EPI_BF16_LEAKY, s);
+    for (int r = 1; r <= Lv; r++) {
+        const int Hp = H >> (r - 1), Wp = W >> (r - 1), Hr = H >> r, Wr = W >> r;
+        launch_avgpool_fwd(V.cat[r - 1], 2 * C(r - 1), 0, n, Hp, Wp, C(r - 1), V.pool[r], s);
+        N.launches++;
+        const LayerDesc &d0 = N.L[layer_index_down(N, r, 0)], &d1 = N.L[layer_index_down(N, r, 1)];
+        conv3_fwd(N, d0, N.w16 + d0.off, n, Hr, Wr, V.pool[r], C(r - 1), 0, C(r - 1), V.tmp[r], C(r), 0,
+                  EPI_BF16_LEAKY, s);
+        if (r < Lv)
+            conv3_fwd(N, d1, N.w16 + d1.off, n, Hr, Wr, V.tmp[r], C(r), 0, C(r), V.cat[r], 2 * C(r), 0,
+                      EPI_BF16_LEAKY, s);
+        else
+            conv3_fwd(N, d1, N.w16 + d1.off, n, Hr, Wr, V.tmp[r], C(r), 0, C(r), V.bottom, C(r), 0,
+                      EPI_BF16_LEAKY, s);
+    }
+    const __nv_bfloat16 *a = V.bottom;
+    int as = C(Lv);
+    for (int l = 1; l <= Lv; l++) {
+        const int r = Lv - l;
+        const int Hr = H >> r, Wr = W >> r;
+        const LayerDesc &dt = N.L[layer_index_up(N, l, 0)];
+        FpropArgs t{};
+        t.src = a;
+        t.src_stride = as;
+        t.src_off = 0;
+        t.Hs = H >> (r + 1);
+        t.Ws = W >> (r + 1);
+        t.C = C(r + 1);
+        t.ntaps = 1;
+        t.scale = 1;
+        t.dh[0] = t.dw[0] = 0;
+        t.Ho = H >> (r + 1);
+        t.Wo = W >> (r + 1);
+        t.M = n * t.Ho * t.Wo;
+        t.N = 4 * C(r);
+        t.bt = N.w16 + dt.off;
+        t.bias = N.theta + dt.off + dt.nw;
+        t.dst_bf16 = V.cat[r];
+        t.dst_stride = 2 * C(r);
+        t.dst_off = C(r);
+        launch_fprop(t, EPI_BF16_CONVT, s);
+        N.launches++;
+        const LayerDesc &d0 = N.L[layer_index_up(N, l, 1)], &d1 = N.L[layer_index_up(N, l, 2)];
+        conv3_fwd(N, d0, N.w16 + d0.off, n, Hr, Wr, V.cat[r], 2 * C(r), 0, 2 * C(r), V.dec0[r], C(r), 0,
+                  EPI_BF16_LEAKY, s);
+        conv3_fwd(N, d1, N.w16 + d1.off, n, Hr, Wr, V.dec0[r], C(r), 0, C(r), V.dec1[r], C(r), 0,
+                  EPI_BF16_LEAKY, s);
+        a = V.dec1[r];
+        as = C(r);
+    }
+    const LayerDesc &dout = N.L[layer_index_out(N)];
+    launch_conv1x1_fwd(V.dec1[0], C(0), (long long)n * H * W, N.w16 + dout.off, N.theta + dout.off + dout.nw,
+                       V.out, s);
+    N.launches++;
+}
+
+// Backward of one conv + LeakyReLU block: dA (float, dense [P][co]) is the
+// gradient of its output a; x its (bf16) input.  Writes the weight and bias
+// gradients and, when dx != nullptr, the input gradient (float [P][ci]).
+void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int as, int ao, const __nv_bfloat16 *x,
+               int xs, int xo, int ci, int nimg, int H, int W, float *dx, cudaStream_t s) {
+    const LayerDesc &d = N.L[li];
+    const long long P = (long long)nimg * H * W;
+    launch_leaky_bwd(dA, a, as, ao, P, d.co, 0.2f, N.V.gbuf, s);
+    WgradArgs w{};
+    w.mode = WG_CONV;
+    w.g = N.V.gbuf;
+    w.g_stride = d.co;
+    w.x = x;
+    w.x_stride = xs;
+    w.x_off = xo;
+    w.nimg = nimg;
+    w.H = H;
+    w.W = W;
+    w.ci = ci;
+    w.M = d.co;
+    w.N = 9 * ci;
+    w.part = N.wg_part;
+    const int sp = wgrad_splits(P, w.M, w.N);
+    float *dw = li == 0 ? N.g0pad : N.grad + d.off;
+    launch_wgrad(w, sp, dw, s);
+    launch_bias_grad(N.V.gbuf, d.co, d.co, P, N.red_part, RED_BLOCKS, N.grad + d.off + d.nw, s);
+    N.launches += 5;
+    if (li == 0) {
+        launch_unpad_first_grad(N.g0pad, d.co, CPAD, N.grad + d.off, s);
+        N.launches++;
+    }
+    if (dx) {
+        FpropArgs a{};
+        a.src = N.V.gbuf;
+        a.src_stride = d.co;
+        a.src_off = 0;
+        a.Hs = H;
+        a.Ws = W;
+        a.C = d.co;
+        a.ntaps = 9;
+        a.scale = 1;
+        for (int t = 0; t < 9; t++) {
+            a.dh[t] = 1 - t / 3;
+            a.dw[t] = 1 - t % 3;
+        }
+        a.Ho = H;
+        a.Wo = W;
+        a.M = (int)P;
+        a.N = ci;
+        a.bt = N.wt16 + d.off;
+        a.dst_f32 = dx;
+        a.dst_stride = ci;
+        a.dst_off = 0;
+        launch_fprop(a, EPI_F32, s);
+        N.launches++;
+    }
+}
+
+void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
+    const int Lv = N.levels;
+    auto C = [&](int r) { return N.base << r; };
+    NetState::Views &V = N.V;
+    const long long P0 = (long long)n * H * W;
+    // Output layer: g_out (bf16 [P0]) was written by the loss kernel into gbuf.
+    const LayerDesc &dout = N.L[layer_index_out(N)];
+    // Keep g_out apart from gbuf, which the blocks reuse: stage it in dB.
+    __nv_bfloat16 *gout = reinterpret_cast<__nv_bfloat16 *>(V.dB);
+    launch_conv1x1_bwd(gout, V.dec1[0], P0, C(0), N.w16 + dout.off, V.dA, N.red_part, RED_BLOCKS,
+                       N.grad + dout.off, s);
+    N.launches += 3;
+    float *dA = V.dA, *dB = V.dB;
+    for (int l = Lv; l >= 1; l--) {
+        const int r = Lv - l;
+        const int Hr = H >> r, Wr = W >> r;
+        const long long Pr = (long long)n * Hr * Wr;
+        // up_l.1: output dec1, input dec0.
+        block_bwd(N, layer_index_up(N, l, 2), dA, V.dec1[r], C(r), 0, V.dec0[r], C(r), 0, C(r), n, Hr, Wr, dB, s);
+        // up_l.0: output dec0, input cat (2C).
+        block_bwd(N, layer_index_up(N, l, 1), dB, V.dec0[r], C(r), 0, V.cat[r], 2 * C(r), 0, 2 * C(r), n, Hr, Wr, dA,
+                  s);
+        // dA = d(cat) [Pr][2C]: skip half kept, up half to bf16.
+        cudaMemsetAsync(V.dskip[r], 0, sizeof(float) * Pr * C(r), s);
+        launch_add_slice(dA, 2 * C(r), 0, Pr, C(r), V.dskip[r], s);
+        launch_f32_to_bf16_slice(dA, 2 * C(r), C(r), Pr, C(r), V.gbuf, s);
+        N.launches += 2;
+        // Transposed conv: input is the level-(r+1) activation.
+        const int li = layer_index_up(N, l, 0);
+        const LayerDesc &dt = N.L[li];
+        const __nv_bfloat16 *xin = l == 1 ? V.bottom : V.dec1[r + 1];
+        const int Hc = H >> (r + 1), Wc = W >> (r + 1);
+        WgradArgs w{};
+        w.mode = WG_CONVT;
+        w.g = V.gbuf;
+        w.g_stride = C(r);
+        w.x = xin;
+        w.x_stride = C(r + 1);
+        w.x_off = 0;
+        w.nimg = n;
+        w.H = Hc;
+        w.W = Wc;
+        w.co = C(r);
+        w.M = 4 * C(r);
+        w.N = C(r + 1);
+        w.part = N.wg_part;
+        const int sp = wgrad_splits((long long)n * Hc * Wc, w.M, w.N);
+        launch_wgrad(w, sp, N.grad + dt.off, s);
+        launch_bias_grad(V.gbuf, C(r), C(r), Pr, N.red_part, RED_BLOCKS, N.grad + dt.off + dt.nw, s);
+        FpropArgs a{};
+        a.src = V.gbuf;
+        a.src_stride = C(r);
+        a.src_off = 0;
+        a.Hs = Hr;
+        a.Ws = Wr;
+        a.C = C(r);
+        a.ntaps = 4;
+        a.scale = 2;
+        for (int t = 0; t < 4; t++) {
+            a.dh[t] = t >> 1;
+            a.dw[t] = t & 1;
+        }
+        a.Ho = Hc;
+        a.Wo = Wc;
+        a.M = n * Hc * Wc;
+        a.N = C(r + 1);
+        a.bt = N.wt16 + dt.off;
+        a.dst_f32 = dB;
+        a.dst_stride = C(r + 1);
+        a.dst_off = 0;
+        launch_fprop(a, EPI_F32, s);
+        N.launches += 5;
+        std::swap(dA, dB);
+    }
+    // dA: gradient of the bottom activation.
+    for (int r = Lv; r >= 1; r--) {
+        const int Hr = H >> r, Wr = W >> r;
+        const long long Pr = (long long)n * Hr * Wr;
+        if (r < Lv) {
+            launch_add_slice(V.dskip[r], C(r), 0, Pr, C(r), dA, s);
+            N.launches++;
+        }
+        const __nv_bfloat16 *ar = r < Lv ? V.cat[r] : V.bottom;
+        const int ars = r < Lv ? 2 * C(r) : C(r);
+        block_bwd(N, layer_index_down(N, r, 1), dA, ar, ars, 0, V.tmp[r], C(r), 0, C(r), n, Hr, Wr, dB, s);
+        block_bwd(N, layer_index_down(N, r, 0), dB, V.tmp[r], C(r), 0, V.pool[r], C(r - 1), 0, C(r - 1), n, Hr, Wr,
+                  dA, s);
+        launch_avgpool_bwd(dA, n, H >> (r - 1), W >> (r - 1), C(r - 1), dB, 0, s);
+        N.launches++;
+        std::swap(dA, dB);
+    }
+    launch_add_slice(V.dskip[0], C(0), 0, P0, C(0), dA, s);
+    N.launches++;
+    block_bwd(N, 1, dA, V.cat[0], 2 * C(0), 0, V.a_inc0, C(0), 0, C(0), n, H, W, dB, s);
+    block_bwd(N, 0, dB, V.a_inc0, C(0), 0, V.xin, CPAD, 0, CPAD, n, H, W, nullptr, s);
+}
+
+// Loss of the current batch: MSE against yf; writes g_out (bf16) to the
+// staging slot read by backward().
+void loss(NetState &N, int n, int H, int W, cudaStream_t s) {
+    launch_mse(N.V.out, N.V.yf, (long long)n * H * W, reinterpret_cast<__nv_bfloat16 *>(N.V.dB), N.mse_part,
+               MSE_BLOCKS, s);
+    N.launches++;
+}
+
+int ensure_small(dhfwi_ctx *ctx, NetState &N) {
+    int rc;
+    if (!N.mse_part && (rc = dev_alloc(ctx, (void **)&N.mse_part, sizeof(double) * MSE_BLOCKS))) return rc;
+    if (!N.loss_acc && (rc = dev_alloc(ctx, (void **)&N.loss_acc, sizeof(double) * 4096))) return rc;
+    if (!N.mx && (rc = dev_alloc(ctx, (void **)&N.mx, 16))) return rc;
+    if (!N.scales && (rc = dev_alloc(ctx, (void **)&N.scales, 4 * sizeof(float)))) return rc;
+    return DHFWI_OK;
+}
+
+int ensure_net(dhfwi_ctx *ctx, int base, int levels) {
+    NetState *&net = ctx_net(ctx);
+    if (base < 8 || base % 8 != 0 || levels < 1 || levels > 6)
+        return fail(ctx, DHFWI_ERR_ARG, "network needs base_channels a multiple of 8 (>= 8) and 1 <= levels <= 6");
+    if (!net) net = new NetState();
+    if (net->base != base || net->levels != levels || !net->theta) {
+        build_layers(*net, base, levels);
+        int rc = alloc_params(ctx, *net);
+        if (rc) return rc;
+        net->have_weights = false;
+        if (net->arena) cudaFree(net->arena);
+        net->arena = nullptr;
+        net->wsN = net->wsH = net->wsW = 0;
+    }
+    return ensure_small(ctx, *net);
+}
+
+int upload_params(dhfwi_ctx *ctx, NetState &N, const float *host, cudaStream_t s) {
+    NCK(cudaMemcpyAsync(N.theta, host, sizeof(float) * N.nparams, cudaMemcpyHostToDevice, s));
+    NCK(cudaStreamSynchronize(s));
+    refresh_weights(N, s, true);
+    N.have_weights = true;
+    return DHFWI_OK;
+}
+
+}  // namespace
+
+void net_destroy(NetState *net) {
+    if (!net) return;
+    free_params(*net);
+    void *ps[] = {net->arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->mx, net->scales,
+                  net->oz, net->ox, net->perm, net->patch_x, net->patch_y};
+    for (void *p : ps) dev_free(p);
+    delete net;
+}
 
 }  // namespace dhfwi
+
+using namespace dhfwi;
+
+extern "C" {
+
+int dhfwi_net_init(dhfwi_ctx *ctx, int base_channels, int levels, unsigned long long seed) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx_begin(ctx);
+    cudaSetDevice(ctx_device(ctx));
+    int rc = ensure_net(ctx, base_channels, levels);
+    if (rc) return rc;
+    NetState &N = *ctx_net(ctx);
+    std::vector<float> h;
+    init_host(N, seed, h);
+    return upload_params(ctx, N, h.data(), 0);
+}
+
+long long dhfwi_net_size(const dhfwi_ctx *ctx) {
+    if (!ctx) return -1;
+    NetState *net = ctx_net(const_cast<dhfwi_ctx *>(ctx));
+    return net ? net->nparams : 0;
+}
+
+int dhfwi_net_get(dhfwi_ctx *ctx, float *host, size_t n) {
+    if (!ctx || !host) return DHFWI_ERR_ARG;
+    ctx_begin(ctx);
+    NetState *net = ctx_net(ctx);
+    if (!net || !net->have_weights) return fail(ctx, DHFWI_ERR_STATE, "the network has no weights yet");
+    if (n != (size_t)net->nparams) return fail(ctx, DHFWI_ERR_ARG, "n must equal dhfwi_net_size()");
+    cudaSetDevice(ctx_device(ctx));
+    NCK(cudaMemcpy(host, net->theta, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    return DHFWI_OK;
+}
+
+int dhfwi_net_set(dhfwi_ctx *ctx, const float *host, size_t n) {
+    if (!ctx || !host) return DHFWI_ERR_ARG;
+    ctx_begin(ctx);
+    NetState *net = ctx_net(ctx);
+    if (!net) return fail(ctx, DHFWI_ERR_STATE, "call dhfwi_net_init first to fix the architecture");
+    if (n != (size_t)net->nparams) return fail(ctx, DHFWI_ERR_ARG, "n must equal dhfwi_net_size()");
+    cudaSetDevice(ctx_device(ctx));
+    return upload_params(ctx, *net, host, 0);
+}
+
+int deblur_forward(dhfwi_ctx *ctx, const float *x_dev, int n, int h, int w, float *out_dev, void *stream) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx_begin(ctx);
+    NetState *net = ctx_net(ctx);
+    if (!net || !net->have_weights) return fail(ctx, DHFWI_ERR_STATE, "the network has no weights yet");
+    if (!x_dev || !out_dev || n < 1 || h < 1 || w < 1) return fail(ctx, DHFWI_ERR_ARG, "bad batch arguments");
+    if (!ilog_mult(h, net->levels) || !ilog_mult(w, net->levels))
+        return fail(ctx, DHFWI_ERR_ARG, "h and w must be multiples of 2^levels");
+    cudaSetDevice(ctx_device(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    net->launches = 0;
+    int rc = layout(ctx, *net, n, h, w);
+    if (rc) return rc;
+    const size_t P = (size_t)n * h * w;
+    NCK(cudaMemcpyAsync(net->V.xf, x_dev, 4 * P, cudaMemcpyDeviceToDevice, s));
+    forward(*net, n, h, w, s);
+    NCK(cudaMemcpyAsync(out_dev, net->V.out, 4 * P, cudaMemcpyDeviceToDevice, s));
+    NCK(cudaGetLastError());
+    ctx_count_launches(ctx, net->launches);
+    return DHFWI_OK;
+}
+
+int deblur_grad(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int n, int h, int w, float *grad_dev,
+                double *loss_out, void *stream) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx_begin(ctx);
+    NetState *net = ctx_net(ctx);
+    if (!net || !net->have_weights) return fail(ctx, DHFWI_ERR_STATE, "the network has no weights yet");
+    if (!x_dev || !y_dev || !grad_dev || n < 1 || h < 1 || w < 1) return fail(ctx, DHFWI_ERR_ARG, "bad arguments");
+    if (!ilog_mult(h, net->levels) || !ilog_mult(w, net->levels))
+        return fail(ctx, DHFWI_ERR_ARG, "h and w must be multiples of 2^levels");
+    cudaSetDevice(ctx_device(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    net->launches = 0;
+    int rc = layout(ctx, *net, n, h, w);
+    if (rc) return rc;
+    const size_t P = (size_t)n * h * w;
+    NCK(cudaMemcpyAsync(net->V.xf, x_dev, 4 * P, cudaMemcpyDeviceToDevice, s));
+    NCK(cudaMemcpyAsync(net->V.yf, y_dev, 4 * P, cudaMemcpyDeviceToDevice, s));
+    forward(*net, n, h, w, s);
+    loss(*net, n, h, w, s);
+    backward(*net, n, h, w, s);
+    NCK(cudaMemcpyAsync(grad_dev, net->grad, 4 * (size_t)net->nparams, cudaMemcpyDeviceToDevice, s));
+    if (loss_out) {
+        double part[MSE_BLOCKS];
+        NCK(cudaMemcpyAsync(part, net->mse_part, sizeof part, cudaMemcpyDeviceToHost, s));
+        NCK(cudaStreamSynchronize(s));
+        double sum = 0.0;
+        for (int i = 0; i < MSE_BLOCKS; i++) sum += part[i];
+        *loss_out = sum / (double)P;
+    }
+    NCK(cudaGetLastError());
+    ctx_count_launches(ctx, net->launches);
+    return DHFWI_OK;
+}
+
+int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz, int nx, const dhfwi_train_cfg *cfg,
+                 int warm_start, float *loss_hist, void *stream) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx_begin(ctx);
+    if (!cfg || !x_dev || !y_dev) return fail(ctx, DHFWI_ERR_ARG, "NULL argument");
+    if (cfg->patch < 1 || cfg->stride < 1 || cfg->batch < 1 || cfg->epochs < 1 || !(cfg->lr > 0.f) ||
+        cfg->epochs > 4096)
+        return fail(ctx, DHFWI_ERR_ARG, "bad training configuration");
+    if (nz < cfg->patch || nx < cfg->patch) return fail(ctx, DHFWI_ERR_ARG, "image smaller than the patch");
+    cudaSetDevice(ctx_device(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_net(ctx, cfg->base_channels, cfg->levels);
+    if (rc) return rc;
+    NetState &N = *ctx_net(ctx);
+    if (!ilog_mult(cfg->patch, N.levels)) return fail(ctx, DHFWI_ERR_ARG, "patch must be a multiple of 2^levels");
+    N.launches = 0;
+    if (!warm_start || !N.have_weights) {
+        std::vector<float> h;
+        init_host(N, cfg->seed, h);
+        if ((rc = upload_params(ctx, N, h.data(), s))) return rc;
+    }
+    const int p = cfg->patch;
+    const std::vector<int> oz = patch_origins(nz, p, cfg->stride), ox = patch_origins(nx, p, cfg->stride);
+    const int npatch = (int)(oz.size() * ox.size());
+    std::vector<int> hoz(npatch), hox(npatch);
+    for (size_t a = 0; a < oz.size(); a++)
+        for (size_t b = 0; b < ox.size(); b++) {
+            hoz[a * ox.size() + b] = oz[a];
+            hox[a * ox.size() + b] = ox[b];
+        }
+    const int B = std::min(cfg->batch, npatch);
+    if ((rc = layout(ctx, N, B, p, p))) return rc;
+    if (N.oz_cap < (size_t)npatch) {
+        dev_free(N.oz);
+        dev_free(N.ox);
+        N.oz = N.ox = nullptr;
+        if ((rc = dev_alloc(ctx, (void **)&N.oz, 4 * (size_t)npatch))) return rc;
+        if ((rc = dev_alloc(ctx, (void **)&N.ox, 4 * (size_t)npatch))) return rc;
+        N.oz_cap = npatch;
+    }
+    if (N.perm_cap < (size_t)npatch * cfg->epochs) {
+        dev_free(N.perm);
+        N.perm = nullptr;
+        if ((rc = dev_alloc(ctx, (void **)&N.perm, 4 * (size_t)npatch * cfg->epochs))) return rc;
+        N.perm_cap = (size_t)npatch * cfg->epochs;
+    }
+    std::vector<int> perms((size_t)npatch * cfg->epochs), one;
+    for (int e = 0; e < cfg->epochs; e++) {
+        permutation_host(npatch, cfg->seed, e, one);
+        std::copy(one.begin(), one.end(), perms.begin() + (size_t)e * npatch);
+    }
+    NCK(cudaMemcpyAsync(N.oz, hoz.data(), 4 * (size_t)npatch, cudaMemcpyHostToDevice, s));
+    NCK(cudaMemcpyAsync(N.ox, hox.data(), 4 * (size_t)npatch, cudaMemcpyHostToDevice, s));
+    NCK(cudaMemcpyAsync(N.perm, perms.data(), 4 * perms.size(), cudaMemcpyHostToDevice, s));
+    // Normalisation by max |.| of each image (Section 2.3.1 pair: x = delta m_1, y = g).
+    launch_absmax(x_dev, (long long)nz * nx, N.mx, N.scales, s);
+    launch_absmax(y_dev, (long long)nz * nx, N.mx + 1, N.scales + 2, s);
+    N.launches += 6;
+    // Adam state reset for this session.
+    NCK(cudaMemsetAsync(N.m, 0, sizeof(float) * N.nparams, s));
+    NCK(cudaMemsetAsync(N.v, 0, sizeof(float) * N.nparams, s));
+    NCK(cudaMemsetAsync(N.loss_acc, 0, sizeof(double) * cfg->epochs, s));
+    const int nb = (npatch + B - 1) / B;
+    const long long T = (long long)cfg->epochs * nb;
+    long long t = 0;
+    for (int e = 0; e < cfg->epochs; e++) {
+        for (int b = 0; b < nb; b++) {
+            const int cnt = std::min(B, npatch - b * B);
+            const int *sel = N.perm + (size_t)e * npatch + (size_t)b * B;
+            launch_gather_patches(x_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales, N.V.xf, s);
+            launch_gather_patches(y_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales + 2, N.V.yf, s);
+            N.launches += 2;
+            forward(N, cnt, p, p, s);
+            loss(N, cnt, p, p, s);
+            launch_loss_accum(N.mse_part, MSE_BLOCKS, (double)cnt / ((double)cnt * p * p), N.loss_acc + e, s);
+            backward(N, cnt, p, p, s);
+            const double lr = 0.5 * cfg->lr * (1.0 + std::cos(M_PI * (double)t / (double)T));
+            launch_adam(N.theta, N.grad, N.m, N.v, N.nparams, (float)lr, cfg->beta1, cfg->beta2, cfg->eps, (int)(t + 1),
+                        N.w16, s);
+            refresh_weights(N, s, false);
+            N.launches += 2;
+            t++;
+        }
+        NCK(cudaGetLastError());
+    }
+    N.have_weights = true;
+    if (loss_hist) {
+        std::vector<double> acc(cfg->epochs);
+        NCK(cudaMemcpyAsync(acc.data(), N.loss_acc, sizeof(double) * cfg->epochs, cudaMemcpyDeviceToHost, s));
+        NCK(cudaStreamSynchronize(s));
+        // loss_acc[e] = sum_b cnt_b * mean_b(r^2); per-epoch mean over patches.
+        for (int e = 0; e < cfg->epochs; e++) loss_hist[e] = (float)(acc[e] / (double)npatch);
+    }
+    ctx_count_launches(ctx, N.launches);
+    return DHFWI_OK;
+}
+
+int deblur_apply(dhfwi_ctx *ctx, const float *g_dev, int nz, int nx, float *out_dev, void *stream) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx_begin(ctx);
+    NetState *net = ctx_net(ctx);
+    if (!net || !net->have_weights) return fail(ctx, DHFWI_ERR_STATE, "train or set the network first");
+    if (!g_dev || !out_dev || nz < 1 || nx < 1) return fail(ctx, DHFWI_ERR_ARG, "bad arguments");
+    cudaSetDevice(ctx_device(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    NetState &N = *net;
+    N.launches = 0;
+    const int mult = 1 << N.levels;
+    const int Hp = (nz + mult - 1) / mult * mult, Wp = (nx + mult - 1) / mult * mult;
+    int rc = layout(ctx, N, 1, Hp, Wp);
+    if (rc) return rc;
+    launch_absmax(g_dev, (long long)nz * nx, N.mx, N.scales, s);
+    launch_pad_image(g_dev, nz, nx, Hp, Wp, N.scales, N.V.xf, s);
+    forward(N, 1, Hp, Wp, s);
+    launch_crop_image(N.V.out, Hp, Wp, nz, nx, N.scales + 1, out_dev, s);
+    N.launches += 5;
+    NCK(cudaGetLastError());
+    ctx_count_launches(ctx, N.launches);
+    return DHFWI_OK;
+}
+
+}  // extern "C"

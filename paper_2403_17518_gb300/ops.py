@@ -159,6 +159,83 @@ class Context:
         """delta m_1 = L~^T L~ g (Section 2.3.1, Eq. 15)."""
         return self.rtm_mig(v0, geom, self.born_demig(v0, geom, g_img))
 
+    def fwi_update(self, v: torch.Tensor, direction: torch.Tensor, alpha: float, vmin: float, vmax: float,
+                   mute_rows: int = 0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """clamp(v - alpha * dir / max|dir|, vmin, vmax) with the top rows muted."""
+        out = out if out is not None else self.new_model()
+        self._check(self.lib.fwi_update(self.handle, self._model(v, "v"), self._model(direction, "dir"),
+                                        float(alpha), float(vmin), float(vmax), int(mute_rows),
+                                        self._model(out, "out"), self._stream(stream)))
+        return out
+
+    def data_misfit(self, a: torch.Tensor, b: torch.Tensor, stream=None) -> float:
+        """1/2 ||a - b||^2 accumulated in float64 on the device."""
+        if a.numel() != b.numel():
+            raise ValueError("a and b must have the same size")
+        J = ctypes.c_double(0.0)
+        self._check(self.lib.data_misfit(self.handle, self._dense(a, "a"), self._dense(b, "b"), a.numel(),
+                                         ctypes.byref(J), self._stream(stream)))
+        return J.value
+
+    # -- deblurring network -----------------------------------------------
+    def _dense(self, t: torch.Tensor, name: str) -> ctypes.c_void_p:
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.device == self.device):
+            raise ValueError(f"{name} must be a contiguous float32 tensor on {self.device}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def net_init(self, base_channels: int = 32, levels: int = 4, seed: int = 29):
+        self._check(self.lib.dhfwi_net_init(self.handle, int(base_channels), int(levels), int(seed)))
+
+    def net_size(self) -> int:
+        return int(self.lib.dhfwi_net_size(self.handle))
+
+    def net_get(self) -> np.ndarray:
+        n = self.net_size()
+        out = np.empty(n, dtype=np.float32)
+        self._check(self.lib.dhfwi_net_get(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n))
+        return out
+
+    def net_set(self, params) -> None:
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self.lib.dhfwi_net_set(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+
+    def deblur_forward(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        """Raw network on a batch x [n, h, w] (no normalisation)."""
+        n, h, w = x.shape
+        out = torch.empty_like(x)
+        self._check(self.lib.deblur_forward(self.handle, self._dense(x, "x"), n, h, w, self._dense(out, "out"),
+                                            self._stream(stream)))
+        return out
+
+    def deblur_grad(self, x: torch.Tensor, y: torch.Tensor, stream=None):
+        """(loss, flat parameter gradient) of mean((net(x) - y)^2) on a batch."""
+        n, h, w = x.shape
+        g = torch.empty(self.net_size(), dtype=torch.float32, device=self.device)
+        L = ctypes.c_double(0.0)
+        self._check(self.lib.deblur_grad(self.handle, self._dense(x, "x"), self._dense(y, "y"), n, h, w,
+                                         self._dense(g, "grad"), ctypes.byref(L), self._stream(stream)))
+        return L.value, g
+
+    def deblur_train(self, x_img: torch.Tensor, y_img: torch.Tensor, warm_start: bool = True, base_channels=32,
+                     levels=4, patch=128, stride=64, batch=32, epochs=200, lr=1e-3, beta1=0.9, beta2=0.999,
+                     eps=1e-8, seed=29, stream=None):
+        """Train x (doubly migrated image) -> y (gradient); returns per-epoch losses."""
+        nz, nx = x_img.shape
+        cfg = _lib.TrainCfg(int(base_channels), int(levels), int(patch), int(stride), int(batch), int(epochs),
+                            float(lr), float(beta1), float(beta2), float(eps), int(seed))
+        hist = np.zeros(int(epochs), dtype=np.float32)
+        self._check(self.lib.deblur_train(self.handle, self._dense(x_img, "x"), self._dense(y_img, "y"), nz, nx,
+                                          ctypes.byref(cfg), 1 if warm_start else 0,
+                                          hist.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self._stream(stream)))
+        return hist
+
+    def deblur_apply(self, g: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        nz, nx = g.shape
+        out = out if out is not None else torch.empty_like(g)
+        self._check(self.lib.deblur_apply(self.handle, self._dense(g, "g"), nz, nx, self._dense(out, "out"),
+                                          self._stream(stream)))
+        return out
+
 
 class FWIMisfit(torch.autograd.Function):
     """J(v) = 1/2 ||d_s(v) - d_o||^2 with the adjoint-state gradient as backward.

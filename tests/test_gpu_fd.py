@@ -214,3 +214,19 @@ def test_config2_gradient_two_shots(config2):
     J, g = ctx.fwi_gradient(to_dev(v0), geom, to_dev(d_obs))
     assert abs(J - J_ref) <= TOL * J_ref
     assert rel_l2(to_host(g), g_ref) <= TOL
+
+
+def test_fwi_update_and_data_misfit():
+    c = CASES["tiny"]
+    ctx = gpu_ctx(c)
+    g = np.random.Generator(np.random.PCG64(12))
+    v = f32(c.v_init)
+    d = f32(g.standard_normal(v.shape))
+    out = to_host(ctx.fwi_update(to_dev(v), to_dev(d), 25.0, 1500.0, 2200.0, 3))
+    dm = d.copy()
+    dm[:3] = 0.0
+    ref = np.clip(v - 25.0 * dm / np.abs(dm).max(), 1500.0, 2200.0)
+    assert np.abs(out - ref).max() <= 1e-3
+    a, b = f32(g.standard_normal(1000)), f32(g.standard_normal(1000))
+    J = ctx.data_misfit(to_dev(a), to_dev(b))
+    assert J == pytest.approx(oracle.misfit(a, b), rel=1e-6)

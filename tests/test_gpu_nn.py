@@ -1,0 +1,120 @@
+"""GPU parity of the deblurring network against the FP64 oracle that rounds
+operands to bfloat16 at the same points (Section 2.4 / Appendix A).
+
+Tolerances: bitwise initialisation; network output and whole parameter
+gradient relative L2 <= 1e-2 end to end; each parameter tensor's gradient
+<= 0.1.  The per-tensor bound comes from the oracle's own sensitivity: bf16
+rounding decisions flip when pre-rounding values move by as little as 1e-7
+relative (below float32 accumulation error), and perturbing the oracle that
+way moves its deeper tensors' gradients by 5-7 % (whole gradient 0.35 %).  A
+wrong layout in a layer gives ~100 %.  Training: per-epoch loss within 2e-2;
+weights after 24 Adam steps within 0.1 (Adam's sign-like steps amplify the
+same flips).  All calls go through the C ABI.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import rel_l2
+from oracle import nn as onn
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_17518_gb300 import build
+    from paper_2403_17518_gb300.ops import Context
+
+    build()
+    return Context(16, 16, 10.0, 1e-3, 4)
+
+
+def _dev(a):
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+@pytest.mark.parametrize("base,levels", [(8, 2), (16, 3)])
+def test_init_is_bitwise_identical(base, levels):
+    ctx = _ctx()
+    ctx.net_init(base, levels, seed=5)
+    spec = onn.UNetSpec(base=base, levels=levels)
+    assert ctx.net_size() == onn.n_params(spec)
+    assert np.array_equal(ctx.net_get(), onn.init_params(spec, 5))
+
+
+@pytest.mark.parametrize("base,levels,n,h,w", [(8, 2, 2, 32, 32), (16, 3, 3, 24, 40), (32, 4, 2, 128, 128)])
+def test_forward_and_gradient_parity(base, levels, n, h, w):
+    ctx = _ctx()
+    spec = onn.UNetSpec(base=base, levels=levels)
+    ctx.net_init(base, levels, seed=11)
+    g = np.random.Generator(np.random.PCG64(3))
+    x = g.standard_normal((n, h, w)).astype(np.float32)
+    y = g.standard_normal((n, h, w)).astype(np.float32)
+    out = ctx.deblur_forward(_dev(x)).cpu().numpy()
+    flat = onn.init_params(spec, 11)
+    ref, cache = onn.forward(flat, x[:, None].astype(np.float64), spec)
+    assert rel_l2(out, ref[:, 0]) <= 1e-2
+    loss, grad = ctx.deblur_grad(_dev(x), _dev(y))
+    lref, dout = onn.mse(ref, y[:, None].astype(np.float64))
+    gref = onn.backward(flat, cache, dout, spec)
+    assert abs(loss - lref) <= 1e-3 * lref
+    grad = grad.cpu().numpy()
+    assert rel_l2(grad, gref) <= 1e-2
+    # Every tensor individually (catches a wrong layout in one layer).
+    k = 0
+    for name, kind, ci, co in onn.param_specs(spec):
+        cnt = int(np.prod(onn.weight_shape(kind, ci, co))) + co
+        assert rel_l2(grad[k:k + cnt], gref[k:k + cnt]) <= 0.1, name
+        k += cnt
+
+
+def test_gradient_is_deterministic():
+    ctx = _ctx()
+    ctx.net_init(8, 2, seed=1)
+    g = np.random.Generator(np.random.PCG64(9))
+    x, y = _dev(g.standard_normal((4, 32, 32))), _dev(g.standard_normal((4, 32, 32)))
+    l1, g1 = ctx.deblur_grad(x, y)
+    l2, g2 = ctx.deblur_grad(x, y)
+    assert l1 == l2 and bool((g1 == g2).all())
+
+
+def test_training_and_apply_parity():
+    ctx = _ctx()
+    from scipy.ndimage import gaussian_filter
+
+    g = np.random.Generator(np.random.PCG64(8))
+    img = np.cumsum(g.standard_normal((40, 72)), axis=1)
+    x = gaussian_filter(img, 1.5).astype(np.float32)
+    y = img.astype(np.float32)
+    spec = onn.UNetSpec(base=8, levels=2)
+    cfg = onn.TrainCfg(patch=16, stride=8, batch=4, epochs=3, lr=1e-2, seed=4)
+    hist = ctx.deblur_train(_dev(x), _dev(y), warm_start=False, base_channels=8, levels=2, patch=16, stride=8,
+                            batch=4, epochs=3, lr=1e-2, seed=4)
+    theta, href = onn.train(onn.init_params(spec, 4), x.astype(np.float64), y.astype(np.float64), spec, cfg)
+    assert np.allclose(hist, href, rtol=2e-2), (hist, href)
+    w = ctx.net_get()
+    assert rel_l2(w, theta) <= 0.1
+    out = ctx.deblur_apply(_dev(y)).cpu().numpy()
+    ref = onn.apply(w.astype(np.float64), y.astype(np.float64), spec)
+    assert rel_l2(out, ref) <= 1e-2
+    # Warm start continues from the trained weights (lower first-epoch loss).
+    hist2 = ctx.deblur_train(_dev(x), _dev(y), warm_start=True, base_channels=8, levels=2, patch=16, stride=8,
+                             batch=4, epochs=1, lr=1e-2, seed=4)
+    assert hist2[0] < hist[0]
+
+
+def test_network_errors():
+    ctx = _ctx()
+    from paper_2403_17518_gb300.ops import DhfwiError
+
+    with pytest.raises(DhfwiError, match="STATE"):
+        ctx.deblur_apply(_dev(np.ones((16, 16))))
+    with pytest.raises(DhfwiError, match="ARG"):
+        ctx.deblur_train(_dev(np.ones((16, 16))), _dev(np.ones((16, 16))), base_channels=12)
+    ctx.net_init(8, 2, 1)
+    with pytest.raises(DhfwiError, match="ARG"):
+        ctx.deblur_forward(_dev(np.ones((1, 18, 16))))
