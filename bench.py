@@ -54,8 +54,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--only", default="", choices=["", "fwd"],
-                   help="fwd: time batched forward modelling (model_shots) alone; used for profiling")
+    p.add_argument("--only", default="", choices=["", "fwd", "nn"],
+                   help="fwd: time batched forward modelling (model_shots) alone; nn: the network's training "
+                        "and apply alone on seeded smooth images of the workload's size; used for profiling")
+    p.add_argument("--nn-epochs", type=int, default=20)
     return p.parse_args()
 
 
@@ -309,6 +311,46 @@ def workload_config(case, args):
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
+def run_network_only(args, dist, case):
+    """Network training (warm, --nn-epochs) and full-image apply alone."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2403_17518_gb300.ops import Context
+
+    ctx = Context(case.nz, case.nx, case.h, case.dt, case.nb, device=dist.local)
+    dev = torch.device("cuda", dist.local)
+    x = torch.tensor(synth.smooth_random_field(case.nz, case.nx, 1, 3.0), dtype=torch.float32, device=dev)
+    y = torch.tensor(synth.smooth_random_field(case.nz, case.nx, 2, 1.5), dtype=torch.float32, device=dev)
+    out = torch.empty_like(y)
+    ctx.deblur_train(x, y, warm_start=False, epochs=1, **NET)
+    for _ in range(args.warmup):
+        ctx.deblur_train(x, y, warm_start=True, epochs=args.nn_epochs, **NET)
+        ctx.deblur_apply(y, out=out)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    for _ in range(args.steps):
+        ctx.deblur_train(x, y, warm_start=True, epochs=args.nn_epochs, **NET)
+    e1.record()
+    for _ in range(args.steps):
+        ctx.deblur_apply(y, out=out)
+    e2.record()
+    torch.cuda.synchronize()
+    npatch = n_patches(case.nz, NET["patch"], NET["stride"]) * n_patches(case.nx, NET["patch"], NET["stride"])
+    f_train = args.nn_epochs * npatch * 3 * conv_flops(NET["base_channels"], NET["levels"], NET["patch"], NET["patch"])
+    f_apply = conv_flops(NET["base_channels"], NET["levels"], case.nz, case.nx)
+    t_train = e0.elapsed_time(e1) / max(args.steps, 1)
+    t_apply = e1.elapsed_time(e2) / max(args.steps, 1)
+    if dist.rank == 0:
+        print(json.dumps({"only": "nn", "epochs": args.nn_epochs, "patches": npatch,
+                          "train_ms": round(t_train, 2), "train_tflops": round(f_train / t_train / 1e9, 2),
+                          "apply_ms": round(t_apply, 2), "apply_tflops": round(f_apply / t_apply / 1e9, 2)}),
+              flush=True)
+    ctx.close()
+
+
 def run_forward_only(args, dist, ctx, case, geom, v0, d_out):
     """Batched forward modelling alone (model_shots), for kernel profiling."""
     import torch
@@ -349,6 +391,10 @@ def main():
     torch.cuda.set_device(dist.local)
     build()
     case = make_case(args.workload)
+    if args.only == "nn":
+        run_network_only(args, dist, case)
+        dist.close()
+        return
     dev = torch.device("cuda", dist.local)
     ctx = Context(case.nz, case.nx, case.h, case.dt, case.nb, device=dist.local)
     geom = GeomArgs(case.geom)

@@ -27,6 +27,8 @@ struct FpropArgs {
     __nv_bfloat16 *dst_bf16;
     float *dst_f32;
     int dst_stride, dst_off;
+    float *part;                // optional split-k scratch ([splits][M][N] float32)
+    long long part_floats;      // its capacity
 };
 
 // Split-k weight-gradient GEMM; see igemm_wgrad_kernel.

@@ -8,6 +8,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "nn_internal.h"
 
 namespace dhfwi {
@@ -68,7 +70,11 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int K = P.ntaps * P.C;
-    const int nk = (K + BK - 1) / BK;
+    const int nk_all = (K + BK - 1) / BK;
+    // Split-k: this CTA takes k-tiles [kt0, kt0 + nk).
+    const int per = (nk_all + gridDim.z - 1) / gridDim.z;
+    const int kt0 = blockIdx.z * per;
+    const int nk = max(0, min(nk_all, kt0 + per) - kt0);
     const int HWo = P.Ho * P.Wo;
 
     // Each thread loads fixed 16-byte chunks of the A and B tiles.
@@ -87,6 +93,7 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
         a_wo[i] = r - a_ho[i] * P.Wo;
     }
     auto load_stage = [&](int st, int kt) {
+        kt += kt0;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             const int idx = tid + i * 128;
@@ -161,6 +168,24 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
 
     // Epilogue.
     const int g = lane >> 2, t = lane & 3;
+    if (P.part) {  // split-k: raw partial sums, the epilogue runs in fprop_reduce_kernel
+        float *out = P.part + (long long)blockIdx.z * P.M * P.N;
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                const int m = m0 + warp * 32 + i * 16 + g + half * 8;
+                if (m >= P.M) continue;
+#pragma unroll
+                for (int j = 0; j < BN / 8; j++)
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        const int n = n0 + j * 8 + 2 * t + e;
+                        if (n < P.N) out[(long long)m * P.N + n] = acc[i][j][half * 2 + e];
+                    }
+            }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 2; i++) {
 #pragma unroll
@@ -195,6 +220,37 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
                     }
                 }
             }
+        }
+    }
+}
+
+// Split-k reduction of the fprop partials (fixed split order) with the
+// epilogue of igemm_fprop_kernel.
+template <int EPI>
+__global__ void fprop_reduce_kernel(FpropArgs P, int splits) {
+    const long long MN = (long long)P.M * P.N;
+    const int HWo = P.Ho * P.Wo;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < MN;
+         idx += (long long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < splits; z++) v += P.part[(long long)z * MN + idx];
+        const int m = (int)(idx / P.N), n = (int)(idx - (long long)m * P.N);
+        if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
+            v += P.bias[n];
+            if (EPI == EPI_BF16_LEAKY) v = v > 0.f ? v : P.slope * v;
+            P.dst_bf16[(long long)m * P.dst_stride + P.dst_off + n] = __float2bfloat16_rn(v);
+        } else if (EPI == EPI_BF16_CONVT) {
+            const int img = m / HWo;
+            const int r = m - img * HWo;
+            const int ho = r / P.Wo, wo = r - ho * P.Wo;
+            const int co = n >> 2, a = (n >> 1) & 1, b = n & 1;
+            v += P.bias[co];
+            const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
+            P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v);
+        } else {
+            const long long o = (long long)m * P.dst_stride + P.dst_off + n;
+            if (EPI == EPI_F32_ADD) v += P.dst_f32[o];
+            P.dst_f32[o] = v;
         }
     }
 }
@@ -678,8 +734,26 @@ static void fprop_launch(const FpropArgs &a, cudaStream_t s) {
         cudaFuncSetAttribute(igemm_fprop_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
-    dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN);
-    igemm_fprop_kernel<BN, EPI><<<grid, 128, sm, s>>>(a);
+    const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
+    const int nk = (a.ntaps * a.C + BK - 1) / BK;
+    int splits = 1;
+    if (a.part && a.part_floats > 0) {
+        // Split k when the tiles fill less than ~2 waves (4 CTAs per SM), keeping
+        // at least 8 k-tiles per split and the partials within their buffer.
+        const int want = (2 * 152 * 4 + tiles - 1) / tiles;
+        splits = std::min(want, nk / 8);
+        const long long cap = a.part_floats / ((long long)a.M * a.N);
+        if (splits > cap) splits = (int)cap;
+        if (splits < 2) splits = 1;
+    }
+    FpropArgs b = a;
+    if (splits == 1) b.part = nullptr;
+    dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, splits);
+    igemm_fprop_kernel<BN, EPI><<<grid, 128, sm, s>>>(b);
+    if (splits > 1) {
+        const long long mn = (long long)a.M * a.N;
+        fprop_reduce_kernel<EPI><<<grid_for(mn), 256, 0, s>>>(b, splits);
+    }
 }
 
 void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {

@@ -60,6 +60,8 @@ struct NetState {
     size_t red_part_floats = 0;
     float *wg_part = nullptr;
     size_t wg_part_floats = 0;
+    float *fp_part = nullptr;    // split-k partials of the fprop GEMMs
+    size_t fp_part_floats = 0;
     unsigned *mx = nullptr;
     float *scales = nullptr;  // [0..1] x scale, [2..3] y scale
     int *oz = nullptr, *ox = nullptr, *perm = nullptr;
@@ -333,6 +335,18 @@ int layout(dhfwi_ctx *ctx, NetState &N, int n, int H, int W) {
         if ((rc = dev_alloc(ctx, (void **)&N.wg_part, 4 * need))) return rc;
         N.wg_part_floats = need;
     }
+    // Split-k partials of the forward / input-gradient GEMMs: up to ~1216
+    // tiles' worth of 128 x 64 outputs, and at least the deepest level's M x N x 8.
+    {
+        size_t fneed = (size_t)2 * 152 * 4 * 128 * 64;
+        fneed = std::max(fneed, (size_t)8 * P(Lv) * 4 * C(Lv));
+        if (N.fp_part_floats < fneed) {
+            dev_free(N.fp_part);
+            N.fp_part = nullptr;
+            if ((rc = dev_alloc(ctx, (void **)&N.fp_part, 4 * fneed))) return rc;
+            N.fp_part_floats = fneed;
+        }
+    }
     const size_t rneed = (size_t)RED_BLOCKS * (2 * C(Lv) + 2);
     if (N.red_part_floats < rneed) {
         dev_free(N.red_part);
@@ -372,8 +386,10 @@ void conv3_fwd(NetState &N, const LayerDesc &d, const __nv_bfloat16 *w, int nimg
         a.dst_bf16 = (__nv_bfloat16 *)dst;
     a.dst_stride = ds;
     a.dst_off = dof;
+    a.part = N.fp_part;
+    a.part_floats = (long long)N.fp_part_floats;
     launch_fprop(a, epi, s);
-    N.launches++;
+    N.launches += 2;
 }
 
 void forward(NetState &N, int n, int H, int W, cudaStream_t s) {
@@ -424,6 +440,8 @@ void forward(NetState &N, int n, int H, int W, cudaStream_t s) {
         t.dst_bf16 = V.cat[r];
         t.dst_stride = 2 * C(r);
         t.dst_off = C(r);
+        t.part = N.fp_part;
+        t.part_floats = (long long)N.fp_part_floats;
         launch_fprop(t, EPI_BF16_CONVT, s);
         N.launches++;
         const LayerDesc &d0 = N.L[layer_index_up(N, l, 1)], &d1 = N.L[layer_index_up(N, l, 2)];
@@ -493,8 +511,10 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
         a.dst_f32 = dx;
         a.dst_stride = ci;
         a.dst_off = 0;
+        a.part = N.fp_part;
+        a.part_floats = (long long)N.fp_part_floats;
         launch_fprop(a, EPI_F32, s);
-        N.launches++;
+        N.launches += 2;
     }
 }
 
@@ -568,8 +588,10 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         a.dst_f32 = dB;
         a.dst_stride = C(r + 1);
         a.dst_off = 0;
+        a.part = N.fp_part;
+        a.part_floats = (long long)N.fp_part_floats;
         launch_fprop(a, EPI_F32, s);
-        N.launches += 5;
+        N.launches += 6;
         std::swap(dA, dB);
     }
     // dA: gradient of the bottom activation.
@@ -642,7 +664,8 @@ int upload_params(dhfwi_ctx *ctx, NetState &N, const float *host, cudaStream_t s
 void net_destroy(NetState *net) {
     if (!net) return;
     free_params(*net);
-    void *ps[] = {net->arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->mx, net->scales,
+    void *ps[] = {net->arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->mx,
+                  net->scales,
                   net->oz, net->ox, net->perm, net->patch_x, net->patch_y};
     for (void *p : ps) dev_free(p);
     delete net;

@@ -1,0 +1,175 @@
+"""FWI driver: plain steepest descent vs deblurred-gradient FWI (Section 2.3).
+
+Each iteration of either arm computes the misfit and gradient (Eq. 2, Eq.
+13).  The deblurred arm then forms the doubly migrated image of the gradient
+(Eq. 15), trains the network to map it back to the gradient (warm-started
+from the previous iteration, re-initialised at each new frequency band) and
+applies the network to the gradient to get the direction (Section 2.3.1).
+Both arms take the same step rule: the direction normalised to unit max, a
+two-trial parabolic line search on the misfit, velocity clamped to the model
+range, the top rows muted.  GPU time is the sum of CUDA-event intervals
+around every call of an iteration (line-search forwards and training
+included), so the arms are compared at equal GPU-seconds.
+
+All arithmetic runs in libdhfwi.so; this module only sequences the calls and
+low-pass filters the observed data and the wavelet per band on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import copy
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from .ops import Context, GeomArgs
+
+
+def lowpass(x: np.ndarray, dt: float, fc: float, axis: int = -1) -> np.ndarray:
+    """Zero-phase low-pass: unit gain below fc, cosine taper to 0 at 1.25 fc."""
+    n = x.shape[axis]
+    nf = 1 << int(math.ceil(math.log2(2 * n)))
+    X = np.fft.rfft(x, nf, axis=axis)
+    f = np.fft.rfftfreq(nf, dt)
+    H = np.where(f <= fc, 1.0, np.where(f >= 1.25 * fc, 0.0, 0.5 * (1 + np.cos(np.pi * (f - fc) / (0.25 * fc)))))
+    shape = [1] * X.ndim
+    shape[axis] = -1
+    y = np.fft.irfft(X * H.reshape(shape), nf, axis=axis)
+    return np.take(y, np.arange(n), axis=axis)
+
+
+def band_data(d_obs: np.ndarray, geom, dt: float, fc: float) -> np.ndarray:
+    """Low-pass each shot record [nt_s][nrec_s] along time."""
+    out = np.empty_like(d_obs)
+    off = geom.data_offsets()
+    for s in range(geom.n_shots):
+        nr = geom.nrec(s)
+        blk = d_obs[off[s]:off[s + 1]].reshape(int(geom.nt[s]), nr)
+        out[off[s]:off[s + 1]] = lowpass(blk, dt, fc, axis=0).ravel()
+    return out
+
+
+class Timer:
+    """Sums CUDA-event intervals on the current stream."""
+
+    def __init__(self):
+        self.pairs = []
+
+    def __enter__(self):
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+        self.e0.record()
+        return self
+
+    def __exit__(self, *a):
+        self.e1.record()
+        self.pairs.append((self.e0, self.e1))
+
+    def seconds(self) -> float:
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in self.pairs) / 1e3
+
+
+def model_rms(v: torch.Tensor, v_true: torch.Tensor) -> float:
+    return float(torch.sqrt(torch.mean((v - v_true) ** 2)).item())
+
+
+def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, cold_epochs: int, warm_epochs: int,
+            vmin: float, vmax: float, mute_rows: int = 5, log=None):
+    dev = ctx.device
+    v_true = torch.tensor(case.v_true, dtype=torch.float32, device=dev)
+    v = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
+    d_full = ctx.model_shots(v_true, case.geom).cpu().numpy()
+    hist = [{"band": None, "iter": 0, "gpu_s": 0.0, "model_rms": model_rms(v, v_true), "misfit": None}]
+    timer = Timer()
+    grad = ctx.new_model()
+    direction = ctx.new_model()
+    dm1 = ctx.new_model()
+    trial = ctx.new_model()
+    for fc in bands:
+        g = copy.deepcopy(case.geom)
+        g.wavelet = lowpass(np.asarray(g.wavelet, dtype=np.float64), case.dt, fc)
+        ga = GeomArgs(g)
+        d_obs = torch.tensor(band_data(d_full, case.geom, case.dt, fc), dtype=torch.float32, device=dev)
+        d_born = ctx.new_data(ga)
+        d_try = ctx.new_data(ga)
+        for it in range(iters):
+            with timer:
+                J0, _ = ctx.fwi_gradient(v, ga, d_obs, grad=grad)
+                if mode == "deblur":
+                    ctx.born_demig(v, ga, grad, out=d_born)
+                    ctx.rtm_mig(v, ga, d_born, out=dm1)
+                    ctx.deblur_train(dm1, grad, warm_start=it > 0, epochs=warm_epochs if it > 0 else cold_epochs,
+                                     **net_cfg)
+                    ctx.deblur_apply(grad, out=direction)
+                    dirn = direction
+                else:
+                    dirn = grad
+                a1 = 0.01 * float(np.mean(case.v_init))
+                Js = []
+                for a in (a1, 2 * a1):
+                    ctx.fwi_update(v, dirn, a, vmin, vmax, mute_rows, out=trial)
+                    ctx.model_shots(trial, ga, out=d_try)
+                    Js.append(ctx.data_misfit(d_try, d_obs))
+                # Parabola through (0, J0), (a1, J1), (2 a1, J2).
+                J1, J2 = Js
+                curv = (J2 - 2 * J1 + J0) / (2 * a1 * a1)
+                slope = (4 * J1 - 3 * J0 - J2) / (2 * a1)
+                if curv > 0:
+                    a_best = -slope / (2 * curv)
+                else:
+                    a_best = 2 * a1 if J2 < J1 else a1
+                a_best = min(max(a_best, 0.0), 4 * a1)
+                if min(J1, J2) < J0 and a_best == 0.0:
+                    a_best = a1 if J1 <= J2 else 2 * a1
+                ctx.fwi_update(v, dirn, a_best, vmin, vmax, mute_rows, out=v)
+            rec = {"band": fc, "iter": it + 1, "gpu_s": timer.seconds(), "model_rms": model_rms(v, v_true),
+                   "misfit": J0, "alpha": a_best}
+            hist.append(rec)
+            if log:
+                log(mode, rec)
+    return hist
+
+
+def main():
+    import synth
+
+    p = argparse.ArgumentParser(description="plain vs deblurred FWI at equal GPU-seconds")
+    p.add_argument("--nz", type=int, default=150)
+    p.add_argument("--nx", type=int, default=500)
+    p.add_argument("--h", type=float, default=20.0)
+    p.add_argument("--dt", type=float, default=2e-3)
+    p.add_argument("--shots", type=int, default=25)
+    p.add_argument("--nt", type=int, default=1500)
+    p.add_argument("--bands", default="3,5")
+    p.add_argument("--iters", type=int, default=8)
+    p.add_argument("--out", default="")
+    a = p.parse_args()
+    v = synth.layered_fault_model(a.nz, a.nx, a.h, seed=31)
+    v0 = synth.smooth_model(v, 10.0)
+    wav = synth.ricker(8.0, a.dt, a.nt)
+    geom = synth.surface_geometry(a.nx, a.shots, seed=31, nrec_range=(a.nx // 3, a.nx // 2),
+                                  nt_range=(int(a.nt * 0.8), a.nt), margin=a.nx // 10, src_lo=10,
+                                  src_hi=a.nx - 11, wavelet=wav)
+    case = synth.Case(a.nz, a.nx, a.h, a.dt, 20, v, v0, geom, name="fwi-loop")
+    ctx = Context(a.nz, a.nx, a.h, a.dt, 20)
+    net = dict(base_channels=32, levels=4, patch=64, stride=32, batch=32, lr=1e-3, seed=29)
+    bands = [float(b) for b in a.bands.split(",")]
+    out = {"config": vars(a), "net": net}
+    t0 = time.time()
+    for mode in ("plain", "deblur"):
+        out[mode] = run_arm(ctx, case, mode, bands, a.iters, net, 200, 20, 1500.0, 4500.0,
+                            log=lambda m, r: print(m, json.dumps(r), flush=True))
+    out["wall_s"] = time.time() - t0
+    s = json.dumps(out)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(s)
+    print(s)
+
+
+if __name__ == "__main__":
+    main()
