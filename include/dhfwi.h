@@ -185,6 +185,39 @@ int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long lon
                 void *stream);
 
 /* ------------------------------------------------------------------------
+ * Forward modelling without device allocation.  The paper has no
+ * counterpart: this serves callers that may not call cudaMalloc (code running
+ * inside a framework that owns every device allocation, memory-capped
+ * services, or callers that must avoid the device synchronisation that
+ * cudaMalloc/cudaFree can cause).
+ *
+ * model_shots_static computes exactly what model_shots computes (same
+ * kernels, same results), without a context.  All its temporary buffers
+ * (padded model arrays, wavefield state, geometry tables) live in one
+ * file-scope device array of DHFWI_STATIC_SCRATCH_BYTES that every GPU
+ * loading this library holds until the process exits; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.  The caller passes
+ * v_dev ([nz][nx] float32, device) and d_dev (packed records, device), as for
+ * model_shots.
+ *   - Problems whose scratch exceeds the array return DHFWI_ERR_ARG with the
+ *     sizes in model_shots_static_error().
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and leaves its contents behind (each call
+ *     clears what must start at zero); calls that overlap on the GPU (other
+ *     streams, other host threads, other contexts of the same device) race.
+ *   - Synchronises `stream` once, for the velocity/CFL check.
+ * ------------------------------------------------------------------------ */
+#define DHFWI_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+int model_shots_static(const dhfwi_grid *g, const float *v_dev, const dhfwi_geom *geom, float *d_dev,
+                       void *stream);
+
+/* Message of the last failed model_shots_static call of this host thread. */
+const char *model_shots_static_error(void);
+
+/* ------------------------------------------------------------------------
  * Deblurring network: an approximate inverse Hessian (Section 2.3.1 and
  * Section 2.4, architecture in Appendix A).  A UNet-like network is trained to
  * map the doubly migrated image delta m_1 (Eq. 15) to the gradient g

@@ -237,6 +237,27 @@ class Context:
         return out
 
 
+def model_shots_static(nz: int, nx: int, h: float, dt: float, nb: int, v: torch.Tensor, geom,
+                       out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Forward modelling without device allocation by the library: all
+    temporaries live in the library's fixed static device array (see
+    model_shots_static in include/dhfwi.h for the limits)."""
+    lib = _lib.load()
+    g = _as_geom(geom)
+    if not (v.is_cuda and v.dtype == torch.float32 and v.is_contiguous() and tuple(v.shape) == (nz, nx)):
+        raise ValueError("v must be a contiguous float32 CUDA tensor of shape (nz, nx)")
+    d = out if out is not None else torch.empty(g.n_data, dtype=torch.float32, device=v.device)
+    if not (d.is_cuda and d.dtype == torch.float32 and d.is_contiguous() and d.numel() == g.n_data):
+        raise ValueError("out must be a contiguous float32 CUDA tensor with n_data values")
+    grid = _lib.Grid(int(nz), int(nx), int(nb), float(h), float(dt))
+    s = stream if stream is not None else torch.cuda.current_stream(v.device)
+    rc = lib.model_shots_static(ctypes.byref(grid), ctypes.c_void_p(v.data_ptr()), ctypes.byref(g.struct),
+                                ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    if rc != 0:
+        raise DhfwiError(rc, lib.model_shots_static_error().decode())
+    return d
+
+
 class FWIMisfit(torch.autograd.Function):
     """J(v) = 1/2 ||d_s(v) - d_o||^2 with the adjoint-state gradient as backward.
 
