@@ -243,6 +243,10 @@ typedef struct {
     float lr;           /* initial learning rate of the cosine schedule */
     float beta1, beta2, eps;     /* Adam */
     unsigned long long seed;     /* initialisation (cold start) and shuffling */
+    int mute_rows;               /* rows from the top taken as 0 in x and y (source/receiver
+                                    footprint); also used by deblur_apply */
+    float warmup_frac;           /* linear learning-rate ramp over this fraction of the call's
+                                    steps (0 = none), in [0, 1] */
 } dhfwi_train_cfg;
 
 /* Fix the architecture and initialise the weights from `seed` (SplitMix64,
@@ -269,10 +273,12 @@ int deblur_grad(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int n, i
                 double *loss_out, void *stream);
 
 /* Train on the pair (x = doubly migrated image, y = gradient), both [nz][nx]
- * float32 device images, each normalised by its max |.|, cut into patches.
+ * float32 device images, each normalised by its max |.| below the first
+ * cfg->mute_rows rows (which are taken as 0), cut into patches.
  * Adam with lr_t = lr (1 + cos(pi t / T)) / 2 over the T steps of this call,
- * moments reset at the start of each call; warm_start != 0 keeps the current
- * weights (transfer learning), 0 re-initialises them from cfg->seed.
+ * times min(1, (t+1)/W) for W = ceil(warmup_frac T) warm-up steps; fresh Adam
+ * moments at every call; warm_start != 0 keeps the current weights (transfer
+ * learning), 0 re-initialises them from cfg->seed.
  * loss_hist (host, may be NULL): cfg->epochs per-epoch mean MSE; when given,
  * the stream is synchronised.  Errors: DHFWI_ERR_ARG for a bad cfg. */
 int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz, int nx,
@@ -280,7 +286,8 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
 
 /* Update direction from the gradient (Section 2.3.1): out = net(g / max|g|)
  * * max|g| on the full image, zero padded to a multiple of 2^levels and
- * cropped.  g_dev, out_dev [nz][nx] float32 device.  DHFWI_ERR_STATE before
+ * cropped; the first mute_rows rows (of the last training cfg) of g are taken
+ * as 0 and excluded from max|g|.  g_dev, out_dev [nz][nx] float32 device.  DHFWI_ERR_STATE before
  * the network has weights. */
 int deblur_apply(dhfwi_ctx *ctx, const float *g_dev, int nz, int nx, float *out_dev, void *stream);
 

@@ -12,7 +12,8 @@ gradient (Section 2.3.1).
 Readings where the paper is silent (shared with the CUDA path by
 specification only): AvgPool padding 1 counting the padding; transposed conv
 kernel 2x2 stride 2; concatenation order [skip, up]; biases in every conv;
-Adam betas (0.9, 0.999), eps 1e-8, moments reset at each training session;
+Adam betas (0.9, 0.999), eps 1e-8, fresh moments at each training session,
+an optional linear learning-rate warm-up over the first steps of a session;
 lr_t = lr0 (1 + cos(pi t / T)) / 2; Kaiming-uniform init bound 1/sqrt(fan_in)
 drawn from SplitMix64; LeakyReLU derivative 0.2 at 0.
 
@@ -377,9 +378,12 @@ def permutation(n: int, seed: int, epoch: int):
     return perm
 
 
-def normalize(img):
-    m = float(np.max(np.abs(img)))
-    return (np.asarray(img, dtype=np.float64) / m if m > 0 else np.asarray(img, dtype=np.float64)), m
+def normalize(img, mute_rows: int = 0):
+    """img / max|img| with the first mute_rows rows taken as 0 (and left out of the max)."""
+    a = np.array(img, dtype=np.float64)
+    a[:mute_rows] = 0.0
+    m = float(np.max(np.abs(a)))
+    return (a / m if m > 0 else a), m
 
 
 @dataclasses.dataclass
@@ -393,21 +397,25 @@ class TrainCfg:
     beta2: float = 0.999
     eps: float = 1e-8
     seed: int = 29
+    mute_rows: int = 0
+    warmup_frac: float = 0.0
 
 
 def train(flat, x_img, y_img, spec: UNetSpec, cfg: TrainCfg, round_bf16: bool = True):
-    """Train from `flat` on (x_img -> y_img), each normalised by its max |.|.
-    Returns (flat float64, per-epoch mean batch loss list)."""
-    xn, _ = normalize(x_img)
-    yn, _ = normalize(y_img)
+    """Train from `flat` on (x_img -> y_img), each normalised by its max |.|,
+    with fresh Adam moments.  The learning rate at step t of T is the cosine
+    value times min(1, (t+1)/W), W = ceil(warmup_frac T).  Returns (flat
+    float64, per-epoch mean batch loss list)."""
+    xn, _ = normalize(x_img, cfg.mute_rows)
+    yn, _ = normalize(y_img, cfg.mute_rows)
     X = extract_patches(xn, cfg.patch, cfg.stride)[:, None]
     Y = extract_patches(yn, cfg.patch, cfg.stride)[:, None]
     n = X.shape[0]
     nb = -(-n // cfg.batch)
     T = cfg.epochs * nb
     theta = np.asarray(flat, dtype=np.float64).copy()
-    m = np.zeros_like(theta)
-    v = np.zeros_like(theta)
+    m, v = np.zeros_like(theta), np.zeros_like(theta)
+    W = math.ceil(cfg.warmup_frac * T)
     hist, t = [], 0
     for e in range(cfg.epochs):
         perm = permutation(n, cfg.seed, e)
@@ -417,17 +425,19 @@ def train(flat, x_img, y_img, spec: UNetSpec, cfg: TrainCfg, round_bf16: bool = 
             out, cache = forward(theta, X[idx], spec, round_bf16)
             loss, dout = mse(out, Y[idx])
             g = backward(theta, cache, dout, spec, round_bf16)
-            theta, m, v = adam_step(theta, g, m, v, t + 1, cosine_lr(cfg.lr, t, T), cfg.beta1, cfg.beta2, cfg.eps)
+            lr = cosine_lr(cfg.lr, t, T) * (min(1.0, (t + 1) / W) if W > 0 else 1.0)
+            theta, m, v = adam_step(theta, g, m, v, t + 1, lr, cfg.beta1, cfg.beta2, cfg.eps)
             t += 1
             tot += loss * len(idx)
         hist.append(tot / n)
     return theta, hist
 
 
-def apply(flat, img, spec: UNetSpec, round_bf16: bool = True):
-    """net(img / max|img|) * max|img| on the full image, zero-padded at the
-    bottom/right to a multiple of 2**levels and cropped back."""
-    xn, m = normalize(img)
+def apply(flat, img, spec: UNetSpec, round_bf16: bool = True, mute_rows: int = 0):
+    """net(img / max|img|) * max|img| on the full image (first mute_rows rows
+    taken as 0), zero-padded at the bottom/right to a multiple of 2**levels and
+    cropped back."""
+    xn, m = normalize(img, mute_rows)
     H, W = xn.shape
     mult = 1 << spec.levels
     Hp, Wp = -(-H // mult) * mult, -(-W // mult) * mult

@@ -54,7 +54,8 @@ class TrainCfg(ctypes.Structure):
     _fields_ = [("base_channels", ctypes.c_int), ("levels", ctypes.c_int), ("patch", ctypes.c_int),
                 ("stride", ctypes.c_int), ("batch", ctypes.c_int), ("epochs", ctypes.c_int),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("eps", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
+                ("eps", ctypes.c_float), ("seed", ctypes.c_ulonglong), ("mute_rows", ctypes.c_int),
+                ("warmup_frac", ctypes.c_float)]
 
 
 _lock = threading.Lock()

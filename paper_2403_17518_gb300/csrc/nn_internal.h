@@ -40,13 +40,16 @@ struct WgradArgs {
     int x_stride, x_off;
     int nimg, H, W;             // grid of the summed pixels (coarse grid for WG_CONVT)
     int co, ci;                 // channels (co used by WG_CONVT, ci by WG_CONV)
-    int M, N;
+    int M, N;                   // N = nw + 8: weight columns, then a ones column (bias) and 7 zero columns
+    int nw;                     // weight columns (9*ci for WG_CONV, ci for WG_CONVT)
+    const __nv_bfloat16 *ones;  // 8 bf16 values {1, 0, ..., 0}
     float *part;                // [splits][M][N]
 };
 
 void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s);
 int wgrad_splits(long long kpix, int M, int N);
-void launch_wgrad(const WgradArgs &a, int splits, float *dw, cudaStream_t s);
+// Weight gradient into dw (parameter layout) and bias gradient into db.
+void launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s);
 void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, float *part, int max_blocks, float *db,
                       cudaStream_t s);
 void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H, int W, int C, __nv_bfloat16 *y,
@@ -68,8 +71,8 @@ void launch_to_bf16(const float *x, long long n, __nv_bfloat16 *y, cudaStream_t 
 void launch_transpose_w(const __nv_bfloat16 *w, int co, int taps, int ci, __nv_bfloat16 *wt, cudaStream_t s);
 void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cudaStream_t s);
 void launch_gather_patches(const float *img, int nx, const int *oz, const int *ox, const int *sel, int nb, int p,
-                           const float *scale, float *dst, cudaStream_t s);
-void launch_pad_image(const float *img, int nz, int nx, int Hp, int Wp, const float *scale, float *dst,
+                           const float *scale, int mute, float *dst, cudaStream_t s);
+void launch_pad_image(const float *img, int nz, int nx, int Hp, int Wp, const float *scale, int mute, float *dst,
                       cudaStream_t s);
 void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const float *scale, float *dst,
                        cudaStream_t s);

@@ -312,12 +312,15 @@ __global__ void __launch_bounds__(128) igemm_wgrad_kernel(WgradArgs P) {
                 }
                 cp16(&S.a[st][kr][ch * 8], src, ok);
             }
-            // B chunk: 8 consecutive n.
+            // B chunk: 8 consecutive n (the chunk at nw is the ones column).
             {
                 const int n = n0 + ch * 8;
                 bool ok = k < ke && n < P.N;
                 const __nv_bfloat16 *src = P.x;
-                if (ok) {
+                if (ok && n >= P.nw) {
+                    src = P.ones;
+                    ok = n == P.nw;
+                } else if (ok) {
                     const int img = (int)(k / HW);
                     const int r = (int)(k - img * HW);
                     const int h = r / P.W, w = r - h * P.W;
@@ -407,20 +410,35 @@ __global__ void __launch_bounds__(128) igemm_wgrad_kernel(WgradArgs P) {
 
 // Sum of the split partials in split order; writes the weight gradient in
 // the parameter layout (conv: [co][tap][ci] = C[co][n]; transposed conv:
-// [co][a][b][ci] = C[(a*2+b)*Co + co][ci]).
-__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, int M, int N, int mode, int co_n,
-                                    float *__restrict__ dw) {
+// [co][a][b][ci] = C[(a*2+b)*Co + co][ci]) and the bias gradient from the
+// ones column (transposed conv: summed over the four (a, b) rows).
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, int M, int N, int nw, int mode,
+                                    int co_n, float *__restrict__ dw, float *__restrict__ db) {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)M * N) return;
+    const int m = (int)(idx / N), n = (int)(idx - (long long)m * N);
+    if (n > nw) return;
+    if (n == nw) {
+        if (mode == WG_CONV) {
+            float s = 0.f;
+            for (int z = 0; z < splits; z++) s += part[(long long)z * M * N + idx];
+            db[m] = s;
+        } else if (m < co_n) {  // one thread per co sums the rows (ab*co_n + m)
+            float s = 0.f;
+            for (int ab = 0; ab < 4; ab++)
+                for (int z = 0; z < splits; z++) s += part[(long long)z * M * N + (long long)(ab * co_n + m) * N + n];
+            db[m] = s;
+        }
+        return;
+    }
     float s = 0.f;
     for (int z = 0; z < splits; z++) s += part[(long long)z * M * N + idx];
-    const int m = (int)(idx / N), n = (int)(idx - (long long)m * N);
     long long o;
     if (mode == WG_CONV) {
-        o = idx;
+        o = (long long)m * nw + n;
     } else {
         const int ab = m / co_n, co = m - ab * co_n;
-        o = ((long long)co * 4 + ab) * N + n;
+        o = ((long long)co * 4 + ab) * nw + n;
     }
     dw[o] = s;
 }
@@ -642,10 +660,11 @@ __global__ void input_pack_kernel(const float *__restrict__ x, long long P, int 
     }
 }
 
-// Patches: dst[b][i][j] = img[oz + i][ox + j] * scale for patch b = sel[b].
+// Patches: dst[b][i][j] = img[oz + i][ox + j] * scale for patch b = sel[b]
+// (0 in the first `mute` image rows).
 __global__ void gather_patches_kernel(const float *__restrict__ img, int nx, const int *__restrict__ oz,
                                       const int *__restrict__ ox, const int *__restrict__ sel, int nb, int p,
-                                      const float *__restrict__ scale, float *__restrict__ dst) {
+                                      const float *__restrict__ scale, int mute, float *__restrict__ dst) {
     const long long n = (long long)nb * p * p;
     const float sc = *scale;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -654,18 +673,19 @@ __global__ void gather_patches_kernel(const float *__restrict__ img, int nx, con
         const int ii = (int)(r % p);
         const int b = (int)(r / p);
         const int pi = sel[b];
-        dst[i] = img[(long long)(oz[pi] + ii) * nx + ox[pi] + j] * sc;
+        const int row = oz[pi] + ii;
+        dst[i] = row < mute ? 0.f : img[(long long)row * nx + ox[pi] + j] * sc;
     }
 }
 
-// Full-image input: zero padded to Hp x Wp, scaled.
+// Full-image input: zero padded to Hp x Wp, scaled, first `mute` rows 0.
 __global__ void pad_image_kernel(const float *__restrict__ img, int nz, int nx, int Hp, int Wp,
-                                 const float *__restrict__ scale, float *__restrict__ dst) {
+                                 const float *__restrict__ scale, int mute, float *__restrict__ dst) {
     const long long n = (long long)Hp * Wp;
     const float sc = *scale;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int w = (int)(i % Wp), h = (int)(i / Wp);
-        dst[i] = (h < nz && w < nx) ? img[(long long)h * nx + w] * sc : 0.f;
+        dst[i] = (h >= mute && h < nz && w < nx) ? img[(long long)h * nx + w] * sc : 0.f;
     }
 }
 
@@ -777,7 +797,7 @@ int wgrad_splits(long long kpix, int M, int N) {
     return (int)want;
 }
 
-void launch_wgrad(const WgradArgs &a, int splits, float *dw, cudaStream_t s) {
+void launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s) {
     const size_t sm = sizeof(WgradSmem);
     static bool attr = false;
     if (!attr) {
@@ -787,7 +807,8 @@ void launch_wgrad(const WgradArgs &a, int splits, float *dw, cudaStream_t s) {
     dim3 grid((a.M + WBM - 1) / WBM, (a.N + WBN - 1) / WBN, splits);
     igemm_wgrad_kernel<<<grid, 128, sm, s>>>(a);
     const long long mn = (long long)a.M * a.N;
-    wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, splits, a.M, a.N, a.mode, a.co, dw);
+    wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, splits, a.M, a.N, a.nw, a.mode, a.co, dw,
+                                                                 db);
 }
 
 void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, float *part, int max_blocks,
@@ -852,12 +873,13 @@ void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cu
     input_pack_kernel<<<grid_for(P * Cp), 256, 0, s>>>(x, P, Cp, y);
 }
 void launch_gather_patches(const float *img, int nx, const int *oz, const int *ox, const int *sel, int nb, int p,
-                           const float *scale, float *dst, cudaStream_t s) {
-    gather_patches_kernel<<<grid_for((long long)nb * p * p), 256, 0, s>>>(img, nx, oz, ox, sel, nb, p, scale, dst);
+                           const float *scale, int mute, float *dst, cudaStream_t s) {
+    gather_patches_kernel<<<grid_for((long long)nb * p * p), 256, 0, s>>>(img, nx, oz, ox, sel, nb, p, scale, mute,
+                                                                          dst);
 }
-void launch_pad_image(const float *img, int nz, int nx, int Hp, int Wp, const float *scale, float *dst,
+void launch_pad_image(const float *img, int nz, int nx, int Hp, int Wp, const float *scale, int mute, float *dst,
                       cudaStream_t s) {
-    pad_image_kernel<<<grid_for((long long)Hp * Wp), 256, 0, s>>>(img, nz, nx, Hp, Wp, scale, dst);
+    pad_image_kernel<<<grid_for((long long)Hp * Wp), 256, 0, s>>>(img, nz, nx, Hp, Wp, scale, mute, dst);
 }
 void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const float *scale, float *dst,
                        cudaStream_t s) {

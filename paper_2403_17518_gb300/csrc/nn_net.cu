@@ -62,12 +62,13 @@ struct NetState {
     size_t wg_part_floats = 0;
     float *fp_part = nullptr;    // split-k partials of the fprop GEMMs
     size_t fp_part_floats = 0;
+    __nv_bfloat16 *ones = nullptr;  // {1, 0, ..., 0}: bias column of the weight-gradient GEMMs
     unsigned *mx = nullptr;
     float *scales = nullptr;  // [0..1] x scale, [2..3] y scale
     int *oz = nullptr, *ox = nullptr, *perm = nullptr;
     size_t oz_cap = 0, perm_cap = 0;
-    float *patch_x = nullptr, *patch_y = nullptr;
-    size_t patch_floats = 0;
+    int mute_rows = 0;           // from the last training configuration
+    long long adam_t = 0;        // Adam steps of the current training call
     long long launches = 0;
 
     // Workspace views (filled by layout()).
@@ -315,7 +316,8 @@ int layout(dhfwi_ctx *ctx, NetState &N, int n, int H, int W) {
     N.wsW = W;
     // Weight-gradient partials: splits x M x N over every weight-gradient call.
     size_t need = 0;
-    auto consider = [&](long long kpix, int M, int Nn) {
+    auto consider = [&](long long kpix, int M, int Nw) {
+        const int Nn = Nw + 8;  // + bias column block
         need = std::max(need, (size_t)wgrad_splits(kpix, M, Nn) * M * Nn);
     };
     consider((long long)P(0), (int)C(0), 9 * CPAD);  // first layer (padded input)
@@ -478,13 +480,14 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
     w.W = W;
     w.ci = ci;
     w.M = d.co;
-    w.N = 9 * ci;
+    w.nw = 9 * ci;
+    w.N = w.nw + 8;
+    w.ones = N.ones;
     w.part = N.wg_part;
     const int sp = wgrad_splits(P, w.M, w.N);
     float *dw = li == 0 ? N.g0pad : N.grad + d.off;
-    launch_wgrad(w, sp, dw, s);
-    launch_bias_grad(N.V.gbuf, d.co, d.co, P, N.red_part, RED_BLOCKS, N.grad + d.off + d.nw, s);
-    N.launches += 5;
+    launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, s);
+    N.launches += 3;
     if (li == 0) {
         launch_unpad_first_grad(N.g0pad, d.co, CPAD, N.grad + d.off, s);
         N.launches++;
@@ -562,11 +565,12 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         w.W = Wc;
         w.co = C(r);
         w.M = 4 * C(r);
-        w.N = C(r + 1);
+        w.nw = C(r + 1);
+        w.N = w.nw + 8;
+        w.ones = N.ones;
         w.part = N.wg_part;
         const int sp = wgrad_splits((long long)n * Hc * Wc, w.M, w.N);
-        launch_wgrad(w, sp, N.grad + dt.off, s);
-        launch_bias_grad(V.gbuf, C(r), C(r), Pr, N.red_part, RED_BLOCKS, N.grad + dt.off + dt.nw, s);
+        launch_wgrad(w, sp, N.grad + dt.off, N.grad + dt.off + dt.nw, s);
         FpropArgs a{};
         a.src = V.gbuf;
         a.src_stride = C(r);
@@ -591,7 +595,7 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         a.part = N.fp_part;
         a.part_floats = (long long)N.fp_part_floats;
         launch_fprop(a, EPI_F32, s);
-        N.launches += 6;
+        N.launches += 5;
         std::swap(dA, dB);
     }
     // dA: gradient of the bottom activation.
@@ -631,6 +635,12 @@ int ensure_small(dhfwi_ctx *ctx, NetState &N) {
     if (!N.loss_acc && (rc = dev_alloc(ctx, (void **)&N.loss_acc, sizeof(double) * 4096))) return rc;
     if (!N.mx && (rc = dev_alloc(ctx, (void **)&N.mx, 16))) return rc;
     if (!N.scales && (rc = dev_alloc(ctx, (void **)&N.scales, 4 * sizeof(float)))) return rc;
+    if (!N.ones) {
+        if ((rc = dev_alloc(ctx, (void **)&N.ones, 16))) return rc;
+        __nv_bfloat16 h[8];
+        for (int i = 0; i < 8; i++) h[i] = __float2bfloat16_rn(i == 0 ? 1.0f : 0.0f);
+        NCK(cudaMemcpy(N.ones, h, sizeof h, cudaMemcpyHostToDevice));
+    }
     return DHFWI_OK;
 }
 
@@ -664,9 +674,8 @@ int upload_params(dhfwi_ctx *ctx, NetState &N, const float *host, cudaStream_t s
 void net_destroy(NetState *net) {
     if (!net) return;
     free_params(*net);
-    void *ps[] = {net->arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->mx,
-                  net->scales,
-                  net->oz, net->ox, net->perm, net->patch_x, net->patch_y};
+    void *ps[] = {net->arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->ones,
+                  net->mx, net->scales, net->oz, net->ox, net->perm};
     for (void *p : ps) dev_free(p);
     delete net;
 }
@@ -781,6 +790,9 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
         cfg->epochs > 4096)
         return fail(ctx, DHFWI_ERR_ARG, "bad training configuration");
     if (nz < cfg->patch || nx < cfg->patch) return fail(ctx, DHFWI_ERR_ARG, "image smaller than the patch");
+    if (cfg->mute_rows < 0 || cfg->mute_rows >= nz) return fail(ctx, DHFWI_ERR_ARG, "mute_rows must be in [0, nz)");
+    if (!(cfg->warmup_frac >= 0.f) || cfg->warmup_frac > 1.f)
+        return fail(ctx, DHFWI_ERR_ARG, "warmup_frac must be in [0, 1]");
     cudaSetDevice(ctx_device(ctx));
     cudaStream_t s = (cudaStream_t)stream;
     int rc = ensure_net(ctx, cfg->base_channels, cfg->levels);
@@ -826,31 +838,40 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
     NCK(cudaMemcpyAsync(N.oz, hoz.data(), 4 * (size_t)npatch, cudaMemcpyHostToDevice, s));
     NCK(cudaMemcpyAsync(N.ox, hox.data(), 4 * (size_t)npatch, cudaMemcpyHostToDevice, s));
     NCK(cudaMemcpyAsync(N.perm, perms.data(), 4 * perms.size(), cudaMemcpyHostToDevice, s));
-    // Normalisation by max |.| of each image (Section 2.3.1 pair: x = delta m_1, y = g).
-    launch_absmax(x_dev, (long long)nz * nx, N.mx, N.scales, s);
-    launch_absmax(y_dev, (long long)nz * nx, N.mx + 1, N.scales + 2, s);
+    // Normalisation by max |.| of each image below the muted rows (Section
+    // 2.3.1 pair: x = delta m_1, y = g).
+    N.mute_rows = cfg->mute_rows;
+    const long long moff = (long long)N.mute_rows * nx;
+    launch_absmax(x_dev + moff, (long long)nz * nx - moff, N.mx, N.scales, s);
+    launch_absmax(y_dev + moff, (long long)nz * nx - moff, N.mx + 1, N.scales + 2, s);
     N.launches += 6;
-    // Adam state reset for this session.
+    // Fresh Adam moments for every training call; the learning rate ramps up
+    // linearly over the first warmup steps so that the sign-like first
+    // steps of fresh moments stay small.
     NCK(cudaMemsetAsync(N.m, 0, sizeof(float) * N.nparams, s));
     NCK(cudaMemsetAsync(N.v, 0, sizeof(float) * N.nparams, s));
+    N.adam_t = 0;
     NCK(cudaMemsetAsync(N.loss_acc, 0, sizeof(double) * cfg->epochs, s));
     const int nb = (npatch + B - 1) / B;
     const long long T = (long long)cfg->epochs * nb;
+    const long long warm_n = (long long)std::ceil((double)cfg->warmup_frac * (double)T);
     long long t = 0;
     for (int e = 0; e < cfg->epochs; e++) {
         for (int b = 0; b < nb; b++) {
             const int cnt = std::min(B, npatch - b * B);
             const int *sel = N.perm + (size_t)e * npatch + (size_t)b * B;
-            launch_gather_patches(x_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales, N.V.xf, s);
-            launch_gather_patches(y_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales + 2, N.V.yf, s);
+            launch_gather_patches(x_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales, N.mute_rows, N.V.xf, s);
+            launch_gather_patches(y_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales + 2, N.mute_rows, N.V.yf, s);
             N.launches += 2;
             forward(N, cnt, p, p, s);
             loss(N, cnt, p, p, s);
             launch_loss_accum(N.mse_part, MSE_BLOCKS, (double)cnt / ((double)cnt * p * p), N.loss_acc + e, s);
             backward(N, cnt, p, p, s);
-            const double lr = 0.5 * cfg->lr * (1.0 + std::cos(M_PI * (double)t / (double)T));
-            launch_adam(N.theta, N.grad, N.m, N.v, N.nparams, (float)lr, cfg->beta1, cfg->beta2, cfg->eps, (int)(t + 1),
-                        N.w16, s);
+            double lr = 0.5 * cfg->lr * (1.0 + std::cos(M_PI * (double)t / (double)T));
+            if (warm_n > 0 && t < warm_n) lr *= (double)(t + 1) / (double)warm_n;
+            N.adam_t++;
+            launch_adam(N.theta, N.grad, N.m, N.v, N.nparams, (float)lr, cfg->beta1, cfg->beta2, cfg->eps,
+                        (int)N.adam_t, N.w16, s);
             refresh_weights(N, s, false);
             N.launches += 2;
             t++;
@@ -883,8 +904,10 @@ int deblur_apply(dhfwi_ctx *ctx, const float *g_dev, int nz, int nx, float *out_
     const int Hp = (nz + mult - 1) / mult * mult, Wp = (nx + mult - 1) / mult * mult;
     int rc = layout(ctx, N, 1, Hp, Wp);
     if (rc) return rc;
-    launch_absmax(g_dev, (long long)nz * nx, N.mx, N.scales, s);
-    launch_pad_image(g_dev, nz, nx, Hp, Wp, N.scales, N.V.xf, s);
+    const int mute = std::min(N.mute_rows, nz - 1);
+    const long long moff = (long long)mute * nx;
+    launch_absmax(g_dev + moff, (long long)nz * nx - moff, N.mx, N.scales, s);
+    launch_pad_image(g_dev, nz, nx, Hp, Wp, N.scales, mute, N.V.xf, s);
     forward(N, 1, Hp, Wp, s);
     launch_crop_image(N.V.out, Hp, Wp, nz, nx, N.scales + 1, out_dev, s);
     N.launches += 5;

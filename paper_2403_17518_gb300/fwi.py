@@ -77,13 +77,39 @@ def model_rms(v: torch.Tensor, v_true: torch.Tensor) -> float:
     return float(torch.sqrt(torch.mean((v - v_true) ** 2)).item())
 
 
+def line_search(ctx, v, dirn, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_rows):
+    """Two-trial parabolic line search on the misfit along -dirn; returns
+    (alpha, whether a trial lowered the misfit)."""
+    Js = []
+    for a in (a1, 2 * a1):
+        ctx.fwi_update(v, dirn, a, vmin, vmax, mute_rows, out=trial)
+        ctx.model_shots(trial, ga, out=d_try)
+        Js.append(ctx.data_misfit(d_try, d_obs))
+    # Parabola through (0, J0), (a1, J1), (2 a1, J2).
+    J1, J2 = Js
+    curv = (J2 - 2 * J1 + J0) / (2 * a1 * a1)
+    slope = (4 * J1 - 3 * J0 - J2) / (2 * a1)
+    if curv > 0:
+        a_best = -slope / (2 * curv)
+    else:
+        a_best = 2 * a1 if J2 < J1 else a1
+    a_best = min(max(a_best, 0.0), 4 * a1)
+    improved = min(J1, J2) < J0
+    if improved and a_best == 0.0:
+        a_best = a1 if J1 <= J2 else 2 * a1
+    if not improved:
+        a_best = 0.0
+    return a_best, improved
+
+
 def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, cold_epochs: int, warm_epochs: int,
             vmin: float, vmax: float, mute_rows: int = 5, log=None):
     dev = ctx.device
     v_true = torch.tensor(case.v_true, dtype=torch.float32, device=dev)
     v = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
     d_full = ctx.model_shots(v_true, case.geom).cpu().numpy()
-    hist = [{"band": None, "iter": 0, "gpu_s": 0.0, "model_rms": model_rms(v, v_true), "misfit": None}]
+    hist = [{"band": None, "iter": 0, "gpu_s": 0.0, "solves": 0, "model_rms": model_rms(v, v_true), "misfit": None}]
+    solves = 0
     timer = Timer()
     grad = ctx.new_model()
     direction = ctx.new_model()
@@ -99,39 +125,61 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
         for it in range(iters):
             with timer:
                 J0, _ = ctx.fwi_gradient(v, ga, d_obs, grad=grad)
+                a1 = 0.01 * float(np.mean(case.v_init))
+                fallback = False
+                loss = None
+                solves += 2  # forward + adjoint of the gradient (checkpoint recomputation not counted)
                 if mode == "deblur":
+                    solves += 2  # Born modelling + its adjoint (Section 3.1: two more solves)
                     ctx.born_demig(v, ga, grad, out=d_born)
                     ctx.rtm_mig(v, ga, d_born, out=dm1)
-                    ctx.deblur_train(dm1, grad, warm_start=it > 0, epochs=warm_epochs if it > 0 else cold_epochs,
-                                     **net_cfg)
+                    h = ctx.deblur_train(dm1, grad, warm_start=it > 0,
+                                         epochs=warm_epochs if it > 0 else cold_epochs, mute_rows=mute_rows,
+                                         warmup_frac=0.1, **net_cfg)
+                    loss = [float(h[0]), float(h[-1])]
                     ctx.deblur_apply(grad, out=direction)
+                    a_best, ok = line_search(ctx, v, direction, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
+                                             mute_rows)
+                    solves += 2
                     dirn = direction
+                    if not ok:
+                        solves += 2
+                        # The plain gradient is the fallback when the network's
+                        # direction does not lower the misfit.
+                        fallback = True
+                        dirn = grad
+                        a_best, _ = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
+                                                mute_rows)
                 else:
                     dirn = grad
-                a1 = 0.01 * float(np.mean(case.v_init))
-                Js = []
-                for a in (a1, 2 * a1):
-                    ctx.fwi_update(v, dirn, a, vmin, vmax, mute_rows, out=trial)
-                    ctx.model_shots(trial, ga, out=d_try)
-                    Js.append(ctx.data_misfit(d_try, d_obs))
-                # Parabola through (0, J0), (a1, J1), (2 a1, J2).
-                J1, J2 = Js
-                curv = (J2 - 2 * J1 + J0) / (2 * a1 * a1)
-                slope = (4 * J1 - 3 * J0 - J2) / (2 * a1)
-                if curv > 0:
-                    a_best = -slope / (2 * curv)
-                else:
-                    a_best = 2 * a1 if J2 < J1 else a1
-                a_best = min(max(a_best, 0.0), 4 * a1)
-                if min(J1, J2) < J0 and a_best == 0.0:
-                    a_best = a1 if J1 <= J2 else 2 * a1
+                    a_best, _ = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_rows)
+                    solves += 2
                 ctx.fwi_update(v, dirn, a_best, vmin, vmax, mute_rows, out=v)
-            rec = {"band": fc, "iter": it + 1, "gpu_s": timer.seconds(), "model_rms": model_rms(v, v_true),
-                   "misfit": J0, "alpha": a_best}
+            rec = {"band": fc, "iter": it + 1, "gpu_s": timer.seconds(), "solves": solves,
+                   "model_rms": model_rms(v, v_true),
+                   "misfit": J0, "alpha": a_best, "fallback": fallback, "train_loss": loss}
             hist.append(rec)
             if log:
                 log(mode, rec)
     return hist
+
+
+def error_at(hist, budget: float, key: str = "gpu_s") -> float:
+    """Model RMS error reached within `budget` (of GPU seconds or solves)."""
+    best = hist[0]["model_rms"]
+    for r in hist:
+        if r[key] <= budget:
+            best = r["model_rms"]
+    return best
+
+
+def summarize(plain, deblur):
+    t = min(plain[-1]["gpu_s"], deblur[-1]["gpu_s"])
+    n = min(plain[-1]["solves"], deblur[-1]["solves"])
+    return {"equal_gpu_s": t, "plain_model_rms": error_at(plain, t), "deblur_model_rms": error_at(deblur, t),
+            "equal_solves": n, "plain_model_rms_at_solves": error_at(plain, n, "solves"),
+            "deblur_model_rms_at_solves": error_at(deblur, n, "solves"),
+            "initial_model_rms": plain[0]["model_rms"], "plain_final": plain[-1], "deblur_final": deblur[-1]}
 
 
 def main():
@@ -145,7 +193,10 @@ def main():
     p.add_argument("--shots", type=int, default=25)
     p.add_argument("--nt", type=int, default=1500)
     p.add_argument("--bands", default="3,5")
-    p.add_argument("--iters", type=int, default=8)
+    p.add_argument("--iters", type=int, default=8, help="iterations per band, deblurred arm")
+    p.add_argument("--iters-plain", type=int, default=0, help="iterations per band, plain arm (default --iters)")
+    p.add_argument("--mute", type=int, default=5, help="top rows muted in the update and the network input")
+    p.add_argument("--lr", type=float, default=2e-4, help="network learning rate")
     p.add_argument("--out", default="")
     a = p.parse_args()
     v = synth.layered_fault_model(a.nz, a.nx, a.h, seed=31)
@@ -156,14 +207,16 @@ def main():
                                   src_hi=a.nx - 11, wavelet=wav)
     case = synth.Case(a.nz, a.nx, a.h, a.dt, 20, v, v0, geom, name="fwi-loop")
     ctx = Context(a.nz, a.nx, a.h, a.dt, 20)
-    net = dict(base_channels=32, levels=4, patch=64, stride=32, batch=32, lr=1e-3, seed=29)
+    net = dict(base_channels=32, levels=4, patch=64, stride=32, batch=32, lr=a.lr, seed=29)
     bands = [float(b) for b in a.bands.split(",")]
     out = {"config": vars(a), "net": net}
     t0 = time.time()
     for mode in ("plain", "deblur"):
-        out[mode] = run_arm(ctx, case, mode, bands, a.iters, net, 200, 20, 1500.0, 4500.0,
+        iters = a.iters if mode == "deblur" or a.iters_plain <= 0 else a.iters_plain
+        out[mode] = run_arm(ctx, case, mode, bands, iters, net, 200, 20, 1500.0, 4500.0, mute_rows=a.mute,
                             log=lambda m, r: print(m, json.dumps(r), flush=True))
     out["wall_s"] = time.time() - t0
+    out["summary"] = summarize(out["plain"], out["deblur"])
     s = json.dumps(out)
     if a.out:
         with open(a.out, "w") as f:

@@ -218,11 +218,12 @@ class Context:
 
     def deblur_train(self, x_img: torch.Tensor, y_img: torch.Tensor, warm_start: bool = True, base_channels=32,
                      levels=4, patch=128, stride=64, batch=32, epochs=200, lr=1e-3, beta1=0.9, beta2=0.999,
-                     eps=1e-8, seed=29, stream=None):
+                     eps=1e-8, seed=29, mute_rows=0, warmup_frac=0.0, stream=None):
         """Train x (doubly migrated image) -> y (gradient); returns per-epoch losses."""
         nz, nx = x_img.shape
         cfg = _lib.TrainCfg(int(base_channels), int(levels), int(patch), int(stride), int(batch), int(epochs),
-                            float(lr), float(beta1), float(beta2), float(eps), int(seed))
+                            float(lr), float(beta1), float(beta2), float(eps), int(seed), int(mute_rows),
+                            float(warmup_frac))
         hist = np.zeros(int(epochs), dtype=np.float32)
         self._check(self.lib.deblur_train(self.handle, self._dense(x_img, "x"), self._dense(y_img, "y"), nz, nx,
                                           ctypes.byref(cfg), 1 if warm_start else 0,

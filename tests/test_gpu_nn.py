@@ -105,6 +105,16 @@ def test_training_and_apply_parity():
     hist2 = ctx.deblur_train(_dev(x), _dev(y), warm_start=True, base_channels=8, levels=2, patch=16, stride=8,
                              batch=4, epochs=1, lr=1e-2, seed=4)
     assert hist2[0] < hist[0]
+    # Muted top rows and a learning-rate warm-up: training and apply match the oracle.
+    ctx.net_set(w)
+    hist3 = ctx.deblur_train(_dev(x), _dev(y), warm_start=True, base_channels=8, levels=2, patch=16, stride=8,
+                             batch=4, epochs=2, lr=1e-2, seed=4, mute_rows=5, warmup_frac=0.25)
+    cfg3 = onn.TrainCfg(patch=16, stride=8, batch=4, epochs=2, lr=1e-2, seed=4, mute_rows=5, warmup_frac=0.25)
+    w3, href3 = onn.train(w.astype(np.float64), x.astype(np.float64), y.astype(np.float64), spec, cfg3)
+    assert np.allclose(hist3, href3, rtol=2e-2), (hist3, href3)
+    out3 = ctx.deblur_apply(_dev(y)).cpu().numpy()
+    ref3 = onn.apply(ctx.net_get().astype(np.float64), y.astype(np.float64), spec, mute_rows=5)
+    assert rel_l2(out3, ref3) <= 1e-2
 
 
 def test_network_errors():
