@@ -207,21 +207,36 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # ncu traffic from the committed profile (null when the kernel has changed)
 # ---------------------------------------------------------------------------
-def kernel_source_hash() -> str:
-    src = os.path.join(ROOT, "paper_2403_17518_gb300", "csrc", "fd_kernels.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+# Sources of each forward step kernel: its profile under profiles/ records
+# their hash, and its DRAM figures are used only while the hash matches.
+KERNEL_SOURCES = {
+    "fwd_step_kernel": ["fd_kernels.cu", "fd_device.cuh"],
+    "fwd_tma_kernel": ["fd_tma.cu", "fd_device.cuh"],
+}
 
 
-def profiled_traffic(cells_per_launch: float):
+def kernel_source_hash(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(ROOT, "paper_2403_17518_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def forward_kernel(variant: int) -> str:
+    """Name of the forward step kernel a step-kernel variant launches."""
+    return "fwd_tma_kernel" if variant >= 3 else "fwd_step_kernel"
+
+
+def profiled_traffic(kernel: str, cells_per_launch: float):
     """DRAM bytes per launch of the forward step kernel from profiles/, scaled
     to this launch size, or None if absent or taken on another kernel source."""
-    path = os.path.join(ROOT, "profiles", "fwd_step_kernel_config2.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_config2.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_hash = re.search(r"kernel source sha256\[:16\]:\s*`?([0-9a-f]{16})", txt)
     m_bpc = re.search(r"DRAM bytes per cell update:\s*([0-9.]+)", txt)
-    if not m_hash or not m_bpc or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_bpc or m_hash.group(1) != kernel_source_hash(kernel):
         return None
     return float(m_bpc.group(1)) * cells_per_launch
 
@@ -489,7 +504,8 @@ def main():
     fwd_ms_per_launch = phase["ms"] / max(phase["launches"], 1)
     cells_per_launch = phase["cells"] / max(phase["launches"], 1)
     achieved = FWD_BYTES_PER_CELL * phase["cells"] / (phase["ms"] / 1e3) / 1e9 if phase["ms"] > 0 else None
-    traffic = profiled_traffic(cells_per_launch)
+    fwd_kernel = forward_kernel(ctx.stats()["step_variant"][0])
+    traffic = profiled_traffic(fwd_kernel, cells_per_launch)
 
     # End to end through the public API with host buffers.
     e2e = None
@@ -547,7 +563,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(case, args),
             "roofline": {
-                "kernel": "fwd_step_kernel (forward passes of fwi_gradient and rtm_mig)",
+                "kernel": f"{fwd_kernel} (forward passes of fwi_gradient and rtm_mig)",
                 "bound": "hbm", "achieved": round(achieved, 2) if achieved else None, "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
                 "traffic": round(traffic) if traffic else None,

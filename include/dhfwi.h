@@ -55,7 +55,8 @@ extern "C" {
 #define DHFWI_ERR_CFL (-3)        /* kappa_max * 13.0032 > 4: the scheme is unstable */
 #define DHFWI_ERR_NONFINITE (-4)  /* non-finite or non-positive velocity, or non-finite result */
 #define DHFWI_ERR_OOM (-5)        /* device allocation failed */
-#define DHFWI_ERR_TIMEOUT (-6)    /* a bounded device-side wait ran out */
+#define DHFWI_ERR_TIMEOUT (-6)    /* a bounded device-side wait ran out (a step kernel's tile copies did
+                                     not land within ~1 s); reported by the next call on the context */
 #define DHFWI_ERR_CUDA (-7)       /* any other CUDA runtime error */
 #define DHFWI_ERR_STATE (-8)      /* call made in the wrong state (e.g. apply before train) */
 

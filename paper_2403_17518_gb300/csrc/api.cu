@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -37,6 +39,7 @@ struct Plan {
     std::vector<TileRec> recs;
     std::vector<int> tiles_prefix;     // tiles of the first m slots
     long long pool_floats = 0;
+    int pitch = 0;                     // row pitch of every window in a pool
     long long n_data = 0;
     long long cells_per_step_all = 0;  // padded cells of all shots
     DevBuf d_shots, d_tiles, d_recs, d_slot_of, d_wav;
@@ -51,7 +54,7 @@ struct dhfwi_ctx {
     int pf = 0;             // pitch of padded model arrays
     int NZ = 0, NXF = 0;
     Plan plan;
-    DevBuf kap, vpad, g2v, dkap, status, partial;
+    DevBuf kap, dkap, status, partial;
     DevBuf fields;          // general wavefield pools
     DevBuf ck;              // checkpoints
     DevBuf abuf;            // segment buffer of a^n
@@ -69,11 +72,15 @@ struct dhfwi_ctx {
     int nsm = 1;
     cudaEvent_t ev[3][2] = {};
     bool ev_used[3] = {};
+    // Tensor maps of the TMA-staged kernels by (base pointer, shape kind);
+    // cleared when a new plan changes the pool layout.
+    std::map<std::pair<const void *, int>, CUtensorMap> tmaps;
 };
 
 namespace {
 
 constexpr int RESID_BLOCKS = 1024;
+constexpr int TFLAG_WORD = 4;  // status word set by a timed-out TMA wait
 constexpr int NPOOLS = 7;  // field pools: u (2) + D, nu (2) + D_nu, image
 
 int fail(dhfwi_ctx *ctx, int code, const std::string &msg) {
@@ -127,6 +134,26 @@ unsigned long long fnv(unsigned long long h, const void *p, size_t n) {
 }
 
 int round_up(int a, int m) { return (a + m - 1) / m * m; }
+
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point
+// (no link-time dependency on the driver library); null when unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
 
 // Host validation of the geometry against the grid.
 int validate_geom(dhfwi_ctx *ctx, const dhfwi_geom *G) {
@@ -209,6 +236,7 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
     // The plan's device tables may still be read by earlier work on any stream.
     CK(cudaDeviceSynchronize());
     P.hash = 0;
+    ctx->tmaps.clear();
     P.n_shots = ns;
     P.nt_max = G->nt_max;
     std::vector<int> order(ns);
@@ -224,6 +252,11 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
     P.tiles.clear();
     P.recs.clear();
     P.tiles_prefix.assign(ns + 1, 0);
+    // One row pitch for all windows: a pool is then a [slot][NZ][pitch] array
+    // that a single 3-D tensor map describes.
+    int pitch = POOL_ALIGN;
+    for (int s = 0; s < ns; s++) pitch = std::max(pitch, round_up(G->win_x1[s] - G->win_x0[s] + 2 * nb, POOL_ALIGN));
+    P.pitch = pitch;
     long long foff = 0;
     P.cells_per_step_all = 0;
     for (int k = 0; k < ns; k++) {
@@ -231,9 +264,9 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
         ShotDesc &sd = P.shots[k];
         const int x0 = G->win_x0[s], x1 = G->win_x1[s];
         sd.nxw = x1 - x0 + 2 * nb;
-        sd.pitch = round_up(sd.nxw, POOL_ALIGN);
+        sd.pitch = pitch;
         sd.foff = foff;
-        foff += (long long)sd.pitch * NZ;
+        foff += (long long)pitch * NZ;
         sd.doff = doff[s];
         sd.x0 = x0;
         sd.sz = G->src_iz[s] + nb;
@@ -297,14 +330,126 @@ StepCommon common(dhfwi_ctx *ctx) {
     c.tiles = (const Tile *)ctx->plan.d_tiles.p;
     c.recs = (const TileRec *)ctx->plan.d_recs.p;
     c.kap = (const float *)ctx->kap.p;
-    c.vpad = (const float *)ctx->vpad.p;
-    c.g2v = (const float *)ctx->g2v.p;
     c.mstride = (long long)ctx->NZ * ctx->pf;
     c.wav = (const float *)ctx->plan.d_wav.p;
     c.pf = ctx->pf;
     c.NZ = ctx->NZ;
     c.nb = ctx->g.nb;
+    c.tflag = (unsigned *)ctx->status.p + TFLAG_WORD;
     return c;
+}
+
+// Tensor-map shape kinds: field pool with halo box, field pool cell box,
+// model array (4 copies) cell box.
+enum { MAP_POOL_HALO = 0, MAP_POOL_CELL = 1, MAP_MODEL = 2 };
+
+// The tensor map of one array for the TMA-staged kernels (cached).
+int tensor_map(dhfwi_ctx *ctx, const float *base, int kind, CUtensorMap *out) {
+    auto key = std::make_pair((const void *)base, kind);
+    auto it = ctx->tmaps.find(key);
+    if (it != ctx->tmaps.end()) {
+        *out = it->second;
+        return DHFWI_OK;
+    }
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return fail(ctx, DHFWI_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const Plan &P = ctx->plan;
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3] = {TX, TZ, 1}, estr[3] = {1, 1, 1};
+    if (kind == MAP_MODEL) {
+        dims[0] = ctx->pf;
+        dims[1] = ctx->NZ;
+        dims[2] = 4;
+        strides[0] = sizeof(float) * (cuuint64_t)ctx->pf;
+        strides[1] = sizeof(float) * (cuuint64_t)ctx->NZ * ctx->pf;
+    } else {
+        dims[0] = P.pitch;
+        dims[1] = ctx->NZ;
+        dims[2] = P.n_shots;
+        strides[0] = sizeof(float) * (cuuint64_t)P.pitch;
+        strides[1] = sizeof(float) * (cuuint64_t)P.pitch * ctx->NZ;
+        if (kind == MAP_POOL_HALO) {
+            box[0] = TX + 2 * HALO;
+            box[1] = TZ + 2 * HALO;
+        }
+    }
+    CUtensorMap m;
+    const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char msg[128];
+        snprintf(msg, sizeof msg, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+        return fail(ctx, DHFWI_ERR_CUDA, msg);
+    }
+    ctx->tmaps[key] = m;
+    *out = m;
+    return DHFWI_OK;
+}
+
+// Maps of a forward-step launch (u^n halo, D^n, kappa).
+int fwd_maps(dhfwi_ctx *ctx, const FwdArgs &a, TileMaps *M) {
+    int rc;
+    if ((rc = tensor_map(ctx, a.u, MAP_POOL_HALO, &M->m[0]))) return rc;
+    if ((rc = tensor_map(ctx, a.dd, MAP_POOL_CELL, &M->m[1]))) return rc;
+    return tensor_map(ctx, a.c.kap, MAP_MODEL, &M->m[2]);
+}
+
+// Maps of an adjoint-step launch (nu^{k+1} halo, D_nu, kappa, a^{k-1}).
+int adj_maps(dhfwi_ctx *ctx, const AdjArgs &b, TileMaps *M) {
+    int rc;
+    if ((rc = tensor_map(ctx, b.nu, MAP_POOL_HALO, &M->m[0]))) return rc;
+    if ((rc = tensor_map(ctx, b.dd, MAP_POOL_CELL, &M->m[1]))) return rc;
+    if ((rc = tensor_map(ctx, b.c.kap, MAP_MODEL, &M->m[2]))) return rc;
+    return tensor_map(ctx, b.a, MAP_POOL_CELL, &M->m[3]);
+}
+
+// Maps of a Born-step launch (u0^n and p^n halos, D_u0, D_p, kappa, d kappa).
+int born_maps(dhfwi_ctx *ctx, const BornArgs &b, TileMaps *M) {
+    int rc;
+    if ((rc = tensor_map(ctx, b.u, MAP_POOL_HALO, &M->m[0]))) return rc;
+    if ((rc = tensor_map(ctx, b.p, MAP_POOL_HALO, &M->m[1]))) return rc;
+    if ((rc = tensor_map(ctx, b.du, MAP_POOL_CELL, &M->m[2]))) return rc;
+    if ((rc = tensor_map(ctx, b.dp, MAP_POOL_CELL, &M->m[3]))) return rc;
+    if ((rc = tensor_map(ctx, b.c.kap, MAP_MODEL, &M->m[4]))) return rc;
+    return tensor_map(ctx, b.dkap, MAP_MODEL, &M->m[5]);
+}
+
+int adj_step(dhfwi_ctx *ctx, const AdjArgs &b, int ntiles, const StepLaunch &L, cudaStream_t st) {
+    if (L.variant >= FIRST_TMA_VARIANT) {
+        TileMaps M;
+        int rc = adj_maps(ctx, b, &M);
+        if (rc) return rc;
+        launch_adj_step(b, ntiles, L, &M, st);
+    } else {
+        launch_adj_step(b, ntiles, L, nullptr, st);
+    }
+    return DHFWI_OK;
+}
+
+int born_step(dhfwi_ctx *ctx, const BornArgs &b, int ntiles, const StepLaunch &L, cudaStream_t st) {
+    if (L.variant >= FIRST_TMA_VARIANT) {
+        TileMaps M;
+        int rc = born_maps(ctx, b, &M);
+        if (rc) return rc;
+        launch_born_step(b, ntiles, L, &M, st);
+    } else {
+        launch_born_step(b, ntiles, L, nullptr, st);
+    }
+    return DHFWI_OK;
+}
+
+// Forward-step launch with the maps its variant needs.
+int fwd_step(dhfwi_ctx *ctx, const FwdArgs &a, int ntiles, const StepLaunch &L, cudaStream_t st) {
+    if (L.variant >= FIRST_TMA_VARIANT) {
+        TileMaps M;
+        int rc = fwd_maps(ctx, a, &M);
+        if (rc) return rc;
+        launch_fwd_step(a, ntiles, L, &M, st);
+    } else {
+        launch_fwd_step(a, ntiles, L, nullptr, st);
+    }
+    return DHFWI_OK;
 }
 
 // Padded model arrays from v (and dv), with the velocity / CFL check.
@@ -313,19 +458,21 @@ int prep_model(dhfwi_ctx *ctx, const float *v, const float *dv, int rel, cudaStr
     size_t mb = sizeof(float) * (size_t)ctx->NZ * ctx->pf;
     int rc;
     if ((rc = ensure(ctx, ctx->kap, 4 * mb, "kappa"))) return rc;
-    if ((rc = ensure(ctx, ctx->vpad, mb, "padded velocity"))) return rc;
-    if ((rc = ensure(ctx, ctx->g2v, 4 * mb, "padded 2/v"))) return rc;
     if (dv && (rc = ensure(ctx, ctx->dkap, 4 * mb, "d kappa"))) return rc;
     CK(cudaMemsetAsync(ctx->status.p, 0, 2 * sizeof(unsigned), st));
     const double c = ((double)ctx->g.dt * ctx->g.dt) / ((double)ctx->g.h * ctx->g.h);
     launch_prep_model(v, dv, rel, ctx->g.nz, ctx->g.nx, ctx->g.nb, c, (float *)ctx->kap.p,
-                      (float *)ctx->vpad.p, (float *)ctx->g2v.p, dv ? (float *)ctx->dkap.p : nullptr, ctx->pf,
-                      (long long)ctx->NZ * ctx->pf,
+                      dv ? (float *)ctx->dkap.p : nullptr, ctx->pf, (long long)ctx->NZ * ctx->pf,
                       (unsigned *)ctx->status.p, st);
     ctx->stats.kernel_launches++;
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(ctx->h_status, ctx->status.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status.p, (TFLAG_WORD + 1) * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                       st));
     CK(cudaStreamSynchronize(st));
+    if (ctx->h_status[TFLAG_WORD]) {
+        CK(cudaMemset((unsigned *)ctx->status.p + TFLAG_WORD, 0, sizeof(unsigned)));
+        return fail(ctx, DHFWI_ERR_TIMEOUT, "a step kernel of an earlier call timed out waiting for its tile copies");
+    }
     if (ctx->h_status[0])
         return fail(ctx, DHFWI_ERR_NONFINITE, "velocity must be finite and > 0 (and dv finite)");
     float kmax;
@@ -381,7 +528,7 @@ int end_call(dhfwi_ctx *ctx) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
     ctx->stats.checkpoint_every = ctx->ck_every;
     for (int k = 0; k < 4; k++) ctx->stats.step_variant[k] = ctx->launch[k].variant;
-    double ws = ctx->kap.bytes + ctx->vpad.bytes + ctx->dkap.bytes + ctx->fields.bytes + ctx->ck.bytes +
+    double ws = ctx->kap.bytes + ctx->dkap.bytes + ctx->fields.bytes + ctx->ck.bytes +
                 ctx->abuf.bytes + ctx->dtmp.bytes + ctx->rtmp.bytes;
     ctx->stats.workspace_bytes = ws;
     return DHFWI_OK;
@@ -402,10 +549,15 @@ void set_variant(dhfwi_ctx *ctx, int kind, int v) {
 int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
     const Plan &P = ctx->plan;
     if (ctx->tuned_hash == P.hash) return DHFWI_OK;
+    static const int kernel_kind[4] = {0, 0, 1, 2};
     const char *pin = getenv("DHFWI_STEP_VARIANT");
     if (pin && *pin) {
+        // A kind without the pinned variant takes its last one (a pin past
+        // every kind's range, or negative, takes the default).
         const int v = atoi(pin);
-        for (int k = 0; k < 4; k++) set_variant(ctx, k, v < 0 || v >= N_STEP_VARIANTS ? 1 : v);
+        const bool valid = v >= 0 && v < N_STEP_VARIANTS;
+        for (int k = 0; k < 4; k++)
+            set_variant(ctx, k, valid ? std::min(v, step_variants(kernel_kind[k]) - 1) : 1);
         ctx->tuned_hash = P.hash;
         return DHFWI_OK;
     }
@@ -423,13 +575,17 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    long long timed = 0;
     for (int kind = 0; kind < 4; kind++) {
         float best = 1e30f;
         int best_v = 1;
-        for (int v = 0; v < N_STEP_VARIANTS; v++) {
+        int nv = step_variants(kernel_kind[kind]);
+        if (!encode_tiled()) nv = std::min(nv, (int)FIRST_TMA_VARIANT);
+        for (int v = 0; v < nv; v++) {
             set_variant(ctx, kind, v);
             float ms = 0.f;
-            for (int rep = -1; rep < reps; rep++) {
+            rc = DHFWI_OK;
+            for (int rep = -1; rep < reps && !rc; rep++) {
                 if (rep == 0) cudaEventRecord(e0, st);
                 if (kind <= 1) {
                     FwdArgs a{};
@@ -440,7 +596,7 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
                     a.a_out = kind == 1 ? F + 3 * pool : nullptr;
                     a.d = kind == 0 ? (float *)ctx->dtmp.p : nullptr;
                     a.n = 0;
-                    launch_fwd_step(a, ntiles, ctx->launch[kind], st);
+                    if ((rc = fwd_step(ctx, a, ntiles, ctx->launch[kind], st))) break;
                 } else if (kind == 2) {
                     AdjArgs b{};
                     b.c = common(ctx);
@@ -451,7 +607,7 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
                     b.g = F + 4 * pool;
                     b.r = (const float *)ctx->rtmp.p;
                     b.k = 1;
-                    launch_adj_step(b, ntiles, ctx->launch[kind], st);
+                    if ((rc = adj_step(ctx, b, ntiles, ctx->launch[kind], st))) break;
                 } else {
                     BornArgs b{};
                     b.c = common(ctx);
@@ -464,7 +620,7 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
                     b.dkap = (const float *)ctx->kap.p;
                     b.d = (float *)ctx->dtmp.p;
                     b.n = 0;
-                    launch_born_step(b, ntiles, ctx->launch[kind], st);
+                    if ((rc = born_step(ctx, b, ntiles, ctx->launch[kind], st))) break;
                 }
             }
             cudaEventRecord(e1, st);
@@ -474,6 +630,11 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
                 cudaEventDestroy(e1);
                 return cuda_fail(ctx, e, "autotune");
             }
+            if (rc) {  // a variant that cannot be launched here is not a candidate
+                ctx->err.clear();
+                continue;
+            }
+            timed += reps + 1;
             cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best) {
                 best = ms;
@@ -484,7 +645,7 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->stats.kernel_launches += 4LL * N_STEP_VARIANTS * (reps + 1);
+    ctx->stats.kernel_launches += timed;
     ctx->tuned_hash = P.hash;
     CK(cudaGetLastError());
     return DHFWI_OK;
@@ -516,7 +677,8 @@ int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *d, float
             a.ck_u = a.ck_d = nullptr;
         }
         a.n = n;
-        launch_fwd_step(a, nt, ctx->launch[0], st);
+        int rc = fwd_step(ctx, a, nt, ctx->launch[0], st);
+        if (rc) return rc;
         ctx->stats.kernel_launches++;
         ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
         std::swap(cur, nxt);
@@ -557,7 +719,8 @@ int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float 
             f.d = nullptr;
             f.ck_u = f.ck_d = nullptr;
             f.n = n;
-            launch_fwd_step(f, active_tiles(P, n), ctx->launch[1], st);
+            int rc = fwd_step(ctx, f, active_tiles(P, n), ctx->launch[1], st);
+            if (rc) return rc;
             ctx->stats.kernel_launches++;
             ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
             std::swap(cur, nxt);
@@ -567,7 +730,8 @@ int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float 
             b.nun = nnxt;
             b.a = abuf + (long long)(k - 1 - n0) * pool;
             b.k = k;
-            launch_adj_step(b, active_tiles(P, k - 1), ctx->launch[2], st);
+            int rc = adj_step(ctx, b, active_tiles(P, k - 1), ctx->launch[2], st);
+            if (rc) return rc;
             ctx->stats.kernel_launches++;
             ctx->stats.cell_updates += active_cells(P, k - 1, ctx->NZ);
             std::swap(ncur, nnxt);
@@ -660,7 +824,7 @@ int dhfwi_create(dhfwi_ctx **out, const dhfwi_grid *g, int device) {
 void dhfwi_destroy(dhfwi_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
-    DevBuf *bufs[] = {&ctx->kap, &ctx->vpad, &ctx->g2v, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
+    DevBuf *bufs[] = {&ctx->kap, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
                       &ctx->ck, &ctx->abuf, &ctx->dtmp, &ctx->rtmp, &ctx->plan.d_shots, &ctx->plan.d_tiles,
                       &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav};
     for (DevBuf *b : bufs) release(*b);
@@ -740,6 +904,9 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     float *uA = F, *uB = F + pool, *ud = F + 2 * pool;
     float *nuA = F + 3 * pool, *nuB = F + 4 * pool, *nud = F + 5 * pool, *gp = F + 6 * pool;
     CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
+    // Checkpoints are staged back as halo tiles: their padding columns, which
+    // no kernel writes, must read as zero.
+    CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
     if ((rc = run_forward(ctx, uA, uB, ud, dsyn, (float *)ctx->ck.p, K, st))) return rc;
     float *r = (float *)ctx->rtmp.p;
     launch_residual(dsyn, d_obs_dev, r, (long long)nd, (double *)ctx->partial.p, RESID_BLOCKS, st);
@@ -792,7 +959,7 @@ int born_demig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, cons
         a.p = p;
         a.pn = pn;
         a.n = n;
-        launch_born_step(a, active_tiles(P, n), ctx->launch[3], st);
+        if ((rc = born_step(ctx, a, active_tiles(P, n), ctx->launch[3], st))) return rc;
         ctx->stats.kernel_launches++;
         ctx->stats.cell_updates += 2 * active_cells(P, n, ctx->NZ);
         std::swap(u, un);
@@ -820,6 +987,9 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
     float *uA = F, *uB = F + pool, *ud = F + 2 * pool;
     float *nuA = F + 3 * pool, *nuB = F + 4 * pool, *nud = F + 5 * pool, *gp = F + 6 * pool;
     CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
+    // Checkpoints are staged back as halo tiles: their padding columns, which
+    // no kernel writes, must read as zero.
+    CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
     if ((rc = run_forward(ctx, uA, uB, ud, nullptr, (float *)ctx->ck.p, K, st))) return rc;
     if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, nuA, nuB, nud, gp, d_dev, st)))
         return rc;

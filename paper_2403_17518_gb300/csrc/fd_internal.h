@@ -2,6 +2,7 @@
 // finite-difference kernels (fd_kernels.cu).  Not part of the C ABI.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type only; maps are encoded in api.cu)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -50,16 +51,27 @@ struct StepCommon {
     const ShotDesc *shots;
     const Tile *tiles;
     const TileRec *recs;
-    // Padded model arrays [NZ][pf]; kap, g2v and dkap hold four copies
-    // (mstride floats apart): copy r is copy 0 shifted left by r columns.
+    // Padded model arrays [NZ][pf]; kap and dkap hold four copies (mstride
+    // floats apart): copy r is copy 0 shifted left by r columns.
     const float *kap;     // kappa = v^2 dt^2/h^2
-    const float *vpad;    // velocity (one copy)
-    const float *g2v;     // 2 / v (imaging-condition factor)
     long long mstride;    // floats between consecutive copies
     const float *wav;     // wavelets
     int pf;               // pitch of the padded model arrays
     int NZ;               // padded rows = nz + 2 nb
     int nb;
+    unsigned *tflag;      // set to 1 by a TMA-staged kernel whose bounded wait ran out
+};
+
+// Tensor maps of one TMA-staged step launch (kernel parameters).  A field
+// pool is a 3-D float array [slot][NZ][pitch] (x = column, y = row, z =
+// slot), a model array [copy][NZ][pf] (z = copy).  Halo maps have a
+// (TX + 8) x (TZ + 8) box, cell maps TX x TZ; elements outside the array read
+// as zero.  Slot use per kind:
+//   forward: 0 u^n (halo), 1 D^n, 2 kappa
+//   adjoint: 0 nu^{k+1} (halo), 1 D_nu, 2 kappa, 3 a^{k-1}, 4 image
+//   Born:    0 u0^n (halo), 1 p^n (halo), 2 D_u0, 3 D_p, 4 kappa, 5 d kappa
+struct TileMaps {
+    CUtensorMap m[6];
 };
 
 // Every propagated field is kept in "summed" form: the field u^n and its
@@ -78,7 +90,7 @@ struct FwdArgs {
     float *dd;        // pool: D^n, overwritten with D^{n+1}
     float *ck_u;      // nullable: store u^n here (checkpoint)
     float *ck_d;      // nullable: store D^n here (checkpoint)
-    float *a_out;     // nullable: store (2/v) a^n, a^n = D u^n + q^n (segment buffer slot)
+    float *a_out;     // nullable: store a^n = D u^n + q^n (segment buffer slot)
     float *d;         // nullable: packed records, sample n written from u^{n+1}
     int n;
 };
@@ -92,8 +104,8 @@ struct AdjArgs {
     float *nun;           // pool: nu^k (written)
     float *dd;            // pool: D_nu^{k+1}, overwritten with D_nu^k
     const float *r;       // packed data injected at the receivers (sample k-1)
-    const float *a;       // pool: (2/v) a^{k-1} of the background forward field
-    float *g;             // pool: per-shot image accumulator, += (2/v) a^{k-1} nu^k
+    const float *a;       // pool: a^{k-1} of the background forward field
+    float *g;             // pool: per-shot image accumulator, += a^{k-1} nu^k
     int k;
 };
 
@@ -107,12 +119,24 @@ struct BornArgs {
     int n;
 };
 
-// Step-kernel variants: rows per thread (2, 4 or 8; CTA = 32 x 64/R
-// threads).  The autotuner in api.cu times them per geometry.
-constexpr int N_STEP_VARIANTS = 3;
+// Step-kernel variants.  Variants 0-2: tiles staged by per-thread cp.async,
+// R = 2, 4, 8 rows per thread (CTA = 32 x 64/R threads).  Variants 3-5:
+// tiles staged by TMA (cp.async.bulk.tensor issued by one thread, mbarrier
+// completion), R = 4, 8, 16; the adjoint and Born kernels stop at R = 8
+// (step_variants()).  The autotuner in api.cu times them per geometry.
+constexpr int N_STEP_VARIANTS = 6;
+constexpr int FIRST_TMA_VARIANT = 3;
 int step_variant_rows(int v);
+// Variants available for a kernel kind (0 forward, 1 adjoint, 2 Born).
+int step_variants(int kind);
 // Resident CTAs per SM of a step kernel; kind 0 forward, 1 adjoint, 2 Born.
 int step_occupancy(int kind, int variant, int store_a);
+
+// TMA-staged step kernels (fd_tma.cu); variant >= FIRST_TMA_VARIANT.
+void launch_fwd_step_tma(const FwdArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s);
+void launch_adj_step_tma(const AdjArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s);
+void launch_born_step_tma(const BornArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s);
+int tma_occupancy(int kind, int variant);
 
 struct StepLaunch {
     int variant = 1;     // index into the variant table
@@ -120,17 +144,18 @@ struct StepLaunch {
 };
 
 // Persistent launches: grid = min(ntiles, max_ctas); each CTA walks the tile
-// list with a stride of gridDim.x.
-void launch_fwd_step(const FwdArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s);
-void launch_adj_step(const AdjArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s);
-void launch_born_step(const BornArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s);
+// list with a stride of gridDim.x.  maps: the launch's tensor maps, required
+// by the TMA variants, ignored (may be null) by the others.
+void launch_fwd_step(const FwdArgs &a, int ntiles, const StepLaunch &L, const TileMaps *maps, cudaStream_t s);
+void launch_adj_step(const AdjArgs &a, int ntiles, const StepLaunch &L, const TileMaps *maps, cudaStream_t s);
+void launch_born_step(const BornArgs &a, int ntiles, const StepLaunch &L, const TileMaps *maps, cudaStream_t s);
 
-// Padded model preparation: kap, vpad (and dkap when dv != nullptr) from the
+// Padded model preparation: kap (and dkap when dv != nullptr) from the
 // physical [nz][nx] model, columns [0, pf) (clamped beyond the model); also
 // checks v (finite, > 0) and records max kappa.
 // status[0] |= 1 for a bad velocity; status[1] = bits of max kappa (float).
 void launch_prep_model(const float *v, const float *dv, int rel, int nz, int nx, int nb, double c,
-                       float *kap, float *vpad, float *g2v, float *dkap, int pf, long long mstride,
+                       float *kap, float *dkap, int pf, long long mstride,
                        unsigned *status, cudaStream_t s);
 
 // r = d_syn - d_obs, and per-block partial sums of r^2 (double).
@@ -144,7 +169,8 @@ void launch_update_model(const float *v, const float *dir, int nz, int nx, int m
 
 // Sum of the per-shot image accumulators into the physical [nz][nx] grid,
 // folding the sponge cells onto the edge cells they copy (transpose of the
-// extension), shots in original order; rel != 0 multiplies by v.
+// extension), shots in original order, times the imaging factor 2/v (rel !=
+// 0: times v as well, i.e. times 2).
 void launch_reduce_image(const ShotDesc *shots, const int *slot_of_shot, int n_shots,
                          const float *gpool, int nz, int nx, int nb, const float *v, int rel,
                          float *out, cudaStream_t s);

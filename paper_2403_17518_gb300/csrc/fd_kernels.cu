@@ -19,26 +19,18 @@
 // Adjoint: the exact transpose of the recurrence, written for the scaled
 // field nu = kappa w lambda, obeys the same recurrence with the data injected
 // where the source is, and gives the velocity gradient (Eq. 13 with the sign
-// of dJ/dv) as sum_k (2/v) a^{k-1} nu^k.
+// of dJ/dv) as (2/v) sum_k a^{k-1} nu^k: the step kernels accumulate the sum,
+// the image reduction applies 2/v.
 //
 // Born (Section 2.2 Eqs. 9-11, solved jointly): the tangent of the recurrence
 // in v, secondary source w dkappa a0^n with dkappa = 2 kappa dv / v.
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "fd_device.cuh"
 #include "fd_internal.h"
 
 namespace dhfwi {
-
-// 8th-order central second-difference weights for unit spacing (c0 is
-// implied by c0 = -2 (c1 + c2 + c3 + c4)).
-#define FD_C1 (8.0f / 5.0f)
-#define FD_C2 (-1.0f / 5.0f)
-#define FD_C3 (8.0f / 315.0f)
-#define FD_C4 (-1.0f / 560.0f)
-
-typedef float STile[SROWS][SROW];
-typedef float CTile[TZ][TX];
 
 // ---------------------------------------------------------------------------
 // Asynchronous global -> shared copies (16 bytes, zero-filled past src_bytes)
@@ -89,99 +81,6 @@ __device__ __forceinline__ void issue_cell_tile(CTile &s, const float *__restric
     }
 }
 
-// ---------------------------------------------------------------------------
-// Packed two-lane FP32 arithmetic (sm_100+ add/sub/mul/fma .f32x2): lane 0 is
-// the low word (float2.x).  Each lane is rounded exactly like the scalar op.
-// ---------------------------------------------------------------------------
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 pk(float2 a) { return *reinterpret_cast<f2 *>(&a); }
-__device__ __forceinline__ float2 upk(f2 a) { return *reinterpret_cast<float2 *>(&a); }
-__device__ __forceinline__ f2 pk2(float lo, float hi) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// Difference-form D u for the two cells (row lzr, columns lxp, lxp+1) of a
-// thread, both lanes at once.  zc holds the two columns for rows lzr-4 ..
-// lzr+4 (index 4 = the cells).
-__device__ __forceinline__ f2 lap8x2(const STile &s, const float2 *zc, int lzr, int lxp) {
-    // Row segment: columns lxp .. lxp+9 (the cells sit at lxp+4, lxp+5).
-    const float2 *rp = reinterpret_cast<const float2 *>(&s[lzr + HALO][lxp]);
-    const float2 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4];
-    // r0=(x-4,x-3) r1=(x-2,x-1) r2=(x,x+1) r3=(x+2,x+3) r4=(x+4,x+5), x = lxp+4
-    const f2 u = pk(r2);
-    const f2 m4 = pk(r0), p4 = pk(r4);
-    const f2 m3 = pk2(r0.y, r1.x), p3 = pk2(r3.y, r4.x);
-    const f2 m2 = pk(r1), p2 = pk(r3);
-    const f2 m1 = pk2(r1.y, r2.x), p1 = pk2(r2.y, r3.x);
-    const f2 c1 = pk2(FD_C1, FD_C1), c2 = pk2(FD_C2, FD_C2), c3 = pk2(FD_C3, FD_C3), c4 = pk2(FD_C4, FD_C4);
-    f2 a = mul2(c4, add2(add2(sub2(p4, u), sub2(m4, u)), add2(sub2(pk(zc[8]), u), sub2(pk(zc[0]), u))));
-    a = fma2(c3, add2(add2(sub2(p3, u), sub2(m3, u)), add2(sub2(pk(zc[7]), u), sub2(pk(zc[1]), u))), a);
-    a = fma2(c2, add2(add2(sub2(p2, u), sub2(m2, u)), add2(sub2(pk(zc[6]), u), sub2(pk(zc[2]), u))), a);
-    a = fma2(c1, add2(add2(sub2(p1, u), sub2(m1, u)), add2(sub2(pk(zc[5]), u), sub2(pk(zc[3]), u))), a);
-    return a;
-}
-
-// Source injection into lane 0 / 1 of a when the cell is the source node.
-__device__ __forceinline__ f2 inject(f2 a, int i, int j, int sz, int sx, float q) {
-    if (i == sz && (j == sx || j + 1 == sx)) {
-        float2 v = upk(a);
-        if (j == sx) v.x += q;
-        else v.y += q;
-        a = pk(v);
-    }
-    return a;
-}
-
-// Cerjan sponge factor along one axis: exp(-(0.015 (nb - d))^2), d = cells
-// from the outer edge; 1 inside.
-__device__ __forceinline__ float sponge1(int i, int N, int nb) {
-    const int d = min(i, N - 1 - i);
-    const int p = nb - d;
-    return p > 0 ? expf(-2.25e-4f * (float)(p * p)) : 1.0f;
-}
-
-template <int NT>
-__device__ __forceinline__ void sample_receivers(const STile &so, const Tile &t, const Tile &tn,
-                                                 const TileRec *__restrict__ recs, const ShotDesc &sd,
-                                                 float *__restrict__ d, int n) {
-    const int tid = threadIdx.x + threadIdx.y * 32;
-    for (int e = t.rec_begin + tid; e < tn.rec_begin; e += NT) {
-        const TileRec tr = recs[e];
-        d[sd.doff + (long long)n * sd.nrec + tr.r] = so[tr.cell / TX + HALO][tr.cell % TX + HALO];
-    }
-}
-
-// Model arrays are stored as 4 copies, copy r shifted left by r columns, so
-// the model row of a window starting at model column x0 is 16-byte aligned in
-// copy (x0 & 3) at column (x0 & ~3).
-__device__ __forceinline__ const float *model_base(const float *arr, const StepCommon &c, int x0) {
-    return arr + (long long)(x0 & 3) * c.mstride + (x0 & ~3);
-}
-
-template <typename T>
-__device__ __forceinline__ T &sm2(float *p) { return *reinterpret_cast<T *>(p); }
 
 // ---------------------------------------------------------------------------
 // Step kernels.  Persistent CTAs walk tiles blockIdx.x, blockIdx.x +
@@ -190,13 +89,7 @@ __device__ __forceinline__ T &sm2(float *p) { return *reinterpret_cast<T *>(p); 
 // one.  A warp covers the 64 columns of a tile (two per thread, float2
 // shared/global accesses); each thread owns R rows.
 // ---------------------------------------------------------------------------
-template <bool STORE_A>
 struct FwdStage {
-    STile u;
-    CTile d, k, g;  // g: 2/v, for the segment store
-};
-template <>
-struct FwdStage<false> {
     STile u;
     CTile d, k;
 };
@@ -205,19 +98,17 @@ template <int R, bool STORE_A>
 __global__ void __launch_bounds__(32 * (TZ / R), 1) fwd_step_kernel(FwdArgs A, int ntiles) {
     constexpr int NT = 32 * (TZ / R);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FwdStage<STORE_A> *st = reinterpret_cast<FwdStage<STORE_A> *>(smem_raw);
+    FwdStage *st = reinterpret_cast<FwdStage *>(smem_raw);
     const int NZ = A.c.NZ;
     const int lxp = 2 * threadIdx.x;
     const int lz0 = threadIdx.y * R;
 
-    auto issue = [&](FwdStage<STORE_A> &S, int tix) {
+    auto issue = [&](FwdStage &S, int tix) {
         const Tile t = A.c.tiles[tix];
         const ShotDesc sd = A.c.shots[t.slot];
         issue_halo_tile<NT>(S.u, A.u, sd, NZ, t.z0, t.x0);
         issue_cell_tile<NT>(S.d, A.dd + sd.foff, sd.pitch, NZ, sd.nxw, t.z0, t.x0);
         issue_cell_tile<NT>(S.k, model_base(A.c.kap, A.c, sd.x0), A.c.pf, NZ, sd.nxw, t.z0, t.x0);
-        if constexpr (STORE_A)
-            issue_cell_tile<NT>(S.g, model_base(A.c.g2v, A.c, sd.x0), A.c.pf, NZ, sd.nxw, t.z0, t.x0);
     };
 
     int k = 0;
@@ -228,13 +119,13 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) fwd_step_kernel(FwdArgs A, i
         cp_async_commit();
         cp_async_wait_prev();
         __syncthreads();
-        FwdStage<STORE_A> &S = st[k];
+        FwdStage &S = st[k];
         const Tile t = A.c.tiles[tix];
         const ShotDesc sd = A.c.shots[t.slot];
         const int j = t.x0 + lxp;
         const int i0 = t.z0 + lz0;
         const int nrow = min(R, NZ - i0);
-        const bool ok = j < sd.nxw;
+        const bool ok = j < sd.nxw, hi = j + 1 < sd.nxw;
         const float q = A.c.wav[sd.wav_off + A.n];
         const float wx0 = sponge1(j, sd.nxw, A.c.nb), wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
         float2 zc[R + 2 * HALO];
@@ -253,8 +144,8 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) fwd_step_kernel(FwdArgs A, i
                 const f2 u = pk(zc[rr + HALO]);
                 const f2 dv = pk(sm2<float2>(&S.d[lz0 + rr][lxp]));
                 const f2 kv = pk(sm2<float2>(&S.k[lz0 + rr][lxp]));
-                const f2 dn = mul2(w, fma2(kv, a, dv));
-                const f2 un = fma2(w, u, dn);
+                const f2 dn = keep_lo(mul2(w, fma2(kv, a, dv)), hi);
+                const f2 un = keep_lo(fma2(w, u, dn), hi);
                 const long long c = cbase + (long long)rr * sd.pitch;
                 *reinterpret_cast<f2 *>(A.dd + c) = dn;
                 *reinterpret_cast<f2 *>(A.un + c) = un;
@@ -262,10 +153,7 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) fwd_step_kernel(FwdArgs A, i
                     *reinterpret_cast<f2 *>(A.ck_u + c) = u;
                     *reinterpret_cast<f2 *>(A.ck_d + c) = dv;
                 }
-                if constexpr (STORE_A) {
-                    const f2 gv = pk(sm2<float2>(&S.g[lz0 + rr][lxp]));
-                    *reinterpret_cast<f2 *>(A.a_out + c) = mul2(gv, a);
-                }
+                if constexpr (STORE_A) *reinterpret_cast<f2 *>(A.a_out + c) = keep_lo(a, hi);
                 out[rr] = upk(un);
             }
         }
@@ -333,7 +221,7 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) adj_step_kernel(AdjArgs A, i
         const int j = t.x0 + lxp;
         const int i0 = t.z0 + lz0;
         const int nrow = min(R, NZ - i0);
-        const bool ok = j < sd.nxw;
+        const bool ok = j < sd.nxw, hi = j + 1 < sd.nxw;
         const float wx0 = sponge1(j, sd.nxw, A.c.nb), wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
         float2 zc[R + 2 * HALO];
 #pragma unroll
@@ -352,12 +240,12 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) adj_step_kernel(AdjArgs A, i
                 const f2 kv = pk(sm2<float2>(&S.k[lz0 + rr][lxp]));
                 const f2 av = pk(sm2<float2>(&S.a[lz0 + rr][lxp]));
                 const f2 gv = pk(sm2<float2>(&S.g[lz0 + rr][lxp]));
-                const f2 dn = mul2(w, fma2(kv, a, dv));
-                const f2 nn = fma2(w, nu, dn);
+                const f2 dn = keep_lo(mul2(w, fma2(kv, a, dv)), hi);
+                const f2 nn = keep_lo(fma2(w, nu, dn), hi);
                 const long long c = cbase + (long long)rr * sd.pitch;
                 *reinterpret_cast<f2 *>(A.dd + c) = dn;
                 *reinterpret_cast<f2 *>(A.nun + c) = nn;
-                *reinterpret_cast<f2 *>(A.g + c) = fma2(av, nn, gv);
+                *reinterpret_cast<f2 *>(A.g + c) = keep_lo(fma2(av, nn, gv), hi);
             }
         }
         __syncthreads();
@@ -404,7 +292,7 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) born_step_kernel(BornArgs A,
         const int j = t.x0 + lxp;
         const int i0 = t.z0 + lz0;
         const int nrow = min(R, NZ - i0);
-        const bool ok = j < sd.nxw;
+        const bool ok = j < sd.nxw, hi = j + 1 < sd.nxw;
         const float q = A.c.wav[sd.wav_off + A.n];
         const float wx0 = sponge1(j, sd.nxw, A.c.nb), wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
         float2 zu[R + 2 * HALO], zp[R + 2 * HALO];
@@ -428,13 +316,13 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) born_step_kernel(BornArgs A,
                 const f2 dpv = pk(sm2<float2>(&S.dp[lz0 + rr][lxp]));
                 const f2 kv = pk(sm2<float2>(&S.k[lz0 + rr][lxp]));
                 const f2 dkv = pk(sm2<float2>(&S.dk[lz0 + rr][lxp]));
-                const f2 du = mul2(w, fma2(kv, a0, duv));
-                const f2 dp = mul2(w, fma2(dkv, a0, fma2(kv, ap, dpv)));
-                const f2 pn = fma2(w, pk(zp[rr + HALO]), dp);
+                const f2 du = keep_lo(mul2(w, fma2(kv, a0, duv)), hi);
+                const f2 dp = keep_lo(mul2(w, fma2(dkv, a0, fma2(kv, ap, dpv))), hi);
+                const f2 pn = keep_lo(fma2(w, pk(zp[rr + HALO]), dp), hi);
                 const long long c = cbase + (long long)rr * sd.pitch;
                 *reinterpret_cast<f2 *>(A.du + c) = du;
                 *reinterpret_cast<f2 *>(A.dp + c) = dp;
-                *reinterpret_cast<f2 *>(A.un + c) = fma2(w, pk(zu[rr + HALO]), du);
+                *reinterpret_cast<f2 *>(A.un + c) = keep_lo(fma2(w, pk(zu[rr + HALO]), du), hi);
                 *reinterpret_cast<f2 *>(A.pn + c) = pn;
                 out[rr] = upk(pn);
             }
@@ -456,19 +344,18 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) born_step_kernel(BornArgs A,
 // Variants (rows per thread) and their launchers.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kRows[N_STEP_VARIANTS] = {2, 4, 8};
+constexpr int kRows[N_STEP_VARIANTS] = {2, 4, 8, 4, 8, 16};
 
-template <int R, bool SA>
-constexpr size_t fwd_smem() { return 2 * sizeof(FwdStage<SA>); }
+constexpr size_t fwd_smem() { return 2 * sizeof(FwdStage); }
 constexpr size_t adj_smem() { return 2 * sizeof(AdjStage) + sizeof(CTile); }
 constexpr size_t born_smem() { return 2 * sizeof(BornStage); }
 
 template <int R>
 void fwd_launch(const FwdArgs &a, int ntiles, int grid, cudaStream_t s) {
     if (a.a_out)
-        fwd_step_kernel<R, true><<<grid, dim3(32, TZ / R), fwd_smem<R, true>(), s>>>(a, ntiles);
+        fwd_step_kernel<R, true><<<grid, dim3(32, TZ / R), fwd_smem(), s>>>(a, ntiles);
     else
-        fwd_step_kernel<R, false><<<grid, dim3(32, TZ / R), fwd_smem<R, false>(), s>>>(a, ntiles);
+        fwd_step_kernel<R, false><<<grid, dim3(32, TZ / R), fwd_smem(), s>>>(a, ntiles);
 }
 template <int R>
 void adj_launch(const AdjArgs &a, int ntiles, int grid, cudaStream_t s) {
@@ -494,7 +381,7 @@ int occ_of(int kind, int store_a) {
     size_t sm;
     if (kind == 0) {
         fn = store_a ? (const void *)fwd_step_kernel<R, true> : (const void *)fwd_step_kernel<R, false>;
-        sm = store_a ? fwd_smem<R, true>() : fwd_smem<R, false>();
+        sm = store_a ? fwd_smem() : fwd_smem();
     } else if (kind == 1) {
         fn = (const void *)adj_step_kernel<R>;
         sm = adj_smem();
@@ -510,7 +397,10 @@ int occ_of(int kind, int store_a) {
 
 int step_variant_rows(int v) { return kRows[v]; }
 
+int step_variants(int kind) { return kind == 0 ? N_STEP_VARIANTS : N_STEP_VARIANTS - 1; }
+
 int step_occupancy(int kind, int variant, int store_a) {
+    if (variant >= FIRST_TMA_VARIANT) return tma_occupancy(kind, variant);
     switch (variant) {
     case 0: return occ_of<2>(kind, store_a);
     case 1: return occ_of<4>(kind, store_a);
@@ -518,19 +408,31 @@ int step_occupancy(int kind, int variant, int store_a) {
     }
 }
 
-void launch_fwd_step(const FwdArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s) {
+void launch_fwd_step(const FwdArgs &a, int ntiles, const StepLaunch &L, const TileMaps *maps, cudaStream_t s) {
     if (ntiles <= 0) return;
     const int grid = ntiles < L.max_ctas ? ntiles : L.max_ctas;
+    if (L.variant >= FIRST_TMA_VARIANT) {
+        launch_fwd_step_tma(a, ntiles, L.variant, grid, *maps, s);
+        return;
+    }
     DHFWI_DISPATCH(fwd_launch, L.variant, a, ntiles, grid, s);
 }
-void launch_adj_step(const AdjArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s) {
+void launch_adj_step(const AdjArgs &a, int ntiles, const StepLaunch &L, const TileMaps *maps, cudaStream_t s) {
     if (ntiles <= 0) return;
     const int grid = ntiles < L.max_ctas ? ntiles : L.max_ctas;
+    if (L.variant >= FIRST_TMA_VARIANT) {
+        launch_adj_step_tma(a, ntiles, L.variant, grid, *maps, s);
+        return;
+    }
     DHFWI_DISPATCH(adj_launch, L.variant, a, ntiles, grid, s);
 }
-void launch_born_step(const BornArgs &a, int ntiles, const StepLaunch &L, cudaStream_t s) {
+void launch_born_step(const BornArgs &a, int ntiles, const StepLaunch &L, const TileMaps *maps, cudaStream_t s) {
     if (ntiles <= 0) return;
     const int grid = ntiles < L.max_ctas ? ntiles : L.max_ctas;
+    if (L.variant >= FIRST_TMA_VARIANT) {
+        launch_born_step_tma(a, ntiles, L.variant, grid, *maps, s);
+        return;
+    }
     DHFWI_DISPATCH(born_launch, L.variant, a, ntiles, grid, s);
 }
 
@@ -538,8 +440,8 @@ void launch_born_step(const BornArgs &a, int ntiles, const StepLaunch &L, cudaSt
 // Model preparation
 // ---------------------------------------------------------------------------
 __global__ void prep_model_kernel(const float *__restrict__ v, const float *__restrict__ dv, int rel,
-                                  int nz, int nx, int nb, double c, float *kap, float *vpad,
-                                  float *g2v, float *dkap, int pf, long long mstride, unsigned *status) {
+                                  int nz, int nx, int nb, double c, float *kap, float *dkap, int pf,
+                                  long long mstride, unsigned *status) {
     const int NZ = nz + 2 * nb, NXF = nx + 2 * nb;
     const int pc = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
@@ -558,8 +460,6 @@ __global__ void prep_model_kernel(const float *__restrict__ v, const float *__re
             const float k = (float)((double)vv * (double)vv * c);
             const long long o = copy * mstride + (long long)i * pf + pc;
             kap[o] = k;
-            g2v[o] = (float)(2.0 / (double)vv);
-            if (copy == 0) vpad[(long long)i * pf + pc] = vv;
             if (dkap) {
                 const float dd = dv[(long long)iz * nx + ix];
                 bad = bad || (inside && !isfinite(dd));
@@ -581,12 +481,10 @@ __global__ void prep_model_kernel(const float *__restrict__ v, const float *__re
 }
 
 void launch_prep_model(const float *v, const float *dv, int rel, int nz, int nx, int nb, double c,
-                       float *kap, float *vpad, float *g2v, float *dkap, int pf, long long mstride,
-                       unsigned *status, cudaStream_t s) {
+                       float *kap, float *dkap, int pf, long long mstride, unsigned *status, cudaStream_t s) {
     const int NZ = nz + 2 * nb;
     dim3 grid((pf + 127) / 128, NZ);
-    prep_model_kernel<<<grid, 128, 0, s>>>(v, dv, rel, nz, nx, nb, c, kap, vpad, g2v, dkap, pf, mstride,
-                                           status);
+    prep_model_kernel<<<grid, 128, 0, s>>>(v, dv, rel, nz, nx, nb, c, kap, dkap, pf, mstride, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -675,8 +573,11 @@ __global__ void reduce_image_kernel(const ShotDesc *__restrict__ shots, const in
         for (int i = i_lo; i <= i_hi; i++)
             for (int j = j_lo; j <= j_hi; j++) acc += g[(long long)i * sd.pitch + j];
     }
-    if (rel) acc *= v[(long long)iz * nx + ix];
-    out[(long long)iz * nx + ix] = acc;
+    // The imaging factor 2/v is constant in time and equal on the sponge
+    // cells folded here (they copy this cell's velocity), so it is applied
+    // once; for the relative perturbation v dJ/dv it cancels to 2.
+    const float vv = v[(long long)iz * nx + ix];
+    out[(long long)iz * nx + ix] = rel ? 2.0f * acc : acc * (float)(2.0 / (double)vv);
 }
 
 void launch_reduce_image(const ShotDesc *shots, const int *slot_of_shot, int n_shots,

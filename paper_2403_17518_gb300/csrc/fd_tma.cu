@@ -1,0 +1,546 @@
+// TMA-staged step kernels for sm_103a: forward, adjoint and Born.  Each has
+// the arithmetic of its cp.async counterpart in fd_kernels.cu (Section 2.1
+// Eq. 1 in summed form with the difference-form Laplacian, the adjoint for
+// Eq. 13, the Born system of Section 2.2), in the same order, so every
+// variant gives bit-identical results.  What differs is how the tiles reach
+// shared memory: one thread issues a few cp.async.bulk.tensor loads per tile
+// (fields with their halo, state differences, kappa, ...) that complete on
+// an mbarrier, instead of every thread computing and issuing ~13 cp.async
+// chunks.  Out-of-range rows and columns read as zero from the tensor map,
+// which requires the padding columns of a pool (past a window's width) to
+// hold zero: every step kernel writes them as zero (keep_lo), and the host
+// zeroes pools and checkpoints before a pass.
+//
+// Tiles fully inside the sponge-free interior (and, where there is one, away
+// from the source) take a path with no sponge factor, no bounds masks and no
+// injection test; the sponge factor there is exactly 1, so both paths round
+// identically.  Receivers are sampled from the pool after the tile's stores.
+//
+// Pipeline: two stages; at tile i every thread waits for stage i mod 2, a
+// barrier then certifies that all threads are done with tile i-1, and the
+// leader issues tile i+1 into the freed stage.  Waits are bounded: a tile
+// whose copies have not landed after about one second makes the whole CTA
+// leave the kernel after setting *tflag = 1 (2: a misaligned shared-memory
+// base, checked before any copy), which the host reports as
+// DHFWI_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "fd_device.cuh"
+#include "fd_internal.h"
+
+namespace dhfwi {
+namespace {
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// its later async-proxy (TMA) ones.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the phase of the given parity to complete; false after ~1 s.
+__device__ __noinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; i++)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+// 3-D tiled tensor load into shared memory, completing on bar.  x (the
+// column) is always a multiple of 4 floats (16 bytes).
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int x, int y, int z, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+struct TmaFwdStage {
+    STile u;
+    CTile d, k;
+};
+constexpr unsigned kFwdStageBytes = sizeof(STile) + 2 * sizeof(CTile);
+static_assert(sizeof(TmaFwdStage) == kFwdStageBytes, "stage layout");
+static_assert(sizeof(STile) % 128 == 0 && sizeof(CTile) % 128 == 0, "TMA destinations stay 128-byte aligned");
+constexpr size_t kFwdSmem = 2 * sizeof(TmaFwdStage) + 16;
+
+// R rows x 2 columns of one tile for this thread.  FULL: the tile lies in
+// the sponge-free interior, holds no source and needs no bounds masks.
+template <int R, bool STORE_A, bool FULL>
+__device__ __forceinline__ void fwd_rows(const FwdArgs &A, const TmaFwdStage &S, const Tile &t, const ShotDesc &sd,
+                                         int lxp, int lz0) {
+    const int NZ = A.c.NZ;
+    const int j = t.x0 + lxp;
+    const int i0 = t.z0 + lz0;
+    float2 zc[R + 2 * HALO];
+#pragma unroll
+    for (int r = 0; r < R + 2 * HALO; r++)
+        zc[r] = *reinterpret_cast<const float2 *>(&S.u[lz0 + r][lxp + HALO]);
+    const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+    if constexpr (FULL) {
+#pragma unroll
+        for (int rr = 0; rr < R; rr++) {
+            const f2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
+            const f2 u = pk(zc[rr + HALO]);
+            const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[lz0 + rr][lxp]));
+            const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr][lxp]));
+            const f2 dn = fma2(kv, a, dv);
+            const long long c = cbase + (long long)rr * sd.pitch;
+            *reinterpret_cast<f2 *>(A.dd + c) = dn;
+            *reinterpret_cast<f2 *>(A.un + c) = add2(u, dn);
+            if (!STORE_A && A.ck_u) {
+                *reinterpret_cast<f2 *>(A.ck_u + c) = u;
+                *reinterpret_cast<f2 *>(A.ck_d + c) = dv;
+            }
+            if constexpr (STORE_A) *reinterpret_cast<f2 *>(A.a_out + c) = a;
+        }
+    } else {
+        const int nrow = min(R, NZ - i0);
+        const bool ok = j < sd.nxw, hi = j + 1 < sd.nxw;
+        const float q = A.c.wav[sd.wav_off + A.n];
+        const float wx0 = sponge1(j, sd.nxw, A.c.nb), wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
+#pragma unroll
+        for (int rr = 0; rr < R; rr++) {
+            if (ok && rr < nrow) {
+                const int i = i0 + rr;
+                const f2 a = inject(lap8x2(S.u, zc + rr, lz0 + rr, lxp), i, j, sd.sz, sd.sx, q);
+                const float wz = sponge1(i, NZ, A.c.nb);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                const f2 u = pk(zc[rr + HALO]);
+                const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[lz0 + rr][lxp]));
+                const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr][lxp]));
+                const f2 dn = keep_lo(mul2(w, fma2(kv, a, dv)), hi);
+                const long long c = cbase + (long long)rr * sd.pitch;
+                *reinterpret_cast<f2 *>(A.dd + c) = dn;
+                *reinterpret_cast<f2 *>(A.un + c) = keep_lo(fma2(w, u, dn), hi);
+                if (!STORE_A && A.ck_u) {
+                    *reinterpret_cast<f2 *>(A.ck_u + c) = keep_lo(u, hi);
+                    *reinterpret_cast<f2 *>(A.ck_d + c) = keep_lo(dv, hi);
+                }
+                if constexpr (STORE_A) *reinterpret_cast<f2 *>(A.a_out + c) = keep_lo(a, hi);
+            }
+        }
+    }
+}
+
+template <int R, bool STORE_A>
+__global__ void __launch_bounds__(32 * (TZ / R), 1)
+    fwd_tma_kernel(FwdArgs A, const __grid_constant__ TileMaps M, int ntiles) {
+    constexpr int NT = 32 * (TZ / R);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaFwdStage *st = reinterpret_cast<TmaFwdStage *>(smem_raw);
+    const unsigned bar0 = smem_u32(smem_raw + 2 * sizeof(TmaFwdStage));
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const int NZ = A.c.NZ, nb = A.c.nb;
+    const int lxp = 2 * threadIdx.x;
+    const int lz0 = threadIdx.y * R;
+
+    // TMA destinations must be 128-byte aligned; the stage offsets are, so
+    // only the base is checked (uniform: the whole CTA leaves together).
+    if (smem_u32(smem_raw) & 127u) {
+        if (leader) atomicExch(A.c.tflag, 2u);
+        return;
+    }
+    if (leader) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // Leader only: stage s receives tile tix.
+    auto issue = [&](int s, int tix) {
+        const Tile t = A.c.tiles[tix];
+        const int x0 = A.c.shots[t.slot].x0;
+        const unsigned b = bar0 + 8 * s;
+        fence_proxy_async();
+        mbar_expect_tx(b, kFwdStageBytes);
+        tma_load_3d(smem_u32(&st[s].u), &M.m[0], t.x0 - HALO, t.z0 - HALO, t.slot, b);
+        tma_load_3d(smem_u32(&st[s].d), &M.m[1], t.x0, t.z0, t.slot, b);
+        tma_load_3d(smem_u32(&st[s].k), &M.m[2], (x0 & ~3) + t.x0, t.z0, x0 & 3, b);
+    };
+
+    if (leader && (int)blockIdx.x < ntiles) issue(0, blockIdx.x);
+    unsigned phase = 0;
+    int k = 0;
+    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
+        const bool landed = mbar_wait(bar0 + 8 * k, (phase >> k) & 1u);
+        phase ^= 1u << k;
+        // Every thread has finished the previous tile here, so the other
+        // stage is free; a timeout is decided for the whole CTA at once.
+        if (__syncthreads_or(!landed)) {
+            if (leader) atomicExch(A.c.tflag, 1u);
+            return;
+        }
+        if (leader && tix + (int)gridDim.x < ntiles) issue(k ^ 1, tix + gridDim.x);
+        const Tile t = A.c.tiles[tix];
+        const ShotDesc sd = A.c.shots[t.slot];
+        const bool src_here = sd.sz >= t.z0 && sd.sz < t.z0 + TZ && sd.sx >= t.x0 && sd.sx < t.x0 + TX;
+        const bool full = t.z0 >= nb && t.z0 + TZ <= NZ - nb && t.x0 >= nb && t.x0 + TX <= sd.nxw - nb && !src_here;
+        if (full) fwd_rows<R, STORE_A, true>(A, st[k], t, sd, lxp, lz0);
+        else fwd_rows<R, STORE_A, false>(A, st[k], t, sd, lxp, lz0);
+        if (!STORE_A && A.d) {
+            const int rb = A.c.tiles[tix + 1].rec_begin;
+            if (rb > t.rec_begin) {
+                // Receivers read u^{n+1} back from the pool: this CTA's
+                // stores are visible to it after the barrier.
+                __syncthreads();
+                const int tid = threadIdx.x + threadIdx.y * 32;
+                for (int e = t.rec_begin + tid; e < rb; e += NT) {
+                    const TileRec tr = A.c.recs[e];
+                    const long long c = sd.foff + (long long)(t.z0 + tr.cell / TX) * sd.pitch + t.x0 + tr.cell % TX;
+                    A.d[sd.doff + (long long)A.n * sd.nrec + tr.r] = A.un[c];
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint step (see adj_step_kernel): nu^{k+1} with halo, D_nu, kappa and the
+// stored a^{k-1} by TMA; the image accumulator is read with plain loads
+// issued before the arithmetic (keeping two CTAs' worth of stages would not
+// fit), the receiver injection tile is built per tile with shared atomics.
+// ---------------------------------------------------------------------------
+struct TmaAdjStage {
+    STile u;
+    CTile d, k, a;
+};
+constexpr unsigned kAdjStageBytes = sizeof(STile) + 3 * sizeof(CTile);
+static_assert(sizeof(TmaAdjStage) == kAdjStageBytes, "stage layout");
+constexpr size_t kAdjSmem = 2 * sizeof(TmaAdjStage) + sizeof(CTile) + 16;
+
+template <int R, bool FULL>
+__device__ __forceinline__ void adj_rows(const AdjArgs &A, const TmaAdjStage &S, const CTile &inj, bool has_rec,
+                                         const Tile &t, const ShotDesc &sd, int lxp, int lz0) {
+    const int NZ = A.c.NZ;
+    const int j = t.x0 + lxp;
+    const int i0 = t.z0 + lz0;
+    const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+    const int nrow = FULL ? R : min(R, NZ - i0);
+    const bool ok = FULL || j < sd.nxw, hi = FULL || j + 1 < sd.nxw;
+    float2 gv[R];
+#pragma unroll
+    for (int rr = 0; rr < R; rr++)
+        gv[rr] = (ok && rr < nrow) ? *reinterpret_cast<const float2 *>(A.g + cbase + (long long)rr * sd.pitch)
+                                   : make_float2(0.f, 0.f);
+    float2 zc[R + 2 * HALO];
+#pragma unroll
+    for (int r = 0; r < R + 2 * HALO; r++)
+        zc[r] = *reinterpret_cast<const float2 *>(&S.u[lz0 + r][lxp + HALO]);
+    float wx0 = 1.f, wx1 = 1.f;
+    if constexpr (!FULL) {
+        wx0 = sponge1(j, sd.nxw, A.c.nb);
+        wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
+    }
+#pragma unroll
+    for (int rr = 0; rr < R; rr++) {
+        if (ok && rr < nrow) {
+            f2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
+            if (has_rec) a = add2(a, pk(*reinterpret_cast<const float2 *>(&inj[lz0 + rr][lxp])));
+            const f2 nu = pk(zc[rr + HALO]);
+            const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[lz0 + rr][lxp]));
+            const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr][lxp]));
+            const f2 av = pk(*reinterpret_cast<const float2 *>(&S.a[lz0 + rr][lxp]));
+            f2 dn, nn;
+            if constexpr (FULL) {
+                dn = fma2(kv, a, dv);
+                nn = add2(nu, dn);
+            } else {
+                const float wz = sponge1(i0 + rr, NZ, A.c.nb);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                dn = keep_lo(mul2(w, fma2(kv, a, dv)), hi);
+                nn = keep_lo(fma2(w, nu, dn), hi);
+            }
+            const long long c = cbase + (long long)rr * sd.pitch;
+            *reinterpret_cast<f2 *>(A.dd + c) = dn;
+            *reinterpret_cast<f2 *>(A.nun + c) = nn;
+            *reinterpret_cast<f2 *>(A.g + c) = keep_lo(fma2(av, nn, pk(gv[rr])), hi);
+        }
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * (TZ / R), 1)
+    adj_tma_kernel(AdjArgs A, const __grid_constant__ TileMaps M, int ntiles) {
+    constexpr int NT = 32 * (TZ / R);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaAdjStage *st = reinterpret_cast<TmaAdjStage *>(smem_raw);
+    CTile &inj = *reinterpret_cast<CTile *>(smem_raw + 2 * sizeof(TmaAdjStage));
+    const unsigned bar0 = smem_u32(smem_raw + 2 * sizeof(TmaAdjStage) + sizeof(CTile));
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const int tid = threadIdx.x + threadIdx.y * 32;
+    const int NZ = A.c.NZ, nb = A.c.nb;
+    const int lxp = 2 * threadIdx.x;
+    const int lz0 = threadIdx.y * R;
+    if (smem_u32(smem_raw) & 127u) {
+        if (leader) atomicExch(A.c.tflag, 2u);
+        return;
+    }
+    if (leader) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int s, int tix) {
+        const Tile t = A.c.tiles[tix];
+        const int x0 = A.c.shots[t.slot].x0;
+        const unsigned b = bar0 + 8 * s;
+        fence_proxy_async();
+        mbar_expect_tx(b, kAdjStageBytes);
+        tma_load_3d(smem_u32(&st[s].u), &M.m[0], t.x0 - HALO, t.z0 - HALO, t.slot, b);
+        tma_load_3d(smem_u32(&st[s].d), &M.m[1], t.x0, t.z0, t.slot, b);
+        tma_load_3d(smem_u32(&st[s].k), &M.m[2], (x0 & ~3) + t.x0, t.z0, x0 & 3, b);
+        tma_load_3d(smem_u32(&st[s].a), &M.m[3], t.x0, t.z0, t.slot, b);
+    };
+    if (leader && (int)blockIdx.x < ntiles) issue(0, blockIdx.x);
+    unsigned phase = 0;
+    int k = 0;
+    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
+        const bool landed = mbar_wait(bar0 + 8 * k, (phase >> k) & 1u);
+        phase ^= 1u << k;
+        if (__syncthreads_or(!landed)) {
+            if (leader) atomicExch(A.c.tflag, 1u);
+            return;
+        }
+        if (leader && tix + (int)gridDim.x < ntiles) issue(k ^ 1, tix + gridDim.x);
+        const Tile t = A.c.tiles[tix];
+        const int rb = A.c.tiles[tix + 1].rec_begin;
+        const ShotDesc sd = A.c.shots[t.slot];
+        const bool has_rec = rb > t.rec_begin;
+        if (has_rec) {
+            for (int e = tid; e < TZ * TX; e += NT) (&inj[0][0])[e] = 0.f;
+            __syncthreads();
+            const float *rk = A.r + sd.doff + (long long)(A.k - 1) * sd.nrec;
+            for (int e = t.rec_begin + tid; e < rb; e += NT) {
+                const TileRec tr = A.c.recs[e];
+                atomicAdd(&inj[tr.cell / TX][tr.cell % TX], rk[tr.r]);
+            }
+            __syncthreads();
+        }
+        const bool full = t.z0 >= nb && t.z0 + TZ <= NZ - nb && t.x0 >= nb && t.x0 + TX <= sd.nxw - nb;
+        if (full) adj_rows<R, true>(A, st[k], inj, has_rec, t, sd, lxp, lz0);
+        else adj_rows<R, false>(A, st[k], inj, has_rec, t, sd, lxp, lz0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Born joint step (see born_step_kernel): u0^n and p^n with halos, D_u0,
+// D_p, kappa and d kappa by TMA.
+// ---------------------------------------------------------------------------
+struct TmaBornStage {
+    STile u, p;
+    CTile du, dp, k, dk;
+};
+constexpr unsigned kBornStageBytes = 2 * sizeof(STile) + 4 * sizeof(CTile);
+static_assert(sizeof(TmaBornStage) == kBornStageBytes, "stage layout");
+constexpr size_t kBornSmem = 2 * sizeof(TmaBornStage) + 16;
+
+template <int R, bool FULL>
+__device__ __forceinline__ void born_rows(const BornArgs &A, const TmaBornStage &S, const Tile &t, const ShotDesc &sd,
+                                          int lxp, int lz0) {
+    const int NZ = A.c.NZ;
+    const int j = t.x0 + lxp;
+    const int i0 = t.z0 + lz0;
+    const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+    const int nrow = FULL ? R : min(R, NZ - i0);
+    const bool ok = FULL || j < sd.nxw, hi = FULL || j + 1 < sd.nxw;
+    float2 zu[R + 2 * HALO], zp[R + 2 * HALO];
+#pragma unroll
+    for (int r = 0; r < R + 2 * HALO; r++) {
+        zu[r] = *reinterpret_cast<const float2 *>(&S.u[lz0 + r][lxp + HALO]);
+        zp[r] = *reinterpret_cast<const float2 *>(&S.p[lz0 + r][lxp + HALO]);
+    }
+    float wx0 = 1.f, wx1 = 1.f, q = 0.f;
+    if constexpr (!FULL) {
+        wx0 = sponge1(j, sd.nxw, A.c.nb);
+        wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
+        q = A.c.wav[sd.wav_off + A.n];
+    }
+#pragma unroll
+    for (int rr = 0; rr < R; rr++) {
+        if (ok && rr < nrow) {
+            f2 a0 = lap8x2(S.u, zu + rr, lz0 + rr, lxp);
+            if constexpr (!FULL) a0 = inject(a0, i0 + rr, j, sd.sz, sd.sx, q);
+            const f2 ap = lap8x2(S.p, zp + rr, lz0 + rr, lxp);
+            const f2 duv = pk(*reinterpret_cast<const float2 *>(&S.du[lz0 + rr][lxp]));
+            const f2 dpv = pk(*reinterpret_cast<const float2 *>(&S.dp[lz0 + rr][lxp]));
+            const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr][lxp]));
+            const f2 dkv = pk(*reinterpret_cast<const float2 *>(&S.dk[lz0 + rr][lxp]));
+            f2 du, dp, un, pn;
+            if constexpr (FULL) {
+                du = fma2(kv, a0, duv);
+                dp = fma2(dkv, a0, fma2(kv, ap, dpv));
+                un = add2(pk(zu[rr + HALO]), du);
+                pn = add2(pk(zp[rr + HALO]), dp);
+            } else {
+                const float wz = sponge1(i0 + rr, NZ, A.c.nb);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                du = keep_lo(mul2(w, fma2(kv, a0, duv)), hi);
+                dp = keep_lo(mul2(w, fma2(dkv, a0, fma2(kv, ap, dpv))), hi);
+                un = keep_lo(fma2(w, pk(zu[rr + HALO]), du), hi);
+                pn = keep_lo(fma2(w, pk(zp[rr + HALO]), dp), hi);
+            }
+            const long long c = cbase + (long long)rr * sd.pitch;
+            *reinterpret_cast<f2 *>(A.du + c) = du;
+            *reinterpret_cast<f2 *>(A.dp + c) = dp;
+            *reinterpret_cast<f2 *>(A.un + c) = un;
+            *reinterpret_cast<f2 *>(A.pn + c) = pn;
+        }
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * (TZ / R), 1)
+    born_tma_kernel(BornArgs A, const __grid_constant__ TileMaps M, int ntiles) {
+    constexpr int NT = 32 * (TZ / R);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaBornStage *st = reinterpret_cast<TmaBornStage *>(smem_raw);
+    const unsigned bar0 = smem_u32(smem_raw + 2 * sizeof(TmaBornStage));
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const int NZ = A.c.NZ, nb = A.c.nb;
+    const int lxp = 2 * threadIdx.x;
+    const int lz0 = threadIdx.y * R;
+    if (smem_u32(smem_raw) & 127u) {
+        if (leader) atomicExch(A.c.tflag, 2u);
+        return;
+    }
+    if (leader) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int s, int tix) {
+        const Tile t = A.c.tiles[tix];
+        const int x0 = A.c.shots[t.slot].x0;
+        const unsigned b = bar0 + 8 * s;
+        fence_proxy_async();
+        mbar_expect_tx(b, kBornStageBytes);
+        tma_load_3d(smem_u32(&st[s].u), &M.m[0], t.x0 - HALO, t.z0 - HALO, t.slot, b);
+        tma_load_3d(smem_u32(&st[s].p), &M.m[1], t.x0 - HALO, t.z0 - HALO, t.slot, b);
+        tma_load_3d(smem_u32(&st[s].du), &M.m[2], t.x0, t.z0, t.slot, b);
+        tma_load_3d(smem_u32(&st[s].dp), &M.m[3], t.x0, t.z0, t.slot, b);
+        tma_load_3d(smem_u32(&st[s].k), &M.m[4], (x0 & ~3) + t.x0, t.z0, x0 & 3, b);
+        tma_load_3d(smem_u32(&st[s].dk), &M.m[5], (x0 & ~3) + t.x0, t.z0, x0 & 3, b);
+    };
+    if (leader && (int)blockIdx.x < ntiles) issue(0, blockIdx.x);
+    unsigned phase = 0;
+    int k = 0;
+    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
+        const bool landed = mbar_wait(bar0 + 8 * k, (phase >> k) & 1u);
+        phase ^= 1u << k;
+        if (__syncthreads_or(!landed)) {
+            if (leader) atomicExch(A.c.tflag, 1u);
+            return;
+        }
+        if (leader && tix + (int)gridDim.x < ntiles) issue(k ^ 1, tix + gridDim.x);
+        const Tile t = A.c.tiles[tix];
+        const ShotDesc sd = A.c.shots[t.slot];
+        const bool src_here = sd.sz >= t.z0 && sd.sz < t.z0 + TZ && sd.sx >= t.x0 && sd.sx < t.x0 + TX;
+        const bool full = t.z0 >= nb && t.z0 + TZ <= NZ - nb && t.x0 >= nb && t.x0 + TX <= sd.nxw - nb && !src_here;
+        if (full) born_rows<R, true>(A, st[k], t, sd, lxp, lz0);
+        else born_rows<R, false>(A, st[k], t, sd, lxp, lz0);
+        const int rb = A.c.tiles[tix + 1].rec_begin;
+        if (rb > t.rec_begin) {
+            __syncthreads();  // p^{n+1} of this tile is in the pool
+            const int tid = threadIdx.x + threadIdx.y * 32;
+            for (int e = t.rec_begin + tid; e < rb; e += NT) {
+                const TileRec tr = A.c.recs[e];
+                const long long c = sd.foff + (long long)(t.z0 + tr.cell / TX) * sd.pitch + t.x0 + tr.cell % TX;
+                A.d[sd.doff + (long long)A.n * sd.nrec + tr.r] = A.pn[c];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers and occupancy per variant (R = 4, 8, 16 for variants 3, 4, 5).
+// ---------------------------------------------------------------------------
+template <int R>
+void fwd_launch_r(const FwdArgs &a, int ntiles, int grid, const TileMaps &maps, cudaStream_t s) {
+    if (a.a_out)
+        fwd_tma_kernel<R, true><<<grid, dim3(32, TZ / R), kFwdSmem, s>>>(a, maps, ntiles);
+    else
+        fwd_tma_kernel<R, false><<<grid, dim3(32, TZ / R), kFwdSmem, s>>>(a, maps, ntiles);
+}
+
+int occupancy(const void *fn, int threads, size_t smem) {
+    int n = 0;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
+    return n < 1 ? 1 : n;
+}
+
+template <int R>
+int occ_r(int kind) {
+    const int nt = 32 * (TZ / R);
+    if (kind == 0) {
+        const int a = occupancy((const void *)fwd_tma_kernel<R, true>, nt, kFwdSmem);
+        const int b = occupancy((const void *)fwd_tma_kernel<R, false>, nt, kFwdSmem);
+        return a < b ? a : b;
+    }
+    if constexpr (R <= 8) {  // the adjoint and Born kernels have no R = 16 variant
+        if (kind == 1) return occupancy((const void *)adj_tma_kernel<R>, nt, kAdjSmem);
+        return occupancy((const void *)born_tma_kernel<R>, nt, kBornSmem);
+    }
+    return 1;
+}
+
+}  // namespace
+
+void launch_fwd_step_tma(const FwdArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s) {
+    switch (variant) {
+    case FIRST_TMA_VARIANT: fwd_launch_r<4>(a, ntiles, grid, maps, s); break;
+    case FIRST_TMA_VARIANT + 1: fwd_launch_r<8>(a, ntiles, grid, maps, s); break;
+    default: fwd_launch_r<16>(a, ntiles, grid, maps, s); break;
+    }
+}
+
+void launch_adj_step_tma(const AdjArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s) {
+    switch (variant) {
+    case FIRST_TMA_VARIANT: adj_tma_kernel<4><<<grid, dim3(32, TZ / 4), kAdjSmem, s>>>(a, maps, ntiles); break;
+    default: adj_tma_kernel<8><<<grid, dim3(32, TZ / 8), kAdjSmem, s>>>(a, maps, ntiles); break;
+    }
+}
+
+void launch_born_step_tma(const BornArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s) {
+    switch (variant) {
+    case FIRST_TMA_VARIANT: born_tma_kernel<4><<<grid, dim3(32, TZ / 4), kBornSmem, s>>>(a, maps, ntiles); break;
+    default: born_tma_kernel<8><<<grid, dim3(32, TZ / 8), kBornSmem, s>>>(a, maps, ntiles); break;
+    }
+}
+
+int tma_occupancy(int kind, int variant) {
+    switch (variant) {
+    case FIRST_TMA_VARIANT: return occ_r<4>(kind);
+    case FIRST_TMA_VARIANT + 1: return occ_r<8>(kind);
+    default: return kind == 0 ? occ_r<16>(0) : occ_r<8>(kind);
+    }
+}
+
+}  // namespace dhfwi

@@ -156,8 +156,6 @@ int model_shots_static(const dhfwi_grid *g, const float *v_dev, const dhfwi_geom
     const long long mstride = (long long)NZ * pf;
     Carve cv;
     const size_t o_kap = cv.take(sizeof(float) * 4 * mstride);
-    const size_t o_vpad = cv.take(sizeof(float) * mstride);
-    const size_t o_g2v = cv.take(sizeof(float) * 4 * mstride);
     const size_t o_status = cv.take(16);
     const size_t o_shots = cv.take(sizeof(ShotDesc) * shots.size());
     const size_t o_tiles = cv.take(sizeof(Tile) * tiles.size());
@@ -191,8 +189,8 @@ int model_shots_static(const dhfwi_grid *g, const float *v_dev, const dhfwi_geom
     SCK(cudaMemsetAsync(S + o_status, 0, 16, st));
     SCK(cudaMemsetAsync(S + o_u, 0, sizeof(float) * 3 * (size_t)foff, st));
     const double c = ((double)g->dt * g->dt) / ((double)g->h * g->h);
-    launch_prep_model(v_dev, nullptr, 0, g->nz, g->nx, nb, c, (float *)(S + o_kap), (float *)(S + o_vpad),
-                      (float *)(S + o_g2v), nullptr, pf, mstride, (unsigned *)(S + o_status), st);
+    launch_prep_model(v_dev, nullptr, 0, g->nz, g->nx, nb, c, (float *)(S + o_kap), nullptr, pf, mstride,
+                      (unsigned *)(S + o_status), st);
     SCK(cudaGetLastError());
     unsigned status[2] = {0, 0};
     SCK(cudaMemcpyAsync(status, S + o_status, sizeof status, cudaMemcpyDeviceToHost, st));
@@ -214,8 +212,6 @@ int model_shots_static(const dhfwi_grid *g, const float *v_dev, const dhfwi_geom
     a.c.tiles = (const Tile *)(S + o_tiles);
     a.c.recs = (const TileRec *)(S + o_recs);
     a.c.kap = (const float *)(S + o_kap);
-    a.c.vpad = (const float *)(S + o_vpad);
-    a.c.g2v = (const float *)(S + o_g2v);
     a.c.mstride = mstride;
     a.c.wav = (const float *)(S + o_wav);
     a.c.pf = pf;
@@ -232,7 +228,7 @@ int model_shots_static(const dhfwi_grid *g, const float *v_dev, const dhfwi_geom
         a.u = cur;
         a.un = nxt;
         a.n = n;
-        launch_fwd_step(a, prefix[m], L, st);
+        launch_fwd_step(a, prefix[m], L, nullptr, st);
         std::swap(cur, nxt);
     }
     SCK(cudaGetLastError());
