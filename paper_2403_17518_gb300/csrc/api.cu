@@ -37,12 +37,13 @@ struct Plan {
     std::vector<int> nt_sorted;        // nt by slot (non-increasing)
     std::vector<Tile> tiles;           // with a sentinel at the end
     std::vector<TileRec> recs;
+    std::vector<TileInfo> infos;       // per tile, same order (no sentinel)
     std::vector<int> tiles_prefix;     // tiles of the first m slots
     long long pool_floats = 0;
     int pitch = 0;                     // row pitch of every window in a pool
     long long n_data = 0;
     long long cells_per_step_all = 0;  // padded cells of all shots
-    DevBuf d_shots, d_tiles, d_recs, d_slot_of, d_wav;
+    DevBuf d_shots, d_tiles, d_recs, d_slot_of, d_wav, d_infos;
 };
 
 }  // namespace
@@ -294,6 +295,31 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
         P.tiles_prefix[k + 1] = (int)P.tiles.size();
     }
     P.tiles.push_back(Tile{0, 0, 0, (int)P.recs.size()});  // sentinel
+    P.infos.resize(P.tiles.size() - 1);
+    for (size_t i = 0; i + 1 < P.tiles.size(); i++) {
+        const Tile &t = P.tiles[i];
+        const ShotDesc &sd = P.shots[t.slot];
+        TileInfo &T = P.infos[i];
+        T = TileInfo{};
+        T.slot = t.slot;
+        T.z0 = t.z0;
+        T.x0 = t.x0;
+        T.mx = (sd.x0 & ~3) + t.x0;
+        T.mc = sd.x0 & 3;
+        T.nxw = sd.nxw;
+        T.pitch = sd.pitch;
+        T.sz = sd.sz;
+        T.sx = sd.sx;
+        T.wav_off = sd.wav_off;
+        T.nrec = sd.nrec;
+        T.rec_begin = t.rec_begin;
+        T.rec_end = P.tiles[i + 1].rec_begin;
+        T.foff = sd.foff;
+        T.doff = sd.doff;
+        const bool interior = t.z0 >= nb && t.z0 + TZ <= NZ - nb && t.x0 >= nb && t.x0 + TX <= sd.nxw - nb;
+        const bool src = sd.sz >= t.z0 && sd.sz < t.z0 + TZ && sd.sx >= t.x0 && sd.sx < t.x0 + TX;
+        T.flags = (interior ? TI_INTERIOR : 0) | (interior && !src ? TI_FULL_FWD : 0);
+    }
     P.pool_floats = foff;
     std::vector<float> wav((size_t)G->nt_max * (G->wavelet_shared ? 1 : ns));
     std::memcpy(wav.data(), G->wavelet, sizeof(float) * wav.size());
@@ -302,6 +328,7 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
     if ((rc = upload(ctx, P.d_recs, P.recs, "receiver table"))) return rc;
     if ((rc = upload(ctx, P.d_slot_of, P.slot_of_shot, "slot table"))) return rc;
     if ((rc = upload(ctx, P.d_wav, wav, "wavelets"))) return rc;
+    if ((rc = upload(ctx, P.d_infos, P.infos, "tile descriptors"))) return rc;
     P.hash = h;
     return DHFWI_OK;
 }
@@ -329,6 +356,7 @@ StepCommon common(dhfwi_ctx *ctx) {
     c.shots = (const ShotDesc *)ctx->plan.d_shots.p;
     c.tiles = (const Tile *)ctx->plan.d_tiles.p;
     c.recs = (const TileRec *)ctx->plan.d_recs.p;
+    c.infos = (const TileInfo *)ctx->plan.d_infos.p;
     c.kap = (const float *)ctx->kap.p;
     c.mstride = (long long)ctx->NZ * ctx->pf;
     c.wav = (const float *)ctx->plan.d_wav.p;
@@ -826,7 +854,7 @@ void dhfwi_destroy(dhfwi_ctx *ctx) {
     cudaSetDevice(ctx->device);
     DevBuf *bufs[] = {&ctx->kap, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
                       &ctx->ck, &ctx->abuf, &ctx->dtmp, &ctx->rtmp, &ctx->plan.d_shots, &ctx->plan.d_tiles,
-                      &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav};
+                      &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav, &ctx->plan.d_infos};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_partial) cudaFreeHost(ctx->h_partial);

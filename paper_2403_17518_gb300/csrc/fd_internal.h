@@ -41,6 +41,24 @@ struct Tile {
     int rec_begin;    // first receiver entry of this tile (entries are [rec_begin, next tile's))
 };
 
+// Per-tile descriptor of the TMA-staged kernels: the tile and the fields of
+// its shot they read, denormalised so that one 80-byte copy gives them all
+// (no dependent shot-table load on a kernel's critical path).
+enum { TI_INTERIOR = 1, TI_FULL_FWD = 2 };
+struct alignas(16) TileInfo {
+    int slot, z0, x0;
+    int mx;             // model-array column of the tile: (shot x0 & ~3) + x0, in copy mc
+    int mc;             // shot x0 & 3
+    int nxw, pitch;
+    int sz, sx;         // source node, window coordinates
+    int wav_off, nrec;
+    int rec_begin, rec_end;
+    int flags;          // TI_INTERIOR: inside the sponge-free interior (all cells valid);
+                        // TI_FULL_FWD: interior and without the source node
+    int pad0, pad1;
+    long long foff, doff;
+};
+
 // A receiver that falls inside a tile.
 struct TileRec {
     int cell;         // (lz * TX + lx) inside the tile
@@ -55,6 +73,7 @@ struct StepCommon {
     // floats apart): copy r is copy 0 shifted left by r columns.
     const float *kap;     // kappa = v^2 dt^2/h^2
     long long mstride;    // floats between consecutive copies
+    const TileInfo *infos;  // per-tile descriptors (TMA-staged kernels)
     const float *wav;     // wavelets
     int pf;               // pitch of the padded model arrays
     int NZ;               // padded rows = nz + 2 nb

@@ -68,6 +68,15 @@ __device__ __noinline__ bool mbar_wait(unsigned bar, unsigned parity) {
         if (global_ns() - t0 > 1000000000ull) return false;
     }
 }
+// Programmatic dependent launch: wait until the previous kernel in the
+// stream has completed and its writes are visible; let the next one start
+// its prologue.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // 3-D tiled tensor load into shared memory, completing on bar.  x (the
 // column) is always a multiple of 4 floats (16 bytes).
 __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int x, int y, int z, unsigned bar) {
@@ -78,6 +87,109 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map
         : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Tile pipeline shared by the three kernels.  Two stages; shared memory holds
+// the stages, then PipeTail (two mbarriers and the two stages' tile
+// descriptors).  At tile i every thread waits for stage i mod 2; a barrier
+// then certifies that all threads are done with tile i-1, and the leader
+// (thread 0) issues tile i+1 into the freed stage: the tensor loads (coordinates
+// prefetched into registers one tile earlier) and a cp.async copy of its
+// TileInfo into the stage's descriptor slot, awaited before the next barrier.
+// The tile's arithmetic then reads the descriptor from shared memory, so no
+// dependent global load sits on its critical path.
+//
+// Launched as programmatic dependents: the prologue (barrier init, first
+// descriptors: data no kernel writes) overlaps the previous step kernel, and
+// griddepcontrol.wait precedes every access to the fields.
+// ---------------------------------------------------------------------------
+struct PipeTail {
+    unsigned long long bar[2];
+    TileInfo desc[2];
+};
+static_assert(sizeof(TileInfo) == 80 && alignof(TileInfo) == 16, "TileInfo is five 16-byte chunks");
+static_assert(sizeof(PipeTail) % 16 == 0, "tail layout");
+
+__device__ __forceinline__ void fetch_coords(const TileInfo *infos, int tix, int4 &co, int &mc) {
+    co = __ldg(reinterpret_cast<const int4 *>(&infos[tix].slot));  // slot, z0, x0, mx
+    mc = __ldg(&infos[tix].mc);
+}
+__device__ __forceinline__ void copy_desc(TileInfo *dst, const TileInfo *src) {
+#pragma unroll
+    for (int q = 0; q < 5; q++) cp_async16(reinterpret_cast<int4 *>(dst) + q, reinterpret_cast<const int4 *>(src) + q);
+}
+
+// Runs the CTA's tiles blockIdx.x, blockIdx.x + gridDim.x, ... < ntiles.
+// issue_loads(stage, bar, co, mc): the leader's tensor loads of one tile;
+// body(stage, desc): the tile's arithmetic (called by every thread).
+template <class Stage, class IssueFn, class BodyFn>
+__device__ __forceinline__ void run_tiles(const StepCommon &c, unsigned stage_bytes, int ntiles, Stage *st,
+                                          PipeTail *tail, IssueFn issue_loads, BodyFn body) {
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const unsigned bar0 = smem_u32(&tail->bar[0]);
+    const int b = blockIdx.x, g = gridDim.x;
+    int4 co = make_int4(0, 0, 0, 0);
+    int mc = 0;
+    // TMA destinations must be 128-byte aligned; the stage sizes keep them
+    // so, only the base is checked (uniform: the whole CTA leaves together).
+    if (smem_u32(st) & 127u) {
+        if (leader) atomicExch(c.tflag, 2u);
+        return;
+    }
+    if (leader) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        fence_mbar_init();
+        fetch_coords(c.infos, b, co, mc);
+        copy_desc(&tail->desc[0], &c.infos[b]);
+    }
+    griddep_wait();
+    griddep_launch_dependents();
+    auto issue = [&](int s) {
+        fence_proxy_async();
+        mbar_expect_tx(bar0 + 8 * s, stage_bytes);
+        issue_loads(st[s], bar0 + 8 * s, co, mc);
+    };
+    if (leader) {
+        issue(0);
+        if (b + g < ntiles) fetch_coords(c.infos, b + g, co, mc);
+    }
+    __syncthreads();  // barrier init visible before anyone waits
+    unsigned phase = 0;
+    int k = 0;
+    for (int tix = b; tix < ntiles; tix += g, k ^= 1) {
+        const bool landed = mbar_wait(bar0 + 8 * k, (phase >> k) & 1u);
+        phase ^= 1u << k;
+        if (leader) cp_async_wait_all();  // this stage's descriptor
+        if (__syncthreads_or(!landed)) {
+            if (leader) atomicExch(c.tflag, 1u);
+            return;
+        }
+        if (leader && tix + g < ntiles) {
+            copy_desc(&tail->desc[k ^ 1], &c.infos[tix + g]);
+            issue(k ^ 1);
+            if (tix + 2 * g < ntiles) fetch_coords(c.infos, tix + 2 * g, co, mc);
+        }
+        body(st[k], tail->desc[k]);
+    }
+}
+
+// Receivers of a tile, sampled from the pool the tile has just written
+// (this CTA's stores are visible to it after the barrier).
+template <int NT>
+__device__ __forceinline__ void sample_from_pool(const StepCommon &c, const TileInfo &T, const float *__restrict__ f,
+                                                 float *__restrict__ d, int n) {
+    __syncthreads();
+    const int tid = threadIdx.x + threadIdx.y * 32;
+    for (int e = T.rec_begin + tid; e < T.rec_end; e += NT) {
+        const TileRec tr = c.recs[e];
+        const long long cell = T.foff + (long long)(T.z0 + tr.cell / TX) * T.pitch + T.x0 + tr.cell % TX;
+        d[T.doff + (long long)n * T.nrec + tr.r] = f[cell];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward step (see fwd_step_kernel): u^n with halo, D^n and kappa by TMA.
+// ---------------------------------------------------------------------------
 struct TmaFwdStage {
     STile u;
     CTile d, k;
@@ -85,21 +197,22 @@ struct TmaFwdStage {
 constexpr unsigned kFwdStageBytes = sizeof(STile) + 2 * sizeof(CTile);
 static_assert(sizeof(TmaFwdStage) == kFwdStageBytes, "stage layout");
 static_assert(sizeof(STile) % 128 == 0 && sizeof(CTile) % 128 == 0, "TMA destinations stay 128-byte aligned");
-constexpr size_t kFwdSmem = 2 * sizeof(TmaFwdStage) + 16;
+constexpr size_t kFwdSmem = 2 * sizeof(TmaFwdStage) + sizeof(PipeTail);
 
 // R rows x 2 columns of one tile for this thread.  FULL: the tile lies in
 // the sponge-free interior, holds no source and needs no bounds masks.
 template <int R, bool STORE_A, bool FULL>
-__device__ __forceinline__ void fwd_rows(const FwdArgs &A, const TmaFwdStage &S, const Tile &t, const ShotDesc &sd,
-                                         int lxp, int lz0) {
+__device__ __forceinline__ void fwd_rows(const FwdArgs &A, const TmaFwdStage &S, const TileInfo &T, int lxp,
+                                         int lz0) {
     const int NZ = A.c.NZ;
-    const int j = t.x0 + lxp;
-    const int i0 = t.z0 + lz0;
+    const int j = T.x0 + lxp;
+    const int i0 = T.z0 + lz0;
+    const int nxw = T.nxw, pitch = T.pitch;
     float2 zc[R + 2 * HALO];
 #pragma unroll
     for (int r = 0; r < R + 2 * HALO; r++)
         zc[r] = *reinterpret_cast<const float2 *>(&S.u[lz0 + r][lxp + HALO]);
-    const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+    const long long cbase = T.foff + (long long)i0 * pitch + j;
     if constexpr (FULL) {
 #pragma unroll
         for (int rr = 0; rr < R; rr++) {
@@ -108,7 +221,7 @@ __device__ __forceinline__ void fwd_rows(const FwdArgs &A, const TmaFwdStage &S,
             const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[lz0 + rr][lxp]));
             const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr][lxp]));
             const f2 dn = fma2(kv, a, dv);
-            const long long c = cbase + (long long)rr * sd.pitch;
+            const long long c = cbase + (long long)rr * pitch;
             *reinterpret_cast<f2 *>(A.dd + c) = dn;
             *reinterpret_cast<f2 *>(A.un + c) = add2(u, dn);
             if (!STORE_A && A.ck_u) {
@@ -119,21 +232,21 @@ __device__ __forceinline__ void fwd_rows(const FwdArgs &A, const TmaFwdStage &S,
         }
     } else {
         const int nrow = min(R, NZ - i0);
-        const bool ok = j < sd.nxw, hi = j + 1 < sd.nxw;
-        const float q = A.c.wav[sd.wav_off + A.n];
-        const float wx0 = sponge1(j, sd.nxw, A.c.nb), wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
+        const bool ok = j < nxw, hi = j + 1 < nxw;
+        const float q = A.c.wav[T.wav_off + A.n];
+        const float wx0 = sponge1(j, nxw, A.c.nb), wx1 = sponge1(j + 1, nxw, A.c.nb);
 #pragma unroll
         for (int rr = 0; rr < R; rr++) {
             if (ok && rr < nrow) {
                 const int i = i0 + rr;
-                const f2 a = inject(lap8x2(S.u, zc + rr, lz0 + rr, lxp), i, j, sd.sz, sd.sx, q);
+                const f2 a = inject(lap8x2(S.u, zc + rr, lz0 + rr, lxp), i, j, T.sz, T.sx, q);
                 const float wz = sponge1(i, NZ, A.c.nb);
                 const f2 w = pk2(wz * wx0, wz * wx1);
                 const f2 u = pk(zc[rr + HALO]);
                 const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[lz0 + rr][lxp]));
                 const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr][lxp]));
                 const f2 dn = keep_lo(mul2(w, fma2(kv, a, dv)), hi);
-                const long long c = cbase + (long long)rr * sd.pitch;
+                const long long c = cbase + (long long)rr * pitch;
                 *reinterpret_cast<f2 *>(A.dd + c) = dn;
                 *reinterpret_cast<f2 *>(A.un + c) = keep_lo(fma2(w, u, dn), hi);
                 if (!STORE_A && A.ck_u) {
@@ -152,78 +265,29 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1)
     constexpr int NT = 32 * (TZ / R);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TmaFwdStage *st = reinterpret_cast<TmaFwdStage *>(smem_raw);
-    const unsigned bar0 = smem_u32(smem_raw + 2 * sizeof(TmaFwdStage));
-    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-    const int NZ = A.c.NZ, nb = A.c.nb;
+    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + 2 * sizeof(TmaFwdStage));
     const int lxp = 2 * threadIdx.x;
     const int lz0 = threadIdx.y * R;
-
-    // TMA destinations must be 128-byte aligned; the stage offsets are, so
-    // only the base is checked (uniform: the whole CTA leaves together).
-    if (smem_u32(smem_raw) & 127u) {
-        if (leader) atomicExch(A.c.tflag, 2u);
-        return;
-    }
-    if (leader) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    // Leader only: stage s receives tile tix.
-    auto issue = [&](int s, int tix) {
-        const Tile t = A.c.tiles[tix];
-        const int x0 = A.c.shots[t.slot].x0;
-        const unsigned b = bar0 + 8 * s;
-        fence_proxy_async();
-        mbar_expect_tx(b, kFwdStageBytes);
-        tma_load_3d(smem_u32(&st[s].u), &M.m[0], t.x0 - HALO, t.z0 - HALO, t.slot, b);
-        tma_load_3d(smem_u32(&st[s].d), &M.m[1], t.x0, t.z0, t.slot, b);
-        tma_load_3d(smem_u32(&st[s].k), &M.m[2], (x0 & ~3) + t.x0, t.z0, x0 & 3, b);
-    };
-
-    if (leader && (int)blockIdx.x < ntiles) issue(0, blockIdx.x);
-    unsigned phase = 0;
-    int k = 0;
-    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
-        const bool landed = mbar_wait(bar0 + 8 * k, (phase >> k) & 1u);
-        phase ^= 1u << k;
-        // Every thread has finished the previous tile here, so the other
-        // stage is free; a timeout is decided for the whole CTA at once.
-        if (__syncthreads_or(!landed)) {
-            if (leader) atomicExch(A.c.tflag, 1u);
-            return;
-        }
-        if (leader && tix + (int)gridDim.x < ntiles) issue(k ^ 1, tix + gridDim.x);
-        const Tile t = A.c.tiles[tix];
-        const ShotDesc sd = A.c.shots[t.slot];
-        const bool src_here = sd.sz >= t.z0 && sd.sz < t.z0 + TZ && sd.sx >= t.x0 && sd.sx < t.x0 + TX;
-        const bool full = t.z0 >= nb && t.z0 + TZ <= NZ - nb && t.x0 >= nb && t.x0 + TX <= sd.nxw - nb && !src_here;
-        if (full) fwd_rows<R, STORE_A, true>(A, st[k], t, sd, lxp, lz0);
-        else fwd_rows<R, STORE_A, false>(A, st[k], t, sd, lxp, lz0);
-        if (!STORE_A && A.d) {
-            const int rb = A.c.tiles[tix + 1].rec_begin;
-            if (rb > t.rec_begin) {
-                // Receivers read u^{n+1} back from the pool: this CTA's
-                // stores are visible to it after the barrier.
-                __syncthreads();
-                const int tid = threadIdx.x + threadIdx.y * 32;
-                for (int e = t.rec_begin + tid; e < rb; e += NT) {
-                    const TileRec tr = A.c.recs[e];
-                    const long long c = sd.foff + (long long)(t.z0 + tr.cell / TX) * sd.pitch + t.x0 + tr.cell % TX;
-                    A.d[sd.doff + (long long)A.n * sd.nrec + tr.r] = A.un[c];
-                }
-            }
-        }
-    }
+    run_tiles(
+        A.c, kFwdStageBytes, ntiles, st, tail,
+        [&](TmaFwdStage &S, unsigned bar, int4 co, int mc) {
+            tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO, co.y - HALO, co.x, bar);
+            tma_load_3d(smem_u32(&S.d), &M.m[1], co.z, co.y, co.x, bar);
+            tma_load_3d(smem_u32(&S.k), &M.m[2], co.w, co.y, mc, bar);
+        },
+        [&](const TmaFwdStage &S, const TileInfo &T) {
+            if (T.flags & TI_FULL_FWD) fwd_rows<R, STORE_A, true>(A, S, T, lxp, lz0);
+            else fwd_rows<R, STORE_A, false>(A, S, T, lxp, lz0);
+            if (!STORE_A && A.d && T.rec_end > T.rec_begin) sample_from_pool<NT>(A.c, T, A.un, A.d, A.n);
+        });
 }
 
 // ---------------------------------------------------------------------------
 // Adjoint step (see adj_step_kernel): nu^{k+1} with halo, D_nu, kappa and the
 // stored a^{k-1} by TMA; the image accumulator is read with plain loads
-// issued before the arithmetic (keeping two CTAs' worth of stages would not
-// fit), the receiver injection tile is built per tile with shared atomics.
+// issued before the arithmetic (a fifth staged tile would leave room for only
+// one stage), the receiver injection tile is built per tile with shared
+// atomics.
 // ---------------------------------------------------------------------------
 struct TmaAdjStage {
     STile u;
@@ -231,21 +295,22 @@ struct TmaAdjStage {
 };
 constexpr unsigned kAdjStageBytes = sizeof(STile) + 3 * sizeof(CTile);
 static_assert(sizeof(TmaAdjStage) == kAdjStageBytes, "stage layout");
-constexpr size_t kAdjSmem = 2 * sizeof(TmaAdjStage) + sizeof(CTile) + 16;
+constexpr size_t kAdjSmem = 2 * sizeof(TmaAdjStage) + sizeof(PipeTail) + sizeof(CTile);
 
 template <int R, bool FULL>
 __device__ __forceinline__ void adj_rows(const AdjArgs &A, const TmaAdjStage &S, const CTile &inj, bool has_rec,
-                                         const Tile &t, const ShotDesc &sd, int lxp, int lz0) {
+                                         const TileInfo &T, int lxp, int lz0) {
     const int NZ = A.c.NZ;
-    const int j = t.x0 + lxp;
-    const int i0 = t.z0 + lz0;
-    const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+    const int j = T.x0 + lxp;
+    const int i0 = T.z0 + lz0;
+    const int nxw = T.nxw, pitch = T.pitch;
+    const long long cbase = T.foff + (long long)i0 * pitch + j;
     const int nrow = FULL ? R : min(R, NZ - i0);
-    const bool ok = FULL || j < sd.nxw, hi = FULL || j + 1 < sd.nxw;
+    const bool ok = FULL || j < nxw, hi = FULL || j + 1 < nxw;
     float2 gv[R];
 #pragma unroll
     for (int rr = 0; rr < R; rr++)
-        gv[rr] = (ok && rr < nrow) ? *reinterpret_cast<const float2 *>(A.g + cbase + (long long)rr * sd.pitch)
+        gv[rr] = (ok && rr < nrow) ? *reinterpret_cast<const float2 *>(A.g + cbase + (long long)rr * pitch)
                                    : make_float2(0.f, 0.f);
     float2 zc[R + 2 * HALO];
 #pragma unroll
@@ -253,8 +318,8 @@ __device__ __forceinline__ void adj_rows(const AdjArgs &A, const TmaAdjStage &S,
         zc[r] = *reinterpret_cast<const float2 *>(&S.u[lz0 + r][lxp + HALO]);
     float wx0 = 1.f, wx1 = 1.f;
     if constexpr (!FULL) {
-        wx0 = sponge1(j, sd.nxw, A.c.nb);
-        wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
+        wx0 = sponge1(j, nxw, A.c.nb);
+        wx1 = sponge1(j + 1, nxw, A.c.nb);
     }
 #pragma unroll
     for (int rr = 0; rr < R; rr++) {
@@ -275,7 +340,7 @@ __device__ __forceinline__ void adj_rows(const AdjArgs &A, const TmaAdjStage &S,
                 dn = keep_lo(mul2(w, fma2(kv, a, dv)), hi);
                 nn = keep_lo(fma2(w, nu, dn), hi);
             }
-            const long long c = cbase + (long long)rr * sd.pitch;
+            const long long c = cbase + (long long)rr * pitch;
             *reinterpret_cast<f2 *>(A.dd + c) = dn;
             *reinterpret_cast<f2 *>(A.nun + c) = nn;
             *reinterpret_cast<f2 *>(A.g + c) = keep_lo(fma2(av, nn, pk(gv[rr])), hi);
@@ -289,63 +354,34 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1)
     constexpr int NT = 32 * (TZ / R);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TmaAdjStage *st = reinterpret_cast<TmaAdjStage *>(smem_raw);
-    CTile &inj = *reinterpret_cast<CTile *>(smem_raw + 2 * sizeof(TmaAdjStage));
-    const unsigned bar0 = smem_u32(smem_raw + 2 * sizeof(TmaAdjStage) + sizeof(CTile));
-    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + 2 * sizeof(TmaAdjStage));
+    CTile &inj = *reinterpret_cast<CTile *>(smem_raw + 2 * sizeof(TmaAdjStage) + sizeof(PipeTail));
     const int tid = threadIdx.x + threadIdx.y * 32;
-    const int NZ = A.c.NZ, nb = A.c.nb;
     const int lxp = 2 * threadIdx.x;
     const int lz0 = threadIdx.y * R;
-    if (smem_u32(smem_raw) & 127u) {
-        if (leader) atomicExch(A.c.tflag, 2u);
-        return;
-    }
-    if (leader) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    auto issue = [&](int s, int tix) {
-        const Tile t = A.c.tiles[tix];
-        const int x0 = A.c.shots[t.slot].x0;
-        const unsigned b = bar0 + 8 * s;
-        fence_proxy_async();
-        mbar_expect_tx(b, kAdjStageBytes);
-        tma_load_3d(smem_u32(&st[s].u), &M.m[0], t.x0 - HALO, t.z0 - HALO, t.slot, b);
-        tma_load_3d(smem_u32(&st[s].d), &M.m[1], t.x0, t.z0, t.slot, b);
-        tma_load_3d(smem_u32(&st[s].k), &M.m[2], (x0 & ~3) + t.x0, t.z0, x0 & 3, b);
-        tma_load_3d(smem_u32(&st[s].a), &M.m[3], t.x0, t.z0, t.slot, b);
-    };
-    if (leader && (int)blockIdx.x < ntiles) issue(0, blockIdx.x);
-    unsigned phase = 0;
-    int k = 0;
-    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
-        const bool landed = mbar_wait(bar0 + 8 * k, (phase >> k) & 1u);
-        phase ^= 1u << k;
-        if (__syncthreads_or(!landed)) {
-            if (leader) atomicExch(A.c.tflag, 1u);
-            return;
-        }
-        if (leader && tix + (int)gridDim.x < ntiles) issue(k ^ 1, tix + gridDim.x);
-        const Tile t = A.c.tiles[tix];
-        const int rb = A.c.tiles[tix + 1].rec_begin;
-        const ShotDesc sd = A.c.shots[t.slot];
-        const bool has_rec = rb > t.rec_begin;
-        if (has_rec) {
-            for (int e = tid; e < TZ * TX; e += NT) (&inj[0][0])[e] = 0.f;
-            __syncthreads();
-            const float *rk = A.r + sd.doff + (long long)(A.k - 1) * sd.nrec;
-            for (int e = t.rec_begin + tid; e < rb; e += NT) {
-                const TileRec tr = A.c.recs[e];
-                atomicAdd(&inj[tr.cell / TX][tr.cell % TX], rk[tr.r]);
+    run_tiles(
+        A.c, kAdjStageBytes, ntiles, st, tail,
+        [&](TmaAdjStage &S, unsigned bar, int4 co, int mc) {
+            tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO, co.y - HALO, co.x, bar);
+            tma_load_3d(smem_u32(&S.d), &M.m[1], co.z, co.y, co.x, bar);
+            tma_load_3d(smem_u32(&S.k), &M.m[2], co.w, co.y, mc, bar);
+            tma_load_3d(smem_u32(&S.a), &M.m[3], co.z, co.y, co.x, bar);
+        },
+        [&](const TmaAdjStage &S, const TileInfo &T) {
+            const bool has_rec = T.rec_end > T.rec_begin;
+            if (has_rec) {
+                for (int e = tid; e < TZ * TX; e += NT) (&inj[0][0])[e] = 0.f;
+                __syncthreads();
+                const float *rk = A.r + T.doff + (long long)(A.k - 1) * T.nrec;
+                for (int e = T.rec_begin + tid; e < T.rec_end; e += NT) {
+                    const TileRec tr = A.c.recs[e];
+                    atomicAdd(&inj[tr.cell / TX][tr.cell % TX], rk[tr.r]);
+                }
+                __syncthreads();
             }
-            __syncthreads();
-        }
-        const bool full = t.z0 >= nb && t.z0 + TZ <= NZ - nb && t.x0 >= nb && t.x0 + TX <= sd.nxw - nb;
-        if (full) adj_rows<R, true>(A, st[k], inj, has_rec, t, sd, lxp, lz0);
-        else adj_rows<R, false>(A, st[k], inj, has_rec, t, sd, lxp, lz0);
-    }
+            if (T.flags & TI_INTERIOR) adj_rows<R, true>(A, S, inj, has_rec, T, lxp, lz0);
+            else adj_rows<R, false>(A, S, inj, has_rec, T, lxp, lz0);
+        });
 }
 
 // ---------------------------------------------------------------------------
@@ -358,17 +394,18 @@ struct TmaBornStage {
 };
 constexpr unsigned kBornStageBytes = 2 * sizeof(STile) + 4 * sizeof(CTile);
 static_assert(sizeof(TmaBornStage) == kBornStageBytes, "stage layout");
-constexpr size_t kBornSmem = 2 * sizeof(TmaBornStage) + 16;
+constexpr size_t kBornSmem = 2 * sizeof(TmaBornStage) + sizeof(PipeTail);
 
 template <int R, bool FULL>
-__device__ __forceinline__ void born_rows(const BornArgs &A, const TmaBornStage &S, const Tile &t, const ShotDesc &sd,
-                                          int lxp, int lz0) {
+__device__ __forceinline__ void born_rows(const BornArgs &A, const TmaBornStage &S, const TileInfo &T, int lxp,
+                                          int lz0) {
     const int NZ = A.c.NZ;
-    const int j = t.x0 + lxp;
-    const int i0 = t.z0 + lz0;
-    const long long cbase = sd.foff + (long long)i0 * sd.pitch + j;
+    const int j = T.x0 + lxp;
+    const int i0 = T.z0 + lz0;
+    const int nxw = T.nxw, pitch = T.pitch;
+    const long long cbase = T.foff + (long long)i0 * pitch + j;
     const int nrow = FULL ? R : min(R, NZ - i0);
-    const bool ok = FULL || j < sd.nxw, hi = FULL || j + 1 < sd.nxw;
+    const bool ok = FULL || j < nxw, hi = FULL || j + 1 < nxw;
     float2 zu[R + 2 * HALO], zp[R + 2 * HALO];
 #pragma unroll
     for (int r = 0; r < R + 2 * HALO; r++) {
@@ -377,15 +414,15 @@ __device__ __forceinline__ void born_rows(const BornArgs &A, const TmaBornStage 
     }
     float wx0 = 1.f, wx1 = 1.f, q = 0.f;
     if constexpr (!FULL) {
-        wx0 = sponge1(j, sd.nxw, A.c.nb);
-        wx1 = sponge1(j + 1, sd.nxw, A.c.nb);
-        q = A.c.wav[sd.wav_off + A.n];
+        wx0 = sponge1(j, nxw, A.c.nb);
+        wx1 = sponge1(j + 1, nxw, A.c.nb);
+        q = A.c.wav[T.wav_off + A.n];
     }
 #pragma unroll
     for (int rr = 0; rr < R; rr++) {
         if (ok && rr < nrow) {
             f2 a0 = lap8x2(S.u, zu + rr, lz0 + rr, lxp);
-            if constexpr (!FULL) a0 = inject(a0, i0 + rr, j, sd.sz, sd.sx, q);
+            if constexpr (!FULL) a0 = inject(a0, i0 + rr, j, T.sz, T.sx, q);
             const f2 ap = lap8x2(S.p, zp + rr, lz0 + rr, lxp);
             const f2 duv = pk(*reinterpret_cast<const float2 *>(&S.du[lz0 + rr][lxp]));
             const f2 dpv = pk(*reinterpret_cast<const float2 *>(&S.dp[lz0 + rr][lxp]));
@@ -405,7 +442,7 @@ __device__ __forceinline__ void born_rows(const BornArgs &A, const TmaBornStage 
                 un = keep_lo(fma2(w, pk(zu[rr + HALO]), du), hi);
                 pn = keep_lo(fma2(w, pk(zp[rr + HALO]), dp), hi);
             }
-            const long long c = cbase + (long long)rr * sd.pitch;
+            const long long c = cbase + (long long)rr * pitch;
             *reinterpret_cast<f2 *>(A.du + c) = du;
             *reinterpret_cast<f2 *>(A.dp + c) = dp;
             *reinterpret_cast<f2 *>(A.un + c) = un;
@@ -420,73 +457,50 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1)
     constexpr int NT = 32 * (TZ / R);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TmaBornStage *st = reinterpret_cast<TmaBornStage *>(smem_raw);
-    const unsigned bar0 = smem_u32(smem_raw + 2 * sizeof(TmaBornStage));
-    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-    const int NZ = A.c.NZ, nb = A.c.nb;
+    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + 2 * sizeof(TmaBornStage));
     const int lxp = 2 * threadIdx.x;
     const int lz0 = threadIdx.y * R;
-    if (smem_u32(smem_raw) & 127u) {
-        if (leader) atomicExch(A.c.tflag, 2u);
-        return;
-    }
-    if (leader) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    auto issue = [&](int s, int tix) {
-        const Tile t = A.c.tiles[tix];
-        const int x0 = A.c.shots[t.slot].x0;
-        const unsigned b = bar0 + 8 * s;
-        fence_proxy_async();
-        mbar_expect_tx(b, kBornStageBytes);
-        tma_load_3d(smem_u32(&st[s].u), &M.m[0], t.x0 - HALO, t.z0 - HALO, t.slot, b);
-        tma_load_3d(smem_u32(&st[s].p), &M.m[1], t.x0 - HALO, t.z0 - HALO, t.slot, b);
-        tma_load_3d(smem_u32(&st[s].du), &M.m[2], t.x0, t.z0, t.slot, b);
-        tma_load_3d(smem_u32(&st[s].dp), &M.m[3], t.x0, t.z0, t.slot, b);
-        tma_load_3d(smem_u32(&st[s].k), &M.m[4], (x0 & ~3) + t.x0, t.z0, x0 & 3, b);
-        tma_load_3d(smem_u32(&st[s].dk), &M.m[5], (x0 & ~3) + t.x0, t.z0, x0 & 3, b);
-    };
-    if (leader && (int)blockIdx.x < ntiles) issue(0, blockIdx.x);
-    unsigned phase = 0;
-    int k = 0;
-    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x, k ^= 1) {
-        const bool landed = mbar_wait(bar0 + 8 * k, (phase >> k) & 1u);
-        phase ^= 1u << k;
-        if (__syncthreads_or(!landed)) {
-            if (leader) atomicExch(A.c.tflag, 1u);
-            return;
-        }
-        if (leader && tix + (int)gridDim.x < ntiles) issue(k ^ 1, tix + gridDim.x);
-        const Tile t = A.c.tiles[tix];
-        const ShotDesc sd = A.c.shots[t.slot];
-        const bool src_here = sd.sz >= t.z0 && sd.sz < t.z0 + TZ && sd.sx >= t.x0 && sd.sx < t.x0 + TX;
-        const bool full = t.z0 >= nb && t.z0 + TZ <= NZ - nb && t.x0 >= nb && t.x0 + TX <= sd.nxw - nb && !src_here;
-        if (full) born_rows<R, true>(A, st[k], t, sd, lxp, lz0);
-        else born_rows<R, false>(A, st[k], t, sd, lxp, lz0);
-        const int rb = A.c.tiles[tix + 1].rec_begin;
-        if (rb > t.rec_begin) {
-            __syncthreads();  // p^{n+1} of this tile is in the pool
-            const int tid = threadIdx.x + threadIdx.y * 32;
-            for (int e = t.rec_begin + tid; e < rb; e += NT) {
-                const TileRec tr = A.c.recs[e];
-                const long long c = sd.foff + (long long)(t.z0 + tr.cell / TX) * sd.pitch + t.x0 + tr.cell % TX;
-                A.d[sd.doff + (long long)A.n * sd.nrec + tr.r] = A.pn[c];
-            }
-        }
-    }
+    run_tiles(
+        A.c, kBornStageBytes, ntiles, st, tail,
+        [&](TmaBornStage &S, unsigned bar, int4 co, int mc) {
+            tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO, co.y - HALO, co.x, bar);
+            tma_load_3d(smem_u32(&S.p), &M.m[1], co.z - HALO, co.y - HALO, co.x, bar);
+            tma_load_3d(smem_u32(&S.du), &M.m[2], co.z, co.y, co.x, bar);
+            tma_load_3d(smem_u32(&S.dp), &M.m[3], co.z, co.y, co.x, bar);
+            tma_load_3d(smem_u32(&S.k), &M.m[4], co.w, co.y, mc, bar);
+            tma_load_3d(smem_u32(&S.dk), &M.m[5], co.w, co.y, mc, bar);
+        },
+        [&](const TmaBornStage &S, const TileInfo &T) {
+            if (T.flags & TI_FULL_FWD) born_rows<R, true>(A, S, T, lxp, lz0);
+            else born_rows<R, false>(A, S, T, lxp, lz0);
+            if (T.rec_end > T.rec_begin) sample_from_pool<NT>(A.c, T, A.pn, A.d, A.n);
+        });
 }
 
 // ---------------------------------------------------------------------------
 // Launchers and occupancy per variant (R = 4, 8, 16 for variants 3, 4, 5).
 // ---------------------------------------------------------------------------
+// Launch as a programmatic dependent of the previous kernel in the stream.
+template <typename Args>
+void launch_pdl(void (*kernel)(Args, TileMaps, int), int grid, int R, size_t smem, cudaStream_t s, const Args &a,
+                const TileMaps &maps, int ntiles) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32, TZ / R);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, a, maps, ntiles);
+}
+
 template <int R>
 void fwd_launch_r(const FwdArgs &a, int ntiles, int grid, const TileMaps &maps, cudaStream_t s) {
-    if (a.a_out)
-        fwd_tma_kernel<R, true><<<grid, dim3(32, TZ / R), kFwdSmem, s>>>(a, maps, ntiles);
-    else
-        fwd_tma_kernel<R, false><<<grid, dim3(32, TZ / R), kFwdSmem, s>>>(a, maps, ntiles);
+    if (a.a_out) launch_pdl(fwd_tma_kernel<R, true>, grid, R, kFwdSmem, s, a, maps, ntiles);
+    else launch_pdl(fwd_tma_kernel<R, false>, grid, R, kFwdSmem, s, a, maps, ntiles);
 }
 
 int occupancy(const void *fn, int threads, size_t smem) {
@@ -523,15 +537,15 @@ void launch_fwd_step_tma(const FwdArgs &a, int ntiles, int variant, int grid, co
 
 void launch_adj_step_tma(const AdjArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s) {
     switch (variant) {
-    case FIRST_TMA_VARIANT: adj_tma_kernel<4><<<grid, dim3(32, TZ / 4), kAdjSmem, s>>>(a, maps, ntiles); break;
-    default: adj_tma_kernel<8><<<grid, dim3(32, TZ / 8), kAdjSmem, s>>>(a, maps, ntiles); break;
+    case FIRST_TMA_VARIANT: launch_pdl(adj_tma_kernel<4>, grid, 4, kAdjSmem, s, a, maps, ntiles); break;
+    default: launch_pdl(adj_tma_kernel<8>, grid, 8, kAdjSmem, s, a, maps, ntiles); break;
     }
 }
 
 void launch_born_step_tma(const BornArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s) {
     switch (variant) {
-    case FIRST_TMA_VARIANT: born_tma_kernel<4><<<grid, dim3(32, TZ / 4), kBornSmem, s>>>(a, maps, ntiles); break;
-    default: born_tma_kernel<8><<<grid, dim3(32, TZ / 8), kBornSmem, s>>>(a, maps, ntiles); break;
+    case FIRST_TMA_VARIANT: launch_pdl(born_tma_kernel<4>, grid, 4, kBornSmem, s, a, maps, ntiles); break;
+    default: launch_pdl(born_tma_kernel<8>, grid, 8, kBornSmem, s, a, maps, ntiles); break;
     }
 }
 
