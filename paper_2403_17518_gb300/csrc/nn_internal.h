@@ -29,6 +29,7 @@ struct FpropArgs {
     int dst_stride, dst_off;
     float *part;                // optional split-k scratch ([splits][M][N] float32)
     long long part_floats;      // its capacity
+    unsigned *err;              // nullable: set to 1 by a tensor-core GEMM whose bounded wait ran out
 };
 
 // Split-k weight-gradient GEMM; see igemm_wgrad_kernel.
@@ -46,7 +47,12 @@ struct WgradArgs {
     float *part;                // [splits][M][N]
 };
 
+// mma.sync GEMM (igemm_fprop_kernel), or the tcgen05 one (nn_umma.cu) when
+// DHFWI_NN_GEMM=tc.
 void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s);
+void launch_fprop_umma(const FpropArgs &a, int epi, cudaStream_t s);
+// Sum of split-k partials a.part[splits][M][N] with the epilogue epi.
+void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s);
 int wgrad_splits(long long kpix, int M, int N);
 // Weight gradient into dw (parameter layout) and bias gradient into db.
 void launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s);

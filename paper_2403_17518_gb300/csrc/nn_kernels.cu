@@ -9,6 +9,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "nn_internal.h"
 
@@ -776,7 +778,31 @@ static void fprop_launch(const FpropArgs &a, cudaStream_t s) {
     }
 }
 
+void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s) {
+    const int g = grid_for((long long)a.M * a.N);
+    switch (epi) {
+    case EPI_BF16_LEAKY: fprop_reduce_kernel<EPI_BF16_LEAKY><<<g, 256, 0, s>>>(a, splits); break;
+    case EPI_BF16: fprop_reduce_kernel<EPI_BF16><<<g, 256, 0, s>>>(a, splits); break;
+    case EPI_BF16_CONVT: fprop_reduce_kernel<EPI_BF16_CONVT><<<g, 256, 0, s>>>(a, splits); break;
+    case EPI_F32: fprop_reduce_kernel<EPI_F32><<<g, 256, 0, s>>>(a, splits); break;
+    default: fprop_reduce_kernel<EPI_F32_ADD><<<g, 256, 0, s>>>(a, splits); break;
+    }
+}
+
+// DHFWI_NN_GEMM=tc selects the tcgen05 GEMM for the forward-form
+// convolutions; the mma.sync kernel is the default (faster on this network's
+// gather-bound shapes, see nn_umma.cu).  Read per launch so a process can
+// switch.
+static bool use_umma() {
+    const char *e = getenv("DHFWI_NN_GEMM");
+    return e && strcmp(e, "tc") == 0;
+}
+
 void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
+    if (use_umma()) {
+        launch_fprop_umma(a, epi, s);
+        return;
+    }
     const bool small = a.N <= 32;
     switch (epi) {
     case EPI_BF16_LEAKY: small ? fprop_launch<32, EPI_BF16_LEAKY>(a, s) : fprop_launch<64, EPI_BF16_LEAKY>(a, s); break;

@@ -64,6 +64,7 @@ struct NetState {
     size_t fp_part_floats = 0;
     __nv_bfloat16 *ones = nullptr;  // {1, 0, ..., 0}: bias column of the weight-gradient GEMMs
     unsigned *mx = nullptr;
+    unsigned *err = nullptr;     // set by a tensor-core GEMM whose bounded wait ran out
     float *scales = nullptr;  // [0..1] x scale, [2..3] y scale
     int *oz = nullptr, *ox = nullptr, *perm = nullptr;
     size_t oz_cap = 0, perm_cap = 0;
@@ -390,6 +391,7 @@ void conv3_fwd(NetState &N, const LayerDesc &d, const __nv_bfloat16 *w, int nimg
     a.dst_off = dof;
     a.part = N.fp_part;
     a.part_floats = (long long)N.fp_part_floats;
+    a.err = N.err;
     launch_fprop(a, epi, s);
     N.launches += 2;
 }
@@ -444,6 +446,7 @@ void forward(NetState &N, int n, int H, int W, cudaStream_t s) {
         t.dst_off = C(r);
         t.part = N.fp_part;
         t.part_floats = (long long)N.fp_part_floats;
+        t.err = N.err;
         launch_fprop(t, EPI_BF16_CONVT, s);
         N.launches++;
         const LayerDesc &d0 = N.L[layer_index_up(N, l, 1)], &d1 = N.L[layer_index_up(N, l, 2)];
@@ -516,6 +519,8 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
         a.dst_off = 0;
         a.part = N.fp_part;
         a.part_floats = (long long)N.fp_part_floats;
+        a.err = N.err;
+    a.err = N.err;
         launch_fprop(a, EPI_F32, s);
         N.launches += 2;
     }
@@ -594,6 +599,8 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         a.dst_off = 0;
         a.part = N.fp_part;
         a.part_floats = (long long)N.fp_part_floats;
+        a.err = N.err;
+    a.err = N.err;
         launch_fprop(a, EPI_F32, s);
         N.launches += 5;
         std::swap(dA, dB);
@@ -634,6 +641,10 @@ int ensure_small(dhfwi_ctx *ctx, NetState &N) {
     if (!N.mse_part && (rc = dev_alloc(ctx, (void **)&N.mse_part, sizeof(double) * MSE_BLOCKS))) return rc;
     if (!N.loss_acc && (rc = dev_alloc(ctx, (void **)&N.loss_acc, sizeof(double) * 4096))) return rc;
     if (!N.mx && (rc = dev_alloc(ctx, (void **)&N.mx, 16))) return rc;
+    if (!N.err) {
+        if ((rc = dev_alloc(ctx, (void **)&N.err, 16))) return rc;
+        NCK(cudaMemset(N.err, 0, 16));
+    }
     if (!N.scales && (rc = dev_alloc(ctx, (void **)&N.scales, 4 * sizeof(float)))) return rc;
     if (!N.ones) {
         if ((rc = dev_alloc(ctx, (void **)&N.ones, 16))) return rc;
@@ -661,6 +672,18 @@ int ensure_net(dhfwi_ctx *ctx, int base, int levels) {
     return ensure_small(ctx, *net);
 }
 
+// DHFWI_ERR_TIMEOUT if a tensor-core GEMM of this or an earlier call ran out
+// its bounded wait (the word is cleared); synchronises the stream.
+int check_gemm_err(dhfwi_ctx *ctx, NetState &N, cudaStream_t s) {
+    if (!N.err) return DHFWI_OK;
+    unsigned e = 0;
+    NCK(cudaMemcpyAsync(&e, N.err, sizeof e, cudaMemcpyDeviceToHost, s));
+    NCK(cudaStreamSynchronize(s));
+    if (!e) return DHFWI_OK;
+    NCK(cudaMemsetAsync(N.err, 0, sizeof e, s));
+    return fail(ctx, DHFWI_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting for its MMAs");
+}
+
 int upload_params(dhfwi_ctx *ctx, NetState &N, const float *host, cudaStream_t s) {
     NCK(cudaMemcpyAsync(N.theta, host, sizeof(float) * N.nparams, cudaMemcpyHostToDevice, s));
     NCK(cudaStreamSynchronize(s));
@@ -675,7 +698,7 @@ void net_destroy(NetState *net) {
     if (!net) return;
     free_params(*net);
     void *ps[] = {net->arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->ones,
-                  net->mx, net->scales, net->oz, net->ox, net->perm};
+                  net->mx, net->err, net->scales, net->oz, net->ox, net->perm};
     for (void *p : ps) dev_free(p);
     delete net;
 }
@@ -885,6 +908,7 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
         NCK(cudaStreamSynchronize(s));
         // loss_acc[e] = sum_b cnt_b * mean_b(r^2); per-epoch mean over patches.
         for (int e = 0; e < cfg->epochs; e++) loss_hist[e] = (float)(acc[e] / (double)npatch);
+        if ((rc = check_gemm_err(ctx, N, s))) return rc;
     }
     ctx_count_launches(ctx, N.launches);
     return DHFWI_OK;

@@ -46,8 +46,14 @@ def test_init_is_bitwise_identical(base, levels):
     assert np.array_equal(ctx.net_get(), onn.init_params(spec, 5))
 
 
+# Both convolution GEMMs: mma.sync (default) and tcgen05 (DHFWI_NN_GEMM=tc).
+GEMMS = ["mma", "tc"]
+
+
+@pytest.mark.parametrize("gemm", GEMMS)
 @pytest.mark.parametrize("base,levels,n,h,w", [(8, 2, 2, 32, 32), (16, 3, 3, 24, 40), (32, 4, 2, 128, 128)])
-def test_forward_and_gradient_parity(base, levels, n, h, w):
+def test_forward_and_gradient_parity(base, levels, n, h, w, gemm, monkeypatch):
+    monkeypatch.setenv("DHFWI_NN_GEMM", gemm)
     ctx = _ctx()
     spec = onn.UNetSpec(base=base, levels=levels)
     ctx.net_init(base, levels, seed=11)
@@ -82,7 +88,9 @@ def test_gradient_is_deterministic():
     assert l1 == l2 and bool((g1 == g2).all())
 
 
-def test_training_and_apply_parity():
+@pytest.mark.parametrize("gemm", GEMMS)
+def test_training_and_apply_parity(gemm, monkeypatch):
+    monkeypatch.setenv("DHFWI_NN_GEMM", gemm)
     ctx = _ctx()
     from scipy.ndimage import gaussian_filter
 
