@@ -82,7 +82,7 @@ namespace {
 
 constexpr int RESID_BLOCKS = 1024;
 constexpr int TFLAG_WORD = 4;  // status word set by a timed-out TMA wait
-constexpr int NPOOLS = 7;  // field pools: u (2) + D, nu (2) + D_nu, image
+constexpr int NPOOLS = 8;  // field pools: u (2) + D, nu (2) + D_nu, image, second D
 
 int fail(dhfwi_ctx *ctx, int code, const std::string &msg) {
     if (ctx) ctx->err = msg;
@@ -318,7 +318,14 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
         T.doff = sd.doff;
         const bool interior = t.z0 >= nb && t.z0 + TZ <= NZ - nb && t.x0 >= nb && t.x0 + TX <= sd.nxw - nb;
         const bool src = sd.sz >= t.z0 && sd.sz < t.z0 + TZ && sd.sx >= t.x0 && sd.sx < t.x0 + TX;
-        T.flags = (interior ? TI_INTERIOR : 0) | (interior && !src ? TI_FULL_FWD : 0);
+        // The same with the tile grown by HALO on every side (two-step kernel).
+        const bool interior2 = t.z0 - HALO >= nb && t.z0 + TZ + HALO <= NZ - nb && t.x0 - HALO >= nb &&
+                               t.x0 + TX + HALO <= sd.nxw - nb;
+        const bool src2 = sd.sz >= t.z0 - HALO && sd.sz < t.z0 + TZ + HALO && sd.sx >= t.x0 - HALO &&
+                          sd.sx < t.x0 + TX + HALO;
+        T.flags = (interior ? TI_INTERIOR : 0) | (interior && !src ? TI_FULL_FWD : 0) |
+                  (interior2 && !src2 ? TI_FULL2 : 0);
+        T.nt = sd.nt;
     }
     P.pool_floats = foff;
     std::vector<float> wav((size_t)G->nt_max * (G->wavelet_shared ? 1 : ns));
@@ -369,7 +376,7 @@ StepCommon common(dhfwi_ctx *ctx) {
 
 // Tensor-map shape kinds: field pool with halo box, field pool cell box,
 // model array (4 copies) cell box.
-enum { MAP_POOL_HALO = 0, MAP_POOL_CELL = 1, MAP_MODEL = 2 };
+enum { MAP_POOL_HALO = 0, MAP_POOL_CELL = 1, MAP_MODEL = 2, MAP_POOL_HALO2 = 3, MAP_MODEL_HALO = 4 };
 
 // The tensor map of one array for the TMA-staged kernels (cached).
 int tensor_map(dhfwi_ctx *ctx, const float *base, int kind, CUtensorMap *out) {
@@ -384,7 +391,14 @@ int tensor_map(dhfwi_ctx *ctx, const float *base, int kind, CUtensorMap *out) {
     const Plan &P = ctx->plan;
     cuuint64_t dims[3], strides[2];
     cuuint32_t box[3] = {TX, TZ, 1}, estr[3] = {1, 1, 1};
-    if (kind == MAP_MODEL) {
+    if (kind == MAP_POOL_HALO || kind == MAP_MODEL_HALO) {
+        box[0] = TX + 2 * HALO;
+        box[1] = TZ + 2 * HALO;
+    } else if (kind == MAP_POOL_HALO2) {
+        box[0] = TX + 2 * HALO2;
+        box[1] = TZ + 2 * HALO2;
+    }
+    if (kind == MAP_MODEL || kind == MAP_MODEL_HALO) {
         dims[0] = ctx->pf;
         dims[1] = ctx->NZ;
         dims[2] = 4;
@@ -396,10 +410,6 @@ int tensor_map(dhfwi_ctx *ctx, const float *base, int kind, CUtensorMap *out) {
         dims[2] = P.n_shots;
         strides[0] = sizeof(float) * (cuuint64_t)P.pitch;
         strides[1] = sizeof(float) * (cuuint64_t)P.pitch * ctx->NZ;
-        if (kind == MAP_POOL_HALO) {
-            box[0] = TX + 2 * HALO;
-            box[1] = TZ + 2 * HALO;
-        }
     }
     CUtensorMap m;
     const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, estr,
@@ -679,24 +689,73 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
     return DHFWI_OK;
 }
 
-// Forward pass over all steps.  State pools uA (u^0), uB (scratch) and dd
-// (D^0) must be zeroed by the caller.  d (nullable) receives samples; ck
-// (nullable) receives (u^n, D^n) every K steps, two pools per checkpoint.
-int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *d, float *ck, int K, cudaStream_t st) {
+// Two-step (time-blocked) forward launches are used unless
+// DHFWI_TIME_BLOCK=0 or tensor maps are unavailable (read per call).
+bool time_blocking() {
+    const char *e = getenv("DHFWI_TIME_BLOCK");
+    return !(e && strcmp(e, "0") == 0) && encode_tiled() != nullptr;
+}
+
+// Maps of a two-step forward launch (u^n with the doubled halo, D^n with
+// its ring, kappa with its ring).
+int pair_maps(dhfwi_ctx *ctx, const FwdArgs &a, TileMaps *M) {
+    int rc;
+    if ((rc = tensor_map(ctx, a.u, MAP_POOL_HALO2, &M->m[0]))) return rc;
+    if ((rc = tensor_map(ctx, a.dd, MAP_POOL_HALO, &M->m[1]))) return rc;
+    return tensor_map(ctx, a.c.kap, MAP_MODEL_HALO, &M->m[2]);
+}
+
+// Advances the forward state from step n: two steps with one two-step launch
+// when blocking is on and n + 1 < n_end, else one.  State: u in *cur (next
+// in *nxt), D in *dcur (*dnxt: the two-step kernel's output pool).  a_slot(n)
+// gives the segment slot for a^n (nullptr: no segment store).  Returns the
+// number of steps taken, or a negative error code.
+template <typename SlotFn>
+int forward_steps(dhfwi_ctx *ctx, FwdArgs &a, int n, int n_end, float *&cur, float *&nxt, float *&dcur,
+                  float *&dnxt, const StepLaunch &L, bool blocking, SlotFn a_slot, cudaStream_t st) {
+    const Plan &P = ctx->plan;
+    a.u = cur;
+    a.un = nxt;
+    a.dd = dcur;
+    a.n = n;
+    a.a_out = a_slot(n);
+    int rc;
+    if (blocking && n + 1 < n_end) {
+        a.dd_out = dnxt;
+        a.a_out2 = a.a_out ? a_slot(n + 1) : nullptr;
+        TileMaps M;
+        if ((rc = pair_maps(ctx, a, &M))) return rc;
+        launch_fwd_pair(a, active_tiles(P, n), M, st);
+        ctx->stats.kernel_launches++;
+        ctx->stats.cell_updates += active_cells(P, n, ctx->NZ) + active_cells(P, n + 1, ctx->NZ);
+        std::swap(cur, nxt);
+        std::swap(dcur, dnxt);
+        return 2;
+    }
+    a.dd_out = a.a_out2 = nullptr;
+    if ((rc = fwd_step(ctx, a, active_tiles(P, n), L, st))) return rc;
+    ctx->stats.kernel_launches++;
+    ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
+    std::swap(cur, nxt);
+    return 1;
+}
+
+// Forward pass over all steps.  State pools uA (u^0), uB (scratch), dd
+// (D^0) and dd2 (scratch) must be zeroed by the caller.  d (nullable)
+// receives samples; ck (nullable) receives (u^n, D^n) every K steps (K
+// even), two pools per checkpoint.
+int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, float *d, float *ck, int K,
+                cudaStream_t st) {
     const Plan &P = ctx->plan;
     FwdArgs a{};
     a.c = common(ctx);
-    float *cur = uA, *nxt = uB;
+    a.d = d;
+    float *cur = uA, *nxt = uB, *dcur = dd, *dnxt = dd2;
     const long long pool = P.pool_floats;
+    const bool blocking = time_blocking();
     const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
     phase_begin(ctx, 0, st);
-    for (int n = 0; n < P.nt_max; n++) {
-        const int nt = active_tiles(P, n);
-        a.u = cur;
-        a.un = nxt;
-        a.dd = dd;
-        a.d = d;
-        a.a_out = nullptr;
+    for (int n = 0; n < P.nt_max;) {
         if (ck && n % K == 0) {
             const long long j = n / K;
             a.ck_u = ck + (2 * j) * pool;
@@ -704,27 +763,26 @@ int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *d, float
         } else {
             a.ck_u = a.ck_d = nullptr;
         }
-        a.n = n;
-        int rc = fwd_step(ctx, a, nt, ctx->launch[0], st);
-        if (rc) return rc;
-        ctx->stats.kernel_launches++;
-        ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
-        std::swap(cur, nxt);
+        const int rc = forward_steps(ctx, a, n, P.nt_max, cur, nxt, dcur, dnxt, ctx->launch[0], blocking,
+                                     [](int) -> float * { return nullptr; }, st);
+        if (rc < 0) return rc;
+        n += rc;
     }
     phase_end(ctx, 0, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
     CK(cudaGetLastError());
     return DHFWI_OK;
 }
 
-// Backward sweep: recompute each segment from its checkpoint (u in the
-// checkpoint and the work pool w, D in place in the checkpoint), then the
-// adjoint steps over it with the data r injected; image accumulated in gpool.
-// Adjoint state pools nuA, nuB, nud must be zeroed by the caller.
-int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float *nuA, float *nuB, float *nud,
-                 float *gpool, const float *r, cudaStream_t st) {
+// Backward sweep: recompute each segment from its checkpoint (u and D start
+// in the checkpoint pools and alternate with the work pools w and w2), then
+// the adjoint steps over it with the data r injected; image accumulated in
+// gpool.  Adjoint state pools nuA, nuB, nud must be zeroed by the caller.
+int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float *w2, float *nuA, float *nuB,
+                 float *nud, float *gpool, const float *r, cudaStream_t st) {
     const Plan &P = ctx->plan;
     const long long pool = P.pool_floats;
     const int nseg = (P.nt_max + K - 1) / K;
+    const bool blocking = time_blocking();
     FwdArgs f{};
     f.c = common(ctx);
     AdjArgs b{};
@@ -737,21 +795,15 @@ int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float 
     phase_begin(ctx, 1, st);
     for (int js = nseg - 1; js >= 0; js--) {
         const int n0 = js * K, n1 = std::min(n0 + K, P.nt_max);
-        float *cur = ck + (2 * (long long)js) * pool;
-        float *nxt = w;
-        f.dd = ck + (2 * (long long)js + 1) * pool;
-        for (int n = n0; n < n1; n++) {
-            f.u = cur;
-            f.un = nxt;
-            f.a_out = abuf + (long long)(n - n0) * pool;
-            f.d = nullptr;
-            f.ck_u = f.ck_d = nullptr;
-            f.n = n;
-            int rc = fwd_step(ctx, f, active_tiles(P, n), ctx->launch[1], st);
-            if (rc) return rc;
-            ctx->stats.kernel_launches++;
-            ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
-            std::swap(cur, nxt);
+        float *cur = ck + (2 * (long long)js) * pool, *nxt = w;
+        float *dcur = ck + (2 * (long long)js + 1) * pool, *dnxt = w2;
+        f.d = nullptr;
+        f.ck_u = f.ck_d = nullptr;
+        auto slot = [&](int n) { return abuf + (long long)(n - n0) * pool; };
+        for (int n = n0; n < n1;) {
+            const int rc = forward_steps(ctx, f, n, n1, cur, nxt, dcur, dnxt, ctx->launch[1], blocking, slot, st);
+            if (rc < 0) return rc;
+            n += rc;
         }
         for (int k = n1; k >= n0 + 1; k--) {
             b.nu = ncur;
@@ -788,6 +840,7 @@ int ensure_backward_ws(dhfwi_ctx *ctx, int *K_out) {
         release(ctx->ck);
         release(ctx->abuf);
         K = std::max(K, (int)std::ceil(std::sqrt(2.0 * P.nt_max)));
+        K += K & 1;  // checkpoints at even steps: a two-step launch never straddles one
     }
     if (rc) return rc;
     *K_out = K;
@@ -903,8 +956,9 @@ int model_shots(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, floa
     const size_t pool = sizeof(float) * (size_t)ctx->plan.pool_floats;
     if ((rc = ensure(ctx, ctx->fields, NPOOLS * pool, "wavefield pools"))) return rc;
     float *uA = (float *)ctx->fields.p, *uB = uA + ctx->plan.pool_floats, *ud = uB + ctx->plan.pool_floats;
-    CK(cudaMemsetAsync(uA, 0, 3 * pool, st));
-    if ((rc = run_forward(ctx, uA, uB, ud, d_dev, nullptr, 1, st))) return rc;
+    float *ud2 = ud + ctx->plan.pool_floats;
+    CK(cudaMemsetAsync(uA, 0, 4 * pool, st));
+    if ((rc = run_forward(ctx, uA, uB, ud, ud2, d_dev, nullptr, 2, st))) return rc;
     return end_call(ctx);
 }
 
@@ -935,11 +989,11 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     // Checkpoints are staged back as halo tiles: their padding columns, which
     // no kernel writes, must read as zero.
     CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
-    if ((rc = run_forward(ctx, uA, uB, ud, dsyn, (float *)ctx->ck.p, K, st))) return rc;
+    if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, dsyn, (float *)ctx->ck.p, K, st))) return rc;
     float *r = (float *)ctx->rtmp.p;
     launch_residual(dsyn, d_obs_dev, r, (long long)nd, (double *)ctx->partial.p, RESID_BLOCKS, st);
     ctx->stats.kernel_launches++;
-    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, nuA, nuB, nud, gp, r, st)))
+    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, uB, nuA, nuB, nud, gp, r, st)))
         return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v_dev, 0, grad_dev, st);
@@ -1018,8 +1072,9 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
     // Checkpoints are staged back as halo tiles: their padding columns, which
     // no kernel writes, must read as zero.
     CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
-    if ((rc = run_forward(ctx, uA, uB, ud, nullptr, (float *)ctx->ck.p, K, st))) return rc;
-    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, nuA, nuB, nud, gp, d_dev, st)))
+    if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, nullptr, (float *)ctx->ck.p, K, st))) return rc;
+    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, uB, nuA, nuB, nud, gp, d_dev,
+                           st)))
         return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v0_dev, flags == DHFWI_REL, img_dev, st);

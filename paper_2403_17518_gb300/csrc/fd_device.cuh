@@ -57,11 +57,11 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
 // Difference-form D u for the two cells (row lzr, columns lxp, lxp+1) of a
 // thread, both lanes at once.  zc holds the two columns for rows lzr-4 ..
 // lzr+4 (index 4 = the cells).
-__device__ __forceinline__ f2 lap8x2(const STile &s, const float2 *zc, int lzr, int lxp) {
-    // Row segment: columns lxp .. lxp+9 (the cells sit at lxp+4, lxp+5).
-    const float2 *rp = reinterpret_cast<const float2 *>(&s[lzr + HALO][lxp]);
+// rp: the row segment of the two cells, columns x-4 .. x+5 as five float2
+// (the cells are x, x+1); zc: the two columns for rows -4 .. +4.
+__device__ __forceinline__ f2 lap8x2_seg(const float2 *rp, const float2 *zc) {
     const float2 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4];
-    // r0=(x-4,x-3) r1=(x-2,x-1) r2=(x,x+1) r3=(x+2,x+3) r4=(x+4,x+5), x = lxp+4
+    // r0=(x-4,x-3) r1=(x-2,x-1) r2=(x,x+1) r3=(x+2,x+3) r4=(x+4,x+5)
     const f2 u = pk(r2);
     const f2 m4 = pk(r0), p4 = pk(r4);
     const f2 m3 = pk2(r0.y, r1.x), p3 = pk2(r3.y, r4.x);
@@ -73,6 +73,10 @@ __device__ __forceinline__ f2 lap8x2(const STile &s, const float2 *zc, int lzr, 
     a = fma2(c2, add2(add2(sub2(p2, u), sub2(m2, u)), add2(sub2(pk(zc[6]), u), sub2(pk(zc[2]), u))), a);
     a = fma2(c1, add2(add2(sub2(p1, u), sub2(m1, u)), add2(sub2(pk(zc[5]), u), sub2(pk(zc[3]), u))), a);
     return a;
+}
+__device__ __forceinline__ f2 lap8x2(const STile &s, const float2 *zc, int lzr, int lxp) {
+    // Row segment: columns lxp .. lxp+9 (the cells sit at lxp+4, lxp+5).
+    return lap8x2_seg(reinterpret_cast<const float2 *>(&s[lzr + HALO][lxp]), zc);
 }
 
 // Source injection into lane 0 / 1 of a when the cell is the source node.

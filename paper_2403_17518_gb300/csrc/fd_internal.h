@@ -44,7 +44,7 @@ struct Tile {
 // Per-tile descriptor of the TMA-staged kernels: the tile and the fields of
 // its shot they read, denormalised so that one 80-byte copy gives them all
 // (no dependent shot-table load on a kernel's critical path).
-enum { TI_INTERIOR = 1, TI_FULL_FWD = 2 };
+enum { TI_INTERIOR = 1, TI_FULL_FWD = 2, TI_FULL2 = 4 };
 struct alignas(16) TileInfo {
     int slot, z0, x0;
     int mx;             // model-array column of the tile: (shot x0 & ~3) + x0, in copy mc
@@ -54,8 +54,11 @@ struct alignas(16) TileInfo {
     int wav_off, nrec;
     int rec_begin, rec_end;
     int flags;          // TI_INTERIOR: inside the sponge-free interior (all cells valid);
-                        // TI_FULL_FWD: interior and without the source node
-    int pad0, pad1;
+                        // TI_FULL_FWD: interior and without the source node;
+                        // TI_FULL2: the tile grown by HALO on every side is interior
+                        //           and holds no source node (two-step kernel)
+    int nt;             // record length of the shot
+    int pad1;
     long long foff, doff;
 };
 
@@ -112,6 +115,11 @@ struct FwdArgs {
     float *a_out;     // nullable: store a^n = D u^n + q^n (segment buffer slot)
     float *d;         // nullable: packed records, sample n written from u^{n+1}
     int n;
+    // Two-step kernel only (steps n and n+1 in one launch): D^n is read with a
+    // ring of neighbour cells, so D^{n+2} goes to another pool; u^{n+2} goes
+    // to un; a^{n+1} to a_out2; tiles of shots with nt = n+1 take one step.
+    float *dd_out;
+    float *a_out2;
 };
 
 // Adjoint step k for the scaled multiplier nu = kappa w lambda, which obeys
@@ -150,6 +158,13 @@ int step_variant_rows(int v);
 int step_variants(int kind);
 // Resident CTAs per SM of a step kernel; kind 0 forward, 1 adjoint, 2 Born.
 int step_occupancy(int kind, int variant, int store_a);
+
+// Two-step (time-blocked) TMA forward kernel (fd_tma2.cu): steps n and n+1
+// of the tiles active at step n.  maps: 0 u^n (HALO2 box), 1 D^n (halo box),
+// 2 kappa (model halo box).
+constexpr int HALO2 = 2 * HALO;
+void launch_fwd_pair(const FwdArgs &a, int ntiles, const TileMaps &maps, cudaStream_t s);
+int fwd_pair_occupancy();
 
 // TMA-staged step kernels (fd_tma.cu); variant >= FIRST_TMA_VARIANT.
 void launch_fwd_step_tma(const FwdArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s);
