@@ -5,12 +5,11 @@
 //
 // Per 64 x 64 tile the TMA stages u^n with an 8-cell halo (80 x 80) and D^n
 // and kappa with a 4-cell ring (72 x 72).  Step n is computed on the tile
-// grown by the ring (the core with two columns per thread and R rows, the
-// ring as 544 column pairs spread over the CTA), giving u^{n+1} on 72 x 72
-// in shared memory (zero outside the window: the Dirichlet boundary) and
-// D^{n+1} of the core in registers; step n+1 is then computed on the core
-// from them.  The ring cells are recomputed by each tile that needs them, so
-// tiles never exchange data within the launch; since they read D^n on their
+// grown by the ring (36 column pairs x 72 rows, 9 rows per thread), giving
+// u^{n+1} and D^{n+1} on 72 x 72 in shared memory (zero outside the window:
+// the Dirichlet boundary); step n+1 is then computed on the core from them.
+// The ring cells are recomputed by each tile that needs them, so tiles
+// never exchange data within the launch; since they read D^n on their
 // neighbours' cells, D^{n+2} goes to a second pool.  Every cell goes through
 // the same floating-point operations in the same order as in the one-step
 // kernels, so the results are bit-identical.
@@ -41,169 +40,149 @@ struct Fwd2Stage {
 constexpr unsigned kFwd2StageBytes = sizeof(UTile2) + 2 * sizeof(ETile);
 static_assert(sizeof(Fwd2Stage) == kFwd2StageBytes && sizeof(Fwd2Stage) % 128 == 0, "stage layout");
 constexpr int NS2 = 1;  // one stage per CTA; two CTAs per SM cover each other's loads
-constexpr size_t kFwd2Smem = NS2 * sizeof(Fwd2Stage) + sizeof(ETile) + sizeof(PipeTail);
-constexpr int RING_PAIRS = 2 * HALO * (E / 2) + 2 * TZ * (HALO / 2);  // 544 column pairs
-static_assert(RING_PAIRS == 544, "ring size");
+constexpr size_t kFwd2Smem = NS2 * sizeof(Fwd2Stage) + 2 * sizeof(ETile) + sizeof(PipeTail);
+// Thread layout: 288 threads.  Step n covers the 72 x 72 grown tile with
+// 36 column pairs x 8 blocks of R1 = 9 rows; step n+1 covers the 64 x 64
+// core with the first 256 threads, 32 column pairs x 8 blocks of R2 = 8 rows.
+constexpr int NT2 = 288, R1 = 9, R2 = 8, PAIRS1 = E / 2;
+static_assert(PAIRS1 * (E / R1) == NT2 && (TX / 2) * (TZ / R2) == 256, "thread layout");
 
-// Ring pair p -> extended coordinates (ez, ex) of its left cell (ex even).
-__device__ __forceinline__ void ring_pair(int p, int &ez, int &ex) {
-    constexpr int strip = HALO * (E / 2);  // 144 pairs in the top (bottom) strip
-    if (p < 2 * strip) {
-        const int q = p < strip ? p : p - strip;
-        ez = (p < strip ? 0 : TZ + HALO) + q / (E / 2);
-        ex = 2 * (q % (E / 2));
-    } else {
-        const int q = p - 2 * strip;
-        const int side = q / (TZ * (HALO / 2));  // 0 left, 1 right
-        const int r = q - side * TZ * (HALO / 2);
-        ez = HALO + r / (HALO / 2);
-        ex = (side ? TX + HALO : 0) + 2 * (r % (HALO / 2));
-    }
-}
-
-template <int R, bool STORE_A, bool FULL>
-__device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, ETile &V, const TileInfo &T, int lxp,
-                                          int lz0, int tid, bool two) {
-    constexpr int NT = 32 * (TZ / R);
+template <bool STORE_A, bool FULL>
+__device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, ETile &V, ETile &Dn, const TileInfo &T,
+                                          int tid, bool two) {
     const int NZ = A.c.NZ, nb = A.c.nb, nxw = T.nxw, pitch = T.pitch, n = A.n;
-    const int j = T.x0 + lxp;
-    const int i0 = T.z0 + lz0;
-    const long long cbase = T.foff + (long long)i0 * pitch + j;
-    const int nrow = FULL ? R : min(R, NZ - i0);
-    const bool ok = FULL || j < nxw, hi = FULL || j + 1 < nxw;
-    float q0 = 0.f, q1 = 0.f, wx0 = 1.f, wx1 = 1.f;
+    float q0 = 0.f, q1 = 0.f;
     if constexpr (!FULL) {
         q0 = A.c.wav[T.wav_off + n];
         q1 = two ? A.c.wav[T.wav_off + n + 1] : 0.f;
-        wx0 = sponge1(j, nxw, nb);
-        wx1 = sponge1(j + 1, nxw, nb);
     }
 
-    // ---- step n on the core -------------------------------------------
-    float2 zc[R + 2 * HALO];
-#pragma unroll
-    for (int r = 0; r < R + 2 * HALO; r++)
-        zc[r] = *reinterpret_cast<const float2 *>(&S.u[lz0 + HALO + r][lxp + HALO2]);
-    f2 dn1[R];
-#pragma unroll
-    for (int rr = 0; rr < R; rr++) {
-        const bool valid = ok && rr < nrow;
-        f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&S.u[lz0 + rr + HALO2][lxp + HALO]), zc + rr);
-        if constexpr (!FULL) a = inject(a, i0 + rr, j, T.sz, T.sx, q0);
-        const f2 u = pk(zc[rr + HALO]);
-        const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[lz0 + rr + HALO][lxp + HALO]));
-        const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]));
-        f2 dn, un;
-        if constexpr (FULL) {
-            dn = fma2(kv, a, dv);
-            un = add2(u, dn);
-        } else {
-            const float wz = sponge1(i0 + rr, NZ, nb);
-            const f2 w = pk2(wz * wx0, wz * wx1);
-            dn = keep_lo(mul2(w, fma2(kv, a, dv)), hi);
-            un = keep_lo(fma2(w, u, dn), hi);
-            if (!valid) dn = un = 0ull;
+    // ---- step n on the grown tile -----------------------------------------
+    {
+        const int ex = 2 * (tid % PAIRS1), ez0 = R1 * (tid / PAIRS1);
+        const int jj = T.x0 - HALO + ex;  // window column of lane 0
+        const bool core_x = ex >= HALO && ex < TX + HALO;
+        float wx0 = 1.f, wx1 = 1.f;
+        bool c0ok = true, c1ok = true;
+        if constexpr (!FULL) {
+            c0ok = jj >= 0 && jj < nxw;
+            c1ok = jj + 1 >= 0 && jj + 1 < nxw;
+            wx0 = sponge1(jj, nxw, nb);
+            wx1 = sponge1(jj + 1, nxw, nb);
         }
-        dn1[rr] = dn;
-        *reinterpret_cast<f2 *>(&V[lz0 + rr + HALO][lxp + HALO]) = un;
-        if (valid) {
-            const long long c = cbase + (long long)rr * pitch;
-            if (!STORE_A && A.ck_u) {
-                *reinterpret_cast<f2 *>(A.ck_u + c) = keep_lo(u, hi);
-                *reinterpret_cast<f2 *>(A.ck_d + c) = keep_lo(dv, hi);
+        float2 zc[R1 + 2 * HALO];
+#pragma unroll
+        for (int r = 0; r < R1 + 2 * HALO; r++) zc[r] = *reinterpret_cast<const float2 *>(&S.u[ez0 + r][ex + HALO]);
+#pragma unroll
+        for (int rr = 0; rr < R1; rr++) {
+            const int ez = ez0 + rr;
+            const int i = T.z0 - HALO + ez;
+            f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&S.u[ez + HALO][ex]), zc + rr);
+            const f2 u = pk(zc[rr + HALO]);
+            const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[ez][ex]));
+            const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[ez][ex]));
+            f2 dn, un;
+            bool v0 = true, v1 = true;
+            if constexpr (FULL) {
+                dn = fma2(kv, a, dv);
+                un = add2(u, dn);
+            } else {
+                const bool rok = i >= 0 && i < NZ;
+                v0 = rok && c0ok;
+                v1 = rok && c1ok;
+                a = inject(a, i, jj, T.sz, T.sx, q0);
+                const float wz = sponge1(i, NZ, nb);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                dn = keep_lo(mul2(w, fma2(kv, a, dv)), v1);
+                un = keep_lo(fma2(w, u, dn), v1);
+                if (!v0) dn = un = 0ull;
             }
-            if constexpr (STORE_A) *reinterpret_cast<f2 *>(A.a_out + c) = keep_lo(a, hi);
+            *reinterpret_cast<f2 *>(&V[ez][ex]) = un;
+            *reinterpret_cast<f2 *>(&Dn[ez][ex]) = dn;
+            if (core_x && ez >= HALO && ez < TZ + HALO && v0) {
+                const long long c = T.foff + (long long)i * pitch + jj;
+                if (!STORE_A && A.ck_u) {
+                    *reinterpret_cast<f2 *>(A.ck_u + c) = keep_lo(u, v1);
+                    *reinterpret_cast<f2 *>(A.ck_d + c) = keep_lo(dv, v1);
+                }
+                if constexpr (STORE_A) *reinterpret_cast<f2 *>(A.a_out + c) = keep_lo(a, v1);
+            }
         }
     }
-
-    // ---- step n on the ring ----------------------------------------------
-    for (int p = tid; p < RING_PAIRS; p += NT) {
-        int ez, ex;
-        ring_pair(p, ez, ex);
-        float2 zr[2 * HALO + 1];
-#pragma unroll
-        for (int r = 0; r <= 2 * HALO; r++) zr[r] = *reinterpret_cast<const float2 *>(&S.u[ez + r][ex + HALO]);
-        f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&S.u[ez + HALO][ex]), zr);
-        const f2 u = pk(zr[HALO]);
-        const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[ez][ex]));
-        const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[ez][ex]));
-        f2 un;
-        if constexpr (FULL) {
-            un = add2(u, fma2(kv, a, dv));
-        } else {
-            const int i = T.z0 - HALO + ez, jj = T.x0 - HALO + ex;
-            const bool rok = i >= 0 && i < NZ;
-            const bool v0 = rok && jj >= 0 && jj < nxw, v1 = rok && jj + 1 >= 0 && jj + 1 < nxw;
-            a = inject(a, i, jj, T.sz, T.sx, q0);
-            const float wz = sponge1(i, NZ, nb);
-            const f2 w = pk2(wz * sponge1(jj, nxw, nb), wz * sponge1(jj + 1, nxw, nb));
-            const f2 dn = mul2(w, fma2(kv, a, dv));
-            un = fma2(w, u, dn);
-            if (!v0) un &= 0xffffffff00000000ull;
-            if (!v1) un &= 0x00000000ffffffffull;
-        }
-        *reinterpret_cast<f2 *>(&V[ez][ex]) = un;
-    }
-    __syncthreads();  // u^{n+1} complete on the grown tile
+    __syncthreads();  // u^{n+1}, D^{n+1} complete on the grown tile
 
     // Receivers: sample n is u^{n+1}.
     if (!STORE_A && A.d) {
-        for (int e = T.rec_begin + tid; e < T.rec_end; e += NT) {
+        for (int e = T.rec_begin + tid; e < T.rec_end; e += NT2) {
             const TileRec tr = A.c.recs[e];
             A.d[T.doff + (long long)n * T.nrec + tr.r] = V[tr.cell / TX + HALO][tr.cell % TX + HALO];
         }
     }
+
+    // ---- step n+1 on the core (threads 0..255) ---------------------------------
+    const int lxp = 2 * (tid % 32), lz0 = R2 * (tid / 32);
+    const bool worker = tid < 256;
+    const int j = T.x0 + lxp;
+    const int i0 = T.z0 + lz0;
+    const long long cbase = T.foff + (long long)i0 * pitch + j;
+    const int nrow = FULL ? R2 : min(R2, NZ - i0);
+    const bool ok = worker && (FULL || j < nxw), hi = FULL || j + 1 < nxw;
     if (!two) {  // the record ends at n+1: store u^{n+1}, D^{n+1}
 #pragma unroll
-        for (int rr = 0; rr < R; rr++) {
+        for (int rr = 0; rr < R2; rr++) {
             if (ok && rr < nrow) {
                 const long long c = cbase + (long long)rr * pitch;
                 *reinterpret_cast<f2 *>(A.un + c) = *reinterpret_cast<const f2 *>(&V[lz0 + rr + HALO][lxp + HALO]);
-                *reinterpret_cast<f2 *>(A.dd_out + c) = dn1[rr];
+                *reinterpret_cast<f2 *>(A.dd_out + c) = *reinterpret_cast<const f2 *>(&Dn[lz0 + rr + HALO][lxp + HALO]);
             }
         }
         return;
     }
-
-    // ---- step n+1 on the core ---------------------------------------------
-#pragma unroll
-    for (int r = 0; r < R + 2 * HALO; r++) zc[r] = *reinterpret_cast<const float2 *>(&V[lz0 + r][lxp + HALO]);
-#pragma unroll
-    for (int rr = 0; rr < R; rr++) {
-        if (!(ok && rr < nrow)) continue;
-        f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&V[lz0 + rr + HALO][lxp]), zc + rr);
-        if constexpr (!FULL) a = inject(a, i0 + rr, j, T.sz, T.sx, q1);
-        const f2 u = pk(zc[rr + HALO]);
-        const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]));
-        f2 dn, un;
-        if constexpr (FULL) {
-            dn = fma2(kv, a, dn1[rr]);
-            un = add2(u, dn);
-        } else {
-            const float wz = sponge1(i0 + rr, NZ, nb);
-            const f2 w = pk2(wz * wx0, wz * wx1);
-            dn = keep_lo(mul2(w, fma2(kv, a, dn1[rr])), hi);
-            un = keep_lo(fma2(w, u, dn), hi);
+    if (worker) {
+        float wx0 = 1.f, wx1 = 1.f;
+        if constexpr (!FULL) {
+            wx0 = sponge1(j, nxw, nb);
+            wx1 = sponge1(j + 1, nxw, nb);
         }
-        const long long c = cbase + (long long)rr * pitch;
-        *reinterpret_cast<f2 *>(A.dd_out + c) = dn;
-        *reinterpret_cast<f2 *>(A.un + c) = un;
-        if constexpr (STORE_A) *reinterpret_cast<f2 *>(A.a_out2 + c) = keep_lo(a, hi);
+        float2 zc[R2 + 2 * HALO];
+#pragma unroll
+        for (int r = 0; r < R2 + 2 * HALO; r++) zc[r] = *reinterpret_cast<const float2 *>(&V[lz0 + r][lxp + HALO]);
+#pragma unroll
+        for (int rr = 0; rr < R2; rr++) {
+            if (!(ok && rr < nrow)) continue;
+            f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&V[lz0 + rr + HALO][lxp]), zc + rr);
+            if constexpr (!FULL) a = inject(a, i0 + rr, j, T.sz, T.sx, q1);
+            const f2 u = pk(zc[rr + HALO]);
+            const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]));
+            const f2 d1 = *reinterpret_cast<const f2 *>(&Dn[lz0 + rr + HALO][lxp + HALO]);
+            f2 dn, un;
+            if constexpr (FULL) {
+                dn = fma2(kv, a, d1);
+                un = add2(u, dn);
+            } else {
+                const float wz = sponge1(i0 + rr, NZ, nb);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                dn = keep_lo(mul2(w, fma2(kv, a, d1)), hi);
+                un = keep_lo(fma2(w, u, dn), hi);
+            }
+            const long long c = cbase + (long long)rr * pitch;
+            *reinterpret_cast<f2 *>(A.dd_out + c) = dn;
+            *reinterpret_cast<f2 *>(A.un + c) = un;
+            if constexpr (STORE_A) *reinterpret_cast<f2 *>(A.a_out2 + c) = keep_lo(a, hi);
+        }
     }
     // Receivers: sample n+1 is u^{n+2}, read back from the pool.
-    if (!STORE_A && A.d && T.rec_end > T.rec_begin) sample_from_pool<NT>(A.c, T, A.un, A.d, n + 1);
+    if (!STORE_A && A.d && T.rec_end > T.rec_begin) sample_from_pool<NT2>(A.c, T, A.un, A.d, n + 1);
 }
 
 template <bool STORE_A>
-__global__ void __launch_bounds__(256, 1) fwd_pair_kernel(FwdArgs A, const __grid_constant__ TileMaps M, int ntiles) {
-    constexpr int R = 8;
+__global__ void __launch_bounds__(NT2, 2) fwd_pair_kernel(FwdArgs A, const __grid_constant__ TileMaps M, int ntiles) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Fwd2Stage *st = reinterpret_cast<Fwd2Stage *>(smem_raw);
     ETile &V = *reinterpret_cast<ETile *>(smem_raw + NS2 * sizeof(Fwd2Stage));
-    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + NS2 * sizeof(Fwd2Stage) + sizeof(ETile));
+    ETile &Dn = *reinterpret_cast<ETile *>(smem_raw + NS2 * sizeof(Fwd2Stage) + sizeof(ETile));
+    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + NS2 * sizeof(Fwd2Stage) + 2 * sizeof(ETile));
     const int tid = threadIdx.x + threadIdx.y * 32;
-    const int lxp = 2 * threadIdx.x;
-    const int lz0 = threadIdx.y * R;
     run_tiles<NS2>(
         A.c, kFwd2StageBytes, ntiles, st, tail,
         [&](Fwd2Stage &S, unsigned bar, int4 co, int mc) {
@@ -213,8 +192,8 @@ __global__ void __launch_bounds__(256, 1) fwd_pair_kernel(FwdArgs A, const __gri
         },
         [&](const Fwd2Stage &S, const TileInfo &T) {
             const bool two = T.nt > A.n + 1;
-            if ((T.flags & TI_FULL2) && two) pair_tile<R, STORE_A, true>(A, S, V, T, lxp, lz0, tid, true);
-            else pair_tile<R, STORE_A, false>(A, S, V, T, lxp, lz0, tid, two);
+            if ((T.flags & TI_FULL2) && two) pair_tile<STORE_A, true>(A, S, V, Dn, T, tid, true);
+            else pair_tile<STORE_A, false>(A, S, V, Dn, T, tid, two);
         });
 }
 
@@ -222,7 +201,7 @@ template <typename K>
 void launch_pdl2(K kernel, int grid, const FwdArgs &a, const TileMaps &maps, int ntiles, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(32, TZ / 8);
+    cfg.blockDim = dim3(32, NT2 / 32);
     cfg.dynamicSmemBytes = kFwd2Smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -236,7 +215,7 @@ void launch_pdl2(K kernel, int grid, const FwdArgs &a, const TileMaps &maps, int
 int occupancy_of(const void *fn) {
     int n = 0;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwd2Smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, kFwd2Smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NT2, kFwd2Smem);
     return n < 1 ? 1 : n;
 }
 
