@@ -39,17 +39,18 @@ struct Fwd2Stage {
 };
 constexpr unsigned kFwd2StageBytes = sizeof(UTile2) + 2 * sizeof(ETile);
 static_assert(sizeof(Fwd2Stage) == kFwd2StageBytes && sizeof(Fwd2Stage) % 128 == 0, "stage layout");
-constexpr int NS2 = 1;  // one stage per CTA; two CTAs per SM cover each other's loads
-constexpr size_t kFwd2Smem = NS2 * sizeof(Fwd2Stage) + 2 * sizeof(ETile) + sizeof(PipeTail);
+constexpr size_t kFwd2Smem = sizeof(Fwd2Stage) + 2 * sizeof(ETile) + sizeof(PipeTail);
 // Thread layout: 288 threads.  Step n covers the 72 x 72 grown tile with
 // 36 column pairs x 8 blocks of R1 = 9 rows; step n+1 covers the 64 x 64
 // core with the first 256 threads, 32 column pairs x 8 blocks of R2 = 8 rows.
 constexpr int NT2 = 288, R1 = 9, R2 = 8, PAIRS1 = E / 2;
 static_assert(PAIRS1 * (E / R1) == NT2 && (TX / 2) * (TZ / R2) == 256, "thread layout");
 
-template <bool STORE_A, bool FULL>
+// mid(): called by every thread once the stage is no longer read (after
+// step n; kappa of the core is then in registers): the leader refills it.
+template <bool STORE_A, bool FULL, class MidFn>
 __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, ETile &V, ETile &Dn, const TileInfo &T,
-                                          int tid, bool two) {
+                                          int tid, bool two, MidFn mid) {
     const int NZ = A.c.NZ, nb = A.c.nb, nxw = T.nxw, pitch = T.pitch, n = A.n;
     float q0 = 0.f, q1 = 0.f;
     if constexpr (!FULL) {
@@ -111,6 +112,15 @@ __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, 
     }
     __syncthreads();  // u^{n+1}, D^{n+1} complete on the grown tile
 
+    // kappa of this thread's core cells for step n+1, then the stage is free.
+    const int lxp = 2 * (tid % 32), lz0 = R2 * (tid / 32);
+    const bool worker = tid < 256;
+    f2 kv2[R2];
+#pragma unroll
+    for (int rr = 0; rr < R2; rr++)
+        kv2[rr] = worker ? *reinterpret_cast<const f2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]) : 0ull;
+    mid();
+
     // Receivers: sample n is u^{n+1}.
     if (!STORE_A && A.d) {
         for (int e = T.rec_begin + tid; e < T.rec_end; e += NT2) {
@@ -120,8 +130,6 @@ __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, 
     }
 
     // ---- step n+1 on the core (threads 0..255) ---------------------------------
-    const int lxp = 2 * (tid % 32), lz0 = R2 * (tid / 32);
-    const bool worker = tid < 256;
     const int j = T.x0 + lxp;
     const int i0 = T.z0 + lz0;
     const long long cbase = T.foff + (long long)i0 * pitch + j;
@@ -153,7 +161,7 @@ __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, 
             f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&V[lz0 + rr + HALO][lxp]), zc + rr);
             if constexpr (!FULL) a = inject(a, i0 + rr, j, T.sz, T.sx, q1);
             const f2 u = pk(zc[rr + HALO]);
-            const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]));
+            const f2 kv = kv2[rr];
             const f2 d1 = *reinterpret_cast<const f2 *>(&Dn[lz0 + rr + HALO][lxp + HALO]);
             f2 dn, un;
             if constexpr (FULL) {
@@ -175,26 +183,70 @@ __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, 
     if (!STORE_A && A.d && T.rec_end > T.rec_begin) sample_from_pool<NT2>(A.c, T, A.un, A.d, n + 1);
 }
 
+// Tile loop: one stage, refilled in the middle of a tile (see mid() in
+// pair_tile) so that the next tile's loads overlap step n+1; the descriptor
+// slot is refilled at the end of the tile.  Waits bounded as in run_tiles.
 template <bool STORE_A>
 __global__ void __launch_bounds__(NT2, 2) fwd_pair_kernel(FwdArgs A, const __grid_constant__ TileMaps M, int ntiles) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Fwd2Stage *st = reinterpret_cast<Fwd2Stage *>(smem_raw);
-    ETile &V = *reinterpret_cast<ETile *>(smem_raw + NS2 * sizeof(Fwd2Stage));
-    ETile &Dn = *reinterpret_cast<ETile *>(smem_raw + NS2 * sizeof(Fwd2Stage) + sizeof(ETile));
-    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + NS2 * sizeof(Fwd2Stage) + 2 * sizeof(ETile));
+    Fwd2Stage &S = *reinterpret_cast<Fwd2Stage *>(smem_raw);
+    ETile &V = *reinterpret_cast<ETile *>(smem_raw + sizeof(Fwd2Stage));
+    ETile &Dn = *reinterpret_cast<ETile *>(smem_raw + sizeof(Fwd2Stage) + sizeof(ETile));
+    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + sizeof(Fwd2Stage) + 2 * sizeof(ETile));
     const int tid = threadIdx.x + threadIdx.y * 32;
-    run_tiles<NS2>(
-        A.c, kFwd2StageBytes, ntiles, st, tail,
-        [&](Fwd2Stage &S, unsigned bar, int4 co, int mc) {
-            tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO2, co.y - HALO2, co.x, bar);
-            tma_load_3d(smem_u32(&S.d), &M.m[1], co.z - HALO, co.y - HALO, co.x, bar);
-            tma_load_3d(smem_u32(&S.k), &M.m[2], co.w - HALO, co.y - HALO, mc, bar);
-        },
-        [&](const Fwd2Stage &S, const TileInfo &T) {
-            const bool two = T.nt > A.n + 1;
-            if ((T.flags & TI_FULL2) && two) pair_tile<STORE_A, true>(A, S, V, Dn, T, tid, true);
-            else pair_tile<STORE_A, false>(A, S, V, Dn, T, tid, two);
-        });
+    const bool leader = tid == 0;
+    const unsigned bar = smem_u32(&tail->bar[0]);
+    const int b = blockIdx.x, g = gridDim.x;
+    int4 co = make_int4(0, 0, 0, 0);
+    int mc = 0;
+    if (smem_u32(&S) & 127u) {
+        if (leader) atomicExch(A.c.tflag, 2u);
+        return;
+    }
+    if (leader) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fetch_coords(A.c.infos, b, co, mc);
+        copy_desc(&tail->desc[0], &A.c.infos[b]);
+    }
+    griddep_wait();
+    griddep_launch_dependents();
+    auto issue = [&]() {
+        fence_proxy_async();
+        mbar_expect_tx(bar, kFwd2StageBytes);
+        tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO2, co.y - HALO2, co.x, bar);
+        tma_load_3d(smem_u32(&S.d), &M.m[1], co.z - HALO, co.y - HALO, co.x, bar);
+        tma_load_3d(smem_u32(&S.k), &M.m[2], co.w - HALO, co.y - HALO, mc, bar);
+    };
+    if (leader) {
+        issue();
+        if (b + g < ntiles) fetch_coords(A.c.infos, b + g, co, mc);
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    for (int tix = b; tix < ntiles; tix += g) {
+        const bool landed = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (leader) cp_async_wait_all();
+        if (__syncthreads_or(!landed)) {
+            if (leader) atomicExch(A.c.tflag, 1u);
+            return;
+        }
+        const bool more = tix + g < ntiles;
+        auto mid = [&]() {
+            __syncthreads();  // every thread is done with the stage
+            if (leader && more) issue();
+        };
+        const TileInfo &T = tail->desc[0];
+        const bool two = T.nt > A.n + 1;
+        if ((T.flags & TI_FULL2) && two) pair_tile<STORE_A, true>(A, S, V, Dn, T, tid, true, mid);
+        else pair_tile<STORE_A, false>(A, S, V, Dn, T, tid, two, mid);
+        __syncthreads();  // the descriptor, V and Dn are free
+        if (leader && more) {
+            copy_desc(&tail->desc[0], &A.c.infos[tix + g]);
+            if (tix + 2 * g < ntiles) fetch_coords(A.c.infos, tix + 2 * g, co, mc);
+        }
+    }
 }
 
 template <typename K>
