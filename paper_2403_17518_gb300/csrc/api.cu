@@ -39,11 +39,13 @@ struct Plan {
     std::vector<TileRec> recs;
     std::vector<TileInfo> infos;       // per tile, same order (no sentinel)
     std::vector<int> tiles_prefix;     // tiles of the first m slots
+    std::vector<int> rtiles;           // tiles with receivers, in tile order
+    std::vector<int> rtiles_prefix;    // of those, the tiles of the first m slots
     long long pool_floats = 0;
     int pitch = 0;                     // row pitch of every window in a pool
     long long n_data = 0;
     long long cells_per_step_all = 0;  // padded cells of all shots
-    DevBuf d_shots, d_tiles, d_recs, d_slot_of, d_wav, d_infos;
+    DevBuf d_shots, d_tiles, d_recs, d_slot_of, d_wav, d_infos, d_rtiles;
 };
 
 }  // namespace
@@ -82,7 +84,7 @@ namespace {
 
 constexpr int RESID_BLOCKS = 1024;
 constexpr int TFLAG_WORD = 4;  // status word set by a timed-out TMA wait
-constexpr int NPOOLS = 8;  // field pools: u (2) + D, nu (2) + D_nu, image, second D
+constexpr int NPOOLS = 9;  // field pools: u (2) + D, nu (2) + D_nu, image, second D, second D_nu
 
 int fail(dhfwi_ctx *ctx, int code, const std::string &msg) {
     if (ctx) ctx->err = msg;
@@ -253,6 +255,8 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
     P.tiles.clear();
     P.recs.clear();
     P.tiles_prefix.assign(ns + 1, 0);
+    P.rtiles.clear();
+    P.rtiles_prefix.assign(ns + 1, 0);
     // One row pitch for all windows: a pool is then a [slot][NZ][pitch] array
     // that a single 3-D tensor map describes.
     int pitch = POOL_ALIGN;
@@ -290,9 +294,21 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
         for (int tz = 0; tz < ntz; tz++)
             for (int tx = 0; tx < ntx; tx++) {
                 P.tiles.push_back(Tile{k, tz * TZ, tx * TX, (int)P.recs.size()});
-                for (const TileRec &e : bucket[(size_t)tz * ntx + tx]) P.recs.push_back(e);
+                // By cell, then receiver: the adjoint sums receivers sharing a
+                // cell in this order (deterministic injection).
+                std::vector<TileRec> &bk = bucket[(size_t)tz * ntx + tx];
+                std::sort(bk.begin(), bk.end(), [](const TileRec &a, const TileRec &b) {
+                    return a.cell < b.cell || (a.cell == b.cell && a.r < b.r);
+                });
+                for (const TileRec &e : bk) P.recs.push_back(e);
             }
         P.tiles_prefix[k + 1] = (int)P.tiles.size();
+        for (int ti = P.tiles_prefix[k]; ti < P.tiles_prefix[k + 1]; ti++) {
+            const int rb = P.tiles[ti].rec_begin;
+            const int re = ti + 1 < (int)P.tiles.size() ? P.tiles[ti + 1].rec_begin : (int)P.recs.size();
+            if (re > rb) P.rtiles.push_back(ti);
+        }
+        P.rtiles_prefix[k + 1] = (int)P.rtiles.size();
     }
     P.tiles.push_back(Tile{0, 0, 0, (int)P.recs.size()});  // sentinel
     P.infos.resize(P.tiles.size() - 1);
@@ -324,7 +340,7 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
         const bool src2 = sd.sz >= t.z0 - HALO && sd.sz < t.z0 + TZ + HALO && sd.sx >= t.x0 - HALO &&
                           sd.sx < t.x0 + TX + HALO;
         T.flags = (interior ? TI_INTERIOR : 0) | (interior && !src ? TI_FULL_FWD : 0) |
-                  (interior2 && !src2 ? TI_FULL2 : 0);
+                  (interior2 && !src2 ? TI_FULL2 : 0) | (interior2 ? TI_INTERIOR2 : 0);
         T.nt = sd.nt;
     }
     P.pool_floats = foff;
@@ -336,6 +352,7 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
     if ((rc = upload(ctx, P.d_slot_of, P.slot_of_shot, "slot table"))) return rc;
     if ((rc = upload(ctx, P.d_wav, wav, "wavelets"))) return rc;
     if ((rc = upload(ctx, P.d_infos, P.infos, "tile descriptors"))) return rc;
+    if ((rc = upload(ctx, P.d_rtiles, P.rtiles, "receiver tile list"))) return rc;
     P.hash = h;
     return DHFWI_OK;
 }
@@ -350,6 +367,17 @@ inline int active_tiles(const Plan &P, int n) {
         else hi = mid;
     }
     return P.tiles_prefix[lo];
+}
+
+// Number of slots (shots) with nt > n.
+inline int active_slots(const Plan &P, int n) {
+    int lo = 0, hi = P.n_shots;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (P.nt_sorted[mid] > n) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 long long active_cells(const Plan &P, int n, int NZ) {
@@ -705,6 +733,15 @@ int pair_maps(dhfwi_ctx *ctx, const FwdArgs &a, TileMaps *M) {
     return tensor_map(ctx, a.c.kap, MAP_MODEL_HALO, &M->m[2]);
 }
 
+// Maps of a two-step adjoint launch (nu^{k+1} with the doubled halo, D_nu
+// with its ring, kappa with its ring).
+int adj_pair_maps(dhfwi_ctx *ctx, const AdjArgs &b, TileMaps *M) {
+    int rc;
+    if ((rc = tensor_map(ctx, b.nu, MAP_POOL_HALO2, &M->m[0]))) return rc;
+    if ((rc = tensor_map(ctx, b.dd, MAP_POOL_HALO, &M->m[1]))) return rc;
+    return tensor_map(ctx, b.c.kap, MAP_MODEL_HALO, &M->m[2]);
+}
+
 // Advances the forward state from step n: two steps with one two-step launch
 // when blocking is on and n + 1 < n_end, else one.  State: u in *cur (next
 // in *nxt), D in *dcur (*dnxt: the two-step kernel's output pool).  a_slot(n)
@@ -776,9 +813,10 @@ int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, flo
 // Backward sweep: recompute each segment from its checkpoint (u and D start
 // in the checkpoint pools and alternate with the work pools w and w2), then
 // the adjoint steps over it with the data r injected; image accumulated in
-// gpool.  Adjoint state pools nuA, nuB, nud must be zeroed by the caller.
+// gpool.  Adjoint state pools nuA, nuB, nud, nud2 must be zeroed by the
+// caller; with time blocking the adjoint also advances two steps per launch.
 int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float *w2, float *nuA, float *nuB,
-                 float *nud, float *gpool, const float *r, cudaStream_t st) {
+                 float *nud, float *nud2, float *gpool, const float *r, cudaStream_t st) {
     const Plan &P = ctx->plan;
     const long long pool = P.pool_floats;
     const int nseg = (P.nt_max + K - 1) / K;
@@ -789,8 +827,7 @@ int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float 
     b.c = f.c;
     b.r = r;
     b.g = gpool;
-    b.dd = nud;
-    float *ncur = nuA, *nnxt = nuB;
+    float *ncur = nuA, *nnxt = nuB, *dcur_nu = nud, *dnxt_nu = nud2;
     const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
     phase_begin(ctx, 1, st);
     for (int js = nseg - 1; js >= 0; js--) {
@@ -805,16 +842,37 @@ int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float 
             if (rc < 0) return rc;
             n += rc;
         }
-        for (int k = n1; k >= n0 + 1; k--) {
+        for (int k = n1; k >= n0 + 1;) {
             b.nu = ncur;
             b.nun = nnxt;
+            b.dd = dcur_nu;
             b.a = abuf + (long long)(k - 1 - n0) * pool;
             b.k = k;
+            if (blocking && k - 1 >= n0 + 1) {
+                // Steps k and k-1: the data of step k go into D_nu first.
+                const int nrt = P.rtiles_prefix[active_slots(P, k - 1)];
+                launch_adj_inject(b, (const int *)P.d_rtiles.p, nrt, st);
+                b.dd_out = dnxt_nu;
+                b.a2 = abuf + (long long)(k - 2 - n0) * pool;
+                TileMaps M;
+                int rc = adj_pair_maps(ctx, b, &M);
+                if (rc) return rc;
+                launch_adj_pair(b, active_tiles(P, k - 2), M, st);
+                ctx->stats.kernel_launches += 1 + (nrt > 0);
+                ctx->stats.cell_updates += active_cells(P, k - 1, ctx->NZ) + active_cells(P, k - 2, ctx->NZ);
+                std::swap(ncur, nnxt);
+                std::swap(dcur_nu, dnxt_nu);
+                k -= 2;
+                continue;
+            }
+            b.dd_out = nullptr;
+            b.a2 = nullptr;
             int rc = adj_step(ctx, b, active_tiles(P, k - 1), ctx->launch[2], st);
             if (rc) return rc;
             ctx->stats.kernel_launches++;
             ctx->stats.cell_updates += active_cells(P, k - 1, ctx->NZ);
             std::swap(ncur, nnxt);
+            k--;
         }
         CK(cudaGetLastError());
     }
@@ -907,7 +965,8 @@ void dhfwi_destroy(dhfwi_ctx *ctx) {
     cudaSetDevice(ctx->device);
     DevBuf *bufs[] = {&ctx->kap, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
                       &ctx->ck, &ctx->abuf, &ctx->dtmp, &ctx->rtmp, &ctx->plan.d_shots, &ctx->plan.d_tiles,
-                      &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav, &ctx->plan.d_infos};
+                      &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav, &ctx->plan.d_infos,
+                      &ctx->plan.d_rtiles};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_partial) cudaFreeHost(ctx->h_partial);
@@ -993,7 +1052,8 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     float *r = (float *)ctx->rtmp.p;
     launch_residual(dsyn, d_obs_dev, r, (long long)nd, (double *)ctx->partial.p, RESID_BLOCKS, st);
     ctx->stats.kernel_launches++;
-    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, uB, nuA, nuB, nud, gp, r, st)))
+    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, uB, nuA, nuB, nud, F + 8 * pool, gp,
+                           r, st)))
         return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v_dev, 0, grad_dev, st);
@@ -1073,8 +1133,8 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
     // no kernel writes, must read as zero.
     CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
     if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, nullptr, (float *)ctx->ck.p, K, st))) return rc;
-    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, uB, nuA, nuB, nud, gp, d_dev,
-                           st)))
+    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, uB, nuA, nuB, nud, F + 8 * pool, gp,
+                           d_dev, st)))
         return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v0_dev, flags == DHFWI_REL, img_dev, st);

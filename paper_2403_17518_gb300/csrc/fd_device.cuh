@@ -119,6 +119,32 @@ __device__ __forceinline__ const float *model_base(const float *arr, const StepC
 template <typename T>
 __device__ __forceinline__ T &sm2(float *p) { return *reinterpret_cast<T *>(p); }
 
+// Receiver injection of one adjoint step into a TZ x TX tile: inj[cell] =
+// the sum of the data sample rk[r] over the tile's receivers at that cell,
+// zero elsewhere.  A tile's receiver entries are sorted by cell, then by
+// receiver, so duplicates are summed in a fixed order by the thread that
+// owns the first entry of their cell (deterministic, no atomics).  Ends
+// with a barrier.
+__device__ __forceinline__ float receiver_sum(const TileRec *__restrict__ recs, int e, int re,
+                                              const float *__restrict__ rk) {
+    const int cell = recs[e].cell;
+    float s = rk[recs[e].r];
+    for (int f = e + 1; f < re && recs[f].cell == cell; f++) s += rk[recs[f].r];
+    return s;
+}
+template <int NT>
+__device__ __forceinline__ void build_injection(CTile &inj, const TileRec *__restrict__ recs, int rb, int re,
+                                                const float *__restrict__ rk, int tid) {
+    for (int e = tid; e < TZ * TX; e += NT) (&inj[0][0])[e] = 0.f;
+    __syncthreads();
+    for (int e = rb + tid; e < re; e += NT)
+        if (e == rb || recs[e - 1].cell != recs[e].cell) {
+            const int cell = recs[e].cell;
+            inj[cell / TX][cell % TX] = receiver_sum(recs, e, re, rk);
+        }
+    __syncthreads();
+}
+
 // Lane 1 (column j+1) cleared when it lies past the window (odd widths), so
 // the padding columns of a field pool stay zero: tiles staged straight from
 // a pool read them as the zero boundary.

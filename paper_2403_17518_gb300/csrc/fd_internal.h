@@ -44,7 +44,7 @@ struct Tile {
 // Per-tile descriptor of the TMA-staged kernels: the tile and the fields of
 // its shot they read, denormalised so that one 80-byte copy gives them all
 // (no dependent shot-table load on a kernel's critical path).
-enum { TI_INTERIOR = 1, TI_FULL_FWD = 2, TI_FULL2 = 4 };
+enum { TI_INTERIOR = 1, TI_FULL_FWD = 2, TI_FULL2 = 4, TI_INTERIOR2 = 8 };
 struct alignas(16) TileInfo {
     int slot, z0, x0;
     int mx;             // model-array column of the tile: (shot x0 & ~3) + x0, in copy mc
@@ -56,7 +56,8 @@ struct alignas(16) TileInfo {
     int flags;          // TI_INTERIOR: inside the sponge-free interior (all cells valid);
                         // TI_FULL_FWD: interior and without the source node;
                         // TI_FULL2: the tile grown by HALO on every side is interior
-                        //           and holds no source node (two-step kernel)
+                        //           and holds no source node (two-step kernel);
+                        // TI_INTERIOR2: the grown tile is interior (two-step adjoint)
     int nt;             // record length of the shot
     int pad1;
     long long foff, doff;
@@ -134,6 +135,11 @@ struct AdjArgs {
     const float *a;       // pool: a^{k-1} of the background forward field
     float *g;             // pool: per-shot image accumulator, += a^{k-1} nu^k
     int k;
+    // Two-step kernel only (steps k and k-1 in one launch): dd holds D_nu^{k+1}
+    // with the data of step k already injected (launch_adj_inject), D_nu^{k-1}
+    // goes to dd_out, nu^{k-1} to nun, a2 = a^{k-2}.
+    float *dd_out;
+    const float *a2;
 };
 
 // Born joint step n: background u0 and scattered p advance together.
@@ -165,6 +171,13 @@ int step_occupancy(int kind, int variant, int store_a);
 constexpr int HALO2 = 2 * HALO;
 void launch_fwd_pair(const FwdArgs &a, int ntiles, const TileMaps &maps, cudaStream_t s);
 int fwd_pair_occupancy();
+// Two-step adjoint (fd_tma2.cu): steps k and k-1 of the tiles active at step
+// k-1; maps: 0 nu^{k+1} (HALO2 box), 1 D_nu (halo box), 2 kappa (model halo
+// box).  Before it, launch_adj_inject adds kappa r^{k-1} (the data of step k,
+// receivers sharing a cell summed in order) to D_nu at the receiver cells of
+// the first nrtiles tiles listed in rtiles (tiles with receivers, by slot).
+void launch_adj_pair(const AdjArgs &a, int ntiles, const TileMaps &maps, cudaStream_t s);
+void launch_adj_inject(const AdjArgs &a, const int *rtiles, int nrtiles, cudaStream_t s);
 
 // TMA-staged step kernels (fd_tma.cu); variant >= FIRST_TMA_VARIANT.
 void launch_fwd_step_tma(const FwdArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s);

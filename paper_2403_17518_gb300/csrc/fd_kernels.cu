@@ -20,7 +20,10 @@
 // field nu = kappa w lambda, obeys the same recurrence with the data injected
 // where the source is, and gives the velocity gradient (Eq. 13 with the sign
 // of dJ/dv) as (2/v) sum_k a^{k-1} nu^k: the step kernels accumulate the sum,
-// the image reduction applies 2/v.
+// the image reduction applies 2/v.  The injected data r enter the state
+// difference first, D' = D + kappa r (one fma), then D_nu = w (D' + kappa D nu)
+// (an exact rearrangement of w (D + kappa (D nu + r))), so that a launch can
+// also take the injection from a separate pass over the receivers.
 //
 // Born (Section 2.2 Eqs. 9-11, solved jointly): the tangent of the recurrence
 // in v, secondary source w dkappa a0^n with dkappa = 2 kappa dv / v.
@@ -206,15 +209,9 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) adj_step_kernel(AdjArgs A, i
         const Tile tn = A.c.tiles[tix + 1];
         const ShotDesc sd = A.c.shots[t.slot];
         const bool has_rec = tn.rec_begin > t.rec_begin;
-        if (has_rec) {
-            for (int e = tid; e < TZ * TX; e += NT) (&inj[0][0])[e] = 0.f;
-            __syncthreads();
-            const float *rk = A.r + sd.doff + (long long)(A.k - 1) * sd.nrec;
-            for (int e = t.rec_begin + tid; e < tn.rec_begin; e += NT) {
-                const TileRec tr = A.c.recs[e];
-                atomicAdd(&inj[tr.cell / TX][tr.cell % TX], rk[tr.r]);
-            }
-        }
+        if (has_rec)
+            build_injection<NT>(inj, A.c.recs, t.rec_begin, tn.rec_begin,
+                                A.r + sd.doff + (long long)(A.k - 1) * sd.nrec, tid);
         cp_async_wait_prev();
         __syncthreads();
         AdjStage &S = st[k];
@@ -231,13 +228,13 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) adj_step_kernel(AdjArgs A, i
         for (int rr = 0; rr < R; rr++) {
             if (ok && rr < nrow) {
                 const int i = i0 + rr;
-                f2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
-                if (has_rec) a = add2(a, pk(sm2<float2>(&inj[lz0 + rr][lxp])));
+                const f2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
                 const float wz = sponge1(i, NZ, A.c.nb);
                 const f2 w = pk2(wz * wx0, wz * wx1);
                 const f2 nu = pk(zc[rr + HALO]);
-                const f2 dv = pk(sm2<float2>(&S.d[lz0 + rr][lxp]));
                 const f2 kv = pk(sm2<float2>(&S.k[lz0 + rr][lxp]));
+                f2 dv = pk(sm2<float2>(&S.d[lz0 + rr][lxp]));
+                if (has_rec) dv = fma2(kv, pk(sm2<float2>(&inj[lz0 + rr][lxp])), dv);
                 const f2 av = pk(sm2<float2>(&S.a[lz0 + rr][lxp]));
                 const f2 gv = pk(sm2<float2>(&S.g[lz0 + rr][lxp]));
                 const f2 dn = keep_lo(mul2(w, fma2(kv, a, dv)), hi);

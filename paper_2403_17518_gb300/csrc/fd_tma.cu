@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1)
 // Adjoint step (see adj_step_kernel): nu^{k+1} with halo, D_nu, kappa and the
 // stored a^{k-1} by TMA; the image accumulator is read with plain loads
 // issued before the arithmetic (a fifth staged tile would leave room for only
-// one stage), the receiver injection tile is built per tile with shared
-// atomics.
+// one stage), the receiver injection tile is built per tile
+// (build_injection).
 // ---------------------------------------------------------------------------
 struct TmaAdjStage {
     STile u;
@@ -167,11 +167,11 @@ __device__ __forceinline__ void adj_rows(const AdjArgs &A, const TmaAdjStage &S,
 #pragma unroll
     for (int rr = 0; rr < R; rr++) {
         if (ok && rr < nrow) {
-            f2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
-            if (has_rec) a = add2(a, pk(*reinterpret_cast<const float2 *>(&inj[lz0 + rr][lxp])));
+            const f2 a = lap8x2(S.u, zc + rr, lz0 + rr, lxp);
             const f2 nu = pk(zc[rr + HALO]);
-            const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[lz0 + rr][lxp]));
             const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr][lxp]));
+            f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[lz0 + rr][lxp]));
+            if (has_rec) dv = fma2(kv, pk(*reinterpret_cast<const float2 *>(&inj[lz0 + rr][lxp])), dv);
             const f2 av = pk(*reinterpret_cast<const float2 *>(&S.a[lz0 + rr][lxp]));
             f2 dn, nn;
             if constexpr (FULL) {
@@ -212,16 +212,9 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1)
         },
         [&](const TmaAdjStage &S, const TileInfo &T) {
             const bool has_rec = T.rec_end > T.rec_begin;
-            if (has_rec) {
-                for (int e = tid; e < TZ * TX; e += NT) (&inj[0][0])[e] = 0.f;
-                __syncthreads();
-                const float *rk = A.r + T.doff + (long long)(A.k - 1) * T.nrec;
-                for (int e = T.rec_begin + tid; e < T.rec_end; e += NT) {
-                    const TileRec tr = A.c.recs[e];
-                    atomicAdd(&inj[tr.cell / TX][tr.cell % TX], rk[tr.r]);
-                }
-                __syncthreads();
-            }
+            if (has_rec)
+                build_injection<NT>(inj, A.c.recs, T.rec_begin, T.rec_end,
+                                    A.r + T.doff + (long long)(A.k - 1) * T.nrec, tid);
             if (T.flags & TI_INTERIOR) adj_rows<R, true>(A, S, inj, has_rec, T, lxp, lz0);
             else adj_rows<R, false>(A, S, inj, has_rec, T, lxp, lz0);
         });

@@ -249,8 +249,205 @@ __global__ void __launch_bounds__(NT2, 2) fwd_pair_kernel(FwdArgs A, const __gri
     }
 }
 
-template <typename K>
-void launch_pdl2(K kernel, int grid, const FwdArgs &a, const TileMaps &maps, int ntiles, cudaStream_t s) {
+// ---------------------------------------------------------------------------
+// Two-step adjoint: steps k (nu^{k+1} -> nu^k) and k-1 in one launch, the
+// same layout and stage refill as fwd_pair_kernel.  The data of step k are
+// already in the staged D_nu (D' = D + kappa r^{k-1}, launch_adj_inject, so
+// ring cells need no injection tile); the data of step k-1 are added to the
+// core's D_nu^k in shared memory after step k.  The image accumulator takes
+// a^{k-1} nu^k (tiles whose record reaches step k) and then a^{k-2} nu^{k-1},
+// in that order, as two one-step launches would.
+// ---------------------------------------------------------------------------
+template <bool FULL, class MidFn>
+__device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage &S, ETile &V, ETile &Dn,
+                                              const TileInfo &T, int tid, MidFn mid) {
+    const int NZ = A.c.NZ, nb = A.c.nb, nxw = T.nxw, pitch = T.pitch, k = A.k;
+
+    // ---- step k on the grown tile -------------------------------------------
+    {
+        const int ex = 2 * (tid % PAIRS1), ez0 = R1 * (tid / PAIRS1);
+        const int jj = T.x0 - HALO + ex;
+        float wx0 = 1.f, wx1 = 1.f;
+        bool c0ok = true, c1ok = true;
+        if constexpr (!FULL) {
+            c0ok = jj >= 0 && jj < nxw;
+            c1ok = jj + 1 >= 0 && jj + 1 < nxw;
+            wx0 = sponge1(jj, nxw, nb);
+            wx1 = sponge1(jj + 1, nxw, nb);
+        }
+        float2 zc[R1 + 2 * HALO];
+#pragma unroll
+        for (int r = 0; r < R1 + 2 * HALO; r++) zc[r] = *reinterpret_cast<const float2 *>(&S.u[ez0 + r][ex + HALO]);
+#pragma unroll
+        for (int rr = 0; rr < R1; rr++) {
+            const int ez = ez0 + rr;
+            const int i = T.z0 - HALO + ez;
+            const f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&S.u[ez + HALO][ex]), zc + rr);
+            const f2 nu = pk(zc[rr + HALO]);
+            const f2 dv = pk(*reinterpret_cast<const float2 *>(&S.d[ez][ex]));
+            const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[ez][ex]));
+            f2 dn, nn;
+            if constexpr (FULL) {
+                dn = fma2(kv, a, dv);
+                nn = add2(nu, dn);
+            } else {
+                const bool rok = i >= 0 && i < NZ;
+                const bool v0 = rok && c0ok, v1 = rok && c1ok;
+                const float wz = sponge1(i, NZ, nb);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                dn = keep_lo(mul2(w, fma2(kv, a, dv)), v1);
+                nn = keep_lo(fma2(w, nu, dn), v1);
+                if (!v0) dn = nn = 0ull;
+            }
+            *reinterpret_cast<f2 *>(&V[ez][ex]) = nn;
+            *reinterpret_cast<f2 *>(&Dn[ez][ex]) = dn;
+        }
+    }
+    __syncthreads();  // nu^k, D_nu^k complete on the grown tile
+
+    // Data of step k-1 at the tile's receivers: D' = D_nu^k + kappa r^{k-2}.
+    if (T.rec_end > T.rec_begin) {
+        const float *rk = A.r + T.doff + (long long)(k - 2) * T.nrec;
+        for (int e = T.rec_begin + tid; e < T.rec_end; e += NT2)
+            if (e == T.rec_begin || A.c.recs[e - 1].cell != A.c.recs[e].cell) {
+                const int cell = A.c.recs[e].cell;
+                const int lz = cell / TX + HALO, lx = cell % TX + HALO;
+                Dn[lz][lx] = fmaf(S.k[lz][lx], receiver_sum(A.c.recs, e, T.rec_end, rk), Dn[lz][lx]);
+            }
+        __syncthreads();
+    }
+
+    const int lxp = 2 * (tid % 32), lz0 = R2 * (tid / 32);
+    const bool worker = tid < 256;
+    f2 kv2[R2];
+#pragma unroll
+    for (int rr = 0; rr < R2; rr++)
+        kv2[rr] = worker ? *reinterpret_cast<const f2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]) : 0ull;
+    mid();
+
+    // ---- step k-1 on the core (threads 0..255), imaging of both steps -----
+    if (!worker) return;
+    const int j = T.x0 + lxp;
+    const int i0 = T.z0 + lz0;
+    const long long cbase = T.foff + (long long)i0 * pitch + j;
+    const int nrow = FULL ? R2 : min(R2, NZ - i0);
+    const bool ok = FULL || j < nxw, hi = FULL || j + 1 < nxw;
+    const bool image_k = T.nt > k - 1;  // the record reaches step k
+    float wx0 = 1.f, wx1 = 1.f;
+    if constexpr (!FULL) {
+        wx0 = sponge1(j, nxw, nb);
+        wx1 = sponge1(j + 1, nxw, nb);
+    }
+    float2 zc[R2 + 2 * HALO];
+#pragma unroll
+    for (int r = 0; r < R2 + 2 * HALO; r++) zc[r] = *reinterpret_cast<const float2 *>(&V[lz0 + r][lxp + HALO]);
+#pragma unroll
+    for (int rr = 0; rr < R2; rr++) {
+        if (!(ok && rr < nrow)) continue;
+        const long long c = cbase + (long long)rr * pitch;
+        f2 gv = *reinterpret_cast<const f2 *>(A.g + c);
+        const f2 a1 = *reinterpret_cast<const f2 *>(A.a + c);
+        const f2 a2 = *reinterpret_cast<const f2 *>(A.a2 + c);
+        const f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&V[lz0 + rr + HALO][lxp]), zc + rr);
+        const f2 nu = pk(zc[rr + HALO]);  // nu^k
+        const f2 d1 = *reinterpret_cast<const f2 *>(&Dn[lz0 + rr + HALO][lxp + HALO]);
+        f2 dn, nn;
+        if constexpr (FULL) {
+            dn = fma2(kv2[rr], a, d1);
+            nn = add2(nu, dn);
+        } else {
+            const float wz = sponge1(i0 + rr, NZ, nb);
+            const f2 w = pk2(wz * wx0, wz * wx1);
+            dn = keep_lo(mul2(w, fma2(kv2[rr], a, d1)), hi);
+            nn = keep_lo(fma2(w, nu, dn), hi);
+        }
+        if (image_k) gv = keep_lo(fma2(a1, nu, gv), hi);
+        gv = keep_lo(fma2(a2, nn, gv), hi);
+        *reinterpret_cast<f2 *>(A.dd_out + c) = dn;
+        *reinterpret_cast<f2 *>(A.nun + c) = nn;
+        *reinterpret_cast<f2 *>(A.g + c) = gv;
+    }
+}
+
+__global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __grid_constant__ TileMaps M, int ntiles) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Fwd2Stage &S = *reinterpret_cast<Fwd2Stage *>(smem_raw);
+    ETile &V = *reinterpret_cast<ETile *>(smem_raw + sizeof(Fwd2Stage));
+    ETile &Dn = *reinterpret_cast<ETile *>(smem_raw + sizeof(Fwd2Stage) + sizeof(ETile));
+    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + sizeof(Fwd2Stage) + 2 * sizeof(ETile));
+    const int tid = threadIdx.x + threadIdx.y * 32;
+    const bool leader = tid == 0;
+    const unsigned bar = smem_u32(&tail->bar[0]);
+    const int b = blockIdx.x, g = gridDim.x;
+    int4 co = make_int4(0, 0, 0, 0);
+    int mc = 0;
+    if (smem_u32(&S) & 127u) {
+        if (leader) atomicExch(A.c.tflag, 2u);
+        return;
+    }
+    if (leader) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fetch_coords(A.c.infos, b, co, mc);
+        copy_desc(&tail->desc[0], &A.c.infos[b]);
+    }
+    griddep_wait();
+    griddep_launch_dependents();
+    auto issue = [&]() {
+        fence_proxy_async();
+        mbar_expect_tx(bar, kFwd2StageBytes);
+        tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO2, co.y - HALO2, co.x, bar);
+        tma_load_3d(smem_u32(&S.d), &M.m[1], co.z - HALO, co.y - HALO, co.x, bar);
+        tma_load_3d(smem_u32(&S.k), &M.m[2], co.w - HALO, co.y - HALO, mc, bar);
+    };
+    if (leader) {
+        issue();
+        if (b + g < ntiles) fetch_coords(A.c.infos, b + g, co, mc);
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    for (int tix = b; tix < ntiles; tix += g) {
+        const bool landed = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (leader) cp_async_wait_all();
+        if (__syncthreads_or(!landed)) {
+            if (leader) atomicExch(A.c.tflag, 1u);
+            return;
+        }
+        const bool more = tix + g < ntiles;
+        auto mid = [&]() {
+            __syncthreads();  // every thread is done with the stage
+            if (leader && more) issue();
+        };
+        const TileInfo &T = tail->desc[0];
+        if (T.flags & TI_INTERIOR2) adj_pair_tile<true>(A, S, V, Dn, T, tid, mid);
+        else adj_pair_tile<false>(A, S, V, Dn, T, tid, mid);
+        __syncthreads();  // the descriptor, V and Dn are free
+        if (leader && more) {
+            copy_desc(&tail->desc[0], &A.c.infos[tix + g]);
+            if (tix + 2 * g < ntiles) fetch_coords(A.c.infos, tix + 2 * g, co, mc);
+        }
+    }
+}
+
+// D' = D_nu + kappa r^{k-1} at the receiver cells of the listed tiles (one
+// CTA per tile; receivers sharing a cell summed in order, as in
+// build_injection).
+__global__ void adj_inject_kernel(AdjArgs A, const int *__restrict__ rtiles) {
+    const TileInfo &T = A.c.infos[rtiles[blockIdx.x]];
+    const float *rk = A.r + T.doff + (long long)(A.k - 1) * T.nrec;
+    for (int e = T.rec_begin + threadIdx.x; e < T.rec_end; e += blockDim.x)
+        if (e == T.rec_begin || A.c.recs[e - 1].cell != A.c.recs[e].cell) {
+            const int cell = A.c.recs[e].cell;
+            const int z = T.z0 + cell / TX, lx = cell % TX;
+            const float kap = A.c.kap[(long long)T.mc * A.c.mstride + (long long)z * A.c.pf + T.mx + lx];
+            float *d = A.dd + T.foff + (long long)z * T.pitch + T.x0 + lx;
+            *d = fmaf(kap, receiver_sum(A.c.recs, e, T.rec_end, rk), *d);
+        }
+}
+
+template <typename K, typename Args>
+void launch_pdl2(K kernel, int grid, const Args &a, const TileMaps &maps, int ntiles, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(32, NT2 / 32);
@@ -272,6 +469,24 @@ int occupancy_of(const void *fn) {
 }
 
 }  // namespace
+
+void launch_adj_pair(const AdjArgs &a, int ntiles, const TileMaps &maps, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    static int sms = 0, occ = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        occ = occupancy_of((const void *)adj_pair_kernel);
+    }
+    const int cap = occ * sms;
+    launch_pdl2(adj_pair_kernel, ntiles < cap ? ntiles : cap, a, maps, ntiles, s);
+}
+
+void launch_adj_inject(const AdjArgs &a, const int *rtiles, int nrtiles, cudaStream_t s) {
+    if (nrtiles <= 0) return;
+    adj_inject_kernel<<<nrtiles, 128, 0, s>>>(a, rtiles);
+}
 
 int fwd_pair_occupancy() {
     const int a = occupancy_of((const void *)fwd_pair_kernel<true>);
