@@ -268,80 +268,118 @@ __global__ void fprop_reduce_kernel(FpropArgs P, int splits) {
 // Tiles are stored k-major in shared memory and read with ldmatrix.trans.
 // Each CTA writes its partial C tile to part[blockIdx.z][M][N].
 // ---------------------------------------------------------------------------
-constexpr int WBM = 64, WBN = 64, WBK = 32, WSM = WBM + 8, WSN = WBN + 8;
+constexpr int WBK = 32;
 
-struct WgradSmem {
-    __nv_bfloat16 a[STAGES][WBK][WSM];
-    __nv_bfloat16 b[STAGES][WBK][WSN];
+// Tile shape: WMW x WNW warps of 32 x 32 (BM = 32 WMW, BN = 32 WNW, 4 warps):
+// 64 x 64 in general, 32 x 128 when M <= 32 (no half-empty m tiles).
+template <int WMW, int WNW>
+struct WgradTile {
+    static constexpr int BM = 32 * WMW, BN = 32 * WNW, SM = BM + 8, SN = BN + 8;
+    static constexpr int ACH = BM / 8, BCH = BN / 8;  // 16-byte chunks per k-row
+    static constexpr int AI = WBK * ACH / 128, BI = WBK * BCH / 128;  // chunks per thread
+    __nv_bfloat16 a[STAGES][WBK][SM];
+    __nv_bfloat16 b[STAGES][WBK][SN];
 };
 
+template <int WMW, int WNW>
 __global__ void __launch_bounds__(128) igemm_wgrad_kernel(WgradArgs P) {
+    using TL = WgradTile<WMW, WNW>;
+    constexpr int BM = TL::BM, BN = TL::BN;
     extern __shared__ __align__(16) unsigned char smraw[];
-    WgradSmem &S = *reinterpret_cast<WgradSmem *>(smraw);
+    TL &S = *reinterpret_cast<TL *>(smraw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m0 = blockIdx.x * WBM, n0 = blockIdx.y * WBN;
-    const long long HW = (long long)P.H * P.W;
-    const long long KP = (long long)P.nimg * HW;
-    const long long per = (KP + gridDim.z - 1) / gridDim.z;
-    const long long kb = (long long)blockIdx.z * per;
-    const long long ke = kb + per < KP ? kb + per : KP;
-    const int nk = ke > kb ? (int)((ke - kb + WBK - 1) / WBK) : 0;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // Pixel indices fit in 32 bits (the host checks nimg * H * W < 2^31).
+    const int HW = P.H * P.W;
+    const int KP = P.nimg * HW;
+    const int per = (KP + gridDim.z - 1) / gridDim.z;
+    const int kb = blockIdx.z * per;
+    const int ke = kb + per < KP ? kb + per : KP;
+    const int nk = ke > kb ? (ke - kb + WBK - 1) / WBK : 0;
 
-    // A tile: 32 k-rows x 64 m = 32 x 8 chunks = 256 chunks -> 2 per thread.
-    // B tile: 32 k-rows x 64 n = 256 chunks -> 2 per thread.
+    // B chunks: fixed column chunk per slot, so the tap split of n is done
+    // once; the pixel (img, h, w) of each slot's k-row advances by WBK per
+    // stage.
+    int b_row[TL::BI], b_off[TL::BI], b_dh[TL::BI], b_dw[TL::BI], b_img[TL::BI], b_h[TL::BI], b_w[TL::BI];
+    unsigned b_kind = 0;  // bit i: slot i is the ones column; bit 16+i: slot i is empty
+#pragma unroll
+    for (int i = 0; i < TL::BI; i++) {
+        const int idx = tid + i * 128;
+        b_row[i] = idx / TL::BCH;
+        const int n = n0 + (idx % TL::BCH) * 8;
+        b_off[i] = n;
+        b_dh[i] = b_dw[i] = 0;
+        if (n >= P.N || n > P.nw) b_kind |= 1u << (16 + i);
+        else if (n == P.nw) b_kind |= 1u << i;
+        else if (P.mode == WG_CONV) {
+            const int tap = n / P.ci;
+            b_off[i] = n - tap * P.ci;
+            b_dh[i] = tap / 3 - 1;
+            b_dw[i] = tap % 3 - 1;
+        }
+        const int k = kb + b_row[i];
+        b_img[i] = k / HW;
+        const int r = k - b_img[i] * HW;
+        b_h[i] = r / P.W;
+        b_w[i] = r - b_h[i] * P.W;
+    }
     auto load_stage = [&](int st, int kt) {
 #pragma unroll
-        for (int i = 0; i < 2; i++) {
+        for (int i = 0; i < TL::AI; i++) {
             const int idx = tid + i * 128;
-            const int kr = idx >> 3, ch = idx & 7;
-            const long long k = kb + (long long)kt * WBK + kr;
-            // A chunk: 8 consecutive m.
-            {
-                const int m = m0 + ch * 8;
-                bool ok = k < ke && m < P.M;
-                const __nv_bfloat16 *src = P.g;
-                if (ok) {
-                    const int img = (int)(k / HW);
-                    const int r = (int)(k - img * HW);
+            const int kr = idx / TL::ACH, ch = idx % TL::ACH;
+            const int k = kb + kt * WBK + kr;
+            const int m = m0 + ch * 8;
+            const bool ok = k < ke && m < P.M;
+            const __nv_bfloat16 *src = P.g;
+            if (ok) {
+                if (P.mode == WG_CONV) {
+                    src = P.g + (long long)k * P.g_stride + m;
+                } else {  // WG_CONVT: m = ab*Co + co at the fine pixel (2h + a, 2w + b)
+                    const int img = k / HW;
+                    const int r = k - img * HW;
                     const int h = r / P.W, w = r - h * P.W;
-                    if (P.mode == WG_CONV) {
-                        src = P.g + k * P.g_stride + m;
-                    } else {  // WG_CONVT: m = ab*Co + co
-                        const int ab = m / P.co, co = m - ab * P.co;
-                        const long long pix = ((long long)img * (2 * P.H) + 2 * h + (ab >> 1)) * (2 * P.W) + 2 * w + (ab & 1);
-                        src = P.g + pix * P.g_stride + co;
-                    }
+                    const int ab = m / P.co, co = m - ab * P.co;
+                    const long long pix =
+                        ((long long)img * (2 * P.H) + 2 * h + (ab >> 1)) * (2 * P.W) + 2 * w + (ab & 1);
+                    src = P.g + pix * P.g_stride + co;
                 }
-                cp16(&S.a[st][kr][ch * 8], src, ok);
             }
-            // B chunk: 8 consecutive n (the chunk at nw is the ones column).
-            {
-                const int n = n0 + ch * 8;
-                bool ok = k < ke && n < P.N;
-                const __nv_bfloat16 *src = P.x;
-                if (ok && n >= P.nw) {
-                    src = P.ones;
-                    ok = n == P.nw;
-                } else if (ok) {
-                    const int img = (int)(k / HW);
-                    const int r = (int)(k - img * HW);
-                    const int h = r / P.W, w = r - h * P.W;
-                    if (P.mode == WG_CONV) {
-                        const int tap = n / P.ci, c = n - tap * P.ci;
-                        const int hs = h + tap / 3 - 1, ws = w + tap % 3 - 1;
-                        ok = hs >= 0 && hs < P.H && ws >= 0 && ws < P.W;
-                        if (ok) src = P.x + (((long long)img * P.H + hs) * P.W + ws) * P.x_stride + P.x_off + c;
-                    } else {
-                        src = P.x + k * P.x_stride + P.x_off + n;
-                    }
+            cp16(&S.a[st][kr][ch * 8], src, ok);
+        }
+#pragma unroll
+        for (int i = 0; i < TL::BI; i++) {
+            const int idx = tid + i * 128;
+            const int ch = idx % TL::BCH;
+            const int k = kb + kt * WBK + b_row[i];
+            bool ok = k < ke && !((b_kind >> (16 + i)) & 1u);
+            const __nv_bfloat16 *src = P.x;
+            if (ok && ((b_kind >> i) & 1u)) {
+                src = P.ones;
+            } else if (ok) {
+                if (P.mode == WG_CONV) {
+                    const int hs = b_h[i] + b_dh[i], ws = b_w[i] + b_dw[i];
+                    ok = hs >= 0 && hs < P.H && ws >= 0 && ws < P.W;
+                    if (ok) src = P.x + (((long long)b_img[i] * P.H + hs) * P.W + ws) * P.x_stride + P.x_off + b_off[i];
+                } else {
+                    src = P.x + (long long)k * P.x_stride + P.x_off + b_off[i];
                 }
-                cp16(&S.b[st][kr][ch * 8], src, ok);
+            }
+            cp16(&S.b[st][b_row[i]][ch * 8], src, ok);
+            // Next stage of this slot: pixel k + WBK.
+            b_w[i] += WBK;
+            while (b_w[i] >= P.W) {
+                b_w[i] -= P.W;
+                if (++b_h[i] == P.H) {
+                    b_h[i] = 0;
+                    b_img[i]++;
+                }
             }
         }
     };
 
-    // Warps: 2 x 2 over the 64 x 64 tile, each 32 x 32.
-    const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+    // Warps: WMW x WNW over the tile, each 32 x 32.
+    const int wm = (warp % WMW) * 32, wn = (warp / WMW) * 32;
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; i++)
@@ -350,6 +388,8 @@ __global__ void __launch_bounds__(128) igemm_wgrad_kernel(WgradArgs P) {
 #pragma unroll
             for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
 
+    // Stages are loaded in order kt = 0, 1, 2, ...: the per-slot pixel
+    // counters above advance once per load.
 #pragma unroll
     for (int s = 0; s < STAGES - 1; s++) {
         if (s < nk) load_stage(s, s);
@@ -813,8 +853,12 @@ void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
     }
 }
 
+// Tile shape of the weight-gradient GEMM for an M-row problem.
+static bool wgrad_narrow(int M) { return M <= 32; }
+
 int wgrad_splits(long long kpix, int M, int N) {
-    const int tiles = ((M + WBM - 1) / WBM) * ((N + WBN - 1) / WBN);
+    const int BM = wgrad_narrow(M) ? 32 : 64, BN = wgrad_narrow(M) ? 128 : 64;
+    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     long long want = (152LL * 4 + tiles - 1) / tiles;
     long long maxs = (kpix + 255) / 256;  // at least 256 pixels per split
     if (want > maxs) want = maxs;
@@ -823,15 +867,22 @@ int wgrad_splits(long long kpix, int M, int N) {
     return (int)want;
 }
 
-void launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s) {
-    const size_t sm = sizeof(WgradSmem);
+template <int WMW, int WNW>
+static void wgrad_launch(const WgradArgs &a, int splits, cudaStream_t s) {
+    using TL = WgradTile<WMW, WNW>;
+    const size_t sm = sizeof(TL);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(igemm_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(igemm_wgrad_kernel<WMW, WNW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
-    dim3 grid((a.M + WBM - 1) / WBM, (a.N + WBN - 1) / WBN, splits);
-    igemm_wgrad_kernel<<<grid, 128, sm, s>>>(a);
+    dim3 grid((a.M + TL::BM - 1) / TL::BM, (a.N + TL::BN - 1) / TL::BN, splits);
+    igemm_wgrad_kernel<WMW, WNW><<<grid, 128, sm, s>>>(a);
+}
+
+void launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s) {
+    if (wgrad_narrow(a.M)) wgrad_launch<1, 4>(a, splits, s);
+    else wgrad_launch<2, 2>(a, splits, s);
     const long long mn = (long long)a.M * a.N;
     wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, splits, a.M, a.N, a.nw, a.mode, a.co, dw,
                                                                  db);

@@ -777,6 +777,7 @@ int deblur_grad(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int n, i
     NetState *net = ctx_net(ctx);
     if (!net || !net->have_weights) return fail(ctx, DHFWI_ERR_STATE, "the network has no weights yet");
     if (!x_dev || !y_dev || !grad_dev || n < 1 || h < 1 || w < 1) return fail(ctx, DHFWI_ERR_ARG, "bad arguments");
+    if ((long long)n * h * w >= (1LL << 31)) return fail(ctx, DHFWI_ERR_ARG, "n * h * w must be below 2^31");
     if (!ilog_mult(h, net->levels) || !ilog_mult(w, net->levels))
         return fail(ctx, DHFWI_ERR_ARG, "h and w must be multiples of 2^levels");
     cudaSetDevice(ctx_device(ctx));
@@ -813,6 +814,8 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
         cfg->epochs > 4096)
         return fail(ctx, DHFWI_ERR_ARG, "bad training configuration");
     if (nz < cfg->patch || nx < cfg->patch) return fail(ctx, DHFWI_ERR_ARG, "image smaller than the patch");
+    if ((long long)cfg->batch * cfg->patch * cfg->patch >= (1LL << 31))
+        return fail(ctx, DHFWI_ERR_ARG, "batch * patch^2 must be below 2^31");
     if (cfg->mute_rows < 0 || cfg->mute_rows >= nz) return fail(ctx, DHFWI_ERR_ARG, "mute_rows must be in [0, nz)");
     if (!(cfg->warmup_frac >= 0.f) || cfg->warmup_frac > 1.f)
         return fail(ctx, DHFWI_ERR_ARG, "warmup_frac must be in [0, 1]");
