@@ -103,7 +103,11 @@ def line_search(ctx, v, dirn, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_
 
 
 def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, cold_epochs: int, warm_epochs: int,
-            vmin: float, vmax: float, mute_rows: int = 5, log=None):
+            vmin: float, vmax: float, mute_rows: int = 5, log=None, hybrid_iters: int = 0):
+    """mode: "plain" (gradient), "deblur" (network direction every iteration)
+    or "hybrid" (network direction for the first hybrid_iters iterations of
+    the run, the gradient after: the Hessian approximation steers the early
+    iterations, then conventional FWI continues, Section 4)."""
     dev = ctx.device
     v_true = torch.tensor(case.v_true, dtype=torch.float32, device=dev)
     v = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
@@ -115,7 +119,9 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
     direction = ctx.new_model()
     dm1 = ctx.new_model()
     trial = ctx.new_model()
+    done_iters = 0
     for fc in bands:
+        trained_in_band = False  # the network restarts from scratch in each band (Section 4)
         g = copy.deepcopy(case.geom)
         g.wavelet = lowpass(np.asarray(g.wavelet, dtype=np.float64), case.dt, fc)
         ga = GeomArgs(g)
@@ -123,19 +129,21 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
         d_born = ctx.new_data(ga)
         d_try = ctx.new_data(ga)
         for it in range(iters):
+            use_net = mode == "deblur" or (mode == "hybrid" and done_iters < hybrid_iters)
             with timer:
                 J0, _ = ctx.fwi_gradient(v, ga, d_obs, grad=grad)
                 a1 = 0.01 * float(np.mean(case.v_init))
                 fallback = False
                 loss = None
                 solves += 2  # forward + adjoint of the gradient (checkpoint recomputation not counted)
-                if mode == "deblur":
+                if use_net:
                     solves += 2  # Born modelling + its adjoint (Section 3.1: two more solves)
                     ctx.born_demig(v, ga, grad, out=d_born)
                     ctx.rtm_mig(v, ga, d_born, out=dm1)
-                    h = ctx.deblur_train(dm1, grad, warm_start=it > 0,
-                                         epochs=warm_epochs if it > 0 else cold_epochs, mute_rows=mute_rows,
-                                         warmup_frac=0.1, **net_cfg)
+                    warm = it > 0 and trained_in_band
+                    h = ctx.deblur_train(dm1, grad, warm_start=warm, epochs=warm_epochs if warm else cold_epochs,
+                                         mute_rows=mute_rows, warmup_frac=0.1, **net_cfg)
+                    trained_in_band = True
                     loss = [float(h[0]), float(h[-1])]
                     ctx.deblur_apply(grad, out=direction)
                     a_best, ok = line_search(ctx, v, direction, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
@@ -155,8 +163,9 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
                     a_best, _ = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_rows)
                     solves += 2
                 ctx.fwi_update(v, dirn, a_best, vmin, vmax, mute_rows, out=v)
+            done_iters += 1
             rec = {"band": fc, "iter": it + 1, "gpu_s": timer.seconds(), "solves": solves,
-                   "model_rms": model_rms(v, v_true),
+                   "model_rms": model_rms(v, v_true), "net": use_net,
                    "misfit": J0, "alpha": a_best, "fallback": fallback, "train_loss": loss}
             hist.append(rec)
             if log:
@@ -173,13 +182,17 @@ def error_at(hist, budget: float, key: str = "gpu_s") -> float:
     return best
 
 
-def summarize(plain, deblur):
-    t = min(plain[-1]["gpu_s"], deblur[-1]["gpu_s"])
-    n = min(plain[-1]["solves"], deblur[-1]["solves"])
-    return {"equal_gpu_s": t, "plain_model_rms": error_at(plain, t), "deblur_model_rms": error_at(deblur, t),
-            "equal_solves": n, "plain_model_rms_at_solves": error_at(plain, n, "solves"),
-            "deblur_model_rms_at_solves": error_at(deblur, n, "solves"),
-            "initial_model_rms": plain[0]["model_rms"], "plain_final": plain[-1], "deblur_final": deblur[-1]}
+def summarize(arms: dict):
+    """Model RMS error of every arm at the GPU time (and solve count) all
+    arms reached."""
+    t = min(h[-1]["gpu_s"] for h in arms.values())
+    n = min(h[-1]["solves"] for h in arms.values())
+    out = {"equal_gpu_s": t, "equal_solves": n, "initial_model_rms": next(iter(arms.values()))[0]["model_rms"]}
+    for name, h in arms.items():
+        out[f"{name}_model_rms"] = error_at(h, t)
+        out[f"{name}_model_rms_at_solves"] = error_at(h, n, "solves")
+        out[f"{name}_final"] = h[-1]
+    return out
 
 
 def main():
@@ -197,6 +210,10 @@ def main():
     p.add_argument("--iters-plain", type=int, default=0, help="iterations per band, plain arm (default --iters)")
     p.add_argument("--mute", type=int, default=5, help="top rows muted in the update and the network input")
     p.add_argument("--lr", type=float, default=2e-4, help="network learning rate")
+    p.add_argument("--arms", default="plain,deblur", help="comma list of plain, deblur, hybrid or hybridN")
+    p.add_argument("--iters-hybrid", type=int, default=0, help="iterations per band, hybrid arm (default --iters)")
+    p.add_argument("--hybrid-net-iters", type=int, default=5,
+                   help="hybrid arm: iterations at the start of the run that use the network direction")
     p.add_argument("--out", default="")
     a = p.parse_args()
     v = synth.layered_fault_model(a.nz, a.nx, a.h, seed=31)
@@ -211,12 +228,21 @@ def main():
     bands = [float(b) for b in a.bands.split(",")]
     out = {"config": vars(a), "net": net}
     t0 = time.time()
-    for mode in ("plain", "deblur"):
-        iters = a.iters if mode == "deblur" or a.iters_plain <= 0 else a.iters_plain
-        out[mode] = run_arm(ctx, case, mode, bands, iters, net, 200, 20, 1500.0, 4500.0, mute_rows=a.mute,
-                            log=lambda m, r: print(m, json.dumps(r), flush=True))
+    arms = {}
+    for name in a.arms.split(","):
+        # "hybridN": hybrid arm with the network for the first N iterations.
+        mode = "hybrid" if name.startswith("hybrid") else name
+        hyb = int(name[6:]) if mode == "hybrid" and name[6:] else a.hybrid_net_iters
+        iters = a.iters
+        if mode == "plain" and a.iters_plain > 0:
+            iters = a.iters_plain
+        if mode == "hybrid" and a.iters_hybrid > 0:
+            iters = a.iters_hybrid
+        arms[name] = run_arm(ctx, case, mode, bands, iters, net, 200, 20, 1500.0, 4500.0, mute_rows=a.mute,
+                             log=lambda m, r, nm=name: print(nm, json.dumps(r), flush=True), hybrid_iters=hyb)
+        out[name] = arms[name]
     out["wall_s"] = time.time() - t0
-    out["summary"] = summarize(out["plain"], out["deblur"])
+    out["summary"] = summarize(arms)
     s = json.dumps(out)
     if a.out:
         with open(a.out, "w") as f:
