@@ -780,6 +780,146 @@ __global__ void loss_accum_kernel(const double *__restrict__ partial, int nblock
     acc[0] += weight * s;
 }
 
+// ---------------------------------------------------------------------------
+// 3x3 convolutions (forward and input gradient: nine taps, shifts in
+// {-1, 0, 1}, stride 1) with a shared-memory halo tile: a CTA computes a
+// block of 8 x 16 output pixels for BN output channels.  For each slice of
+// 32 input channels the block's input patch (10 x 18 pixels) is staged once
+// and the nine taps read their A fragments from it with ldmatrix at shifted
+// row addresses, instead of gathering every tap from global memory.  The
+// k-steps (channel slice, tap) run through a 3-stage pipeline of weight
+// tiles; patches are double-buffered and loaded with the first tap of their
+// slice.  Same GEMM (k = tap * C + c), accumulation and epilogues as
+// igemm_fprop_kernel, no split-k.
+// ---------------------------------------------------------------------------
+constexpr int HBH = 8, HBW = 16;                          // output block
+constexpr int HPH = HBH + 2, HPW = HBW + 2, HPOS = HPH * HPW;  // 10 x 18 patch
+constexpr int HCB = 32, HSK = HCB + 8;                     // channels per slice, padded row
+
+template <int BN>
+struct HaloSmem {
+    __nv_bfloat16 patch[2][HPOS][HSK];
+    __nv_bfloat16 b[STAGES][BN][HSK];
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128) conv3_halo_kernel(FpropArgs P, int bh_n, int bw_n) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    HaloSmem<BN> &S = *reinterpret_cast<HaloSmem<BN> *>(smraw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int blk = blockIdx.x;
+    const int bw = blk % bw_n;
+    blk /= bw_n;
+    const int bh = blk % bh_n;
+    const int img = blk / bh_n;
+    const int h0 = bh * HBH, w0 = bw * HBW;
+    const int n0 = blockIdx.y * BN;
+    const int H = P.Hs, W = P.Ws;
+    const int nslices = P.C / HCB;
+    const int nk = nslices * 9;  // k-steps (slice, tap)
+    const int K = 9 * P.C;
+
+    auto load_step = [&](int st, int ks) {
+        const int sl = ks / 9, tap = ks - sl * 9;
+        if (tap == 0) {  // the slice's patch, into buffer sl & 1
+            for (int idx = tid; idx < HPOS * (HCB / 8); idx += 128) {
+                const int pos = idx >> 2, ch = idx & 3;
+                const int hs = h0 - 1 + pos / HPW, ws = w0 - 1 + pos % HPW;
+                const bool ok = hs >= 0 && hs < H && ws >= 0 && ws < W;
+                const __nv_bfloat16 *src =
+                    ok ? P.src + (((long long)img * H + hs) * W + ws) * P.src_stride + P.src_off + sl * HCB + ch * 8
+                       : P.src;
+                cp16(&S.patch[sl & 1][pos][ch * 8], src, ok);
+            }
+        }
+        for (int idx = tid; idx < BN * (HCB / 8); idx += 128) {
+            const int row = idx >> 2, ch = idx & 3;
+            const int n = n0 + row;
+            const bool ok = n < P.N;
+            cp16(&S.b[st][row][ch * 8], ok ? P.bt + (long long)n * K + tap * P.C + sl * HCB + ch * 8 : P.bt, ok);
+        }
+    };
+
+    float acc[2][BN / 8][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < BN / 8; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
+
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; s++) {
+        if (s < nk) load_step(s, s);
+        cp_commit();
+    }
+    for (int ks = 0; ks < nk; ks++) {
+        cp_wait<STAGES - 2>();
+        __syncthreads();
+        {
+            const int nxt = ks + STAGES - 1;
+            if (nxt < nk) load_step(nxt % STAGES, nxt);
+            cp_commit();
+        }
+        const int st = ks % STAGES;
+        const int sl = ks / 9, tap = ks - sl * 9;
+        const int dh = P.dh[tap], dw = P.dw[tap];
+        const __nv_bfloat16(*patch)[HSK] = S.patch[sl & 1];
+#pragma unroll
+        for (int kk = 0; kk < HCB; kk += 16) {
+            unsigned af[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int p = warp * 32 + i * 16 + (lane & 15);  // pixel of the block
+                const int pos = (p / HBW + 1 + dh) * HPW + p % HBW + 1 + dw;
+                ldsm_x4(af[i], &patch[pos][kk + (lane >> 4) * 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < BN / 8; j += 2) {
+                unsigned bf[4];
+                const int r = j * 8 + (lane & 7) + ((lane >> 4) << 3);
+                ldsm_x4(bf, &S.b[st][r][kk + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    mma16816(acc[i][j], af[i], bf[0], bf[1]);
+                    mma16816(acc[i][j + 1], af[i], bf[2], bf[3]);
+                }
+            }
+        }
+    }
+    cp_wait<0>();
+
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            const int p = warp * 32 + i * 16 + g + half * 8;
+            const int h = h0 + p / HBW, w = w0 + p % HBW;
+            if (h >= H || w >= W) continue;
+            const long long m = ((long long)img * H + h) * W + w;
+#pragma unroll
+            for (int j = 0; j < BN / 8; j++) {
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int n = n0 + j * 8 + 2 * t + e;
+                    if (n >= P.N) continue;
+                    float v = acc[i][j][half * 2 + e];
+                    if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
+                        v += P.bias[n];
+                        if (EPI == EPI_BF16_LEAKY) v = v > 0.f ? v : P.slope * v;
+                        P.dst_bf16[m * P.dst_stride + P.dst_off + n] = __float2bfloat16_rn(v);
+                    } else {  // EPI_F32 / EPI_F32_ADD
+                        const long long o = m * P.dst_stride + P.dst_off + n;
+                        if (EPI == EPI_F32_ADD) v += P.dst_f32[o];
+                        P.dst_f32[o] = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ===========================================================================
 // Host launchers
 // ===========================================================================
@@ -838,9 +978,60 @@ static bool use_umma() {
     return e && strcmp(e, "tc") == 0;
 }
 
+template <int BN, int EPI>
+static void halo_launch(const FpropArgs &a, int bh_n, int bw_n, int nimg, cudaStream_t s) {
+    const size_t sm = sizeof(HaloSmem<BN>);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(conv3_halo_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    dim3 grid(nimg * bh_n * bw_n, (a.N + BN - 1) / BN);
+    conv3_halo_kernel<BN, EPI><<<grid, 128, sm, s>>>(a, bh_n, bw_n);
+}
+
+template <int EPI>
+static void halo_dispatch(const FpropArgs &a, int bh_n, int bw_n, int nimg, cudaStream_t s) {
+    if (a.N <= 32) halo_launch<32, EPI>(a, bh_n, bw_n, nimg, s);
+    else halo_launch<64, EPI>(a, bh_n, bw_n, nimg, s);
+}
+
+// The halo-tile kernel serves 3x3 convolutions (nine taps with shifts in
+// {-1, 0, 1}, stride 1, same grid in and out) with input channels in slices
+// of 32, on grids large enough to fill the GPU without split-k.
+// DHFWI_NN_HALO=0 turns it off; =1 uses it for every such convolution
+// whatever the grid size.
+static bool halo_eligible(const FpropArgs &a, int epi, int *bh_n, int *bw_n, int *nimg) {
+    const char *e = getenv("DHFWI_NN_HALO");
+    if (e && strcmp(e, "0") == 0) return false;
+    const bool force = e && strcmp(e, "1") == 0;
+    if (a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws || a.C % HCB != 0) return false;
+    if (epi == EPI_BF16_CONVT) return false;
+    if ((a.src_stride | a.src_off) & 7) return false;
+    for (int t = 0; t < 9; t++)
+        if (a.dh[t] < -1 || a.dh[t] > 1 || a.dw[t] < -1 || a.dw[t] > 1) return false;
+    const long long HW = (long long)a.Hs * a.Ws;
+    if (HW <= 0 || a.M % HW != 0) return false;
+    *nimg = (int)(a.M / HW);
+    *bh_n = (a.Hs + HBH - 1) / HBH;
+    *bw_n = (a.Ws + HBW - 1) / HBW;
+    const long long ctas = (long long)*nimg * *bh_n * *bw_n * ((a.N + 63) / 64);
+    return force || ctas >= 152 * 4;
+}
+
 void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
     if (use_umma()) {
         launch_fprop_umma(a, epi, s);
+        return;
+    }
+    int bh_n, bw_n, nimg;
+    if (halo_eligible(a, epi, &bh_n, &bw_n, &nimg)) {
+        switch (epi) {
+        case EPI_BF16_LEAKY: halo_dispatch<EPI_BF16_LEAKY>(a, bh_n, bw_n, nimg, s); break;
+        case EPI_BF16: halo_dispatch<EPI_BF16>(a, bh_n, bw_n, nimg, s); break;
+        case EPI_F32: halo_dispatch<EPI_F32>(a, bh_n, bw_n, nimg, s); break;
+        default: halo_dispatch<EPI_F32_ADD>(a, bh_n, bw_n, nimg, s); break;
+        }
         return;
     }
     const bool small = a.N <= 32;

@@ -520,7 +520,6 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
         a.part = N.fp_part;
         a.part_floats = (long long)N.fp_part_floats;
         a.err = N.err;
-    a.err = N.err;
         launch_fprop(a, EPI_F32, s);
         N.launches += 2;
     }
@@ -600,7 +599,6 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         a.part = N.fp_part;
         a.part_floats = (long long)N.fp_part_floats;
         a.err = N.err;
-    a.err = N.err;
         launch_fprop(a, EPI_F32, s);
         N.launches += 5;
         std::swap(dA, dB);

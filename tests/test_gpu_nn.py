@@ -46,14 +46,21 @@ def test_init_is_bitwise_identical(base, levels):
     assert np.array_equal(ctx.net_get(), onn.init_params(spec, 5))
 
 
-# Both convolution GEMMs: mma.sync (default) and tcgen05 (DHFWI_NN_GEMM=tc).
-GEMMS = ["mma", "tc"]
+# The convolution GEMMs: mma.sync with per-tap gathers, mma.sync with the
+# shared-memory halo tile for 3x3 convolutions (forced for every eligible
+# layer), tcgen05.
+GEMMS = ["mma", "halo", "tc"]
+
+
+def _set_gemm(monkeypatch, gemm):
+    monkeypatch.setenv("DHFWI_NN_GEMM", "tc" if gemm == "tc" else "mma")
+    monkeypatch.setenv("DHFWI_NN_HALO", "1" if gemm == "halo" else "0")
 
 
 @pytest.mark.parametrize("gemm", GEMMS)
 @pytest.mark.parametrize("base,levels,n,h,w", [(8, 2, 2, 32, 32), (16, 3, 3, 24, 40), (32, 4, 2, 128, 128)])
 def test_forward_and_gradient_parity(base, levels, n, h, w, gemm, monkeypatch):
-    monkeypatch.setenv("DHFWI_NN_GEMM", gemm)
+    _set_gemm(monkeypatch, gemm)
     ctx = _ctx()
     spec = onn.UNetSpec(base=base, levels=levels)
     ctx.net_init(base, levels, seed=11)
@@ -90,7 +97,7 @@ def test_gradient_is_deterministic():
 
 @pytest.mark.parametrize("gemm", GEMMS)
 def test_training_and_apply_parity(gemm, monkeypatch):
-    monkeypatch.setenv("DHFWI_NN_GEMM", gemm)
+    _set_gemm(monkeypatch, gemm)
     ctx = _ctx()
     from scipy.ndimage import gaussian_filter
 
