@@ -46,8 +46,9 @@ constexpr size_t kFwd2Smem = sizeof(Fwd2Stage) + 2 * sizeof(ETile) + sizeof(Pipe
 constexpr int NT2 = 288, R1 = 9, R2 = 8, PAIRS1 = E / 2;
 static_assert(PAIRS1 * (E / R1) == NT2 && (TX / 2) * (TZ / R2) == 256, "thread layout");
 
-// mid(): called by every thread once the stage is no longer read (after
-// step n; kappa of the core is then in registers): the leader refills it.
+// mid(): called by every thread after the barrier that ends step n (the
+// stage is no longer read; kappa of the core is in registers): the leader
+// refills the stage.
 template <bool STORE_A, bool FULL, class MidFn>
 __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, ETile &V, ETile &Dn, const TileInfo &T,
                                           int tid, bool two, MidFn mid) {
@@ -110,15 +111,15 @@ __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, 
             }
         }
     }
-    __syncthreads();  // u^{n+1}, D^{n+1} complete on the grown tile
-
-    // kappa of this thread's core cells for step n+1, then the stage is free.
+    // kappa of this thread's core cells for step n+1; after the barrier the
+    // stage is no longer read and u^{n+1}, D^{n+1} are complete.
     const int lxp = 2 * (tid % 32), lz0 = R2 * (tid / 32);
     const bool worker = tid < 256;
     f2 kv2[R2];
 #pragma unroll
     for (int rr = 0; rr < R2; rr++)
         kv2[rr] = worker ? *reinterpret_cast<const f2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]) : 0ull;
+    __syncthreads();
     mid();
 
     // Receivers: sample n is u^{n+1}.
@@ -233,8 +234,7 @@ __global__ void __launch_bounds__(NT2, 2) fwd_pair_kernel(FwdArgs A, const __gri
             return;
         }
         const bool more = tix + g < ntiles;
-        auto mid = [&]() {
-            __syncthreads();  // every thread is done with the stage
+        auto mid = [&]() {  // after a barrier: every thread is done with the stage
             if (leader && more) issue();
         };
         const TileInfo &T = tail->desc[0];
@@ -303,6 +303,12 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
             *reinterpret_cast<f2 *>(&Dn[ez][ex]) = dn;
         }
     }
+    const int lxp = 2 * (tid % 32), lz0 = R2 * (tid / 32);
+    const bool worker = tid < 256;
+    f2 kv2[R2];
+#pragma unroll
+    for (int rr = 0; rr < R2; rr++)
+        kv2[rr] = worker ? *reinterpret_cast<const f2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]) : 0ull;
     __syncthreads();  // nu^k, D_nu^k complete on the grown tile
 
     // Data of step k-1 at the tile's receivers: D' = D_nu^k + kappa r^{k-2}.
@@ -316,14 +322,7 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
             }
         __syncthreads();
     }
-
-    const int lxp = 2 * (tid % 32), lz0 = R2 * (tid / 32);
-    const bool worker = tid < 256;
-    f2 kv2[R2];
-#pragma unroll
-    for (int rr = 0; rr < R2; rr++)
-        kv2[rr] = worker ? *reinterpret_cast<const f2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]) : 0ull;
-    mid();
+    mid();  // the stage is no longer read
 
     // ---- step k-1 on the core (threads 0..255), imaging of both steps -----
     if (!worker) return;
@@ -415,8 +414,7 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
             return;
         }
         const bool more = tix + g < ntiles;
-        auto mid = [&]() {
-            __syncthreads();  // every thread is done with the stage
+        auto mid = [&]() {  // after a barrier: every thread is done with the stage
             if (leader && more) issue();
         };
         const TileInfo &T = tail->desc[0];
