@@ -8,7 +8,11 @@
 namespace dhfwi {
 namespace nn {
 
-enum { EPI_BF16_LEAKY = 0, EPI_BF16 = 1, EPI_BF16_CONVT = 2, EPI_F32 = 3, EPI_F32_ADD = 4 };
+// Epilogues of the forward-form GEMM: bf16 with bias and LeakyReLU, bf16
+// with bias, transposed-conv scatter, f32 store, f32 accumulate, and bf16 of
+// the result times the LeakyReLU derivative of a stored activation (act),
+// i.e. an input gradient fused with the next layer's activation backward.
+enum { EPI_BF16_LEAKY = 0, EPI_BF16 = 1, EPI_BF16_CONVT = 2, EPI_F32 = 3, EPI_F32_ADD = 4, EPI_BF16_LEAKYBWD = 5 };
 enum { WG_CONV = 0, WG_CONVT = 1 };
 
 // Implicit GEMM C[m][n] = sum_k A[m][k] B^T[n][k]; see igemm_fprop_kernel.
@@ -30,6 +34,8 @@ struct FpropArgs {
     float *part;                // optional split-k scratch ([splits][M][N] float32)
     long long part_floats;      // its capacity
     unsigned *err;              // nullable: set to 1 by a tensor-core GEMM whose bounded wait ran out
+    const __nv_bfloat16 *act;   // EPI_BF16_LEAKYBWD: activation [M][act_stride] at act_off
+    int act_stride, act_off;
 };
 
 // Split-k weight-gradient GEMM; see igemm_wgrad_kernel.

@@ -215,6 +215,10 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
                         v += P.bias[co];
                         const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
                         P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v);
+                    } else if (EPI == EPI_BF16_LEAKYBWD) {
+                        const float av = __bfloat162float(P.act[(long long)m * P.act_stride + P.act_off + n]);
+                        P.dst_bf16[(long long)m * P.dst_stride + P.dst_off + n] =
+                            __float2bfloat16_rn(v * (av > 0.f ? 1.0f : P.slope));
                     } else {  // EPI_F32 / EPI_F32_ADD
                         const long long o = (long long)m * P.dst_stride + P.dst_off + n;
                         if (EPI == EPI_F32_ADD) v += P.dst_f32[o];
@@ -249,6 +253,9 @@ __global__ void fprop_reduce_kernel(FpropArgs P, int splits) {
             v += P.bias[co];
             const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
             P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v);
+        } else if (EPI == EPI_BF16_LEAKYBWD) {
+            const float av = __bfloat162float(P.act[(long long)m * P.act_stride + P.act_off + n]);
+            P.dst_bf16[(long long)m * P.dst_stride + P.dst_off + n] = __float2bfloat16_rn(v * (av > 0.f ? 1.0f : P.slope));
         } else {
             const long long o = (long long)m * P.dst_stride + P.dst_off + n;
             if (EPI == EPI_F32_ADD) v += P.dst_f32[o];
@@ -909,6 +916,9 @@ __global__ void __launch_bounds__(128) conv3_halo_kernel(FpropArgs P, int bh_n, 
                         v += P.bias[n];
                         if (EPI == EPI_BF16_LEAKY) v = v > 0.f ? v : P.slope * v;
                         P.dst_bf16[m * P.dst_stride + P.dst_off + n] = __float2bfloat16_rn(v);
+                    } else if (EPI == EPI_BF16_LEAKYBWD) {
+                        const float av = __bfloat162float(P.act[m * P.act_stride + P.act_off + n]);
+                        P.dst_bf16[m * P.dst_stride + P.dst_off + n] = __float2bfloat16_rn(v * (av > 0.f ? 1.0f : P.slope));
                     } else {  // EPI_F32 / EPI_F32_ADD
                         const long long o = m * P.dst_stride + P.dst_off + n;
                         if (EPI == EPI_F32_ADD) v += P.dst_f32[o];
@@ -965,6 +975,7 @@ void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s
     case EPI_BF16: fprop_reduce_kernel<EPI_BF16><<<g, 256, 0, s>>>(a, splits); break;
     case EPI_BF16_CONVT: fprop_reduce_kernel<EPI_BF16_CONVT><<<g, 256, 0, s>>>(a, splits); break;
     case EPI_F32: fprop_reduce_kernel<EPI_F32><<<g, 256, 0, s>>>(a, splits); break;
+    case EPI_BF16_LEAKYBWD: fprop_reduce_kernel<EPI_BF16_LEAKYBWD><<<g, 256, 0, s>>>(a, splits); break;
     default: fprop_reduce_kernel<EPI_F32_ADD><<<g, 256, 0, s>>>(a, splits); break;
     }
 }
@@ -996,15 +1007,13 @@ static void halo_dispatch(const FpropArgs &a, int bh_n, int bw_n, int nimg, cuda
     else halo_launch<64, EPI>(a, bh_n, bw_n, nimg, s);
 }
 
-// The halo-tile kernel serves 3x3 convolutions (nine taps with shifts in
-// {-1, 0, 1}, stride 1, same grid in and out) with input channels in slices
-// of 32, on grids large enough to fill the GPU without split-k.
-// DHFWI_NN_HALO=0 turns it off; =1 uses it for every such convolution
-// whatever the grid size.
+// The halo-tile kernel serves every 3x3 convolution (nine taps with shifts
+// in {-1, 0, 1}, stride 1, same grid in and out) with input channels in
+// slices of 32: measured faster than the gathering kernel with split-k also
+// on the small grids of the deep levels.  DHFWI_NN_HALO=0 turns it off.
 static bool halo_eligible(const FpropArgs &a, int epi, int *bh_n, int *bw_n, int *nimg) {
     const char *e = getenv("DHFWI_NN_HALO");
     if (e && strcmp(e, "0") == 0) return false;
-    const bool force = e && strcmp(e, "1") == 0;
     if (a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws || a.C % HCB != 0) return false;
     if (epi == EPI_BF16_CONVT) return false;
     if ((a.src_stride | a.src_off) & 7) return false;
@@ -1015,8 +1024,7 @@ static bool halo_eligible(const FpropArgs &a, int epi, int *bh_n, int *bw_n, int
     *nimg = (int)(a.M / HW);
     *bh_n = (a.Hs + HBH - 1) / HBH;
     *bw_n = (a.Ws + HBW - 1) / HBW;
-    const long long ctas = (long long)*nimg * *bh_n * *bw_n * ((a.N + 63) / 64);
-    return force || ctas >= 152 * 4;
+    return true;
 }
 
 void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
@@ -1030,6 +1038,7 @@ void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
         case EPI_BF16_LEAKY: halo_dispatch<EPI_BF16_LEAKY>(a, bh_n, bw_n, nimg, s); break;
         case EPI_BF16: halo_dispatch<EPI_BF16>(a, bh_n, bw_n, nimg, s); break;
         case EPI_F32: halo_dispatch<EPI_F32>(a, bh_n, bw_n, nimg, s); break;
+        case EPI_BF16_LEAKYBWD: halo_dispatch<EPI_BF16_LEAKYBWD>(a, bh_n, bw_n, nimg, s); break;
         default: halo_dispatch<EPI_F32_ADD>(a, bh_n, bw_n, nimg, s); break;
         }
         return;
@@ -1040,6 +1049,9 @@ void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
     case EPI_BF16: small ? fprop_launch<32, EPI_BF16>(a, s) : fprop_launch<64, EPI_BF16>(a, s); break;
     case EPI_BF16_CONVT: small ? fprop_launch<32, EPI_BF16_CONVT>(a, s) : fprop_launch<64, EPI_BF16_CONVT>(a, s); break;
     case EPI_F32: small ? fprop_launch<32, EPI_F32>(a, s) : fprop_launch<64, EPI_F32>(a, s); break;
+    case EPI_BF16_LEAKYBWD:
+        small ? fprop_launch<32, EPI_BF16_LEAKYBWD>(a, s) : fprop_launch<64, EPI_BF16_LEAKYBWD>(a, s);
+        break;
     default: small ? fprop_launch<32, EPI_F32_ADD>(a, s) : fprop_launch<64, EPI_F32_ADD>(a, s); break;
     }
 }

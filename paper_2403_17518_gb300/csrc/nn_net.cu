@@ -76,7 +76,7 @@ struct NetState {
     struct Views {
         __nv_bfloat16 *xin, *a_inc0;
         std::vector<__nv_bfloat16 *> cat, pool, tmp, dec0, dec1;
-        __nv_bfloat16 *bottom, *gbuf;
+        __nv_bfloat16 *bottom, *gbuf, *gbuf2;
         float *xf, *yf, *out, *dA, *dB;
         std::vector<float *> dskip;
     } V;
@@ -274,6 +274,7 @@ int layout(dhfwi_ctx *ctx, NetState &N, int n, int H, int W) {
     }
     const size_t o_bottom = take(2 * P(Lv) * C(Lv));
     const size_t o_gbuf = take(2 * max_pc2);
+    const size_t o_gbuf2 = take(2 * max_pc2);
     const size_t o_xf = take(4 * P(0));
     const size_t o_yf = take(4 * P(0));
     const size_t o_out = take(4 * P(0));
@@ -307,6 +308,7 @@ int layout(dhfwi_ctx *ctx, NetState &N, int n, int H, int W) {
     }
     N.V.bottom = bf(o_bottom);
     N.V.gbuf = bf(o_gbuf);
+    N.V.gbuf2 = bf(o_gbuf2);
     N.V.xf = fl(o_xf);
     N.V.yf = fl(o_yf);
     N.V.out = fl(o_out);
@@ -466,14 +468,32 @@ void forward(NetState &N, int n, int H, int W, cudaStream_t s) {
 // Backward of one conv + LeakyReLU block: dA (float, dense [P][co]) is the
 // gradient of its output a; x its (bf16) input.  Writes the weight and bias
 // gradients and, when dx != nullptr, the input gradient (float [P][ci]).
+// The layer's output gradient g (bf16) is either computed here from dA
+// (f32) and the layer's activation a, or given as g_in (already computed by
+// the previous block's fused epilogue).  The input gradient goes to dx (f32),
+// or, when next_g is set, straight into the next block's g: times the
+// LeakyReLU derivative of next_act, the input x's activation (the two give
+// the same bits as storing dx and running the activation backward after).
+struct FuseNext {
+    const __nv_bfloat16 *act = nullptr;
+    int stride = 0, off = 0;
+    __nv_bfloat16 *g = nullptr;
+};
+
 void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int as, int ao, const __nv_bfloat16 *x,
-               int xs, int xo, int ci, int nimg, int H, int W, float *dx, cudaStream_t s) {
+               int xs, int xo, int ci, int nimg, int H, int W, float *dx, cudaStream_t s,
+               const __nv_bfloat16 *g_in = nullptr, const FuseNext &next = FuseNext()) {
     const LayerDesc &d = N.L[li];
     const long long P = (long long)nimg * H * W;
-    launch_leaky_bwd(dA, a, as, ao, P, d.co, 0.2f, N.V.gbuf, s);
+    const __nv_bfloat16 *g = g_in;
+    if (!g) {
+        launch_leaky_bwd(dA, a, as, ao, P, d.co, 0.2f, N.V.gbuf, s);
+        g = N.V.gbuf;
+        N.launches++;
+    }
     WgradArgs w{};
     w.mode = WG_CONV;
-    w.g = N.V.gbuf;
+    w.g = g;
     w.g_stride = d.co;
     w.x = x;
     w.x_stride = xs;
@@ -490,14 +510,14 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
     const int sp = wgrad_splits(P, w.M, w.N);
     float *dw = li == 0 ? N.g0pad : N.grad + d.off;
     launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, s);
-    N.launches += 3;
+    N.launches += 2;
     if (li == 0) {
         launch_unpad_first_grad(N.g0pad, d.co, CPAD, N.grad + d.off, s);
         N.launches++;
     }
-    if (dx) {
+    if (dx || next.g) {
         FpropArgs a{};
-        a.src = N.V.gbuf;
+        a.src = g;
         a.src_stride = d.co;
         a.src_off = 0;
         a.Hs = H;
@@ -514,13 +534,22 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
         a.M = (int)P;
         a.N = ci;
         a.bt = N.wt16 + d.off;
-        a.dst_f32 = dx;
         a.dst_stride = ci;
         a.dst_off = 0;
         a.part = N.fp_part;
         a.part_floats = (long long)N.fp_part_floats;
         a.err = N.err;
-        launch_fprop(a, EPI_F32, s);
+        if (next.g) {
+            a.dst_bf16 = next.g;
+            a.act = next.act;
+            a.act_stride = next.stride;
+            a.act_off = next.off;
+            a.slope = 0.2f;
+            launch_fprop(a, EPI_BF16_LEAKYBWD, s);
+        } else {
+            a.dst_f32 = dx;
+            launch_fprop(a, EPI_F32, s);
+        }
         N.launches += 2;
     }
 }
@@ -542,11 +571,17 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         const int r = Lv - l;
         const int Hr = H >> r, Wr = W >> r;
         const long long Pr = (long long)n * Hr * Wr;
-        // up_l.1: output dec1, input dec0.
-        block_bwd(N, layer_index_up(N, l, 2), dA, V.dec1[r], C(r), 0, V.dec0[r], C(r), 0, C(r), n, Hr, Wr, dB, s);
+        // up_l.1: output dec1, input dec0; its input gradient goes straight into
+        // up_l.0's output gradient (dec0's activation backward fused).
+        FuseNext fu;
+        fu.act = V.dec0[r];
+        fu.stride = C(r);
+        fu.g = V.gbuf2;
+        block_bwd(N, layer_index_up(N, l, 2), dA, V.dec1[r], C(r), 0, V.dec0[r], C(r), 0, C(r), n, Hr, Wr, nullptr, s,
+                  nullptr, fu);
         // up_l.0: output dec0, input cat (2C).
-        block_bwd(N, layer_index_up(N, l, 1), dB, V.dec0[r], C(r), 0, V.cat[r], 2 * C(r), 0, 2 * C(r), n, Hr, Wr, dA,
-                  s);
+        block_bwd(N, layer_index_up(N, l, 1), nullptr, nullptr, 0, 0, V.cat[r], 2 * C(r), 0, 2 * C(r), n, Hr, Wr, dA,
+                  s, V.gbuf2);
         // dA = d(cat) [Pr][2C]: skip half kept, up half to bf16.
         cudaMemsetAsync(V.dskip[r], 0, sizeof(float) * Pr * C(r), s);
         launch_add_slice(dA, 2 * C(r), 0, Pr, C(r), V.dskip[r], s);
@@ -613,17 +648,26 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         }
         const __nv_bfloat16 *ar = r < Lv ? V.cat[r] : V.bottom;
         const int ars = r < Lv ? 2 * C(r) : C(r);
-        block_bwd(N, layer_index_down(N, r, 1), dA, ar, ars, 0, V.tmp[r], C(r), 0, C(r), n, Hr, Wr, dB, s);
-        block_bwd(N, layer_index_down(N, r, 0), dB, V.tmp[r], C(r), 0, V.pool[r], C(r - 1), 0, C(r - 1), n, Hr, Wr,
-                  dA, s);
+        FuseNext fd;
+        fd.act = V.tmp[r];
+        fd.stride = C(r);
+        fd.g = V.gbuf2;
+        block_bwd(N, layer_index_down(N, r, 1), dA, ar, ars, 0, V.tmp[r], C(r), 0, C(r), n, Hr, Wr, nullptr, s,
+                  nullptr, fd);
+        block_bwd(N, layer_index_down(N, r, 0), nullptr, nullptr, 0, 0, V.pool[r], C(r - 1), 0, C(r - 1), n, Hr, Wr,
+                  dA, s, V.gbuf2);
         launch_avgpool_bwd(dA, n, H >> (r - 1), W >> (r - 1), C(r - 1), dB, 0, s);
         N.launches++;
         std::swap(dA, dB);
     }
     launch_add_slice(V.dskip[0], C(0), 0, P0, C(0), dA, s);
     N.launches++;
-    block_bwd(N, 1, dA, V.cat[0], 2 * C(0), 0, V.a_inc0, C(0), 0, C(0), n, H, W, dB, s);
-    block_bwd(N, 0, dB, V.a_inc0, C(0), 0, V.xin, CPAD, 0, CPAD, n, H, W, nullptr, s);
+    FuseNext f0;
+    f0.act = V.a_inc0;
+    f0.stride = C(0);
+    f0.g = V.gbuf2;
+    block_bwd(N, 1, dA, V.cat[0], 2 * C(0), 0, V.a_inc0, C(0), 0, C(0), n, H, W, nullptr, s, nullptr, f0);
+    block_bwd(N, 0, nullptr, nullptr, 0, 0, V.xin, CPAD, 0, CPAD, n, H, W, nullptr, s, V.gbuf2);
 }
 
 // Loss of the current batch: MSE against yf; writes g_out (bf16) to the

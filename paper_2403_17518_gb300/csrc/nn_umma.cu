@@ -279,6 +279,15 @@ __global__ void __launch_bounds__(128) igemm_umma_kernel(FpropArgs P) {
                     const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
                     P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v[q] + P.bias[co]);
                 }
+            } else if (EPI == EPI_BF16_LEAKYBWD) {
+                const __nv_bfloat16 *ap = P.act + (long long)m * P.act_stride + P.act_off + nb;
+                __nv_bfloat16 *o = P.dst_bf16 + (long long)m * P.dst_stride + P.dst_off + nb;
+#pragma unroll
+                for (int q = 0; q < 16; q++)
+                    if (nb + q < P.N) {
+                        const float av = __bfloat162float(ap[q]);
+                        o[q] = __float2bfloat16_rn(v[q] * (av > 0.f ? 1.0f : P.slope));
+                    }
             } else {  // EPI_F32 / EPI_F32_ADD
                 float *o = P.dst_f32 + (long long)m * P.dst_stride + P.dst_off + nb;
 #pragma unroll
@@ -338,6 +347,7 @@ void launch_fprop_umma(const FpropArgs &a, int epi, cudaStream_t s) {
     case EPI_BF16: umma_dispatch<EPI_BF16>(a, s); break;
     case EPI_BF16_CONVT: umma_dispatch<EPI_BF16_CONVT>(a, s); break;
     case EPI_F32: umma_dispatch<EPI_F32>(a, s); break;
+    case EPI_BF16_LEAKYBWD: umma_dispatch<EPI_BF16_LEAKYBWD>(a, s); break;
     default: umma_dispatch<EPI_F32_ADD>(a, s); break;
     }
 }

@@ -46,9 +46,9 @@ def test_init_is_bitwise_identical(base, levels):
     assert np.array_equal(ctx.net_get(), onn.init_params(spec, 5))
 
 
-# The convolution GEMMs: mma.sync with per-tap gathers, mma.sync with the
-# shared-memory halo tile for 3x3 convolutions (forced for every eligible
-# layer), tcgen05.
+# The convolution GEMMs: mma.sync with per-tap gathers (halo tiles off),
+# mma.sync with the shared-memory halo tile for 3x3 convolutions (the
+# default), tcgen05 for the other forward-form GEMMs.
 GEMMS = ["mma", "halo", "tc"]
 
 
