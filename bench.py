@@ -54,19 +54,27 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--only", default="", choices=["", "fwd", "nn"],
-                   help="fwd: time batched forward modelling (model_shots) alone; nn: the network's training "
+    p.add_argument("--only", default="", choices=["", "fwd", "grad", "nn"],
+                   help="fwd: time batched forward modelling (model_shots) alone; grad: the FWI gradient "
+                        "(fwi_gradient: forward, segment recompute, adjoint) alone; nn: the network's training "
                         "and apply alone on seeded smooth images of the workload's size; used for profiling")
     p.add_argument("--nn-epochs", type=int, default=20)
+    p.add_argument("--shots", type=int, default=0,
+                   help="with --only fwd/grad: the first SHOTS shots of the batch (small profiling captures)")
     p.add_argument("--cold-epochs", type=int, default=COLD_EPOCHS,
                    help="epochs of the network's cold start before the timed region (setup only)")
     return p.parse_args()
 
 
-def make_case(name):
+def make_case(name, shots=0):
+    """The workload; shots > 0 keeps the first shots of the 64-shot batch
+    (profiling modes only: small captures of the same kernels)."""
     import synth
 
-    return synth.config2_case() if name == "config2" else synth.config1_case()
+    case = synth.config2_case() if name == "config2" else synth.config1_case()
+    if shots > 0 and shots < case.geom.n_shots:
+        case.geom = case.geom.subset(list(range(shots)))
+    return case
 
 
 def algorithmic_cells(case) -> int:
@@ -393,6 +401,32 @@ def run_forward_only(args, dist, ctx, case, geom, v0, d_out):
                           "bytes_per_cell": 16, "effective_GBps": round(16 * U / ms / 1e6, 1)}), flush=True)
 
 
+def run_gradient_only(args, dist, ctx, case, geom, v0, d_obs):
+    """The FWI gradient alone (fwi_gradient), for kernel profiling."""
+    import torch
+
+    grad = ctx.new_model()
+    ctx.set_timing(True)
+    for _ in range(args.warmup):
+        ctx.fwi_gradient(v0, geom, d_obs, grad=grad)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.fwi_gradient(v0, geom, d_obs, grad=grad)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    st = ctx.stats()
+    U = case.geom.cell_updates(case.nz, case.nb)
+    if dist.rank == 0:
+        print(json.dumps({"only": "grad", "workload": case.name, "ms_per_call": round(ms, 3),
+                          "forward_ms": round(st["phase_ms"][0], 3), "backward_ms": round(st["phase_ms"][1], 3),
+                          "step_variants": st["step_variant"], "launches_per_call": st["kernel_launches"],
+                          "gcell_per_s": round(2 * U / ms / 1e6, 3)}), flush=True)
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -408,7 +442,7 @@ def main():
 
     torch.cuda.set_device(dist.local)
     build()
-    case = make_case(args.workload)
+    case = make_case(args.workload, args.shots if args.only in ("fwd", "grad") else 0)
     if args.only == "nn":
         run_network_only(args, dist, case)
         dist.close()
@@ -420,8 +454,8 @@ def main():
     v0 = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
     d_obs = ctx.model_shots(v_true, geom)
     setup_launches = ctx.stats()["kernel_launches"]
-    if args.only == "fwd":
-        run_forward_only(args, dist, ctx, case, geom, v0, d_obs)
+    if args.only in ("fwd", "grad"):
+        (run_forward_only if args.only == "fwd" else run_gradient_only)(args, dist, ctx, case, geom, v0, d_obs)
         ctx.close()
         dist.close()
         return

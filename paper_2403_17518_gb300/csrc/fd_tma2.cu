@@ -305,10 +305,11 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
     }
     const int lxp = 2 * (tid % 32), lz0 = R2 * (tid / 32);
     const bool worker = tid < 256;
-    f2 kv2[R2];
-#pragma unroll
-    for (int rr = 0; rr < R2; rr++)
-        kv2[rr] = worker ? *reinterpret_cast<const f2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]) : 0ull;
+    const int j = T.x0 + lxp;
+    const int i0 = T.z0 + lz0;
+    const long long cbase = T.foff + (long long)i0 * pitch + j;
+    const int nrow = FULL ? R2 : min(R2, NZ - i0);
+    const bool ok = worker && (FULL || j < nxw), hi = FULL || j + 1 < nxw;
     __syncthreads();  // nu^k, D_nu^k complete on the grown tile
 
     // Data of step k-1 at the tile's receivers: D' = D_nu^k + kappa r^{k-2}.
@@ -322,15 +323,23 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
             }
         __syncthreads();
     }
-    mid();  // the stage is no longer read
+    mid();  // u and D_nu of the stage are no longer read (kappa is: it is refilled at the tile's end)
 
     // ---- step k-1 on the core (threads 0..255), imaging of both steps -----
     if (!worker) return;
-    const int j = T.x0 + lxp;
-    const int i0 = T.z0 + lz0;
-    const long long cbase = T.foff + (long long)i0 * pitch + j;
-    const int nrow = FULL ? R2 : min(R2, NZ - i0);
-    const bool ok = FULL || j < nxw, hi = FULL || j + 1 < nxw;
+    // Global operands (image accumulator, a^{k-1}, a^{k-2}) kept PF rows
+    // ahead of the arithmetic, so that their latency overlaps it.
+    constexpr int PF = 2;
+    f2 gq[PF], a1q[PF], a2q[PF];
+    auto fetch = [&](int rr, int q) {
+        const bool v = ok && rr < nrow;
+        const long long c = cbase + (long long)rr * pitch;
+        gq[q] = v ? *reinterpret_cast<const f2 *>(A.g + c) : 0ull;
+        a1q[q] = v ? *reinterpret_cast<const f2 *>(A.a + c) : 0ull;
+        a2q[q] = v ? *reinterpret_cast<const f2 *>(A.a2 + c) : 0ull;
+    };
+#pragma unroll
+    for (int q = 0; q < PF; q++) fetch(q, q);
     const bool image_k = T.nt > k - 1;  // the record reaches step k
     float wx0 = 1.f, wx1 = 1.f;
     if constexpr (!FULL) {
@@ -342,29 +351,31 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
     for (int r = 0; r < R2 + 2 * HALO; r++) zc[r] = *reinterpret_cast<const float2 *>(&V[lz0 + r][lxp + HALO]);
 #pragma unroll
     for (int rr = 0; rr < R2; rr++) {
+        const int q = rr % PF;
+        f2 g = gq[q];
+        const f2 a1 = a1q[q], a2 = a2q[q];
+        if (rr + PF < R2) fetch(rr + PF, q);
         if (!(ok && rr < nrow)) continue;
         const long long c = cbase + (long long)rr * pitch;
-        f2 gv = *reinterpret_cast<const f2 *>(A.g + c);
-        const f2 a1 = *reinterpret_cast<const f2 *>(A.a + c);
-        const f2 a2 = *reinterpret_cast<const f2 *>(A.a2 + c);
+        const f2 kv = *reinterpret_cast<const f2 *>(&S.k[lz0 + rr + HALO][lxp + HALO]);
         const f2 a = lap8x2_seg(reinterpret_cast<const float2 *>(&V[lz0 + rr + HALO][lxp]), zc + rr);
         const f2 nu = pk(zc[rr + HALO]);  // nu^k
         const f2 d1 = *reinterpret_cast<const f2 *>(&Dn[lz0 + rr + HALO][lxp + HALO]);
         f2 dn, nn;
         if constexpr (FULL) {
-            dn = fma2(kv2[rr], a, d1);
+            dn = fma2(kv, a, d1);
             nn = add2(nu, dn);
         } else {
             const float wz = sponge1(i0 + rr, NZ, nb);
             const f2 w = pk2(wz * wx0, wz * wx1);
-            dn = keep_lo(mul2(w, fma2(kv2[rr], a, d1)), hi);
+            dn = keep_lo(mul2(w, fma2(kv, a, d1)), hi);
             nn = keep_lo(fma2(w, nu, dn), hi);
         }
-        if (image_k) gv = keep_lo(fma2(a1, nu, gv), hi);
-        gv = keep_lo(fma2(a2, nn, gv), hi);
+        if (image_k) g = keep_lo(fma2(a1, nu, g), hi);
+        g = keep_lo(fma2(a2, nn, g), hi);
         *reinterpret_cast<f2 *>(A.dd_out + c) = dn;
         *reinterpret_cast<f2 *>(A.nun + c) = nn;
-        *reinterpret_cast<f2 *>(A.g + c) = gv;
+        *reinterpret_cast<f2 *>(A.g + c) = g;
     }
 }
 
@@ -392,15 +403,22 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
     }
     griddep_wait();
     griddep_launch_dependents();
-    auto issue = [&]() {
+    // The stage is refilled in two parts on one mbarrier phase: u and D_nu
+    // once the first step is done, kappa (read by the second step too) at
+    // the end of the tile.
+    auto issue_ud = [&]() {
         fence_proxy_async();
         mbar_expect_tx(bar, kFwd2StageBytes);
         tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO2, co.y - HALO2, co.x, bar);
         tma_load_3d(smem_u32(&S.d), &M.m[1], co.z - HALO, co.y - HALO, co.x, bar);
+    };
+    auto issue_k = [&]() {
+        fence_proxy_async();
         tma_load_3d(smem_u32(&S.k), &M.m[2], co.w - HALO, co.y - HALO, mc, bar);
     };
     if (leader) {
-        issue();
+        issue_ud();
+        issue_k();
         if (b + g < ntiles) fetch_coords(A.c.infos, b + g, co, mc);
     }
     __syncthreads();
@@ -414,14 +432,15 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
             return;
         }
         const bool more = tix + g < ntiles;
-        auto mid = [&]() {  // after a barrier: every thread is done with the stage
-            if (leader && more) issue();
+        auto mid = [&]() {  // after a barrier: every thread is done with u and D_nu
+            if (leader && more) issue_ud();
         };
         const TileInfo &T = tail->desc[0];
         if (T.flags & TI_INTERIOR2) adj_pair_tile<true>(A, S, V, Dn, T, tid, mid);
         else adj_pair_tile<false>(A, S, V, Dn, T, tid, mid);
-        __syncthreads();  // the descriptor, V and Dn are free
+        __syncthreads();  // kappa, the descriptor, V and Dn are free
         if (leader && more) {
+            issue_k();
             copy_desc(&tail->desc[0], &A.c.infos[tix + g]);
             if (tix + 2 * g < ntiles) fetch_coords(A.c.infos, tix + 2 * g, co, mc);
         }
