@@ -7,7 +7,9 @@ receivers and 3000-4000 samples each, all shots in one batched pass.
 
 One step = one deblurred FWI iteration, in the order of the paper:
   1. fwi_gradient: forward modelling + misfit + adjoint-state gradient
-     (forward pass with checkpoints, segment recomputation, adjoint pass);
+     (forward pass storing a^n of every step device memory holds -- all of
+     them on one GB300 -- checkpoints and segment recomputation for any
+     others, adjoint pass);
   2. born_demig of the gradient (background + scattered fields jointly);
   3. rtm_mig of those Born data -> the doubly migrated image (Eq. 15);
   4. deblur_train: warm-started U-Net training on the (doubly migrated
@@ -17,7 +19,7 @@ One step = one deblurred FWI iteration, in the order of the paper:
 value = algorithmic cell updates per second, Gcell-updates/s: per step
 6 U (forward U + adjoint U for the gradient, 2 U for Born, forward U +
 adjoint U for migration), U = sum over shots of nt_s x padded window cells.
-Checkpoint recomputation (2 U more per step) is overhead and not counted.
+Checkpoint recomputation (up to 2 U more per step) is overhead and not counted.
 
 --impl reference times the FP64 CPU oracle (the only other implementation
 of this path) on a bounded sample of the same workload.
@@ -42,6 +44,7 @@ if ROOT not in sys.path:
 METRIC = "FD Gcell-updates/s & HBM roofline %; model error vs GPU-s, deblurred vs plain"
 UNIT = "Gcell-updates/s"
 FWD_BYTES_PER_CELL = 16  # read u^n and D^n, write u^{n+1} and D^{n+1} (kappa: L2-resident shared model)
+HIST_BYTES_PER_CELL = 4  # and write a^n, where the forward pass stores the history
 
 
 def parse():
@@ -329,7 +332,8 @@ def workload_config(case, args):
         "receivers_range": [int(min(case.geom.nrec(s) for s in range(case.geom.n_shots))),
                             int(max(case.geom.nrec(s) for s in range(case.geom.n_shots)))],
         "cell_updates_per_step": algorithmic_cells(case),
-        "l2": "inputs larger than L2 (wavefield pools + checkpoints ~15 GB per step)",
+        "l2": "inputs larger than L2 (72 MB wavefield pools; the a^n history, ~250 GB, is written and read "
+              "once per gradient and migration call)",
         "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
     }
 
@@ -424,6 +428,7 @@ def run_gradient_only(args, dist, ctx, case, geom, v0, d_obs):
         print(json.dumps({"only": "grad", "workload": case.name, "ms_per_call": round(ms, 3),
                           "forward_ms": round(st["phase_ms"][0], 3), "backward_ms": round(st["phase_ms"][1], 3),
                           "step_variants": st["step_variant"], "launches_per_call": st["kernel_launches"],
+                          "history_steps": st["history_steps"], "workspace_gb": round(st["workspace_bytes"] / 1e9, 2),
                           "gcell_per_s": round(2 * U / ms / 1e6, 3)}), flush=True)
 
 
@@ -476,7 +481,7 @@ def main():
     ctx.deblur_train(dm1, grad, warm_start=False, epochs=args.cold_epochs, **NET)
     setup_launches += ctx.stats()["kernel_launches"]
     nn_ev = []
-    phase = {"ms": 0.0, "launches": 0, "cells": 0, "steps": 0}
+    phase = {"ms": 0.0, "launches": 0, "cells": 0, "steps": 0, "hist_cells": 0, "hist_steps": 0}
     nt_max = int(max(case.geom.nt))
     breakdown = {"forward_ms": 0.0, "backward_ms": 0.0, "born_ms": 0.0}
     launches = [0]
@@ -506,6 +511,8 @@ def main():
                 phase["ms"] += st["phase_ms"][0]
                 phase["launches"] += st["phase_launches"][0]
                 phase["cells"] += st["phase_cells"][0]
+                phase["hist_cells"] += st["history_cells"]
+                phase["hist_steps"] = max(phase["hist_steps"], st["history_steps"])
                 phase["steps"] += nt_max if st["phase_launches"][0] > 0 else 0
                 breakdown["forward_ms"] += st["phase_ms"][0]
                 breakdown["backward_ms"] += st["phase_ms"][1]
@@ -540,7 +547,8 @@ def main():
     peak, peak_kind = peaks()
     fwd_ms_per_launch = phase["ms"] / max(phase["launches"], 1)
     cells_per_launch = phase["cells"] / max(phase["launches"], 1)
-    achieved = FWD_BYTES_PER_CELL * phase["cells"] / (phase["ms"] / 1e3) / 1e9 if phase["ms"] > 0 else None
+    fwd_bytes = FWD_BYTES_PER_CELL * phase["cells"] + HIST_BYTES_PER_CELL * phase["hist_cells"]
+    achieved = fwd_bytes / (phase["ms"] / 1e3) / 1e9 if phase["ms"] > 0 else None
     # Two time steps per launch when the forward passes ran time-blocked.
     steps_per_launch = phase["steps"] / max(phase["launches"], 1)
     fwd_kernel = "fwd_pair_kernel" if steps_per_launch > 1.5 else forward_kernel(ctx.stats()["step_variant"][0])
@@ -606,7 +614,7 @@ def main():
                 "bound": "hbm", "achieved": round(achieved, 2) if achieved else None, "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
                 "traffic": round(traffic) if traffic else None,
-                "algorithmic_bytes_per_launch": round(FWD_BYTES_PER_CELL * cells_per_launch),
+                "algorithmic_bytes_per_launch": round(fwd_bytes / max(phase["launches"], 1)),
                 "avg_launch_ms": round(fwd_ms_per_launch, 6), "peak_kind": f"{peak_kind} (hbm_gbs)",
             },
             "cpu_baseline": cpu,
@@ -614,6 +622,8 @@ def main():
             "gpu_launches": int(launches[0]),
             "launches_before_timed_region": int(launches_before),
             "step_variants": ctx.stats()["step_variant"],
+            "history_steps": {"stored": phase["hist_steps"], "of": nt_max,
+                              "workspace_gb": round(ctx.stats()["workspace_bytes"] / 1e9, 2)},
             "phase_ms_per_step": dict({k: round(v / args.steps, 2) for k, v in breakdown.items()},
                                       network_ms=round(nn_ms, 2)),
             "roofline_network": {

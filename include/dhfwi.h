@@ -112,6 +112,15 @@ typedef struct {
     /* Step-kernel variant chosen by the autotuner for: forward, forward with
      * segment store, adjoint, Born (index into the library's variant table). */
     int step_variant[4];
+    /* Steps whose a^n (the Laplacian term of the forward update, which the
+     * gradient and migration images correlate with the adjoint field) the
+     * last fwi_gradient or rtm_mig call stored during its forward pass; the
+     * backward sweep recomputes the other steps from checkpoints.  The
+     * history is as long as device memory allows, or as DHFWI_HISTORY_MB
+     * (MiB, environment, 0 = none) caps it; results are the same bit for bit
+     * either way. */
+    int history_steps;
+    long long history_cells;   /* phase-0 cell updates that also stored a^n */
 } dhfwi_stats_t;
 
 /* Create a context on CUDA device `device` for grid `g`.  The context owns all
@@ -147,8 +156,9 @@ int model_shots(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, floa
  *   grad_dev   [nz][nx] device, written with dJ/dv (m/s)^-1 scaled units.
  *              The paper's g = L~^T (d_o - d_s) equals -grad.
  *   d_syn_dev  optional (may be NULL) packed synthetic records d_s.
- * Uses forward checkpoints and segment recomputation; synchronises the stream
- * when misfit_out is not NULL. */
+ * The forward pass stores a^n of as many steps as device memory allows (see
+ * history_steps in dhfwi_stats_t); the backward sweep recomputes the others
+ * from checkpoints.  Synchronises the stream when misfit_out is not NULL. */
 int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom,
                  const float *d_obs_dev, float *grad_dev, double *misfit_out, float *d_syn_dev,
                  void *stream);
@@ -165,7 +175,7 @@ int born_demig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, cons
 
 /* Migration img = L~^T d (Section 2.3.1 Eq. 13 applied to arbitrary data; the
  * exact transpose of born_demig with the same flags).  The doubly migrated
- * image of Eq. 15 is rtm_mig(born_demig(g)).
+ * image of Eq. 15 is rtm_mig(born_demig(g)).  Workspace as fwi_gradient.
  *   d_dev   packed records, device
  *   img_dev [nz][nx] device, written */
 int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const float *d_dev,

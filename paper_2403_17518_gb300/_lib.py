@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("checkpoint_every", ctypes.c_int), ("shot_groups", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_double), ("phase_ms", ctypes.c_double * 3),
                 ("phase_launches", ctypes.c_longlong * 3), ("phase_cells", ctypes.c_longlong * 3),
-                ("step_variant", ctypes.c_int * 4)]
+                ("step_variant", ctypes.c_int * 4), ("history_steps", ctypes.c_int),
+                ("history_cells", ctypes.c_longlong)]
 
 
 class TrainCfg(ctypes.Structure):

@@ -59,8 +59,16 @@ struct dhfwi_ctx {
     Plan plan;
     DevBuf kap, dkap, status, partial;
     DevBuf fields;          // general wavefield pools
-    DevBuf ck;              // checkpoints
-    DevBuf abuf;            // segment buffer of a^n
+    DevBuf ck;              // checkpoints of the segments that are recomputed
+    DevBuf abuf;            // segment buffer of a^n (recomputed segments)
+    // Stored a^n of the first hist_segs segments of ck_every steps, written by
+    // the forward pass and read by the backward sweep (no recompute there).
+    // Step n holds the active slots only: hoff[n] is its offset in floats.
+    DevBuf hist;
+    std::vector<long long> hoff;
+    int hist_segs = 0;
+    unsigned long long hist_plan = 0;  // plan hash and limit the split was made for
+    long long hist_limit = -2;
     DevBuf dtmp, rtmp;      // data-sized temporaries
     unsigned *h_status = nullptr;   // pinned
     double *h_partial = nullptr;    // pinned
@@ -561,6 +569,8 @@ int begin_call(dhfwi_ctx *ctx) {
     ctx->stats.cell_updates = 0;
     ctx->stats.kernel_launches = 0;
     ctx->stats.shot_groups = 1;
+    ctx->stats.history_steps = 0;
+    ctx->stats.history_cells = 0;
     for (int i = 0; i < 3; i++) {
         ctx->stats.phase_ms[i] = 0.0;
         ctx->stats.phase_launches[i] = 0;
@@ -595,7 +605,7 @@ int end_call(dhfwi_ctx *ctx) {
     ctx->stats.checkpoint_every = ctx->ck_every;
     for (int k = 0; k < 4; k++) ctx->stats.step_variant[k] = ctx->launch[k].variant;
     double ws = ctx->kap.bytes + ctx->dkap.bytes + ctx->fields.bytes + ctx->ck.bytes +
-                ctx->abuf.bytes + ctx->dtmp.bytes + ctx->rtmp.bytes;
+                ctx->abuf.bytes + ctx->hist.bytes + ctx->dtmp.bytes + ctx->rtmp.bytes;
     ctx->stats.workspace_bytes = ws;
     return DHFWI_OK;
 }
@@ -779,9 +789,10 @@ int forward_steps(dhfwi_ctx *ctx, FwdArgs &a, int n, int n_end, float *&cur, flo
 
 // Forward pass over all steps.  State pools uA (u^0), uB (scratch), dd
 // (D^0) and dd2 (scratch) must be zeroed by the caller.  d (nullable)
-// receives samples; ck (nullable) receives (u^n, D^n) every K steps (K
-// even), two pools per checkpoint.
-int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, float *d, float *ck, int K,
+// receives samples.  With backward set (workspace from ensure_backward_ws)
+// the pass also stores a^n of the steps kept in the history and, at the
+// start of every other segment of K steps, the checkpoint (u^n, D^n).
+int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, float *d, bool backward,
                 cudaStream_t st) {
     const Plan &P = ctx->plan;
     FwdArgs a{};
@@ -790,37 +801,50 @@ int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, flo
     float *cur = uA, *nxt = uB, *dcur = dd, *dnxt = dd2;
     const long long pool = P.pool_floats;
     const bool blocking = time_blocking();
+    const int K = ctx->ck_every, S = backward ? ctx->hist_segs : 0;
+    const int H = std::min(S * K, P.nt_max);  // steps whose a^n are stored
+    float *ck = (float *)ctx->ck.p, *hist = (float *)ctx->hist.p;
+    auto slot = [&](int n) -> float * { return n < H ? hist + ctx->hoff[n] : nullptr; };
     const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
     phase_begin(ctx, 0, st);
     for (int n = 0; n < P.nt_max;) {
-        if (ck && n % K == 0) {
-            const long long j = n / K;
+        // K and H are even and two-step launches start at even n: a launch
+        // never straddles a segment or the end of the history.
+        if (backward && n >= H && n % K == 0) {
+            const long long j = n / K - S;
             a.ck_u = ck + (2 * j) * pool;
             a.ck_d = ck + (2 * j + 1) * pool;
         } else {
             a.ck_u = a.ck_d = nullptr;
         }
-        const int rc = forward_steps(ctx, a, n, P.nt_max, cur, nxt, dcur, dnxt, ctx->launch[0], blocking,
-                                     [](int) -> float * { return nullptr; }, st);
+        const long long cn = ctx->stats.cell_updates;
+        const int rc = forward_steps(ctx, a, n, P.nt_max, cur, nxt, dcur, dnxt, ctx->launch[n < H ? 1 : 0], blocking,
+                                     slot, st);
         if (rc < 0) return rc;
+        if (n < H) ctx->stats.history_cells += ctx->stats.cell_updates - cn;
         n += rc;
     }
+    if (backward) ctx->stats.history_steps = H;
     phase_end(ctx, 0, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
     CK(cudaGetLastError());
     return DHFWI_OK;
 }
 
-// Backward sweep: recompute each segment from its checkpoint (u and D start
-// in the checkpoint pools and alternate with the work pools w and w2), then
-// the adjoint steps over it with the data r injected; image accumulated in
-// gpool.  Adjoint state pools nuA, nuB, nud, nud2 must be zeroed by the
-// caller; with time blocking the adjoint also advances two steps per launch.
-int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float *w2, float *nuA, float *nuB,
-                 float *nud, float *nud2, float *gpool, const float *r, cudaStream_t st) {
+// Backward sweep, segment by segment from the last: a^n of a segment comes
+// from the history, or is recomputed from the segment's checkpoint (u and D
+// start in the checkpoint pools and alternate with the work pools w and w2)
+// into the segment buffer; then the adjoint steps over it with the data r
+// injected, the image accumulated in gpool.  Adjoint state pools nuA, nuB,
+// nud, nud2 must be zeroed by the caller; with time blocking the adjoint
+// also advances two steps per launch.
+int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *nuA, float *nuB, float *nud, float *nud2, float *gpool,
+                 const float *r, cudaStream_t st) {
     const Plan &P = ctx->plan;
     const long long pool = P.pool_floats;
+    const int K = ctx->ck_every, S = ctx->hist_segs;
     const int nseg = (P.nt_max + K - 1) / K;
     const bool blocking = time_blocking();
+    float *ck = (float *)ctx->ck.p, *abuf = (float *)ctx->abuf.p, *hist = (float *)ctx->hist.p;
     FwdArgs f{};
     f.c = common(ctx);
     AdjArgs b{};
@@ -832,28 +856,33 @@ int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float 
     phase_begin(ctx, 1, st);
     for (int js = nseg - 1; js >= 0; js--) {
         const int n0 = js * K, n1 = std::min(n0 + K, P.nt_max);
-        float *cur = ck + (2 * (long long)js) * pool, *nxt = w;
-        float *dcur = ck + (2 * (long long)js + 1) * pool, *dnxt = w2;
-        f.d = nullptr;
-        f.ck_u = f.ck_d = nullptr;
-        auto slot = [&](int n) { return abuf + (long long)(n - n0) * pool; };
-        for (int n = n0; n < n1;) {
-            const int rc = forward_steps(ctx, f, n, n1, cur, nxt, dcur, dnxt, ctx->launch[1], blocking, slot, st);
-            if (rc < 0) return rc;
-            n += rc;
+        const bool stored = js < S;
+        auto slot = [&](int n) -> float * {
+            return stored ? hist + ctx->hoff[n] : abuf + (long long)(n - n0) * pool;
+        };
+        if (!stored) {
+            float *cur = ck + (2 * (long long)(js - S)) * pool, *nxt = w;
+            float *dcur = ck + (2 * (long long)(js - S) + 1) * pool, *dnxt = w2;
+            f.d = nullptr;
+            f.ck_u = f.ck_d = nullptr;
+            for (int n = n0; n < n1;) {
+                const int rc = forward_steps(ctx, f, n, n1, cur, nxt, dcur, dnxt, ctx->launch[1], blocking, slot, st);
+                if (rc < 0) return rc;
+                n += rc;
+            }
         }
         for (int k = n1; k >= n0 + 1;) {
             b.nu = ncur;
             b.nun = nnxt;
             b.dd = dcur_nu;
-            b.a = abuf + (long long)(k - 1 - n0) * pool;
+            b.a = slot(k - 1);
             b.k = k;
             if (blocking && k - 1 >= n0 + 1) {
                 // Steps k and k-1: the data of step k go into D_nu first.
                 const int nrt = P.rtiles_prefix[active_slots(P, k - 1)];
                 launch_adj_inject(b, (const int *)P.d_rtiles.p, nrt, st);
                 b.dd_out = dnxt_nu;
-                b.a2 = abuf + (long long)(k - 2 - n0) * pool;
+                b.a2 = slot(k - 2);
                 TileMaps M;
                 int rc = adj_pair_maps(ctx, b, &M);
                 if (rc) return rc;
@@ -880,30 +909,103 @@ int run_backward(dhfwi_ctx *ctx, float *ck, int K, float *abuf, float *w, float 
     return DHFWI_OK;
 }
 
-// Workspace for a backward-capable pass: 2 field pools + image pool + 2 adjoint
-// pools, nseg checkpoint pairs, K segment slots.
-int ensure_backward_ws(dhfwi_ctx *ctx, int *K_out) {
+// Cap on the stored history in bytes from DHFWI_HISTORY_MB (MiB): -1 when
+// unset (as much as device memory allows), 0 for none.
+long long history_limit() {
+    const char *e = std::getenv("DHFWI_HISTORY_MB");
+    if (!e || !*e) return -1;
+    const long long mb = std::atoll(e);
+    return mb < 0 ? -1 : mb << 20;
+}
+
+// Workspace for a backward-capable pass: the field pools; the history of
+// a^n for the first S segments of K steps (K even) and, for the other
+// segments, a checkpoint pair each plus the K-slot segment buffer.  The
+// history trades memory for the recompute of those segments: it holds the
+// active slots of each step only (sum over shots of nt x NZ x pitch floats,
+// plus one pool so that a tensor map over any step stays inside it).  S is
+// as large as DHFWI_HISTORY_MB allows, else as device memory allows with
+// max(16 GiB, 1/16 of the device) left free; chosen once per plan.
+int ensure_backward_ws(dhfwi_ctx *ctx) {
     const Plan &P = ctx->plan;
     const size_t pool = sizeof(float) * (size_t)P.pool_floats;
-    int K = ctx->ck_every;
     int rc = ensure(ctx, ctx->fields, NPOOLS * pool, "wavefield pools");
     if (rc) return rc;
-    for (int attempt = 0; attempt < 2; attempt++) {
+    const long long limit = history_limit();
+    if (ctx->hist_plan != P.hash || ctx->hist_limit != limit) {
+        const int K = ctx->ck_every;
         const int nseg = (P.nt_max + K - 1) / K;
-        rc = ensure(ctx, ctx->ck, 2 * (size_t)nseg * pool, "checkpoints");
+        const size_t slot = sizeof(float) * (size_t)ctx->NZ * P.pitch;
+        std::vector<size_t> seg(nseg, 0);
+        for (int n = 0; n < P.nt_max; n++) seg[n / K] += (size_t)active_slots(P, n) * slot;
+        release(ctx->hist);
+        size_t avail;
+        if (limit >= 0) {
+            avail = (size_t)limit;
+        } else {
+            release(ctx->ck);
+            release(ctx->abuf);
+            size_t fr = 0, tot = 0;
+            CK(cudaMemGetInfo(&fr, &tot));
+            const size_t reserve = std::max<size_t>(16ull << 30, tot / 16);
+            avail = fr > reserve ? fr - reserve : 0;
+        }
+        // Largest S whose history (and, in the automatic case, the
+        // checkpoints and segment buffer of the rest) fits.
+        int S = 0;
+        size_t h = pool;
+        for (int t = 1; t <= nseg; t++) {
+            h += seg[t - 1];
+            const size_t rest = t < nseg ? (2 * (size_t)(nseg - t) + (size_t)std::min(K, P.nt_max)) * pool : 0;
+            if (h + (limit >= 0 ? 0 : rest) <= avail) S = t;
+        }
+        if (S > 0) {
+            size_t hb = pool;
+            for (int t = 0; t < S; t++) hb += seg[t];
+            if (ensure(ctx, ctx->hist, hb, "wavefield history") != DHFWI_OK) {
+                ctx->err.clear();
+                S = 0;
+            }
+        }
+        ctx->hist_segs = S;
+        ctx->hoff.assign((size_t)std::min(S * K, P.nt_max), 0);
+        long long off = 0;
+        for (size_t n = 0; n < ctx->hoff.size(); n++) {
+            ctx->hoff[n] = off;
+            off += (long long)active_slots(P, (int)n) * ctx->NZ * P.pitch;
+        }
+        ctx->hist_plan = P.hash;
+        ctx->hist_limit = limit;
+    }
+    // Checkpoints and segment buffer of the recomputed segments.  Out of
+    // memory: drop the history first, then fall back to ~sqrt(2 nt)
+    // segments, which minimises 2 nt/K + K.
+    for (int attempt = 0; attempt < 3; attempt++) {
+        const int K = ctx->ck_every, S = ctx->hist_segs;
+        const int nseg = (P.nt_max + K - 1) / K;
+        if (S >= nseg) {
+            release(ctx->ck);
+            release(ctx->abuf);
+            return DHFWI_OK;
+        }
+        rc = ensure(ctx, ctx->ck, 2 * (size_t)(nseg - S) * pool, "checkpoints");
         if (!rc) rc = ensure(ctx, ctx->abuf, (size_t)std::min(K, P.nt_max) * pool, "segment buffer");
-        if (!rc) break;
         if (rc != DHFWI_ERR_OOM) return rc;
-        // Fall back to ~sqrt(2 nt) segments, which minimises 2 nt/K + K.
         release(ctx->ck);
         release(ctx->abuf);
-        K = std::max(K, (int)std::ceil(std::sqrt(2.0 * P.nt_max)));
-        K += K & 1;  // checkpoints at even steps: a two-step launch never straddles one
+        if (attempt == 2) break;
+        ctx->err.clear();
+        if (S > 0) {
+            release(ctx->hist);
+            ctx->hist_segs = 0;
+            ctx->hoff.clear();
+        } else {
+            int K2 = std::max(K, (int)std::ceil(std::sqrt(2.0 * P.nt_max)));
+            K2 += K2 & 1;  // checkpoints at even steps: a two-step launch never straddles one
+            ctx->ck_every = K2;
+        }
     }
-    if (rc) return rc;
-    *K_out = K;
-    ctx->ck_every = K;
-    return DHFWI_OK;
+    return rc;
 }
 
 }  // namespace
@@ -964,7 +1066,7 @@ void dhfwi_destroy(dhfwi_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     DevBuf *bufs[] = {&ctx->kap, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
-                      &ctx->ck, &ctx->abuf, &ctx->dtmp, &ctx->rtmp, &ctx->plan.d_shots, &ctx->plan.d_tiles,
+                      &ctx->ck, &ctx->abuf, &ctx->hist, &ctx->dtmp, &ctx->rtmp, &ctx->plan.d_shots, &ctx->plan.d_tiles,
                       &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav, &ctx->plan.d_infos,
                       &ctx->plan.d_rtiles};
     for (DevBuf *b : bufs) release(*b);
@@ -1017,7 +1119,7 @@ int model_shots(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, floa
     float *uA = (float *)ctx->fields.p, *uB = uA + ctx->plan.pool_floats, *ud = uB + ctx->plan.pool_floats;
     float *ud2 = ud + ctx->plan.pool_floats;
     CK(cudaMemsetAsync(uA, 0, 4 * pool, st));
-    if ((rc = run_forward(ctx, uA, uB, ud, ud2, d_dev, nullptr, 2, st))) return rc;
+    if ((rc = run_forward(ctx, uA, uB, ud, ud2, d_dev, false, st))) return rc;
     return end_call(ctx);
 }
 
@@ -1031,8 +1133,7 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     if ((rc = prep_model(ctx, v_dev, nullptr, 0, st))) return rc;
     if ((rc = autotune(ctx, st))) return rc;
     const Plan &P = ctx->plan;
-    int K = 0;
-    if ((rc = ensure_backward_ws(ctx, &K))) return rc;
+    if ((rc = ensure_backward_ws(ctx))) return rc;
     const size_t nd = (size_t)P.n_data;
     if ((rc = ensure(ctx, ctx->rtmp, sizeof(float) * std::max<size_t>(nd, 1), "residual"))) return rc;
     float *dsyn = d_syn_dev;
@@ -1047,13 +1148,12 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
     // Checkpoints are staged back as halo tiles: their padding columns, which
     // no kernel writes, must read as zero.
-    CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
-    if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, dsyn, (float *)ctx->ck.p, K, st))) return rc;
+    if (ctx->ck.p) CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
+    if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, dsyn, true, st))) return rc;
     float *r = (float *)ctx->rtmp.p;
     launch_residual(dsyn, d_obs_dev, r, (long long)nd, (double *)ctx->partial.p, RESID_BLOCKS, st);
     ctx->stats.kernel_launches++;
-    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, uB, nuA, nuB, nud, F + 8 * pool, gp,
-                           r, st)))
+    if ((rc = run_backward(ctx, uA, uB, nuA, nuB, nud, F + 8 * pool, gp, r, st)))
         return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v_dev, 0, grad_dev, st);
@@ -1122,8 +1222,7 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
     if ((rc = prep_model(ctx, v0_dev, nullptr, 0, st))) return rc;
     if ((rc = autotune(ctx, st))) return rc;
     const Plan &P = ctx->plan;
-    int K = 0;
-    if ((rc = ensure_backward_ws(ctx, &K))) return rc;
+    if ((rc = ensure_backward_ws(ctx))) return rc;
     const long long pool = P.pool_floats;
     float *F = (float *)ctx->fields.p;
     float *uA = F, *uB = F + pool, *ud = F + 2 * pool;
@@ -1131,10 +1230,9 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
     CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
     // Checkpoints are staged back as halo tiles: their padding columns, which
     // no kernel writes, must read as zero.
-    CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
-    if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, nullptr, (float *)ctx->ck.p, K, st))) return rc;
-    if ((rc = run_backward(ctx, (float *)ctx->ck.p, K, (float *)ctx->abuf.p, uA, uB, nuA, nuB, nud, F + 8 * pool, gp,
-                           d_dev, st)))
+    if (ctx->ck.p) CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
+    if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, nullptr, true, st))) return rc;
+    if ((rc = run_backward(ctx, uA, uB, nuA, nuB, nud, F + 8 * pool, gp, d_dev, st)))
         return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v0_dev, flags == DHFWI_REL, img_dev, st);

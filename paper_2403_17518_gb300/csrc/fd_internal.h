@@ -111,9 +111,9 @@ struct FwdArgs {
     const float *u;   // pool: u^n
     float *un;        // pool: u^{n+1} (written)
     float *dd;        // pool: D^n, overwritten with D^{n+1}
-    float *ck_u;      // nullable: store u^n here (checkpoint)
+    float *ck_u;      // nullable: store u^n here (checkpoint; ignored when a_out is set)
     float *ck_d;      // nullable: store D^n here (checkpoint)
-    float *a_out;     // nullable: store a^n = D u^n + q^n (segment buffer slot)
+    float *a_out;     // nullable: store a^n = D u^n + q^n (history or segment buffer slot)
     float *d;         // nullable: packed records, sample n written from u^{n+1}
     int n;
     // Two-step kernel only (steps n and n+1 in one launch): D^n is read with a

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) fwd_step_kernel(FwdArgs A, i
         }
         const Tile tn = A.c.tiles[tix + 1];
         __syncthreads();
-        if (!STORE_A && A.d && tn.rec_begin > t.rec_begin) {
+        if (A.d && tn.rec_begin > t.rec_begin) {
 #pragma unroll
             for (int rr = 0; rr < R; rr++) sm2<float2>(&S.u[lz0 + rr + HALO][lxp + HALO]) = out[rr];
             __syncthreads();

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1)
         [&](const TmaFwdStage &S, const TileInfo &T) {
             if (T.flags & TI_FULL_FWD) fwd_rows<R, STORE_A, true>(A, S, T, lxp, lz0);
             else fwd_rows<R, STORE_A, false>(A, S, T, lxp, lz0);
-            if (!STORE_A && A.d && T.rec_end > T.rec_begin) sample_from_pool<NT>(A.c, T, A.un, A.d, A.n);
+            if (A.d && T.rec_end > T.rec_begin) sample_from_pool<NT>(A.c, T, A.un, A.d, A.n);
         });
 }
 

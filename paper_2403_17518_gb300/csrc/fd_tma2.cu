@@ -123,7 +123,7 @@ __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, 
     mid();
 
     // Receivers: sample n is u^{n+1}.
-    if (!STORE_A && A.d) {
+    if (A.d) {
         for (int e = T.rec_begin + tid; e < T.rec_end; e += NT2) {
             const TileRec tr = A.c.recs[e];
             A.d[T.doff + (long long)n * T.nrec + tr.r] = V[tr.cell / TX + HALO][tr.cell % TX + HALO];
@@ -181,7 +181,7 @@ __device__ __forceinline__ void pair_tile(const FwdArgs &A, const Fwd2Stage &S, 
         }
     }
     // Receivers: sample n+1 is u^{n+2}, read back from the pool.
-    if (!STORE_A && A.d && T.rec_end > T.rec_begin) sample_from_pool<NT2>(A.c, T, A.un, A.d, n + 1);
+    if (A.d && T.rec_end > T.rec_begin) sample_from_pool<NT2>(A.c, T, A.un, A.d, n + 1);
 }
 
 // Tile loop: one stage, refilled in the middle of a tile (see mid() in
@@ -329,18 +329,20 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
     if (!worker) return;
     // Global operands (image accumulator, a^{k-1}, a^{k-2}) kept PF rows
     // ahead of the arithmetic, so that their latency overlaps it.
+    // a^{k-1} exists only where the record reaches step k (a stored history
+    // holds the shots active at each step only).
+    const bool image_k = T.nt > k - 1;
     constexpr int PF = 2;
     f2 gq[PF], a1q[PF], a2q[PF];
     auto fetch = [&](int rr, int q) {
         const bool v = ok && rr < nrow;
         const long long c = cbase + (long long)rr * pitch;
         gq[q] = v ? *reinterpret_cast<const f2 *>(A.g + c) : 0ull;
-        a1q[q] = v ? *reinterpret_cast<const f2 *>(A.a + c) : 0ull;
+        a1q[q] = v && image_k ? *reinterpret_cast<const f2 *>(A.a + c) : 0ull;
         a2q[q] = v ? *reinterpret_cast<const f2 *>(A.a2 + c) : 0ull;
     };
 #pragma unroll
     for (int q = 0; q < PF; q++) fetch(q, q);
-    const bool image_k = T.nt > k - 1;  // the record reaches step k
     float wx0 = 1.f, wx1 = 1.f;
     if constexpr (!FULL) {
         wx0 = sponge1(j, nxw, nb);

@@ -10,7 +10,10 @@ bit):
   kernels take a single step at the end of a record);
 * a window three columns wide, a window on the model's edge with the source
   next to it;
-* a source on a window's edge column.
+* a source on a window's edge column;
+
+and with a^n taken from the stored history, recomputed from checkpoints, or
+both.
 """
 import numpy as np
 import pytest
@@ -55,10 +58,14 @@ CASE = _case()
 DV = f32(synth.gaussian_field((CASE.nz, CASE.nx), seed=43))
 
 
-def _run(blocking, monkeypatch):
+def _run(blocking, monkeypatch, history_mb=None):
     import torch
 
     monkeypatch.setenv("DHFWI_TIME_BLOCK", "1" if blocking else "0")
+    if history_mb is None:
+        monkeypatch.delenv("DHFWI_HISTORY_MB", raising=False)
+    else:
+        monkeypatch.setenv("DHFWI_HISTORY_MB", str(history_mb))
     c = CASE
     ctx = gpu_ctx(c)
     geom = f32_geom(c.geom)
@@ -107,6 +114,18 @@ def test_edge_geometry_two_step_bitwise(monkeypatch):
     for k in ("d", "ds", "g", "m", "b"):
         np.testing.assert_array_equal(two[k], one[k], err_msg=k)
     assert two["J"] == one["J"]
+
+
+@pytest.mark.parametrize("history_mb", [0, 40])
+def test_edge_geometry_recompute_bitwise(history_mb, monkeypatch):
+    """a^n recomputed from checkpoints for every segment (0), or for all but
+    the first (a 40 MiB history holds one segment of this case): the same
+    results bit for bit as the full history."""
+    full = _run(True, monkeypatch)
+    part = _run(True, monkeypatch, history_mb)
+    for k in ("d", "ds", "g", "m", "b"):
+        np.testing.assert_array_equal(part[k], full[k], err_msg=k)
+    assert part["J"] == full["J"]
 
 
 def test_edge_case_layout():

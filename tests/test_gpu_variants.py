@@ -2,7 +2,8 @@
 TMA staging with 4/8/16, and the two-step time-blocked forward kernel)
 computes the same arithmetic in the same order, so records, gradients and
 images agree bit for bit across variants, and each matches the FP64 oracle
-within 1e-5.
+within 1e-5.  So do the three ways the backward sweep gets a^n: stored
+history, checkpoint recompute, or history for some segments only.
 
 The case has odd window widths of different sizes (a common pool pitch
 leaves padding columns that the TMA variants read as the zero boundary),
@@ -53,10 +54,12 @@ def _run(variant, monkeypatch, blocking=False):
     ds = torch.empty(geom.n_data, dtype=torch.float32, device="cuda")
     J, g = ctx.fwi_gradient(v0, geom, d_obs, d_syn=ds)
     m = ctx.rtm_mig(v0, geom, d_obs)
-    used = ctx.stats()["step_variant"]
+    st = ctx.stats()
+    used = st["step_variant"]
     b = ctx.born_demig(v0, geom, to_dev(DV))
     ctx.close()
-    return {"d": to_host(d), "ds": to_host(ds), "g": to_host(g), "m": to_host(m), "b": to_host(b), "J": J}, used
+    return {"d": to_host(d), "ds": to_host(ds), "g": to_host(g), "m": to_host(m), "b": to_host(b), "J": J,
+            "history_steps": st["history_steps"], "checkpoint_every": st["checkpoint_every"]}, used
 
 
 @pytest.fixture(scope="module")
@@ -98,6 +101,39 @@ def test_two_step_kernel_agrees_bitwise(variant, reference_variant, monkeypatch)
     step; nt_max is even and the checkpoint segments are 50 steps."""
     assert CASE.geom.nt[1] % 2 == 1
     out, used = _run(variant, monkeypatch, blocking=True)
+    for k in KEYS:
+        np.testing.assert_array_equal(out[k], reference_variant[k], err_msg=k)
+    assert out["J"] == reference_variant["J"]
+
+
+def history_cap_mb(case, segs, K=50):
+    """MiB that hold the a^n history of the first `segs` segments of K steps:
+    each step keeps its active shots (nt > n) as NZ x pitch slots, plus one
+    spare pool of all shots."""
+    g, nb = case.geom, case.nb
+    NZ = case.nz + 2 * nb
+    pitch = -(-int((g.win_x1 - g.win_x0).max() + 2 * nb) // 64) * 64
+    slot = 4 * NZ * pitch
+    nt = np.asarray(g.nt)
+    total = slot * len(nt) + sum(int((nt > n).sum()) * slot for n in range(min(segs * K, int(nt.max()))))
+    return -(-total // (1 << 20))
+
+
+@pytest.mark.parametrize("blocking", [False, True])
+@pytest.mark.parametrize("history", ["none", "first-segment", "all"])
+def test_history_modes_agree_bitwise(history, blocking, reference_variant, monkeypatch):
+    """The backward sweep takes a^n from the history stored by the forward
+    pass, or recomputes it from checkpoints, or both (a history of the first
+    of five segments, the cap set through DHFWI_HISTORY_MB): the same
+    records, gradient and image bit for bit."""
+    if history == "all":
+        monkeypatch.delenv("DHFWI_HISTORY_MB", raising=False)
+    else:
+        monkeypatch.setenv("DHFWI_HISTORY_MB", "0" if history == "none" else str(history_cap_mb(CASE, 1)))
+    out, _ = _run(4, monkeypatch, blocking=blocking)
+    K, nt_max = out["checkpoint_every"], int(CASE.geom.nt.max())
+    assert K == 50 and -(-nt_max // K) == 5
+    assert out["history_steps"] == {"none": 0, "first-segment": K, "all": nt_max}[history]
     for k in KEYS:
         np.testing.assert_array_equal(out[k], reference_variant[k], err_msg=k)
     assert out["J"] == reference_variant["J"]
