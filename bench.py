@@ -59,24 +59,32 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--only", default="", choices=["", "fwd", "grad", "nn"],
                    help="fwd: time batched forward modelling (model_shots) alone; grad: the FWI gradient "
-                        "(fwi_gradient: forward, segment recompute, adjoint) alone; nn: the network's training "
+                        "(fwi_gradient: forward storing the history, adjoint) alone; nn: the network's training "
                         "and apply alone on seeded smooth images of the workload's size; used for profiling")
     p.add_argument("--nn-epochs", type=int, default=20)
     p.add_argument("--shots", type=int, default=0,
                    help="with --only fwd/grad: the first SHOTS shots of the batch (small profiling captures)")
+    p.add_argument("--nt", type=int, default=0,
+                   help="with --only fwd/grad: records truncated to NT samples (small profiling captures)")
     p.add_argument("--cold-epochs", type=int, default=COLD_EPOCHS,
                    help="epochs of the network's cold start before the timed region (setup only)")
     return p.parse_args()
 
 
-def make_case(name, shots=0):
-    """The workload; shots > 0 keeps the first shots of the 64-shot batch
-    (profiling modes only: small captures of the same kernels)."""
+def make_case(name, shots=0, nt=0):
+    """The workload; shots > 0 keeps the first shots of the 64-shot batch,
+    nt > 0 truncates the records (profiling modes only: small captures of
+    the same kernels)."""
+    import numpy as np
     import synth
 
     case = synth.config2_case() if name == "config2" else synth.config1_case()
     if shots > 0 and shots < case.geom.n_shots:
         case.geom = case.geom.subset(list(range(shots)))
+    if nt > 0:
+        g = case.geom
+        g.nt = np.minimum(g.nt, nt).astype(np.int32)
+        g.wavelet = np.ascontiguousarray(g.wavelet[..., : int(g.nt.max())])
     return case
 
 
@@ -447,7 +455,8 @@ def main():
 
     torch.cuda.set_device(dist.local)
     build()
-    case = make_case(args.workload, args.shots if args.only in ("fwd", "grad") else 0)
+    prof = args.only in ("fwd", "grad")
+    case = make_case(args.workload, args.shots if prof else 0, args.nt if prof else 0)
     if args.only == "nn":
         run_network_only(args, dist, case)
         dist.close()

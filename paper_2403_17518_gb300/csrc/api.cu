@@ -744,12 +744,18 @@ int pair_maps(dhfwi_ctx *ctx, const FwdArgs &a, TileMaps *M) {
 }
 
 // Maps of a two-step adjoint launch (nu^{k+1} with the doubled halo, D_nu
-// with its ring, kappa with its ring).
+// with its ring, kappa with its ring; the image, a^{k-1} and a^{k-2}, which
+// the kernel only prefetches into L2).  A history step's map spans all
+// slots from its base: the spare pool at the history's end keeps it inside
+// the allocation.
 int adj_pair_maps(dhfwi_ctx *ctx, const AdjArgs &b, TileMaps *M) {
     int rc;
     if ((rc = tensor_map(ctx, b.nu, MAP_POOL_HALO2, &M->m[0]))) return rc;
     if ((rc = tensor_map(ctx, b.dd, MAP_POOL_HALO, &M->m[1]))) return rc;
-    return tensor_map(ctx, b.c.kap, MAP_MODEL_HALO, &M->m[2]);
+    if ((rc = tensor_map(ctx, b.c.kap, MAP_MODEL_HALO, &M->m[2]))) return rc;
+    if ((rc = tensor_map(ctx, b.g, MAP_POOL_CELL, &M->m[3]))) return rc;
+    if ((rc = tensor_map(ctx, b.a, MAP_POOL_CELL, &M->m[4]))) return rc;
+    return tensor_map(ctx, b.a2, MAP_POOL_CELL, &M->m[5]);
 }
 
 // Advances the forward state from step n: two steps with one two-step launch

@@ -68,6 +68,15 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map
         : "memory");
 }
 
+// 3-D tile of a tensor map prefetched into L2 (no shared memory, nothing to
+// wait for); coordinates as for tma_load_3d.
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap *map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<unsigned long long>(map)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Tile pipeline of the TMA kernels.  Shared memory holds the stages, then
 // PipeTail (two mbarriers and the two stages' tile descriptors).  With two

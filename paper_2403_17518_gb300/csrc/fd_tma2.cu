@@ -310,6 +310,23 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
     const long long cbase = T.foff + (long long)i0 * pitch + j;
     const int nrow = FULL ? R2 : min(R2, NZ - i0);
     const bool ok = worker && (FULL || j < nxw), hi = FULL || j + 1 < nxw;
+    // Global operands of the second step (image accumulator, a^{k-1},
+    // a^{k-2}; prefetched into L2 a tile ahead) kept PF rows ahead of the
+    // arithmetic, the first rows requested before the barrier.  a^{k-1}
+    // exists only where the record reaches step k (a stored history holds
+    // the shots active at each step only).
+    const bool image_k = T.nt > k - 1;
+    constexpr int PF = 2;
+    f2 gq[PF], a1q[PF], a2q[PF];
+    auto fetch = [&](int rr, int q) {
+        const bool v = ok && rr < nrow;
+        const long long c = cbase + (long long)rr * pitch;
+        gq[q] = v ? *reinterpret_cast<const f2 *>(A.g + c) : 0ull;
+        a1q[q] = v && image_k ? *reinterpret_cast<const f2 *>(A.a + c) : 0ull;
+        a2q[q] = v ? *reinterpret_cast<const f2 *>(A.a2 + c) : 0ull;
+    };
+#pragma unroll
+    for (int q = 0; q < PF; q++) fetch(q, q);
     __syncthreads();  // nu^k, D_nu^k complete on the grown tile
 
     // Data of step k-1 at the tile's receivers: D' = D_nu^k + kappa r^{k-2}.
@@ -327,22 +344,6 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
 
     // ---- step k-1 on the core (threads 0..255), imaging of both steps -----
     if (!worker) return;
-    // Global operands (image accumulator, a^{k-1}, a^{k-2}) kept PF rows
-    // ahead of the arithmetic, so that their latency overlaps it.
-    // a^{k-1} exists only where the record reaches step k (a stored history
-    // holds the shots active at each step only).
-    const bool image_k = T.nt > k - 1;
-    constexpr int PF = 2;
-    f2 gq[PF], a1q[PF], a2q[PF];
-    auto fetch = [&](int rr, int q) {
-        const bool v = ok && rr < nrow;
-        const long long c = cbase + (long long)rr * pitch;
-        gq[q] = v ? *reinterpret_cast<const f2 *>(A.g + c) : 0ull;
-        a1q[q] = v && image_k ? *reinterpret_cast<const f2 *>(A.a + c) : 0ull;
-        a2q[q] = v ? *reinterpret_cast<const f2 *>(A.a2 + c) : 0ull;
-    };
-#pragma unroll
-    for (int q = 0; q < PF; q++) fetch(q, q);
     float wx0 = 1.f, wx1 = 1.f;
     if constexpr (!FULL) {
         wx0 = sponge1(j, nxw, nb);
@@ -407,12 +408,17 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
     griddep_launch_dependents();
     // The stage is refilled in two parts on one mbarrier phase: u and D_nu
     // once the first step is done, kappa (read by the second step too) at
-    // the end of the tile.
+    // the end of the tile.  The same tile's image, a^{k-1} and a^{k-2},
+    // which the second step loads from global memory, are prefetched into L2
+    // then, a tile ahead of their use.
     auto issue_ud = [&]() {
         fence_proxy_async();
         mbar_expect_tx(bar, kFwd2StageBytes);
         tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO2, co.y - HALO2, co.x, bar);
         tma_load_3d(smem_u32(&S.d), &M.m[1], co.z - HALO, co.y - HALO, co.x, bar);
+        tma_prefetch_l2_3d(&M.m[3], co.z, co.y, co.x);
+        tma_prefetch_l2_3d(&M.m[4], co.z, co.y, co.x);
+        tma_prefetch_l2_3d(&M.m[5], co.z, co.y, co.x);
     };
     auto issue_k = [&]() {
         fence_proxy_async();
