@@ -57,6 +57,9 @@ struct WgradArgs {
 // DHFWI_NN_GEMM=tc.
 void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s);
 void launch_fprop_umma(const FpropArgs &a, int epi, cudaStream_t s);
+// TMA-fed tcgen05 kernel for the 3x3 convolutions with >= 64 output channels
+// (nn_umma.cu); false when the GEMM is not of that form (nothing launched).
+bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s);
 // Sum of split-k partials a.part[splits][M][N] with the epilogue epi.
 void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s);
 int wgrad_splits(long long kpix, int M, int N);

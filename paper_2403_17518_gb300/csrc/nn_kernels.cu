@@ -980,13 +980,17 @@ void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s
     }
 }
 
-// DHFWI_NN_GEMM=tc selects the tcgen05 GEMM for the forward-form
-// convolutions; the mma.sync kernel is the default (faster on this network's
-// gather-bound shapes, see nn_umma.cu).  Read per launch so a process can
-// switch.
-static bool use_umma() {
+// Forward-form GEMM kernels.  By default the 3x3 convolutions with at least
+// 64 output channels run on the TMA-fed tcgen05 kernel (nn_umma.cu) and the
+// rest on mma.sync (halo tiles for the 3x3 convolutions).  DHFWI_NN_GEMM=mma
+// keeps every GEMM on mma.sync; DHFWI_NN_GEMM=tc puts every one on the
+// cp.async-fed tcgen05 kernel.  Read per launch so a process can switch.
+enum { GEMM_DEFAULT = 0, GEMM_UMMA_ALL = 1, GEMM_MMA_ONLY = 2 };
+static int gemm_mode() {
     const char *e = getenv("DHFWI_NN_GEMM");
-    return e && strcmp(e, "tc") == 0;
+    if (e && strcmp(e, "tc") == 0) return GEMM_UMMA_ALL;
+    if (e && strcmp(e, "mma") == 0) return GEMM_MMA_ONLY;
+    return GEMM_DEFAULT;
 }
 
 template <int BN, int EPI>
@@ -1028,10 +1032,12 @@ static bool halo_eligible(const FpropArgs &a, int epi, int *bh_n, int *bw_n, int
 }
 
 void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
-    if (use_umma()) {
+    const int mode = gemm_mode();
+    if (mode == GEMM_UMMA_ALL) {
         launch_fprop_umma(a, epi, s);
         return;
     }
+    if (mode == GEMM_DEFAULT && launch_conv3_tma(a, epi, s)) return;
     int bh_n, bw_n, nimg;
     if (halo_eligible(a, epi, &bh_n, &bw_n, &nimg)) {
         switch (epi) {

@@ -17,6 +17,7 @@
 //
 // Waits are bounded (~1 s): on a timeout the CTA sets *err, waits for its
 // own copies, frees its tensor memory and leaves.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -47,6 +48,14 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 __device__ __forceinline__ uint64_t smem_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// The same for a K-major operand written by TMA with the 128-byte swizzle:
+// rows of 128 B (64 bf16 of k) in 8-row atoms of 1024 B (stride-byte offset
+// 1024; the leading-byte offset is unused), layout type 2 (SWIZZLE_128B) in
+// bits 61-63.  A K = 16 slice starts 32 B further along the row.
+__device__ __forceinline__ uint64_t smem_desc_sw128(unsigned saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
 // BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -331,6 +340,360 @@ void umma_launch(const FpropArgs &a, cudaStream_t s) {
     if (splits > 1) launch_fprop_reduce(b, EPI, splits, s);
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed, warp-specialised tcgen05 implicit GEMM for the 3x3 convolutions
+// (stride 1, same grid in and out, C a multiple of 32, N >= 64): the forward
+// and input-gradient GEMMs of the double-conv blocks below the top level.
+//
+// Output tile: 128 pixels (BI images x BH rows x BW columns: 1 x 8 x 16, or
+// 2 x 8 x 8 and 1 x 16 x 8 on grids at most 8 wide) by BN output channels.
+// K runs over (tap, block of BK channels); a k-tile is one tap's BK
+// channels, so its A operand is the source shifted by that tap, loaded as
+// 4-D TMA boxes (channels, BW, BH, BI) that the TMA fills with zero outside
+// the grid (the convolution's padding).  With BK = 64 one box of 64
+// channels lands as 128 rows of 128 B in the 128-byte swizzled K-major
+// layout (8-row atoms of 1024 B), and the weights B^T [N][K] as BN such rows.
+// With BK = 32 (32-channel sources) one box per 16-byte k-chunk lands as 128
+// rows of 16 B, a column of 8-row core matrices: the no-swizzle K-major
+// layout with core matrices 128 B apart along m and k-chunks 2048 B apart
+// (leading-byte offset 2048, stride-byte offset 128); the weights the same
+// way, BN rows per k-chunk (leading-byte offset 16 BN).
+//
+// Warps: 0 = producer (one lane issues a stage's TMA loads once the MMAs
+// that read it have completed), 1 = TMEM owner and MMA issuer (one lane),
+// 2-5 = epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31).  Hand-off on
+// mbarriers: full[s] (the stage's bytes landed), empty[s] (tcgen05.commit of
+// the MMAs that read it), accf (the accumulator is final).  Waits are
+// bounded (~1 s): the thread that runs out sets *err, the producer still
+// waits for its loads in flight, and TMEM is freed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init1(unsigned bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, int c0, int c1, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+struct ConvTile {
+    int BW, BH, BI;  // tile = BI images x BH rows x BW columns (128 pixels)
+    int tw, th;      // tiles along w and h (then images)
+    int nk_all;      // k-tiles over all taps
+    int nimg;
+};
+
+constexpr int TMA_THREADS = 192;
+
+template <int BN, int BK, int ST>
+constexpr size_t conv3_tma_smem() {
+    return (size_t)ST * (128 * BK * 2 + BN * BK * 2) + 2048;  // + alignment slack, barriers, TMEM address
+}
+
+template <int BN, int BK, int ST, int EPI>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    conv3_tma_umma_kernel(FpropArgs P, const __grid_constant__ CUtensorMap mapA,
+                          const __grid_constant__ CUtensorMap mapB, ConvTile G) {
+    // BK = 64: 128-byte rows, swizzled; BK = 32: 16-byte k-chunks, no swizzle.
+    constexpr bool SW128 = BK == 64;
+    constexpr unsigned A_CH = 128 * 16, B_CH = BN * 16;  // bytes of one 16-byte k-chunk (no swizzle)
+    constexpr unsigned A_BYTES = A_CH * (BK / 8), B_BYTES = B_CH * (BK / 8), STAGE = A_BYTES + B_BYTES;
+    constexpr unsigned TMEM_COLS = BN;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    const unsigned sbase = (smem_u32(smraw) + 1023u) & ~1023u;
+    unsigned char *tail = smraw + (sbase - smem_u32(smraw)) + ST * STAGE;
+    const unsigned full0 = smem_u32(tail), empty0 = full0 + 8 * ST, accf = empty0 + 8 * ST;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(tail + 16 * ST + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int t = blockIdx.x;
+    const int w0 = (t % G.tw) * G.BW;
+    t /= G.tw;
+    const int h0 = (t % G.th) * G.BH;
+    const int i0 = (t / G.th) * G.BI;
+    const int n0 = blockIdx.y * BN;
+    const int per = (G.nk_all + gridDim.z - 1) / gridDim.z;
+    const int kt0 = blockIdx.z * per;
+    const int nk = max(0, min(G.nk_all, kt0 + per) - kt0);
+
+    if (tid == 0) {
+        for (int s = 0; s < ST; s++) {
+            mbar_init1(full0 + 8 * s);
+            mbar_init1(empty0 + 8 * s);
+        }
+        mbar_init1(accf);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kt = 0; kt < nk; kt++) {
+                const int s = kt % ST;
+                if (kt >= ST && !mbar_wait(empty0 + 8 * s, ((kt / ST) - 1) & 1u)) {
+                    if (P.err) atomicExch(P.err, 1u);
+                    break;
+                }
+                const unsigned fb = full0 + 8 * s;
+                mbar_expect_tx(fb, STAGE);
+                const int k = (kt0 + kt) * BK;
+                const int tap = k / P.C, c0 = k - tap * P.C;
+                const int ws = w0 + P.dw[tap], hs = h0 + P.dh[tap];
+                const unsigned sa = sbase + s * STAGE, sb = sa + A_BYTES;
+                if constexpr (SW128) {  // one 128-byte-wide box per operand
+                    tma_load_4d(sa, &mapA, c0, ws, hs, i0, fb);
+                    tma_load_2d(sb, &mapB, k, n0, fb);
+                } else {  // one box per 16-byte k-chunk
+#pragma unroll
+                    for (int ch = 0; ch < BK / 8; ch++)
+                        tma_load_4d(sa + ch * A_CH, &mapA, c0 + 8 * ch, ws, hs, i0, fb);
+#pragma unroll
+                    for (int ch = 0; ch < BK / 8; ch++) tma_load_2d(sb + ch * B_CH, &mapB, k + 8 * ch, n0, fb);
+                }
+                issued = kt + 1;
+            }
+            // Loads in flight land before the CTA leaves (bounded as well).
+            for (int kt = max(0, issued - ST); kt < issued; kt++) mbar_wait(full0 + 8 * (kt % ST), (kt / ST) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16(UBM, BN);
+            for (int kt = 0; kt < nk; kt++) {
+                const int s = kt % ST;
+                if (!mbar_wait(full0 + 8 * s, (kt / ST) & 1u)) {
+                    if (P.err) atomicExch(P.err, 1u);
+                    break;
+                }
+                tc_fence_after();
+                const unsigned sa = sbase + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; kk++) {
+                    const uint64_t da = SW128 ? smem_desc_sw128(sa + 32 * kk) : smem_desc(sa + 2 * kk * A_CH, A_CH, 128);
+                    const uint64_t db = SW128 ? smem_desc_sw128(sb + 32 * kk) : smem_desc(sb + 2 * kk * B_CH, B_CH, 128);
+                    mma_bf16(tmem, da, db, IDESC, (kt > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(accf);  // arrives once every MMA issued above is complete
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        const bool good = mbar_wait(accf, 0);
+        tc_fence_after();
+        if (!good) {
+            if (lane == 0 && P.err) atomicExch(P.err, 1u);
+        } else {
+            const int r = q * 32 + lane;  // tile row = TMEM lane
+            const int per_img = G.BW * G.BH;
+            const int img = i0 + r / per_img, rem = r % per_img;
+            const int ho = h0 + rem / G.BW, wo = w0 + rem % G.BW;
+            const bool valid = img < G.nimg && ho < P.Ho && wo < P.Wo;
+            const long long m = ((long long)img * P.Ho + ho) * P.Wo + wo;
+            const unsigned trow = tmem + ((unsigned)(q * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                if (n0 + c0 >= P.N) break;  // uniform across the warp
+                float v[16];
+                if (nk > 0) tmem_ld16(trow + c0, v);
+                else
+#pragma unroll
+                    for (int e = 0; e < 16; e++) v[e] = 0.f;
+                if (!valid) continue;
+                const int nb = n0 + c0;
+                const bool full16 = nb + 16 <= P.N;
+                if (P.part) {  // split-k: raw partial sums
+                    float *out = P.part + (long long)blockIdx.z * P.M * P.N + m * P.N + nb;
+                    if (full16 && (P.N & 3) == 0) {
+#pragma unroll
+                        for (int e = 0; e < 16; e += 4)
+                            *reinterpret_cast<float4 *>(out + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (nb + e < P.N) out[e] = v[e];
+                    }
+                    continue;
+                }
+                if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
+                    __nv_bfloat16 *o = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
+                    __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        float x = v[e] + (nb + e < P.N ? P.bias[nb + e] : 0.f);
+                        if (EPI == EPI_BF16_LEAKY) x = x > 0.f ? x : P.slope * x;
+                        h[e] = __float2bfloat16_rn(x);
+                    }
+                    if (full16 && ((P.dst_stride | P.dst_off) & 7) == 0) {
+                        reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
+                        reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (nb + e < P.N) o[e] = h[e];
+                    }
+                } else if (EPI == EPI_BF16_LEAKYBWD) {
+                    const __nv_bfloat16 *ap = P.act + m * P.act_stride + P.act_off + nb;
+                    __nv_bfloat16 *o = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
+                    if (full16 && (((uintptr_t)ap | (uintptr_t)o) & 15) == 0) {  // 16-byte loads and stores
+                        __align__(16) __nv_bfloat16 av[16], h[16];
+                        reinterpret_cast<uint4 *>(av)[0] = reinterpret_cast<const uint4 *>(ap)[0];
+                        reinterpret_cast<uint4 *>(av)[1] = reinterpret_cast<const uint4 *>(ap)[1];
+#pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            h[e] = __float2bfloat16_rn(v[e] * (__bfloat162float(av[e]) > 0.f ? 1.0f : P.slope));
+                        reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
+                        reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (nb + e < P.N) {
+                                const float av = __bfloat162float(ap[e]);
+                                o[e] = __float2bfloat16_rn(v[e] * (av > 0.f ? 1.0f : P.slope));
+                            }
+                    }
+                } else {  // EPI_F32 / EPI_F32_ADD
+                    float *o = P.dst_f32 + m * P.dst_stride + P.dst_off + nb;
+                    if (full16 && ((uintptr_t)o & 15) == 0) {  // 16-byte loads and stores
+#pragma unroll
+                        for (int e = 0; e < 16; e += 4) {
+                            float4 x = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                            if (EPI == EPI_F32_ADD) {
+                                const float4 y = *reinterpret_cast<const float4 *>(o + e);
+                                x.x += y.x;
+                                x.y += y.y;
+                                x.z += y.z;
+                                x.w += y.w;
+                            }
+                            *reinterpret_cast<float4 *>(o + e) = x;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (nb + e < P.N) o[e] = (EPI == EPI_F32_ADD ? o[e] : 0.f) + v[e];
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tma_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+template <int BN, int BK, int EPI>
+bool conv3_tma_launch(const FpropArgs &a, const ConvTile &G0, cudaStream_t s) {
+    constexpr int ST = (BK == 32 ? 2 : 1) * (BN <= 128 ? 3 : 4);
+    const size_t sm = conv3_tma_smem<BN, BK, ST>();
+    EncodeTiledFn enc = tma_encoder();
+    if (!enc) return false;
+    ConvTile G = G0;
+    G.nk_all = a.ntaps * a.C / BK;
+    // A: the source [img][h][w][c] (channel stride src_stride, slice at
+    // src_off), box (8, BW, BH, BI); B: the weights [N][K], box (8, BN).
+    CUtensorMap ma, mb;
+    {
+        const cuuint64_t es = sizeof(__nv_bfloat16);
+        cuuint64_t dims[4] = {(cuuint64_t)a.C, (cuuint64_t)a.Ws, (cuuint64_t)a.Hs, (cuuint64_t)G.nimg};
+        cuuint64_t str[3] = {es * a.src_stride, es * a.src_stride * a.Ws, es * a.src_stride * a.Ws * a.Hs};
+        const cuuint32_t inner = BK == 64 ? 64 : 8;
+        const CUtensorMapSwizzle swz = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE;
+        cuuint32_t box[4] = {inner, (cuuint32_t)G.BW, (cuuint32_t)G.BH, (cuuint32_t)G.BI}, estr[4] = {1, 1, 1, 1};
+        if (enc(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(a.src + a.src_off), dims, str, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+        const cuuint64_t K = (cuuint64_t)a.ntaps * a.C;
+        cuuint64_t dimsb[2] = {K, (cuuint64_t)a.N};
+        cuuint64_t strb[1] = {es * K};
+        cuuint32_t boxb[2] = {inner, (cuuint32_t)BN}, estrb[2] = {1, 1};
+        if (enc(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)a.bt, dimsb, strb, boxb, estrb,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(conv3_tma_umma_kernel<BN, BK, ST, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+        attr = true;
+    }
+    const int mt = G.tw * G.th * ((G.nimg + G.BI - 1) / G.BI);
+    const int tiles = mt * ((a.N + BN - 1) / BN);
+    int splits = 1;
+    if (a.part && a.part_floats > 0) {
+        // Split k when the tiles fill less than one wave, keeping at least 4
+        // k-tiles per split and the partials within their buffer.
+        const int want = (152 + tiles - 1) / tiles;
+        splits = std::min(want, G.nk_all / 4);
+        const long long cap = a.part_floats / ((long long)a.M * a.N);
+        if (splits > cap) splits = (int)cap;
+        if (splits < 2) splits = 1;
+    }
+    FpropArgs b = a;
+    if (splits == 1) b.part = nullptr;
+    dim3 grid(mt, (a.N + BN - 1) / BN, splits);
+    conv3_tma_umma_kernel<BN, BK, ST, EPI><<<grid, TMA_THREADS, sm, s>>>(b, ma, mb, G);
+    if (splits > 1) launch_fprop_reduce(b, EPI, splits, s);
+    return true;
+}
+
+template <int EPI>
+bool conv3_tma_dispatch(const FpropArgs &a, const ConvTile &G, cudaStream_t s) {
+    if (a.C % 64 == 0) {
+        if (a.N <= 64) return conv3_tma_launch<64, 64, EPI>(a, G, s);
+        if (a.N <= 128) return conv3_tma_launch<128, 64, EPI>(a, G, s);
+        return conv3_tma_launch<256, 64, EPI>(a, G, s);
+    }
+    if (a.N <= 64) return conv3_tma_launch<64, 32, EPI>(a, G, s);
+    if (a.N <= 128) return conv3_tma_launch<128, 32, EPI>(a, G, s);
+    return conv3_tma_launch<256, 32, EPI>(a, G, s);
+}
+
 template <int EPI>
 void umma_dispatch(const FpropArgs &a, cudaStream_t s) {
     if (a.N <= 32) umma_launch<32, EPI>(a, s);
@@ -340,6 +703,38 @@ void umma_dispatch(const FpropArgs &a, cudaStream_t s) {
 }
 
 }  // namespace
+
+// The TMA-fed kernel serves a GEMM when it is a 3x3 convolution (taps with
+// shifts in {-1, 0, 1}, stride 1, same grid in and out) with C a multiple of
+// 32, at least 64 output channels, 16-byte aligned operands and a row
+// stride that is a multiple of 8 channels.  Returns false (nothing launched)
+// otherwise.
+bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
+    if (epi == EPI_BF16_CONVT || a.N < 64 || a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws ||
+        a.C % 32 != 0 || a.C <= 0)
+        return false;
+    if (((a.src_stride | a.src_off) & 7) != 0) return false;
+    if (((uintptr_t)(a.src + a.src_off) & 15) != 0 || ((uintptr_t)a.bt & 15) != 0) return false;
+    for (int t = 0; t < 9; t++)
+        if (a.dh[t] < -1 || a.dh[t] > 1 || a.dw[t] < -1 || a.dw[t] > 1) return false;
+    const long long HW = (long long)a.Ho * a.Wo;
+    if (HW <= 0 || a.M % HW != 0) return false;
+    ConvTile G{};
+    G.nimg = (int)(a.M / HW);
+    G.BW = a.Wo > 8 ? 16 : 8;
+    G.BI = (G.BW == 8 && a.Ho <= 8) ? 2 : 1;
+    G.BH = 128 / (G.BW * G.BI);
+    G.tw = (a.Wo + G.BW - 1) / G.BW;
+    G.th = (a.Ho + G.BH - 1) / G.BH;
+    switch (epi) {
+    case EPI_BF16_LEAKY: return conv3_tma_dispatch<EPI_BF16_LEAKY>(a, G, s);
+    case EPI_BF16: return conv3_tma_dispatch<EPI_BF16>(a, G, s);
+    case EPI_F32: return conv3_tma_dispatch<EPI_F32>(a, G, s);
+    case EPI_BF16_LEAKYBWD: return conv3_tma_dispatch<EPI_BF16_LEAKYBWD>(a, G, s);
+    case EPI_F32_ADD: return conv3_tma_dispatch<EPI_F32_ADD>(a, G, s);
+    default: return false;
+    }
+}
 
 void launch_fprop_umma(const FpropArgs &a, int epi, cudaStream_t s) {
     switch (epi) {

@@ -49,12 +49,19 @@ def test_init_is_bitwise_identical(base, levels):
 # The convolution GEMMs: mma.sync with per-tap gathers (halo tiles off),
 # mma.sync with the shared-memory halo tile for 3x3 convolutions (the
 # default), tcgen05 for the other forward-form GEMMs.
-GEMMS = ["mma", "halo", "tc"]
+GEMMS = ["mma", "halo", "tc", "default"]
 
 
 def _set_gemm(monkeypatch, gemm):
-    monkeypatch.setenv("DHFWI_NN_GEMM", "tc" if gemm == "tc" else "mma")
-    monkeypatch.setenv("DHFWI_NN_HALO", "1" if gemm == "halo" else "0")
+    """mma: mma.sync gathering kernels only; halo: mma.sync with halo tiles;
+    tc: the cp.async-fed tcgen05 kernel for every forward-form GEMM; default:
+    the TMA-fed tcgen05 kernel for the 3x3 convolutions with >= 64 output
+    channels, halo tiles for the rest."""
+    if gemm == "default":
+        monkeypatch.delenv("DHFWI_NN_GEMM", raising=False)
+    else:
+        monkeypatch.setenv("DHFWI_NN_GEMM", "tc" if gemm == "tc" else "mma")
+    monkeypatch.setenv("DHFWI_NN_HALO", "0" if gemm == "mma" else "1")
 
 
 @pytest.mark.parametrize("gemm", GEMMS)
