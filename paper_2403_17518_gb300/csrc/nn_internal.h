@@ -84,6 +84,15 @@ void launch_adam(float *theta, const float *grad, float *m, float *v, long long 
                  float eps, int t, __nv_bfloat16 *shadow, cudaStream_t s);
 void launch_to_bf16(const float *x, long long n, __nv_bfloat16 *y, cudaStream_t s);
 void launch_transpose_w(const __nv_bfloat16 *w, int co, int taps, int ci, __nv_bfloat16 *wt, cudaStream_t s);
+// Several layers' transposes [co][taps][ci] -> [ci][taps][co] in one launch,
+// each at its parameter offset in w and wt.
+struct TransposeJobs {
+    static constexpr int MAX = 32;
+    int n;
+    long long off[MAX];
+    int co[MAX], taps[MAX], ci[MAX];
+};
+void launch_transpose_w_batch(const __nv_bfloat16 *w, __nv_bfloat16 *wt, const TransposeJobs &jobs, cudaStream_t s);
 void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cudaStream_t s);
 void launch_gather_patches(const float *img, int nx, const int *oz, const int *ox, const int *sel, int nb, int p,
                            const float *scale, int mute, float *dst, cudaStream_t s);

@@ -543,6 +543,49 @@ __global__ void avgpool_fwd_kernel(const __nv_bfloat16 *__restrict__ x, int xs, 
 }
 
 // dx[h][w] (+)= sum of dy/9 over the pooling windows containing (h, w).
+// Four channels per thread (C a multiple of 4, 16-byte aligned rows): the
+// same sums in the same order as avgpool_bwd_kernel.
+__global__ void avgpool_bwd4_kernel(const float *__restrict__ dy, int nimg, int H, int W, int C4,
+                                    float *__restrict__ dx, int accumulate) {
+    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
+    const long long n = (long long)nimg * H * W * C4;
+    const float4 *dy4 = reinterpret_cast<const float4 *>(dy);
+    float4 *dx4 = reinterpret_cast<float4 *>(dx);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C4);
+        const long long r0 = i / C4;
+        const int w = (int)(r0 % W);
+        const long long r1 = r0 / W;
+        const int h = (int)(r1 % H);
+        const long long img = r1 / H;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int ho = (h > 0 ? h / 2 : 0); ho <= (h + 1) / 2 && ho < Ho; ho++) {
+            if (2 * ho - 1 > h || 2 * ho + 1 < h) continue;
+            for (int wo = (w > 0 ? w / 2 : 0); wo <= (w + 1) / 2 && wo < Wo; wo++) {
+                if (2 * wo - 1 > w || 2 * wo + 1 < w) continue;
+                const float4 v = dy4[((img * Ho + ho) * Wo + wo) * C4 + c];
+                s.x += v.x;
+                s.y += v.y;
+                s.z += v.z;
+                s.w += v.w;
+            }
+        }
+        const float k = 1.0f / 9.0f;
+        s.x *= k;
+        s.y *= k;
+        s.z *= k;
+        s.w *= k;
+        if (accumulate) {
+            const float4 o = dx4[i];
+            s.x = o.x + s.x;
+            s.y = o.y + s.y;
+            s.z = o.z + s.z;
+            s.w = o.w + s.w;
+        }
+        dx4[i] = s;
+    }
+}
+
 __global__ void avgpool_bwd_kernel(const float *__restrict__ dy, int nimg, int H, int W, int C, float *__restrict__ dx,
                                    int accumulate) {
     const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
@@ -647,19 +690,29 @@ __global__ void conv1x1_bwd_data_kernel(const __nv_bfloat16 *__restrict__ g, lon
     }
 }
 
+// part[blk][c] for c < C, part[blk][C] = sum g over the block's `rows`
+// pixels.  Threads (c, j): channel c (blockDim.x = C + 1 rounded up to 32)
+// over the pixels p0 + j, p0 + j + S, ... (S = blockDim.y streams); the
+// streams are then summed in order j = 0, 1, ... (deterministic).
 __global__ void conv1x1_wgrad_partial_kernel(const __nv_bfloat16 *__restrict__ g, const __nv_bfloat16 *__restrict__ a,
                                              long long P, int C, int rows, float *__restrict__ part) {
-    // part[blk][c] for c < C, part[blk][C] = sum g
-    const int c = threadIdx.x;
+    extern __shared__ float red[];  // [S][blockDim.x]
+    const int c = threadIdx.x, j = threadIdx.y, S = blockDim.y;
     const long long p0 = (long long)blockIdx.x * rows;
     const long long p1 = p0 + rows < P ? p0 + rows : P;
-    if (c > C) return;
     float s = 0.f;
-    for (long long p = p0; p < p1; p++) {
-        const float gv = __bfloat162float(g[p]);
-        s += c < C ? gv * __bfloat162float(a[p * C + c]) : gv;
+    if (c <= C)
+        for (long long p = p0 + j; p < p1; p += S) {
+            const float gv = __bfloat162float(g[p]);
+            s += c < C ? gv * __bfloat162float(a[p * C + c]) : gv;
+        }
+    red[j * blockDim.x + c] = s;
+    __syncthreads();
+    if (j == 0 && c <= C) {
+        float t = red[c];
+        for (int q = 1; q < S; q++) t += red[q * blockDim.x + c];
+        part[(long long)blockIdx.x * (C + 1) + c] = t;
     }
-    part[(long long)blockIdx.x * (C + 1) + c] = s;
 }
 
 // Adam with bias correction (Adam's step t is 1-based), master weights fp32,
@@ -696,6 +749,22 @@ __global__ void transpose_w_kernel(const __nv_bfloat16 *__restrict__ w, int co, 
         const int t = (int)(r % taps);
         const int o = (int)(r / taps);
         wt[((long long)c * taps + t) * co + o] = w[i];
+    }
+}
+
+// The transposes of several layers in one launch: job j = blockIdx.y.
+__global__ void transpose_w_batch_kernel(const __nv_bfloat16 *__restrict__ w, __nv_bfloat16 *__restrict__ wt,
+                                         TransposeJobs J) {
+    const int j = blockIdx.y;
+    const long long off = J.off[j];
+    const int co = J.co[j], taps = J.taps[j], ci = J.ci[j];
+    const long long n = (long long)co * taps * ci;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % ci);
+        const long long r = i / ci;
+        const int t = (int)(r % taps);
+        const long long o = r / taps;
+        wt[off + ((long long)c * taps + t) * co + o] = w[off + i];
     }
 }
 
@@ -1114,7 +1183,10 @@ void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H,
 }
 void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *dx, int accumulate, cudaStream_t s) {
     const long long n = (long long)nimg * H * W * C;
-    avgpool_bwd_kernel<<<grid_for(n), 256, 0, s>>>(dy, nimg, H, W, C, dx, accumulate);
+    if (C % 4 == 0 && (((uintptr_t)dy | (uintptr_t)dx) & 15) == 0)
+        avgpool_bwd4_kernel<<<grid_for(n / 4), 256, 0, s>>>(dy, nimg, H, W, C / 4, dx, accumulate);
+    else
+        avgpool_bwd_kernel<<<grid_for(n), 256, 0, s>>>(dy, nimg, H, W, C, dx, accumulate);
 }
 void launch_leaky_bwd(const float *dA, const __nv_bfloat16 *a, int as, int ao, long long P, int C, float slope,
                       __nv_bfloat16 *g, cudaStream_t s) {
@@ -1140,7 +1212,10 @@ void launch_conv1x1_bwd(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long lon
     int rows = (int)((P + max_blocks - 1) / max_blocks);
     if (rows < 64) rows = 64;
     const int nblk = (int)((P + rows - 1) / rows);
-    conv1x1_wgrad_partial_kernel<<<nblk, ((C + 1 + 31) / 32) * 32, 0, s>>>(g, a, P, C, rows, part);
+    const int cx = ((C + 1 + 31) / 32) * 32;
+    const int streams = std::max(1, std::min(8, 1024 / cx));
+    conv1x1_wgrad_partial_kernel<<<nblk, dim3(cx, streams), sizeof(float) * cx * streams, s>>>(g, a, P, C, rows,
+                                                                                                 part);
     // dw_db[0..C) = dW, dw_db[C] = db: reuse the bias-final reduction over C+1 columns.
     bias_grad_final_kernel<<<(C + 1 + 127) / 128, 128, 0, s>>>(part, nblk, C + 1, dw_db);
 }
@@ -1155,6 +1230,14 @@ void launch_to_bf16(const float *x, long long n, __nv_bfloat16 *y, cudaStream_t 
 void launch_transpose_w(const __nv_bfloat16 *w, int co, int taps, int ci, __nv_bfloat16 *wt, cudaStream_t s) {
     transpose_w_kernel<<<grid_for((long long)co * taps * ci), 256, 0, s>>>(w, co, taps, ci, wt);
 }
+void launch_transpose_w_batch(const __nv_bfloat16 *w, __nv_bfloat16 *wt, const TransposeJobs &jobs, cudaStream_t s) {
+    if (jobs.n <= 0) return;
+    long long most = 0;
+    for (int j = 0; j < jobs.n; j++) most = std::max(most, (long long)jobs.co[j] * jobs.taps[j] * jobs.ci[j]);
+    const int gx = (int)std::min<long long>((most + 255) / 256, 152 * 4);
+    transpose_w_batch_kernel<<<dim3(gx, jobs.n), 256, 0, s>>>(w, wt, jobs);
+}
+
 void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cudaStream_t s) {
     input_pack_kernel<<<grid_for(P * Cp), 256, 0, s>>>(x, P, Cp, y);
 }

@@ -228,16 +228,26 @@ void refresh_weights(NetState &N, cudaStream_t s, bool shadow_from_theta) {
         launch_to_bf16(N.theta, N.nparams, N.w16, s);
         N.launches++;
     }
+    // Transposed copies of the 3x3 (but the first) and transposed-conv
+    // layers, in batches of up to TransposeJobs::MAX layers per launch.
+    TransposeJobs jobs{};
+    auto flush = [&]() {
+        if (jobs.n == 0) return;
+        launch_transpose_w_batch(N.w16, N.wt16, jobs, s);
+        N.launches++;
+        jobs.n = 0;
+    };
     for (size_t i = 0; i < N.L.size(); i++) {
         const LayerDesc &d = N.L[i];
-        if (d.kind == K_C3 && i != 0) {
-            launch_transpose_w(N.w16 + d.off, d.co, 9, d.ci, N.wt16 + d.off, s);
-            N.launches++;
-        } else if (d.kind == K_CT) {
-            launch_transpose_w(N.w16 + d.off, d.co, 4, d.ci, N.wt16 + d.off, s);
-            N.launches++;
-        }
+        const int taps = d.kind == K_C3 && i != 0 ? 9 : d.kind == K_CT ? 4 : 0;
+        if (!taps) continue;
+        jobs.off[jobs.n] = (long long)d.off;
+        jobs.co[jobs.n] = d.co;
+        jobs.taps[jobs.n] = taps;
+        jobs.ci[jobs.n] = d.ci;
+        if (++jobs.n == TransposeJobs::MAX) flush();
     }
+    flush();
     launch_pad_first_w(N.w16 + N.L[0].off, N.base, CPAD, N.w0pad, s);
     N.launches++;
 }
