@@ -60,3 +60,36 @@ def test_product_path_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
                 assert "liboracle" not in txt, f
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """Every field offset and struct size of the binding's ctypes mirrors
+    equals the C compiler's layout of include/dhfwi.h (a mismatch would pass
+    garbage through the ABI without any error)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2403_17518_gb300 import _lib
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"dhfwi_grid": _lib.Grid, "dhfwi_geom": _lib.Geom, "dhfwi_stats_t": _lib.Stats,
+               "dhfwi_train_cfg": _lib.TrainCfg}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dhfwi.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
