@@ -624,6 +624,91 @@ __global__ void leaky_bwd_kernel(const float *__restrict__ dA, const __nv_bfloat
     }
 }
 
+// Four channels per thread (C, strides and offsets multiples of 4, aligned
+// pointers): the same per-element arithmetic as the kernels above and below.
+struct alignas(8) Bf16x4 {
+    __nv_bfloat162 lo, hi;
+};
+__device__ __forceinline__ float4 bf4_to_f4(Bf16x4 v) {
+    const float2 a = __bfloat1622float2(v.lo), b = __bfloat1622float2(v.hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ Bf16x4 f4_to_bf4(float4 v) {
+    Bf16x4 r;
+    r.lo = __halves2bfloat162(__float2bfloat16_rn(v.x), __float2bfloat16_rn(v.y));
+    r.hi = __halves2bfloat162(__float2bfloat16_rn(v.z), __float2bfloat16_rn(v.w));
+    return r;
+}
+
+__global__ void leaky_bwd4_kernel(const float4 *__restrict__ dA, const __nv_bfloat16 *__restrict__ a, int as, int ao,
+                                  long long P, int C4, float slope, Bf16x4 *__restrict__ g) {
+    const long long n = P * C4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C4;
+        const int c = (int)(i - p * C4) * 4;
+        const float4 av = bf4_to_f4(*reinterpret_cast<const Bf16x4 *>(a + p * as + ao + c));
+        const float4 d = dA[i];
+        g[i] = f4_to_bf4(make_float4(d.x * (av.x > 0.f ? 1.0f : slope), d.y * (av.y > 0.f ? 1.0f : slope),
+                                     d.z * (av.z > 0.f ? 1.0f : slope), d.w * (av.w > 0.f ? 1.0f : slope)));
+    }
+}
+
+__global__ void f32_to_bf16_slice4_kernel(const float *__restrict__ x, int xs, int xo, long long P, int C4,
+                                          Bf16x4 *__restrict__ y) {
+    const long long n = P * C4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C4;
+        const int c = (int)(i - p * C4) * 4;
+        y[i] = f4_to_bf4(*reinterpret_cast<const float4 *>(x + p * xs + xo + c));
+    }
+}
+
+__global__ void add_slice4_kernel(const float *__restrict__ src, int ss, int so, long long P, int C4,
+                                  float4 *__restrict__ dst) {
+    const long long n = P * C4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C4;
+        const int c = (int)(i - p * C4) * 4;
+        const float4 v = *reinterpret_cast<const float4 *>(src + p * ss + so + c);
+        float4 d = dst[i];
+        d.x += v.x;
+        d.y += v.y;
+        d.z += v.z;
+        d.w += v.w;
+        dst[i] = d;
+    }
+}
+
+__global__ void avgpool_fwd4_kernel(const __nv_bfloat16 *__restrict__ x, int xs, int xo, int nimg, int H, int W,
+                                    int C4, Bf16x4 *__restrict__ y) {
+    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
+    const long long n = (long long)nimg * Ho * Wo * C4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C4) * 4;
+        long long r = i / C4;
+        const int wo = (int)(r % Wo);
+        r /= Wo;
+        const int ho = (int)(r % Ho);
+        const long long img = r / Ho;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int a = 0; a < 3; a++) {
+            const int h = 2 * ho + a - 1;
+            if (h < 0 || h >= H) continue;
+            for (int b = 0; b < 3; b++) {
+                const int w = 2 * wo + b - 1;
+                if (w < 0 || w >= W) continue;
+                const float4 v = bf4_to_f4(*reinterpret_cast<const Bf16x4 *>(x + ((img * H + h) * W + w) * xs + xo + c));
+                s.x += v.x;
+                s.y += v.y;
+                s.z += v.z;
+                s.w += v.w;
+            }
+        }
+        const float k = 1.0f / 9.0f;
+        y[i] = f4_to_bf4(make_float4(s.x * k, s.y * k, s.z * k, s.w * k));
+    }
+}
+
 // Copy channels [off, off+C) of a float32 [P][Ct] tensor into bf16 [P][C].
 __global__ void f32_to_bf16_slice_kernel(const float *__restrict__ x, int xs, int xo, long long P, int C,
                                          __nv_bfloat16 *__restrict__ y) {
@@ -1179,7 +1264,11 @@ void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, fl
 void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H, int W, int C, __nv_bfloat16 *y,
                         cudaStream_t s) {
     const long long n = (long long)nimg * ((H - 1) / 2 + 1) * ((W - 1) / 2 + 1) * C;
-    avgpool_fwd_kernel<<<grid_for(n), 256, 0, s>>>(x, xs, xo, nimg, H, W, C, y);
+    if (C % 4 == 0 && ((xs | xo) & 3) == 0 && (((uintptr_t)x | (uintptr_t)y) & 7) == 0)
+        avgpool_fwd4_kernel<<<grid_for(n / 4), 256, 0, s>>>(x, xs, xo, nimg, H, W, C / 4,
+                                                            reinterpret_cast<Bf16x4 *>(y));
+    else
+        avgpool_fwd_kernel<<<grid_for(n), 256, 0, s>>>(x, xs, xo, nimg, H, W, C, y);
 }
 void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *dx, int accumulate, cudaStream_t s) {
     const long long n = (long long)nimg * H * W * C;
@@ -1190,13 +1279,24 @@ void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *d
 }
 void launch_leaky_bwd(const float *dA, const __nv_bfloat16 *a, int as, int ao, long long P, int C, float slope,
                       __nv_bfloat16 *g, cudaStream_t s) {
-    leaky_bwd_kernel<<<grid_for(P * C), 256, 0, s>>>(dA, a, as, ao, P, C, slope, g);
+    if (C % 4 == 0 && ((as | ao) & 3) == 0 && (((uintptr_t)a | (uintptr_t)g) & 7) == 0 && ((uintptr_t)dA & 15) == 0)
+        leaky_bwd4_kernel<<<grid_for(P * C / 4), 256, 0, s>>>(reinterpret_cast<const float4 *>(dA), a, as, ao, P,
+                                                              C / 4, slope, reinterpret_cast<Bf16x4 *>(g));
+    else
+        leaky_bwd_kernel<<<grid_for(P * C), 256, 0, s>>>(dA, a, as, ao, P, C, slope, g);
 }
 void launch_f32_to_bf16_slice(const float *x, int xs, int xo, long long P, int C, __nv_bfloat16 *y, cudaStream_t s) {
-    f32_to_bf16_slice_kernel<<<grid_for(P * C), 256, 0, s>>>(x, xs, xo, P, C, y);
+    if (C % 4 == 0 && ((xs | xo) & 3) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 7) == 0)
+        f32_to_bf16_slice4_kernel<<<grid_for(P * C / 4), 256, 0, s>>>(x, xs, xo, P, C / 4,
+                                                                      reinterpret_cast<Bf16x4 *>(y));
+    else
+        f32_to_bf16_slice_kernel<<<grid_for(P * C), 256, 0, s>>>(x, xs, xo, P, C, y);
 }
 void launch_add_slice(const float *src, int ss, int so, long long P, int C, float *dst, cudaStream_t s) {
-    add_slice_kernel<<<grid_for(P * C), 256, 0, s>>>(src, ss, so, P, C, dst);
+    if (C % 4 == 0 && ((ss | so) & 3) == 0 && (((uintptr_t)src | (uintptr_t)dst) & 15) == 0)
+        add_slice4_kernel<<<grid_for(P * C / 4), 256, 0, s>>>(src, ss, so, P, C / 4, reinterpret_cast<float4 *>(dst));
+    else
+        add_slice_kernel<<<grid_for(P * C), 256, 0, s>>>(src, ss, so, P, C, dst);
 }
 void launch_conv1x1_fwd(const __nv_bfloat16 *a, int C, long long P, const __nv_bfloat16 *w, const float *b, float *out,
                         cudaStream_t s) {
