@@ -53,7 +53,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="config2", choices=["config2", "config1"])
+    p.add_argument("--workload", default="config2", choices=["config2", "config1", "marmousi"],
+                   help="config2: the 64-shot 400 x 1200 batch (the benchmark); config1: the small parity case; "
+                        "marmousi: the 30-shot 221 x 601 case of the paper's Marmousi test's shape")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -78,7 +80,8 @@ def make_case(name, shots=0, nt=0):
     import numpy as np
     import synth
 
-    case = synth.config2_case() if name == "config2" else synth.config1_case()
+    case = {"config2": synth.config2_case, "config1": synth.config1_case,
+            "marmousi": synth.marmousi_shaped_case}[name]()
     if shots > 0 and shots < case.geom.n_shots:
         case.geom = case.geom.subset(list(range(shots)))
     if nt > 0:

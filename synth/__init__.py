@@ -341,6 +341,24 @@ def config5_case(n_shots: int = 200, nt: int = 6000) -> Case:
     return Case(nz, nx, h, dt, nb, v, v0, geom, name="config5-600x2000-200shots")
 
 
+def marmousi_shaped_case(nt: int = 2400) -> Case:
+    """A workload with the shape of the paper's Marmousi test (Section 3.1):
+    221 x 601 nodes at 15 m (3.3 km x 9 km), 30 sources and 300 receivers
+    (every second node) on the surface, a 5 Hz Ricker wavelet.  The Marmousi
+    model itself is not available: a seeded layered model with two normal
+    faults over Marmousi's velocity range (1500-4700 m/s) stands in for it.
+    dt = 1.5 ms keeps the Courant number at 0.47 (the 8th-order limit in 2D
+    is 0.555)."""
+    nz, nx, h, dt, nb = 221, 601, 15.0, 1.5e-3, 20
+    v = layered_fault_model(nz, nx, h, seed=41, vmin=1500.0, vmax=4700.0)
+    v0 = smooth_model(v, 10.0)
+    wav = ricker(5.0, dt, nt)
+    src = np.round(np.linspace(10, nx - 11, 30)).astype(int)
+    rec = np.arange(0, 600, 2)
+    geom = uniform_geometry(src, rec, nt, wav, nx)
+    return Case(nz, nx, h, dt, nb, v, v0, geom, name="marmousi-shaped-221x601-30shots")
+
+
 def gaussian_field(shape, seed: int) -> np.ndarray:
     """Seeded standard-normal array (used for dot-product tests)."""
     return rng(seed).standard_normal(shape)
