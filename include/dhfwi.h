@@ -190,6 +190,14 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
 int fwi_update(dhfwi_ctx *ctx, const float *v_dev, const float *dir_dev, float alpha, float vmin, float vmax,
                int mute_rows, float *v_out_dev, void *stream);
 
+/* Quality-control filter of a migrated image (Section 3.3 images the data
+ * with the estimated models to validate them; the paper names no filter, so
+ * this is the reading adopted): out = -(D2 img) / h^2 with D2 the 5-point
+ * Laplacian, the image's edge values repeated outside the grid.  It damps
+ * the low-wavenumber part of a migration image.  img_dev, out_dev
+ * [nz][nx] float32 device (out must not alias img).  Asynchronous. */
+int image_laplacian(dhfwi_ctx *ctx, const float *img_dev, float *out_dev, void *stream);
+
 /* Data misfit J = 1/2 sum (a - b)^2 (Section 2.1 Eq. 2) of two device
  * vectors of n float32 values, accumulated in float64.  Synchronises. */
 int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long long n, double *misfit_out,

@@ -1259,6 +1259,16 @@ int fwi_update(dhfwi_ctx *ctx, const float *v_dev, const float *dir_dev, float a
     return end_call(ctx);
 }
 
+int image_laplacian(dhfwi_ctx *ctx, const float *img_dev, float *out_dev, void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!img_dev || !out_dev) return fail(ctx, DHFWI_ERR_ARG, "NULL image pointer");
+    if (img_dev == out_dev) return fail(ctx, DHFWI_ERR_ARG, "out must not alias img");
+    launch_image_laplacian(img_dev, ctx->g.nz, ctx->g.nx, ctx->g.h, out_dev, (cudaStream_t)stream);
+    ctx->stats.kernel_launches++;
+    return end_call(ctx);
+}
+
 int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long long n, double *misfit_out,
                 void *stream) {
     int rc = begin_call(ctx);

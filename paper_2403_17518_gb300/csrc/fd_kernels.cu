@@ -547,6 +547,27 @@ void launch_update_model(const float *v, const float *dir, int nz, int nx, int m
 }
 
 // ---------------------------------------------------------------------------
+// Image QC filter: out = -(5-point Laplacian of img) / h^2, the grid's edge
+// values repeated outside it (zero normal derivative).
+// ---------------------------------------------------------------------------
+__global__ void image_laplacian_kernel(const float *__restrict__ img, int nz, int nx, float inv_h2,
+                                       float *__restrict__ out) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iz = blockIdx.y;
+    if (ix >= nx || iz >= nz) return;
+    const long long c = (long long)iz * nx + ix;
+    const float v = img[c];
+    const float up = img[c - (iz > 0 ? nx : 0)], dn = img[c + (iz < nz - 1 ? nx : 0)];
+    const float lf = img[c - (ix > 0 ? 1 : 0)], rt = img[c + (ix < nx - 1 ? 1 : 0)];
+    out[c] = -(((up - v) + (dn - v)) + ((lf - v) + (rt - v))) * inv_h2;
+}
+
+void launch_image_laplacian(const float *img, int nz, int nx, float h, float *out, cudaStream_t s) {
+    dim3 grid((nx + 255) / 256, nz);
+    image_laplacian_kernel<<<grid, 256, 0, s>>>(img, nz, nx, 1.0f / (h * h), out);
+}
+
+// ---------------------------------------------------------------------------
 // Image reduction: shots in original order, sponge folded onto edge cells.
 // ---------------------------------------------------------------------------
 __global__ void reduce_image_kernel(const ShotDesc *__restrict__ shots, const int *__restrict__ slot_of,

@@ -159,6 +159,19 @@ class Context:
         """delta m_1 = L~^T L~ g (Section 2.3.1, Eq. 15)."""
         return self.rtm_mig(v0, geom, self.born_demig(v0, geom, g_img))
 
+    def image_laplacian(self, img: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """-(5-point Laplacian) / h^2 of an image, edge values repeated: the
+        quality-control filter of migrated images."""
+        out = out if out is not None else self.new_model()
+        self._check(self.lib.image_laplacian(self.handle, self._model(img, "img"), self._model(out, "out"),
+                                             self._stream(stream)))
+        return out
+
+    def rtm_qc(self, v: torch.Tensor, geom, d: torch.Tensor, stream=None) -> torch.Tensor:
+        """Migration of data d through the model v, then the Laplacian filter
+        (imaging with an estimated model to validate it, Section 3.3)."""
+        return self.image_laplacian(self.rtm_mig(v, geom, d, stream=stream), stream=stream)
+
     def fwi_update(self, v: torch.Tensor, direction: torch.Tensor, alpha: float, vmin: float, vmax: float,
                    mute_rows: int = 0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """clamp(v - alpha * dir / max|dir|, vmin, vmax) with the top rows muted."""

@@ -230,3 +230,22 @@ def test_fwi_update_and_data_misfit():
     a, b = f32(g.standard_normal(1000)), f32(g.standard_normal(1000))
     J = ctx.data_misfit(to_dev(a), to_dev(b))
     assert J == pytest.approx(oracle.misfit(a, b), rel=1e-6)
+
+
+def test_image_laplacian_and_rtm_qc():
+    """The image QC filter against its definition (float64, edge values
+    repeated), and rtm_qc = filter(rtm_mig) bit for bit."""
+    c = CASES["ragged"]
+    ctx = gpu_ctx(c)
+    g = np.random.Generator(np.random.PCG64(5))
+    img = f32(g.standard_normal((c.nz, c.nx)))
+    out = to_host(ctx.image_laplacian(to_dev(img)))
+    x = img.astype(np.float64)
+    p = np.pad(x, 1, mode="edge")
+    ref = -((p[:-2, 1:-1] - x) + (p[2:, 1:-1] - x) + (p[1:-1, :-2] - x) + (p[1:-1, 2:] - x)) / c.h ** 2
+    assert np.abs(out - ref).max() <= 1e-6 * np.abs(ref).max()
+    geom = f32_geom(c.geom)
+    v0 = to_dev(f32(c.v_init))
+    d = to_dev(f32(oracle.model_shots(f32(c.v_true), geom, c.h, c.dt, c.nb)))
+    qc = to_host(ctx.rtm_qc(v0, geom, d))
+    np.testing.assert_array_equal(qc, to_host(ctx.image_laplacian(ctx.rtm_mig(v0, geom, d))))
