@@ -48,7 +48,8 @@ def ricker(f0: float, dt: float, nt: int, t0: float | None = None) -> np.ndarray
 
     The paper names only the peak frequency of its Ricker sources (5 Hz for
     Marmousi, Section 3.1; 20 Hz for the Volve synthetic, Section 3.2).  The
-    delay t0 = 1.5/f0 is a reading (the paper gives only the peak frequency); the amplitude is 1 at t0.
+    delay t0 = 1.5/f0 is a reading (the paper gives none); the amplitude is 1
+    at t0.
     Returned in float64.
     """
     if t0 is None:
