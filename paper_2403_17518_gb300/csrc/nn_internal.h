@@ -51,6 +51,7 @@ struct WgradArgs {
     int nw;                     // weight columns (9*ci for WG_CONV, ci for WG_CONVT)
     const __nv_bfloat16 *ones;  // 8 bf16 values {1, 0, ..., 0}
     float *part;                // [splits][M][N]
+    unsigned *err;              // nullable: set to 1 by a tensor-core GEMM whose bounded wait ran out
 };
 
 // mma.sync GEMM (igemm_fprop_kernel), or the tcgen05 one (nn_umma.cu) when
@@ -60,11 +61,16 @@ void launch_fprop_umma(const FpropArgs &a, int epi, cudaStream_t s);
 // TMA-fed tcgen05 kernel for the 3x3 convolutions with >= 64 output channels
 // (nn_umma.cu); false when the GEMM is not of that form (nothing launched).
 bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s);
+// tcgen05 weight gradient of a 3x3 convolution (nn_umma.cu; off with
+// DHFWI_NN_WGRAD=mma or DHFWI_NN_GEMM=mma): the splits it wrote, 0 when not
+// applicable.
+int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s);
 // Sum of split-k partials a.part[splits][M][N] with the epilogue epi.
 void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s);
 int wgrad_splits(long long kpix, int M, int N);
 // Weight gradient into dw (parameter layout) and bias gradient into db.
-void launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s);
+// Returns the number of kernels launched.
+int launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s);
 void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, float *part, int max_blocks, float *db,
                       cudaStream_t s);
 void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H, int W, int C, __nv_bfloat16 *y,

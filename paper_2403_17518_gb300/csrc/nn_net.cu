@@ -517,10 +517,10 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
     w.N = w.nw + 8;
     w.ones = N.ones;
     w.part = N.wg_part;
+    w.err = N.err;
     const int sp = wgrad_splits(P, w.M, w.N);
     float *dw = li == 0 ? N.g0pad : N.grad + d.off;
-    launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, s);
-    N.launches += 2;
+    N.launches += launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, s);
     if (li == 0) {
         launch_unpad_first_grad(N.g0pad, d.co, CPAD, N.grad + d.off, s);
         N.launches++;

@@ -23,6 +23,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "nn_internal.h"
 
@@ -56,6 +58,14 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned saddr, unsigned lbo, unsi
 __device__ __forceinline__ uint64_t smem_desc_sw128(unsigned saddr) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// MN-major operand in the 128-byte swizzle: rows of 128 B hold 64 elements
+// along M / N, 8-row groups along K are 1024 B apart (stride-byte offset),
+// 64-element blocks along M / N `block` bytes apart (leading-byte offset),
+// layout type 2.  A K = 16 step starts 2048 B further.
+__device__ __forceinline__ uint64_t smem_desc_sw128_mn(unsigned saddr, unsigned block) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((block >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
 // BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -704,6 +714,211 @@ void umma_dispatch(const FpropArgs &a, cudaStream_t s) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Weight gradient of a 3x3 convolution on tcgen05 (input channels ci and
+// output channels co multiples of 64):
+//   part[z][co][tap * ci + c] = sum over the pixels of split z of
+//                               G[p][co] X[p + shift(tap)][c].
+// The MMA's M = 128 rows are two (tap, 64-channel block) pairs of the input
+// X, N = NB output channels of the output gradient G, K = pixels in blocks
+// of 128 (the conv kernel's tile geometry).  Both operands arrive as 4-D TMA
+// boxes (64 channels, BW, BH, BI) of the NHWC tensors (X shifted by the
+// pair's tap, zero outside the grid), i.e. MN-major in the 128-byte
+// swizzle: 64-channel blocks 16 KB apart (leading-byte offset 16384),
+// 8-pixel groups 1024 B apart (stride-byte offset 1024), a K = 16 step
+// 2048 B further.  Same warp roles, mbarrier hand-off and bounded waits as
+// conv3_tma_umma_kernel.  The epilogue writes lane r's row (one input
+// channel of one tap) for 16 output channels at a time, so a warp stores 32
+// consecutive columns of part.  The bias column is left to the caller.
+// ---------------------------------------------------------------------------
+struct WgradTile {
+    int BW, BH, BI, tw, th;
+    int npb;        // pixel blocks in total
+    int per;        // pixel blocks per split
+    int pairs;      // (tap, 64-channel block) pairs: 9 * ci / 64
+    int nimg;
+};
+
+template <int NB, int ST>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    wgrad_tma_umma_kernel(WgradArgs P, const __grid_constant__ CUtensorMap mapX,
+                          const __grid_constant__ CUtensorMap mapG, WgradTile G) {
+    constexpr unsigned BOX = 16384;  // 64 channels x 128 pixels of bf16
+    constexpr unsigned A_BYTES = 2 * BOX, B_BYTES = (NB / 64) * BOX, STAGE = A_BYTES + B_BYTES;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    const unsigned sbase = (smem_u32(smraw) + 1023u) & ~1023u;
+    unsigned char *tail = smraw + (sbase - smem_u32(smraw)) + ST * STAGE;
+    const unsigned full0 = smem_u32(tail), empty0 = full0 + 8 * ST, accf = empty0 + 8 * ST;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(tail + 16 * ST + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q0 = 2 * blockIdx.x;  // first (tap, channel block) pair of this M tile
+    const bool two = q0 + 1 < G.pairs;
+    const int cbn = P.ci / 64;
+    const int co0 = blockIdx.y * NB;
+    const int pb0 = blockIdx.z * G.per;
+    const int nk = max(0, min(G.npb, pb0 + G.per) - pb0);
+    const unsigned stage_tx = (two ? 2 : 1) * BOX + B_BYTES;
+
+    if (tid == 0) {
+        for (int s = 0; s < ST; s++) {
+            mbar_init1(full0 + 8 * s);
+            mbar_init1(empty0 + 8 * s);
+        }
+        mbar_init1(accf);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((unsigned)NB));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int tapv[2], cbv[2];
+            for (int h = 0; h < 2; h++) {
+                const int q = q0 + h < G.pairs ? q0 + h : q0;
+                tapv[h] = q / cbn;
+                cbv[h] = q - tapv[h] * cbn;
+            }
+            int issued = 0;
+            for (int kt = 0; kt < nk; kt++) {
+                const int s = kt % ST;
+                if (kt >= ST && !mbar_wait(empty0 + 8 * s, ((kt / ST) - 1) & 1u)) {
+                    if (P.err) atomicExch(P.err, 1u);
+                    break;
+                }
+                const unsigned fb = full0 + 8 * s;
+                mbar_expect_tx(fb, stage_tx);
+                int b = pb0 + kt;
+                const int w0 = (b % G.tw) * G.BW;
+                b /= G.tw;
+                const int h0 = (b % G.th) * G.BH;
+                const int i0 = (b / G.th) * G.BI;
+                const unsigned sa = sbase + s * STAGE, sb = sa + A_BYTES;
+                for (int h = 0; h < (two ? 2 : 1); h++) {
+                    const int t = tapv[h];
+                    tma_load_4d(sa + h * BOX, &mapX, cbv[h] * 64, w0 + (t % 3) - 1, h0 + (t / 3) - 1, i0, fb);
+                }
+#pragma unroll
+                for (int j = 0; j < NB / 64; j++) tma_load_4d(sb + j * BOX, &mapG, co0 + 64 * j, w0, h0, i0, fb);
+                issued = kt + 1;
+            }
+            for (int kt = max(0, issued - ST); kt < issued; kt++) mbar_wait(full0 + 8 * (kt % ST), (kt / ST) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // M = 128, N = NB, both operands MN-major (bits 15, 16).
+            constexpr uint32_t IDESC = idesc_bf16(UBM, NB) | (1u << 15) | (1u << 16);
+            for (int kt = 0; kt < nk; kt++) {
+                const int s = kt % ST;
+                if (!mbar_wait(full0 + 8 * s, (kt / ST) & 1u)) {
+                    if (P.err) atomicExch(P.err, 1u);
+                    break;
+                }
+                tc_fence_after();
+                const unsigned sa = sbase + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < 8; kk++)
+                    mma_bf16(tmem, smem_desc_sw128_mn(sa + 2048 * kk, BOX), smem_desc_sw128_mn(sb + 2048 * kk, BOX),
+                             IDESC, (kt > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(accf);
+        }
+        __syncwarp();
+    } else {
+        const int qw = warp & 3;
+        const bool good = mbar_wait(accf, 0);
+        tc_fence_after();
+        if (!good) {
+            if (lane == 0 && P.err) atomicExch(P.err, 1u);
+        } else {
+            const int r = qw * 32 + lane;
+            const int q = q0 + (r >> 6);
+            const bool valid = q < G.pairs && (r < 64 || two);
+            const int tap = q / cbn, cb = q - tap * cbn;
+            const int n = tap * P.ci + cb * 64 + (r & 63);
+            float *out = P.part + (long long)blockIdx.z * P.M * P.N + n;
+            const unsigned trow = tmem + ((unsigned)(qw * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < NB; c0 += 16) {
+                float v[16];
+                if (nk > 0) tmem_ld16(trow + c0, v);
+                else
+#pragma unroll
+                    for (int e = 0; e < 16; e++) v[e] = 0.f;
+                if (!valid) continue;
+#pragma unroll
+                for (int e = 0; e < 16; e++) out[(long long)(co0 + c0 + e) * P.N] = v[e];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)NB));
+    }
+}
+
+template <int NB>
+int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
+    constexpr int ST = NB == 64 ? 4 : NB == 128 ? 3 : 2;
+    const size_t sm = (size_t)ST * (2 * 16384 + (NB / 64) * 16384) + 2048;
+    EncodeTiledFn enc = tma_encoder();
+    if (!enc) return 0;
+    WgradTile G{};
+    G.nimg = a.nimg;
+    G.BW = a.W > 8 ? 16 : 8;
+    G.BI = (G.BW == 8 && a.H <= 8) ? 2 : 1;
+    G.BH = 128 / (G.BW * G.BI);
+    G.tw = (a.W + G.BW - 1) / G.BW;
+    G.th = (a.H + G.BH - 1) / G.BH;
+    G.npb = G.tw * G.th * ((a.nimg + G.BI - 1) / G.BI);
+    G.pairs = 9 * (a.ci / 64);
+    const int mt = (G.pairs + 1) / 2, ntl = a.M / NB;
+    const int tiles = mt * ntl;
+    int splits = (152 + tiles - 1) / tiles;
+    splits = std::min(splits, std::max(1, G.npb / 4));
+    splits = std::max(1, std::min(splits, max_splits));
+    G.per = (G.npb + splits - 1) / splits;
+    splits = (G.npb + G.per - 1) / G.per;
+    CUtensorMap mx, mg;
+    const cuuint64_t es = sizeof(__nv_bfloat16);
+    cuuint32_t box[4] = {64, (cuuint32_t)G.BW, (cuuint32_t)G.BH, (cuuint32_t)G.BI}, estr[4] = {1, 1, 1, 1};
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)a.ci, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.nimg};
+        cuuint64_t str[3] = {es * a.x_stride, es * a.x_stride * a.W, es * a.x_stride * a.W * a.H};
+        if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(a.x + a.x_off), dims, str, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return 0;
+    }
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)a.M, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.nimg};
+        cuuint64_t str[3] = {es * a.g_stride, es * a.g_stride * a.W, es * a.g_stride * a.W * a.H};
+        if (enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)a.g, dims, str, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return 0;
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(wgrad_tma_umma_kernel<NB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    // The bias column and the 7 zero columns are not written by the kernel.
+    cudaMemsetAsync(a.part, 0, sizeof(float) * (size_t)splits * a.M * a.N, s);
+    wgrad_tma_umma_kernel<NB, ST><<<dim3(mt, ntl, splits), TMA_THREADS, sm, s>>>(a, mx, mg, G);
+    return splits;
+}
+
 // The TMA-fed kernel serves a GEMM when it is a 3x3 convolution (taps with
 // shifts in {-1, 0, 1}, stride 1, same grid in and out) with C a multiple of
 // 32, at least 64 output channels, 16-byte aligned operands and a row
@@ -734,6 +949,24 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
     case EPI_F32_ADD: return conv3_tma_dispatch<EPI_F32_ADD>(a, G, s);
     default: return false;
     }
+}
+
+// The tcgen05 weight gradient (the default; DHFWI_NN_WGRAD=mma or
+// DHFWI_NN_GEMM=mma keep the mma.sync one) for WG_CONV with ci and co
+// multiples of 64 and aligned operands.  Partials as igemm_wgrad_kernel's,
+// bias column zero.  Returns the number of splits written (0: not
+// applicable, nothing launched).
+int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s) {
+    const char *e = getenv("DHFWI_NN_WGRAD"), *g = getenv("DHFWI_NN_GEMM");
+    if ((e && strcmp(e, "mma") == 0) || (g && strcmp(g, "mma") == 0)) return 0;
+    if (a.mode != WG_CONV || a.ci % 64 != 0 || a.M % 64 != 0 || a.ci <= 0 || a.M <= 0) return 0;
+    if (a.nw != 9 * a.ci || a.N != a.nw + 8) return 0;
+    if (((a.x_stride | a.x_off | a.g_stride) & 7) != 0) return 0;
+    if ((((uintptr_t)(a.x + a.x_off)) | (uintptr_t)a.g) & 15) return 0;
+    if ((long long)a.nimg * a.H * a.W >= (1LL << 31)) return 0;
+    if (a.M % 256 == 0) return wgrad_tma_launch<256>(a, max_splits, s);
+    if (a.M % 128 == 0) return wgrad_tma_launch<128>(a, max_splits, s);
+    return wgrad_tma_launch<64>(a, max_splits, s);
 }
 
 void launch_fprop_umma(const FpropArgs &a, int epi, cudaStream_t s) {

@@ -54,13 +54,16 @@ GEMMS = ["mma", "halo", "tc", "default"]
 
 def _set_gemm(monkeypatch, gemm):
     """mma: mma.sync gathering kernels only; halo: mma.sync with halo tiles;
-    tc: the cp.async-fed tcgen05 kernel for every forward-form GEMM; default:
-    the TMA-fed tcgen05 kernel for the 3x3 convolutions with >= 64 output
-    channels, halo tiles for the rest."""
+    tc: the cp.async-fed tcgen05 kernel for every forward-form GEMM (with the
+    mma.sync weight gradient); default: the TMA-fed tcgen05 kernels for the
+    3x3 convolutions with >= 64 channels (forward, input gradient and weight
+    gradient), mma.sync halo tiles for the rest."""
     if gemm == "default":
         monkeypatch.delenv("DHFWI_NN_GEMM", raising=False)
+        monkeypatch.delenv("DHFWI_NN_WGRAD", raising=False)
     else:
         monkeypatch.setenv("DHFWI_NN_GEMM", "tc" if gemm == "tc" else "mma")
+        monkeypatch.setenv("DHFWI_NN_WGRAD", "mma")
     monkeypatch.setenv("DHFWI_NN_HALO", "0" if gemm == "mma" else "1")
 
 
