@@ -198,6 +198,14 @@ int fwi_update(dhfwi_ctx *ctx, const float *v_dev, const float *dir_dev, float a
  * [nz][nx] float32 device (out must not alias img).  Asynchronous. */
 int image_laplacian(dhfwi_ctx *ctx, const float *img_dev, float *out_dev, void *stream);
 
+/* Self-test of the failure path (no counterpart in the paper): launches one
+ * kernel whose bounded device-side wait (~1 s, the step kernels' limit) runs
+ * out on a barrier that nothing arrives at; it records that as a timed-out
+ * step kernel does, so the next call on this context returns
+ * DHFWI_ERR_TIMEOUT and clears the record, and later calls work normally.
+ * Nothing faults or hangs.  Asynchronous. */
+int dhfwi_selftest_timeout(dhfwi_ctx *ctx, void *stream);
+
 /* Data misfit J = 1/2 sum (a - b)^2 (Section 2.1 Eq. 2) of two device
  * vectors of n float32 values, accumulated in float64.  Synchronises. */
 int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long long n, double *misfit_out,

@@ -78,6 +78,7 @@ SIGNATURES = [
                                   _VP, _VP]),
     ("data_misfit", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _VP]),
     ("image_laplacian", ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    ("dhfwi_selftest_timeout", ctypes.c_int, [_VP, _VP]),
     ("model_shots_static", ctypes.c_int, [ctypes.POINTER(Grid), _VP, ctypes.POINTER(Geom), _VP, _VP]),
     ("model_shots_static_error", ctypes.c_char_p, []),
     ("dhfwi_net_init", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong]),

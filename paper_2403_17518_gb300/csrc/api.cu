@@ -1259,6 +1259,14 @@ int fwi_update(dhfwi_ctx *ctx, const float *v_dev, const float *dir_dev, float a
     return end_call(ctx);
 }
 
+int dhfwi_selftest_timeout(dhfwi_ctx *ctx, void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    launch_wait_timeout_selftest((unsigned *)ctx->status.p + TFLAG_WORD, (cudaStream_t)stream);
+    ctx->stats.kernel_launches++;
+    return end_call(ctx);
+}
+
 int image_laplacian(dhfwi_ctx *ctx, const float *img_dev, float *out_dev, void *stream) {
     int rc = begin_call(ctx);
     if (rc) return rc;

@@ -214,6 +214,10 @@ void launch_residual(const float *ds, const float *dobs, float *r, long long n, 
 void launch_update_model(const float *v, const float *dir, int nz, int nx, int mute_rows, float alpha, float vmin,
                          float vmax, unsigned *mxbits, float *vout, cudaStream_t s);
 
+// One kernel whose bounded wait runs out (on a barrier nothing arrives at)
+// and sets *tflag, as a step kernel's timed-out wait does.
+void launch_wait_timeout_selftest(unsigned *tflag, cudaStream_t s);
+
 // out = -(5-point Laplacian of img) / h^2 on [nz][nx], edge values repeated
 // outside the grid; out must not alias img.
 void launch_image_laplacian(const float *img, int nz, int nx, float h, float *out, cudaStream_t s);

@@ -314,6 +314,23 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1)
 }
 
 // ---------------------------------------------------------------------------
+// Self-test of the failure path: one warp waits, with the step kernels'
+// bounded wait (~1 s), on an mbarrier that nothing arrives at, and reports
+// the timeout in tflag as they do.  Nothing faults and nothing hangs.
+// ---------------------------------------------------------------------------
+__global__ void wait_timeout_selftest_kernel(unsigned *tflag) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool landed = mbar_wait(b, 0);
+    if (!landed && threadIdx.x == 0) atomicExch(tflag, 1u);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers and occupancy per variant (R = 4, 8, 16 for variants 3, 4, 5).
 // ---------------------------------------------------------------------------
 // Launch as a programmatic dependent of the previous kernel in the stream.
@@ -383,6 +400,10 @@ void launch_born_step_tma(const BornArgs &a, int ntiles, int variant, int grid, 
     case FIRST_TMA_VARIANT: launch_pdl(born_tma_kernel<4>, grid, 4, kBornSmem, s, a, maps, ntiles); break;
     default: launch_pdl(born_tma_kernel<8>, grid, 8, kBornSmem, s, a, maps, ntiles); break;
     }
+}
+
+void launch_wait_timeout_selftest(unsigned *tflag, cudaStream_t s) {
+    wait_timeout_selftest_kernel<<<1, 32, 0, s>>>(tflag);
 }
 
 int tma_occupancy(int kind, int variant) {

@@ -159,6 +159,11 @@ class Context:
         """delta m_1 = L~^T L~ g (Section 2.3.1, Eq. 15)."""
         return self.rtm_mig(v0, geom, self.born_demig(v0, geom, g_img))
 
+    def selftest_timeout(self, stream=None):
+        """Make one bounded device-side wait run out: the next call raises
+        DhfwiError with DHFWI_ERR_TIMEOUT, later calls work normally."""
+        self._check(self.lib.dhfwi_selftest_timeout(self.handle, self._stream(stream)))
+
     def image_laplacian(self, img: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """-(5-point Laplacian) / h^2 of an image, edge values repeated: the
         quality-control filter of migrated images."""

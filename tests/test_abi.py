@@ -50,6 +50,7 @@ def test_null_context_is_rejected():
     L = _lib.load()
     assert L.model_shots(None, None, None, None, None) == -1
     assert L.image_laplacian(None, None, None, None) == -1
+    assert L.dhfwi_selftest_timeout(None, None) == -1
     L.dhfwi_destroy(None)  # accepted
 
 

@@ -182,6 +182,23 @@ def test_errors_are_reported():
     assert np.isfinite(to_host(d)).all()
 
 
+def test_bounded_wait_timeout_is_reported_and_context_survives():
+    """A device-side wait that runs out (a barrier nothing arrives at, the
+    step kernels' ~1 s limit) is reported by the next call as
+    DHFWI_ERR_TIMEOUT; the call after that computes the records correctly."""
+    c = CASES["tiny"]
+    ctx = gpu_ctx(c)
+    from paper_2403_17518_gb300.ops import DhfwiError
+
+    v, geom = f32(c.v_true), f32_geom(c.geom)
+    ctx.selftest_timeout()
+    with pytest.raises(DhfwiError) as e:
+        ctx.model_shots(to_dev(v), geom)
+    assert e.value.code == -6 and "TIMEOUT" in str(e.value)
+    d = to_host(ctx.model_shots(to_dev(v), geom))
+    assert rel_l2(d, oracle.model_shots(v, geom, c.h, c.dt, c.nb)) <= TOL
+
+
 # ---------------------------------------------------------------------------
 # Full-size workload (400 x 1200, 64 shots, nt 3000-4000): the batched launch
 # the benchmark times, checked on shots the oracle computes one by one.
