@@ -103,9 +103,10 @@ typedef struct {
     double workspace_bytes;   /* device workspace held by the context */
     /* Device time of the phases of the last call, from CUDA events recorded on
      * the call's stream around each phase (0 unless timing is on, see
-     * dhfwi_set_timing).  Phase 0: forward passes (forward step kernel only);
-     * 1: backward sweeps (segment recompute + adjoint step kernels); 2: Born
-     * joint passes. */
+     * dhfwi_set_timing).  Phase 0: forward passes (forward step kernel only,
+     * storing the a^n history where it covers the step); 1: backward sweeps
+     * (adjoint step kernels, plus the segment recompute for steps outside the
+     * history); 2: Born joint passes. */
     double phase_ms[3];
     long long phase_launches[3];
     long long phase_cells[3];  /* cell updates in that phase (Born counts 2 per cell) */
