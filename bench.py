@@ -43,8 +43,19 @@ if ROOT not in sys.path:
 
 METRIC = "FD Gcell-updates/s & HBM roofline %; model error vs GPU-s, deblurred vs plain"
 UNIT = "Gcell-updates/s"
-FWD_BYTES_PER_CELL = 16  # read u^n and D^n, write u^{n+1} and D^{n+1} (kappa: L2-resident shared model)
-HIST_BYTES_PER_CELL = 4  # and write a^n, where the forward pass stores the history
+# Algorithmic bytes per cell update (the three-level count: kappa and the
+# sponge come from a model shared by every shot, L2-resident, so they are not
+# counted).  A forward update reads u^n and u^{n-1} and writes u^{n+1}; the
+# forward pass of a gradient or migration also stores a^n; an adjoint update
+# moves the same 12 B plus the read of a^n; a Born cell-step advances two
+# fields (24 B) and reads the perturbation (4 B), counted as two updates.
+FWD_BYTES_PER_CELL = 12
+HIST_BYTES_PER_CELL = 4
+ADJ_BYTES_PER_CELL = 16
+BORN_BYTES_PER_CELL_STEP = 28
+# The bytes the summed form the kernels use must move (u and D = u - w u^{n-1}
+# both change every step): 16 B per forward update.  Reported as an extra.
+SUMMED_FWD_BYTES_PER_CELL = 16
 
 
 def parse():
@@ -59,15 +70,16 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--only", default="", choices=["", "fwd", "grad", "nn"],
+    p.add_argument("--only", default="", choices=["", "fwd", "grad", "born", "nn"],
                    help="fwd: time batched forward modelling (model_shots) alone; grad: the FWI gradient "
-                        "(fwi_gradient: forward storing the history, adjoint) alone; nn: the network's training "
-                        "and apply alone on seeded smooth images of the workload's size; used for profiling")
+                        "(fwi_gradient: forward storing the history, adjoint) alone; born: Born demigration "
+                        "(born_demig) alone; nn: the network's training and apply alone on seeded smooth images "
+                        "of the workload's size; used for profiling")
     p.add_argument("--nn-epochs", type=int, default=20)
     p.add_argument("--shots", type=int, default=0,
-                   help="with --only fwd/grad: the first SHOTS shots of the batch (small profiling captures)")
+                   help="with --only fwd/grad/born: the first SHOTS shots of the batch (small profiling captures)")
     p.add_argument("--nt", type=int, default=0,
-                   help="with --only fwd/grad: records truncated to NT samples (small profiling captures)")
+                   help="with --only fwd/grad/born: records truncated to NT samples (small profiling captures)")
     p.add_argument("--cold-epochs", type=int, default=COLD_EPOCHS,
                    help="epochs of the network's cold start before the timed region (setup only)")
     return p.parse_args()
@@ -229,12 +241,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # ncu traffic from the committed profile (null when the kernel has changed)
 # ---------------------------------------------------------------------------
-# Sources of each forward step kernel: its profile under profiles/ records
-# their hash, and its DRAM figures are used only while the hash matches.
+# Sources of each step kernel: its profile under profiles/ records their
+# hash, and its DRAM figures are used only while the hash matches.
 KERNEL_SOURCES = {
     "fwd_step_kernel": ["fd_kernels.cu", "fd_device.cuh"],
     "fwd_tma_kernel": ["fd_tma.cu", "fd_tma.cuh", "fd_device.cuh"],
     "fwd_pair_kernel": ["fd_tma2.cu", "fd_tma.cuh", "fd_device.cuh"],
+    "adj_pair_kernel": ["fd_tma2.cu", "fd_tma.cuh", "fd_device.cuh"],
+    "born_tma_kernel": ["fd_tma.cu", "fd_tma.cuh", "fd_device.cuh"],
 }
 
 
@@ -251,10 +265,11 @@ def forward_kernel(variant: int) -> str:
 
 
 def profiled_traffic(kernel: str, cells_per_launch: float):
-    """DRAM bytes per launch of the forward step kernel from profiles/, scaled
-    to this launch size, or None if absent or taken on another kernel source."""
+    """DRAM bytes per launch of a step kernel from profiles/, scaled to this
+    launch size by its cell updates, or None if absent or taken on another
+    kernel source."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_config2.md")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
     txt = open(path).read()
     m_hash = re.search(r"kernel source sha256\[:16\]:\s*`?([0-9a-f]{16})", txt)
@@ -443,6 +458,37 @@ def run_gradient_only(args, dist, ctx, case, geom, v0, d_obs):
                           "gcell_per_s": round(2 * U / ms / 1e6, 3)}), flush=True)
 
 
+def run_born_only(args, dist, ctx, case, geom, v0, d_obs):
+    """Born demigration alone (born_demig), for kernel profiling."""
+    import torch
+
+    import synth
+
+    dv = torch.tensor(synth.smooth_random_field(case.nz, case.nx, 5) * 100.0, dtype=torch.float32,
+                      device=v0.device)
+    d = ctx.new_data(geom)
+    ctx.set_timing(True)
+    for _ in range(args.warmup):
+        ctx.born_demig(v0, geom, dv, out=d)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.born_demig(v0, geom, dv, out=d)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    st = ctx.stats()
+    U = case.geom.cell_updates(case.nz, case.nb)
+    if dist.rank == 0:
+        print(json.dumps({"only": "born", "workload": case.name, "ms_per_call": round(ms, 3),
+                          "born_ms": round(st["phase_ms"][2], 3), "step_variants": st["step_variant"],
+                          "launches_per_call": st["kernel_launches"], "gcell_per_s": round(2 * U / ms / 1e6, 3),
+                          "GBps_at_28B_per_cell_step": round(BORN_BYTES_PER_CELL_STEP * U / ms / 1e6, 1)}),
+              flush=True)
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -458,7 +504,7 @@ def main():
 
     torch.cuda.set_device(dist.local)
     build()
-    prof = args.only in ("fwd", "grad")
+    prof = args.only in ("fwd", "grad", "born")
     case = make_case(args.workload, args.shots if prof else 0, args.nt if prof else 0)
     if args.only == "nn":
         run_network_only(args, dist, case)
@@ -471,8 +517,9 @@ def main():
     v0 = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
     d_obs = ctx.model_shots(v_true, geom)
     setup_launches = ctx.stats()["kernel_launches"]
-    if args.only in ("fwd", "grad"):
-        (run_forward_only if args.only == "fwd" else run_gradient_only)(args, dist, ctx, case, geom, v0, d_obs)
+    if args.only in ("fwd", "grad", "born"):
+        {"fwd": run_forward_only, "grad": run_gradient_only, "born": run_born_only}[args.only](
+            args, dist, ctx, case, geom, v0, d_obs)
         ctx.close()
         dist.close()
         return
@@ -493,9 +540,11 @@ def main():
     ctx.deblur_train(dm1, grad, warm_start=False, epochs=args.cold_epochs, **NET)
     setup_launches += ctx.stats()["kernel_launches"]
     nn_ev = []
-    phase = {"ms": 0.0, "launches": 0, "cells": 0, "steps": 0, "hist_cells": 0, "hist_steps": 0}
+    # Library phases (CUDA events on the call's stream): 0 forward passes,
+    # 1 backward sweeps, 2 Born joint passes.
+    ph = [{"ms": 0.0, "launches": 0, "cells": 0} for _ in range(3)]
+    hist = {"cells": 0, "steps": 0, "fwd_steps": 0}
     nt_max = int(max(case.geom.nt))
-    breakdown = {"forward_ms": 0.0, "backward_ms": 0.0, "born_ms": 0.0}
     launches = [0]
 
     def step(collect=False):
@@ -520,15 +569,13 @@ def main():
         for st in stats:
             launches[0] += st["kernel_launches"]
             if collect:
-                phase["ms"] += st["phase_ms"][0]
-                phase["launches"] += st["phase_launches"][0]
-                phase["cells"] += st["phase_cells"][0]
-                phase["hist_cells"] += st["history_cells"]
-                phase["hist_steps"] = max(phase["hist_steps"], st["history_steps"])
-                phase["steps"] += nt_max if st["phase_launches"][0] > 0 else 0
-                breakdown["forward_ms"] += st["phase_ms"][0]
-                breakdown["backward_ms"] += st["phase_ms"][1]
-                breakdown["born_ms"] += st["phase_ms"][2]
+                for k in range(3):
+                    ph[k]["ms"] += st["phase_ms"][k]
+                    ph[k]["launches"] += st["phase_launches"][k]
+                    ph[k]["cells"] += st["phase_cells"][k]
+                hist["cells"] += st["history_cells"]
+                hist["steps"] = max(hist["steps"], st["history_steps"])
+                hist["fwd_steps"] += nt_max if st["phase_launches"][0] > 0 else 0
         return J
 
     for _ in range(args.warmup):
@@ -555,16 +602,44 @@ def main():
     cells_step = algorithmic_cells(case)
     value = dist.world * cells_step * args.steps / (ms_max / 1e3) / 1e9
 
-    # Roofline of the forward step kernel (pure forward passes of the step).
+    # Rooflines of the stencil kernels: each library phase's algorithmic
+    # bytes over its CUDA-event time inside the timed region.
     peak, peak_kind = peaks()
-    fwd_ms_per_launch = phase["ms"] / max(phase["launches"], 1)
-    cells_per_launch = phase["cells"] / max(phase["launches"], 1)
-    fwd_bytes = FWD_BYTES_PER_CELL * phase["cells"] + HIST_BYTES_PER_CELL * phase["hist_cells"]
-    achieved = fwd_bytes / (phase["ms"] / 1e3) / 1e9 if phase["ms"] > 0 else None
-    # Two time steps per launch when the forward passes ran time-blocked.
-    steps_per_launch = phase["steps"] / max(phase["launches"], 1)
-    fwd_kernel = "fwd_pair_kernel" if steps_per_launch > 1.5 else forward_kernel(ctx.stats()["step_variant"][0])
-    traffic = profiled_traffic(fwd_kernel, cells_per_launch)
+    variants = ctx.stats()["step_variant"]
+    fwd_pair = hist["fwd_steps"] / max(ph[0]["launches"], 1) > 1.5  # two time steps per launch
+    kernels = [
+        ("fwd_pair_kernel" if fwd_pair else forward_kernel(variants[0]),
+         "forward passes of fwi_gradient and rtm_mig, storing the a^n history",
+         FWD_BYTES_PER_CELL * ph[0]["cells"] + HIST_BYTES_PER_CELL * hist["cells"],
+         f"{FWD_BYTES_PER_CELL} B per update (read u^n, u^(n-1), write u^(n+1)) + {HIST_BYTES_PER_CELL} B per "
+         f"update that stores a^n"),
+        ("adj_pair_kernel" if fwd_pair else ("adj_tma_kernel" if variants[2] >= 3 else "adj_step_kernel"),
+         "backward sweeps of fwi_gradient and rtm_mig (adjoint steps with imaging, a^n read from the history)",
+         ADJ_BYTES_PER_CELL * ph[1]["cells"],
+         f"{ADJ_BYTES_PER_CELL} B per update (12 B for the adjoint field + 4 B to read a^n)"),
+        ("born_tma_kernel" if variants[3] >= 3 else "born_step_kernel",
+         "Born joint passes of born_demig (background and scattered fields)",
+         BORN_BYTES_PER_CELL_STEP * ph[2]["cells"] // 2,
+         f"{BORN_BYTES_PER_CELL_STEP} B per cell-step (two fields, 24 B, + 4 B for dv)"),
+    ]
+    rooflines = []
+    for k, (kern, what, alg, rule) in enumerate(kernels):
+        p_ms, nl, cells = ph[k]["ms"], max(ph[k]["launches"], 1), ph[k]["cells"]
+        ach = alg / (p_ms / 1e3) / 1e9 if p_ms > 0 else None
+        traffic = profiled_traffic(kern, cells / nl)
+        rooflines.append({
+            "kernel": f"{kern} ({what})", "bound": "hbm", "achieved": round(ach, 2) if ach else None, "peak": peak,
+            "unit": "GB/s", "frac": round(ach / peak, 4) if ach else None,
+            "traffic": round(traffic) if traffic else None,
+            "algorithmic_bytes_per_launch": round(alg / nl), "bytes_rule": rule,
+            "avg_launch_ms": round(p_ms / nl, 6), "launches_per_step": nl // max(args.steps, 1),
+            "ms_per_step": round(p_ms / max(args.steps, 1), 2),
+            "gcell_per_s": round(cells / (p_ms / 1e3) / 1e9, 2) if p_ms > 0 else None,
+            "peak_kind": f"{peak_kind} (hbm_gbs)"})
+    if ph[0]["ms"] > 0:
+        summed = SUMMED_FWD_BYTES_PER_CELL * ph[0]["cells"] + HIST_BYTES_PER_CELL * hist["cells"]
+        rooflines[0]["summed_form_GBps"] = round(summed / (ph[0]["ms"] / 1e3) / 1e9, 2)
+    dominant = max(range(3), key=lambda k: ph[k]["ms"])
 
     # End to end through the public API with host buffers.
     e2e = None
@@ -621,23 +696,19 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(case, args),
-            "roofline": {
-                "kernel": f"{fwd_kernel} (forward passes of fwi_gradient and rtm_mig)",
-                "bound": "hbm", "achieved": round(achieved, 2) if achieved else None, "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
-                "traffic": round(traffic) if traffic else None,
-                "algorithmic_bytes_per_launch": round(fwd_bytes / max(phase["launches"], 1)),
-                "avg_launch_ms": round(fwd_ms_per_launch, 6), "peak_kind": f"{peak_kind} (hbm_gbs)",
-            },
+            # The stencil kernel that takes the most time of the step.
+            "roofline": rooflines[dominant],
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches[0]),
             "launches_before_timed_region": int(launches_before),
             "step_variants": ctx.stats()["step_variant"],
-            "history_steps": {"stored": phase["hist_steps"], "of": nt_max,
+            "history_steps": {"stored": hist["steps"], "of": nt_max,
                               "workspace_gb": round(ctx.stats()["workspace_bytes"] / 1e9, 2)},
-            "phase_ms_per_step": dict({k: round(v / args.steps, 2) for k, v in breakdown.items()},
-                                      network_ms=round(nn_ms, 2)),
+            "phase_ms_per_step": {"forward_ms": round(ph[0]["ms"] / args.steps, 2),
+                                  "backward_ms": round(ph[1]["ms"] / args.steps, 2),
+                                  "born_ms": round(ph[2]["ms"] / args.steps, 2), "network_ms": round(nn_ms, 2)},
+            "rooflines_stencil": rooflines,
             "roofline_network": {
                 "kernel": "U-Net training (20 warm epochs, 108 patches, batch 32) + full-image apply",
                 "bound": "tensor", "achieved": round(nn_tflops, 2) if nn_tflops else None, "peak": bf16_peak,

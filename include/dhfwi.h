@@ -56,7 +56,9 @@ extern "C" {
 #define DHFWI_ERR_NONFINITE (-4)  /* non-finite or non-positive velocity, or non-finite result */
 #define DHFWI_ERR_OOM (-5)        /* device allocation failed */
 #define DHFWI_ERR_TIMEOUT (-6)    /* a bounded device-side wait ran out (a step kernel's tile copies did
-                                     not land within ~1 s); reported by the next call on the context */
+                                     not land within ~1 s); reported by the call itself when it
+                                     synchronises (misfit_out, data_misfit, loss_hist), else by the
+                                     next call on the context */
 #define DHFWI_ERR_CUDA (-7)       /* any other CUDA runtime error */
 #define DHFWI_ERR_STATE (-8)      /* call made in the wrong state (e.g. apply before train) */
 
@@ -219,8 +221,11 @@ int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long lon
  * services, or callers that must avoid the device synchronisation that
  * cudaMalloc/cudaFree can cause).
  *
- * model_shots_static computes exactly what model_shots computes (same
- * kernels, same results), without a context.  All its temporary buffers
+ * model_shots_static computes what model_shots computes (the same
+ * recurrence), without a context, with the one-step cp.async step kernel
+ * (the variant model_shots runs with DHFWI_TIME_BLOCK=0 and
+ * DHFWI_STEP_VARIANT=1, whose records it reproduces bit for bit; the
+ * default model_shots path agrees to relative L2 1e-5).  All its temporary buffers
  * (padded model arrays, wavefield state, geometry tables) live in one
  * file-scope device array of DHFWI_STATIC_SCRATCH_BYTES that every GPU
  * loading this library holds until the process exits; it calls no
@@ -229,9 +234,13 @@ int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long lon
  * model_shots.
  *   - Problems whose scratch exceeds the array return DHFWI_ERR_ARG with the
  *     sizes in model_shots_static_error().
+ *   - It runs on the CURRENT device: v_dev, d_dev and stream must belong to
+ *     it (make the device current first, e.g. cudaSetDevice).
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and keeps it; make that
+ *     first call before any stream capture.  A cudaDeviceReset of that
+ *     device invalidates the kept address: do not call model_shots_static
+ *     again in a process that has reset a device it used.
  *   - Every call shares the array and leaves its contents behind (each call
  *     clears what must start at zero); calls that overlap on the GPU (other
  *     streams, other host threads, other contexts of the same device) race.
@@ -311,6 +320,31 @@ int deblur_grad(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int n, i
  * the stream is synchronised.  Errors: DHFWI_ERR_ARG for a bad cfg. */
 int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz, int nx,
                  const dhfwi_train_cfg *cfg, int warm_start, float *loss_hist, void *stream);
+
+/* One convolution layer of the network on its own, with the kernels the
+ * network runs for it (Appendix A layers: the 3x3 convolutions and the 2x2
+ * stride-2 transposed convolutions of the up blocks), so that each GEMM path
+ * can be checked against a reference layer by layer.  All arrays float32
+ * device memory, NHWC:
+ *   x  [n][H][W][ci]   layer input (rounded to bfloat16 as the network does)
+ *   w  weights in the parameter layout of deblur's flat vector
+ *      ([co][3][3][ci] or [co][2][2][ci]; rounded to bfloat16), b [co]
+ *   gy [n][Ho][Wo][co] gradient of the layer output (rounded to bfloat16),
+ *      Ho, Wo = H, W (3x3) or 2H, 2W (transposed)
+ *   out  DHFWI_LAYER_FWD: [n][Ho][Wo][co], the stored activation:
+ *          bf16(LeakyReLU_0.2(conv(x) + b)) for the 3x3 convolution,
+ *          bf16(convT(x) + b) for the transposed one (widened to float32);
+ *        DHFWI_LAYER_DGRAD: [n][H][W][ci] = dL/dx for dL/dy = gy;
+ *        DHFWI_LAYER_WGRAD: dL/dw (parameter layout) then dL/db [co].
+ * ci and co are multiples of 8.  Unused pointers may be NULL.  Allocates its
+ * temporaries and synchronises the stream. */
+#define DHFWI_LAYER_CONV3 0
+#define DHFWI_LAYER_CONVT 1
+#define DHFWI_LAYER_FWD 0
+#define DHFWI_LAYER_DGRAD 1
+#define DHFWI_LAYER_WGRAD 2
+int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, int co, const float *x_dev,
+                 const float *w_dev, const float *b_dev, const float *gy_dev, float *out_dev, void *stream);
 
 /* Update direction from the gradient (Section 2.3.1): out = net(g / max|g|)
  * * max|g| on the full image, zero padded to a multiple of 2^levels and

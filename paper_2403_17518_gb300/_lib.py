@@ -91,6 +91,8 @@ SIGNATURES = [
     ("deblur_train", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TrainCfg),
                                     ctypes.c_int, _FP, _VP]),
     ("deblur_apply", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    ("deblur_layer", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
 ]
 OPTIONAL = {}
 

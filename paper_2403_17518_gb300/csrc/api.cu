@@ -563,6 +563,22 @@ int prep_model(dhfwi_ctx *ctx, const float *v, const float *dv, int rel, cudaStr
     return DHFWI_OK;
 }
 
+// Synchronises the stream and returns DHFWI_ERR_TIMEOUT (clearing the
+// record) if a step kernel of this call, or of an earlier one not yet
+// reported, ran out a bounded wait: calls that synchronise anyway report a
+// timeout themselves instead of leaving it to the next call.
+int sync_and_check_timeout(dhfwi_ctx *ctx, cudaStream_t st) {
+    CK(cudaMemcpyAsync(ctx->h_status + TFLAG_WORD, (unsigned *)ctx->status.p + TFLAG_WORD, sizeof(unsigned),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ctx->h_status[TFLAG_WORD]) {
+        ctx->h_status[TFLAG_WORD] = 0;
+        CK(cudaMemset((unsigned *)ctx->status.p + TFLAG_WORD, 0, sizeof(unsigned)));
+        return fail(ctx, DHFWI_ERR_TIMEOUT, "a step kernel timed out waiting for its tile copies");
+    }
+    return DHFWI_OK;
+}
+
 int begin_call(dhfwi_ctx *ctx) {
     if (!ctx) return DHFWI_ERR_ARG;
     ctx->err.clear();
@@ -1167,7 +1183,7 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     CK(cudaGetLastError());
     if (misfit_out) {
         CK(cudaMemcpyAsync(ctx->h_partial, ctx->partial.p, sizeof(double) * RESID_BLOCKS, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        if ((rc = sync_and_check_timeout(ctx, st))) return rc;
         double J = 0.0;
         for (int i = 0; i < RESID_BLOCKS; i++) J += ctx->h_partial[i];
         J *= 0.5;
@@ -1287,7 +1303,7 @@ int data_misfit(dhfwi_ctx *ctx, const float *a_dev, const float *b_dev, long lon
     launch_residual(a_dev, b_dev, (float *)ctx->rtmp.p, n, (double *)ctx->partial.p, RESID_BLOCKS, st);
     ctx->stats.kernel_launches++;
     CK(cudaMemcpyAsync(ctx->h_partial, ctx->partial.p, sizeof(double) * RESID_BLOCKS, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if ((rc = sync_and_check_timeout(ctx, st))) return rc;
     double J = 0.0;
     for (int i = 0; i < RESID_BLOCKS; i++) J += ctx->h_partial[i];
     *misfit_out = 0.5 * J;

@@ -22,7 +22,10 @@
 // whose copies have not landed after about one second makes the whole CTA
 // leave the kernel after setting *tflag = 1 (2: a misaligned shared-memory
 // base, checked before any copy), which the host reports as
-// DHFWI_ERR_TIMEOUT.
+// DHFWI_ERR_TIMEOUT.  Before leaving, the leader waits once more (again
+// bounded) for the copies it issued, so that a late copy does not land in
+// shared memory another CTA owns; if even that wait runs out, the results of
+// the launch and of the context's later calls are not to be trusted.
 #include <cuda.h>
 #include <cuda_runtime.h>
 

@@ -139,10 +139,12 @@ __device__ __forceinline__ void run_tiles(const StepCommon &c, unsigned stage_by
     }
     griddep_wait();
     griddep_launch_dependents();
+    unsigned pending = 0;  // leader: stages whose copies have not been seen to land
     auto issue = [&](int s) {
         fence_proxy_async();
         mbar_expect_tx(bar0 + 8 * s, stage_bytes);
         issue_loads(st[s], bar0 + 8 * s, co, mc);
+        pending |= 1u << s;
     };
     if (leader) {
         issue(0);
@@ -152,13 +154,22 @@ __device__ __forceinline__ void run_tiles(const StepCommon &c, unsigned stage_by
     unsigned phase = 0;
     int k = 0;
     for (int tix = b; tix < ntiles; tix += g, k = NS == 2 ? k ^ 1 : 0) {
-        const bool landed = mbar_wait(bar0 + 8 * k, (phase >> k) & 1u);
+        const unsigned par = (phase >> k) & 1u;
+        const bool landed = mbar_wait(bar0 + 8 * k, par);
         phase ^= 1u << k;
         if (leader) cp_async_wait_all();  // this stage's descriptor
         if (__syncthreads_or(!landed)) {
-            if (leader) atomicExch(c.tflag, 1u);
+            if (leader) {
+                // Before the CTA leaves, give its copies still in flight a
+                // second bounded wait, so that none lands in shared memory
+                // the next CTA on this SM owns.
+                for (int s = 0; s < NS; s++)
+                    if (pending & (1u << s)) mbar_wait(bar0 + 8 * s, s == k ? par : (phase >> s) & 1u);
+                atomicExch(c.tflag, 1u);
+            }
             return;
         }
+        if (leader) pending &= ~(1u << k);
         if (NS == 2 && leader && tix + g < ntiles) {
             copy_desc(&tail->desc[k ^ 1], &c.infos[tix + g]);
             issue(k ^ 1);

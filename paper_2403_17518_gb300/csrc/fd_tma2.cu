@@ -230,7 +230,10 @@ __global__ void __launch_bounds__(NT2, 2) fwd_pair_kernel(FwdArgs A, const __gri
         phase ^= 1u;
         if (leader) cp_async_wait_all();
         if (__syncthreads_or(!landed)) {
-            if (leader) atomicExch(A.c.tflag, 1u);
+            if (leader) {
+                mbar_wait(bar, phase ^ 1u);  // copies in flight: a second bounded wait before leaving
+                atomicExch(A.c.tflag, 1u);
+            }
             return;
         }
         const bool more = tix + g < ntiles;
@@ -436,7 +439,10 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
         phase ^= 1u;
         if (leader) cp_async_wait_all();
         if (__syncthreads_or(!landed)) {
-            if (leader) atomicExch(A.c.tflag, 1u);
+            if (leader) {
+                mbar_wait(bar, phase ^ 1u);  // copies in flight: a second bounded wait before leaving
+                atomicExch(A.c.tflag, 1u);
+            }
             return;
         }
         const bool more = tix + g < ntiles;

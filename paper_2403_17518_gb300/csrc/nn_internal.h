@@ -89,6 +89,7 @@ void launch_conv1x1_bwd(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long lon
 void launch_adam(float *theta, const float *grad, float *m, float *v, long long n, float lr, float b1, float b2,
                  float eps, int t, __nv_bfloat16 *shadow, cudaStream_t s);
 void launch_to_bf16(const float *x, long long n, __nv_bfloat16 *y, cudaStream_t s);
+void launch_bf16_to_f32(const __nv_bfloat16 *x, long long n, float *y, cudaStream_t s);
 void launch_transpose_w(const __nv_bfloat16 *w, int co, int taps, int ci, __nv_bfloat16 *wt, cudaStream_t s);
 // Several layers' transposes [co][taps][ci] -> [ci][taps][co] in one launch,
 // each at its parameter offset in w and wt.

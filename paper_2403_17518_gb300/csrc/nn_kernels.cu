@@ -823,6 +823,11 @@ __global__ void to_bf16_kernel(const float *__restrict__ x, long long n, __nv_bf
         y[i] = __float2bfloat16_rn(x[i]);
 }
 
+__global__ void bf16_to_f32_kernel(const __nv_bfloat16 *__restrict__ x, long long n, float *__restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __bfloat162float(x[i]);
+}
+
 // Transposed weights for the input-gradient GEMM:
 // wt[ci][tap][co] = w[co][tap][ci] (bf16), taps = 9 (conv) or 4 (transposed conv).
 __global__ void transpose_w_kernel(const __nv_bfloat16 *__restrict__ w, int co, int taps, int ci,
@@ -1336,6 +1341,9 @@ void launch_adam(float *theta, const float *grad, float *m, float *v, long long 
 }
 void launch_to_bf16(const float *x, long long n, __nv_bfloat16 *y, cudaStream_t s) {
     to_bf16_kernel<<<grid_for(n), 256, 0, s>>>(x, n, y);
+}
+void launch_bf16_to_f32(const __nv_bfloat16 *x, long long n, float *y, cudaStream_t s) {
+    bf16_to_f32_kernel<<<grid_for(n), 256, 0, s>>>(x, n, y);
 }
 void launch_transpose_w(const __nv_bfloat16 *w, int co, int taps, int ci, __nv_bfloat16 *wt, cudaStream_t s) {
     transpose_w_kernel<<<grid_for((long long)co * taps * ci), 256, 0, s>>>(w, co, taps, ci, wt);

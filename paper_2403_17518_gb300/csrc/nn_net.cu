@@ -969,6 +969,164 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
     return DHFWI_OK;
 }
 
+int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, int co, const float *x_dev,
+                 const float *w_dev, const float *b_dev, const float *gy_dev, float *out_dev, void *stream) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx_begin(ctx);
+    if (kind != DHFWI_LAYER_CONV3 && kind != DHFWI_LAYER_CONVT) return fail(ctx, DHFWI_ERR_ARG, "bad layer kind");
+    if (op != DHFWI_LAYER_FWD && op != DHFWI_LAYER_DGRAD && op != DHFWI_LAYER_WGRAD)
+        return fail(ctx, DHFWI_ERR_ARG, "bad layer operation");
+    if (n < 1 || H < 1 || W < 1 || ci < 8 || co < 8 || ci % 8 || co % 8)
+        return fail(ctx, DHFWI_ERR_ARG, "need n, H, W >= 1 and ci, co positive multiples of 8");
+    const bool conv = kind == DHFWI_LAYER_CONV3;
+    const int taps = conv ? 9 : 4, Ho = conv ? H : 2 * H, Wo = conv ? W : 2 * W;
+    const long long Pin = (long long)n * H * W, Pout = (long long)n * Ho * Wo;
+    if (Pout * std::max(ci, co) >= (1LL << 31)) return fail(ctx, DHFWI_ERR_ARG, "layer too large");
+    if (!out_dev || (op != DHFWI_LAYER_DGRAD && !x_dev) || (op != DHFWI_LAYER_WGRAD && !w_dev) ||
+        (op == DHFWI_LAYER_FWD && !b_dev) || (op != DHFWI_LAYER_FWD && !gy_dev))
+        return fail(ctx, DHFWI_ERR_ARG, "NULL argument");
+    cudaSetDevice(ctx_device(ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long nw = (long long)taps * ci * co;
+    // Temporaries of this call only (freed before it returns).
+    __nv_bfloat16 *x16 = nullptr, *w16 = nullptr, *wt16 = nullptr, *g16 = nullptr, *y16 = nullptr, *ones = nullptr;
+    float *part = nullptr, *wg = nullptr;
+    unsigned *err = nullptr;
+    const int wM = conv ? co : 4 * co, wN = (conv ? 9 * ci : ci) + 8;
+    const int splits = wgrad_splits(Pin, wM, wN);  // summed over the input grid's pixels
+    const long long fp_floats = std::max<long long>(2LL * 152 * 4 * 128 * 64, 8LL * Pout * std::max(ci, 4 * co));
+    const long long wg_floats = std::max<long long>((long long)splits * wM * wN, 512LL * wM);
+    int rc = DHFWI_OK;
+    auto cleanup = [&]() {
+        void *ps[] = {x16, w16, wt16, g16, y16, ones, part, wg, err};
+        for (void *p : ps) dev_free(p);
+    };
+    if ((rc = dev_alloc(ctx, (void **)&x16, 2 * (size_t)Pin * ci)) ||
+        (rc = dev_alloc(ctx, (void **)&w16, 2 * (size_t)nw)) || (rc = dev_alloc(ctx, (void **)&wt16, 2 * (size_t)nw)) ||
+        (rc = dev_alloc(ctx, (void **)&g16, 2 * (size_t)Pout * co)) ||
+        (rc = dev_alloc(ctx, (void **)&y16, 2 * (size_t)Pout * co)) || (rc = dev_alloc(ctx, (void **)&ones, 16)) ||
+        (rc = dev_alloc(ctx, (void **)&part, 4 * (size_t)fp_floats)) ||
+        (rc = dev_alloc(ctx, (void **)&wg, 4 * (size_t)wg_floats)) || (rc = dev_alloc(ctx, (void **)&err, 16))) {
+        cleanup();
+        return rc;
+    }
+    __nv_bfloat16 h1[8];
+    for (int i = 0; i < 8; i++) h1[i] = __float2bfloat16_rn(i == 0 ? 1.0f : 0.0f);
+    cudaError_t e = cudaMemcpy(ones, h1, sizeof h1, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(err, 0, 16);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(ctx, DHFWI_ERR_CUDA, cudaGetErrorString(e));
+    }
+    long long launches = 0;
+    // Operands rounded to bf16 where the network rounds them.
+    if (x_dev) launch_to_bf16(x_dev, Pin * ci, x16, s), launches++;
+    if (w_dev) {
+        launch_to_bf16(w_dev, nw, w16, s);
+        launch_transpose_w(w16, co, taps, ci, wt16, s);
+        launches += 2;
+    }
+    if (gy_dev) launch_to_bf16(gy_dev, Pout * co, g16, s), launches++;
+    if (op == DHFWI_LAYER_FWD) {
+        FpropArgs a{};
+        a.src = x16;
+        a.src_stride = ci;
+        a.C = ci;
+        a.Hs = H;
+        a.Ws = W;
+        a.Ho = H;
+        a.Wo = W;
+        a.M = (int)Pin;
+        a.bt = w16;
+        a.bias = b_dev;
+        a.slope = 0.2f;
+        a.dst_bf16 = y16;
+        a.dst_stride = co;
+        a.part = part;
+        a.part_floats = fp_floats;
+        a.err = err;
+        a.scale = 1;
+        if (conv) {
+            a.ntaps = 9;
+            for (int t = 0; t < 9; t++) {
+                a.dh[t] = t / 3 - 1;
+                a.dw[t] = t % 3 - 1;
+            }
+            a.N = co;
+            launch_fprop(a, EPI_BF16_LEAKY, s);
+        } else {
+            a.ntaps = 1;
+            a.dh[0] = a.dw[0] = 0;
+            a.N = 4 * co;
+            launch_fprop(a, EPI_BF16_CONVT, s);
+        }
+        launch_bf16_to_f32(y16, Pout * co, out_dev, s);
+        launches += 3;
+    } else if (op == DHFWI_LAYER_DGRAD) {
+        FpropArgs a{};
+        a.src = g16;
+        a.src_stride = co;
+        a.C = co;
+        a.Hs = Ho;
+        a.Ws = Wo;
+        a.Ho = H;
+        a.Wo = W;
+        a.M = (int)Pin;
+        a.N = ci;
+        a.bt = wt16;
+        a.dst_f32 = out_dev;
+        a.dst_stride = ci;
+        a.part = part;
+        a.part_floats = fp_floats;
+        a.err = err;
+        if (conv) {
+            a.ntaps = 9;
+            a.scale = 1;
+            for (int t = 0; t < 9; t++) {
+                a.dh[t] = 1 - t / 3;
+                a.dw[t] = 1 - t % 3;
+            }
+        } else {
+            a.ntaps = 4;
+            a.scale = 2;
+            for (int t = 0; t < 4; t++) {
+                a.dh[t] = t >> 1;
+                a.dw[t] = t & 1;
+            }
+        }
+        launch_fprop(a, EPI_F32, s);
+        launches += 2;
+    } else {
+        WgradArgs w{};
+        w.mode = conv ? WG_CONV : WG_CONVT;
+        w.g = g16;
+        w.g_stride = co;
+        w.x = x16;
+        w.x_stride = ci;
+        w.nimg = n;
+        w.H = H;
+        w.W = W;
+        w.ci = ci;
+        w.co = co;
+        w.M = wM;
+        w.nw = conv ? 9 * ci : ci;
+        w.N = wN;
+        w.ones = ones;
+        w.part = wg;
+        w.err = err;
+        launches += launch_wgrad(w, splits, out_dev, out_dev + nw, s);
+    }
+    e = cudaGetLastError();
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return fail(ctx, DHFWI_ERR_CUDA, cudaGetErrorString(e));
+    if (herr) return fail(ctx, DHFWI_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting for its MMAs");
+    ctx_count_launches(ctx, launches);
+    return DHFWI_OK;
+}
+
 int deblur_apply(dhfwi_ctx *ctx, const float *g_dev, int nz, int nx, float *out_dev, void *stream) {
     if (!ctx) return DHFWI_ERR_ARG;
     ctx_begin(ctx);

@@ -248,6 +248,22 @@ class Context:
                                           hist.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self._stream(stream)))
         return hist
 
+    def deblur_layer(self, kind: str, op: str, x=None, w=None, b=None, gy=None, n=1, H=1, W=1, ci=8, co=8,
+                     stream=None) -> torch.Tensor:
+        """One network layer alone (kind "conv3" or "convT"; op "fwd", "dgrad"
+        or "wgrad"), NHWC float32 tensors; see deblur_layer in dhfwi.h."""
+        k = {"conv3": 0, "convT": 1}[kind]
+        o = {"fwd": 0, "dgrad": 1, "wgrad": 2}[op]
+        taps = 9 if k == 0 else 4
+        Ho, Wo = (H, W) if k == 0 else (2 * H, 2 * W)
+        shape = {0: (n, Ho, Wo, co), 1: (n, H, W, ci), 2: (taps * ci * co + co,)}[o]
+        out = torch.empty(shape, dtype=torch.float32, device=self.device)
+        ptr = lambda t, nm: self._dense(t, nm) if t is not None else None
+        self._check(self.lib.deblur_layer(self.handle, k, o, int(n), int(H), int(W), int(ci), int(co), ptr(x, "x"),
+                                          ptr(w, "w"), ptr(b, "b"), ptr(gy, "gy"), self._dense(out, "out"),
+                                          self._stream(stream)))
+        return out
+
     def deblur_apply(self, g: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         nz, nx = g.shape
         out = out if out is not None else torch.empty_like(g)
@@ -268,10 +284,14 @@ def model_shots_static(nz: int, nx: int, h: float, dt: float, nb: int, v: torch.
     d = out if out is not None else torch.empty(g.n_data, dtype=torch.float32, device=v.device)
     if not (d.is_cuda and d.dtype == torch.float32 and d.is_contiguous() and d.numel() == g.n_data):
         raise ValueError("out must be a contiguous float32 CUDA tensor with n_data values")
+    if d.device != v.device:
+        raise ValueError("out must be on v's device")
     grid = _lib.Grid(int(nz), int(nx), int(nb), float(h), float(dt))
-    s = stream if stream is not None else torch.cuda.current_stream(v.device)
-    rc = lib.model_shots_static(ctypes.byref(grid), ctypes.c_void_p(v.data_ptr()), ctypes.byref(g.struct),
-                                ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    # The C call runs on the current device: make it v's.
+    with torch.cuda.device(v.device):
+        s = stream if stream is not None else torch.cuda.current_stream(v.device)
+        rc = lib.model_shots_static(ctypes.byref(grid), ctypes.c_void_p(v.data_ptr()), ctypes.byref(g.struct),
+                                    ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(s.cuda_stream))
     if rc != 0:
         raise DhfwiError(rc, lib.model_shots_static_error().decode())
     return d

@@ -34,16 +34,34 @@ def test_step_cell_updates():
 
 
 def test_profile_traffic_needs_the_profiled_source(tmp_path, monkeypatch):
-    kernel = "fwd_pair_kernel"
+    """A profile's DRAM bytes per update scale to the launch size while its
+    recorded source hash is the current one, and are ignored otherwise."""
     cells = 24253680
-    t = bench.profiled_traffic(kernel, cells)
-    txt = open(os.path.join(ROOT, "profiles", f"{kernel}_config2.md")).read()
-    assert ("kernel source sha256[:16]: `%s`" % bench.kernel_source_hash(kernel)) in txt
-    assert t is not None and 8 * cells <= t <= 16 * cells
-    # The same profile under another source hash is not used.
-    fake = tmp_path / "profiles"
-    fake.mkdir()
-    (fake / f"{kernel}_config2.md").write_text(txt.replace(bench.kernel_source_hash(kernel), "0" * 16))
+    src_root = tmp_path / "paper_2403_17518_gb300" / "csrc"
+    src_root.mkdir(parents=True)
+    for kernel in ("fwd_pair_kernel", "adj_pair_kernel", "born_tma_kernel"):
+        for f in bench.KERNEL_SOURCES[kernel]:
+            (src_root / f).write_text(open(os.path.join(ROOT, "paper_2403_17518_gb300", "csrc", f)).read())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda k: "f" * 16)
-    assert bench.profiled_traffic(kernel, cells) is None
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    for kernel in ("fwd_pair_kernel", "adj_pair_kernel", "born_tma_kernel"):
+        h = bench.kernel_source_hash(kernel)
+        (prof / f"{kernel}_config2.md").write_text(
+            f"kernel source sha256[:16]: `{h}`\n\nDRAM bytes per cell update: 12.5\n")
+        assert bench.profiled_traffic(kernel, cells) == 12.5 * cells
+        # The same profile under another source hash is not used.
+        (prof / f"{kernel}_config2.md").write_text(
+            f"kernel source sha256[:16]: `{'0' * 16}`\n\nDRAM bytes per cell update: 12.5\n")
+        assert bench.profiled_traffic(kernel, cells) is None
+    assert bench.profiled_traffic("no_such_kernel", cells) is None
+
+
+def test_committed_profiles_state_their_source_hash():
+    """Every committed step-kernel profile names the source hash it was taken on."""
+    import re
+
+    for kernel in bench.KERNEL_SOURCES:
+        path = os.path.join(ROOT, "profiles", f"{kernel}_config2.md")
+        if os.path.exists(path):
+            assert re.search(r"kernel source sha256\[:16\]:\s*`?[0-9a-f]{16}", open(path).read()), path

@@ -197,6 +197,13 @@ def test_bounded_wait_timeout_is_reported_and_context_survives():
     assert e.value.code == -6 and "TIMEOUT" in str(e.value)
     d = to_host(ctx.model_shots(to_dev(v), geom))
     assert rel_l2(d, oracle.model_shots(v, geom, c.h, c.dt, c.nb)) <= TOL
+    # A call that synchronises anyway (data_misfit) reports the timeout itself.
+    dd = to_dev(d)
+    ctx.selftest_timeout()
+    with pytest.raises(DhfwiError) as e:
+        ctx.data_misfit(dd, dd)
+    assert e.value.code == -6
+    assert ctx.data_misfit(dd, dd) == 0.0
 
 
 # ---------------------------------------------------------------------------
@@ -231,6 +238,47 @@ def test_config2_gradient_two_shots(config2):
     J, g = ctx.fwi_gradient(to_dev(v0), geom, to_dev(d_obs))
     assert abs(J - J_ref) <= TOL * J_ref
     assert rel_l2(to_host(g), g_ref) <= TOL
+
+
+def test_config2_born_and_migration_two_shots(config2):
+    """Born demigration and migration at the full record lengths of the
+    64-shot workload (3000-4000 steps, where FP32 error grows most), on two
+    of its shots, element-wise against the oracle; and the FP32 dot-product
+    test at that length."""
+    c = config2
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom).subset([5, 50])
+    assert int(geom.nt.min()) >= 3000
+    v0 = f32(c.v_init)
+    dv = f32(synth.smooth_random_field(c.nz, c.nx, 5) * 100.0)
+    d_ref = oracle.born_demig(v0, geom, dv, c.h, c.dt, c.nb)
+    d = to_host(ctx.born_demig(to_dev(v0), geom, to_dev(dv)))
+    assert rel_l2(d, d_ref) <= TOL
+    y = f32(synth.gaussian_field(geom.n_data, 24))
+    img_ref = oracle.rtm_mig(v0, geom, y, c.h, c.dt, c.nb)
+    img = to_host(ctx.rtm_mig(to_dev(v0), geom, to_dev(y)))
+    assert rel_l2(img, img_ref) <= TOL
+    x = f32(synth.gaussian_field((c.nz, c.nx), 23))
+    Lx = to_host(ctx.born_demig(to_dev(v0), geom, to_dev(x)))
+    a, b = float(np.dot(Lx, y)), float(np.sum(x * img))
+    assert abs(a - b) <= 1e-4 * max(abs(a), abs(b))
+
+
+@pytest.mark.parametrize("name", ["ragged", "config1"])
+def test_doubly_migrated_image_parity(name):
+    """The chain of the doubly migrated image (Eq. 15): the gradient of a
+    physical misfit, then delta m_1 = L~^T L~ g, against the oracle's
+    composition on the same (float32-rounded) gradient."""
+    c = CASES[name]
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom)
+    v0 = f32(c.v_init)
+    d_obs = ctx.model_shots(to_dev(f32(c.v_true)), geom)
+    _, g = ctx.fwi_gradient(to_dev(v0), geom, d_obs)
+    g_host = to_host(g)
+    dm1 = to_host(ctx.doubly_migrated(to_dev(v0), geom, g))
+    ref = oracle.rtm_mig(v0, geom, oracle.born_demig(v0, geom, g_host, c.h, c.dt, c.nb), c.h, c.dt, c.nb)
+    assert rel_l2(dm1, ref) <= TOL
 
 
 def test_fwi_update_and_data_misfit():

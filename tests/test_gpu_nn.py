@@ -142,6 +142,30 @@ def test_training_and_apply_parity(gemm, monkeypatch):
     assert rel_l2(out3, ref3) <= 1e-2
 
 
+def test_training_parity_base32():
+    """Training at the workload's width (base 32, 4 levels) on 64 x 64
+    patches, so the default tcgen05 kernels (3x3 convolutions and weight
+    gradients of every level below the top) run inside the training loop."""
+    ctx = _ctx()
+    from scipy.ndimage import gaussian_filter
+
+    g = np.random.Generator(np.random.PCG64(31))
+    img = np.cumsum(g.standard_normal((64, 128)), axis=1)
+    x = gaussian_filter(img, 2.0).astype(np.float32)
+    y = img.astype(np.float32)
+    spec = onn.UNetSpec(base=32, levels=4)
+    cfg = onn.TrainCfg(patch=64, stride=32, batch=3, epochs=2, lr=1e-3, seed=6)
+    hist = ctx.deblur_train(_dev(x), _dev(y), warm_start=False, base_channels=32, levels=4, patch=64, stride=32,
+                            batch=3, epochs=2, lr=1e-3, seed=6)
+    theta, href = onn.train(onn.init_params(spec, 6), x.astype(np.float64), y.astype(np.float64), spec, cfg)
+    assert np.allclose(hist, href, rtol=2e-2), (hist, href)
+    w = ctx.net_get()
+    assert rel_l2(w, theta) <= 0.1
+    out = ctx.deblur_apply(_dev(y)).cpu().numpy()
+    ref = onn.apply(w.astype(np.float64), y.astype(np.float64), spec)
+    assert rel_l2(out, ref) <= 1e-2
+
+
 def test_network_errors():
     ctx = _ctx()
     from paper_2403_17518_gb300.ops import DhfwiError

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("name", ["config1", "ragged"])
-def test_static_matches_model_shots_twice(name):
+def test_static_matches_model_shots_twice(name, monkeypatch):
     c = synth.config1_case() if name == "config1" else synth.tiny_case(nz=37, nx=141, nt=150, nb=20,
                                                                       n_shots=3, seed=8)
     ctx = gpu_ctx(c)
@@ -25,13 +25,25 @@ def test_static_matches_model_shots_twice(name):
 
     v, geom = to_dev(f32(c.v_true)), f32_geom(c.geom)
     ref = to_host(ctx.model_shots(v, geom))
+    # model_shots pinned to the kernel the static call runs (one step per
+    # launch, cp.async variant 1), in a fresh context (the variant choice is
+    # made once per context and geometry): the same bits.
+    monkeypatch.setenv("DHFWI_TIME_BLOCK", "0")
+    monkeypatch.setenv("DHFWI_STEP_VARIANT", "1")
+    ctx1 = gpu_ctx(c)
+    ref1 = to_host(ctx1.model_shots(v, geom))
+    ctx1.close()
+    monkeypatch.delenv("DHFWI_TIME_BLOCK")
+    monkeypatch.delenv("DHFWI_STEP_VARIANT")
     for _ in range(2):
         d = to_host(model_shots_static(c.nz, c.nx, c.h, c.dt, c.nb, v, geom))
         assert rel_l2(d, ref) <= 1e-5
+        assert np.array_equal(d, ref1)
     # A different model in between, then the first again: nothing carries over.
     model_shots_static(c.nz, c.nx, c.h, c.dt, c.nb, to_dev(f32(c.v_init)), geom)
     d = to_host(model_shots_static(c.nz, c.nx, c.h, c.dt, c.nb, v, geom))
     assert rel_l2(d, ref) <= 1e-5
+    assert np.array_equal(d, ref1)
 
 
 def test_static_rejects_problems_beyond_the_array():
