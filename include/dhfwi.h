@@ -193,6 +193,17 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
 int fwi_update(dhfwi_ctx *ctx, const float *v_dev, const float *dir_dev, float alpha, float vmin, float vmax,
                int mute_rows, float *v_out_dev, void *stream);
 
+/* Barzilai-Borwein short step of the plain-gradient arm (Section 3.1, Eq. 17):
+ *   alpha = (dx . dg) / (dg . dg),  dx = x_k - x_prev,  dg = g_k - g_prev,
+ * the differences and sums in float64, over the rows from mute_rows down
+ * (the rows the update leaves unchanged are left out).  The BB update is
+ * x_{k+1} = x_k - alpha g_k, i.e. fwi_update with alpha * max|g_k| (the
+ * normalisation of fwi_update divides by max|g_k|); gmax_out (may be NULL)
+ * receives max|g_k| over the same rows.  x_*, g_* [nz][nx] float32 device.
+ * DHFWI_ERR_NONFINITE when dg is zero.  Synchronises the stream. */
+int bb_step(dhfwi_ctx *ctx, const float *x_k, const float *x_prev, const float *g_k, const float *g_prev,
+            int mute_rows, double *alpha_out, double *gmax_out, void *stream);
+
 /* Quality-control filter of a migrated image (Section 3.3 images the data
  * with the estimated models to validate them; the paper names no filter, so
  * this is the reading adopted): out = -(D2 img) / h^2 with D2 the 5-point

@@ -76,6 +76,8 @@ SIGNATURES = [
     ("rtm_mig", ctypes.c_int, [_VP, _VP, ctypes.POINTER(Geom), _VP, _VP, ctypes.c_int, _VP]),
     ("fwi_update", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int,
                                   _VP, _VP]),
+    ("bb_step", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), _VP]),
     ("data_misfit", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _VP]),
     ("image_laplacian", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("dhfwi_selftest_timeout", ctypes.c_int, [_VP, _VP]),

@@ -1275,6 +1275,39 @@ int fwi_update(dhfwi_ctx *ctx, const float *v_dev, const float *dir_dev, float a
     return end_call(ctx);
 }
 
+int bb_step(dhfwi_ctx *ctx, const float *x_k, const float *x_prev, const float *g_k, const float *g_prev,
+            int mute_rows, double *alpha_out, double *gmax_out, void *stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!x_k || !x_prev || !g_k || !g_prev || !alpha_out || mute_rows < 0)
+        return fail(ctx, DHFWI_ERR_ARG, "NULL pointer or negative mute_rows");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long off = (long long)std::min(mute_rows, ctx->g.nz) * ctx->g.nx;
+    const long long n = (long long)ctx->g.nz * ctx->g.nx - off;
+    constexpr int NB = RESID_BLOCKS / 2;  // two sums per block in the partial buffer
+    launch_bb_partials(x_k + off, x_prev + off, g_k + off, g_prev + off, n, (double *)ctx->partial.p, NB,
+                       (unsigned *)ctx->status.p + 2, st);
+    ctx->stats.kernel_launches += 2;
+    CK(cudaMemcpyAsync(ctx->h_partial, ctx->partial.p, sizeof(double) * 2 * NB, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_status + 2, (unsigned *)ctx->status.p + 2, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                       st));
+    if ((rc = sync_and_check_timeout(ctx, st))) return rc;
+    double sxg = 0.0, sgg = 0.0;
+    for (int i = 0; i < NB; i++) {
+        sxg += ctx->h_partial[2 * i];
+        sgg += ctx->h_partial[2 * i + 1];
+    }
+    if (!(sgg > 0.0) || !std::isfinite(sxg) || !std::isfinite(sgg))
+        return fail(ctx, DHFWI_ERR_NONFINITE, "the gradient difference is zero or not finite");
+    *alpha_out = sxg / sgg;
+    if (gmax_out) {
+        float gm;
+        std::memcpy(&gm, &ctx->h_status[2], sizeof gm);
+        *gmax_out = gm;
+    }
+    return end_call(ctx);
+}
+
 int dhfwi_selftest_timeout(dhfwi_ctx *ctx, void *stream) {
     int rc = begin_call(ctx);
     if (rc) return rc;

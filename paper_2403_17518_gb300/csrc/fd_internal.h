@@ -211,6 +211,10 @@ void launch_residual(const float *ds, const float *dobs, float *r, long long n, 
 
 // vout = clamp(v - alpha * dir / max|dir|, vmin, vmax), dir taken as 0 in the
 // first mute_rows rows (also excluded from the max); mxbits: 1 word scratch.
+// Partial sums of Eq. 17 (dx.dg, dg.dg per block into partial[2 * nblocks])
+// and max |g_k| (float bits into *mxbits) over n values.
+void launch_bb_partials(const float *xk, const float *xp, const float *gk, const float *gp, long long n,
+                        double *partial, int nblocks, unsigned *mxbits, cudaStream_t s);
 void launch_update_model(const float *v, const float *dir, int nz, int nx, int mute_rows, float alpha, float vmin,
                          float vmax, unsigned *mxbits, float *vout, cudaStream_t s);
 

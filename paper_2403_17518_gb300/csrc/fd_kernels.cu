@@ -547,6 +547,52 @@ void launch_update_model(const float *v, const float *dir, int nz, int nx, int m
 }
 
 // ---------------------------------------------------------------------------
+// Barzilai-Borwein short step (Eq. 17): per-block float64 partial sums of
+// dx . dg and dg . dg (dx = x_k - x_{k-1}, dg = g_k - g_{k-1}, the
+// differences taken in float64, so exactly), summed on the host in block
+// order.
+// ---------------------------------------------------------------------------
+__global__ void bb_partials_kernel(const float *__restrict__ xk, const float *__restrict__ xp,
+                                   const float *__restrict__ gk, const float *__restrict__ gp, long long n,
+                                   double *__restrict__ partial) {
+    double sxg = 0.0, sgg = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double dx = (double)xk[i] - (double)xp[i], dg = (double)gk[i] - (double)gp[i];
+        sxg += dx * dg;
+        sgg += dg * dg;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sxg += __shfl_xor_sync(0xffffffffu, sxg, off);
+        sgg += __shfl_xor_sync(0xffffffffu, sgg, off);
+    }
+    __shared__ double ws[2][32];
+    if ((threadIdx.x & 31) == 0) {
+        ws[0][threadIdx.x >> 5] = sxg;
+        ws[1][threadIdx.x >> 5] = sgg;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const bool in = threadIdx.x < (blockDim.x >> 5);
+        double a = in ? ws[0][threadIdx.x] : 0.0, b = in ? ws[1][threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, off);
+            b += __shfl_xor_sync(0xffffffffu, b, off);
+        }
+        if (threadIdx.x == 0) {
+            partial[2 * blockIdx.x] = a;
+            partial[2 * blockIdx.x + 1] = b;
+        }
+    }
+}
+
+void launch_bb_partials(const float *xk, const float *xp, const float *gk, const float *gp, long long n,
+                        double *partial, int nblocks, unsigned *mxbits, cudaStream_t s) {
+    bb_partials_kernel<<<nblocks, 256, 0, s>>>(xk, xp, gk, gp, n, partial);
+    cudaMemsetAsync(mxbits, 0, sizeof(unsigned), s);
+    if (n > 0) absmax_bits_kernel<<<512, 256, 0, s>>>(gk, n, mxbits);
+}
+
+// ---------------------------------------------------------------------------
 // Image QC filter: out = -(5-point Laplacian of img) / h^2, the grid's edge
 // values repeated outside it (zero normal derivative).
 // ---------------------------------------------------------------------------

@@ -77,16 +77,11 @@ def model_rms(v: torch.Tensor, v_true: torch.Tensor) -> float:
     return float(torch.sqrt(torch.mean((v - v_true) ** 2)).item())
 
 
-def line_search(ctx, v, dirn, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_rows):
-    """Two-trial parabolic line search on the misfit along -dirn; returns
-    (alpha, whether a trial lowered the misfit)."""
-    Js = []
-    for a in (a1, 2 * a1):
-        ctx.fwi_update(v, dirn, a, vmin, vmax, mute_rows, out=trial)
-        ctx.model_shots(trial, ga, out=d_try)
-        Js.append(ctx.data_misfit(d_try, d_obs))
-    # Parabola through (0, J0), (a1, J1), (2 a1, J2).
-    J1, J2 = Js
+def parabolic_alpha(J0: float, J1: float, J2: float, a1: float):
+    """Step from the misfits at 0, a1 and 2 a1 (the parabola through the three
+    points, minimised on [0, 4 a1]); returns (alpha, whether a trial lowered
+    the misfit).  No improvement: 0; no minimiser, or a clamped vertex at 0:
+    the better trial."""
     curv = (J2 - 2 * J1 + J0) / (2 * a1 * a1)
     slope = (4 * J1 - 3 * J0 - J2) / (2 * a1)
     if curv > 0:
@@ -102,12 +97,26 @@ def line_search(ctx, v, dirn, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_
     return a_best, improved
 
 
+def line_search(ctx, v, dirn, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_rows):
+    """Two-trial parabolic line search on the misfit along -dirn; returns
+    (alpha, whether a trial lowered the misfit)."""
+    Js = []
+    for a in (a1, 2 * a1):
+        ctx.fwi_update(v, dirn, a, vmin, vmax, mute_rows, out=trial)
+        ctx.model_shots(trial, ga, out=d_try)
+        Js.append(ctx.data_misfit(d_try, d_obs))
+    return parabolic_alpha(J0, Js[0], Js[1], a1)
+
+
 def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, cold_epochs: int, warm_epochs: int,
             vmin: float, vmax: float, mute_rows: int = 5, log=None, hybrid_iters: int = 0):
-    """mode: "plain" (gradient), "deblur" (network direction every iteration)
-    or "hybrid" (network direction for the first hybrid_iters iterations of
-    the run, the gradient after: the Hessian approximation steers the early
-    iterations, then conventional FWI continues, Section 4)."""
+    """mode: "plain" (gradient, parabolic line search), "bb" (gradient with
+    the Barzilai-Borwein short step of Eq. 17, the paper's baseline; the
+    first iteration of each band takes the line search), "deblur" (network
+    direction every iteration) or "hybrid" (network direction for the first
+    hybrid_iters iterations of the run, the gradient after: the Hessian
+    approximation steers the early iterations, then conventional FWI
+    continues, Section 4)."""
     dev = ctx.device
     v_true = torch.tensor(case.v_true, dtype=torch.float32, device=dev)
     v = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
@@ -120,8 +129,10 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
     dm1 = ctx.new_model()
     trial = ctx.new_model()
     done_iters = 0
+    v_prev, g_prev = ctx.new_model(), ctx.new_model()
     for fc in bands:
         trained_in_band = False  # the network restarts from scratch in each band (Section 4)
+        have_prev = False  # BB needs two models and gradients of the same band
         g = copy.deepcopy(case.geom)
         g.wavelet = lowpass(np.asarray(g.wavelet, dtype=np.float64), case.dt, fc)
         ga = GeomArgs(g)
@@ -160,8 +171,19 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
                                                 mute_rows)
                 else:
                     dirn = grad
-                    a_best, _ = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_rows)
-                    solves += 2
+                    alpha_bb = 0.0
+                    if mode == "bb" and have_prev:
+                        # Eq. 17: x_{k+1} = x_k - alpha g_k; fwi_update divides by max|g_k|.
+                        alpha_bb, gmax = ctx.bb_step(v, v_prev, grad, g_prev, mute_rows)
+                        a_best = alpha_bb * gmax
+                    if alpha_bb <= 0.0:  # no curvature estimate yet (or a negative one): line search
+                        a_best, _ = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
+                                                mute_rows)
+                        solves += 2
+                if mode == "bb":
+                    v_prev.copy_(v)
+                    g_prev.copy_(grad)
+                    have_prev = True
                 ctx.fwi_update(v, dirn, a_best, vmin, vmax, mute_rows, out=v)
             done_iters += 1
             rec = {"band": fc, "iter": it + 1, "gpu_s": timer.seconds(), "solves": solves,
@@ -210,7 +232,7 @@ def main():
     p.add_argument("--iters-plain", type=int, default=0, help="iterations per band, plain arm (default --iters)")
     p.add_argument("--mute", type=int, default=5, help="top rows muted in the update and the network input")
     p.add_argument("--lr", type=float, default=2e-4, help="network learning rate")
-    p.add_argument("--arms", default="plain,deblur", help="comma list of plain, deblur, hybrid or hybridN")
+    p.add_argument("--arms", default="plain,deblur", help="comma list of plain, bb, deblur, hybrid or hybridN")
     p.add_argument("--iters-hybrid", type=int, default=0, help="iterations per band, hybrid arm (default --iters)")
     p.add_argument("--hybrid-net-iters", type=int, default=5,
                    help="hybrid arm: iterations at the start of the run that use the network direction")
@@ -234,7 +256,7 @@ def main():
         mode = "hybrid" if name.startswith("hybrid") else name
         hyb = int(name[6:]) if mode == "hybrid" and name[6:] else a.hybrid_net_iters
         iters = a.iters
-        if mode == "plain" and a.iters_plain > 0:
+        if mode in ("plain", "bb") and a.iters_plain > 0:
             iters = a.iters_plain
         if mode == "hybrid" and a.iters_hybrid > 0:
             iters = a.iters_hybrid

@@ -186,6 +186,16 @@ class Context:
                                         self._model(out, "out"), self._stream(stream)))
         return out
 
+    def bb_step(self, x_k: torch.Tensor, x_prev: torch.Tensor, g_k: torch.Tensor, g_prev: torch.Tensor,
+                mute_rows: int = 0, stream=None):
+        """(alpha, max|g_k|): the Barzilai-Borwein short step of Eq. 17 below
+        the muted rows; the update is fwi_update(x_k, g_k, alpha * max|g_k|)."""
+        a, gm = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        self._check(self.lib.bb_step(self.handle, self._model(x_k, "x_k"), self._model(x_prev, "x_prev"),
+                                     self._model(g_k, "g_k"), self._model(g_prev, "g_prev"), int(mute_rows),
+                                     ctypes.byref(a), ctypes.byref(gm), self._stream(stream)))
+        return a.value, gm.value
+
     def data_misfit(self, a: torch.Tensor, b: torch.Tensor, stream=None) -> float:
         """1/2 ||a - b||^2 accumulated in float64 on the device."""
         if a.numel() != b.numel():

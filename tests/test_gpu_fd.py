@@ -287,14 +287,39 @@ def test_fwi_update_and_data_misfit():
     g = np.random.Generator(np.random.PCG64(12))
     v = f32(c.v_init)
     d = f32(g.standard_normal(v.shape))
+    from oracle import fwi_step
+
     out = to_host(ctx.fwi_update(to_dev(v), to_dev(d), 25.0, 1500.0, 2200.0, 3))
-    dm = d.copy()
-    dm[:3] = 0.0
-    ref = np.clip(v - 25.0 * dm / np.abs(dm).max(), 1500.0, 2200.0)
+    ref = fwi_step.update(v, d, 25.0, 1500.0, 2200.0, mute_rows=3)
     assert np.abs(out - ref).max() <= 1e-3
     a, b = f32(g.standard_normal(1000)), f32(g.standard_normal(1000))
     J = ctx.data_misfit(to_dev(a), to_dev(b))
     assert J == pytest.approx(oracle.misfit(a, b), rel=1e-6)
+
+
+def test_bb_step_matches_oracle():
+    """The Barzilai-Borwein short step (Eq. 17) over the unmuted rows and
+    max|g_k| there, against the oracle; the BB update through fwi_update."""
+    c = CASES["ragged"]
+    ctx = gpu_ctx(c)
+    from oracle import fwi_step
+
+    g = np.random.Generator(np.random.PCG64(21))
+    xp, xk = f32(c.v_init), f32(c.v_init + g.standard_normal((c.nz, c.nx)))
+    gp, gk = f32(g.standard_normal((c.nz, c.nx))), f32(g.standard_normal((c.nz, c.nx)))
+    gk[:4] = 1e3  # muted rows: left out of both sums and of the max
+    alpha, gmax = ctx.bb_step(to_dev(xk), to_dev(xp), to_dev(gk), to_dev(gp), mute_rows=4)
+    ref = fwi_step.bb_short(xk[4:], xp[4:], gk[4:], gp[4:])
+    assert alpha == pytest.approx(ref, rel=1e-12)
+    assert gmax == np.abs(gk[4:]).max()
+    out = to_host(ctx.fwi_update(to_dev(xk), to_dev(gk), alpha * gmax, 100.0, 9000.0, 4))
+    exp = xk.copy()
+    exp[4:] -= alpha * gk[4:]
+    assert np.abs(out - exp).max() <= 1e-3
+    from paper_2403_17518_gb300.ops import DhfwiError
+
+    with pytest.raises(DhfwiError, match="NONFINITE"):
+        ctx.bb_step(to_dev(xk), to_dev(xp), to_dev(gp), to_dev(gp))
 
 
 def test_image_laplacian_and_rtm_qc():

@@ -178,3 +178,123 @@ def test_training_reduces_loss():
     flat = nn.init_params(spec, 3)
     _, hist = nn.train(flat, x, img, spec, cfg)
     assert hist[-1] < 0.7 * hist[0], hist
+
+
+def test_adam_three_steps_hand_derived():
+    """Three Adam steps of one parameter with beta1 = 1/2, beta2 = 3/4, eps = 0,
+    lr = 1 and gradients 1, -2, 3, derived by hand:
+      t=1: m = 1/2,   v = 1/4,      m^ = 1,   v^ = 1      -> theta = -1
+      t=2: m = -3/4,  v = 19/16,    m^ = -1,  v^ = 19/7   -> theta = -1 + sqrt(7/19)
+      t=3: m = 9/8,   v = 201/64,   m^ = 9/7, v^ = 201/37 -> theta -= (9/7) sqrt(37/201)
+    (swapping the betas, or dropping a bias correction, changes steps 2 and 3)."""
+    th, m, v = np.zeros(1), np.zeros(1), np.zeros(1)
+    out = []
+    for t, g in enumerate((1.0, -2.0, 3.0), start=1):
+        th, m, v = nn.adam_step(th, np.array([g]), m, v, t, 1.0, b1=0.5, b2=0.75, eps=0.0)
+        out.append((float(th[0]), float(m[0]), float(v[0])))
+    th2 = -1.0 + math.sqrt(7.0 / 19.0)
+    th3 = th2 - (9.0 / 7.0) * math.sqrt(37.0 / 201.0)
+    ref = [(-1.0, 0.5, 0.25), (th2, -0.75, 19.0 / 16.0), (th3, 9.0 / 8.0, 201.0 / 64.0)]
+    for got, want in zip(out, ref):
+        assert got == pytest.approx(want, rel=1e-14, abs=1e-15)
+
+
+def test_train_learning_rate_sequence(monkeypatch):
+    """The rate train() passes to Adam: lr0 (1 + cos(pi t / T)) / 2 times the
+    warm-up factor min(1, (t+1)/W), W = ceil(warmup_frac T), with Adam's step
+    count t+1.  3 patches, batch 2 -> 2 steps per epoch, 2 epochs -> T = 4;
+    warmup_frac 0.5 -> W = 2."""
+    seen = []
+    real = nn.adam_step
+
+    def spy(theta, grad, m, v, t, lr, *a, **k):
+        seen.append((t, lr))
+        return real(theta, grad, m, v, t, lr, *a, **k)
+
+    monkeypatch.setattr(nn, "adam_step", spy)
+    spec = nn.UNetSpec(base=4, levels=1)
+    g = rng(3)
+    img = g.standard_normal((8, 16))
+    cfg = nn.TrainCfg(patch=8, stride=4, batch=2, epochs=2, lr=0.4, seed=2, warmup_frac=0.5)
+    nn.train(nn.init_params(spec, 1), img, img, spec, cfg)
+    lr0 = 0.4
+    want = [(1, lr0 * 0.5), (2, 0.5 * lr0 * (1 + math.cos(math.pi / 4))), (3, 0.5 * lr0),
+            (4, 0.5 * lr0 * (1 + math.cos(3 * math.pi / 4)))]
+    assert [t for t, _ in seen] == [t for t, _ in want]
+    for (_, a), (_, b) in zip(seen, want):
+        assert a == pytest.approx(b, rel=1e-14)
+
+
+def test_normalize_mutes_and_scales():
+    img = np.array([[900.0, -1000.0, 5.0], [1.0, -3.0, 2.0], [0.5, 1.5, -2.5]])
+    out, m = nn.normalize(img, mute_rows=1)
+    assert m == 3.0
+    assert np.array_equal(out, np.array([[0.0, 0.0, 0.0], [1 / 3, -1.0, 2 / 3], [0.5 / 3, 0.5, -2.5 / 3]]))
+    out0, m0 = nn.normalize(img)
+    assert m0 == 1000.0 and out0[0, 1] == -1.0
+
+
+def test_train_sees_muted_normalised_patches(monkeypatch):
+    """The patches train() feeds the network: rows above mute_rows zero, the
+    rest scaled by the max below the mute (so the largest |value| is 1)."""
+    batches = []
+    real = nn.forward
+
+    def spy(flat, x, spec, round_bf16=True):
+        batches.append(np.array(x))
+        return real(flat, x, spec, round_bf16)
+
+    monkeypatch.setattr(nn, "forward", spy)
+    spec = nn.UNetSpec(base=4, levels=1)
+    g = rng(4)
+    img = g.standard_normal((8, 12))
+    img[:2] = 50.0  # the footprint rows that the mute removes
+    cfg = nn.TrainCfg(patch=8, stride=4, batch=8, epochs=1, lr=1e-3, seed=2, mute_rows=2)
+    nn.train(nn.init_params(spec, 1), img, img, spec, cfg)
+    X = np.concatenate(batches)
+    assert X.shape == (2, 1, 8, 8)
+    assert np.all(X[:, :, :2] == 0.0)
+    assert np.abs(X).max() == 1.0
+    ref = img / np.abs(img[2:]).max()
+    got = sorted(float(X[k, 0, 2:].sum()) for k in range(2))
+    exp = sorted(float(ref[2:, x0:x0 + 8].sum()) for x0 in (0, 4))
+    assert got == pytest.approx(exp, rel=1e-12)
+
+
+def test_apply_pads_crops_and_rescales(monkeypatch):
+    """apply(): the network sees the muted image over its max, zero-padded at
+    the bottom and right to a multiple of 2^levels; its output is cropped
+    back and multiplied by that max (checked with a stand-in network)."""
+    seen = []
+
+    def fake(flat, x, spec, round_bf16=True):
+        seen.append(np.array(x))
+        H, W = x.shape[2:]
+        ramp = np.arange(H * W, dtype=np.float64).reshape(1, 1, H, W)
+        return 3.0 * x + ramp, None
+
+    monkeypatch.setattr(nn, "forward", fake)
+    spec = nn.UNetSpec(base=4, levels=2)
+    g = rng(5)
+    img = g.standard_normal((13, 22))
+    out = nn.apply(None, img, spec, mute_rows=3)
+    (x,) = seen
+    assert x.shape == (1, 1, 16, 24)
+    m = np.abs(img[3:]).max()
+    exp_in = np.zeros((16, 24))
+    exp_in[3:13, :22] = img[3:] / m
+    assert np.array_equal(x[0, 0], exp_in)
+    ramp = np.arange(16 * 24, dtype=np.float64).reshape(16, 24)
+    assert np.allclose(out, (3.0 * exp_in + ramp)[:13, :22] * m, rtol=1e-15, atol=0)
+
+
+def test_apply_is_scale_equivariant():
+    """apply(c g) = c apply(g) for c > 0: the normalisation takes out the
+    scale and the output rescaling puts it back (exactly, in exact arithmetic;
+    here with bfloat16 rounding off)."""
+    spec = nn.UNetSpec(base=4, levels=2)
+    flat = nn.init_params(spec, 11)
+    img = rng(6).standard_normal((16, 20))
+    a = nn.apply(flat, img, spec, round_bf16=False, mute_rows=2)
+    b = nn.apply(flat, 7.25 * img, spec, round_bf16=False, mute_rows=2)
+    assert np.allclose(b, 7.25 * a, rtol=1e-12, atol=1e-12 * np.abs(b).max())
