@@ -703,6 +703,7 @@ def main():
             "gpu_launches": int(launches[0]),
             "launches_before_timed_region": int(launches_before),
             "step_variants": ctx.stats()["step_variant"],
+            "time_block_depth": {"forward": ctx.stats()["time_block"][0], "adjoint": ctx.stats()["time_block"][1]},
             "history_steps": {"stored": hist["steps"], "of": nt_max,
                               "workspace_gb": round(ctx.stats()["workspace_bytes"] / 1e9, 2)},
             "phase_ms_per_step": {"forward_ms": round(ph[0]["ms"] / args.steps, 2),

@@ -124,6 +124,10 @@ typedef struct {
      * either way. */
     int history_steps;
     long long history_cells;   /* phase-0 cell updates that also stored a^n */
+    /* Time steps per launch (1 or 2) of the forward and the adjoint sweeps:
+     * the autotuner times both depths per geometry; DHFWI_TIME_BLOCK=0
+     * (environment) forces 1, any other value 2. */
+    int time_block[2];
 } dhfwi_stats_t;
 
 /* Create a context on CUDA device `device` for grid `g`.  The context owns all

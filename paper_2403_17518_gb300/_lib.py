@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_double), ("phase_ms", ctypes.c_double * 3),
                 ("phase_launches", ctypes.c_longlong * 3), ("phase_cells", ctypes.c_longlong * 3),
                 ("step_variant", ctypes.c_int * 4), ("history_steps", ctypes.c_int),
-                ("history_cells", ctypes.c_longlong)]
+                ("history_cells", ctypes.c_longlong), ("time_block", ctypes.c_int * 2)]
 
 
 class TrainCfg(ctypes.Structure):

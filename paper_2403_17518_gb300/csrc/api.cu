@@ -79,6 +79,9 @@ struct dhfwi_ctx {
     // Step-kernel launch choice per kind: forward, forward+segment store,
     // adjoint, Born.  Picked by autotune() for the current plan.
     StepLaunch launch[4];
+    // Time steps per launch (1 or 2) of the forward and the adjoint sweeps,
+    // chosen by the autotuner.
+    int depth[2] = {2, 2};
     unsigned long long tuned_hash = 0;
     int nsm = 1;
     cudaEvent_t ev[3][2] = {};
@@ -615,11 +618,14 @@ void phase_end(dhfwi_ctx *ctx, int ph, cudaStream_t st, long long launches, long
     ctx->ev_used[ph] = true;
 }
 
+bool time_blocking(const dhfwi_ctx *ctx, int which);
+
 int end_call(dhfwi_ctx *ctx) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
     ctx->stats.checkpoint_every = ctx->ck_every;
     for (int k = 0; k < 4; k++) ctx->stats.step_variant[k] = ctx->launch[k].variant;
+    for (int k = 0; k < 2; k++) ctx->stats.time_block[k] = time_blocking(ctx, k) ? 2 : 1;
     double ws = ctx->kap.bytes + ctx->dkap.bytes + ctx->fields.bytes + ctx->ck.bytes +
                 ctx->abuf.bytes + ctx->hist.bytes + ctx->dtmp.bytes + ctx->rtmp.bytes;
     ctx->stats.workspace_bytes = ws;
@@ -633,11 +639,15 @@ void set_variant(dhfwi_ctx *ctx, int kind, int v) {
     cudaGetLastError();
 }
 
+int tune_depth(dhfwi_ctx *ctx, cudaStream_t st, const float *one_step_ms, int reps);
+
 // Autotuner: for the current plan, time every step-kernel variant of each
 // kind on the plan's full tile list (all shots active) using the scratch
-// field pools, and keep the fastest.  The pools are zeroed again by the call
-// that follows, so tuning leaves no trace in the results.  Runs once per
-// geometry; DHFWI_STEP_VARIANT=<0..2> pins a variant instead.
+// field pools, and keep the fastest; then the time-blocking depth of the
+// forward and adjoint sweeps (tune_depth).  The pools are zeroed again by the
+// call that follows, so tuning leaves no trace in the results.  Runs once per
+// geometry; DHFWI_STEP_VARIANT=<0..6> pins a variant instead (and the depth
+// stays two unless DHFWI_TIME_BLOCK says otherwise).
 int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
     const Plan &P = ctx->plan;
     if (ctx->tuned_hash == P.hash) return DHFWI_OK;
@@ -668,6 +678,7 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     long long timed = 0;
+    float best_ms[4] = {0.f, 0.f, 0.f, 0.f};
     for (int kind = 0; kind < 4; kind++) {
         float best = 1e30f;
         int best_v = 1;
@@ -734,20 +745,25 @@ int autotune(dhfwi_ctx *ctx, cudaStream_t st) {
             }
         }
         set_variant(ctx, kind, best_v);
+        best_ms[kind] = best;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->stats.kernel_launches += timed;
+    if ((rc = tune_depth(ctx, st, best_ms, reps))) return rc;
     ctx->tuned_hash = P.hash;
     CK(cudaGetLastError());
     return DHFWI_OK;
 }
 
-// Two-step (time-blocked) forward launches are used unless
-// DHFWI_TIME_BLOCK=0 or tensor maps are unavailable (read per call).
-bool time_blocking() {
+// DHFWI_TIME_BLOCK=0 forces one time step per launch, any other value two;
+// unset, the autotuner's choice applies (read per call).  Without tensor
+// maps there are no two-step kernels.
+bool time_blocking(const dhfwi_ctx *ctx, int which) {
+    if (!encode_tiled()) return false;
     const char *e = getenv("DHFWI_TIME_BLOCK");
-    return !(e && strcmp(e, "0") == 0) && encode_tiled() != nullptr;
+    if (e && *e) return strcmp(e, "0") != 0;
+    return ctx->depth[which] == 2;
 }
 
 // Maps of a two-step forward launch (u^n with the doubled halo, D^n with
@@ -772,6 +788,76 @@ int adj_pair_maps(dhfwi_ctx *ctx, const AdjArgs &b, TileMaps *M) {
     if ((rc = tensor_map(ctx, b.g, MAP_POOL_CELL, &M->m[3]))) return rc;
     if ((rc = tensor_map(ctx, b.a, MAP_POOL_CELL, &M->m[4]))) return rc;
     return tensor_map(ctx, b.a2, MAP_POOL_CELL, &M->m[5]);
+}
+
+// Time-blocking depth of the forward and the adjoint sweeps: `reps` launches
+// of the two-step kernel on the plan's full tile list against twice the
+// chosen one-step kernel's time for as many launches (one_step_ms: the
+// variant loop's best time of `reps` launches per kind: forward, forward with
+// store, adjoint, Born).  The faster depth is kept.
+int tune_depth(dhfwi_ctx *ctx, cudaStream_t st, const float *one_step_ms, int reps) {
+    if (!encode_tiled()) return DHFWI_OK;
+    const Plan &P = ctx->plan;
+    const long long pool = P.pool_floats;
+    float *F = (float *)ctx->fields.p;
+    const int ntiles = active_tiles(P, 0);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = DHFWI_OK;
+    for (int which = 0; which < 2 && !rc; which++) {
+        float ms = 0.f;
+        for (int rep = -1; rep < reps && !rc; rep++) {
+            if (rep == 0) cudaEventRecord(e0, st);
+            TileMaps M;
+            if (which == 0) {
+                FwdArgs a{};
+                a.c = common(ctx);
+                a.u = F;
+                a.un = F + pool;
+                a.dd = F + 2 * pool;
+                a.dd_out = F + 7 * pool;
+                a.d = (float *)ctx->dtmp.p;
+                a.n = 0;
+                if (!(rc = pair_maps(ctx, a, &M))) launch_fwd_pair(a, ntiles, M, st);
+                ctx->stats.kernel_launches++;
+            } else {
+                AdjArgs b{};
+                b.c = common(ctx);
+                b.nu = F;
+                b.nun = F + pool;
+                b.dd = F + 2 * pool;
+                b.dd_out = F + 8 * pool;
+                b.a = F + 3 * pool;
+                b.a2 = F + 5 * pool;
+                b.g = F + 4 * pool;
+                b.r = (const float *)ctx->rtmp.p;
+                b.k = 2;
+                const int nrt = P.rtiles_prefix[active_slots(P, 1)];
+                launch_adj_inject(b, (const int *)P.d_rtiles.p, nrt, st);
+                if (!(rc = adj_pair_maps(ctx, b, &M))) launch_adj_pair(b, ntiles, M, st);
+                ctx->stats.kernel_launches += 1 + (nrt > 0);
+            }
+        }
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(ctx, e, "autotune (time-blocking depth)");
+        }
+        if (rc) break;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float one = one_step_ms[which == 0 ? 0 : 2];
+        ctx->depth[which] = ms <= 2.f * one ? 2 : 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {  // no two-step launch possible here: one step per launch
+        ctx->err.clear();
+        ctx->depth[0] = ctx->depth[1] = 1;
+    }
+    return DHFWI_OK;
 }
 
 // Advances the forward state from step n: two steps with one two-step launch
@@ -822,7 +908,7 @@ int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, flo
     a.d = d;
     float *cur = uA, *nxt = uB, *dcur = dd, *dnxt = dd2;
     const long long pool = P.pool_floats;
-    const bool blocking = time_blocking();
+    const bool blocking = time_blocking(ctx, 0);
     const int K = ctx->ck_every, S = backward ? ctx->hist_segs : 0;
     const int H = std::min(S * K, P.nt_max);  // steps whose a^n are stored
     float *ck = (float *)ctx->ck.p, *hist = (float *)ctx->hist.p;
@@ -865,7 +951,7 @@ int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *nuA, float *nuB, fl
     const long long pool = P.pool_floats;
     const int K = ctx->ck_every, S = ctx->hist_segs;
     const int nseg = (P.nt_max + K - 1) / K;
-    const bool blocking = time_blocking();
+    const bool blocking = time_blocking(ctx, 0), blocking_adj = time_blocking(ctx, 1);
     float *ck = (float *)ctx->ck.p, *abuf = (float *)ctx->abuf.p, *hist = (float *)ctx->hist.p;
     FwdArgs f{};
     f.c = common(ctx);
@@ -899,7 +985,7 @@ int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *nuA, float *nuB, fl
             b.dd = dcur_nu;
             b.a = slot(k - 1);
             b.k = k;
-            if (blocking && k - 1 >= n0 + 1) {
+            if (blocking_adj && k - 1 >= n0 + 1) {
                 // Steps k and k-1: the data of step k go into D_nu first.
                 const int nrt = P.rtiles_prefix[active_slots(P, k - 1)];
                 launch_adj_inject(b, (const int *)P.d_rtiles.p, nrt, st);

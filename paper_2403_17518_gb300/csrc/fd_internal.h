@@ -156,8 +156,11 @@ struct BornArgs {
 // R = 2, 4, 8 rows per thread (CTA = 32 x 64/R threads).  Variants 3-5:
 // tiles staged by TMA (cp.async.bulk.tensor issued by one thread, mbarrier
 // completion), R = 4, 8, 16; the adjoint and Born kernels stop at R = 8
-// (step_variants()).  The autotuner in api.cu times them per geometry.
-constexpr int N_STEP_VARIANTS = 6;
+// (step_variants()).  Born only: variants 5 and 6 are its TMA kernel with
+// R = 4 and 8 and ONE stage (refilled after each tile) instead of two, so
+// that two CTAs fit on an SM.  The autotuner in api.cu times them per
+// geometry.
+constexpr int N_STEP_VARIANTS = 7;
 constexpr int FIRST_TMA_VARIANT = 3;
 int step_variant_rows(int v);
 // Variants available for a kernel kind (0 forward, 1 adjoint, 2 Born).

@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(32 * (TZ / R), 1) born_step_kernel(BornArgs A,
 // Variants (rows per thread) and their launchers.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kRows[N_STEP_VARIANTS] = {2, 4, 8, 4, 8, 16};
+constexpr int kRows[N_STEP_VARIANTS] = {2, 4, 8, 4, 8, 16, 8};  // the Born kernel's variant 5 has R = 4
 
 constexpr size_t fwd_smem() { return 2 * sizeof(FwdStage); }
 constexpr size_t adj_smem() { return 2 * sizeof(AdjStage) + sizeof(CTile); }
@@ -394,7 +394,7 @@ int occ_of(int kind, int store_a) {
 
 int step_variant_rows(int v) { return kRows[v]; }
 
-int step_variants(int kind) { return kind == 0 ? N_STEP_VARIANTS : N_STEP_VARIANTS - 1; }
+int step_variants(int kind) { return kind == 0 ? 6 : kind == 1 ? 5 : 7; }
 
 int step_occupancy(int kind, int variant, int store_a) {
     if (variant >= FIRST_TMA_VARIANT) return tma_occupancy(kind, variant);

@@ -233,7 +233,10 @@ struct TmaBornStage {
 };
 constexpr unsigned kBornStageBytes = 2 * sizeof(STile) + 4 * sizeof(CTile);
 static_assert(sizeof(TmaBornStage) == kBornStageBytes, "stage layout");
-constexpr size_t kBornSmem = 2 * sizeof(TmaBornStage) + sizeof(PipeTail);
+// NS stages (2: double-buffered, one CTA per SM; 1: two CTAs per SM).
+template <int NS>
+constexpr size_t born_smem() { return NS * sizeof(TmaBornStage) + sizeof(PipeTail); }
+constexpr size_t kBornSmem = born_smem<2>();
 
 template <int R, bool FULL>
 __device__ __forceinline__ void born_rows(const BornArgs &A, const TmaBornStage &S, const TileInfo &T, int lxp,
@@ -290,16 +293,16 @@ __device__ __forceinline__ void born_rows(const BornArgs &A, const TmaBornStage 
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(32 * (TZ / R), 1)
+template <int R, int NS>
+__global__ void __launch_bounds__(32 * (TZ / R), NS == 1 ? 2 : 1)
     born_tma_kernel(BornArgs A, const __grid_constant__ TileMaps M, int ntiles) {
     constexpr int NT = 32 * (TZ / R);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TmaBornStage *st = reinterpret_cast<TmaBornStage *>(smem_raw);
-    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + 2 * sizeof(TmaBornStage));
+    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + NS * sizeof(TmaBornStage));
     const int lxp = 2 * threadIdx.x;
     const int lz0 = threadIdx.y * R;
-    run_tiles<2>(
+    run_tiles<NS>(
         A.c, kBornStageBytes, ntiles, st, tail,
         [&](TmaBornStage &S, unsigned bar, int4 co, int mc) {
             tma_load_3d(smem_u32(&S.u), &M.m[0], co.z - HALO, co.y - HALO, co.x, bar);
@@ -376,7 +379,7 @@ int occ_r(int kind) {
     }
     if constexpr (R <= 8) {  // the adjoint and Born kernels have no R = 16 variant
         if (kind == 1) return occupancy((const void *)adj_tma_kernel<R>, nt, kAdjSmem);
-        return occupancy((const void *)born_tma_kernel<R>, nt, kBornSmem);
+        return occupancy((const void *)born_tma_kernel<R, 2>, nt, kBornSmem);
     }
     return 1;
 }
@@ -400,8 +403,12 @@ void launch_adj_step_tma(const AdjArgs &a, int ntiles, int variant, int grid, co
 
 void launch_born_step_tma(const BornArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s) {
     switch (variant) {
-    case FIRST_TMA_VARIANT: launch_pdl(born_tma_kernel<4>, grid, 4, kBornSmem, s, a, maps, ntiles); break;
-    default: launch_pdl(born_tma_kernel<8>, grid, 8, kBornSmem, s, a, maps, ntiles); break;
+    case FIRST_TMA_VARIANT: launch_pdl(born_tma_kernel<4, 2>, grid, 4, kBornSmem, s, a, maps, ntiles); break;
+    case FIRST_TMA_VARIANT + 1: launch_pdl(born_tma_kernel<8, 2>, grid, 8, kBornSmem, s, a, maps, ntiles); break;
+    case FIRST_TMA_VARIANT + 2:
+        launch_pdl(born_tma_kernel<4, 1>, grid, 4, born_smem<1>(), s, a, maps, ntiles);
+        break;
+    default: launch_pdl(born_tma_kernel<8, 1>, grid, 8, born_smem<1>(), s, a, maps, ntiles); break;
     }
 }
 
@@ -410,6 +417,10 @@ void launch_wait_timeout_selftest(unsigned *tflag, cudaStream_t s) {
 }
 
 int tma_occupancy(int kind, int variant) {
+    if (kind == 2 && variant == FIRST_TMA_VARIANT + 2)
+        return occupancy((const void *)born_tma_kernel<4, 1>, 32 * (TZ / 4), born_smem<1>());
+    if (kind == 2 && variant == FIRST_TMA_VARIANT + 3)
+        return occupancy((const void *)born_tma_kernel<8, 1>, 32 * (TZ / 8), born_smem<1>());
     switch (variant) {
     case FIRST_TMA_VARIANT: return occ_r<4>(kind);
     case FIRST_TMA_VARIANT + 1: return occ_r<8>(kind);

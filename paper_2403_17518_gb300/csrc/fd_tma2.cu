@@ -465,6 +465,11 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
 // CTA per tile; receivers sharing a cell summed in order, as in
 // build_injection).
 __global__ void adj_inject_kernel(AdjArgs A, const int *__restrict__ rtiles) {
+    // Launched as a programmatic dependent: it may start before the step
+    // kernel that writes D_nu has finished, so it waits for it here, and lets
+    // the next step kernel start its prologue at once.
+    griddep_wait();
+    griddep_launch_dependents();
     const TileInfo &T = A.c.infos[rtiles[blockIdx.x]];
     const float *rk = A.r + T.doff + (long long)(A.k - 1) * T.nrec;
     for (int e = T.rec_begin + threadIdx.x; e < T.rec_end; e += blockDim.x)
@@ -516,7 +521,16 @@ void launch_adj_pair(const AdjArgs &a, int ntiles, const TileMaps &maps, cudaStr
 
 void launch_adj_inject(const AdjArgs &a, const int *rtiles, int nrtiles, cudaStream_t s) {
     if (nrtiles <= 0) return;
-    adj_inject_kernel<<<nrtiles, 128, 0, s>>>(a, rtiles);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nrtiles);
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, adj_inject_kernel, a, rtiles);
 }
 
 int fwd_pair_occupancy() {

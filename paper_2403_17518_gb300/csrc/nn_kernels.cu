@@ -494,23 +494,35 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, 
 
 // Bias gradient: db[c] = sum over pixels of g[p][c] (bf16 in, fixed order:
 // per-block partial sums then a second pass).
+// Column sums of g over a block of rows, four independent accumulators
+// (rows p, p+1, p+2, p+3 of each group of four) combined in a fixed order.
 __global__ void bias_grad_partial_kernel(const __nv_bfloat16 *__restrict__ g, int stride, int C, long long P,
                                          int rows_per_block, float *__restrict__ part) {
     const int c = blockIdx.y * blockDim.x + threadIdx.x;
     if (c >= C) return;
     const long long p0 = (long long)blockIdx.x * rows_per_block;
     const long long p1 = p0 + rows_per_block < P ? p0 + rows_per_block : P;
-    float s = 0.f;
-    for (long long p = p0; p < p1; p++) s += __bfloat162float(g[p * stride + c]);
-    part[(long long)blockIdx.x * C + c] = s;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    long long p = p0;
+    for (; p + 3 < p1; p += 4) {
+        s0 += __bfloat162float(g[p * stride + c]);
+        s1 += __bfloat162float(g[(p + 1) * stride + c]);
+        s2 += __bfloat162float(g[(p + 2) * stride + c]);
+        s3 += __bfloat162float(g[(p + 3) * stride + c]);
+    }
+    for (; p < p1; p++) s0 += __bfloat162float(g[p * stride + c]);
+    part[(long long)blockIdx.x * C + c] = (s0 + s1) + (s2 + s3);
 }
 
+// One warp per channel: lane l sums the partials l, l+32, ..., then a
+// shuffle tree (fixed order, so deterministic).
 __global__ void bias_grad_final_kernel(const float *__restrict__ part, int nblk, int C, float *__restrict__ db) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (c >= C) return;
     float s = 0.f;
-    for (int b = 0; b < nblk; b++) s += part[(long long)b * C + c];
-    db[c] = s;
+    for (int b = lane; b < nblk; b += 32) s += part[(long long)b * C + c];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) db[c] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1271,9 +1283,10 @@ void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, fl
     int rows = (int)((P + max_blocks - 1) / max_blocks);
     if (rows < 64) rows = 64;
     const int nblk = (int)((P + rows - 1) / rows);
-    dim3 grid(nblk, (C + 127) / 128);
-    bias_grad_partial_kernel<<<grid, 128, 0, s>>>(g, stride, C, P, rows, part);
-    bias_grad_final_kernel<<<(C + 127) / 128, 128, 0, s>>>(part, nblk, C, db);
+    const int bd = C < 128 ? (C + 31) / 32 * 32 : 128;
+    dim3 grid(nblk, (C + bd - 1) / bd);
+    bias_grad_partial_kernel<<<grid, bd, 0, s>>>(g, stride, C, P, rows, part);
+    bias_grad_final_kernel<<<(C * 32 + 255) / 256, 256, 0, s>>>(part, nblk, C, db);
 }
 
 void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H, int W, int C, __nv_bfloat16 *y,

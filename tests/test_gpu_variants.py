@@ -22,7 +22,7 @@ from gpu_helpers import f32, f32_geom, gpu_ctx, rel_l2, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-VARIANTS = list(range(6))
+VARIANTS = list(range(7))  # 5 and 6: single-stage Born kernels (the others fall back to their last)
 TMA_VARIANTS = [3, 4, 5]
 
 
@@ -86,8 +86,8 @@ def reference_variant():
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_variants_agree_bitwise(variant, reference_variant, monkeypatch):
     out, used = _run(variant, monkeypatch)
-    assert used[0] == variant and used[1] == variant
-    assert used[2] == used[3] == min(variant, 4)
+    assert used[0] == used[1] == min(variant, 5)
+    assert used[2] == min(variant, 4) and used[3] == variant
     for k in KEYS:
         np.testing.assert_array_equal(out[k], reference_variant[k], err_msg=k)
     assert out["J"] == reference_variant["J"]
@@ -104,6 +104,31 @@ def test_two_step_kernel_agrees_bitwise(variant, reference_variant, monkeypatch)
     for k in KEYS:
         np.testing.assert_array_equal(out[k], reference_variant[k], err_msg=k)
     assert out["J"] == reference_variant["J"]
+
+
+def test_autotuned_kernels_and_depth_agree_bitwise(reference_variant, monkeypatch):
+    """Nothing pinned: the autotuner picks the variants and the time-blocking
+    depth of the forward and adjoint sweeps; the results are the same bits."""
+    import torch
+
+    monkeypatch.delenv("DHFWI_STEP_VARIANT", raising=False)
+    monkeypatch.delenv("DHFWI_TIME_BLOCK", raising=False)
+    c = CASE
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom)
+    v, v0 = to_dev(f32(c.v_true)), to_dev(f32(c.v_init))
+    d = ctx.model_shots(v, geom)
+    ds = torch.empty(geom.n_data, dtype=torch.float32, device="cuda")
+    J, g = ctx.fwi_gradient(v0, geom, 0.5 * d, d_syn=ds)
+    st = ctx.stats()
+    assert all(x in (1, 2) for x in st["time_block"])
+    m = ctx.rtm_mig(v0, geom, 0.5 * d)
+    b = ctx.born_demig(v0, geom, to_dev(DV))
+    out = {"d": to_host(d), "ds": to_host(ds), "g": to_host(g), "m": to_host(m), "b": to_host(b)}
+    ctx.close()
+    for k in KEYS:
+        np.testing.assert_array_equal(out[k], reference_variant[k], err_msg=k)
+    assert J == reference_variant["J"]
 
 
 def history_cap_mb(case, segs, K=50):
