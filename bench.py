@@ -76,6 +76,10 @@ def parse():
                         "(born_demig) alone; nn: the network's training and apply alone on seeded smooth images "
                         "of the workload's size; used for profiling")
     p.add_argument("--nn-epochs", type=int, default=20)
+    p.add_argument("--net", default="workload", choices=["workload", "paper"],
+                   help="with --only nn: workload = base 32 on 128 x 128 patches (the benchmark's network); "
+                        "paper = the paper's network (base 128 doubling to 2048, four levels) trained on the "
+                        "full image (one padded sample per step); --nn-epochs is then the number of steps")
     p.add_argument("--shots", type=int, default=0,
                    help="with --only fwd/grad/born: the first SHOTS shots of the batch (small profiling captures)")
     p.add_argument("--nt", type=int, default=0,
@@ -108,6 +112,8 @@ def algorithmic_cells(case) -> int:
 
 
 NET = dict(base_channels=32, levels=4, patch=128, stride=64, batch=32, lr=1e-3, seed=29, mute_rows=5, warmup_frac=0.1)
+NET_PAPER = dict(base_channels=128, levels=4, patch=0, stride=1, batch=1, lr=1e-4, seed=29, mute_rows=5,
+                 warmup_frac=0.1)
 WARM_EPOCHS, COLD_EPOCHS = 20, 200
 
 
@@ -380,27 +386,37 @@ def run_network_only(args, dist, case):
     x = torch.tensor(synth.smooth_random_field(case.nz, case.nx, 1, 3.0), dtype=torch.float32, device=dev)
     y = torch.tensor(synth.smooth_random_field(case.nz, case.nx, 2, 1.5), dtype=torch.float32, device=dev)
     out = torch.empty_like(y)
-    ctx.deblur_train(x, y, warm_start=False, epochs=1, **NET)
+    net = NET_PAPER if args.net == "paper" else NET
+    ctx.deblur_train(x, y, warm_start=False, epochs=1, **net)
     for _ in range(args.warmup):
-        ctx.deblur_train(x, y, warm_start=True, epochs=args.nn_epochs, **NET)
+        ctx.deblur_train(x, y, warm_start=True, epochs=args.nn_epochs, **net)
         ctx.deblur_apply(y, out=out)
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record()
     for _ in range(args.steps):
-        ctx.deblur_train(x, y, warm_start=True, epochs=args.nn_epochs, **NET)
+        ctx.deblur_train(x, y, warm_start=True, epochs=args.nn_epochs, **net)
     e1.record()
     for _ in range(args.steps):
         ctx.deblur_apply(y, out=out)
     e2.record()
     torch.cuda.synchronize()
-    npatch = n_patches(case.nz, NET["patch"], NET["stride"]) * n_patches(case.nx, NET["patch"], NET["stride"])
-    f_train = args.nn_epochs * npatch * 3 * conv_flops(NET["base_channels"], NET["levels"], NET["patch"], NET["patch"])
-    f_apply = conv_flops(NET["base_channels"], NET["levels"], case.nz, case.nx)
+    mult = 1 << net["levels"]
+    Hp, Wp = -(-case.nz // mult) * mult, -(-case.nx // mult) * mult
+    if args.net == "paper":
+        npatch = 1
+        f_train = args.nn_epochs * 3 * conv_flops(net["base_channels"], net["levels"], Hp, Wp)
+    else:
+        npatch = n_patches(case.nz, net["patch"], net["stride"]) * n_patches(case.nx, net["patch"], net["stride"])
+        f_train = args.nn_epochs * npatch * 3 * conv_flops(net["base_channels"], net["levels"], net["patch"],
+                                                           net["patch"])
+    f_apply = conv_flops(net["base_channels"], net["levels"], Hp, Wp)
     t_train = e0.elapsed_time(e1) / max(args.steps, 1)
     t_apply = e1.elapsed_time(e2) / max(args.steps, 1)
     if dist.rank == 0:
-        print(json.dumps({"only": "nn", "epochs": args.nn_epochs, "patches": npatch,
+        print(json.dumps({"only": "nn", "net": args.net, "base_channels": net["base_channels"],
+                          "full_image": net["patch"] == 0, "params": ctx.net_size(),
+                          "epochs": args.nn_epochs, "patches": npatch,
                           "train_ms": round(t_train, 2), "train_tflops": round(f_train / t_train / 1e9, 2),
                           "apply_ms": round(t_apply, 2), "apply_tflops": round(f_apply / t_apply / 1e9, 2)}),
               flush=True)

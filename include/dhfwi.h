@@ -288,10 +288,14 @@ const char *model_shots_static_error(void);
 typedef struct {
     int base_channels;  /* channels of the input block (multiple of 8); 32 here, 128 in the paper */
     int levels;         /* down/up blocks (4 in the paper) */
-    int patch;          /* square patch size (multiple of 2^levels) */
+    int patch;          /* square patch size (multiple of 2^levels); 0: full-image training, the
+                           paper's choice (Section 2.4): the whole image, zero-padded at the bottom
+                           and right to a multiple of 2^levels, is the one sample of every step
+                           (batch 1; stride and batch are ignored; the loss is the mean over the
+                           padded frame) */
     int stride;         /* patch stride; the last patch of each axis touches the edge */
     int batch;          /* patches per optimiser step */
-    int epochs;         /* passes over the patches (<= 4096) */
+    int epochs;         /* passes over the patches (<= 4096); optimiser steps when patch is 0 */
     float lr;           /* initial learning rate of the cosine schedule */
     float beta1, beta2, eps;     /* Adam */
     unsigned long long seed;     /* initialisation (cold start) and shuffling */

@@ -388,6 +388,9 @@ def normalize(img, mute_rows: int = 0):
 
 @dataclasses.dataclass
 class TrainCfg:
+    # patch 0: full-image training (the paper's choice, Section 2.4): the
+    # whole image, zero-padded at the bottom and right to a multiple of
+    # 2**levels, is the one sample of every step (batch 1, epochs = steps).
     patch: int = 128
     stride: int = 64
     batch: int = 32
@@ -408,8 +411,11 @@ def train(flat, x_img, y_img, spec: UNetSpec, cfg: TrainCfg, round_bf16: bool = 
     float64, per-epoch mean batch loss list)."""
     xn, _ = normalize(x_img, cfg.mute_rows)
     yn, _ = normalize(y_img, cfg.mute_rows)
-    X = extract_patches(xn, cfg.patch, cfg.stride)[:, None]
-    Y = extract_patches(yn, cfg.patch, cfg.stride)[:, None]
+    if cfg.patch == 0:
+        X, Y = pad_to_levels(xn, spec)[None, None], pad_to_levels(yn, spec)[None, None]
+    else:
+        X = extract_patches(xn, cfg.patch, cfg.stride)[:, None]
+        Y = extract_patches(yn, cfg.patch, cfg.stride)[:, None]
     n = X.shape[0]
     nb = -(-n // cfg.batch)
     T = cfg.epochs * nb
@@ -433,15 +439,20 @@ def train(flat, x_img, y_img, spec: UNetSpec, cfg: TrainCfg, round_bf16: bool = 
     return theta, hist
 
 
+def pad_to_levels(img, spec: UNetSpec):
+    """img zero-padded at the bottom and right to multiples of 2**levels."""
+    H, W = img.shape
+    mult = 1 << spec.levels
+    out = np.zeros((-(-H // mult) * mult, -(-W // mult) * mult))
+    out[:H, :W] = img
+    return out
+
+
 def apply(flat, img, spec: UNetSpec, round_bf16: bool = True, mute_rows: int = 0):
     """net(img / max|img|) * max|img| on the full image (first mute_rows rows
     taken as 0), zero-padded at the bottom/right to a multiple of 2**levels and
     cropped back."""
     xn, m = normalize(img, mute_rows)
     H, W = xn.shape
-    mult = 1 << spec.levels
-    Hp, Wp = -(-H // mult) * mult, -(-W // mult) * mult
-    xp = np.zeros((1, 1, Hp, Wp))
-    xp[0, 0, :H, :W] = xn
-    out, _ = forward(flat, xp, spec, round_bf16)
+    out, _ = forward(flat, pad_to_levels(xn, spec)[None, None], spec, round_bf16)
     return out[0, 0, :H, :W] * m

@@ -1345,7 +1345,7 @@ void launch_conv1x1_bwd(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long lon
     conv1x1_wgrad_partial_kernel<<<nblk, dim3(cx, streams), sizeof(float) * cx * streams, s>>>(g, a, P, C, rows,
                                                                                                  part);
     // dw_db[0..C) = dW, dw_db[C] = db: reuse the bias-final reduction over C+1 columns.
-    bias_grad_final_kernel<<<(C + 1 + 127) / 128, 128, 0, s>>>(part, nblk, C + 1, dw_db);
+    bias_grad_final_kernel<<<((C + 1) * 32 + 255) / 256, 256, 0, s>>>(part, nblk, C + 1, dw_db);
 }
 void launch_adam(float *theta, const float *grad, float *m, float *v, long long n, float lr, float b1, float b2,
                  float eps, int t, __nv_bfloat16 *shadow, cudaStream_t s) {

@@ -862,12 +862,17 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
     if (!ctx) return DHFWI_ERR_ARG;
     ctx_begin(ctx);
     if (!cfg || !x_dev || !y_dev) return fail(ctx, DHFWI_ERR_ARG, "NULL argument");
-    if (cfg->patch < 1 || cfg->stride < 1 || cfg->batch < 1 || cfg->epochs < 1 || !(cfg->lr > 0.f) ||
-        cfg->epochs > 4096)
+    // patch == 0: full-image training (one sample: the whole image padded to
+    // a multiple of 2^levels; batch and stride are not used).
+    const bool full = cfg->patch == 0;
+    if (cfg->patch < 0 || (!full && (cfg->stride < 1 || cfg->batch < 1)) || cfg->epochs < 1 || !(cfg->lr > 0.f) ||
+        cfg->epochs > 4096 || nz < 1 || nx < 1)
         return fail(ctx, DHFWI_ERR_ARG, "bad training configuration");
-    if (nz < cfg->patch || nx < cfg->patch) return fail(ctx, DHFWI_ERR_ARG, "image smaller than the patch");
-    if ((long long)cfg->batch * cfg->patch * cfg->patch >= (1LL << 31))
+    if (!full && (nz < cfg->patch || nx < cfg->patch)) return fail(ctx, DHFWI_ERR_ARG, "image smaller than the patch");
+    if (!full && (long long)cfg->batch * cfg->patch * cfg->patch >= (1LL << 31))
         return fail(ctx, DHFWI_ERR_ARG, "batch * patch^2 must be below 2^31");
+    if (full && ((long long)nz + 64) * ((long long)nx + 64) >= (1LL << 31))
+        return fail(ctx, DHFWI_ERR_ARG, "image too large for full-image training");
     if (cfg->mute_rows < 0 || cfg->mute_rows >= nz) return fail(ctx, DHFWI_ERR_ARG, "mute_rows must be in [0, nz)");
     if (!(cfg->warmup_frac >= 0.f) || cfg->warmup_frac > 1.f)
         return fail(ctx, DHFWI_ERR_ARG, "warmup_frac must be in [0, 1]");
@@ -876,15 +881,20 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
     int rc = ensure_net(ctx, cfg->base_channels, cfg->levels);
     if (rc) return rc;
     NetState &N = *ctx_net(ctx);
-    if (!ilog_mult(cfg->patch, N.levels)) return fail(ctx, DHFWI_ERR_ARG, "patch must be a multiple of 2^levels");
+    if (!full && !ilog_mult(cfg->patch, N.levels))
+        return fail(ctx, DHFWI_ERR_ARG, "patch must be a multiple of 2^levels");
     N.launches = 0;
     if (!warm_start || !N.have_weights) {
         std::vector<float> h;
         init_host(N, cfg->seed, h);
         if ((rc = upload_params(ctx, N, h.data(), s))) return rc;
     }
-    const int p = cfg->patch;
-    const std::vector<int> oz = patch_origins(nz, p, cfg->stride), ox = patch_origins(nx, p, cfg->stride);
+    const int mult = 1 << N.levels;
+    const int Hp = (nz + mult - 1) / mult * mult, Wp = (nx + mult - 1) / mult * mult;
+    const int p = full ? 0 : cfg->patch;
+    const int sh = full ? Hp : p, sw = full ? Wp : p;  // sample size
+    const std::vector<int> oz = full ? std::vector<int>{0} : patch_origins(nz, p, cfg->stride),
+                           ox = full ? std::vector<int>{0} : patch_origins(nx, p, cfg->stride);
     const int npatch = (int)(oz.size() * ox.size());
     std::vector<int> hoz(npatch), hox(npatch);
     for (size_t a = 0; a < oz.size(); a++)
@@ -892,8 +902,8 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
             hoz[a * ox.size() + b] = oz[a];
             hox[a * ox.size() + b] = ox[b];
         }
-    const int B = std::min(cfg->batch, npatch);
-    if ((rc = layout(ctx, N, B, p, p))) return rc;
+    const int B = full ? 1 : std::min(cfg->batch, npatch);
+    if ((rc = layout(ctx, N, B, sh, sw))) return rc;
     if (N.oz_cap < (size_t)npatch) {
         dev_free(N.oz);
         dev_free(N.ox);
@@ -934,17 +944,24 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
     const long long T = (long long)cfg->epochs * nb;
     const long long warm_n = (long long)std::ceil((double)cfg->warmup_frac * (double)T);
     long long t = 0;
+    if (full) {  // the one sample, normalised and padded once
+        launch_pad_image(x_dev, nz, nx, Hp, Wp, N.scales, N.mute_rows, N.V.xf, s);
+        launch_pad_image(y_dev, nz, nx, Hp, Wp, N.scales + 2, N.mute_rows, N.V.yf, s);
+        N.launches += 2;
+    }
     for (int e = 0; e < cfg->epochs; e++) {
         for (int b = 0; b < nb; b++) {
             const int cnt = std::min(B, npatch - b * B);
-            const int *sel = N.perm + (size_t)e * npatch + (size_t)b * B;
-            launch_gather_patches(x_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales, N.mute_rows, N.V.xf, s);
-            launch_gather_patches(y_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales + 2, N.mute_rows, N.V.yf, s);
-            N.launches += 2;
-            forward(N, cnt, p, p, s);
-            loss(N, cnt, p, p, s);
-            launch_loss_accum(N.mse_part, MSE_BLOCKS, (double)cnt / ((double)cnt * p * p), N.loss_acc + e, s);
-            backward(N, cnt, p, p, s);
+            if (!full) {
+                const int *sel = N.perm + (size_t)e * npatch + (size_t)b * B;
+                launch_gather_patches(x_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales, N.mute_rows, N.V.xf, s);
+                launch_gather_patches(y_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales + 2, N.mute_rows, N.V.yf, s);
+                N.launches += 2;
+            }
+            forward(N, cnt, sh, sw, s);
+            loss(N, cnt, sh, sw, s);
+            launch_loss_accum(N.mse_part, MSE_BLOCKS, (double)cnt / ((double)cnt * sh * sw), N.loss_acc + e, s);
+            backward(N, cnt, sh, sw, s);
             double lr = 0.5 * cfg->lr * (1.0 + std::cos(M_PI * (double)t / (double)T));
             if (warm_n > 0 && t < warm_n) lr *= (double)(t + 1) / (double)warm_n;
             N.adam_t++;

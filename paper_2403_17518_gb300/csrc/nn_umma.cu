@@ -413,6 +413,106 @@ constexpr size_t conv3_tma_smem() {
     return (size_t)ST * (128 * BK * 2 + BN * BK * 2) + 2048;  // + alignment slack, barriers, TMEM address
 }
 
+// Epilogue of one 128 x BN output tile of the TMA-fed conv kernels: warp q
+// of the four epilogue warps reads TMEM lanes 32 q .. 32 q + 31 (tile rows)
+// of the accumulator whose column base is `tmem` (nk == 0: an empty k-range,
+// zeros), and writes the rows with the epilogue EPI, or raw partial sums to
+// P.part[split] when k is split.
+template <int BN, int EPI>
+__device__ __forceinline__ void conv_tile_epilogue(const FpropArgs &P, const ConvTile &G, unsigned tmem, int q, int lane,
+                                                   int i0, int h0, int w0, int n0, int nk, int split) {
+    const int r = q * 32 + lane;  // tile row = TMEM lane
+    const int per_img = G.BW * G.BH;
+    const int img = i0 + r / per_img, rem = r % per_img;
+    const int ho = h0 + rem / G.BW, wo = w0 + rem % G.BW;
+    const bool valid = img < G.nimg && ho < P.Ho && wo < P.Wo;
+    const long long m = ((long long)img * P.Ho + ho) * P.Wo + wo;
+    const unsigned trow = tmem + ((unsigned)(q * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        if (n0 + c0 >= P.N) break;  // uniform across the warp
+        float v[16];
+        if (nk > 0) tmem_ld16(trow + c0, v);
+        else
+#pragma unroll
+            for (int e = 0; e < 16; e++) v[e] = 0.f;
+        if (!valid) continue;
+        const int nb = n0 + c0;
+        const bool full16 = nb + 16 <= P.N;
+        if (P.part) {  // split-k: raw partial sums
+            float *out = P.part + (long long)split * P.M * P.N + m * P.N + nb;
+            if (full16 && (P.N & 3) == 0) {
+#pragma unroll
+                for (int e = 0; e < 16; e += 4)
+                    *reinterpret_cast<float4 *>(out + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; e++)
+                    if (nb + e < P.N) out[e] = v[e];
+            }
+            continue;
+        }
+        if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
+            __nv_bfloat16 *o = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
+            __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                float x = v[e] + (nb + e < P.N ? P.bias[nb + e] : 0.f);
+                if (EPI == EPI_BF16_LEAKY) x = x > 0.f ? x : P.slope * x;
+                h[e] = __float2bfloat16_rn(x);
+            }
+            if (full16 && ((P.dst_stride | P.dst_off) & 7) == 0) {
+                reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
+                reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; e++)
+                    if (nb + e < P.N) o[e] = h[e];
+            }
+        } else if (EPI == EPI_BF16_LEAKYBWD) {
+            const __nv_bfloat16 *ap = P.act + m * P.act_stride + P.act_off + nb;
+            __nv_bfloat16 *o = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
+            if (full16 && (((uintptr_t)ap | (uintptr_t)o) & 15) == 0) {  // 16-byte loads and stores
+                __align__(16) __nv_bfloat16 av[16], h[16];
+                reinterpret_cast<uint4 *>(av)[0] = reinterpret_cast<const uint4 *>(ap)[0];
+                reinterpret_cast<uint4 *>(av)[1] = reinterpret_cast<const uint4 *>(ap)[1];
+#pragma unroll
+                for (int e = 0; e < 16; e++)
+                    h[e] = __float2bfloat16_rn(v[e] * (__bfloat162float(av[e]) > 0.f ? 1.0f : P.slope));
+                reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
+                reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; e++)
+                    if (nb + e < P.N) {
+                        const float av = __bfloat162float(ap[e]);
+                        o[e] = __float2bfloat16_rn(v[e] * (av > 0.f ? 1.0f : P.slope));
+                    }
+            }
+        } else {  // EPI_F32 / EPI_F32_ADD
+            float *o = P.dst_f32 + m * P.dst_stride + P.dst_off + nb;
+            if (full16 && ((uintptr_t)o & 15) == 0) {  // 16-byte loads and stores
+#pragma unroll
+                for (int e = 0; e < 16; e += 4) {
+                    float4 x = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                    if (EPI == EPI_F32_ADD) {
+                        const float4 y = *reinterpret_cast<const float4 *>(o + e);
+                        x.x += y.x;
+                        x.y += y.y;
+                        x.z += y.z;
+                        x.w += y.w;
+                    }
+                    *reinterpret_cast<float4 *>(o + e) = x;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; e++)
+                    if (nb + e < P.N) o[e] = (EPI == EPI_F32_ADD ? o[e] : 0.f) + v[e];
+            }
+        }
+    }
+}
+
 template <int BN, int BK, int ST, int EPI>
 __global__ void __launch_bounds__(TMA_THREADS, 1)
     conv3_tma_umma_kernel(FpropArgs P, const __grid_constant__ CUtensorMap mapA,
@@ -516,96 +616,197 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         if (!good) {
             if (lane == 0 && P.err) atomicExch(P.err, 1u);
         } else {
-            const int r = q * 32 + lane;  // tile row = TMEM lane
-            const int per_img = G.BW * G.BH;
-            const int img = i0 + r / per_img, rem = r % per_img;
-            const int ho = h0 + rem / G.BW, wo = w0 + rem % G.BW;
-            const bool valid = img < G.nimg && ho < P.Ho && wo < P.Wo;
-            const long long m = ((long long)img * P.Ho + ho) * P.Wo + wo;
-            const unsigned trow = tmem + ((unsigned)(q * 32) << 16);
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                if (n0 + c0 >= P.N) break;  // uniform across the warp
-                float v[16];
-                if (nk > 0) tmem_ld16(trow + c0, v);
-                else
-#pragma unroll
-                    for (int e = 0; e < 16; e++) v[e] = 0.f;
-                if (!valid) continue;
-                const int nb = n0 + c0;
-                const bool full16 = nb + 16 <= P.N;
-                if (P.part) {  // split-k: raw partial sums
-                    float *out = P.part + (long long)blockIdx.z * P.M * P.N + m * P.N + nb;
-                    if (full16 && (P.N & 3) == 0) {
-#pragma unroll
-                        for (int e = 0; e < 16; e += 4)
-                            *reinterpret_cast<float4 *>(out + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            conv_tile_epilogue<BN, EPI>(P, G, tmem, q, lane, i0, h0, w0, n0, nk, blockIdx.z);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of conv3_tma_umma_kernel (the default): grid = the SMs
+// (times the CTAs that fit), each CTA walks the work items (m-tile, n-tile,
+// k-split) with a stride of gridDim.x.  The stage ring runs on across items
+// (one k-tile counter), and the accumulator is double-buffered in TMEM
+// (2 x BN columns) so that the epilogue warps write item i while the MMAs of
+// item i+1 run.  Hand-off on mbarriers: full[s] / empty[s] for the stages as
+// before, tfull[b] (tcgen05.commit: accumulator b is final) and tempty[b]
+// (arrived by each of the four epilogue warps once it has read accumulator
+// b).  Every wait is bounded (~1 s); a role that runs out sets *err and the
+// CTA's abort word, and every role leaves its loop at the next item; the
+// producer still waits (bounded) for its loads in flight, and TMEM is freed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_arrive1(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_init_n(unsigned bar, unsigned n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(n) : "memory");
+}
+
+template <int BN, int BK, int ST, int EPI>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    conv3_tma_persistent_kernel(FpropArgs P, const __grid_constant__ CUtensorMap mapA,
+                                const __grid_constant__ CUtensorMap mapB, ConvTile G, int mt, int ntn, int splits) {
+    constexpr bool SW128 = BK == 64;
+    constexpr unsigned A_CH = 128 * 16, B_CH = BN * 16;
+    constexpr unsigned A_BYTES = A_CH * (BK / 8), B_BYTES = B_CH * (BK / 8), STAGE = A_BYTES + B_BYTES;
+    constexpr unsigned TMEM_COLS = 2 * BN;  // two accumulators; a power of two >= 64
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    const unsigned sbase = (smem_u32(smraw) + 1023u) & ~1023u;
+    unsigned char *tail = smraw + (sbase - smem_u32(smraw)) + ST * STAGE;
+    const unsigned full0 = smem_u32(tail), empty0 = full0 + 8 * ST, tfull0 = empty0 + 8 * ST, tempty0 = tfull0 + 16;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(tail + 16 * ST + 32);
+    volatile unsigned *abort_word = reinterpret_cast<volatile unsigned *>(tail + 16 * ST + 36);
+    const unsigned drain = full0 + 16 * ST + 40;  // the MMA lane's last commit
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int items = mt * ntn * splits;
+    const int per = (G.nk_all + splits - 1) / splits;
+    // Item -> (m-tile, n-tile, split): n-tiles of one m-tile are adjacent (the
+    // source tile is reused from L2), splits outermost.
+    auto decode = [&](int item, int &i0, int &h0, int &w0, int &n0, int &kt0, int &nk, int &z) {
+        const int n = item % ntn;
+        int t = item / ntn;
+        const int m = t % mt;
+        z = t / mt;
+        t = m;
+        w0 = (t % G.tw) * G.BW;
+        t /= G.tw;
+        h0 = (t % G.th) * G.BH;
+        i0 = (t / G.th) * G.BI;
+        n0 = n * BN;
+        kt0 = z * per;
+        nk = max(0, min(G.nk_all, kt0 + per) - kt0);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < ST; s++) {
+            mbar_init1(full0 + 8 * s);
+            mbar_init1(empty0 + 8 * s);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init1(tfull0 + 8 * b);
+            mbar_init_n(tempty0 + 8 * b, 4);
+        }
+        mbar_init1(drain);
+        *abort_word = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+    auto fail = [&]() {
+        *abort_word = 1u;
+        if (P.err) atomicExch(P.err, 1u);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int g = 0;  // k-tiles issued by this CTA
+            for (int item = blockIdx.x; item < items && !*abort_word; item += gridDim.x) {
+                int i0, h0, w0, n0, kt0, nk, z;
+                decode(item, i0, h0, w0, n0, kt0, nk, z);
+                bool ok = true;
+                for (int kt = 0; kt < nk; kt++, g++) {
+                    const int s = g % ST;
+                    if (g >= ST && !mbar_wait(empty0 + 8 * s, ((g / ST) - 1) & 1u)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    const unsigned fb = full0 + 8 * s;
+                    mbar_expect_tx(fb, STAGE);
+                    const int k = (kt0 + kt) * BK;
+                    const int tap = k / P.C, c0 = k - tap * P.C;
+                    const int ws = w0 + P.dw[tap], hs = h0 + P.dh[tap];
+                    const unsigned sa = sbase + s * STAGE, sb = sa + A_BYTES;
+                    if constexpr (SW128) {
+                        tma_load_4d(sa, &mapA, c0, ws, hs, i0, fb);
+                        tma_load_2d(sb, &mapB, k, n0, fb);
                     } else {
 #pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (nb + e < P.N) out[e] = v[e];
+                        for (int ch = 0; ch < BK / 8; ch++)
+                            tma_load_4d(sa + ch * A_CH, &mapA, c0 + 8 * ch, ws, hs, i0, fb);
+#pragma unroll
+                        for (int ch = 0; ch < BK / 8; ch++) tma_load_2d(sb + ch * B_CH, &mapB, k + 8 * ch, n0, fb);
                     }
-                    continue;
                 }
-                if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
-                    __nv_bfloat16 *o = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
-                    __align__(16) __nv_bfloat16 h[16];
-#pragma unroll
-                    for (int e = 0; e < 16; e++) {
-                        float x = v[e] + (nb + e < P.N ? P.bias[nb + e] : 0.f);
-                        if (EPI == EPI_BF16_LEAKY) x = x > 0.f ? x : P.slope * x;
-                        h[e] = __float2bfloat16_rn(x);
-                    }
-                    if (full16 && ((P.dst_stride | P.dst_off) & 7) == 0) {
-                        reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
-                        reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (nb + e < P.N) o[e] = h[e];
-                    }
-                } else if (EPI == EPI_BF16_LEAKYBWD) {
-                    const __nv_bfloat16 *ap = P.act + m * P.act_stride + P.act_off + nb;
-                    __nv_bfloat16 *o = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
-                    if (full16 && (((uintptr_t)ap | (uintptr_t)o) & 15) == 0) {  // 16-byte loads and stores
-                        __align__(16) __nv_bfloat16 av[16], h[16];
-                        reinterpret_cast<uint4 *>(av)[0] = reinterpret_cast<const uint4 *>(ap)[0];
-                        reinterpret_cast<uint4 *>(av)[1] = reinterpret_cast<const uint4 *>(ap)[1];
-#pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            h[e] = __float2bfloat16_rn(v[e] * (__bfloat162float(av[e]) > 0.f ? 1.0f : P.slope));
-                        reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
-                        reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (nb + e < P.N) {
-                                const float av = __bfloat162float(ap[e]);
-                                o[e] = __float2bfloat16_rn(v[e] * (av > 0.f ? 1.0f : P.slope));
-                            }
-                    }
-                } else {  // EPI_F32 / EPI_F32_ADD
-                    float *o = P.dst_f32 + m * P.dst_stride + P.dst_off + nb;
-                    if (full16 && ((uintptr_t)o & 15) == 0) {  // 16-byte loads and stores
-#pragma unroll
-                        for (int e = 0; e < 16; e += 4) {
-                            float4 x = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-                            if (EPI == EPI_F32_ADD) {
-                                const float4 y = *reinterpret_cast<const float4 *>(o + e);
-                                x.x += y.x;
-                                x.y += y.y;
-                                x.z += y.z;
-                                x.w += y.w;
-                            }
-                            *reinterpret_cast<float4 *>(o + e) = x;
-                        }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (nb + e < P.N) o[e] = (EPI == EPI_F32_ADD ? o[e] : 0.f) + v[e];
-                    }
-                }
+                if (!ok) break;
             }
+            // Loads in flight land before the CTA leaves (bounded as well).
+            for (int q = max(0, g - ST); q < g; q++) mbar_wait(full0 + 8 * (q % ST), (q / ST) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16(UBM, BN);
+            int g = 0, b = 0, use[2] = {0, 0};
+            for (int item = blockIdx.x; item < items && !*abort_word; item += gridDim.x, b ^= 1) {
+                int i0, h0, w0, n0, kt0, nk, z;
+                decode(item, i0, h0, w0, n0, kt0, nk, z);
+                // Accumulator b is free once the epilogue has read its last use.
+                if (use[b] > 0 && !mbar_wait(tempty0 + 8 * b, (use[b] - 1) & 1u)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const unsigned acc = tmem + (unsigned)(b * BN);
+                bool ok = true;
+                for (int kt = 0; kt < nk; kt++, g++) {
+                    const int s = g % ST;
+                    if (!mbar_wait(full0 + 8 * s, (g / ST) & 1u)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned sa = sbase + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++) {
+                        const uint64_t da =
+                            SW128 ? smem_desc_sw128(sa + 32 * kk) : smem_desc(sa + 2 * kk * A_CH, A_CH, 128);
+                        const uint64_t db =
+                            SW128 ? smem_desc_sw128(sb + 32 * kk) : smem_desc(sb + 2 * kk * B_CH, B_CH, 128);
+                        mma_bf16(acc, da, db, IDESC, (kt > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(empty0 + 8 * s);
+                }
+                if (!ok) break;
+                mma_commit(tfull0 + 8 * b);  // arrives once the item's MMAs are complete
+                use[b]++;
+            }
+            // Every MMA issued is complete before TMEM is freed (after a
+            // failure too; bounded).
+            mma_commit(drain);
+            mbar_wait(drain, 0);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        int b = 0, use[2] = {0, 0};
+        for (int item = blockIdx.x; item < items; item += gridDim.x, b ^= 1) {
+            int i0, h0, w0, n0, kt0, nk, z;
+            decode(item, i0, h0, w0, n0, kt0, nk, z);
+            const bool good = mbar_wait(tfull0 + 8 * b, use[b] & 1u);
+            tc_fence_after();
+            if (!__all_sync(0xffffffffu, good) || *abort_word) {
+                if (lane == 0) fail();
+                break;
+            }
+            conv_tile_epilogue<BN, EPI>(P, G, tmem + (unsigned)(b * BN), q, lane, i0, h0, w0, n0, nk, z);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(tempty0 + 8 * b);
+            use[b]++;
         }
     }
     tc_fence_before();
@@ -692,8 +893,99 @@ bool conv3_tma_launch(const FpropArgs &a, const ConvTile &G0, cudaStream_t s) {
     return true;
 }
 
+// Stages of the persistent kernel: as many as fit in ~192 KB, at most 8.
+template <int BN, int BK>
+constexpr int persistent_stages() {
+    constexpr int stage = 128 * BK * 2 + BN * BK * 2;
+    return 196608 / stage > 8 ? 8 : 196608 / stage;
+}
+
+// Tensor maps of the conv3 GEMM's operands (see conv3_tma_launch).
+template <int BK>
+bool conv3_maps(const FpropArgs &a, const ConvTile &G, int BN, CUtensorMap *ma, CUtensorMap *mb) {
+    EncodeTiledFn enc = tma_encoder();
+    if (!enc) return false;
+    const cuuint64_t es = sizeof(__nv_bfloat16);
+    cuuint64_t dims[4] = {(cuuint64_t)a.C, (cuuint64_t)a.Ws, (cuuint64_t)a.Hs, (cuuint64_t)G.nimg};
+    cuuint64_t str[3] = {es * a.src_stride, es * a.src_stride * a.Ws, es * a.src_stride * a.Ws * a.Hs};
+    const cuuint32_t inner = BK == 64 ? 64 : 8;
+    const CUtensorMapSwizzle swz = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE;
+    cuuint32_t box[4] = {inner, (cuuint32_t)G.BW, (cuuint32_t)G.BH, (cuuint32_t)G.BI}, estr[4] = {1, 1, 1, 1};
+    if (enc(ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(a.src + a.src_off), dims, str, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t K = (cuuint64_t)a.ntaps * a.C;
+    cuuint64_t dimsb[2] = {K, (cuuint64_t)a.N};
+    cuuint64_t strb[1] = {es * K};
+    cuuint32_t boxb[2] = {inner, (cuuint32_t)BN}, estrb[2] = {1, 1};
+    return enc(mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)a.bt, dimsb, strb, boxb, estrb,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The persistent kernel's launch: same tiles and k-splits as
+// conv3_tma_launch, one CTA per SM (its TMEM holds both accumulators).
+template <int BN, int BK, int EPI>
+bool conv3_persistent_launch(const FpropArgs &a, const ConvTile &G0, cudaStream_t s) {
+    constexpr int ST = persistent_stages<BN, BK>();
+    const size_t sm = conv3_tma_smem<BN, BK, ST>();
+    ConvTile G = G0;
+    G.nk_all = a.ntaps * a.C / BK;
+    CUtensorMap ma, mb;
+    if (!conv3_maps<BK>(a, G, BN, &ma, &mb)) return false;
+    static bool attr = false;
+    static int nsm = 0;
+    if (!attr) {
+        cudaFuncSetAttribute(conv3_tma_persistent_kernel<BN, BK, ST, EPI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        attr = true;
+    }
+    const int mt = G.tw * G.th * ((G.nimg + G.BI - 1) / G.BI);
+    const int ntn = (a.N + BN - 1) / BN;
+    const int tiles = mt * ntn;
+    int splits = 1;
+    if (a.part && a.part_floats > 0) {
+        // Split k when the tiles fill less than one wave, keeping at least 4
+        // k-tiles per split and the partials within their buffer.
+        const int want = (nsm + tiles - 1) / tiles;
+        splits = std::min(want, G.nk_all / 4);
+        const long long cap = a.part_floats / ((long long)a.M * a.N);
+        if (splits > cap) splits = (int)cap;
+        if (splits < 2) splits = 1;
+    }
+    FpropArgs b = a;
+    if (splits == 1) b.part = nullptr;
+    const int items = tiles * splits;
+    const int grid = std::min(items, nsm);
+    conv3_tma_persistent_kernel<BN, BK, ST, EPI><<<grid, TMA_THREADS, sm, s>>>(b, ma, mb, G, mt, ntn, splits);
+    if (splits > 1) launch_fprop_reduce(b, EPI, splits, s);
+    return true;
+}
+
+// DHFWI_NN_CONV=tile: the one-tile-per-CTA kernel instead of the persistent one.
+bool conv3_persistent() {
+    const char *e = getenv("DHFWI_NN_CONV");
+    return !(e && strcmp(e, "tile") == 0);
+}
+
 template <int EPI>
 bool conv3_tma_dispatch(const FpropArgs &a, const ConvTile &G, cudaStream_t s) {
+    if (conv3_persistent()) {
+        if (a.C % 64 == 0) {
+            if (a.N <= 32) return conv3_persistent_launch<32, 64, EPI>(a, G, s);
+            if (a.N <= 64) return conv3_persistent_launch<64, 64, EPI>(a, G, s);
+            if (a.N <= 128) return conv3_persistent_launch<128, 64, EPI>(a, G, s);
+            return conv3_persistent_launch<256, 64, EPI>(a, G, s);
+        }
+        if (a.N <= 32) return conv3_persistent_launch<32, 32, EPI>(a, G, s);
+        if (a.N <= 64) return conv3_persistent_launch<64, 32, EPI>(a, G, s);
+        if (a.N <= 128) return conv3_persistent_launch<128, 32, EPI>(a, G, s);
+        return conv3_persistent_launch<256, 32, EPI>(a, G, s);
+    }
     if (a.C % 64 == 0) {
         if (a.N <= 64) return conv3_tma_launch<64, 64, EPI>(a, G, s);
         if (a.N <= 128) return conv3_tma_launch<128, 64, EPI>(a, G, s);
@@ -925,7 +1217,9 @@ int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
 // stride that is a multiple of 8 channels.  Returns false (nothing launched)
 // otherwise.
 bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
-    if (epi == EPI_BF16_CONVT || a.N < 64 || a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws ||
+    // The persistent kernel also takes the 32-channel outputs (BN = 32).
+    const int min_n = conv3_persistent() ? 32 : 64;
+    if (epi == EPI_BF16_CONVT || a.N < min_n || a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws ||
         a.C % 32 != 0 || a.C <= 0)
         return false;
     if (((a.src_stride | a.src_off) & 7) != 0) return false;

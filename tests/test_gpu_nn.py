@@ -166,6 +166,33 @@ def test_training_parity_base32():
     assert rel_l2(out, ref) <= 1e-2
 
 
+@pytest.mark.parametrize("base,levels,shape,epochs,lr", [(8, 2, (38, 70), 4, 1e-2), (128, 4, (30, 40), 2, 1e-4)],
+                         ids=["base8", "paper-size-base128"])
+def test_full_image_training_parity(base, levels, shape, epochs, lr):
+    """Full-image training (patch 0, the paper's choice): the whole image,
+    padded to a multiple of 2^levels, is the one sample of every step.  Also
+    at the paper's width (base 128 doubling to 2048 channels, four levels)."""
+    ctx = _ctx()
+    from scipy.ndimage import gaussian_filter
+
+    g = np.random.Generator(np.random.PCG64(40 + base))
+    img = np.cumsum(g.standard_normal(shape), axis=1)
+    x = gaussian_filter(img, 1.5).astype(np.float32)
+    y = img.astype(np.float32)
+    spec = onn.UNetSpec(base=base, levels=levels)
+    cfg = onn.TrainCfg(patch=0, epochs=epochs, lr=lr, seed=5, mute_rows=3)
+    hist = ctx.deblur_train(_dev(x), _dev(y), warm_start=False, base_channels=base, levels=levels, patch=0,
+                            epochs=epochs, lr=lr, seed=5, mute_rows=3)
+    theta, href = onn.train(onn.init_params(spec, 5), x.astype(np.float64), y.astype(np.float64), spec, cfg)
+    assert np.allclose(hist, href, rtol=2e-2), (hist, href)
+    w = ctx.net_get()
+    assert w.size == onn.n_params(spec)
+    assert rel_l2(w, theta) <= 0.1
+    out = ctx.deblur_apply(_dev(y)).cpu().numpy()
+    ref = onn.apply(w.astype(np.float64), y.astype(np.float64), spec, mute_rows=3)
+    assert rel_l2(out, ref) <= 1e-2
+
+
 def test_network_errors():
     ctx = _ctx()
     from paper_2403_17518_gb300.ops import DhfwiError

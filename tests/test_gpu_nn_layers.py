@@ -10,7 +10,8 @@ the GPU in float32.  The shapes reach every GEMM path the network runs: the
 the tcgen05 kernels for >= 64 output channels (32- and 64-channel sources),
 the split-k paths of the deepest levels, M tails (pixel counts that are not a
 multiple of the 128-row tile) and the transposed convolutions; each case runs
-under every GEMM selection (DHFWI_NN_GEMM unset, "mma", "tc").
+under every GEMM selection (the default persistent tcgen05 convolution, the
+one-tile-per-CTA one, DHFWI_NN_GEMM "mma" and "tc").
 """
 import math
 
@@ -41,7 +42,7 @@ CONVT = [
     (128, 64, 3, 5, 7),
     (64, 32, 2, 8, 12),
 ]
-MODES = ["default", "mma", "tc"]
+MODES = ["default", "tile", "mma", "tc"]  # tile: the one-tile-per-CTA tcgen05 kernel (DHFWI_NN_CONV=tile)
 
 
 def _data(seed, kind, ci, co, n, H, W):
@@ -82,8 +83,11 @@ def _oracle(kind, op, x, w, b, gy):
 def _run(monkeypatch, mode, kind, shape, seed):
     import torch
 
-    if mode == "default":
+    monkeypatch.delenv("DHFWI_NN_CONV", raising=False)
+    if mode in ("default", "tile"):
         monkeypatch.delenv("DHFWI_NN_GEMM", raising=False)
+        if mode == "tile":
+            monkeypatch.setenv("DHFWI_NN_CONV", "tile")
     else:
         monkeypatch.setenv("DHFWI_NN_GEMM", mode)
     ci, co, n, H, W = shape

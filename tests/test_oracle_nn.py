@@ -298,3 +298,38 @@ def test_apply_is_scale_equivariant():
     a = nn.apply(flat, img, spec, round_bf16=False, mute_rows=2)
     b = nn.apply(flat, 7.25 * img, spec, round_bf16=False, mute_rows=2)
     assert np.allclose(b, 7.25 * a, rtol=1e-12, atol=1e-12 * np.abs(b).max())
+
+
+def test_full_image_training_is_the_one_patch_case():
+    """patch 0 (the whole image, padded to a multiple of 2^levels, as the
+    only sample) gives exactly the patch-mode training whose single patch is
+    the whole image, when the image needs no padding."""
+    spec = nn.UNetSpec(base=4, levels=2)
+    g = rng(12)
+    img = g.standard_normal((16, 16))
+    x = img + 0.3 * g.standard_normal((16, 16))
+    flat = nn.init_params(spec, 2)
+    a = nn.train(flat, x, img, spec, nn.TrainCfg(patch=0, epochs=3, lr=1e-2, seed=1, mute_rows=2))
+    b = nn.train(flat, x, img, spec, nn.TrainCfg(patch=16, stride=8, batch=4, epochs=3, lr=1e-2, seed=1,
+                                                   mute_rows=2))
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+
+
+def test_full_image_training_pads_the_sample(monkeypatch):
+    """A 13 x 22 image trains as one 16 x 24 sample, zero outside the image."""
+    seen = []
+    real = nn.forward
+
+    def spy(flat, x, spec, round_bf16=True):
+        seen.append(np.array(x))
+        return real(flat, x, spec, round_bf16)
+
+    monkeypatch.setattr(nn, "forward", spy)
+    spec = nn.UNetSpec(base=4, levels=2)
+    img = rng(13).standard_normal((13, 22))
+    _, hist = nn.train(nn.init_params(spec, 2), img, img, spec, nn.TrainCfg(patch=0, epochs=2, lr=1e-3, seed=1))
+    assert len(hist) == 2 and len(seen) == 2
+    x = seen[0]
+    assert x.shape == (1, 1, 16, 24)
+    assert np.all(x[0, 0, 13:] == 0) and np.all(x[0, 0, :, 22:] == 0)
+    assert np.array_equal(x[0, 0, :13, :22], img / np.abs(img).max())
