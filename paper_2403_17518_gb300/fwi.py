@@ -108,8 +108,28 @@ def line_search(ctx, v, dirn, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_
     return parabolic_alpha(J0, Js[0], Js[1], a1)
 
 
+class BandData:
+    """Observed data of the true model and their band-limited versions (the
+    wavelet low-passed identically), computed once and shared by the arms."""
+
+    def __init__(self, ctx: Context, case):
+        v_true = torch.tensor(case.v_true, dtype=torch.float32, device=ctx.device)
+        self.d_full = ctx.model_shots(v_true, case.geom).cpu().numpy()
+        self.case = case
+        self.bands = {}
+
+    def get(self, fc: float):
+        if fc not in self.bands:
+            g = copy.deepcopy(self.case.geom)
+            g.wavelet = lowpass(np.asarray(g.wavelet, dtype=np.float64), self.case.dt, fc)
+            d = band_data(self.d_full, self.case.geom, self.case.dt, fc).astype(np.float32)
+            self.bands[fc] = (GeomArgs(g), d)
+        return self.bands[fc]
+
+
 def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, cold_epochs: int, warm_epochs: int,
-            vmin: float, vmax: float, mute_rows: int = 5, log=None, hybrid_iters: int = 0):
+            vmin: float, vmax: float, mute_rows: int = 5, log=None, hybrid_iters: int = 0, data: BandData = None,
+            timer=None):
     """mode: "plain" (gradient, parabolic line search), "bb" (gradient with
     the Barzilai-Borwein short step of Eq. 17, the paper's baseline; the
     first iteration of each band takes the line search), "deblur" (network
@@ -120,10 +140,10 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
     dev = ctx.device
     v_true = torch.tensor(case.v_true, dtype=torch.float32, device=dev)
     v = torch.tensor(case.v_init, dtype=torch.float32, device=dev)
-    d_full = ctx.model_shots(v_true, case.geom).cpu().numpy()
+    data = data if data is not None else BandData(ctx, case)
     hist = [{"band": None, "iter": 0, "gpu_s": 0.0, "solves": 0, "model_rms": model_rms(v, v_true), "misfit": None}]
     solves = 0
-    timer = Timer()
+    timer = timer if timer is not None else Timer()
     grad = ctx.new_model()
     direction = ctx.new_model()
     dm1 = ctx.new_model()
@@ -133,10 +153,8 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
     for fc in bands:
         trained_in_band = False  # the network restarts from scratch in each band (Section 4)
         have_prev = False  # BB needs two models and gradients of the same band
-        g = copy.deepcopy(case.geom)
-        g.wavelet = lowpass(np.asarray(g.wavelet, dtype=np.float64), case.dt, fc)
-        ga = GeomArgs(g)
-        d_obs = torch.tensor(band_data(d_full, case.geom, case.dt, fc), dtype=torch.float32, device=dev)
+        ga, d_band = data.get(fc)
+        d_obs = torch.tensor(d_band, dtype=torch.float32, device=dev)
         d_born = ctx.new_data(ga)
         d_try = ctx.new_data(ga)
         for it in range(iters):
@@ -173,9 +191,11 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
                     dirn = grad
                     alpha_bb = 0.0
                     if mode == "bb" and have_prev:
-                        # Eq. 17: x_{k+1} = x_k - alpha g_k; fwi_update divides by max|g_k|.
+                        # Eq. 17: x_{k+1} = x_k - alpha g_k; fwi_update divides by
+                        # max|g_k|.  Safeguard: the largest model change is
+                        # bounded as in the line search (4 a1).
                         alpha_bb, gmax = ctx.bb_step(v, v_prev, grad, g_prev, mute_rows)
-                        a_best = alpha_bb * gmax
+                        a_best = min(alpha_bb * gmax, 4 * a1)
                     if alpha_bb <= 0.0:  # no curvature estimate yet (or a negative one): line search
                         a_best, _ = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
                                                 mute_rows)
@@ -236,20 +256,32 @@ def main():
     p.add_argument("--iters-hybrid", type=int, default=0, help="iterations per band, hybrid arm (default --iters)")
     p.add_argument("--hybrid-net-iters", type=int, default=5,
                    help="hybrid arm: iterations at the start of the run that use the network direction")
+    p.add_argument("--case", default="custom", choices=["custom", "config5"],
+                   help="config5: the 600 x 2000, 200-shot multiscale workload (dx 10 m, dt 0.8 ms, nt 6000, "
+                        "uneven apertures and record lengths); custom: the --nz/--nx/... model")
+    p.add_argument("--patch", type=int, default=64, help="network training patch (128 for config 5)")
+    p.add_argument("--cold-epochs", type=int, default=200)
+    p.add_argument("--warm-epochs", type=int, default=20)
     p.add_argument("--out", default="")
     a = p.parse_args()
-    v = synth.layered_fault_model(a.nz, a.nx, a.h, seed=31)
-    v0 = synth.smooth_model(v, 10.0)
-    wav = synth.ricker(8.0, a.dt, a.nt)
-    geom = synth.surface_geometry(a.nx, a.shots, seed=31, nrec_range=(a.nx // 3, a.nx // 2),
-                                  nt_range=(int(a.nt * 0.8), a.nt), margin=a.nx // 10, src_lo=10,
-                                  src_hi=a.nx - 11, wavelet=wav)
-    case = synth.Case(a.nz, a.nx, a.h, a.dt, 20, v, v0, geom, name="fwi-loop")
-    ctx = Context(a.nz, a.nx, a.h, a.dt, 20)
-    net = dict(base_channels=32, levels=4, patch=64, stride=32, batch=32, lr=a.lr, seed=29)
+    if a.case == "config5":
+        case = synth.config5_case()
+        a.nz, a.nx, a.h, a.dt, a.shots, a.nt = case.nz, case.nx, case.h, case.dt, case.geom.n_shots, int(
+            case.geom.nt.max())
+    else:
+        v = synth.layered_fault_model(a.nz, a.nx, a.h, seed=31)
+        v0 = synth.smooth_model(v, 10.0)
+        wav = synth.ricker(8.0, a.dt, a.nt)
+        geom = synth.surface_geometry(a.nx, a.shots, seed=31, nrec_range=(a.nx // 3, a.nx // 2),
+                                      nt_range=(int(a.nt * 0.8), a.nt), margin=a.nx // 10, src_lo=10,
+                                      src_hi=a.nx - 11, wavelet=wav)
+        case = synth.Case(a.nz, a.nx, a.h, a.dt, 20, v, v0, geom, name="fwi-loop")
+    ctx = Context(case.nz, case.nx, case.h, case.dt, case.nb)
+    net = dict(base_channels=32, levels=4, patch=a.patch, stride=a.patch // 2, batch=32, lr=a.lr, seed=29)
     bands = [float(b) for b in a.bands.split(",")]
     out = {"config": vars(a), "net": net}
     t0 = time.time()
+    data = BandData(ctx, case)
     arms = {}
     for name in a.arms.split(","):
         # "hybridN": hybrid arm with the network for the first N iterations.
@@ -260,9 +292,13 @@ def main():
             iters = a.iters_plain
         if mode == "hybrid" and a.iters_hybrid > 0:
             iters = a.iters_hybrid
-        arms[name] = run_arm(ctx, case, mode, bands, iters, net, 200, 20, 1500.0, 4500.0, mute_rows=a.mute,
-                             log=lambda m, r, nm=name: print(nm, json.dumps(r), flush=True), hybrid_iters=hyb)
+        arms[name] = run_arm(ctx, case, mode, bands, iters, net, a.cold_epochs, a.warm_epochs, 1500.0, 4500.0,
+                             mute_rows=a.mute, log=lambda m, r, nm=name: print(nm, json.dumps(r), flush=True),
+                             hybrid_iters=hyb, data=data)
         out[name] = arms[name]
+        if a.out:  # partial results survive a run cut short
+            with open(a.out, "w") as f:
+                f.write(json.dumps(dict(out, summary=summarize(arms))))
     out["wall_s"] = time.time() - t0
     out["summary"] = summarize(arms)
     s = json.dumps(out)
