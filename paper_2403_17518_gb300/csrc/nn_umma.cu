@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Persistent form of conv3_tma_umma_kernel (the default): grid = the SMs
+// Persistent form of conv3_tma_umma_kernel (large GEMMs): grid = the SMs
 // (times the CTAs that fit), each CTA walks the work items (m-tile, n-tile,
 // k-split) with a stride of gridDim.x.  The stage ring runs on across items
 // (one k-tile counter), and the accumulator is double-buffered in TMEM
@@ -966,15 +966,27 @@ bool conv3_persistent_launch(const FpropArgs &a, const ConvTile &G0, cudaStream_
     return true;
 }
 
-// DHFWI_NN_CONV=tile: the one-tile-per-CTA kernel instead of the persistent one.
-bool conv3_persistent() {
+// Kernel choice for a conv3 GEMM: DHFWI_NN_CONV=tile (one tile per CTA),
+// =persistent, or unset: the persistent kernel when the GEMM has at least
+// four waves of 128 x 128 output tiles (large layers, where the overlap of
+// one tile's epilogue with the next tile's MMAs pays), else one tile per CTA
+// (measured at least as fast on the small layers of the 128 x 128 patches).
+int conv3_mode() {
     const char *e = getenv("DHFWI_NN_CONV");
-    return !(e && strcmp(e, "tile") == 0);
+    if (e && strcmp(e, "tile") == 0) return 0;
+    if (e && strcmp(e, "persistent") == 0) return 1;
+    return 2;
+}
+bool conv3_persistent(const FpropArgs &a) {
+    const int m = conv3_mode();
+    if (m != 2) return m == 1;
+    const long long tiles = ((long long)a.M + 127) / 128 * ((a.N + 127) / 128);
+    return tiles >= 4 * 152;
 }
 
 template <int EPI>
 bool conv3_tma_dispatch(const FpropArgs &a, const ConvTile &G, cudaStream_t s) {
-    if (conv3_persistent()) {
+    if (conv3_persistent(a)) {
         if (a.C % 64 == 0) {
             if (a.N <= 32) return conv3_persistent_launch<32, 64, EPI>(a, G, s);
             if (a.N <= 64) return conv3_persistent_launch<64, 64, EPI>(a, G, s);
@@ -1008,7 +1020,8 @@ void umma_dispatch(const FpropArgs &a, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Weight gradient of a 3x3 convolution on tcgen05 (input channels ci and
-// output channels co multiples of 64):
+// output channels co multiples of 32; a 32-channel tensor is read as 64
+// channels, the TMA filling the missing half with zeros):
 //   part[z][co][tap * ci + c] = sum over the pixels of split z of
 //                               G[p][co] X[p + shift(tap)][c].
 // The MMA's M = 128 rows are two (tap, 64-channel block) pairs of the input
@@ -1046,7 +1059,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q0 = 2 * blockIdx.x;  // first (tap, channel block) pair of this M tile
     const bool two = q0 + 1 < G.pairs;
-    const int cbn = P.ci / 64;
+    const int cbn = (P.ci + 63) / 64;  // 64-channel blocks of X (the last one zero-filled past ci)
     const int co0 = blockIdx.y * NB;
     const int pb0 = blockIdx.z * G.per;
     const int nk = max(0, min(G.npb, pb0 + G.per) - pb0);
@@ -1133,8 +1146,9 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         } else {
             const int r = qw * 32 + lane;
             const int q = q0 + (r >> 6);
-            const bool valid = q < G.pairs && (r < 64 || two);
             const int tap = q / cbn, cb = q - tap * cbn;
+            // Rows past ci (a 32-channel X read as a 64-channel box) are zero.
+            const bool valid = q < G.pairs && (r < 64 || two) && cb * 64 + (r & 63) < P.ci;
             const int n = tap * P.ci + cb * 64 + (r & 63);
             float *out = P.part + (long long)blockIdx.z * P.M * P.N + n;
             const unsigned trow = tmem + ((unsigned)(qw * 32) << 16);
@@ -1147,7 +1161,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                     for (int e = 0; e < 16; e++) v[e] = 0.f;
                 if (!valid) continue;
 #pragma unroll
-                for (int e = 0; e < 16; e++) out[(long long)(co0 + c0 + e) * P.N] = v[e];
+                for (int e = 0; e < 16; e++)  // columns past M: a 32-channel G read as 64
+                    if (co0 + c0 + e < P.M) out[(long long)(co0 + c0 + e) * P.N] = v[e];
             }
         }
     }
@@ -1173,8 +1188,8 @@ int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
     G.tw = (a.W + G.BW - 1) / G.BW;
     G.th = (a.H + G.BH - 1) / G.BH;
     G.npb = G.tw * G.th * ((a.nimg + G.BI - 1) / G.BI);
-    G.pairs = 9 * (a.ci / 64);
-    const int mt = (G.pairs + 1) / 2, ntl = a.M / NB;
+    G.pairs = 9 * ((a.ci + 63) / 64);
+    const int mt = (G.pairs + 1) / 2, ntl = (a.M + NB - 1) / NB;
     const int tiles = mt * ntl;
     int splits = (152 + tiles - 1) / tiles;
     splits = std::min(splits, std::max(1, G.npb / 4));
@@ -1217,8 +1232,10 @@ int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
 // stride that is a multiple of 8 channels.  Returns false (nothing launched)
 // otherwise.
 bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
-    // The persistent kernel also takes the 32-channel outputs (BN = 32).
-    const int min_n = conv3_persistent() ? 32 : 64;
+    // 32-channel outputs go to tcgen05 only when the persistent kernel is
+    // forced (BN = 32); by default the shared-memory halo kernel takes them
+    // (it reuses the input patch for all nine taps, measured 2x faster).
+    const int min_n = conv3_mode() == 1 ? 32 : 64;
     if (epi == EPI_BF16_CONVT || a.N < min_n || a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws ||
         a.C % 32 != 0 || a.C <= 0)
         return false;
@@ -1247,13 +1264,16 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
 
 // The tcgen05 weight gradient (the default; DHFWI_NN_WGRAD=mma or
 // DHFWI_NN_GEMM=mma keep the mma.sync one) for WG_CONV with ci and co
-// multiples of 64 and aligned operands.  Partials as igemm_wgrad_kernel's,
+// multiples of 32 and aligned operands.  Partials as igemm_wgrad_kernel's,
 // bias column zero.  Returns the number of splits written (0: not
 // applicable, nothing launched).
 int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s) {
     const char *e = getenv("DHFWI_NN_WGRAD"), *g = getenv("DHFWI_NN_GEMM");
     if ((e && strcmp(e, "mma") == 0) || (g && strcmp(g, "mma") == 0)) return 0;
-    if (a.mode != WG_CONV || a.ci % 64 != 0 || a.M % 64 != 0 || a.ci <= 0 || a.M <= 0) return 0;
+    // ci and co multiples of 32: a 32-channel operand is read as a 64-channel
+    // TMA box whose upper half the copy fills with zeros (rows and columns the
+    // epilogue does not write).
+    if (a.mode != WG_CONV || a.ci % 32 != 0 || a.M % 32 != 0 || a.ci <= 0 || a.M <= 0) return 0;
     if (a.nw != 9 * a.ci || a.N != a.nw + 8) return 0;
     if (((a.x_stride | a.x_off | a.g_stride) & 7) != 0) return 0;
     if ((((uintptr_t)(a.x + a.x_off)) | (uintptr_t)a.g) & 15) return 0;

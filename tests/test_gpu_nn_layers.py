@@ -10,8 +10,8 @@ the GPU in float32.  The shapes reach every GEMM path the network runs: the
 the tcgen05 kernels for >= 64 output channels (32- and 64-channel sources),
 the split-k paths of the deepest levels, M tails (pixel counts that are not a
 multiple of the 128-row tile) and the transposed convolutions; each case runs
-under every GEMM selection (the default persistent tcgen05 convolution, the
-one-tile-per-CTA one, DHFWI_NN_GEMM "mma" and "tc").
+under every GEMM selection (the default choice, the one-tile-per-CTA and the
+persistent tcgen05 convolutions forced, DHFWI_NN_GEMM "mma" and "tc").
 """
 import math
 
@@ -42,7 +42,8 @@ CONVT = [
     (128, 64, 3, 5, 7),
     (64, 32, 2, 8, 12),
 ]
-MODES = ["default", "tile", "mma", "tc"]  # tile: the one-tile-per-CTA tcgen05 kernel (DHFWI_NN_CONV=tile)
+# tile / persistent: the one-tile-per-CTA or the persistent tcgen05 conv kernel forced (DHFWI_NN_CONV)
+MODES = ["default", "tile", "persistent", "mma", "tc"]
 
 
 def _data(seed, kind, ci, co, n, H, W):
@@ -84,10 +85,10 @@ def _run(monkeypatch, mode, kind, shape, seed):
     import torch
 
     monkeypatch.delenv("DHFWI_NN_CONV", raising=False)
-    if mode in ("default", "tile"):
+    if mode in ("default", "tile", "persistent"):
         monkeypatch.delenv("DHFWI_NN_GEMM", raising=False)
-        if mode == "tile":
-            monkeypatch.setenv("DHFWI_NN_CONV", "tile")
+        if mode != "default":
+            monkeypatch.setenv("DHFWI_NN_CONV", mode)
     else:
         monkeypatch.setenv("DHFWI_NN_GEMM", mode)
     ci, co, n, H, W = shape
