@@ -494,24 +494,33 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, 
 
 // Bias gradient: db[c] = sum over pixels of g[p][c] (bf16 in, fixed order:
 // per-block partial sums then a second pass).
-// Column sums of g over a block of rows, four independent accumulators
-// (rows p, p+1, p+2, p+3 of each group of four) combined in a fixed order.
+// Column sums of g over a block of rows: threadIdx.x is the channel,
+// threadIdx.y (of blockDim.y) takes every blockDim.y-th row with two
+// independent accumulators; the rows' sums are then combined over y in a
+// fixed order in shared memory (deterministic).
 __global__ void bias_grad_partial_kernel(const __nv_bfloat16 *__restrict__ g, int stride, int C, long long P,
                                          int rows_per_block, float *__restrict__ part) {
+    __shared__ float red[256];
     const int c = blockIdx.y * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+    const int ty = threadIdx.y, ny = blockDim.y;
     const long long p0 = (long long)blockIdx.x * rows_per_block;
     const long long p1 = p0 + rows_per_block < P ? p0 + rows_per_block : P;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    long long p = p0;
-    for (; p + 3 < p1; p += 4) {
-        s0 += __bfloat162float(g[p * stride + c]);
-        s1 += __bfloat162float(g[(p + 1) * stride + c]);
-        s2 += __bfloat162float(g[(p + 2) * stride + c]);
-        s3 += __bfloat162float(g[(p + 3) * stride + c]);
+    float s0 = 0.f, s1 = 0.f;
+    if (c < C) {
+        long long p = p0 + ty;
+        for (; p + ny < p1; p += 2 * ny) {
+            s0 += __bfloat162float(g[p * stride + c]);
+            s1 += __bfloat162float(g[(p + ny) * stride + c]);
+        }
+        if (p < p1) s0 += __bfloat162float(g[p * stride + c]);
     }
-    for (; p < p1; p++) s0 += __bfloat162float(g[p * stride + c]);
-    part[(long long)blockIdx.x * C + c] = (s0 + s1) + (s2 + s3);
+    red[ty * blockDim.x + threadIdx.x] = s0 + s1;
+    __syncthreads();
+    if (ty == 0 && c < C) {
+        float s = 0.f;
+        for (int y = 0; y < ny; y++) s += red[y * blockDim.x + threadIdx.x];
+        part[(long long)blockIdx.x * C + c] = s;
+    }
 }
 
 // One warp per channel: lane l sums the partials l, l+32, ..., then a
@@ -1283,9 +1292,9 @@ void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, fl
     int rows = (int)((P + max_blocks - 1) / max_blocks);
     if (rows < 64) rows = 64;
     const int nblk = (int)((P + rows - 1) / rows);
-    const int bd = C < 128 ? (C + 31) / 32 * 32 : 128;
+    const int bd = C < 128 ? (C + 31) / 32 * 32 : 128;  // channels per block; 256 threads in all
     dim3 grid(nblk, (C + bd - 1) / bd);
-    bias_grad_partial_kernel<<<grid, bd, 0, s>>>(g, stride, C, P, rows, part);
+    bias_grad_partial_kernel<<<grid, dim3(bd, 256 / bd), 0, s>>>(g, stride, C, P, rows, part);
     bias_grad_final_kernel<<<(C * 32 + 255) / 256, 256, 0, s>>>(part, nblk, C, db);
 }
 

@@ -469,6 +469,17 @@ __device__ __forceinline__ void conv_tile_epilogue(const FpropArgs &P, const Con
                 for (int e = 0; e < 16; e++)
                     if (nb + e < P.N) o[e] = h[e];
             }
+        } else if (EPI == EPI_BF16_CONVT) {
+            // Transposed conv: column n = co*4 + a*2 + b of coarse pixel
+            // (img, ho, wo) is fine pixel (2 ho + a, 2 wo + b), channel co.
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                const int n = nb + e;
+                if (n >= P.N) continue;
+                const int co = n >> 2, a = (n >> 1) & 1, b = n & 1;
+                const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
+                P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v[e] + P.bias[co]);
+            }
         } else if (EPI == EPI_BF16_LEAKYBWD) {
             const __nv_bfloat16 *ap = P.act + m * P.act_stride + P.act_off + nb;
             __nv_bfloat16 *o = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
@@ -1236,8 +1247,12 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
     // forced (BN = 32); by default the shared-memory halo kernel takes them
     // (it reuses the input patch for all nine taps, measured 2x faster).
     const int min_n = conv3_mode() == 1 ? 32 : 64;
-    if (epi == EPI_BF16_CONVT || a.N < min_n || a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws ||
-        a.C % 32 != 0 || a.C <= 0)
+    // Also the transposed conv's forward GEMM: one tap without shift on the
+    // coarse grid, scattered to the fine grid by the epilogue.
+    const bool one_tap = a.ntaps == 1 && a.dh[0] == 0 && a.dw[0] == 0;
+    if (getenv("DHFWI_NN_CONVT") && strcmp(getenv("DHFWI_NN_CONVT"), "mma") == 0 && one_tap) return false;
+    if ((epi == EPI_BF16_CONVT && !one_tap) || a.N < min_n || (a.ntaps != 9 && !one_tap) || a.scale != 1 ||
+        a.Ho != a.Hs || a.Wo != a.Ws || a.C % 32 != 0 || a.C <= 0)
         return false;
     if (((a.src_stride | a.src_off) & 7) != 0) return false;
     if (((uintptr_t)(a.src + a.src_off) & 15) != 0 || ((uintptr_t)a.bt & 15) != 0) return false;
@@ -1258,6 +1273,7 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
     case EPI_F32: return conv3_tma_dispatch<EPI_F32>(a, G, s);
     case EPI_BF16_LEAKYBWD: return conv3_tma_dispatch<EPI_BF16_LEAKYBWD>(a, G, s);
     case EPI_F32_ADD: return conv3_tma_dispatch<EPI_F32_ADD>(a, G, s);
+    case EPI_BF16_CONVT: return conv3_tma_dispatch<EPI_BF16_CONVT>(a, G, s);
     default: return false;
     }
 }
