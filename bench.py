@@ -84,6 +84,10 @@ def parse():
                    help="with --only fwd/grad/born: the first SHOTS shots of the batch (small profiling captures)")
     p.add_argument("--nt", type=int, default=0,
                    help="with --only fwd/grad/born: records truncated to NT samples (small profiling captures)")
+    p.add_argument("--reuse", action="store_true",
+                   help="turn on dhfwi_set_reuse (Born and migration take the background from the gradient's stored "
+                        "forward pass); the value still counts the step's 6 U algorithmic updates, and "
+                        "performed_cell_updates_per_step says how many ran")
     p.add_argument("--cold-epochs", type=int, default=COLD_EPOCHS,
                    help="epochs of the network's cold start before the timed region (setup only)")
     return p.parse_args()
@@ -545,6 +549,8 @@ def main():
     v1 = ctx.new_model()
     d_born = ctx.new_data(geom)
     ctx.set_timing(True)
+    ctx.set_reuse(args.reuse)
+    performed = [0]
     alpha = 0.01 * float(np.mean(case.v_init))
     # Cold start of the network (first FWI iteration), outside the timed region.
     ctx.fwi_gradient(v0, geom, d_obs, grad=grad)
@@ -585,6 +591,7 @@ def main():
         for st in stats:
             launches[0] += st["kernel_launches"]
             if collect:
+                performed[0] += st["cell_updates"]
                 for k in range(3):
                     ph[k]["ms"] += st["phase_ms"][k]
                     ph[k]["launches"] += st["phase_launches"][k]
@@ -720,6 +727,8 @@ def main():
             "launches_before_timed_region": int(launches_before),
             "step_variants": ctx.stats()["step_variant"],
             "time_block_depth": {"forward": ctx.stats()["time_block"][0], "adjoint": ctx.stats()["time_block"][1]},
+            "reuse": bool(args.reuse),
+            "performed_cell_updates_per_step": int(performed[0] // max(args.steps, 1)),
             "history_steps": {"stored": hist["steps"], "of": nt_max,
                               "workspace_gb": round(ctx.stats()["workspace_bytes"] / 1e9, 2)},
             "phase_ms_per_step": {"forward_ms": round(ph[0]["ms"] / args.steps, 2),

@@ -128,6 +128,10 @@ typedef struct {
      * the autotuner times both depths per geometry; DHFWI_TIME_BLOCK=0
      * (environment) forces 1, any other value 2. */
     int time_block[2];
+    /* What the last call took from the stored forward pass of an earlier
+     * call (dhfwi_set_reuse): bit 0, rtm_mig skipped its forward pass; bit 1,
+     * born_demig read the background term from the history. */
+    int reused;
 } dhfwi_stats_t;
 
 /* Create a context on CUDA device `device` for grid `g`.  The context owns all
@@ -149,6 +153,23 @@ int dhfwi_stats(const dhfwi_ctx *ctx, dhfwi_stats_t *out);
 
 /* Turn per-phase CUDA-event timing on (1) or off (0) for later calls. */
 int dhfwi_set_timing(dhfwi_ctx *ctx, int on);
+
+/* Reuse of the forward wavefield between calls, off by default (no
+ * counterpart in the paper: an implementation choice for the FWI iteration,
+ * whose gradient, Born demigration and migration all propagate the same
+ * background field).  With reuse on, a backward-capable forward pass
+ * (fwi_gradient, rtm_mig) leaves its a^n history and checkpoints intact
+ * (the segment recompute of the backward sweep starts from copies of the
+ * checkpoints), and a later rtm_mig or born_demig at the same velocity model
+ * and geometry takes the background from them instead of propagating it
+ * again: rtm_mig skips its forward pass, and born_demig, when the history
+ * holds every step, advances only the scattered field, reading the
+ * background term a^n = D u0^n + q^n.  The model is identified by a 64-bit
+ * hash of its values computed on the device at every call, the geometry by
+ * the plan's content hash; a changed model, geometry or workspace split
+ * falls back to propagating.  Results are the same bits either way.  Calls
+ * report what they reused in dhfwi_stats_t.reused. */
+int dhfwi_set_reuse(dhfwi_ctx *ctx, int on);
 
 /* Forward shot modelling (Section 2.1: "the wave equation is solved using a
  * forward modeling scheme such as the finite difference method to obtain the

@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_double), ("phase_ms", ctypes.c_double * 3),
                 ("phase_launches", ctypes.c_longlong * 3), ("phase_cells", ctypes.c_longlong * 3),
                 ("step_variant", ctypes.c_int * 4), ("history_steps", ctypes.c_int),
-                ("history_cells", ctypes.c_longlong), ("time_block", ctypes.c_int * 2)]
+                ("history_cells", ctypes.c_longlong), ("time_block", ctypes.c_int * 2), ("reused", ctypes.c_int)]
 
 
 class TrainCfg(ctypes.Structure):
@@ -69,6 +69,7 @@ SIGNATURES = [
     ("dhfwi_last_error", ctypes.c_char_p, [_VP]),
     ("dhfwi_stats", ctypes.c_int, [_VP, ctypes.POINTER(Stats)]),
     ("dhfwi_set_timing", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("dhfwi_set_reuse", ctypes.c_int, [_VP, ctypes.c_int]),
     ("model_shots", ctypes.c_int, [_VP, _VP, ctypes.POINTER(Geom), _VP, _VP]),
     ("fwi_gradient", ctypes.c_int, [_VP, _VP, ctypes.POINTER(Geom), _VP, _VP,
                                     ctypes.POINTER(ctypes.c_double), _VP, _VP]),

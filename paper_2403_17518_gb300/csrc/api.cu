@@ -82,6 +82,17 @@ struct dhfwi_ctx {
     // Time steps per launch (1 or 2) of the forward and the adjoint sweeps,
     // chosen by the autotuner.
     int depth[2] = {2, 2};
+    // Reuse of the stored forward wavefield between calls (dhfwi_set_reuse):
+    // the identity of the last complete backward-capable forward pass (plan
+    // hash, model hash, history segments, checkpoint interval) whose a^n
+    // history and checkpoints are still intact.
+    bool reuse = false;
+    unsigned long long model_hash = 0;  // of the velocity of the current call (prep_model)
+    struct {
+        bool valid = false;
+        unsigned long long plan = 0, model = 0;
+        int segs = 0, K = 0;
+    } fws;
     unsigned long long tuned_hash = 0;
     int nsm = 1;
     cudaEvent_t ev[3][2] = {};
@@ -250,6 +261,7 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
     // The plan's device tables may still be read by earlier work on any stream.
     CK(cudaDeviceSynchronize());
     P.hash = 0;
+    ctx->fws.valid = false;
     ctx->tmaps.clear();
     P.n_shots = ns;
     P.nt_max = G->nt_max;
@@ -537,15 +549,16 @@ int prep_model(dhfwi_ctx *ctx, const float *v, const float *dv, int rel, cudaStr
     if ((rc = ensure(ctx, ctx->kap, 4 * mb, "kappa"))) return rc;
     if (dv && (rc = ensure(ctx, ctx->dkap, 4 * mb, "d kappa"))) return rc;
     CK(cudaMemsetAsync(ctx->status.p, 0, 2 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync((unsigned *)ctx->status.p + 8, 0, 2 * sizeof(unsigned), st));  // model hash
     const double c = ((double)ctx->g.dt * ctx->g.dt) / ((double)ctx->g.h * ctx->g.h);
     launch_prep_model(v, dv, rel, ctx->g.nz, ctx->g.nx, ctx->g.nb, c, (float *)ctx->kap.p,
                       dv ? (float *)ctx->dkap.p : nullptr, ctx->pf, (long long)ctx->NZ * ctx->pf,
                       (unsigned *)ctx->status.p, st);
     ctx->stats.kernel_launches++;
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(ctx->h_status, ctx->status.p, (TFLAG_WORD + 1) * sizeof(unsigned), cudaMemcpyDeviceToHost,
-                       st));
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status.p, 10 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    ctx->model_hash = (unsigned long long)ctx->h_status[8] | ((unsigned long long)ctx->h_status[9] << 32);
     if (ctx->h_status[TFLAG_WORD]) {
         CK(cudaMemset((unsigned *)ctx->status.p + TFLAG_WORD, 0, sizeof(unsigned)));
         return fail(ctx, DHFWI_ERR_TIMEOUT, "a step kernel of an earlier call timed out waiting for its tile copies");
@@ -590,6 +603,7 @@ int begin_call(dhfwi_ctx *ctx) {
     ctx->stats.shot_groups = 1;
     ctx->stats.history_steps = 0;
     ctx->stats.history_cells = 0;
+    ctx->stats.reused = 0;
     for (int i = 0; i < 3; i++) {
         ctx->stats.phase_ms[i] = 0.0;
         ctx->stats.phase_launches[i] = 0;
@@ -914,6 +928,7 @@ int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, flo
     float *ck = (float *)ctx->ck.p, *hist = (float *)ctx->hist.p;
     auto slot = [&](int n) -> float * { return n < H ? hist + ctx->hoff[n] : nullptr; };
     const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
+    if (backward) ctx->fws.valid = false;  // the history and checkpoints are about to change
     phase_begin(ctx, 0, st);
     for (int n = 0; n < P.nt_max;) {
         // K and H are even and two-step launches start at even n: a launch
@@ -932,10 +947,24 @@ int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, flo
         if (n < H) ctx->stats.history_cells += ctx->stats.cell_updates - cn;
         n += rc;
     }
-    if (backward) ctx->stats.history_steps = H;
+    if (backward) {
+        ctx->stats.history_steps = H;
+        ctx->fws.valid = true;
+        ctx->fws.plan = P.hash;
+        ctx->fws.model = ctx->model_hash;
+        ctx->fws.segs = ctx->hist_segs;
+        ctx->fws.K = ctx->ck_every;
+    }
     phase_end(ctx, 0, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
     CK(cudaGetLastError());
     return DHFWI_OK;
+}
+
+// True when the last backward-capable forward pass ran at this plan and
+// model (its a^n history and checkpoints intact) and reuse is on.
+bool forward_reusable(const dhfwi_ctx *ctx) {
+    return ctx->reuse && ctx->fws.valid && ctx->fws.plan == ctx->plan.hash && ctx->fws.model == ctx->model_hash &&
+           ctx->fws.segs == ctx->hist_segs && ctx->fws.K == ctx->ck_every;
 }
 
 // Backward sweep, segment by segment from the last: a^n of a segment comes
@@ -944,9 +973,13 @@ int run_forward(dhfwi_ctx *ctx, float *uA, float *uB, float *dd, float *dd2, flo
 // into the segment buffer; then the adjoint steps over it with the data r
 // injected, the image accumulated in gpool.  Adjoint state pools nuA, nuB,
 // nud, nud2 must be zeroed by the caller; with time blocking the adjoint
-// also advances two steps per launch.
-int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *nuA, float *nuB, float *nud, float *nud2, float *gpool,
-                 const float *r, cudaStream_t st) {
+// also advances two steps per launch.  With reuse on, a recomputed segment
+// starts from copies of its checkpoint in w3 and w4 (the recompute then
+// alternates w3 / w and w4 / w2), so that the checkpoints stay intact for a
+// later call that reuses this forward pass; without it the recompute
+// overwrites them and the forward pass can no longer be reused.
+int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *w3, float *w4, float *nuA, float *nuB, float *nud,
+                 float *nud2, float *gpool, const float *r, cudaStream_t st) {
     const Plan &P = ctx->plan;
     const long long pool = P.pool_floats;
     const int K = ctx->ck_every, S = ctx->hist_segs;
@@ -971,6 +1004,14 @@ int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *nuA, float *nuB, fl
         if (!stored) {
             float *cur = ck + (2 * (long long)(js - S)) * pool, *nxt = w;
             float *dcur = ck + (2 * (long long)(js - S) + 1) * pool, *dnxt = w2;
+            if (ctx->reuse) {
+                CK(cudaMemcpyAsync(w3, cur, sizeof(float) * (size_t)pool, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(w4, dcur, sizeof(float) * (size_t)pool, cudaMemcpyDeviceToDevice, st));
+                cur = w3;
+                dcur = w4;
+            } else {
+                ctx->fws.valid = false;
+            }
             f.d = nullptr;
             f.ck_u = f.ck_d = nullptr;
             for (int n = n0; n < n1;) {
@@ -1034,7 +1075,21 @@ long long history_limit() {
 // plus one pool so that a tensor map over any step stays inside it).  S is
 // as large as DHFWI_HISTORY_MB allows, else as device memory allows with
 // max(16 GiB, 1/16 of the device) left free; chosen once per plan.
+int ensure_backward_ws_impl(dhfwi_ctx *ctx);
+
+// The workspace of ensure_backward_ws_impl; a change of the history or
+// checkpoint buffers (reallocated, or a new split) ends the reuse of the
+// forward pass stored in them.
 int ensure_backward_ws(dhfwi_ctx *ctx) {
+    const void *h0 = ctx->hist.p, *c0 = ctx->ck.p;
+    const int s0 = ctx->hist_segs, k0 = ctx->ck_every;
+    const int rc = ensure_backward_ws_impl(ctx);
+    if (rc || ctx->hist.p != h0 || ctx->ck.p != c0 || ctx->hist_segs != s0 || ctx->ck_every != k0)
+        ctx->fws.valid = false;
+    return rc;
+}
+
+int ensure_backward_ws_impl(dhfwi_ctx *ctx) {
     const Plan &P = ctx->plan;
     const size_t pool = sizeof(float) * (size_t)P.pool_floats;
     int rc = ensure(ctx, ctx->fields, NPOOLS * pool, "wavefield pools");
@@ -1214,6 +1269,13 @@ int dhfwi_set_timing(dhfwi_ctx *ctx, int on) {
     return DHFWI_OK;
 }
 
+int dhfwi_set_reuse(dhfwi_ctx *ctx, int on) {
+    if (!ctx) return DHFWI_ERR_ARG;
+    ctx->reuse = on != 0;
+    if (!ctx->reuse) ctx->fws.valid = false;
+    return DHFWI_OK;
+}
+
 int model_shots(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, float *d_dev, void *stream) {
     int rc = begin_call(ctx);
     if (rc) return rc;
@@ -1261,7 +1323,7 @@ int fwi_gradient(dhfwi_ctx *ctx, const float *v_dev, const dhfwi_geom *geom, con
     float *r = (float *)ctx->rtmp.p;
     launch_residual(dsyn, d_obs_dev, r, (long long)nd, (double *)ctx->partial.p, RESID_BLOCKS, st);
     ctx->stats.kernel_launches++;
-    if ((rc = run_backward(ctx, uA, uB, nuA, nuB, nud, F + 8 * pool, gp, r, st)))
+    if ((rc = run_backward(ctx, uA, uB, ud, F + 7 * pool, nuA, nuB, nud, F + 8 * pool, gp, r, st)))
         return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v_dev, 0, grad_dev, st);
@@ -1303,6 +1365,29 @@ int born_demig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, cons
     a.dp = F + 5 * pool;
     const long long l0 = ctx->stats.kernel_launches, c0 = ctx->stats.cell_updates;
     phase_begin(ctx, 2, st);
+    // Background from the stored forward pass at this model (every step of
+    // it in the history, TMA available): only the scattered field advances.
+    if (forward_reusable(ctx) && (long long)ctx->hist_segs * ctx->ck_every >= P.nt_max && encode_tiled()) {
+        float *hist = (float *)ctx->hist.p;
+        for (int n = 0; n < P.nt_max; n++) {
+            a.p = p;
+            a.pn = pn;
+            a.n = n;
+            a.a = hist + ctx->hoff[n];
+            TileMaps M;
+            if ((rc = tensor_map(ctx, a.p, MAP_POOL_HALO, &M.m[0])) || (rc = tensor_map(ctx, a.dp, MAP_POOL_CELL, &M.m[1])) ||
+                (rc = tensor_map(ctx, a.c.kap, MAP_MODEL, &M.m[2])) || (rc = tensor_map(ctx, a.dkap, MAP_MODEL, &M.m[3])) ||
+                (rc = tensor_map(ctx, a.a, MAP_POOL_CELL, &M.m[4])))
+                return rc;
+            launch_born_hist_step(a, active_tiles(P, n), M, st);
+            ctx->stats.kernel_launches++;
+            ctx->stats.cell_updates += active_cells(P, n, ctx->NZ);
+            std::swap(p, pn);
+        }
+        ctx->stats.reused |= 2;
+        phase_end(ctx, 2, st, ctx->stats.kernel_launches - l0, ctx->stats.cell_updates - c0);
+        return end_call(ctx);
+    }
     for (int n = 0; n < P.nt_max; n++) {
         a.u = u;
         a.un = un;
@@ -1335,12 +1420,19 @@ int rtm_mig(dhfwi_ctx *ctx, const float *v0_dev, const dhfwi_geom *geom, const f
     float *F = (float *)ctx->fields.p;
     float *uA = F, *uB = F + pool, *ud = F + 2 * pool;
     float *nuA = F + 3 * pool, *nuB = F + 4 * pool, *nud = F + 5 * pool, *gp = F + 6 * pool;
-    CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
-    // Checkpoints are staged back as halo tiles: their padding columns, which
-    // no kernel writes, must read as zero.
-    if (ctx->ck.p) CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
-    if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, nullptr, true, st))) return rc;
-    if ((rc = run_backward(ctx, uA, uB, nuA, nuB, nud, F + 8 * pool, gp, d_dev, st)))
+    if (forward_reusable(ctx)) {
+        // The forward pass stored at this model and geometry is still intact:
+        // only the adjoint state and the image start from zero.
+        CK(cudaMemsetAsync(nuA, 0, sizeof(float) * 6 * (size_t)pool, st));
+        ctx->stats.reused |= 1;
+    } else {
+        CK(cudaMemsetAsync(F, 0, sizeof(float) * NPOOLS * (size_t)pool, st));
+        // Checkpoints are staged back as halo tiles: their padding columns, which
+        // no kernel writes, must read as zero.
+        if (ctx->ck.p) CK(cudaMemsetAsync(ctx->ck.p, 0, ctx->ck.bytes, st));
+        if ((rc = run_forward(ctx, uA, uB, ud, F + 7 * pool, nullptr, true, st))) return rc;
+    }
+    if ((rc = run_backward(ctx, uA, uB, ud, F + 7 * pool, nuA, nuB, nud, F + 8 * pool, gp, d_dev, st)))
         return rc;
     launch_reduce_image((const ShotDesc *)P.d_shots.p, (const int *)P.d_slot_of.p, P.n_shots, gp, ctx->g.nz,
                         ctx->g.nx, ctx->g.nb, v0_dev, flags == DHFWI_REL, img_dev, st);

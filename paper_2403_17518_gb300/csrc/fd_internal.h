@@ -150,6 +150,9 @@ struct BornArgs {
     const float *dkap;                         // padded d kappa = 2 kappa dv / v (four copies)
     float *d;                                  // packed Born records (sample n from p^{n+1})
     int n;
+    // Background term a^n = D u0^n + q^n read from a stored forward history
+    // (launch_born_hist_step; the u fields are then not used).
+    const float *a = nullptr;
 };
 
 // Step-kernel variants.  Variants 0-2: tiles staged by per-thread cp.async,
@@ -186,6 +189,10 @@ void launch_adj_inject(const AdjArgs &a, const int *rtiles, int nrtiles, cudaStr
 void launch_fwd_step_tma(const FwdArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s);
 void launch_adj_step_tma(const AdjArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s);
 void launch_born_step_tma(const BornArgs &a, int ntiles, int variant, int grid, const TileMaps &maps, cudaStream_t s);
+// Born step with the background's a^n read from the forward history (maps:
+// 0 p^n halo, 1 D_p, 2 kappa, 3 d kappa, 4 a^n cell box): only the
+// scattered field is advanced; the same bits as the joint step.
+void launch_born_hist_step(const BornArgs &a, int ntiles, const TileMaps &maps, cudaStream_t s);
 int tma_occupancy(int kind, int variant);
 
 struct StepLaunch {
@@ -203,7 +210,9 @@ void launch_born_step(const BornArgs &a, int ntiles, const StepLaunch &L, const 
 // Padded model preparation: kap (and dkap when dv != nullptr) from the
 // physical [nz][nx] model, columns [0, pf) (clamped beyond the model); also
 // checks v (finite, > 0) and records max kappa.
-// status[0] |= 1 for a bad velocity; status[1] = bits of max kappa (float).
+// status[0] |= 1 for a bad velocity; status[1] = bits of max kappa (float);
+// status[8..9] (64-bit, 8-byte aligned, cleared by the caller) += a hash of
+// v's values and positions.
 void launch_prep_model(const float *v, const float *dv, int rel, int nz, int nx, int nb, double c,
                        float *kap, float *dkap, int pf, long long mstride,
                        unsigned *status, cudaStream_t s);

@@ -444,6 +444,7 @@ __global__ void prep_model_kernel(const float *__restrict__ v, const float *__re
     const int i = blockIdx.y;
     float kmax = 0.f;
     bool bad = false;
+    unsigned long long hsum = 0ull;  // identity of v (reuse of a stored forward wavefield)
     if (pc < pf && i < NZ) {
         const int iz = min(max(i - nb, 0), nz - 1);
         // Copy r holds padded-model column pc + r, so that a window starting
@@ -464,16 +465,27 @@ __global__ void prep_model_kernel(const float *__restrict__ v, const float *__re
                               : (float)(2.0 * (double)vv * c * (double)dd);
             }
             if (inside && !bad) kmax = k;
+            // Each physical cell once: SplitMix64 of (index, value bits),
+            // summed mod 2^64 (an order-independent, deterministic total).
+            if (copy == 0 && i >= nb && i < nb + nz && pc >= nb && pc < nb + nx) {
+                unsigned long long z = ((unsigned long long)((long long)iz * nx + ix) << 32) ^ __float_as_uint(vv);
+                z += 0x9E3779B97F4A7C15ull;
+                z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+                z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+                hsum += z ^ (z >> 31);
+            }
         }
     }
-    // Warp reduction of the max and of the bad flag, one atomic per warp.
+    // Warp reduction of the max, the bad flag and the hash, one atomic per warp.
     for (int off = 16; off > 0; off >>= 1) {
         kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
         bad = __any_sync(0xffffffffu, bad);
+        hsum += __shfl_xor_sync(0xffffffffu, hsum, off);
     }
     if ((threadIdx.x & 31) == 0) {
         if (bad) atomicOr(status, 1u);
         atomicMax(status + 1, __float_as_uint(kmax));
+        atomicAdd(reinterpret_cast<unsigned long long *>(status + 8), hsum);
     }
 }
 

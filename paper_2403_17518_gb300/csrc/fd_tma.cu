@@ -320,6 +320,92 @@ __global__ void __launch_bounds__(32 * (TZ / R), NS == 1 ? 2 : 1)
 }
 
 // ---------------------------------------------------------------------------
+// Born step from the forward history: the background term a^n = D u0^n + q^n
+// that the joint step computes from u0 is read from the a^n the forward pass
+// of fwi_gradient / rtm_mig stored at the same model, so only the scattered
+// field p is staged and advanced (p^n with its halo, D_p, kappa, d kappa and
+// the a^n tile by TMA).  The arithmetic on p is the joint step's, in the same
+// order, and the stored a^n has the bits the joint step recomputes, so the
+// records are identical.
+// ---------------------------------------------------------------------------
+struct TmaBornHistStage {
+    STile p;
+    CTile dp, k, dk, a;
+};
+constexpr unsigned kBornHistStageBytes = sizeof(STile) + 4 * sizeof(CTile);
+static_assert(sizeof(TmaBornHistStage) == kBornHistStageBytes, "stage layout");
+constexpr size_t kBornHistSmem = 2 * sizeof(TmaBornHistStage) + sizeof(PipeTail);
+
+template <int R, bool FULL>
+__device__ __forceinline__ void born_hist_rows(const BornArgs &A, const TmaBornHistStage &S, const TileInfo &T,
+                                               int lxp, int lz0) {
+    const int NZ = A.c.NZ;
+    const int j = T.x0 + lxp;
+    const int i0 = T.z0 + lz0;
+    const int nxw = T.nxw, pitch = T.pitch;
+    const long long cbase = T.foff + (long long)i0 * pitch + j;
+    const int nrow = FULL ? R : min(R, NZ - i0);
+    const bool ok = FULL || j < nxw, hi = FULL || j + 1 < nxw;
+    float2 zp[R + 2 * HALO];
+#pragma unroll
+    for (int r = 0; r < R + 2 * HALO; r++) zp[r] = *reinterpret_cast<const float2 *>(&S.p[lz0 + r][lxp + HALO]);
+    float wx0 = 1.f, wx1 = 1.f;
+    if constexpr (!FULL) {
+        wx0 = sponge1(j, nxw, A.c.nb);
+        wx1 = sponge1(j + 1, nxw, A.c.nb);
+    }
+#pragma unroll
+    for (int rr = 0; rr < R; rr++) {
+        if (ok && rr < nrow) {
+            const f2 a0 = pk(*reinterpret_cast<const float2 *>(&S.a[lz0 + rr][lxp]));
+            const f2 ap = lap8x2(S.p, zp + rr, lz0 + rr, lxp);
+            const f2 dpv = pk(*reinterpret_cast<const float2 *>(&S.dp[lz0 + rr][lxp]));
+            const f2 kv = pk(*reinterpret_cast<const float2 *>(&S.k[lz0 + rr][lxp]));
+            const f2 dkv = pk(*reinterpret_cast<const float2 *>(&S.dk[lz0 + rr][lxp]));
+            f2 dp, pn;
+            if constexpr (FULL) {
+                dp = fma2(dkv, a0, fma2(kv, ap, dpv));
+                pn = add2(pk(zp[rr + HALO]), dp);
+            } else {
+                const float wz = sponge1(i0 + rr, NZ, A.c.nb);
+                const f2 w = pk2(wz * wx0, wz * wx1);
+                dp = keep_lo(mul2(w, fma2(dkv, a0, fma2(kv, ap, dpv))), hi);
+                pn = keep_lo(fma2(w, pk(zp[rr + HALO]), dp), hi);
+            }
+            const long long c = cbase + (long long)rr * pitch;
+            *reinterpret_cast<f2 *>(A.dp + c) = dp;
+            *reinterpret_cast<f2 *>(A.pn + c) = pn;
+        }
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * (TZ / R), 1)
+    born_hist_tma_kernel(BornArgs A, const __grid_constant__ TileMaps M, int ntiles) {
+    constexpr int NT = 32 * (TZ / R);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaBornHistStage *st = reinterpret_cast<TmaBornHistStage *>(smem_raw);
+    PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + 2 * sizeof(TmaBornHistStage));
+    const int lxp = 2 * threadIdx.x;
+    const int lz0 = threadIdx.y * R;
+    run_tiles<2>(
+        A.c, kBornHistStageBytes, ntiles, st, tail,
+        [&](TmaBornHistStage &S, unsigned bar, int4 co, int mc) {
+            tma_load_3d(smem_u32(&S.p), &M.m[0], co.z - HALO, co.y - HALO, co.x, bar);
+            tma_load_3d(smem_u32(&S.dp), &M.m[1], co.z, co.y, co.x, bar);
+            tma_load_3d(smem_u32(&S.k), &M.m[2], co.w, co.y, mc, bar);
+            tma_load_3d(smem_u32(&S.dk), &M.m[3], co.w, co.y, mc, bar);
+            tma_load_3d(smem_u32(&S.a), &M.m[4], co.z, co.y, co.x, bar);
+        },
+        [&](const TmaBornHistStage &S, const TileInfo &T) {
+            // The interior path needs no source test: a^n already holds q^n.
+            if (T.flags & TI_INTERIOR) born_hist_rows<R, true>(A, S, T, lxp, lz0);
+            else born_hist_rows<R, false>(A, S, T, lxp, lz0);
+            if (T.rec_end > T.rec_begin) sample_from_pool<NT>(A.c, T, A.pn, A.d, A.n);
+        });
+}
+
+// ---------------------------------------------------------------------------
 // Self-test of the failure path: one warp waits, with the step kernels'
 // bounded wait (~1 s), on an mbarrier that nothing arrives at, and reports
 // the timeout in tflag as they do.  Nothing faults and nothing hangs.
@@ -410,6 +496,18 @@ void launch_born_step_tma(const BornArgs &a, int ntiles, int variant, int grid, 
         break;
     default: launch_pdl(born_tma_kernel<8, 1>, grid, 8, born_smem<1>(), s, a, maps, ntiles); break;
     }
+}
+
+void launch_born_hist_step(const BornArgs &a, int ntiles, const TileMaps &maps, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    static int cap = 0;
+    if (!cap) {
+        int dev = 0, nsm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cap = occupancy((const void *)born_hist_tma_kernel<4>, 32 * (TZ / 4), kBornHistSmem) * nsm;
+    }
+    launch_pdl(born_hist_tma_kernel<4>, ntiles < cap ? ntiles : cap, 4, kBornHistSmem, s, a, maps, ntiles);
 }
 
 void launch_wait_timeout_selftest(unsigned *tflag, cudaStream_t s) {

@@ -156,7 +156,7 @@ int model_shots_static(const dhfwi_grid *g, const float *v_dev, const dhfwi_geom
     const long long mstride = (long long)NZ * pf;
     Carve cv;
     const size_t o_kap = cv.take(sizeof(float) * 4 * mstride);
-    const size_t o_status = cv.take(16);
+    const size_t o_status = cv.take(64);  // the model kernel's status words (0, 1 and the hash at 8-9)
     const size_t o_shots = cv.take(sizeof(ShotDesc) * shots.size());
     const size_t o_tiles = cv.take(sizeof(Tile) * tiles.size());
     const size_t o_recs = cv.take(sizeof(TileRec) * std::max<size_t>(recs.size(), 1));
@@ -186,7 +186,7 @@ int model_shots_static(const dhfwi_grid *g, const float *v_dev, const dhfwi_geom
     SCK(cudaMemcpyAsync(S + o_wav, G->wavelet, sizeof(float) * nwav, cudaMemcpyHostToDevice, st));
     // The array keeps the previous call's contents: clear the status words and
     // the wavefield state, which must start at zero.
-    SCK(cudaMemsetAsync(S + o_status, 0, 16, st));
+    SCK(cudaMemsetAsync(S + o_status, 0, 64, st));
     SCK(cudaMemsetAsync(S + o_u, 0, sizeof(float) * 3 * (size_t)foff, st));
     const double c = ((double)g->dt * g->dt) / ((double)g->h * g->h);
     launch_prep_model(v_dev, nullptr, 0, g->nz, g->nx, nb, c, (float *)(S + o_kap), nullptr, pf, mstride,

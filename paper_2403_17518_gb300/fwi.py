@@ -262,6 +262,7 @@ def main():
     p.add_argument("--patch", type=int, default=64, help="network training patch (128 for config 5)")
     p.add_argument("--cold-epochs", type=int, default=200)
     p.add_argument("--warm-epochs", type=int, default=20)
+    p.add_argument("--no-reuse", action="store_true", help="propagate the background again in Born and migration")
     p.add_argument("--out", default="")
     a = p.parse_args()
     if a.case == "config5":
@@ -277,6 +278,8 @@ def main():
                                       src_hi=a.nx - 11, wavelet=wav)
         case = synth.Case(a.nz, a.nx, a.h, a.dt, 20, v, v0, geom, name="fwi-loop")
     ctx = Context(case.nz, case.nx, case.h, case.dt, case.nb)
+    # Born and migration at the gradient's model take its stored forward pass.
+    ctx.set_reuse(not a.no_reuse)
     net = dict(base_channels=32, levels=4, patch=a.patch, stride=a.patch // 2, batch=32, lr=a.lr, seed=29)
     bands = [float(b) for b in a.bands.split(",")]
     out = {"config": vars(a), "net": net}

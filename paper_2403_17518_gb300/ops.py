@@ -117,6 +117,11 @@ class Context:
     def set_timing(self, on: bool = True):
         self._check(self.lib.dhfwi_set_timing(self.handle, 1 if on else 0))
 
+    def set_reuse(self, on: bool = True):
+        """Reuse the stored forward wavefield in rtm_mig / born_demig at the
+        model and geometry of the last gradient or migration (same bits)."""
+        self._check(self.lib.dhfwi_set_reuse(self.handle, 1 if on else 0))
+
     # -- the calls of the C ABI ------------------------------------------
     def model_shots(self, v: torch.Tensor, geom, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         g = _as_geom(geom)

@@ -192,3 +192,47 @@ def test_case_exercises_the_fast_path_and_padding():
                 if np.any((rz >= z0) & (rz < z0 + TX) & (rx >= x0) & (rx < x0 + TX)):
                     interior_with_rec = True
     assert interior_with_rec
+
+
+@pytest.mark.parametrize("history", ["all", "first-segment", "none"])
+def test_reuse_of_the_forward_pass_is_bitwise(history, reference_variant, monkeypatch):
+    """dhfwi_set_reuse: after a gradient at v0, the migration at v0 skips its
+    forward pass (the history and, beyond it, the checkpoints kept intact by
+    the backward sweep's recompute), and Born at v0 advances only the
+    scattered field when the history holds every step; the same bits as
+    propagating.  At another model nothing is reused."""
+    import torch
+
+    monkeypatch.delenv("DHFWI_STEP_VARIANT", raising=False)
+    monkeypatch.delenv("DHFWI_TIME_BLOCK", raising=False)
+    if history == "all":
+        monkeypatch.delenv("DHFWI_HISTORY_MB", raising=False)
+    else:
+        monkeypatch.setenv("DHFWI_HISTORY_MB", "0" if history == "none" else str(history_cap_mb(CASE, 1)))
+    c = CASE
+    ctx = gpu_ctx(c)
+    ctx.set_reuse(True)
+    geom = f32_geom(c.geom)
+    v, v0 = to_dev(f32(c.v_true)), to_dev(f32(c.v_init))
+    d = ctx.model_shots(v, geom)
+    ds = torch.empty(geom.n_data, dtype=torch.float32, device="cuda")
+    J, g = ctx.fwi_gradient(v0, geom, 0.5 * d, d_syn=ds)
+    b = ctx.born_demig(v0, geom, to_dev(DV))
+    assert ctx.stats()["reused"] == (2 if history == "all" else 0)
+    m = ctx.rtm_mig(v0, geom, 0.5 * d)
+    assert ctx.stats()["reused"] == 1
+    out = {"d": to_host(d), "ds": to_host(ds), "g": to_host(g), "m": to_host(m), "b": to_host(b)}
+    for k in KEYS:
+        np.testing.assert_array_equal(out[k], reference_variant[k], err_msg=k)
+    assert J == reference_variant["J"]
+    # Another model: propagated again (no stale reuse), equal to a fresh context.
+    v1 = v0 + 7.0
+    b1 = to_host(ctx.born_demig(v1, geom, to_dev(DV)))
+    assert ctx.stats()["reused"] == 0
+    m1 = to_host(ctx.rtm_mig(v1, geom, 0.5 * d))
+    assert ctx.stats()["reused"] == 0
+    ctx.close()
+    ref = gpu_ctx(c)
+    np.testing.assert_array_equal(b1, to_host(ref.born_demig(v1, geom, to_dev(DV))))
+    np.testing.assert_array_equal(m1, to_host(ref.rtm_mig(v1, geom, 0.5 * d)))
+    ref.close()
