@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -71,6 +72,15 @@ struct NetState {
     int mute_rows = 0;           // from the last training configuration
     long long adam_t = 0;        // Adam steps of the current training call
     long long launches = 0;
+    // Side stream of the backward pass: a layer's weight gradient runs there,
+    // concurrently with its input gradient on the caller's stream.  ev_ready:
+    // the output gradient g is written (caller -> side); ev_buf[b]: the last
+    // weight gradient reading gradient buffer b (gbuf, gbuf2) is done (side ->
+    // caller, before b is written again); ev_join: every weight gradient of
+    // the pass is done.  DHFWI_NN_OVERLAP=0 keeps everything on one stream.
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_ready = nullptr, ev_buf[2] = {nullptr, nullptr}, ev_join = nullptr;
+    bool use_side = false;  // this backward pass overlaps
 
     // Workspace views (filled by layout()).
     struct Views {
@@ -475,6 +485,40 @@ void forward(NetState &N, int n, int H, int W, cudaStream_t s) {
     N.launches++;
 }
 
+bool overlap_on() {
+    const char *e = getenv("DHFWI_NN_OVERLAP");
+    return !(e && strcmp(e, "0") == 0);
+}
+
+// The stream the weight gradients run on (the side stream when overlapping).
+cudaStream_t wgrad_stream(NetState &N, cudaStream_t s) { return N.use_side ? N.side : s; }
+
+// Index of gradient buffer p (0 gbuf, 1 gbuf2, -1 neither).
+int gbuf_index(const NetState &N, const void *p) {
+    return p == (const void *)N.V.gbuf ? 0 : p == (const void *)N.V.gbuf2 ? 1 : -1;
+}
+
+// Before the caller's stream writes gradient buffer p: wait for the weight
+// gradient that read it last.
+void before_gbuf_write(NetState &N, const void *p, cudaStream_t s) {
+    const int b = gbuf_index(N, p);
+    if (N.use_side && b >= 0) cudaStreamWaitEvent(s, N.ev_buf[b], 0);
+}
+
+// A weight gradient reading g may start: the side stream waits for the
+// caller's stream up to here.
+void fork_wgrad(NetState &N, cudaStream_t s) {
+    if (!N.use_side) return;
+    cudaEventRecord(N.ev_ready, s);
+    cudaStreamWaitEvent(N.side, N.ev_ready, 0);
+}
+
+// After the weight gradient that read g was launched on the side stream.
+void after_wgrad(NetState &N, const void *g) {
+    const int b = gbuf_index(N, g);
+    if (N.use_side && b >= 0) cudaEventRecord(N.ev_buf[b], N.side);
+}
+
 // Backward of one conv + LeakyReLU block: dA (float, dense [P][co]) is the
 // gradient of its output a; x its (bf16) input.  Writes the weight and bias
 // gradients and, when dx != nullptr, the input gradient (float [P][ci]).
@@ -497,10 +541,13 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
     const long long P = (long long)nimg * H * W;
     const __nv_bfloat16 *g = g_in;
     if (!g) {
+        before_gbuf_write(N, N.V.gbuf, s);
         launch_leaky_bwd(dA, a, as, ao, P, d.co, 0.2f, N.V.gbuf, s);
         g = N.V.gbuf;
         N.launches++;
     }
+    fork_wgrad(N, s);
+    const cudaStream_t ws = wgrad_stream(N, s);
     WgradArgs w{};
     w.mode = WG_CONV;
     w.g = g;
@@ -520,11 +567,12 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
     w.err = N.err;
     const int sp = wgrad_splits(P, w.M, w.N);
     float *dw = li == 0 ? N.g0pad : N.grad + d.off;
-    N.launches += launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, s);
+    N.launches += launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, ws);
     if (li == 0) {
-        launch_unpad_first_grad(N.g0pad, d.co, CPAD, N.grad + d.off, s);
+        launch_unpad_first_grad(N.g0pad, d.co, CPAD, N.grad + d.off, ws);
         N.launches++;
     }
+    after_wgrad(N, g);
     if (dx || next.g) {
         FpropArgs a{};
         a.src = g;
@@ -550,6 +598,7 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
         a.part_floats = (long long)N.fp_part_floats;
         a.err = N.err;
         if (next.g) {
+            before_gbuf_write(N, next.g, s);
             a.dst_bf16 = next.g;
             a.act = next.act;
             a.act_stride = next.stride;
@@ -564,7 +613,36 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
     }
 }
 
+// The side stream and its events (created once, on the context's device).
+bool ensure_side(NetState &N) {
+    if (N.side) return true;
+    if (cudaStreamCreateWithFlags(&N.side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        N.side = nullptr;
+        return false;
+    }
+    cudaEvent_t *evs[] = {&N.ev_ready, &N.ev_buf[0], &N.ev_buf[1], &N.ev_join};
+    for (cudaEvent_t *e : evs)
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    return true;
+}
+
+void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s);
+
 void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
+    N.use_side = overlap_on() && ensure_side(N);
+    backward_impl(N, n, H, W, s);
+    if (N.use_side) {  // every weight gradient is done before the caller's stream goes on
+        cudaEventRecord(N.ev_join, N.side);
+        cudaStreamWaitEvent(s, N.ev_join, 0);
+    }
+    N.use_side = false;
+}
+
+void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
     const int Lv = N.levels;
     auto C = [&](int r) { return N.base << r; };
     NetState::Views &V = N.V;
@@ -595,6 +673,7 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         // dA = d(cat) [Pr][2C]: skip half kept, up half to bf16.
         cudaMemsetAsync(V.dskip[r], 0, sizeof(float) * Pr * C(r), s);
         launch_add_slice(dA, 2 * C(r), 0, Pr, C(r), V.dskip[r], s);
+        before_gbuf_write(N, V.gbuf, s);
         launch_f32_to_bf16_slice(dA, 2 * C(r), C(r), Pr, C(r), V.gbuf, s);
         N.launches += 2;
         // Transposed conv: input is the level-(r+1) activation.
@@ -619,7 +698,9 @@ void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
         w.ones = N.ones;
         w.part = N.wg_part;
         const int sp = wgrad_splits((long long)n * Hc * Wc, w.M, w.N);
-        launch_wgrad(w, sp, N.grad + dt.off, N.grad + dt.off + dt.nw, s);
+        fork_wgrad(N, s);
+        launch_wgrad(w, sp, N.grad + dt.off, N.grad + dt.off + dt.nw, wgrad_stream(N, s));
+        after_wgrad(N, V.gbuf);
         FpropArgs a{};
         a.src = V.gbuf;
         a.src_stride = C(r);
@@ -748,6 +829,13 @@ int upload_params(dhfwi_ctx *ctx, NetState &N, const float *host, cudaStream_t s
 
 void net_destroy(NetState *net) {
     if (!net) return;
+    if (net->side) {
+        cudaStreamSynchronize(net->side);
+        cudaStreamDestroy(net->side);
+    }
+    cudaEvent_t evs[] = {net->ev_ready, net->ev_buf[0], net->ev_buf[1], net->ev_join};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
     free_params(*net);
     void *ps[] = {net->arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->ones,
                   net->mx, net->err, net->scales, net->oz, net->ox, net->perm};
