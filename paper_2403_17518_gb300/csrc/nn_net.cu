@@ -51,7 +51,10 @@ struct NetState {
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *w16 = nullptr, *wt16 = nullptr, *w0pad = nullptr;
     float *g0pad = nullptr;
-    // Workspace (device arena) sized for (wsN, wsH, wsW).
+    // Workspace (device arena) sized for (wsN, wsH, wsW); the workspace of
+    // the previous shape is kept as `prev` (training patches and the
+    // full-image apply alternate every FWI iteration), so switching back
+    // allocates nothing.
     int wsN = 0, wsH = 0, wsW = 0;
     char *arena = nullptr;
     size_t arena_bytes = 0;
@@ -90,6 +93,12 @@ struct NetState {
         float *xf, *yf, *out, *dA, *dB;
         std::vector<float *> dskip;
     } V;
+    struct Workspace {
+        int wsN = 0, wsH = 0, wsW = 0;
+        char *arena = nullptr;
+        size_t arena_bytes = 0;
+        Views V;
+    } prev;
 };
 
 namespace {
@@ -262,9 +271,27 @@ void refresh_weights(NetState &N, cudaStream_t s, bool shadow_from_theta) {
     N.launches++;
 }
 
+// Swap the current workspace with the kept one.
+void swap_workspace(NetState &N) {
+    std::swap(N.wsN, N.prev.wsN);
+    std::swap(N.wsH, N.prev.wsH);
+    std::swap(N.wsW, N.prev.wsW);
+    std::swap(N.arena, N.prev.arena);
+    std::swap(N.arena_bytes, N.prev.arena_bytes);
+    std::swap(N.V, N.prev.V);
+}
+
 // Activation / gradient workspace for batches of up to (n, H, W).
 int layout(dhfwi_ctx *ctx, NetState &N, int n, int H, int W) {
     if (N.arena && N.wsN >= n && N.wsH == H && N.wsW == W) return DHFWI_OK;
+    if (N.prev.arena && N.prev.wsN >= n && N.prev.wsH == H && N.prev.wsW == W) {
+        swap_workspace(N);
+        return DHFWI_OK;
+    }
+    // A new shape: the current workspace becomes the kept one.
+    if (N.prev.arena) cudaFree(N.prev.arena);
+    N.prev = NetState::Workspace{};
+    swap_workspace(N);
     const int Lv = N.levels;
     auto P = [&](int r) { return (size_t)n * (size_t)(H >> r) * (size_t)(W >> r); };
     auto C = [&](int r) { return (size_t)N.base << r; };
@@ -801,6 +828,8 @@ int ensure_net(dhfwi_ctx *ctx, int base, int levels) {
         if (net->arena) cudaFree(net->arena);
         net->arena = nullptr;
         net->wsN = net->wsH = net->wsW = 0;
+        if (net->prev.arena) cudaFree(net->prev.arena);
+        net->prev = NetState::Workspace{};
     }
     return ensure_small(ctx, *net);
 }
@@ -837,7 +866,7 @@ void net_destroy(NetState *net) {
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
     free_params(*net);
-    void *ps[] = {net->arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->ones,
+    void *ps[] = {net->arena, net->prev.arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->ones,
                   net->mx, net->err, net->scales, net->oz, net->ox, net->perm};
     for (void *p : ps) dev_free(p);
     delete net;
