@@ -61,6 +61,10 @@ void launch_fprop_umma(const FpropArgs &a, int epi, cudaStream_t s);
 // TMA-fed tcgen05 kernel for the 3x3 convolutions with >= 64 output channels
 // (nn_umma.cu); false when the GEMM is not of that form (nothing launched).
 bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s);
+// tcgen05 3x3 convolution with the input patch staged once for all nine
+// taps (nn_umma.cu), for sources of 32 or 64 channels and at most 128
+// outputs; false when not applicable (nothing launched).
+bool launch_conv3_patch(const FpropArgs &a, int epi, cudaStream_t s);
 // tcgen05 weight gradient of a 3x3 convolution (nn_umma.cu; off with
 // DHFWI_NN_WGRAD=mma or DHFWI_NN_GEMM=mma): the splits it wrote, 0 when not
 // applicable.

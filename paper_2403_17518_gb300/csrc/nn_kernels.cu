@@ -1217,7 +1217,7 @@ void launch_fprop(const FpropArgs &a, int epi, cudaStream_t s) {
         launch_fprop_umma(a, epi, s);
         return;
     }
-    if (mode == GEMM_DEFAULT && launch_conv3_tma(a, epi, s)) return;
+    if (mode == GEMM_DEFAULT && (launch_conv3_patch(a, epi, s) || launch_conv3_tma(a, epi, s))) return;
     int bh_n, bw_n, nimg;
     if (halo_eligible(a, epi, &bh_n, &bw_n, &nimg)) {
         switch (epi) {

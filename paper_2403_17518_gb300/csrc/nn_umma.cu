@@ -828,6 +828,173 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 3x3 convolution with the input patch reused by all nine taps, for
+// sources of 32 or 64 channels (the network's top levels, where a TMA box
+// per tap re-reads the input nine times in 16-byte rows).  Output tile: 16
+// rows x 8 columns of one image (128 pixels = the MMA's M), BN output
+// channels.  The 18 x 10 input patch (the tile plus the 1-pixel ring) is
+// staged once, channel-chunk-major: chunk c (8 channels, 16 B per pixel)
+// holds the 180 pixels row after row.  For tap (dh, dw) the A operand is the
+// patch window starting at pixel (1 + dh, 1 + dw): in the no-swizzle K-major
+// layout its 8-row core matrices are the 8 pixels of one tile row, 16 B
+// apart, the next tile row 10 pixels (160 B) further (stride-byte offset),
+// the next 8 channels one chunk (2880 B) further (leading-byte offset); so
+// one MMA per (tap, 16 channels) reads the shifted window in place.  The
+// weights B^T [N][9 C] are staged as [k-chunk][n][8] (leading-byte offset
+// 16 BN, stride-byte offset 128).  Loads: 16-byte cp.async by all threads
+// with zero fill outside the grid (the padding); one thread issues the
+// 9 C / 16 MMAs and commits them; the epilogue is conv_tile_epilogue's.
+// The wait for the MMAs is bounded (~1 s) as in the other kernels.
+// ---------------------------------------------------------------------------
+constexpr int PT_H = 16, PT_W = 8, PP_H = PT_H + 2, PP_W = PT_W + 2, PP = PP_H * PP_W;  // 18 x 10 patch
+
+template <int BN, int C>
+constexpr size_t patch_smem() {
+    return (size_t)(C / 8) * PP * 16 + (size_t)BN * 9 * C * 2 + 1024;  // + barrier, TMEM address, alignment
+}
+
+template <int BN, int C, int EPI>
+__global__ void __launch_bounds__(128) conv3_patch_umma_kernel(FpropArgs P, ConvTile G) {
+    constexpr int CH = C / 8;                           // 16-byte channel chunks
+    constexpr unsigned CHUNK = PP * 16;                 // bytes of one chunk of the patch
+    constexpr unsigned A_BYTES = CH * CHUNK, B_CH = BN * 16;
+    constexpr int K = 9 * C;
+    constexpr unsigned TMEM_COLS = BN < 32 ? 32 : BN;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    const unsigned sa = (smem_u32(smraw) + 127u) & ~127u;
+    const unsigned sb = sa + ((A_BYTES + 127u) & ~127u);
+    unsigned char *tail = smraw + (sb - smem_u32(smraw)) + (size_t)(K / 8) * B_CH;
+    const unsigned bar = smem_u32(tail);
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(tail + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int t = blockIdx.x;
+    const int w0 = (t % G.tw) * PT_W;
+    t /= G.tw;
+    const int h0 = (t % G.th) * PT_H;
+    const int i0 = t / G.th;
+    const int n0 = blockIdx.y * BN;
+
+    if (tid == 0) {
+        mbar_init1(bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // The patch (zero outside the image) and the weights.
+    for (int idx = tid; idx < CH * PP; idx += 128) {
+        const int c = idx / PP, pix = idx - c * PP;
+        const int hs = h0 - 1 + pix / PP_W, ws = w0 - 1 + pix % PP_W;
+        const bool ok = hs >= 0 && hs < P.Hs && ws >= 0 && ws < P.Ws;
+        const __nv_bfloat16 *src =
+            ok ? P.src + (((long long)i0 * P.Hs + hs) * P.Ws + ws) * P.src_stride + P.src_off + 8 * c : P.src;
+        cp16(sa + c * CHUNK + pix * 16, src, ok);
+    }
+    for (int idx = tid; idx < (K / 8) * BN; idx += 128) {
+        const int kc = idx / BN, n = idx - kc * BN;
+        const bool ok = n0 + n < P.N;
+        cp16(sb + kc * B_CH + n * 16, ok ? P.bt + (long long)(n0 + n) * K + 8 * kc : P.bt, ok);
+    }
+    cp_commit();
+    cp_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // cp.async data -> tensor-core reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+    if (tid == 0) {
+        constexpr uint32_t IDESC = idesc_bf16(UBM, BN);
+        int q = 0;
+#pragma unroll 1
+        for (int tap = 0; tap < 9; tap++) {
+            const unsigned off = (unsigned)(((1 + P.dh[tap]) * PP_W + 1 + P.dw[tap]) * 16);
+#pragma unroll
+            for (int kk = 0; kk < C / 16; kk++, q++) {
+                const uint64_t da = smem_desc(sa + 2 * kk * CHUNK + off, CHUNK, PP_W * 16);
+                const uint64_t db = smem_desc(sb + (tap * (C / 8) + 2 * kk) * B_CH, B_CH, 128);
+                mma_bf16(tmem, da, db, IDESC, q > 0 ? 1u : 0u);
+            }
+        }
+        mma_commit(bar);
+    }
+    const bool good = mbar_wait(bar, 0);
+    tc_fence_after();
+    if (!__syncthreads_and(good)) {
+        if (tid == 0 && P.err) atomicExch(P.err, 1u);
+    } else {
+        conv_tile_epilogue<BN, EPI>(P, G, tmem, warp, lane, i0, h0, w0, n0, 1, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+template <int BN, int C, int EPI>
+void patch_launch(const FpropArgs &a, const ConvTile &G, cudaStream_t s) {
+    const size_t sm = patch_smem<BN, C>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(conv3_patch_umma_kernel<BN, C, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    dim3 grid(G.tw * G.th * G.nimg, (a.N + BN - 1) / BN);
+    conv3_patch_umma_kernel<BN, C, EPI><<<grid, 128, sm, s>>>(a, G);
+}
+
+template <int EPI>
+bool patch_dispatch(const FpropArgs &a, const ConvTile &G, cudaStream_t s) {
+    switch (a.C) {
+    case 32: a.N <= 32 ? patch_launch<32, 32, EPI>(a, G, s) : patch_launch<64, 32, EPI>(a, G, s); return true;
+    case 64: a.N <= 32 ? patch_launch<32, 64, EPI>(a, G, s) : patch_launch<64, 64, EPI>(a, G, s); return true;
+    default: return false;
+    }
+}
+
+}  // namespace
+
+// The patch kernel serves a 3x3 convolution (stride 1, shifts in {-1, 0, 1},
+// same grid in and out) whose source has 32 or 64 channels (a 16-byte
+// aligned slice) and whose output has 16..128 channels (N-tiles of 32 / 64);
+// DHFWI_NN_PATCH=0 turns it off.  Returns false (nothing launched) otherwise.
+bool launch_conv3_patch(const FpropArgs &a, int epi, cudaStream_t s) {
+    const char *e = getenv("DHFWI_NN_PATCH");
+    if (e && strcmp(e, "0") == 0) return false;
+    if (epi == EPI_BF16_CONVT || a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws) return false;
+    if ((a.C != 32 && a.C != 64) || a.N < 16 || a.N > 128) return false;
+    if (((a.src_stride | a.src_off) & 7) != 0) return false;
+    if (((uintptr_t)(a.src + a.src_off) & 15) != 0 || ((uintptr_t)a.bt & 15) != 0) return false;
+    for (int t = 0; t < 9; t++)
+        if (a.dh[t] < -1 || a.dh[t] > 1 || a.dw[t] < -1 || a.dw[t] > 1) return false;
+    const long long HW = (long long)a.Ho * a.Wo;
+    if (HW <= 0 || a.M % HW != 0) return false;
+    ConvTile G{};
+    G.nimg = (int)(a.M / HW);
+    G.BW = PT_W;
+    G.BH = PT_H;
+    G.BI = 1;
+    G.tw = (a.Wo + PT_W - 1) / PT_W;
+    G.th = (a.Ho + PT_H - 1) / PT_H;
+    if ((long long)G.tw * G.th * G.nimg >= (1LL << 31)) return false;
+    FpropArgs b = a;
+    b.part = nullptr;  // the whole K in one tile: no split
+    switch (epi) {
+    case EPI_BF16_LEAKY: return patch_dispatch<EPI_BF16_LEAKY>(b, G, s);
+    case EPI_BF16: return patch_dispatch<EPI_BF16>(b, G, s);
+    case EPI_F32: return patch_dispatch<EPI_F32>(b, G, s);
+    case EPI_BF16_LEAKYBWD: return patch_dispatch<EPI_BF16_LEAKYBWD>(b, G, s);
+    case EPI_F32_ADD: return patch_dispatch<EPI_F32_ADD>(b, G, s);
+    default: return false;
+    }
+}
+
+namespace {
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);

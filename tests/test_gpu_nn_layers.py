@@ -10,8 +10,9 @@ the GPU in float32.  The shapes reach every GEMM path the network runs: the
 the tcgen05 kernels for >= 64 output channels (32- and 64-channel sources),
 the split-k paths of the deepest levels, M tails (pixel counts that are not a
 multiple of the 128-row tile) and the transposed convolutions; each case runs
-under every GEMM selection (the default choice, the one-tile-per-CTA and the
-persistent tcgen05 convolutions forced, DHFWI_NN_GEMM "mma" and "tc").
+under every GEMM selection (the default choice, without the patch kernel,
+the one-tile-per-CTA and the persistent TMA-fed convolutions forced,
+DHFWI_NN_GEMM "mma" and "tc").
 """
 import math
 
@@ -42,8 +43,9 @@ CONVT = [
     (128, 64, 3, 5, 7),
     (64, 32, 2, 8, 12),
 ]
-# tile / persistent: the one-tile-per-CTA or the persistent tcgen05 conv kernel forced (DHFWI_NN_CONV)
-MODES = ["default", "tile", "persistent", "mma", "tc"]
+# nopatch: without the patch-reuse tcgen05 kernel (DHFWI_NN_PATCH=0); tile / persistent: also the
+# one-tile-per-CTA or the persistent TMA-fed tcgen05 conv kernel forced (DHFWI_NN_CONV)
+MODES = ["default", "nopatch", "tile", "persistent", "mma", "tc"]
 
 
 def _data(seed, kind, ci, co, n, H, W):
@@ -85,9 +87,12 @@ def _run(monkeypatch, mode, kind, shape, seed):
     import torch
 
     monkeypatch.delenv("DHFWI_NN_CONV", raising=False)
-    if mode in ("default", "tile", "persistent"):
+    monkeypatch.delenv("DHFWI_NN_PATCH", raising=False)
+    if mode in ("default", "nopatch", "tile", "persistent"):
         monkeypatch.delenv("DHFWI_NN_GEMM", raising=False)
         if mode != "default":
+            monkeypatch.setenv("DHFWI_NN_PATCH", "0")
+        if mode in ("tile", "persistent"):
             monkeypatch.setenv("DHFWI_NN_CONV", mode)
     else:
         monkeypatch.setenv("DHFWI_NN_GEMM", mode)
