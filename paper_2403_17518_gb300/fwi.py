@@ -97,15 +97,26 @@ def parabolic_alpha(J0: float, J1: float, J2: float, a1: float):
     return a_best, improved
 
 
+BACKTRACK = 8.0  # the second round of trials is this many times shorter
+
+
 def line_search(ctx, v, dirn, ga, d_obs, d_try, trial, J0, a1, vmin, vmax, mute_rows):
-    """Two-trial parabolic line search on the misfit along -dirn; returns
-    (alpha, whether a trial lowered the misfit)."""
-    Js = []
-    for a in (a1, 2 * a1):
-        ctx.fwi_update(v, dirn, a, vmin, vmax, mute_rows, out=trial)
-        ctx.model_shots(trial, ga, out=d_try)
-        Js.append(ctx.data_misfit(d_try, d_obs))
-    return parabolic_alpha(J0, Js[0], Js[1], a1)
+    """Two-trial parabolic line search on the misfit along -dirn, with one
+    backtracking round: when neither a1 nor 2 a1 lowers the misfit, the
+    trials a1 / BACKTRACK and 2 a1 / BACKTRACK are tried.  Returns (alpha,
+    whether a trial lowered the misfit, forward solves spent)."""
+    solves = 0
+    for b1 in (a1, a1 / BACKTRACK):
+        Js = []
+        for a in (b1, 2 * b1):
+            ctx.fwi_update(v, dirn, a, vmin, vmax, mute_rows, out=trial)
+            ctx.model_shots(trial, ga, out=d_try)
+            Js.append(ctx.data_misfit(d_try, d_obs))
+        solves += 2
+        alpha, ok = parabolic_alpha(J0, Js[0], Js[1], b1)
+        if ok:
+            return alpha, True, solves
+    return 0.0, False, solves
 
 
 class BandData:
@@ -163,6 +174,7 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
                 J0, _ = ctx.fwi_gradient(v, ga, d_obs, grad=grad)
                 a1 = 0.01 * float(np.mean(case.v_init))
                 fallback = False
+                stalled = False
                 loss = None
                 solves += 2  # forward + adjoint of the gradient (checkpoint recomputation not counted)
                 if use_net:
@@ -175,18 +187,19 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
                     trained_in_band = True
                     loss = [float(h[0]), float(h[-1])]
                     ctx.deblur_apply(grad, out=direction)
-                    a_best, ok = line_search(ctx, v, direction, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
-                                             mute_rows)
-                    solves += 2
+                    a_best, ok, ns = line_search(ctx, v, direction, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
+                                                 mute_rows)
+                    solves += ns
                     dirn = direction
                     if not ok:
-                        solves += 2
                         # The plain gradient is the fallback when the network's
                         # direction does not lower the misfit.
                         fallback = True
                         dirn = grad
-                        a_best, _ = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
-                                                mute_rows)
+                        a_best, ok, ns = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
+                                                     mute_rows)
+                        solves += ns
+                    stalled = not ok
                 else:
                     dirn = grad
                     alpha_bb = 0.0
@@ -197,9 +210,10 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
                         alpha_bb, gmax = ctx.bb_step(v, v_prev, grad, g_prev, mute_rows)
                         a_best = min(alpha_bb * gmax, 4 * a1)
                     if alpha_bb <= 0.0:  # no curvature estimate yet (or a negative one): line search
-                        a_best, _ = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
-                                                mute_rows)
-                        solves += 2
+                        a_best, ok, ns = line_search(ctx, v, grad, ga, d_obs, d_try, trial, J0, a1, vmin, vmax,
+                                                     mute_rows)
+                        solves += ns
+                        stalled = not ok
                 if mode == "bb":
                     v_prev.copy_(v)
                     g_prev.copy_(grad)
@@ -208,10 +222,14 @@ def run_arm(ctx: Context, case, mode: str, bands, iters: int, net_cfg: dict, col
             done_iters += 1
             rec = {"band": fc, "iter": it + 1, "gpu_s": timer.seconds(), "solves": solves,
                    "model_rms": model_rms(v, v_true), "net": use_net,
-                   "misfit": J0, "alpha": a_best, "fallback": fallback, "train_loss": loss}
+                   "misfit": J0, "alpha": a_best, "fallback": fallback, "train_loss": loss, "stalled": stalled}
             hist.append(rec)
             if log:
                 log(mode, rec)
+            if stalled:
+                # No step lowers the misfit even after backtracking: the next
+                # iteration would repeat this one exactly, so the band ends.
+                break
     return hist
 
 

@@ -175,8 +175,34 @@ def test_network_direction_that_raises_the_misfit_falls_back_to_the_gradient():
     hist, calls = _run("deblur", iters=1, bands=(12.0,), bad_network=True)
     r = hist[1]
     assert r["fallback"] and r["alpha"] > 0
-    # gradient 2 + Born pair 2 + failed line search 2 + gradient line search 2
-    assert r["solves"] == 8 and calls["data_misfit"] == 4
+    # gradient 2 + Born pair 2 + failed line search 2 and its backtracking
+    # round 2 + gradient line search 2
+    assert r["solves"] == 10 and calls["data_misfit"] == 6 and not r["stalled"]
+
+
+class NoDescentContext(FakeContext):
+    """Every line-search trial raises the misfit."""
+
+    def data_misfit(self, a, b):
+        self._count("data_misfit")
+        return 1e30
+
+
+def test_a_stalled_band_ends():
+    """When no trial, nor a backtracked one, lowers the misfit the iteration
+    takes no step and its band ends (the next iteration would repeat it
+    exactly)."""
+    from paper_2403_17518_gb300.fwi import run_arm
+
+    c = _case()
+    ctx = NoDescentContext(c)
+    hist = run_arm(ctx, c, "plain", [12.0, 20.0], 5, dict(base_channels=8), 3, 1, 1500.0, 2600.0, mute_rows=1,
+                   timer=CpuTimer())
+    assert [r["band"] for r in hist[1:]] == [12.0, 20.0]
+    assert all(r["stalled"] and r["alpha"] == 0.0 for r in hist[1:])
+    assert hist[1]["model_rms"] == hist[0]["model_rms"]
+    # gradient 2 + two rounds of trials 4 per band
+    assert [r["solves"] for r in hist[1:]] == [6, 12] and ctx.calls["data_misfit"] == 8
 
 
 def test_hybrid_arm_switches_to_the_gradient():
