@@ -85,6 +85,26 @@ struct NetState {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_ready = nullptr, ev_buf[2] = {nullptr, nullptr}, ev_join = nullptr;
     bool use_side = false;  // this backward pass overlaps
+    bool buf_rec[2] = {false, false};  // ev_buf[b] recorded in this backward pass
+
+    // CUDA graphs of the fixed-shape passes (a training step's forward, loss
+    // and backward; the forward of an apply): a pass seen once eagerly for a
+    // (kind, batch, shape, workspace, GEMM switches) key is captured the
+    // second time and replayed from then on as one graph launch.  Every
+    // buffer a graph touches belongs to the network state (the workspace
+    // arena, parameters, partials); drop_graphs() runs whenever one of them
+    // is reallocated.  DHFWI_NN_GRAPH=0 keeps every pass eager.
+    struct PassGraph {
+        int kind = 0, n = 0, H = 0, W = 0;
+        const char *arena = nullptr;
+        std::string env;
+        int seen = 0;
+        bool failed = false;
+        cudaGraphExec_t exec = nullptr;
+        long long launches = 0;  // kernel launches (and copies) one replay stands for
+    };
+    std::vector<PassGraph> graphs;
+    cudaStream_t cap = nullptr;  // capture stream (the caller's may be the legacy default stream)
 
     // Workspace views (filled by layout()).
     struct Views {
@@ -103,6 +123,8 @@ struct NetState {
 };
 
 namespace {
+
+void drop_graphs(NetState &N);
 
 int layer_index_down(const NetState &N, int l, int j) { return 2 + 2 * (l - 1) + j; }
 int layer_index_up(const NetState &N, int l, int j) { return 2 + 2 * N.levels + 3 * (l - 1) + j; }  // j: 0 t, 1 c0, 2 c1
@@ -290,6 +312,7 @@ int layout(dhfwi_ctx *ctx, NetState &N, int n, int H, int W) {
         return DHFWI_OK;
     }
     // A new shape: the current workspace becomes the kept one.
+    drop_graphs(N);
     if (N.prev.arena) cudaFree(N.prev.arena);
     N.prev = NetState::Workspace{};
     swap_workspace(N);
@@ -530,7 +553,9 @@ int gbuf_index(const NetState &N, const void *p) {
 // gradient that read it last.
 void before_gbuf_write(NetState &N, const void *p, cudaStream_t s) {
     const int b = gbuf_index(N, p);
-    if (N.use_side && b >= 0) cudaStreamWaitEvent(s, N.ev_buf[b], 0);
+    // Only an event of this pass: the previous pass's weight gradients were
+    // joined at its end (and a captured pass may wait on no outside event).
+    if (N.use_side && b >= 0 && N.buf_rec[b]) cudaStreamWaitEvent(s, N.ev_buf[b], 0);
 }
 
 // A weight gradient reading g may start: the side stream waits for the
@@ -544,7 +569,10 @@ void fork_wgrad(NetState &N, cudaStream_t s) {
 // After the weight gradient that read g was launched on the side stream.
 void after_wgrad(NetState &N, const void *g) {
     const int b = gbuf_index(N, g);
-    if (N.use_side && b >= 0) cudaEventRecord(N.ev_buf[b], N.side);
+    if (N.use_side && b >= 0) {
+        cudaEventRecord(N.ev_buf[b], N.side);
+        N.buf_rec[b] = true;
+    }
 }
 
 // Backward of one conv + LeakyReLU block: dA (float, dense [P][co]) is the
@@ -663,6 +691,7 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s);
 
 void backward(NetState &N, int n, int H, int W, cudaStream_t s) {
     N.use_side = overlap_on() && ensure_side(N);
+    N.buf_rec[0] = N.buf_rec[1] = false;
     backward_impl(N, n, H, W, s);
     if (N.use_side) {  // every weight gradient is done before the caller's stream goes on
         cudaEventRecord(N.ev_join, N.side);
@@ -798,6 +827,98 @@ void loss(NetState &N, int n, int H, int W, cudaStream_t s) {
     N.launches++;
 }
 
+void drop_graphs(NetState &N) {
+    for (NetState::PassGraph &g : N.graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    N.graphs.clear();
+}
+
+bool graphs_on() {
+    const char *e = getenv("DHFWI_NN_GRAPH");
+    return !(e && strcmp(e, "0") == 0);
+}
+
+// The switches that change which kernels a pass launches.
+std::string gemm_switches() {
+    static const char *names[] = {"DHFWI_NN_GEMM",  "DHFWI_NN_WGRAD",   "DHFWI_NN_CONV",        "DHFWI_NN_PATCH",
+                                  "DHFWI_NN_HALO",  "DHFWI_NN_CONVT",   "DHFWI_NN_WGRAD_FIXUP", "DHFWI_NN_OVERLAP"};
+    std::string k;
+    for (const char *n : names) {
+        const char *e = getenv(n);
+        k += e ? e : "-";
+        k += '|';
+    }
+    return k;
+}
+
+enum { PASS_TRAIN = 0, PASS_FORWARD = 1 };
+
+void pass_eager(NetState &N, int kind, int n, int H, int W, cudaStream_t s) {
+    forward(N, n, H, W, s);
+    if (kind == PASS_TRAIN) {
+        loss(N, n, H, W, s);
+        backward(N, n, H, W, s);
+    }
+}
+
+// One pass of the given kind on the current workspace (see PassGraph).
+// Returns a CUDA error of the capture or the launch (cudaSuccess after an
+// eager run; a capture that fails marks its key eager for good).
+cudaError_t run_pass(NetState &N, int kind, int n, int H, int W, cudaStream_t s) {
+    if (!graphs_on()) {
+        pass_eager(N, kind, n, H, W, s);
+        return cudaSuccess;
+    }
+    const std::string env = gemm_switches();
+    NetState::PassGraph *g = nullptr;
+    for (NetState::PassGraph &e : N.graphs)
+        if (e.kind == kind && e.n == n && e.H == H && e.W == W && e.arena == N.arena && e.env == env) g = &e;
+    if (!g) {
+        if (N.graphs.size() >= 16) drop_graphs(N);
+        N.graphs.emplace_back();
+        g = &N.graphs.back();
+        g->kind = kind;
+        g->n = n;
+        g->H = H;
+        g->W = W;
+        g->arena = N.arena;
+        g->env = env;
+    }
+    if (g->failed || g->seen++ == 0) {  // first sighting: eager (lazy attributes, streams and events settle)
+        pass_eager(N, kind, n, H, W, s);
+        return cudaSuccess;
+    }
+    if (!g->exec) {
+        if (!N.cap && cudaStreamCreateWithFlags(&N.cap, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            N.cap = nullptr;
+            g->failed = true;
+            pass_eager(N, kind, n, H, W, s);
+            return cudaSuccess;
+        }
+        const long long l0 = N.launches;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(N.cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            pass_eager(N, kind, n, H, W, N.cap);
+            e = cudaStreamEndCapture(N.cap, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        g->launches = N.launches - l0;
+        N.launches = l0;
+        if (e != cudaSuccess) {  // nothing of the captured pass ran: run it eagerly
+            cudaGetLastError();
+            g->exec = nullptr;
+            g->failed = true;
+            pass_eager(N, kind, n, H, W, s);
+            return cudaSuccess;
+        }
+    }
+    N.launches += g->launches;
+    return cudaGraphLaunch(g->exec, s);
+}
+
 int ensure_small(dhfwi_ctx *ctx, NetState &N) {
     int rc;
     if (!N.mse_part && (rc = dev_alloc(ctx, (void **)&N.mse_part, sizeof(double) * MSE_BLOCKS))) return rc;
@@ -827,6 +948,7 @@ int ensure_net(dhfwi_ctx *ctx, int base, int levels) {
         return fail(ctx, DHFWI_ERR_ARG, "network needs base_channels a multiple of 8 (>= 8) and 1 <= levels <= 6");
     if (!net) net = new NetState();
     if (net->base != base || net->levels != levels || !net->theta) {
+        drop_graphs(*net);
         build_layers(*net, base, levels);
         int rc = alloc_params(ctx, *net);
         if (rc) return rc;
@@ -864,6 +986,8 @@ int upload_params(dhfwi_ctx *ctx, NetState &N, const float *host, cudaStream_t s
 
 void net_destroy(NetState *net) {
     if (!net) return;
+    drop_graphs(*net);
+    if (net->cap) cudaStreamDestroy(net->cap);
     if (net->side) {
         cudaStreamSynchronize(net->side);
         cudaStreamDestroy(net->side);
@@ -938,7 +1062,7 @@ int deblur_forward(dhfwi_ctx *ctx, const float *x_dev, int n, int h, int w, floa
     if (rc) return rc;
     const size_t P = (size_t)n * h * w;
     NCK(cudaMemcpyAsync(net->V.xf, x_dev, 4 * P, cudaMemcpyDeviceToDevice, s));
-    forward(*net, n, h, w, s);
+    NCK(run_pass(*net, PASS_FORWARD, n, h, w, s));
     NCK(cudaMemcpyAsync(out_dev, net->V.out, 4 * P, cudaMemcpyDeviceToDevice, s));
     NCK(cudaGetLastError());
     ctx_count_launches(ctx, net->launches);
@@ -963,9 +1087,7 @@ int deblur_grad(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int n, i
     const size_t P = (size_t)n * h * w;
     NCK(cudaMemcpyAsync(net->V.xf, x_dev, 4 * P, cudaMemcpyDeviceToDevice, s));
     NCK(cudaMemcpyAsync(net->V.yf, y_dev, 4 * P, cudaMemcpyDeviceToDevice, s));
-    forward(*net, n, h, w, s);
-    loss(*net, n, h, w, s);
-    backward(*net, n, h, w, s);
+    NCK(run_pass(*net, PASS_TRAIN, n, h, w, s));
     NCK(cudaMemcpyAsync(grad_dev, net->grad, 4 * (size_t)net->nparams, cudaMemcpyDeviceToDevice, s));
     if (loss_out) {
         double part[MSE_BLOCKS];
@@ -1081,10 +1203,8 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
                 launch_gather_patches(y_dev, nx, N.oz, N.ox, sel, cnt, p, N.scales + 2, N.mute_rows, N.V.yf, s);
                 N.launches += 2;
             }
-            forward(N, cnt, sh, sw, s);
-            loss(N, cnt, sh, sw, s);
+            NCK(run_pass(N, PASS_TRAIN, cnt, sh, sw, s));  // forward, loss, backward
             launch_loss_accum(N.mse_part, MSE_BLOCKS, (double)cnt / ((double)cnt * sh * sw), N.loss_acc + e, s);
-            backward(N, cnt, sh, sw, s);
             double lr = 0.5 * cfg->lr * (1.0 + std::cos(M_PI * (double)t / (double)T));
             if (warm_n > 0 && t < warm_n) lr *= (double)(t + 1) / (double)warm_n;
             N.adam_t++;
@@ -1288,7 +1408,7 @@ int deblur_apply(dhfwi_ctx *ctx, const float *g_dev, int nz, int nx, float *out_
     const long long moff = (long long)mute * nx;
     launch_absmax(g_dev + moff, (long long)nz * nx - moff, N.mx, N.scales, s);
     launch_pad_image(g_dev, nz, nx, Hp, Wp, N.scales, mute, N.V.xf, s);
-    forward(N, 1, Hp, Wp, s);
+    NCK(run_pass(N, PASS_FORWARD, 1, Hp, Wp, s));
     launch_crop_image(N.V.out, Hp, Wp, nz, nx, N.scales + 1, out_dev, s);
     N.launches += 5;
     NCK(cudaGetLastError());

@@ -166,6 +166,37 @@ def test_training_parity_base32():
     assert rel_l2(out, ref) <= 1e-2
 
 
+@pytest.mark.parametrize("overlap", ["1", "0"])
+def test_graph_replay_is_bitwise_eager(overlap, monkeypatch):
+    """A pass is run eagerly the first time its shape is seen, captured into a
+    CUDA graph the second time and replayed after: training (two batch
+    sizes: 40 patches in batches of 12 leave a tail of 4), the full-image
+    apply and the gradient give the same bits as with every pass eager
+    (DHFWI_NN_GRAPH=0), with and without the side stream of the weight
+    gradients."""
+    from scipy.ndimage import gaussian_filter
+
+    monkeypatch.setenv("DHFWI_NN_OVERLAP", overlap)
+    g = np.random.Generator(np.random.PCG64(41))
+    img = np.cumsum(g.standard_normal((80, 176)), axis=1)
+    x = gaussian_filter(img, 2.0).astype(np.float32)
+    y = img.astype(np.float32)
+    kw = dict(base_channels=32, levels=4, patch=32, stride=16, batch=12, lr=1e-3, seed=6)
+    res = {}
+    for graph in ("1", "0"):
+        monkeypatch.setenv("DHFWI_NN_GRAPH", graph)
+        ctx = _ctx()
+        hist = ctx.deblur_train(_dev(x), _dev(y), warm_start=False, epochs=4, **kw)
+        outs = [ctx.deblur_apply(_dev(y)).cpu().numpy() for _ in range(3)]
+        grads = [ctx.deblur_grad(_dev(x[:64, :64].reshape(1, 64, 64)), _dev(y[:64, :64].reshape(1, 64, 64)))
+                 for _ in range(3)]
+        res[graph] = (np.asarray(hist), ctx.net_get(), outs, [(l, gr.cpu().numpy()) for l, gr in grads])
+    (h1, w1, o1, g1), (h0, w0, o0, g0) = res["1"], res["0"]
+    assert np.array_equal(h1, h0) and np.array_equal(w1, w0)
+    assert all(np.array_equal(a, b) for a, b in zip(o1, o0))
+    assert all(l1 == l0 and np.array_equal(a, b) for (l1, a), (l0, b) in zip(g1, g0))
+
+
 @pytest.mark.parametrize("base,levels,shape,epochs,lr", [(8, 2, (38, 70), 4, 1e-2), (128, 4, (30, 40), 2, 1e-4)],
                          ids=["base8", "paper-size-base128"])
 def test_full_image_training_parity(base, levels, shape, epochs, lr):
