@@ -957,15 +957,21 @@ bool patch_dispatch(const FpropArgs &a, const ConvTile &G, cudaStream_t s) {
     }
 }
 
+bool launch_conv3_patch_persistent(const FpropArgs &a, const ConvTile &G, int epi, int mode, cudaStream_t s);
+
 }  // namespace
 
 // The patch kernel serves a 3x3 convolution (stride 1, shifts in {-1, 0, 1},
 // same grid in and out) whose source has 32 or 64 channels (a 16-byte
-// aligned slice) and whose output has 16..128 channels (N-tiles of 32 / 64);
-// DHFWI_NN_PATCH=0 turns it off.  Returns false (nothing launched) otherwise.
+// aligned slice) and whose output has 16..128 channels (N-tiles of 32 / 64):
+// the persistent form from two waves of tiles on, else one tile per CTA.
+// DHFWI_NN_PATCH=0 turns both off, =tile keeps the one-tile kernel,
+// =persistent forces the persistent one on a small grid.  Returns false
+// (nothing launched) when not applicable.
 bool launch_conv3_patch(const FpropArgs &a, int epi, cudaStream_t s) {
     const char *e = getenv("DHFWI_NN_PATCH");
     if (e && strcmp(e, "0") == 0) return false;
+    const int pmode = e && strcmp(e, "tile") == 0 ? 0 : e && strcmp(e, "persistent") == 0 ? 1 : 2;
     if (epi == EPI_BF16_CONVT || a.ntaps != 9 || a.scale != 1 || a.Ho != a.Hs || a.Wo != a.Ws) return false;
     if ((a.C != 32 && a.C != 64) || a.N < 16 || a.N > 128) return false;
     if (((a.src_stride | a.src_off) & 7) != 0) return false;
@@ -984,6 +990,7 @@ bool launch_conv3_patch(const FpropArgs &a, int epi, cudaStream_t s) {
     if ((long long)G.tw * G.th * G.nimg >= (1LL << 31)) return false;
     FpropArgs b = a;
     b.part = nullptr;  // the whole K in one tile: no split
+    if (pmode != 0 && launch_conv3_patch_persistent(b, G, epi, pmode, s)) return true;
     switch (epi) {
     case EPI_BF16_LEAKY: return patch_dispatch<EPI_BF16_LEAKY>(b, G, s);
     case EPI_BF16: return patch_dispatch<EPI_BF16>(b, G, s);
@@ -1142,6 +1149,251 @@ bool conv3_persistent_launch(const FpropArgs &a, const ConvTile &G0, cudaStream_
     conv3_tma_persistent_kernel<BN, BK, ST, EPI><<<grid, TMA_THREADS, sm, s>>>(b, ma, mb, G, mt, ntn, splits);
     if (splits > 1) launch_fprop_reduce(b, EPI, splits, s);
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of conv3_patch_umma_kernel (3x3 convolutions of 32- or
+// 64-channel sources over many 16 x 8 output tiles, e.g. the top level of a
+// batch of 128 x 128 patches): the weights of the CTA's BN output channels
+// are staged once; the 18 x 10 input patches of its tiles (tile t =
+// blockIdx.x, blockIdx.x + gridDim.x, ...) stream through a ring of ST
+// stages, each patch as C / 8 TMA boxes (8 channels x 10 x 18 pixels, zero
+// outside the image; one box = one 16-byte channel chunk of the patch,
+// chunks 2944 B apart so that every box lands 128-byte aligned); and the
+// accumulator is double-buffered in TMEM so that the epilogue of tile j
+// overlaps the MMAs of tile j + 1 and the loads of the tiles after it.
+// Roles and hand-off as in conv3_tma_persistent_kernel (warp 0 loads, warp
+// 1 issues the 9 C / 16 MMAs of a tile, warps 2-5 run conv_tile_epilogue);
+// every wait is bounded (~1 s).
+// ---------------------------------------------------------------------------
+constexpr unsigned PATCH_CHS = 2944;  // 180 pixels x 16 B rounded up to 128 B
+
+template <int BN, int C>
+constexpr int patchp_stages() {
+    // Two CTAs per SM when at least three stages fit in ~110 KB, else one
+    // CTA with up to five.
+    constexpr int wbytes = 9 * C * BN * 2, stage = (C / 8) * (int)PATCH_CHS;
+    return (110000 - wbytes) / stage >= 3 ? ((110000 - wbytes) / stage > 6 ? 6 : (110000 - wbytes) / stage)
+                                          : ((195000 - wbytes) / stage > 5 ? 5 : (195000 - wbytes) / stage);
+}
+
+template <int BN, int C, int ST>
+constexpr size_t patchp_smem() {
+    return 128 + (size_t)ST * (C / 8) * PATCH_CHS + (size_t)9 * C * BN * 2 + (2 * ST + 6) * 8 + 64;
+}
+
+template <int BN, int C, int ST, int EPI>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    conv3_patch_persistent_kernel(FpropArgs P, const __grid_constant__ CUtensorMap mapX, ConvTile G, int T) {
+    constexpr int CH = C / 8;
+    constexpr unsigned STAGE = CH * PATCH_CHS, B_CH = BN * 16;
+    constexpr int K = 9 * C;
+    constexpr unsigned TMEM_COLS = 2 * BN;  // two accumulators (64 or 128 columns)
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    const unsigned sa0 = (smem_u32(smraw) + 127u) & ~127u;
+    const unsigned sb = sa0 + ST * STAGE;
+    unsigned char *tail = smraw + (sb - smem_u32(smraw)) + (size_t)(K / 8) * B_CH;
+    const unsigned full0 = smem_u32(tail), empty0 = full0 + 8 * ST, tfull0 = empty0 + 8 * ST, tempty0 = tfull0 + 16;
+    const unsigned drain = tempty0 + 16;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(tail + 16 * ST + 40);
+    volatile unsigned *abort_word = reinterpret_cast<volatile unsigned *>(tail + 16 * ST + 44);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.y * BN;
+    auto decode = [&](int t, int &i0, int &h0, int &w0) {
+        w0 = (t % G.tw) * PT_W;
+        t /= G.tw;
+        h0 = (t % G.th) * PT_H;
+        i0 = t / G.th;
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < ST; s++) {
+            mbar_init1(full0 + 8 * s);
+            mbar_init1(empty0 + 8 * s);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init1(tfull0 + 8 * b);
+            mbar_init_n(tempty0 + 8 * b, 4);
+        }
+        mbar_init1(drain);
+        *abort_word = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // The CTA's weights B^T [n0 .. n0 + BN)[9 C], as [k-chunk][n][8] (zero past N).
+    for (int idx = tid; idx < (K / 8) * BN; idx += TMA_THREADS) {
+        const int kc = idx / BN, n = idx - kc * BN;
+        const bool ok = n0 + n < P.N;
+        cp16(sb + kc * B_CH + n * 16, ok ? P.bt + (long long)(n0 + n) * K + 8 * kc : P.bt, ok);
+    }
+    cp_commit();
+    cp_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // cp.async data -> tensor-core reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+    auto fail = [&]() {
+        *abort_word = 1u;
+        if (P.err) atomicExch(P.err, 1u);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int j = 0;  // patches issued by this CTA
+            for (int t = blockIdx.x; t < T && !*abort_word; t += gridDim.x, j++) {
+                const int s = j % ST;
+                if (j >= ST && !mbar_wait(empty0 + 8 * s, ((j / ST) - 1) & 1u)) {
+                    fail();
+                    break;
+                }
+                int i0, h0, w0;
+                decode(t, i0, h0, w0);
+                const unsigned fb = full0 + 8 * s, sa = sa0 + s * STAGE;
+                mbar_expect_tx(fb, CH * PP * 16);
+#pragma unroll
+                for (int c = 0; c < CH; c++) tma_load_4d(sa + c * PATCH_CHS, &mapX, 8 * c, w0 - 1, h0 - 1, i0, fb);
+            }
+            // Loads in flight land before the CTA leaves (bounded as well).
+            for (int q = max(0, j - ST); q < j; q++) mbar_wait(full0 + 8 * (q % ST), (q / ST) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16(UBM, BN);
+            int j = 0, b = 0, use[2] = {0, 0};
+            for (int t = blockIdx.x; t < T && !*abort_word; t += gridDim.x, j++, b ^= 1) {
+                const int s = j % ST;
+                // Accumulator b is free once the epilogue has read its last use.
+                if (use[b] > 0 && !mbar_wait(tempty0 + 8 * b, (use[b] - 1) & 1u)) {
+                    fail();
+                    break;
+                }
+                if (!mbar_wait(full0 + 8 * s, (j / ST) & 1u)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const unsigned sa = sa0 + s * STAGE, acc = tmem + (unsigned)(b * BN);
+                int q = 0;
+#pragma unroll 1
+                for (int tap = 0; tap < 9; tap++) {
+                    const unsigned off = (unsigned)(((1 + P.dh[tap]) * PP_W + 1 + P.dw[tap]) * 16);
+#pragma unroll
+                    for (int kk = 0; kk < C / 16; kk++, q++) {
+                        const uint64_t da = smem_desc(sa + 2 * kk * PATCH_CHS + off, PATCH_CHS, PP_W * 16);
+                        const uint64_t db = smem_desc(sb + (tap * (C / 8) + 2 * kk) * B_CH, B_CH, 128);
+                        mma_bf16(acc, da, db, IDESC, q > 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit(empty0 + 8 * s);  // the patch stage is free once these MMAs are done
+                mma_commit(tfull0 + 8 * b);  // and the accumulator final
+                use[b]++;
+            }
+            // Every MMA issued is complete before TMEM is freed (bounded).
+            mma_commit(drain);
+            mbar_wait(drain, 0);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        int b = 0, use[2] = {0, 0};
+        for (int t = blockIdx.x; t < T; t += gridDim.x, b ^= 1) {
+            int i0, h0, w0;
+            decode(t, i0, h0, w0);
+            const bool good = mbar_wait(tfull0 + 8 * b, use[b] & 1u);
+            tc_fence_after();
+            if (!__all_sync(0xffffffffu, good) || *abort_word) {
+                if (lane == 0) fail();
+                break;
+            }
+            conv_tile_epilogue<BN, EPI>(P, G, tmem + (unsigned)(b * BN), q, lane, i0, h0, w0, n0, 1, 0);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(tempty0 + 8 * b);
+            use[b]++;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+// Launch of the persistent patch kernel: grid = (the CTAs that fit on the
+// SMs, shared out over the N-tiles) x N-tiles; `small` (the forced mode
+// DHFWI_NN_PATCH=persistent) caps it at 2 CTAs per N-tile so that every CTA
+// walks many tiles (ring wrap-around and accumulator reuse).
+template <int BN, int C, int EPI>
+bool patchp_launch(const FpropArgs &a, const ConvTile &G, bool small, cudaStream_t s) {
+    constexpr int ST = patchp_stages<BN, C>();
+    const size_t sm = patchp_smem<BN, C, ST>();
+    EncodeTiledFn enc = tma_encoder();
+    if (!enc) return false;
+    CUtensorMap mx;
+    {
+        const cuuint64_t es = sizeof(__nv_bfloat16);
+        cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)a.Ws, (cuuint64_t)a.Hs, (cuuint64_t)G.nimg};
+        cuuint64_t str[3] = {es * a.src_stride, es * a.src_stride * a.Ws, es * a.src_stride * a.Ws * a.Hs};
+        cuuint32_t box[4] = {8, (cuuint32_t)PP_W, (cuuint32_t)PP_H, 1}, estr[4] = {1, 1, 1, 1};
+        if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(a.src + a.src_off), dims, str, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    static bool attr = false;
+    static int cap = 0;
+    if (!attr) {
+        cudaFuncSetAttribute(conv3_patch_persistent_kernel<BN, C, ST, EPI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int dev = 0, nsm = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3_patch_persistent_kernel<BN, C, ST, EPI>,
+                                                      TMA_THREADS, sm);
+        cap = nsm * std::max(occ, 1);
+        attr = true;
+    }
+    const int T = G.tw * G.th * G.nimg, ntn = (a.N + BN - 1) / BN;
+    const int per_n = small ? 2 : std::max(1, cap / ntn);
+    dim3 grid(std::min(T, per_n), ntn);
+    conv3_patch_persistent_kernel<BN, C, ST, EPI><<<grid, TMA_THREADS, sm, s>>>(a, mx, G, T);
+    return true;
+}
+
+// Waves of CTAs the one-tile patch kernel would need (tiles over resident
+// CTAs); the persistent one is used from two waves on.
+template <int EPI>
+bool patchp_dispatch(const FpropArgs &a, const ConvTile &G, int mode, cudaStream_t s) {
+    const bool small = mode == 1;
+    if (mode == 2) {  // automatic: many tiles per SM
+        const long long tiles = (long long)G.tw * G.th * G.nimg * ((a.N + 63) / 64);
+        if (tiles < 2LL * 2 * 152) return false;
+    }
+    switch (a.C) {
+    case 32: return a.N <= 32 ? patchp_launch<32, 32, EPI>(a, G, small, s) : patchp_launch<64, 32, EPI>(a, G, small, s);
+    case 64: return a.N <= 32 ? patchp_launch<32, 64, EPI>(a, G, small, s) : patchp_launch<64, 64, EPI>(a, G, small, s);
+    default: return false;
+    }
+}
+
+// The persistent patch kernel for a GEMM launch_conv3_patch accepted (mode
+// 1 forced, 2 automatic); false: not launched (the one-tile kernel runs).
+bool launch_conv3_patch_persistent(const FpropArgs &a, const ConvTile &G, int epi, int mode, cudaStream_t s) {
+    switch (epi) {
+    case EPI_BF16_LEAKY: return patchp_dispatch<EPI_BF16_LEAKY>(a, G, mode, s);
+    case EPI_BF16: return patchp_dispatch<EPI_BF16>(a, G, mode, s);
+    case EPI_F32: return patchp_dispatch<EPI_F32>(a, G, mode, s);
+    case EPI_BF16_LEAKYBWD: return patchp_dispatch<EPI_BF16_LEAKYBWD>(a, G, mode, s);
+    case EPI_F32_ADD: return patchp_dispatch<EPI_F32_ADD>(a, G, mode, s);
+    default: return false;
+    }
 }
 
 // Kernel choice for a conv3 GEMM: DHFWI_NN_CONV=tile (one tile per CTA),

@@ -10,9 +10,10 @@ the GPU in float32.  The shapes reach every GEMM path the network runs: the
 the tcgen05 kernels for >= 64 output channels (32- and 64-channel sources),
 the split-k paths of the deepest levels, M tails (pixel counts that are not a
 multiple of the 128-row tile) and the transposed convolutions; each case runs
-under every GEMM selection (the default choice, without the patch kernel,
-the one-tile-per-CTA and the persistent TMA-fed convolutions forced,
-DHFWI_NN_GEMM "mma" and "tc").
+under every GEMM selection (the default choice, without the patch kernels,
+the one-tile-per-CTA and the persistent TMA-fed convolutions forced, the
+one-tile and the persistent patch kernels forced, DHFWI_NN_GEMM "mma" and
+"tc").
 """
 import math
 
@@ -36,6 +37,8 @@ CONV3 = [
     (256, 512, 8, 4, 4),    # deepest level: few pixels, split-k
     (512, 512, 16, 4, 4),
     (512, 256, 4, 8, 8),    # up1.0 on [skip, up]
+    (32, 32, 4, 128, 128),  # the top level of the benchmark's patches: persistent patch kernel by default
+    (64, 64, 4, 64, 64),    # 64-channel patches, 128 tiles
 ]
 # (ci, co, n, H, W) of transposed convolutions (H, W: the coarse input grid).
 CONVT = [
@@ -43,9 +46,11 @@ CONVT = [
     (128, 64, 3, 5, 7),
     (64, 32, 2, 8, 12),
 ]
-# nopatch: without the patch-reuse tcgen05 kernel (DHFWI_NN_PATCH=0); tile / persistent: also the
-# one-tile-per-CTA or the persistent TMA-fed tcgen05 conv kernel forced (DHFWI_NN_CONV)
-MODES = ["default", "nopatch", "tile", "persistent", "mma", "tc"]
+# nopatch: without the patch-reuse tcgen05 kernels (DHFWI_NN_PATCH=0); tile / persistent: also the
+# one-tile-per-CTA or the persistent TMA-fed tcgen05 conv kernel forced (DHFWI_NN_CONV); patchtile /
+# patchp: the one-tile or the persistent patch kernel forced (DHFWI_NN_PATCH=tile / persistent, the
+# latter on two CTAs per N-tile so that each walks many tiles)
+MODES = ["default", "nopatch", "tile", "persistent", "patchtile", "patchp", "mma", "tc"]
 
 
 def _data(seed, kind, ci, co, n, H, W):
@@ -88,7 +93,10 @@ def _run(monkeypatch, mode, kind, shape, seed):
 
     monkeypatch.delenv("DHFWI_NN_CONV", raising=False)
     monkeypatch.delenv("DHFWI_NN_PATCH", raising=False)
-    if mode in ("default", "nopatch", "tile", "persistent"):
+    if mode in ("patchtile", "patchp"):
+        monkeypatch.delenv("DHFWI_NN_GEMM", raising=False)
+        monkeypatch.setenv("DHFWI_NN_PATCH", "tile" if mode == "patchtile" else "persistent")
+    elif mode in ("default", "nopatch", "tile", "persistent"):
         monkeypatch.delenv("DHFWI_NN_GEMM", raising=False)
         if mode != "default":
             monkeypatch.setenv("DHFWI_NN_PATCH", "0")
