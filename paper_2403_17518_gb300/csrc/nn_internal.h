@@ -52,14 +52,7 @@ struct WgradArgs {
     const __nv_bfloat16 *ones;  // 8 bf16 values {1, 0, ..., 0}
     float *part;                // [splits][M][N]
     unsigned *err;              // nullable: set to 1 by a tensor-core GEMM whose bounded wait ran out
-    // Nullable: zeroed per-tile counters (at least kWgradCounters) that let the
-    // tcgen05 weight gradient sum its own split-k partials (the last CTA of a
-    // tile, in split order) into dw; each launch leaves them zero.  Null:
-    // partials, then a separate reduction.
-    unsigned *tile_count = nullptr;
-    float *dw = nullptr;        // set by launch_wgrad for the tcgen05 kernel
 };
-constexpr int kWgradCounters = 16384;
 
 // mma.sync GEMM (igemm_fprop_kernel), or the tcgen05 one (nn_umma.cu) when
 // DHFWI_NN_GEMM=tc.
@@ -73,9 +66,8 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s);
 // outputs; false when not applicable (nothing launched).
 bool launch_conv3_patch(const FpropArgs &a, int epi, cudaStream_t s);
 // tcgen05 weight gradient of a 3x3 convolution (nn_umma.cu; off with
-// DHFWI_NN_WGRAD=mma or DHFWI_NN_GEMM=mma): 0 when not applicable (nothing
-// launched); -1 when it wrote a.dw itself (a.tile_count given); else the
-// number of split-k partials it wrote into a.part (to be reduced).
+// DHFWI_NN_WGRAD=mma or DHFWI_NN_GEMM=mma): the splits it wrote, 0 when not
+// applicable.
 int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s);
 // Sum of split-k partials a.part[splits][M][N] with the epilogue epi.
 void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s);

@@ -1271,20 +1271,14 @@ static void wgrad_launch(const WgradArgs &a, int splits, cudaStream_t s) {
 
 int launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s) {
     const long long mn = (long long)a.M * a.N;
-    WgradArgs b = a;
-    b.dw = dw;
-    const int tsp = launch_wgrad_tma(b, splits, s);
-    if (tsp != 0) {
-        int n = 3;
-        if (tsp > 0) {  // partials written, not yet summed
-            wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, tsp, a.M, a.N, a.nw, a.mode, a.co,
-                                                                         dw, db);
-            n++;
-        }
-        // The bias gradient (not in the tcgen05 GEMM), with the partial
-        // buffer, free again, as scratch (512 x M floats fit in it).
+    const int tsp = launch_wgrad_tma(a, splits, s);
+    if (tsp > 0) {
+        wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, tsp, a.M, a.N, a.nw, a.mode, a.co, dw,
+                                                                     db);
+        // The bias gradient (its partial column is zero here), with the
+        // partial buffer, free again, as scratch (512 x M floats fit in it).
         launch_bias_grad(a.g, a.g_stride, a.M, (long long)a.nimg * a.H * a.W, a.part, 512, db, s);
-        return n;
+        return 4;
     }
     if (wgrad_narrow(a.M)) wgrad_launch<1, 4>(a, splits, s);
     else wgrad_launch<2, 2>(a, splits, s);

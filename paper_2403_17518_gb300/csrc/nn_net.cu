@@ -64,7 +64,6 @@ struct NetState {
     size_t red_part_floats = 0;
     float *wg_part = nullptr;
     size_t wg_part_floats = 0;
-    unsigned *wg_count = nullptr;  // kWgradCounters zeroed tile counters of the weight-gradient fix-up
     float *fp_part = nullptr;    // split-k partials of the fprop GEMMs
     size_t fp_part_floats = 0;
     __nv_bfloat16 *ones = nullptr;  // {1, 0, ..., 0}: bias column of the weight-gradient GEMMs
@@ -621,7 +620,6 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
     w.ones = N.ones;
     w.part = N.wg_part;
     w.err = N.err;
-    w.tile_count = N.wg_count;
     const int sp = wgrad_splits(P, w.M, w.N);
     float *dw = li == 0 ? N.g0pad : N.grad + d.off;
     N.launches += launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, ws);
@@ -840,8 +838,8 @@ bool graphs_on() {
 
 // The switches that change which kernels a pass launches.
 std::string gemm_switches() {
-    static const char *names[] = {"DHFWI_NN_GEMM",  "DHFWI_NN_WGRAD",   "DHFWI_NN_CONV",        "DHFWI_NN_PATCH",
-                                  "DHFWI_NN_HALO",  "DHFWI_NN_CONVT",   "DHFWI_NN_WGRAD_FIXUP", "DHFWI_NN_OVERLAP"};
+    static const char *names[] = {"DHFWI_NN_GEMM", "DHFWI_NN_WGRAD", "DHFWI_NN_CONV",   "DHFWI_NN_PATCH",
+                                  "DHFWI_NN_HALO", "DHFWI_NN_CONVT", "DHFWI_NN_OVERLAP"};
     std::string k;
     for (const char *n : names) {
         const char *e = getenv(n);
@@ -929,10 +927,6 @@ int ensure_small(dhfwi_ctx *ctx, NetState &N) {
         NCK(cudaMemset(N.err, 0, 16));
     }
     if (!N.scales && (rc = dev_alloc(ctx, (void **)&N.scales, 4 * sizeof(float)))) return rc;
-    if (!N.wg_count) {
-        if ((rc = dev_alloc(ctx, (void **)&N.wg_count, sizeof(unsigned) * kWgradCounters))) return rc;
-        NCK(cudaMemset(N.wg_count, 0, sizeof(unsigned) * kWgradCounters));
-    }
     if (!N.ones) {
         if ((rc = dev_alloc(ctx, (void **)&N.ones, 16))) return rc;
         __nv_bfloat16 h[8];
@@ -996,7 +990,7 @@ void net_destroy(NetState *net) {
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
     free_params(*net);
-    void *ps[] = {net->arena, net->prev.arena, net->wg_count, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->ones,
+    void *ps[] = {net->arena, net->prev.arena, net->mse_part, net->loss_acc, net->red_part, net->wg_part, net->fp_part, net->ones,
                   net->mx, net->err, net->scales, net->oz, net->ox, net->perm};
     for (void *p : ps) dev_free(p);
     delete net;
@@ -1251,14 +1245,14 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
     // Temporaries of this call only (freed before it returns).
     __nv_bfloat16 *x16 = nullptr, *w16 = nullptr, *wt16 = nullptr, *g16 = nullptr, *y16 = nullptr, *ones = nullptr;
     float *part = nullptr, *wg = nullptr;
-    unsigned *err = nullptr, *cnt = nullptr;
+    unsigned *err = nullptr;
     const int wM = conv ? co : 4 * co, wN = (conv ? 9 * ci : ci) + 8;
     const int splits = wgrad_splits(Pin, wM, wN);  // summed over the input grid's pixels
     const long long fp_floats = std::max<long long>(2LL * 152 * 4 * 128 * 64, 8LL * Pout * std::max(ci, 4 * co));
     const long long wg_floats = std::max<long long>((long long)splits * wM * wN, 512LL * wM);
     int rc = DHFWI_OK;
     auto cleanup = [&]() {
-        void *ps[] = {x16, w16, wt16, g16, y16, ones, part, wg, err, cnt};
+        void *ps[] = {x16, w16, wt16, g16, y16, ones, part, wg, err};
         for (void *p : ps) dev_free(p);
     };
     if ((rc = dev_alloc(ctx, (void **)&x16, 2 * (size_t)Pin * ci)) ||
@@ -1266,8 +1260,7 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
         (rc = dev_alloc(ctx, (void **)&g16, 2 * (size_t)Pout * co)) ||
         (rc = dev_alloc(ctx, (void **)&y16, 2 * (size_t)Pout * co)) || (rc = dev_alloc(ctx, (void **)&ones, 16)) ||
         (rc = dev_alloc(ctx, (void **)&part, 4 * (size_t)fp_floats)) ||
-        (rc = dev_alloc(ctx, (void **)&wg, 4 * (size_t)wg_floats)) || (rc = dev_alloc(ctx, (void **)&err, 16)) ||
-        (rc = dev_alloc(ctx, (void **)&cnt, sizeof(unsigned) * kWgradCounters))) {
+        (rc = dev_alloc(ctx, (void **)&wg, 4 * (size_t)wg_floats)) || (rc = dev_alloc(ctx, (void **)&err, 16))) {
         cleanup();
         return rc;
     }
@@ -1275,7 +1268,6 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
     for (int i = 0; i < 8; i++) h1[i] = __float2bfloat16_rn(i == 0 ? 1.0f : 0.0f);
     cudaError_t e = cudaMemcpy(ones, h1, sizeof h1, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(err, 0, 16);
-    if (e == cudaSuccess) e = cudaMemset(cnt, 0, sizeof(unsigned) * kWgradCounters);
     if (e != cudaSuccess) {
         cleanup();
         return fail(ctx, DHFWI_ERR_CUDA, cudaGetErrorString(e));
@@ -1376,7 +1368,6 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
         w.ones = ones;
         w.part = wg;
         w.err = err;
-        w.tile_count = cnt;  // as in the network: split-k partials summed in the GEMM
         launches += launch_wgrad(w, splits, out_dev, out_dev + nw, s);
     }
     e = cudaGetLastError();

@@ -1580,10 +1580,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             // Rows past ci (a 32-channel X read as a 64-channel box) are zero.
             const bool valid = q < G.pairs && (r < 64 || two) && cb * 64 + (r & 63) < P.ci;
             const int n = tap * P.ci + cb * 64 + (r & 63);
-            // With tile counters and a single split, straight into dw.
-            const bool direct = P.tile_count && gridDim.z == 1;
-            float *out = direct ? P.dw + n : P.part + (long long)blockIdx.z * P.M * P.N + n;
-            const long long ostride = direct ? P.nw : P.N;
+            float *out = P.part + (long long)blockIdx.z * P.M * P.N + n;
             const unsigned trow = tmem + ((unsigned)(qw * 32) << 16);
 #pragma unroll 1
             for (int c0 = 0; c0 < NB; c0 += 16) {
@@ -1595,37 +1592,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                 if (!valid) continue;
 #pragma unroll
                 for (int e = 0; e < 16; e++)  // columns past M: a 32-channel G read as 64
-                    if (co0 + c0 + e < P.M) out[(long long)(co0 + c0 + e) * ostride] = v[e];
-            }
-        }
-        if (P.tile_count && gridDim.z > 1) {
-            // Split-k fix-up: the tile's last CTA to finish sums the splits'
-            // partials in split order into dw (the others' writes are
-            // visible after their fence and count).  Counted also after a
-            // timed-out wait, so the counters stay consistent.
-            volatile unsigned *last = reinterpret_cast<volatile unsigned *>(tail + 16 * ST + 16);
-            __threadfence();
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            const unsigned tile = blockIdx.x + blockIdx.y * gridDim.x;
-            if (qw == 2 && lane == 0) *last = atomicAdd(&P.tile_count[tile], 1u) == gridDim.z - 1;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (*last) {
-                __threadfence();
-                const int r = qw * 32 + lane;
-                const int q = q0 + (r >> 6);
-                const int tap = q / cbn, cb = q - tap * cbn;
-                const bool valid = q < G.pairs && (r < 64 || two) && cb * 64 + (r & 63) < P.ci;
-                const int n = tap * P.ci + cb * 64 + (r & 63);
-                if (valid) {
-                    const long long zs = (long long)P.M * P.N;
-                    for (int c = 0; c < NB && co0 + c < P.M; c++) {
-                        const float *pp = P.part + (long long)(co0 + c) * P.N + n;
-                        float acc = 0.f;
-                        for (int z = 0; z < (int)gridDim.z; z++) acc += __ldcg(pp + z * zs);
-                        P.dw[(long long)(co0 + c) * P.nw + n] = acc;
-                    }
-                }
-                if (qw == 2 && lane == 0) P.tile_count[tile] = 0u;
+                    if (co0 + c0 + e < P.M) out[(long long)(co0 + c0 + e) * P.N] = v[e];
             }
         }
     }
@@ -1683,15 +1650,10 @@ int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
         cudaFuncSetAttribute(wgrad_tma_umma_kernel<NB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
-    const bool fixup = a.tile_count && a.dw && mt * ntl <= kWgradCounters && a.mode == WG_CONV;
-    WgradArgs b = a;
-    if (!fixup) {
-        b.tile_count = nullptr;
-        // The bias column and the 7 zero columns are not written by the kernel.
-        cudaMemsetAsync(a.part, 0, sizeof(float) * (size_t)splits * a.M * a.N, s);
-    }
-    wgrad_tma_umma_kernel<NB, ST><<<dim3(mt, ntl, splits), TMA_THREADS, sm, s>>>(b, mx, mg, G);
-    return fixup ? -1 : splits;
+    // The bias column and the 7 zero columns are not written by the kernel.
+    cudaMemsetAsync(a.part, 0, sizeof(float) * (size_t)splits * a.M * a.N, s);
+    wgrad_tma_umma_kernel<NB, ST><<<dim3(mt, ntl, splits), TMA_THREADS, sm, s>>>(a, mx, mg, G);
+    return splits;
 }
 
 // The TMA-fed kernel serves a GEMM when it is a 3x3 convolution (taps with
@@ -1737,20 +1699,12 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
 
 // The tcgen05 weight gradient (the default; DHFWI_NN_WGRAD=mma or
 // DHFWI_NN_GEMM=mma keep the mma.sync one) for WG_CONV with ci and co
-// multiples of 32 and aligned operands.  With tile counters (a.tile_count)
-// it sums its split-k partials itself into a.dw and returns -1
-// (DHFWI_NN_WGRAD_FIXUP=0 turns that off); otherwise it writes partials as
-// igemm_wgrad_kernel's, bias column zero, and returns the number of splits
-// (0: not applicable, nothing launched).
+// multiples of 32 and aligned operands.  Partials as igemm_wgrad_kernel's,
+// bias column zero.  Returns the number of splits written (0: not
+// applicable, nothing launched).
 int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s) {
     const char *e = getenv("DHFWI_NN_WGRAD"), *g = getenv("DHFWI_NN_GEMM");
     if ((e && strcmp(e, "mma") == 0) || (g && strcmp(g, "mma") == 0)) return 0;
-    const char *fx = getenv("DHFWI_NN_WGRAD_FIXUP");
-    if (fx && strcmp(fx, "0") == 0 && a.tile_count) {
-        WgradArgs b = a;
-        b.tile_count = nullptr;
-        return launch_wgrad_tma(b, max_splits, s);
-    }
     // ci and co multiples of 32: a 32-channel operand is read as a 64-channel
     // TMA box whose upper half the copy fills with zeros (rows and columns the
     // epilogue does not write).

@@ -144,13 +144,3 @@ def test_wgrad_mma_path(monkeypatch):
     layers the tcgen05 one takes by default."""
     monkeypatch.setenv("DHFWI_NN_WGRAD", "mma")
     _run(monkeypatch, "default", "conv3", (128, 128, 4, 8, 8), seed=3)
-
-
-@pytest.mark.parametrize("shape", [(32, 32, 3, 17, 23), (256, 512, 8, 4, 4), (64, 64, 2, 9, 13)],
-                         ids=lambda s: "x".join(map(str, s)))
-def test_wgrad_partials_then_reduction(monkeypatch, shape):
-    """The tcgen05 weight gradient with its split-k partials summed by a
-    separate reduction (DHFWI_NN_WGRAD_FIXUP=0) rather than by the tile's
-    last CTA."""
-    monkeypatch.setenv("DHFWI_NN_WGRAD_FIXUP", "0")
-    _run(monkeypatch, "default", "conv3", shape, seed=11 + sum(shape))
