@@ -863,19 +863,31 @@ __global__ void transpose_w_kernel(const __nv_bfloat16 *__restrict__ w, int co, 
     }
 }
 
-// The transposes of several layers in one launch: job j = blockIdx.y.
+// The transposes of several layers in one launch: job j = blockIdx.y, and
+// blockIdx.x one 32 x 32 tile (output channels o x input channels c) of one
+// tap t, staged in shared memory so that both the reads along c and the
+// writes along o are contiguous.
 __global__ void transpose_w_batch_kernel(const __nv_bfloat16 *__restrict__ w, __nv_bfloat16 *__restrict__ wt,
                                          TransposeJobs J) {
+    __shared__ __nv_bfloat16 tile[32][33];
     const int j = blockIdx.y;
     const long long off = J.off[j];
     const int co = J.co[j], taps = J.taps[j], ci = J.ci[j];
-    const long long n = (long long)co * taps * ci;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % ci);
-        const long long r = i / ci;
-        const int t = (int)(r % taps);
-        const long long o = r / taps;
-        wt[off + ((long long)c * taps + t) * co + o] = w[off + i];
+    const int to = (co + 31) / 32, tc = (ci + 31) / 32;
+    int b = blockIdx.x;
+    if (b >= to * tc * taps) return;
+    const int t = b % taps;
+    b /= taps;
+    const int c0 = (b % tc) * 32, o0 = (b / tc) * 32;
+    const int x = threadIdx.x & 31, y = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int r = y; r < 32; r += 8) {  // read rows o0 + r along c
+        const int o = o0 + r, c = c0 + x;
+        if (o < co && c < ci) tile[r][x] = w[off + ((long long)o * taps + t) * ci + c];
+    }
+    __syncthreads();
+    for (int r = y; r < 32; r += 8) {  // write rows c0 + r along o
+        const int c = c0 + r, o = o0 + x;
+        if (o < co && c < ci) wt[off + ((long long)c * taps + t) * co + o] = tile[x][r];
     }
 }
 
@@ -1372,10 +1384,10 @@ void launch_transpose_w(const __nv_bfloat16 *w, int co, int taps, int ci, __nv_b
 }
 void launch_transpose_w_batch(const __nv_bfloat16 *w, __nv_bfloat16 *wt, const TransposeJobs &jobs, cudaStream_t s) {
     if (jobs.n <= 0) return;
-    long long most = 0;
-    for (int j = 0; j < jobs.n; j++) most = std::max(most, (long long)jobs.co[j] * jobs.taps[j] * jobs.ci[j]);
-    const int gx = (int)std::min<long long>((most + 255) / 256, 152 * 4);
-    transpose_w_batch_kernel<<<dim3(gx, jobs.n), 256, 0, s>>>(w, wt, jobs);
+    int most = 0;
+    for (int j = 0; j < jobs.n; j++)
+        most = std::max(most, ((jobs.co[j] + 31) / 32) * ((jobs.ci[j] + 31) / 32) * jobs.taps[j]);
+    transpose_w_batch_kernel<<<dim3(most, jobs.n), 256, 0, s>>>(w, wt, jobs);
 }
 
 void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cudaStream_t s) {
