@@ -66,8 +66,8 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s);
 // outputs; false when not applicable (nothing launched).
 bool launch_conv3_patch(const FpropArgs &a, int epi, cudaStream_t s);
 // tcgen05 weight gradient of a 3x3 convolution (nn_umma.cu; off with
-// DHFWI_NN_WGRAD=mma or DHFWI_NN_GEMM=mma): the splits it wrote, 0 when not
-// applicable.
+// DHFWI_NN_WGRAD=mma or DHFWI_NN_GEMM=mma): the splits it wrote (partials
+// with the bias column), 0 when not applicable.
 int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s);
 // Sum of split-k partials a.part[splits][M][N] with the epilogue epi.
 void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s);
@@ -75,8 +75,6 @@ int wgrad_splits(long long kpix, int M, int N);
 // Weight gradient into dw (parameter layout) and bias gradient into db.
 // Returns the number of kernels launched.
 int launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s);
-void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, float *part, int max_blocks, float *db,
-                      cudaStream_t s);
 void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H, int W, int C, __nv_bfloat16 *y,
                         cudaStream_t s);
 void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *dx, int accumulate, cudaStream_t s);

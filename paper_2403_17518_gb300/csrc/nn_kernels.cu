@@ -492,37 +492,6 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, 
     dw[o] = s;
 }
 
-// Bias gradient: db[c] = sum over pixels of g[p][c] (bf16 in, fixed order:
-// per-block partial sums then a second pass).
-// Column sums of g over a block of rows: threadIdx.x is the channel,
-// threadIdx.y (of blockDim.y) takes every blockDim.y-th row with two
-// independent accumulators; the rows' sums are then combined over y in a
-// fixed order in shared memory (deterministic).
-__global__ void bias_grad_partial_kernel(const __nv_bfloat16 *__restrict__ g, int stride, int C, long long P,
-                                         int rows_per_block, float *__restrict__ part) {
-    __shared__ float red[256];
-    const int c = blockIdx.y * blockDim.x + threadIdx.x;
-    const int ty = threadIdx.y, ny = blockDim.y;
-    const long long p0 = (long long)blockIdx.x * rows_per_block;
-    const long long p1 = p0 + rows_per_block < P ? p0 + rows_per_block : P;
-    float s0 = 0.f, s1 = 0.f;
-    if (c < C) {
-        long long p = p0 + ty;
-        for (; p + ny < p1; p += 2 * ny) {
-            s0 += __bfloat162float(g[p * stride + c]);
-            s1 += __bfloat162float(g[(p + ny) * stride + c]);
-        }
-        if (p < p1) s0 += __bfloat162float(g[p * stride + c]);
-    }
-    red[ty * blockDim.x + threadIdx.x] = s0 + s1;
-    __syncthreads();
-    if (ty == 0 && c < C) {
-        float s = 0.f;
-        for (int y = 0; y < ny; y++) s += red[y * blockDim.x + threadIdx.x];
-        part[(long long)blockIdx.x * C + c] = s;
-    }
-}
-
 // One warp per channel: lane l sums the partials l, l+32, ..., then a
 // shuffle tree (fixed order, so deterministic).
 __global__ void bias_grad_final_kernel(const float *__restrict__ part, int nblk, int C, float *__restrict__ db) {
@@ -1284,30 +1253,16 @@ static void wgrad_launch(const WgradArgs &a, int splits, cudaStream_t s) {
 int launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStream_t s) {
     const long long mn = (long long)a.M * a.N;
     const int tsp = launch_wgrad_tma(a, splits, s);
-    if (tsp > 0) {
+    if (tsp > 0) {  // partials with the bias column: weight and bias gradients in one reduction
         wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, tsp, a.M, a.N, a.nw, a.mode, a.co, dw,
                                                                      db);
-        // The bias gradient (its partial column is zero here), with the
-        // partial buffer, free again, as scratch (512 x M floats fit in it).
-        launch_bias_grad(a.g, a.g_stride, a.M, (long long)a.nimg * a.H * a.W, a.part, 512, db, s);
-        return 4;
+        return 2;
     }
     if (wgrad_narrow(a.M)) wgrad_launch<1, 4>(a, splits, s);
     else wgrad_launch<2, 2>(a, splits, s);
     wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, splits, a.M, a.N, a.nw, a.mode, a.co, dw,
                                                                  db);
     return 2;
-}
-
-void launch_bias_grad(const __nv_bfloat16 *g, int stride, int C, long long P, float *part, int max_blocks,
-                      float *db, cudaStream_t s) {
-    int rows = (int)((P + max_blocks - 1) / max_blocks);
-    if (rows < 64) rows = 64;
-    const int nblk = (int)((P + rows - 1) / rows);
-    const int bd = C < 128 ? (C + 31) / 32 * 32 : 128;  // channels per block; 256 threads in all
-    dim3 grid(nblk, (C + bd - 1) / bd);
-    bias_grad_partial_kernel<<<grid, dim3(bd, 256 / bd), 0, s>>>(g, stride, C, P, rows, part);
-    bias_grad_final_kernel<<<(C * 32 + 255) / 256, 256, 0, s>>>(part, nblk, C, db);
 }
 
 void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H, int W, int C, __nv_bfloat16 *y,

@@ -416,11 +416,12 @@ constexpr size_t conv3_tma_smem() {
 // Epilogue of one 128 x BN output tile of the TMA-fed conv kernels: warp q
 // of the four epilogue warps reads TMEM lanes 32 q .. 32 q + 31 (tile rows)
 // of the accumulator whose column base is `tmem` (nk == 0: an empty k-range,
-// zeros), and writes the rows with the epilogue EPI, or raw partial sums to
-// P.part[split] when k is split.
+// zeros), columns [cbeg, cend) of it, and writes the rows with the epilogue
+// EPI, or raw partial sums to P.part[split] when k is split.
 template <int BN, int EPI>
 __device__ __forceinline__ void conv_tile_epilogue(const FpropArgs &P, const ConvTile &G, unsigned tmem, int q, int lane,
-                                                   int i0, int h0, int w0, int n0, int nk, int split) {
+                                                   int i0, int h0, int w0, int n0, int nk, int split, int cbeg = 0,
+                                                   int cend = BN) {
     const int r = q * 32 + lane;  // tile row = TMEM lane
     const int per_img = G.BW * G.BH;
     const int img = i0 + r / per_img, rem = r % per_img;
@@ -429,7 +430,7 @@ __device__ __forceinline__ void conv_tile_epilogue(const FpropArgs &P, const Con
     const long long m = ((long long)img * P.Ho + ho) * P.Wo + wo;
     const unsigned trow = tmem + ((unsigned)(q * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
         if (n0 + c0 >= P.N) break;  // uniform across the warp
         float v[16];
         if (nk > 0) tmem_ld16(trow + c0, v);
@@ -1053,18 +1054,25 @@ bool conv3_tma_launch(const FpropArgs &a, const ConvTile &G0, cudaStream_t s) {
             return false;
     }
     static bool attr = false;
+    static int wave = 152;  // CTAs resident at once
     if (!attr) {
         cudaFuncSetAttribute(conv3_tma_umma_kernel<BN, BK, ST, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm);
+        int dev = 0, nsm = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3_tma_umma_kernel<BN, BK, ST, EPI>, TMA_THREADS, sm);
+        wave = std::max(1, nsm * occ);
         attr = true;
     }
     const int mt = G.tw * G.th * ((G.nimg + G.BI - 1) / G.BI);
     const int tiles = mt * ((a.N + BN - 1) / BN);
     int splits = 1;
     if (a.part && a.part_floats > 0) {
-        // Split k when the tiles fill less than one wave, keeping at least 4
-        // k-tiles per split and the partials within their buffer.
-        const int want = (152 + tiles - 1) / tiles;
+        // Split k when the tiles fill less than one wave (and no more than
+        // one: a CTA that runs after the others doubles the time), keeping
+        // at least 4 k-tiles per split and the partials within their buffer.
+        const int want = std::max(1, wave / tiles);
         splits = std::min(want, G.nk_all / 4);
         const long long cap = a.part_floats / ((long long)a.M * a.N);
         if (splits > cap) splits = (int)cap;
@@ -1134,9 +1142,10 @@ bool conv3_persistent_launch(const FpropArgs &a, const ConvTile &G0, cudaStream_
     const int tiles = mt * ntn;
     int splits = 1;
     if (a.part && a.part_floats > 0) {
-        // Split k when the tiles fill less than one wave, keeping at least 4
+        // Split k when the tiles fill less than one wave (no more than one
+        // item per CTA: a CTA with two doubles the time), keeping at least 4
         // k-tiles per split and the partials within their buffer.
-        const int want = (nsm + tiles - 1) / tiles;
+        const int want = std::max(1, nsm / tiles);
         splits = std::min(want, G.nk_all / 4);
         const long long cap = a.part_floats / ((long long)a.M * a.N);
         if (splits > cap) splits = (int)cap;
@@ -1163,8 +1172,9 @@ bool conv3_persistent_launch(const FpropArgs &a, const ConvTile &G0, cudaStream_
 // accumulator is double-buffered in TMEM so that the epilogue of tile j
 // overlaps the MMAs of tile j + 1 and the loads of the tiles after it.
 // Roles and hand-off as in conv3_tma_persistent_kernel (warp 0 loads, warp
-// 1 issues the 9 C / 16 MMAs of a tile, warps 2-5 run conv_tile_epilogue);
-// every wait is bounded (~1 s).
+// 1 issues the 9 C / 16 MMAs of a tile), with eight epilogue warps (two per
+// TMEM lane quarter, each writing half of the columns) for more stores in
+// flight; every wait is bounded (~1 s).
 // ---------------------------------------------------------------------------
 constexpr unsigned PATCH_CHS = 2944;  // 180 pixels x 16 B rounded up to 128 B
 
@@ -1182,8 +1192,10 @@ constexpr size_t patchp_smem() {
     return 128 + (size_t)ST * (C / 8) * PATCH_CHS + (size_t)9 * C * BN * 2 + (2 * ST + 6) * 8 + 64;
 }
 
+constexpr int PATCHP_THREADS = 320;  // loader, MMA issuer, 8 epilogue warps
+
 template <int BN, int C, int ST, int EPI>
-__global__ void __launch_bounds__(TMA_THREADS, 1)
+__global__ void __launch_bounds__(PATCHP_THREADS, 1)
     conv3_patch_persistent_kernel(FpropArgs P, const __grid_constant__ CUtensorMap mapX, ConvTile G, int T) {
     constexpr int CH = C / 8;
     constexpr unsigned STAGE = CH * PATCH_CHS, B_CH = BN * 16;
@@ -1214,7 +1226,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         }
         for (int b = 0; b < 2; b++) {
             mbar_init1(tfull0 + 8 * b);
-            mbar_init_n(tempty0 + 8 * b, 4);
+            mbar_init_n(tempty0 + 8 * b, 8);
         }
         mbar_init1(drain);
         *abort_word = 0u;
@@ -1226,7 +1238,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // The CTA's weights B^T [n0 .. n0 + BN)[9 C], as [k-chunk][n][8] (zero past N).
-    for (int idx = tid; idx < (K / 8) * BN; idx += TMA_THREADS) {
+    for (int idx = tid; idx < (K / 8) * BN; idx += PATCHP_THREADS) {
         const int kc = idx / BN, n = idx - kc * BN;
         const bool ok = n0 + n < P.N;
         cp16(sb + kc * B_CH + n * 16, ok ? P.bt + (long long)(n0 + n) * K + 8 * kc : P.bt, ok);
@@ -1300,7 +1312,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         }
         __syncwarp();
     } else {
-        const int q = warp & 3;
+        // Warps 2-9: TMEM lane quarter warp % 4, column half (warp - 2) / 4.
+        const int q = warp & 3, cb = ((warp - 2) >> 2) * (BN / 2);
         int b = 0, use[2] = {0, 0};
         for (int t = blockIdx.x; t < T; t += gridDim.x, b ^= 1) {
             int i0, h0, w0;
@@ -1311,7 +1324,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                 if (lane == 0) fail();
                 break;
             }
-            conv_tile_epilogue<BN, EPI>(P, G, tmem + (unsigned)(b * BN), q, lane, i0, h0, w0, n0, 1, 0);
+            conv_tile_epilogue<BN, EPI>(P, G, tmem + (unsigned)(b * BN), q, lane, i0, h0, w0, n0, 1, 0, cb,
+                                        cb + BN / 2);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive1(tempty0 + 8 * b);
@@ -1352,18 +1366,22 @@ bool patchp_launch(const FpropArgs &a, const ConvTile &G, bool small, cudaStream
     if (!attr) {
         cudaFuncSetAttribute(conv3_patch_persistent_kernel<BN, C, ST, EPI>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        // All of the SM's unified memory as shared memory, so that two CTAs
+        // of the smaller instances fit.
+        cudaFuncSetAttribute(conv3_patch_persistent_kernel<BN, C, ST, EPI>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
         int dev = 0, nsm = 0, occ = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3_patch_persistent_kernel<BN, C, ST, EPI>,
-                                                      TMA_THREADS, sm);
+                                                      PATCHP_THREADS, sm);
         cap = nsm * std::max(occ, 1);
         attr = true;
     }
     const int T = G.tw * G.th * G.nimg, ntn = (a.N + BN - 1) / BN;
     const int per_n = small ? 2 : std::max(1, cap / ntn);
     dim3 grid(std::min(T, per_n), ntn);
-    conv3_patch_persistent_kernel<BN, C, ST, EPI><<<grid, TMA_THREADS, sm, s>>>(a, mx, G, T);
+    conv3_patch_persistent_kernel<BN, C, ST, EPI><<<grid, PATCHP_THREADS, sm, s>>>(a, mx, G, T);
     return true;
 }
 
@@ -1464,7 +1482,8 @@ void umma_dispatch(const FpropArgs &a, cudaStream_t s) {
 // 2048 B further.  Same warp roles, mbarrier hand-off and bounded waits as
 // conv3_tma_umma_kernel.  The epilogue writes lane r's row (one input
 // channel of one tap) for 16 output channels at a time, so a warp stores 32
-// consecutive columns of part.  The bias column is left to the caller.
+// consecutive columns of part.  The CTAs of the first M tile also write the
+// bias column (column nw: the sum of G's column over the split's pixels).
 // ---------------------------------------------------------------------------
 struct WgradTile {
     int BW, BH, BI, tw, th;
@@ -1495,10 +1514,16 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     const int nk = max(0, min(G.npb, pb0 + G.per) - pb0);
     const unsigned stage_tx = (two ? 2 : 1) * BOX + B_BYTES;
 
+    // The first M tile's CTAs also sum the output gradient's columns (the
+    // bias gradient) from the staged G boxes: its four epilogue warps read
+    // every stage too, so a stage is free after the MMAs' commit and their
+    // four arrivals.
+    const bool bias = blockIdx.x == 0;
+
     if (tid == 0) {
         for (int s = 0; s < ST; s++) {
             mbar_init1(full0 + 8 * s);
-            mbar_init1(empty0 + 8 * s);
+            mbar_init_n(empty0 + 8 * s, bias ? 5u : 1u);
         }
         mbar_init1(accf);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1569,6 +1594,55 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         __syncwarp();
     } else {
         const int qw = warp & 3;
+        if (bias) {
+            // Thread t: channel pair cp (channels co0 + 2 cp, + 1) over the
+            // pixel rows grp, grp + ngrp, ... of each 128-pixel block; the
+            // G box rows are 128 B (64 channels) with 16-byte chunks
+            // swizzled by the row's low three bits.
+            constexpr int NP = NB / 2, NGRP = 128 / NP;
+            const int t = qw * 32 + lane, cp = t % NP, grp = t / NP;
+            const int c = 2 * cp, bx = c >> 6, cc = c & 63;
+            float s0 = 0.f, s1 = 0.f;
+            bool ok = true;
+            for (int kt = 0; kt < nk; kt++) {
+                const int s = kt % ST;
+                if (!mbar_wait(full0 + 8 * s, (kt / ST) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned gb = sbase + s * STAGE + A_BYTES + bx * BOX;
+#pragma unroll 4
+                for (int p = grp; p < 128; p += NGRP) {
+                    unsigned v;
+                    asm volatile("ld.shared.b32 %0, [%1];"
+                                 : "=r"(v)
+                                 : "r"(gb + p * 128 + (((cc >> 3) ^ (p & 7)) << 4) + ((cc & 7) << 1)));
+                    __nv_bfloat162 h;
+                    memcpy(&h, &v, 4);
+                    const float2 f = __bfloat1622float2(h);
+                    s0 += f.x;
+                    s1 += f.y;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive1(empty0 + 8 * s);
+            }
+            if (!ok && lane == 0 && P.err) atomicExch(P.err, 1u);
+            // Groups summed in order; the bias column nw of this split's partial.
+            float *red = reinterpret_cast<float *>(tail + 16 * ST + 64);
+            red[2 * t] = s0;
+            red[2 * t + 1] = s1;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (grp == 0) {
+                float a0 = 0.f, a1 = 0.f;
+                for (int g = 0; g < NGRP; g++) {
+                    a0 += red[2 * (g * NP + cp)];
+                    a1 += red[2 * (g * NP + cp) + 1];
+                }
+                float *out = P.part + (long long)blockIdx.z * P.M * P.N + P.nw;
+                if (co0 + c < P.M) out[(long long)(co0 + c) * P.N] = a0;
+                if (co0 + c + 1 < P.M) out[(long long)(co0 + c + 1) * P.N] = a1;
+            }
+        }
         const bool good = mbar_wait(accf, 0);
         tc_fence_after();
         if (!good) {
@@ -1607,7 +1681,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
 template <int NB>
 int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
     constexpr int ST = NB == 64 ? 4 : NB == 128 ? 3 : 2;
-    const size_t sm = (size_t)ST * (2 * 16384 + (NB / 64) * 16384) + 2048;
+    const size_t sm = (size_t)ST * (2 * 16384 + (NB / 64) * 16384) + 2048 + 1024;  // + bias-sum scratch
     EncodeTiledFn enc = tma_encoder();
     if (!enc) return 0;
     WgradTile G{};
@@ -1621,7 +1695,9 @@ int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
     G.pairs = 9 * ((a.ci + 63) / 64);
     const int mt = (G.pairs + 1) / 2, ntl = (a.M + NB - 1) / NB;
     const int tiles = mt * ntl;
-    int splits = (152 + tiles - 1) / tiles;
+    // One CTA per SM (~192 KB of stages): at most one wave, so that no CTA
+    // runs after the others.
+    int splits = std::max(1, 152 / tiles);
     splits = std::min(splits, std::max(1, G.npb / 4));
     splits = std::max(1, std::min(splits, max_splits));
     G.per = (G.npb + splits - 1) / splits;
@@ -1650,7 +1726,7 @@ int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
         cudaFuncSetAttribute(wgrad_tma_umma_kernel<NB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
-    // The bias column and the 7 zero columns are not written by the kernel.
+    // The 7 columns after the bias column are not written by the kernel.
     cudaMemsetAsync(a.part, 0, sizeof(float) * (size_t)splits * a.M * a.N, s);
     wgrad_tma_umma_kernel<NB, ST><<<dim3(mt, ntl, splits), TMA_THREADS, sm, s>>>(a, mx, mg, G);
     return splits;
@@ -1700,7 +1776,7 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
 // The tcgen05 weight gradient (the default; DHFWI_NN_WGRAD=mma or
 // DHFWI_NN_GEMM=mma keep the mma.sync one) for WG_CONV with ci and co
 // multiples of 32 and aligned operands.  Partials as igemm_wgrad_kernel's,
-// bias column zero.  Returns the number of splits written (0: not
+// bias column the sum of G's column.  Returns the number of splits written (0: not
 // applicable, nothing launched).
 int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s) {
     const char *e = getenv("DHFWI_NN_WGRAD"), *g = getenv("DHFWI_NN_GEMM");
