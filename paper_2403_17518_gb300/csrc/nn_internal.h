@@ -102,6 +102,11 @@ struct TransposeJobs {
     int co[MAX], taps[MAX], ci[MAX];
 };
 void launch_transpose_w_batch(const __nv_bfloat16 *w, __nv_bfloat16 *wt, const TransposeJobs &jobs, cudaStream_t s);
+// Transposed-conv weights [co][4][ci] -> [4][co][ci] (jobs' taps ignored):
+// the B^T of the transposed convolutions' forward GEMM, whose columns are
+// tap-major (n = tap * co + channel) in every EPI_BF16_CONVT epilogue.
+void launch_convt_tapmajor_batch(const __nv_bfloat16 *w, __nv_bfloat16 *wp, const TransposeJobs &jobs,
+                                 cudaStream_t s);
 void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cudaStream_t s);
 void launch_gather_patches(const float *img, int nx, const int *oz, const int *ox, const int *sel, int nb, int p,
                            const float *scale, int mute, float *dst, cudaStream_t s);

@@ -210,8 +210,9 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
                         const long long o = (long long)m * P.dst_stride + P.dst_off + n;
                         P.dst_bf16[o] = __float2bfloat16_rn(v);
                     } else if (EPI == EPI_BF16_CONVT) {
-                        // n = co*4 + a*2 + b -> output pixel (2ho+a, 2wo+b), channel co.
-                        const int co = n >> 2, a = (n >> 1) & 1, b = n & 1;
+                        // Columns tap-major: n = (2a + b) * Co + co -> output pixel
+                        // (2ho+a, 2wo+b), channel co.
+                        const int Co = P.N >> 2, tap = n / Co, co = n - tap * Co, a = tap >> 1, b = tap & 1;
                         v += P.bias[co];
                         const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
                         P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v);
@@ -249,7 +250,7 @@ __global__ void fprop_reduce_kernel(FpropArgs P, int splits) {
             const int img = m / HWo;
             const int r = m - img * HWo;
             const int ho = r / P.Wo, wo = r - ho * P.Wo;
-            const int co = n >> 2, a = (n >> 1) & 1, b = n & 1;
+            const int Co = P.N >> 2, tap = n / Co, co = n - tap * Co, a = tap >> 1, b = tap & 1;  // tap-major columns
             v += P.bias[co];
             const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
             P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v);
@@ -860,6 +861,24 @@ __global__ void transpose_w_batch_kernel(const __nv_bfloat16 *__restrict__ w, __
     }
 }
 
+// The transposed convolutions' forward GEMM takes its weight rows
+// tap-major: [co][4][ci] -> [4][co][ci] (job j = blockIdx.y), so that an
+// output tile's 16 consecutive columns are 16 channels of one output
+// sub-pixel (contiguous stores).
+__global__ void convt_tapmajor_batch_kernel(const __nv_bfloat16 *__restrict__ w, __nv_bfloat16 *__restrict__ wp,
+                                            TransposeJobs J) {
+    const int j = blockIdx.y;
+    const long long off = J.off[j];
+    const int co = J.co[j], ci = J.ci[j];
+    const long long n = 4LL * co * ci;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % ci);
+        const long long r = i / ci;
+        const int t = (int)(r & 3), o = (int)(r >> 2);
+        wp[off + ((long long)t * co + o) * ci + c] = w[off + i];
+    }
+}
+
 // Input image (float32 [img][H][W]) into a bf16 NHWC tensor of Cp channels
 // (channel 0 = the image, others 0).
 __global__ void input_pack_kernel(const float *__restrict__ x, long long P, int Cp, __nv_bfloat16 *__restrict__ y) {
@@ -1343,6 +1362,14 @@ void launch_transpose_w_batch(const __nv_bfloat16 *w, __nv_bfloat16 *wt, const T
     for (int j = 0; j < jobs.n; j++)
         most = std::max(most, ((jobs.co[j] + 31) / 32) * ((jobs.ci[j] + 31) / 32) * jobs.taps[j]);
     transpose_w_batch_kernel<<<dim3(most, jobs.n), 256, 0, s>>>(w, wt, jobs);
+}
+
+void launch_convt_tapmajor_batch(const __nv_bfloat16 *w, __nv_bfloat16 *wp, const TransposeJobs &jobs,
+                                 cudaStream_t s) {
+    if (jobs.n <= 0) return;
+    long long most = 0;
+    for (int j = 0; j < jobs.n; j++) most = std::max(most, 4LL * jobs.co[j] * jobs.ci[j]);
+    convt_tapmajor_batch_kernel<<<dim3(grid_for(most), jobs.n), 256, 0, s>>>(w, wp, jobs);
 }
 
 void launch_input_pack(const float *x, long long P, int Cp, __nv_bfloat16 *y, cudaStream_t s) {

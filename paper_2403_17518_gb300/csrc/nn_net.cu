@@ -50,6 +50,7 @@ struct NetState {
     // Parameter state (device).
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *w16 = nullptr, *wt16 = nullptr, *w0pad = nullptr;
+    __nv_bfloat16 *wc16 = nullptr;  // transposed convs' weights tap-major ([4][co][ci]) at their offsets
     float *g0pad = nullptr;
     // Workspace (device arena) sized for (wsN, wsH, wsW); the workspace of
     // the previous shape is kept as `prev` (training patches and the
@@ -241,10 +242,11 @@ void free_params(NetState &N) {
     dev_free(N.v);
     dev_free(N.w16);
     dev_free(N.wt16);
+    dev_free(N.wc16);
     dev_free(N.w0pad);
     dev_free(N.g0pad);
     N.theta = N.grad = N.m = N.v = nullptr;
-    N.w16 = N.wt16 = N.w0pad = nullptr;
+    N.w16 = N.wt16 = N.wc16 = N.w0pad = nullptr;
     N.g0pad = nullptr;
 }
 
@@ -258,6 +260,7 @@ int alloc_params(dhfwi_ctx *ctx, NetState &N) {
     if ((rc = dev_alloc(ctx, (void **)&N.v, 4 * n))) return rc;
     if ((rc = dev_alloc(ctx, (void **)&N.w16, 2 * n))) return rc;
     if ((rc = dev_alloc(ctx, (void **)&N.wt16, 2 * n))) return rc;
+    if ((rc = dev_alloc(ctx, (void **)&N.wc16, 2 * n))) return rc;
     if ((rc = dev_alloc(ctx, (void **)&N.w0pad, 2 * 9 * CPAD * (size_t)N.base))) return rc;
     if ((rc = dev_alloc(ctx, (void **)&N.g0pad, 4 * 9 * CPAD * (size_t)N.base))) return rc;
     return DHFWI_OK;
@@ -289,8 +292,20 @@ void refresh_weights(NetState &N, cudaStream_t s, bool shadow_from_theta) {
         if (++jobs.n == TransposeJobs::MAX) flush();
     }
     flush();
+    // Tap-major copies of the transposed convs' weights (their forward GEMM's B^T).
+    TransposeJobs ct{};
+    for (size_t i = 0; i < N.L.size() && ct.n < TransposeJobs::MAX; i++) {
+        const LayerDesc &d = N.L[i];
+        if (d.kind != K_CT) continue;
+        ct.off[ct.n] = (long long)d.off;
+        ct.co[ct.n] = d.co;
+        ct.taps[ct.n] = 4;
+        ct.ci[ct.n] = d.ci;
+        ct.n++;
+    }
+    launch_convt_tapmajor_batch(N.w16, N.wc16, ct, s);
     launch_pad_first_w(N.w16 + N.L[0].off, N.base, CPAD, N.w0pad, s);
-    N.launches++;
+    N.launches += 2;
 }
 
 // Swap the current workspace with the kept one.
@@ -511,7 +526,7 @@ void forward(NetState &N, int n, int H, int W, cudaStream_t s) {
         t.Wo = W >> (r + 1);
         t.M = n * t.Ho * t.Wo;
         t.N = 4 * C(r);
-        t.bt = N.w16 + dt.off;
+        t.bt = N.wc16 + dt.off;  // tap-major rows
         t.bias = N.theta + dt.off + dt.nw;
         t.dst_bf16 = V.cat[r];
         t.dst_stride = 2 * C(r);
@@ -1277,7 +1292,17 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
     if (x_dev) launch_to_bf16(x_dev, Pin * ci, x16, s), launches++;
     if (w_dev) {
         launch_to_bf16(w_dev, nw, w16, s);
-        launch_transpose_w(w16, co, taps, ci, wt16, s);
+        if (!conv && op == DHFWI_LAYER_FWD) {  // the transposed conv's forward takes tap-major rows
+            TransposeJobs ct{};
+            ct.n = 1;
+            ct.off[0] = 0;
+            ct.co[0] = co;
+            ct.taps[0] = 4;
+            ct.ci[0] = ci;
+            launch_convt_tapmajor_batch(w16, wt16, ct, s);
+        } else {
+            launch_transpose_w(w16, co, taps, ci, wt16, s);
+        }
         launches += 2;
     }
     if (gy_dev) launch_to_bf16(gy_dev, Pout * co, g16, s), launches++;
@@ -1312,6 +1337,7 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
             a.ntaps = 1;
             a.dh[0] = a.dw[0] = 0;
             a.N = 4 * co;
+            a.bt = wt16;  // tap-major copy
             launch_fprop(a, EPI_BF16_CONVT, s);
         }
         launch_bf16_to_f32(y16, Pout * co, out_dev, s);

@@ -289,12 +289,13 @@ __global__ void __launch_bounds__(128) igemm_umma_kernel(FpropArgs P) {
                         if (nb + q < P.N) o[q] = h[q];
                 }
             } else if (EPI == EPI_BF16_CONVT) {
+                // Columns tap-major: n = (2a + b) * Co + co -> output pixel (2ho+a, 2wo+b), channel co.
+                const int Co = P.N >> 2;
 #pragma unroll
                 for (int q = 0; q < 16; q++) {
                     const int n = nb + q;
                     if (n >= P.N) continue;
-                    // n = co*4 + a*2 + b -> output pixel (2ho+a, 2wo+b), channel co.
-                    const int co = n >> 2, a = (n >> 1) & 1, b = n & 1;
+                    const int tap = n / Co, co = n - tap * Co, a = tap >> 1, b = tap & 1;
                     const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
                     P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v[q] + P.bias[co]);
                 }
@@ -471,15 +472,31 @@ __device__ __forceinline__ void conv_tile_epilogue(const FpropArgs &P, const Con
                     if (nb + e < P.N) o[e] = h[e];
             }
         } else if (EPI == EPI_BF16_CONVT) {
-            // Transposed conv: column n = co*4 + a*2 + b of coarse pixel
-            // (img, ho, wo) is fine pixel (2 ho + a, 2 wo + b), channel co.
+            // Transposed conv, columns tap-major: column n = (2a + b) Co + co
+            // of coarse pixel (img, ho, wo) is fine pixel (2 ho + a, 2 wo + b),
+            // channel co; with Co a multiple of 16 the 16 columns are 16
+            // channels of one fine pixel (one 32-byte store).
+            const int Co = P.N >> 2;
+            const int tap = nb / Co, co = nb - tap * Co;
+            const long long pix =
+                ((long long)img * (2 * P.Ho) + 2 * ho + (tap >> 1)) * (2 * P.Wo) + 2 * wo + (tap & 1);
+            __nv_bfloat16 *o = P.dst_bf16 + pix * P.dst_stride + P.dst_off + co;
+            if (full16 && (Co & 15) == 0 && ((uintptr_t)o & 15) == 0) {
+                __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
-            for (int e = 0; e < 16; e++) {
-                const int n = nb + e;
-                if (n >= P.N) continue;
-                const int co = n >> 2, a = (n >> 1) & 1, b = n & 1;
-                const long long pix = ((long long)img * (2 * P.Ho) + 2 * ho + a) * (2 * P.Wo) + 2 * wo + b;
-                P.dst_bf16[pix * P.dst_stride + P.dst_off + co] = __float2bfloat16_rn(v[e] + P.bias[co]);
+                for (int e = 0; e < 16; e++) h[e] = __float2bfloat16_rn(v[e] + P.bias[co + e]);
+                reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
+                reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    const int n = nb + e;
+                    if (n >= P.N) continue;
+                    const int t2 = n / Co, c2 = n - t2 * Co;
+                    const long long px =
+                        ((long long)img * (2 * P.Ho) + 2 * ho + (t2 >> 1)) * (2 * P.Wo) + 2 * wo + (t2 & 1);
+                    P.dst_bf16[px * P.dst_stride + P.dst_off + c2] = __float2bfloat16_rn(v[e] + P.bias[c2]);
+                }
             }
         } else if (EPI == EPI_BF16_LEAKYBWD) {
             const __nv_bfloat16 *ap = P.act + m * P.act_stride + P.act_off + nb;
