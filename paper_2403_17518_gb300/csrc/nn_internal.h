@@ -81,6 +81,14 @@ void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *d
 void launch_leaky_bwd(const float *dA, const __nv_bfloat16 *a, int as, int ao, long long P, int C, float slope,
                       __nv_bfloat16 *g, cudaStream_t s);
 void launch_f32_to_bf16_slice(const float *x, int xs, int xo, long long P, int C, __nv_bfloat16 *y, cudaStream_t s);
+// Fused forms (false: not launched, shapes or alignment not met): d(cat)
+// [P][2C] into its skip half (f32) and upsampled half (bf16); the average
+// pool's backward plus a skip gradient times the LeakyReLU derivative of
+// act, in bf16 (avgpool_bwd, add_slice and leaky_bwd in one pass).
+bool launch_split_cat(const float *src, long long P, int C, float *skip, __nv_bfloat16 *up, cudaStream_t s);
+bool launch_avgpool_bwd_leaky(const float *dy, int nimg, int H, int W, int C, const float *skip,
+                              const __nv_bfloat16 *act, int as, int ao, float slope, __nv_bfloat16 *g,
+                              cudaStream_t s);
 void launch_add_slice(const float *src, int ss, int so, long long P, int C, float *dst, cudaStream_t s);
 void launch_conv1x1_fwd(const __nv_bfloat16 *a, int C, long long P, const __nv_bfloat16 *w, const float *b, float *out,
                         cudaStream_t s);

@@ -670,6 +670,62 @@ __global__ void add_slice4_kernel(const float *__restrict__ src, int ss, int so,
     }
 }
 
+// d(cat) [P][2C] of a decoder level split into its halves: the skip half
+// copied (f32, [P][C]) for the encoder's backward, the upsampled half
+// rounded to bf16 ([P][C]) as the transposed conv's output gradient.
+__global__ void split_cat4_kernel(const float *__restrict__ src, long long P, int C4, float4 *__restrict__ skip,
+                                  Bf16x4 *__restrict__ up) {
+    const long long n = P * C4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C4;
+        const int c = (int)(i - p * C4) * 4;
+        const float *row = src + p * 8 * C4;
+        skip[i] = *reinterpret_cast<const float4 *>(row + c);
+        up[i] = f4_to_bf4(*reinterpret_cast<const float4 *>(row + 4 * C4 + c));
+    }
+}
+
+// Backward of the 3x3 / stride-2 average pool (as avgpool_bwd4_kernel),
+// plus the skip gradient of the same activation, times the LeakyReLU
+// derivative of that activation (bf16 act, stride as, offset ao): the next
+// block's output gradient g in bf16, as avgpool_bwd, add_slice and
+// leaky_bwd in turn would give it.
+__global__ void avgpool_bwd_leaky4_kernel(const float *__restrict__ dy, int nimg, int H, int W, int C4,
+                                          const float4 *__restrict__ skip, const __nv_bfloat16 *__restrict__ act,
+                                          int as, int ao, float slope, Bf16x4 *__restrict__ g) {
+    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
+    const long long n = (long long)nimg * H * W * C4;
+    const float4 *dy4 = reinterpret_cast<const float4 *>(dy);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C4);
+        const long long r0 = i / C4;
+        const int w = (int)(r0 % W);
+        const long long r1 = r0 / W;
+        const int h = (int)(r1 % H);
+        const long long img = r1 / H;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int ho = (h > 0 ? h / 2 : 0); ho <= (h + 1) / 2 && ho < Ho; ho++) {
+            if (2 * ho - 1 > h || 2 * ho + 1 < h) continue;
+            for (int wo = (w > 0 ? w / 2 : 0); wo <= (w + 1) / 2 && wo < Wo; wo++) {
+                if (2 * wo - 1 > w || 2 * wo + 1 < w) continue;
+                const float4 v = dy4[((img * Ho + ho) * Wo + wo) * C4 + c];
+                s.x += v.x;
+                s.y += v.y;
+                s.z += v.z;
+                s.w += v.w;
+            }
+        }
+        const float k = 1.0f / 9.0f;
+        const float4 o = skip[i];
+        // Rounded product then sum (no contraction), as the separate passes.
+        const float4 d = make_float4(__fadd_rn(__fmul_rn(s.x, k), o.x), __fadd_rn(__fmul_rn(s.y, k), o.y),
+                                     __fadd_rn(__fmul_rn(s.z, k), o.z), __fadd_rn(__fmul_rn(s.w, k), o.w));
+        const float4 av = bf4_to_f4(*reinterpret_cast<const Bf16x4 *>(act + r0 * as + ao + 4 * c));
+        g[i] = f4_to_bf4(make_float4(d.x * (av.x > 0.f ? 1.0f : slope), d.y * (av.y > 0.f ? 1.0f : slope),
+                                     d.z * (av.z > 0.f ? 1.0f : slope), d.w * (av.w > 0.f ? 1.0f : slope)));
+    }
+}
+
 __global__ void avgpool_fwd4_kernel(const __nv_bfloat16 *__restrict__ x, int xs, int xo, int nimg, int H, int W,
                                     int C4, Bf16x4 *__restrict__ y) {
     const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
@@ -1299,6 +1355,24 @@ void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *d
         avgpool_bwd4_kernel<<<grid_for(n / 4), 256, 0, s>>>(dy, nimg, H, W, C / 4, dx, accumulate);
     else
         avgpool_bwd_kernel<<<grid_for(n), 256, 0, s>>>(dy, nimg, H, W, C, dx, accumulate);
+}
+bool launch_split_cat(const float *src, long long P, int C, float *skip, __nv_bfloat16 *up, cudaStream_t s) {
+    if (C % 4 != 0 || (((uintptr_t)src | (uintptr_t)skip) & 15) != 0 || ((uintptr_t)up & 7) != 0) return false;
+    split_cat4_kernel<<<grid_for(P * C / 4), 256, 0, s>>>(src, P, C / 4, reinterpret_cast<float4 *>(skip),
+                                                          reinterpret_cast<Bf16x4 *>(up));
+    return true;
+}
+bool launch_avgpool_bwd_leaky(const float *dy, int nimg, int H, int W, int C, const float *skip,
+                              const __nv_bfloat16 *act, int as, int ao, float slope, __nv_bfloat16 *g,
+                              cudaStream_t s) {
+    if (C % 4 != 0 || ((as | ao) & 3) != 0 || (((uintptr_t)dy | (uintptr_t)skip) & 15) != 0 ||
+        (((uintptr_t)act | (uintptr_t)g) & 7) != 0)
+        return false;
+    const long long n = (long long)nimg * H * W * C;
+    avgpool_bwd_leaky4_kernel<<<grid_for(n / 4), 256, 0, s>>>(dy, nimg, H, W, C / 4,
+                                                              reinterpret_cast<const float4 *>(skip), act, as, ao,
+                                                              slope, reinterpret_cast<Bf16x4 *>(g));
+    return true;
 }
 void launch_leaky_bwd(const float *dA, const __nv_bfloat16 *a, int as, int ao, long long P, int C, float slope,
                       __nv_bfloat16 *g, cudaStream_t s) {

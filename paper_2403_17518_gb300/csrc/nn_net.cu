@@ -742,11 +742,15 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
         block_bwd(N, layer_index_up(N, l, 1), nullptr, nullptr, 0, 0, V.cat[r], 2 * C(r), 0, 2 * C(r), n, Hr, Wr, dA,
                   s, V.gbuf2);
         // dA = d(cat) [Pr][2C]: skip half kept, up half to bf16.
-        cudaMemsetAsync(V.dskip[r], 0, sizeof(float) * Pr * C(r), s);
-        launch_add_slice(dA, 2 * C(r), 0, Pr, C(r), V.dskip[r], s);
         before_gbuf_write(N, V.gbuf, s);
-        launch_f32_to_bf16_slice(dA, 2 * C(r), C(r), Pr, C(r), V.gbuf, s);
-        N.launches += 2;
+        if (launch_split_cat(dA, Pr, C(r), V.dskip[r], V.gbuf, s)) {
+            N.launches++;
+        } else {
+            cudaMemsetAsync(V.dskip[r], 0, sizeof(float) * Pr * C(r), s);
+            launch_add_slice(dA, 2 * C(r), 0, Pr, C(r), V.dskip[r], s);
+            launch_f32_to_bf16_slice(dA, 2 * C(r), C(r), Pr, C(r), V.gbuf, s);
+            N.launches += 2;
+        }
         // Transposed conv: input is the level-(r+1) activation.
         const int li = layer_index_up(N, l, 0);
         const LayerDesc &dt = N.L[li];
@@ -800,11 +804,13 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
         N.launches += 5;
         std::swap(dA, dB);
     }
-    // dA: gradient of the bottom activation.
+    // dA: gradient of the bottom activation.  gin: the next block's output
+    // gradient (bf16, gbuf) when the pool's backward already produced it.
+    const __nv_bfloat16 *gin = nullptr;
     for (int r = Lv; r >= 1; r--) {
         const int Hr = H >> r, Wr = W >> r;
         const long long Pr = (long long)n * Hr * Wr;
-        if (r < Lv) {
+        if (r < Lv && !gin) {
             launch_add_slice(V.dskip[r], C(r), 0, Pr, C(r), dA, s);
             N.launches++;
         }
@@ -814,21 +820,33 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
         fd.act = V.tmp[r];
         fd.stride = C(r);
         fd.g = V.gbuf2;
-        block_bwd(N, layer_index_down(N, r, 1), dA, ar, ars, 0, V.tmp[r], C(r), 0, C(r), n, Hr, Wr, nullptr, s,
-                  nullptr, fd);
+        block_bwd(N, layer_index_down(N, r, 1), gin ? nullptr : dA, ar, ars, 0, V.tmp[r], C(r), 0, C(r), n, Hr, Wr,
+                  nullptr, s, gin, fd);
         block_bwd(N, layer_index_down(N, r, 0), nullptr, nullptr, 0, 0, V.pool[r], C(r - 1), 0, C(r - 1), n, Hr, Wr,
                   dA, s, V.gbuf2);
-        launch_avgpool_bwd(dA, n, H >> (r - 1), W >> (r - 1), C(r - 1), dB, 0, s);
+        // Level r-1's output gradient: the pool's backward of dA plus the skip
+        // gradient, times the LeakyReLU derivative of that output (cat[r-1]'s
+        // first half), straight to bf16 for the next block.
+        before_gbuf_write(N, V.gbuf, s);
+        if (launch_avgpool_bwd_leaky(dA, n, H >> (r - 1), W >> (r - 1), C(r - 1), V.dskip[r - 1], V.cat[r - 1],
+                                     2 * C(r - 1), 0, 0.2f, V.gbuf, s)) {
+            gin = V.gbuf;
+        } else {
+            launch_avgpool_bwd(dA, n, H >> (r - 1), W >> (r - 1), C(r - 1), dB, 0, s);
+            std::swap(dA, dB);
+            gin = nullptr;
+        }
         N.launches++;
-        std::swap(dA, dB);
     }
-    launch_add_slice(V.dskip[0], C(0), 0, P0, C(0), dA, s);
-    N.launches++;
+    if (!gin) {
+        launch_add_slice(V.dskip[0], C(0), 0, P0, C(0), dA, s);
+        N.launches++;
+    }
     FuseNext f0;
     f0.act = V.a_inc0;
     f0.stride = C(0);
     f0.g = V.gbuf2;
-    block_bwd(N, 1, dA, V.cat[0], 2 * C(0), 0, V.a_inc0, C(0), 0, C(0), n, H, W, nullptr, s, nullptr, f0);
+    block_bwd(N, 1, gin ? nullptr : dA, V.cat[0], 2 * C(0), 0, V.a_inc0, C(0), 0, C(0), n, H, W, nullptr, s, gin, f0);
     block_bwd(N, 0, nullptr, nullptr, 0, 0, V.xin, CPAD, 0, CPAD, n, H, W, nullptr, s, V.gbuf2);
 }
 
