@@ -231,6 +231,23 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
     }
 }
 
+// Sum over the splits z = 0 .. splits-1 of p[z * stride], in split order;
+// loads are issued eight at a time so that their latencies overlap (the
+// additions keep the order, so the result is that of the plain loop).
+__device__ __forceinline__ float split_sum(const float *__restrict__ p, int splits, long long stride) {
+    float s = 0.f;
+    int z = 0;
+    for (; z + 8 <= splits; z += 8) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = p[(long long)(z + k) * stride];
+#pragma unroll
+        for (int k = 0; k < 8; k++) s += v[k];
+    }
+    for (; z < splits; z++) s += p[(long long)z * stride];
+    return s;
+}
+
 // Split-k reduction of the fprop partials (fixed split order) with the
 // epilogue of igemm_fprop_kernel.
 template <int EPI>
@@ -239,8 +256,7 @@ __global__ void fprop_reduce_kernel(FpropArgs P, int splits) {
     const int HWo = P.Ho * P.Wo;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < MN;
          idx += (long long)gridDim.x * blockDim.x) {
-        float v = 0.f;
-        for (int z = 0; z < splits; z++) v += P.part[(long long)z * MN + idx];
+        float v = split_sum(P.part + idx, splits, MN);
         const int m = (int)(idx / P.N), n = (int)(idx - (long long)m * P.N);
         if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
             v += P.bias[n];
@@ -470,9 +486,7 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, 
     if (n > nw) return;
     if (n == nw) {
         if (mode == WG_CONV) {
-            float s = 0.f;
-            for (int z = 0; z < splits; z++) s += part[(long long)z * M * N + idx];
-            db[m] = s;
+            db[m] = split_sum(part + idx, splits, (long long)M * N);
         } else if (m < co_n) {  // one thread per co sums the rows (ab*co_n + m)
             float s = 0.f;
             for (int ab = 0; ab < 4; ab++)
@@ -481,8 +495,7 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, 
         }
         return;
     }
-    float s = 0.f;
-    for (int z = 0; z < splits; z++) s += part[(long long)z * M * N + idx];
+    const float s = split_sum(part + idx, splits, (long long)M * N);
     long long o;
     if (mode == WG_CONV) {
         o = (long long)m * nw + n;

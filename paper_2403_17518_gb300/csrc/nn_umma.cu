@@ -1392,6 +1392,19 @@ bool patchp_launch(const FpropArgs &a, const ConvTile &G, bool small, cudaStream
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3_patch_persistent_kernel<BN, C, ST, EPI>,
                                                       PATCHP_THREADS, sm);
+        // The runtime's answer has come back as 1 where the launch's own
+        // limits (registers, shared memory) allow 2: take the larger of it
+        // and those limits, at most 2.
+        cudaFuncAttributes fa{};
+        int per_sm_smem = 0;
+        cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (cudaFuncGetAttributes(&fa, conv3_patch_persistent_kernel<BN, C, ST, EPI>) == cudaSuccess &&
+            fa.numRegs > 0 && per_sm_smem > 0) {
+            const int by_regs = 65536 / (((fa.numRegs * 32 + 255) / 256 * 256) * (PATCHP_THREADS / 32));
+            const int by_smem = per_sm_smem / (int)(sm + 1024);
+            occ = std::max(occ, std::min(2, std::min(by_regs, by_smem)));
+        }
+        cudaGetLastError();
         cap = nsm * std::max(occ, 1);
         attr = true;
     }
