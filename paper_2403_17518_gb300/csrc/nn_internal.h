@@ -125,6 +125,12 @@ void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const f
 void launch_absmax(const float *x, long long n, unsigned *mx, float *scale_out, cudaStream_t s);
 void launch_pad_first_w(const __nv_bfloat16 *w, int co, int cpad, __nv_bfloat16 *wp, cudaStream_t s);
 void launch_unpad_first_grad(const float *gp, int co, int cpad, float *g, cudaStream_t s);
+// Weight ([co][9]) and bias gradients of the first convolution from its
+// output gradient g ([P][co] bf16) and its one-channel input (channel 0 of
+// xin, cpad channels per pixel); part: scratch of part_floats floats.
+// Returns the kernels launched (0: scratch too small, nothing launched).
+int launch_first_wgrad(const __nv_bfloat16 *g, int co, const __nv_bfloat16 *xin, int cpad, int nimg, int H, int W,
+                       float *part, long long part_floats, float *dw, float *db, cudaStream_t s);
 void launch_loss_accum(const double *partial, int nblocks, double weight, double *acc, cudaStream_t s);
 
 }  // namespace nn

@@ -1015,6 +1015,66 @@ __global__ void absmax_finish_kernel(const unsigned *mx, float *scale_out) {
 
 // First layer (one input channel) padded to cpad channels: wp[co][tap][c] =
 // w[co][tap] for c == 0, else 0; and the gradient taken back from channel 0.
+// Weight and bias gradients of the first 3x3 convolution, whose input has
+// one real channel (channel 0 of xin, the others zero):
+//   dW[co][t] = sum_p G[p][co] x[p + shift(t)],   db[co] = sum_p G[p][co],
+// a reduction over the pixels on CUDA cores (the tensor-core GEMM would
+// spend 72 of its 80 columns on the zero channels).  Block b takes a run
+// of pixels; lane = output channel (32 per pass), the 8 warps interleave
+// pixels; per-block sums [b][co][10] in a fixed order, then
+// first_wgrad_final_kernel sums the blocks in order.
+__global__ void __launch_bounds__(256) first_wgrad_kernel(const __nv_bfloat16 *__restrict__ g, int co_n,
+                                                          const __nv_bfloat16 *__restrict__ xin, int cpad, int nimg,
+                                                          int H, int W, long long ppb, float *__restrict__ part) {
+    __shared__ float red[8][32][10];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long P = (long long)nimg * H * W;
+    const long long p0 = blockIdx.x * ppb, p1 = p0 + ppb < P ? p0 + ppb : P;
+    for (int cb = 0; cb < co_n; cb += 32) {
+        const int co = cb + lane;
+        const bool valid = co < co_n;
+        float acc[10];
+#pragma unroll
+        for (int k = 0; k < 10; k++) acc[k] = 0.f;
+        for (long long p = p0 + warp; p < p1; p += 8) {
+            const int w = (int)(p % W), h = (int)((p / W) % H);
+            const float gv = valid ? __bfloat162float(g[p * co_n + co]) : 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; t++) {
+                const int dh = t / 3 - 1, dw = t % 3 - 1;
+                const bool in = h + dh >= 0 && h + dh < H && w + dw >= 0 && w + dw < W;
+                const float xv = in ? __bfloat162float(xin[(p + (long long)dh * W + dw) * cpad]) : 0.f;
+                acc[t] += gv * xv;
+            }
+            acc[9] += gv;
+        }
+#pragma unroll
+        for (int k = 0; k < 10; k++) red[warp][lane][k] = acc[k];
+        __syncthreads();
+        if (warp == 0 && valid) {
+#pragma unroll
+            for (int k = 0; k < 10; k++) {
+                float t = 0.f;
+                for (int q = 0; q < 8; q++) t += red[q][lane][k];
+                part[((long long)blockIdx.x * co_n + co) * 10 + k] = t;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// dw[co][9] and db[co] from the per-block sums (blocks in order).
+__global__ void first_wgrad_final_kernel(const float *__restrict__ part, int nblk, int co_n, float *__restrict__ dw,
+                                         float *__restrict__ db) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= co_n * 10) return;
+    const int co = i / 10, k = i - co * 10;
+    float s = 0.f;
+    for (int b = 0; b < nblk; b++) s += part[((long long)b * co_n + co) * 10 + k];
+    if (k < 9) dw[co * 9 + k] = s;
+    else db[co] = s;
+}
+
 __global__ void pad_first_w_kernel(const __nv_bfloat16 *__restrict__ w, int co, int cpad,
                                    __nv_bfloat16 *__restrict__ wp) {
     const int n = co * 9 * cpad;
@@ -1474,6 +1534,18 @@ void launch_pad_image(const float *img, int nz, int nx, int Hp, int Wp, const fl
 void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const float *scale, float *dst,
                        cudaStream_t s) {
     crop_image_kernel<<<grid_for((long long)nz * nx), 256, 0, s>>>(src, Hp, Wp, nz, nx, scale, dst);
+}
+int launch_first_wgrad(const __nv_bfloat16 *g, int co, const __nv_bfloat16 *xin, int cpad, int nimg, int H, int W,
+                       float *part, long long part_floats, float *dw, float *db, cudaStream_t s) {
+    const long long P = (long long)nimg * H * W;
+    int nblk = (int)std::min<long long>(152 * 4, (P + 255) / 256);
+    if (nblk < 1) nblk = 1;
+    if ((long long)nblk * co * 10 > part_floats) nblk = (int)(part_floats / (10LL * co));
+    if (nblk < 1) return 0;
+    const long long ppb = (P + nblk - 1) / nblk;
+    first_wgrad_kernel<<<nblk, 256, 0, s>>>(g, co, xin, cpad, nimg, H, W, ppb, part);
+    first_wgrad_final_kernel<<<(co * 10 + 255) / 256, 256, 0, s>>>(part, nblk, co, dw, db);
+    return 2;
 }
 void launch_pad_first_w(const __nv_bfloat16 *w, int co, int cpad, __nv_bfloat16 *wp, cudaStream_t s) {
     pad_first_w_kernel<<<grid_for((long long)co * 9 * cpad), 256, 0, s>>>(w, co, cpad, wp);

@@ -636,11 +636,19 @@ void block_bwd(NetState &N, int li, const float *dA, const __nv_bfloat16 *a, int
     w.part = N.wg_part;
     w.err = N.err;
     const int sp = wgrad_splits(P, w.M, w.N);
-    float *dw = li == 0 ? N.g0pad : N.grad + d.off;
-    N.launches += launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, ws);
-    if (li == 0) {
-        launch_unpad_first_grad(N.g0pad, d.co, CPAD, N.grad + d.off, ws);
-        N.launches++;
+    // The first layer (one real input channel): a pixel reduction on CUDA cores.
+    const int first = li == 0 ? launch_first_wgrad(g, d.co, x, xs, nimg, H, W, N.wg_part, (long long)N.wg_part_floats,
+                                                   N.grad + d.off, N.grad + d.off + d.nw, ws)
+                              : 0;
+    if (first) {
+        N.launches += first;
+    } else {
+        float *dw = li == 0 ? N.g0pad : N.grad + d.off;
+        N.launches += launch_wgrad(w, sp, dw, N.grad + d.off + d.nw, ws);
+        if (li == 0) {
+            launch_unpad_first_grad(N.g0pad, d.co, CPAD, N.grad + d.off, ws);
+            N.launches++;
+        }
     }
     after_wgrad(N, g);
     if (dx || next.g) {
