@@ -474,28 +474,48 @@ __global__ void __launch_bounds__(128) igemm_wgrad_kernel(WgradArgs P) {
         }
 }
 
-// Sum of the split partials in split order; writes the weight gradient in
-// the parameter layout (conv: [co][tap][ci] = C[co][n]; transposed conv:
-// [co][a][b][ci] = C[(a*2+b)*Co + co][ci]) and the bias gradient from the
-// ones column (transposed conv: summed over the four (a, b) rows).
+// Reduction of the weight-gradient split-k partials (fixed order): block
+// (32, ny) takes 32 consecutive outputs; thread (x, y) sums the splits
+// z = y, y + ny, ... in order (loads eight at a time), and the ny partial
+// sums are added in y order.  The weight gradient goes out in the parameter
+// layout (conv: [co][tap][ci] = C[co][n]; transposed conv: [co][a][b][ci] =
+// C[(a*2+b)*Co + co][ci]), the bias column (n = nw) to db (transposed conv:
+// summed over the four sub-pixel rows ab * co_n + m of output channel m).
 __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, int M, int N, int nw, int mode,
                                     int co_n, float *__restrict__ dw, float *__restrict__ db) {
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)M * N) return;
-    const int m = (int)(idx / N), n = (int)(idx - (long long)m * N);
-    if (n > nw) return;
-    if (n == nw) {
-        if (mode == WG_CONV) {
-            db[m] = split_sum(part + idx, splits, (long long)M * N);
-        } else if (m < co_n) {  // one thread per co sums the rows (ab*co_n + m)
-            float s = 0.f;
-            for (int ab = 0; ab < 4; ab++)
-                for (int z = 0; z < splits; z++) s += part[(long long)z * M * N + (long long)(ab * co_n + m) * N + n];
-            db[m] = s;
+    __shared__ float red[8][32];
+    const long long MN = (long long)M * N;
+    const long long idx = blockIdx.x * 32LL + threadIdx.x;
+    const int ty = threadIdx.y, ny = blockDim.y;
+    const bool in = idx < MN;
+    const int m = in ? (int)(idx / N) : 0, n = in ? (int)(idx - (long long)m * N) : 0;
+    float s = 0.f;
+    if (in && n <= nw) {
+        if (n == nw && mode != WG_CONV) {
+            if (m < co_n)
+                for (int ab = 0; ab < 4; ab++)
+                    for (int z = ty; z < splits; z += ny) s += part[(long long)z * MN + (long long)(ab * co_n + m) * N + n];
+        } else {
+            int z = ty;
+            for (; z + 7 * ny < splits; z += 8 * ny) {
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) v[k] = part[(long long)(z + k * ny) * MN + idx];
+#pragma unroll
+                for (int k = 0; k < 8; k++) s += v[k];
+            }
+            for (; z < splits; z += ny) s += part[(long long)z * MN + idx];
         }
+    }
+    red[ty][threadIdx.x] = s;
+    __syncthreads();
+    if (ty != 0 || !in || n > nw) return;
+    float t = 0.f;
+    for (int y = 0; y < ny; y++) t += red[y][threadIdx.x];
+    if (n == nw) {
+        if (mode == WG_CONV || m < co_n) db[m] = t;
         return;
     }
-    const float s = split_sum(part + idx, splits, (long long)M * N);
     long long o;
     if (mode == WG_CONV) {
         o = (long long)m * nw + n;
@@ -503,7 +523,7 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, 
         const int ab = m / co_n, co = m - ab * co_n;
         o = ((long long)co * 4 + ab) * nw + n;
     }
-    dw[o] = s;
+    dw[o] = t;
 }
 
 // One warp per channel: lane l sums the partials l, l+32, ..., then a
@@ -1402,14 +1422,14 @@ int launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStrea
     const long long mn = (long long)a.M * a.N;
     const int tsp = launch_wgrad_tma(a, splits, s);
     if (tsp > 0) {  // partials with the bias column: weight and bias gradients in one reduction
-        wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, tsp, a.M, a.N, a.nw, a.mode, a.co, dw,
-                                                                     db);
+        wgrad_reduce_kernel<<<(int)((mn + 31) / 32), dim3(32, std::min(8, tsp)), 0, s>>>(a.part, tsp, a.M, a.N, a.nw,
+                                                                                           a.mode, a.co, dw, db);
         return 2;
     }
     if (wgrad_narrow(a.M)) wgrad_launch<1, 4>(a, splits, s);
     else wgrad_launch<2, 2>(a, splits, s);
-    wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, splits, a.M, a.N, a.nw, a.mode, a.co, dw,
-                                                                 db);
+    wgrad_reduce_kernel<<<(int)((mn + 31) / 32), dim3(32, std::max(1, std::min(8, splits))), 0, s>>>(
+        a.part, splits, a.M, a.N, a.nw, a.mode, a.co, dw, db);
     return 2;
 }
 
