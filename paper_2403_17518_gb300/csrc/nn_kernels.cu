@@ -231,32 +231,34 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
     }
 }
 
-// Sum over the splits z = 0 .. splits-1 of p[z * stride], in split order;
-// loads are issued eight at a time so that their latencies overlap (the
-// additions keep the order, so the result is that of the plain loop).
-__device__ __forceinline__ float split_sum(const float *__restrict__ p, int splits, long long stride) {
-    float s = 0.f;
-    int z = 0;
-    for (; z + 8 <= splits; z += 8) {
-        float v[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) v[k] = p[(long long)(z + k) * stride];
-#pragma unroll
-        for (int k = 0; k < 8; k++) s += v[k];
-    }
-    for (; z < splits; z++) s += p[(long long)z * stride];
-    return s;
-}
-
 // Split-k reduction of the fprop partials (fixed split order) with the
 // epilogue of igemm_fprop_kernel.
+// Block (32, ny): 32 consecutive outputs, thread (x, y) summing the splits
+// z = y, y + ny, ... in order; the ny group sums are added in y order.
 template <int EPI>
 __global__ void fprop_reduce_kernel(FpropArgs P, int splits) {
+    __shared__ float red[8][32];
     const long long MN = (long long)P.M * P.N;
     const int HWo = P.Ho * P.Wo;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < MN;
-         idx += (long long)gridDim.x * blockDim.x) {
-        float v = split_sum(P.part + idx, splits, MN);
+    const long long idx = blockIdx.x * 32LL + threadIdx.x;
+    const int ty = threadIdx.y, ny = blockDim.y;
+    float s = 0.f;
+    if (idx < MN) {
+        int z = ty;
+        for (; z + 7 * ny < splits; z += 8 * ny) {
+            float u[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) u[k] = P.part[(long long)(z + k * ny) * MN + idx];
+#pragma unroll
+            for (int k = 0; k < 8; k++) s += u[k];
+        }
+        for (; z < splits; z += ny) s += P.part[(long long)z * MN + idx];
+    }
+    red[ty][threadIdx.x] = s;
+    __syncthreads();
+    if (ty == 0 && idx < MN) {
+        float v = 0.f;
+        for (int y = 0; y < ny; y++) v += red[y][threadIdx.x];
         const int m = (int)(idx / P.N), n = (int)(idx - (long long)m * P.N);
         if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
             v += P.bias[n];
@@ -1298,14 +1300,16 @@ static void fprop_launch(const FpropArgs &a, cudaStream_t s) {
 }
 
 void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s) {
-    const int g = grid_for((long long)a.M * a.N);
+    // Output blocks of 32, split groups of up to 8 (see fprop_reduce_kernel).
+    const int g = (int)(((long long)a.M * a.N + 31) / 32);
+    const dim3 b(32, std::max(1, std::min(8, splits)));
     switch (epi) {
-    case EPI_BF16_LEAKY: fprop_reduce_kernel<EPI_BF16_LEAKY><<<g, 256, 0, s>>>(a, splits); break;
-    case EPI_BF16: fprop_reduce_kernel<EPI_BF16><<<g, 256, 0, s>>>(a, splits); break;
-    case EPI_BF16_CONVT: fprop_reduce_kernel<EPI_BF16_CONVT><<<g, 256, 0, s>>>(a, splits); break;
-    case EPI_F32: fprop_reduce_kernel<EPI_F32><<<g, 256, 0, s>>>(a, splits); break;
-    case EPI_BF16_LEAKYBWD: fprop_reduce_kernel<EPI_BF16_LEAKYBWD><<<g, 256, 0, s>>>(a, splits); break;
-    default: fprop_reduce_kernel<EPI_F32_ADD><<<g, 256, 0, s>>>(a, splits); break;
+    case EPI_BF16_LEAKY: fprop_reduce_kernel<EPI_BF16_LEAKY><<<g, b, 0, s>>>(a, splits); break;
+    case EPI_BF16: fprop_reduce_kernel<EPI_BF16><<<g, b, 0, s>>>(a, splits); break;
+    case EPI_BF16_CONVT: fprop_reduce_kernel<EPI_BF16_CONVT><<<g, b, 0, s>>>(a, splits); break;
+    case EPI_F32: fprop_reduce_kernel<EPI_F32><<<g, b, 0, s>>>(a, splits); break;
+    case EPI_BF16_LEAKYBWD: fprop_reduce_kernel<EPI_BF16_LEAKYBWD><<<g, b, 0, s>>>(a, splits); break;
+    default: fprop_reduce_kernel<EPI_F32_ADD><<<g, b, 0, s>>>(a, splits); break;
     }
 }
 
