@@ -125,6 +125,11 @@ void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const f
 void launch_absmax(const float *x, long long n, unsigned *mx, float *scale_out, cudaStream_t s);
 void launch_pad_first_w(const __nv_bfloat16 *w, int co, int cpad, __nv_bfloat16 *wp, cudaStream_t s);
 void launch_unpad_first_grad(const float *gp, int co, int cpad, float *g, cudaStream_t s);
+// The first convolution (one real input channel, channel 0 of xin; weights
+// bf16 [co][9]) with bias and LeakyReLU into y (bf16, row stride ys), on
+// CUDA cores; false when co or the output alignment does not allow it.
+bool launch_first_conv(const __nv_bfloat16 *xin, int cpad, int nimg, int H, int W, const __nv_bfloat16 *w,
+                       const float *bias, int co, float slope, __nv_bfloat16 *y, int ys, cudaStream_t s);
 // Weight ([co][9]) and bias gradients of the first convolution from its
 // output gradient g ([P][co] bf16) and its one-channel input (channel 0 of
 // xin, cpad channels per pixel); part: scratch of part_floats floats.

@@ -1097,6 +1097,47 @@ __global__ void first_wgrad_final_kernel(const float *__restrict__ part, int nbl
     else db[co] = s;
 }
 
+// The first 3x3 convolution (one real input channel: channel 0 of xin) with
+// bias and LeakyReLU, on CUDA cores: y[p][co] = leaky(sum_t W[co][t]
+// x[p + shift(t)] + b[co]) in bf16.  Thread: one pixel, 8 output channels
+// (fp32 sums over the taps in order; 16-byte store); the weights (bf16
+// [co][9]) and the bias are staged in shared memory as floats.
+__global__ void __launch_bounds__(256) first_conv_kernel(const __nv_bfloat16 *__restrict__ xin, int cpad, int nimg,
+                                                         int H, int W, const __nv_bfloat16 *__restrict__ w,
+                                                         const float *__restrict__ bias, int co_n, float slope,
+                                                         __nv_bfloat16 *__restrict__ y, int ys) {
+    extern __shared__ float sw[];  // [co_n][9] weights, then [co_n] bias
+    for (int i = threadIdx.x; i < co_n * 10; i += blockDim.x)
+        sw[i] = i < co_n * 9 ? __bfloat162float(w[i]) : bias[i - co_n * 9];
+    __syncthreads();
+    const int groups = co_n / 8;
+    const long long P = (long long)nimg * H * W;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P * groups;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long p = t / groups;
+        const int g = (int)(t - p * groups), c0 = 8 * g;
+        const int w0 = (int)(p % W), h0 = (int)((p / W) % H);
+        float xv[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const int dh = k / 3 - 1, dw = k % 3 - 1;
+            const bool in = h0 + dh >= 0 && h0 + dh < H && w0 + dw >= 0 && w0 + dw < W;
+            xv[k] = in ? __bfloat162float(xin[(p + (long long)dh * W + dw) * cpad]) : 0.f;
+        }
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const float *wr = sw + (c0 + e) * 9;
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; k++) a = fmaf(wr[k], xv[k], a);
+            a += sw[co_n * 9 + c0 + e];
+            o[e] = __float2bfloat16_rn(a > 0.f ? a : slope * a);
+        }
+        *reinterpret_cast<uint4 *>(y + p * ys + c0) = *reinterpret_cast<const uint4 *>(o);
+    }
+}
+
 __global__ void pad_first_w_kernel(const __nv_bfloat16 *__restrict__ w, int co, int cpad,
                                    __nv_bfloat16 *__restrict__ wp) {
     const int n = co * 9 * cpad;
@@ -1295,7 +1336,7 @@ static void fprop_launch(const FpropArgs &a, cudaStream_t s) {
     igemm_fprop_kernel<BN, EPI><<<grid, 128, sm, s>>>(b);
     if (splits > 1) {
         const long long mn = (long long)a.M * a.N;
-        fprop_reduce_kernel<EPI><<<grid_for(mn), 256, 0, s>>>(b, splits);
+        fprop_reduce_kernel<EPI><<<(int)((mn + 31) / 32), dim3(32, std::min(8, splits)), 0, s>>>(b, splits);
     }
 }
 
@@ -1570,6 +1611,14 @@ int launch_first_wgrad(const __nv_bfloat16 *g, int co, const __nv_bfloat16 *xin,
     first_wgrad_kernel<<<nblk, 256, 0, s>>>(g, co, xin, cpad, nimg, H, W, ppb, part);
     first_wgrad_final_kernel<<<(co * 10 + 255) / 256, 256, 0, s>>>(part, nblk, co, dw, db);
     return 2;
+}
+bool launch_first_conv(const __nv_bfloat16 *xin, int cpad, int nimg, int H, int W, const __nv_bfloat16 *w,
+                       const float *bias, int co, float slope, __nv_bfloat16 *y, int ys, cudaStream_t s) {
+    if (co % 8 != 0 || ys % 8 != 0 || ((uintptr_t)y & 15) != 0) return false;
+    const long long work = (long long)nimg * H * W * (co / 8);
+    first_conv_kernel<<<grid_for(work), 256, sizeof(float) * co * 10, s>>>(xin, cpad, nimg, H, W, w, bias, co, slope,
+                                                                          y, ys);
+    return true;
 }
 void launch_pad_first_w(const __nv_bfloat16 *w, int co, int cpad, __nv_bfloat16 *wp, cudaStream_t s) {
     pad_first_w_kernel<<<grid_for((long long)co * 9 * cpad), 256, 0, s>>>(w, co, cpad, wp);

@@ -489,7 +489,13 @@ void forward(NetState &N, int n, int H, int W, cudaStream_t s) {
     NetState::Views &V = N.V;
     launch_input_pack(V.xf, (long long)n * H * W, CPAD, V.xin, s);
     N.launches++;
-    conv3_fwd(N, N.L[0], N.w0pad, n, H, W, V.xin, CPAD, 0, CPAD, V.a_inc0, C(0), 0, EPI_BF16_LEAKY, s);
+    // First layer: one real input channel, on CUDA cores (the GEMM would
+    // spend 7 of its 8 padded channels on zeros).
+    if (launch_first_conv(V.xin, CPAD, n, H, W, N.w16 + N.L[0].off, N.theta + N.L[0].off + N.L[0].nw, C(0), 0.2f,
+                          V.a_inc0, C(0), s))
+        N.launches++;
+    else
+        conv3_fwd(N, N.L[0], N.w0pad, n, H, W, V.xin, CPAD, 0, CPAD, V.a_inc0, C(0), 0, EPI_BF16_LEAKY, s);
     conv3_fwd(N, N.L[1], N.w16 + N.L[1].off, n, H, W, V.a_inc0, C(0), 0, C(0), V.cat[0], 2 * C(0), 0,
               EPI_BF16_LEAKY, s);
     for (int r = 1; r <= Lv; r++) {
