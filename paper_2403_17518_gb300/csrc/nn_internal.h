@@ -52,6 +52,10 @@ struct WgradArgs {
     const __nv_bfloat16 *ones;  // 8 bf16 values {1, 0, ..., 0}
     float *part;                // [splits][M][N]
     unsigned *err;              // nullable: set to 1 by a tensor-core GEMM whose bounded wait ran out
+    // WG_CONVT only: g is the output gradient in space-to-depth layout
+    // [coarse pixel][ab][co] (row stride g_stride = 4 co), i.e. column m =
+    // ab*Co + co of coarse pixel k, so the weight gradient is a one-tap GEMM.
+    bool g_s2d = false;
 };
 
 // mma.sync GEMM (igemm_fprop_kernel), or the tcgen05 one (nn_umma.cu) when
@@ -82,10 +86,15 @@ void launch_leaky_bwd(const float *dA, const __nv_bfloat16 *a, int as, int ao, l
                       __nv_bfloat16 *g, cudaStream_t s);
 void launch_f32_to_bf16_slice(const float *x, int xs, int xo, long long P, int C, __nv_bfloat16 *y, cudaStream_t s);
 // Fused forms (false: not launched, shapes or alignment not met): d(cat)
-// [P][2C] into its skip half (f32) and upsampled half (bf16); the average
+// [P][2C] on an H x W grid into its skip half (f32, [P][C]) and upsampled
+// half (bf16, space-to-depth onto the H/2 x W/2 grid, see WgradArgs::g_s2d); the average
 // pool's backward plus a skip gradient times the LeakyReLU derivative of
 // act, in bf16 (avgpool_bwd, add_slice and leaky_bwd in one pass).
-bool launch_split_cat(const float *src, long long P, int C, float *skip, __nv_bfloat16 *up, cudaStream_t s);
+bool launch_split_cat(const float *src, int nimg, int H, int W, int C, float *skip, __nv_bfloat16 *up,
+                      cudaStream_t s);
+// f32 output gradient of a transposed conv on the fine grid (nimg x 2H x 2W x
+// C) into bf16 space-to-depth layout [nimg][H][W][2a+b][C].
+void launch_to_bf16_s2d(const float *x, int nimg, int H, int W, int C, __nv_bfloat16 *y, cudaStream_t s);
 bool launch_avgpool_bwd_leaky(const float *dy, int nimg, int H, int W, int C, const float *skip,
                               const __nv_bfloat16 *act, int as, int ao, float slope, __nv_bfloat16 *g,
                               cudaStream_t s);

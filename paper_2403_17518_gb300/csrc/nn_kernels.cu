@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(128) igemm_wgrad_kernel(WgradArgs P) {
             const bool ok = k < ke && m < P.M;
             const __nv_bfloat16 *src = P.g;
             if (ok) {
-                if (P.mode == WG_CONV) {
+                if (P.mode == WG_CONV || P.g_s2d) {  // (space-to-depth: column m of coarse pixel k)
                     src = P.g + (long long)k * P.g_stride + m;
                 } else {  // WG_CONVT: m = ab*Co + co at the fine pixel (2h + a, 2w + b)
                     const int img = k / HW;
@@ -705,18 +705,40 @@ __global__ void add_slice4_kernel(const float *__restrict__ src, int ss, int so,
     }
 }
 
-// d(cat) [P][2C] of a decoder level split into its halves: the skip half
-// copied (f32, [P][C]) for the encoder's backward, the upsampled half
-// rounded to bf16 ([P][C]) as the transposed conv's output gradient.
-__global__ void split_cat4_kernel(const float *__restrict__ src, long long P, int C4, float4 *__restrict__ skip,
-                                  Bf16x4 *__restrict__ up) {
-    const long long n = P * C4;
+// d(cat) [P][2C] of a decoder level (H x W grid) split into its halves: the
+// skip half copied (f32, [P][C]) for the encoder's backward, the upsampled
+// half rounded to bf16 in space-to-depth layout [img][H/2][W/2][2a+b][C]
+// (fine pixel (2h+a, 2w+b)) as the transposed conv's output gradient.
+__global__ void split_cat4_kernel(const float *__restrict__ src, int nimg, int H, int W, int C4,
+                                  float4 *__restrict__ skip, Bf16x4 *__restrict__ up) {
+    const long long n = (long long)nimg * H * W * C4;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const long long p = i / C4;
-        const int c = (int)(i - p * C4) * 4;
+        const int c = (int)(i - p * C4);
+        const int w = (int)(p % W);
+        const long long r = p / W;
+        const int h = (int)(r % H);
+        const long long img = r / H;
         const float *row = src + p * 8 * C4;
-        skip[i] = *reinterpret_cast<const float4 *>(row + c);
-        up[i] = f4_to_bf4(*reinterpret_cast<const float4 *>(row + 4 * C4 + c));
+        skip[i] = *reinterpret_cast<const float4 *>(row + 4 * c);
+        const long long q = ((img * (H / 2) + h / 2) * (W / 2) + w / 2) * 4 + (h & 1) * 2 + (w & 1);
+        up[q * C4 + c] = f4_to_bf4(*reinterpret_cast<const float4 *>(row + 4 * C4 + 4 * c));
+    }
+}
+
+// f32 [img][2H][2W][C] -> bf16 space-to-depth [img][H][W][2a+b][C].
+__global__ void to_bf16_s2d_kernel(const float *__restrict__ x, int nimg, int H, int W, int C,
+                                   __nv_bfloat16 *__restrict__ y) {
+    const long long n = (long long)nimg * 4 * H * W * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long p = i / C;  // fine pixel
+        const int w = (int)(p % (2 * W));
+        const long long r = p / (2 * W);
+        const int h = (int)(r % (2 * H));
+        const long long img = r / (2 * H);
+        const long long q = ((img * H + h / 2) * W + w / 2) * 4 + (h & 1) * 2 + (w & 1);
+        y[q * C + c] = __float2bfloat16_rn(x[i]);
     }
 }
 
@@ -1494,11 +1516,17 @@ void launch_avgpool_bwd(const float *dy, int nimg, int H, int W, int C, float *d
     else
         avgpool_bwd_kernel<<<grid_for(n), 256, 0, s>>>(dy, nimg, H, W, C, dx, accumulate);
 }
-bool launch_split_cat(const float *src, long long P, int C, float *skip, __nv_bfloat16 *up, cudaStream_t s) {
-    if (C % 4 != 0 || (((uintptr_t)src | (uintptr_t)skip) & 15) != 0 || ((uintptr_t)up & 7) != 0) return false;
-    split_cat4_kernel<<<grid_for(P * C / 4), 256, 0, s>>>(src, P, C / 4, reinterpret_cast<float4 *>(skip),
+bool launch_split_cat(const float *src, int nimg, int H, int W, int C, float *skip, __nv_bfloat16 *up,
+                      cudaStream_t s) {
+    if (C % 4 != 0 || (H | W) & 1 || (((uintptr_t)src | (uintptr_t)skip) & 15) != 0 || ((uintptr_t)up & 7) != 0)
+        return false;
+    const long long P = (long long)nimg * H * W;
+    split_cat4_kernel<<<grid_for(P * C / 4), 256, 0, s>>>(src, nimg, H, W, C / 4, reinterpret_cast<float4 *>(skip),
                                                           reinterpret_cast<Bf16x4 *>(up));
     return true;
+}
+void launch_to_bf16_s2d(const float *x, int nimg, int H, int W, int C, __nv_bfloat16 *y, cudaStream_t s) {
+    to_bf16_s2d_kernel<<<grid_for((long long)nimg * 4 * H * W * C), 256, 0, s>>>(x, nimg, H, W, C, y);
 }
 bool launch_avgpool_bwd_leaky(const float *dy, int nimg, int H, int W, int C, const float *skip,
                               const __nv_bfloat16 *act, int as, int ao, float slope, __nv_bfloat16 *g,

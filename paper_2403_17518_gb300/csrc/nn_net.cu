@@ -755,9 +755,12 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
         // up_l.0: output dec0, input cat (2C).
         block_bwd(N, layer_index_up(N, l, 1), nullptr, nullptr, 0, 0, V.cat[r], 2 * C(r), 0, 2 * C(r), n, Hr, Wr, dA,
                   s, V.gbuf2);
-        // dA = d(cat) [Pr][2C]: skip half kept, up half to bf16.
+        // dA = d(cat) [Pr][2C]: skip half kept, up half to bf16 in
+        // space-to-depth layout on the coarse grid (the transposed conv's
+        // gradients are then one-tap GEMMs).
         before_gbuf_write(N, V.gbuf, s);
-        if (launch_split_cat(dA, Pr, C(r), V.dskip[r], V.gbuf, s)) {
+        const bool s2d = launch_split_cat(dA, n, Hr, Wr, C(r), V.dskip[r], V.gbuf, s);
+        if (s2d) {
             N.launches++;
         } else {
             cudaMemsetAsync(V.dskip[r], 0, sizeof(float) * Pr * C(r), s);
@@ -773,7 +776,8 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
         WgradArgs w{};
         w.mode = WG_CONVT;
         w.g = V.gbuf;
-        w.g_stride = C(r);
+        w.g_stride = s2d ? 4 * C(r) : C(r);
+        w.g_s2d = s2d;
         w.x = xin;
         w.x_stride = C(r + 1);
         w.x_off = 0;
@@ -781,27 +785,39 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
         w.H = Hc;
         w.W = Wc;
         w.co = C(r);
+        w.ci = C(r + 1);
         w.M = 4 * C(r);
         w.nw = C(r + 1);
         w.N = w.nw + 8;
         w.ones = N.ones;
         w.part = N.wg_part;
+        w.err = N.err;
         const int sp = wgrad_splits((long long)n * Hc * Wc, w.M, w.N);
         fork_wgrad(N, s);
         launch_wgrad(w, sp, N.grad + dt.off, N.grad + dt.off + dt.nw, wgrad_stream(N, s));
         after_wgrad(N, V.gbuf);
         FpropArgs a{};
         a.src = V.gbuf;
-        a.src_stride = C(r);
         a.src_off = 0;
-        a.Hs = Hr;
-        a.Ws = Wr;
-        a.C = C(r);
-        a.ntaps = 4;
-        a.scale = 2;
-        for (int t = 0; t < 4; t++) {
-            a.dh[t] = t >> 1;
-            a.dw[t] = t & 1;
+        if (s2d) {  // input gradient: the one-tap GEMM over the 4 C(r) space-to-depth channels
+            a.src_stride = 4 * C(r);
+            a.Hs = Hc;
+            a.Ws = Wc;
+            a.C = 4 * C(r);
+            a.ntaps = 1;
+            a.scale = 1;
+            a.dh[0] = a.dw[0] = 0;
+        } else {
+            a.src_stride = C(r);
+            a.Hs = Hr;
+            a.Ws = Wr;
+            a.C = C(r);
+            a.ntaps = 4;
+            a.scale = 2;
+            for (int t = 0; t < 4; t++) {
+                a.dh[t] = t >> 1;
+                a.dw[t] = t & 1;
+            }
         }
         a.Ho = Hc;
         a.Wo = Wc;
@@ -1337,7 +1353,13 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
         }
         launches += 2;
     }
-    if (gy_dev) launch_to_bf16(gy_dev, Pout * co, g16, s), launches++;
+    // The transposed conv's output gradient in space-to-depth layout, as the
+    // network's backward pass keeps it.
+    if (gy_dev) {
+        if (conv) launch_to_bf16(gy_dev, Pout * co, g16, s);
+        else launch_to_bf16_s2d(gy_dev, n, H, W, co, g16, s);
+        launches++;
+    }
     if (op == DHFWI_LAYER_FWD) {
         FpropArgs a{};
         a.src = x16;
@@ -1398,13 +1420,14 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
                 a.dh[t] = 1 - t / 3;
                 a.dw[t] = 1 - t % 3;
             }
-        } else {
-            a.ntaps = 4;
-            a.scale = 2;
-            for (int t = 0; t < 4; t++) {
-                a.dh[t] = t >> 1;
-                a.dw[t] = t & 1;
-            }
+        } else {  // one tap over the 4 co space-to-depth channels of the coarse grid
+            a.src_stride = 4 * co;
+            a.C = 4 * co;
+            a.Hs = H;
+            a.Ws = W;
+            a.ntaps = 1;
+            a.scale = 1;
+            a.dh[0] = a.dw[0] = 0;
         }
         launch_fprop(a, EPI_F32, s);
         launches += 2;
@@ -1412,7 +1435,8 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
         WgradArgs w{};
         w.mode = conv ? WG_CONV : WG_CONVT;
         w.g = g16;
-        w.g_stride = co;
+        w.g_stride = conv ? co : 4 * co;
+        w.g_s2d = !conv;
         w.x = x16;
         w.x_stride = ci;
         w.nimg = n;

@@ -1519,8 +1519,10 @@ struct WgradTile {
     int BW, BH, BI, tw, th;
     int npb;        // pixel blocks in total
     int per;        // pixel blocks per split
-    int pairs;      // (tap, 64-channel block) pairs: 9 * ci / 64
+    int pairs;      // (tap, 64-channel block) pairs: taps * ci / 64
     int nimg;
+    int taps;       // 9 (3x3 conv, taps shifted by -1..1) or 1 (no shift: a transposed conv's
+                    // gradient in space-to-depth layout)
 };
 
 template <int NB, int ST>
@@ -1593,7 +1595,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                 const unsigned sa = sbase + s * STAGE, sb = sa + A_BYTES;
                 for (int h = 0; h < (two ? 2 : 1); h++) {
                     const int t = tapv[h];
-                    tma_load_4d(sa + h * BOX, &mapX, cbv[h] * 64, w0 + (t % 3) - 1, h0 + (t / 3) - 1, i0, fb);
+                    const int sw = G.taps == 9 ? t % 3 - 1 : 0, sh = G.taps == 9 ? t / 3 - 1 : 0;
+                    tma_load_4d(sa + h * BOX, &mapX, cbv[h] * 64, w0 + sw, h0 + sh, i0, fb);
                 }
 #pragma unroll
                 for (int j = 0; j < NB / 64; j++) tma_load_4d(sb + j * BOX, &mapG, co0 + 64 * j, w0, h0, i0, fb);
@@ -1722,7 +1725,8 @@ int wgrad_tma_launch(const WgradArgs &a, int max_splits, cudaStream_t s) {
     G.tw = (a.W + G.BW - 1) / G.BW;
     G.th = (a.H + G.BH - 1) / G.BH;
     G.npb = G.tw * G.th * ((a.nimg + G.BI - 1) / G.BI);
-    G.pairs = 9 * ((a.ci + 63) / 64);
+    G.taps = a.mode == WG_CONV ? 9 : 1;
+    G.pairs = G.taps * ((a.ci + 63) / 64);
     const int mt = (G.pairs + 1) / 2, ntl = (a.M + NB - 1) / NB;
     const int tiles = mt * ntl;
     // One CTA per SM (~192 KB of stages): at most one wave, so that no CTA
@@ -1775,7 +1779,8 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
     // Also the transposed conv's forward GEMM: one tap without shift on the
     // coarse grid, scattered to the fine grid by the epilogue.
     const bool one_tap = a.ntaps == 1 && a.dh[0] == 0 && a.dw[0] == 0;
-    if (getenv("DHFWI_NN_CONVT") && strcmp(getenv("DHFWI_NN_CONVT"), "mma") == 0 && one_tap) return false;
+    if (getenv("DHFWI_NN_CONVT") && strcmp(getenv("DHFWI_NN_CONVT"), "mma") == 0 && epi == EPI_BF16_CONVT)
+        return false;
     if ((epi == EPI_BF16_CONVT && !one_tap) || a.N < min_n || (a.ntaps != 9 && !one_tap) || a.scale != 1 ||
         a.Ho != a.Hs || a.Wo != a.Ws || a.C % 32 != 0 || a.C <= 0)
         return false;
@@ -1814,8 +1819,12 @@ int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s) {
     // ci and co multiples of 32: a 32-channel operand is read as a 64-channel
     // TMA box whose upper half the copy fills with zeros (rows and columns the
     // epilogue does not write).
-    if (a.mode != WG_CONV || a.ci % 32 != 0 || a.M % 32 != 0 || a.ci <= 0 || a.M <= 0) return 0;
-    if (a.nw != 9 * a.ci || a.N != a.nw + 8) return 0;
+    // A transposed conv's weight gradient with its output gradient in
+    // space-to-depth layout is the one-tap (unshifted) form of the same GEMM,
+    // with the output's columns m = ab*Co + co as the reduction expects.
+    const bool s2d = a.mode == WG_CONVT && a.g_s2d;
+    if ((a.mode != WG_CONV && !s2d) || a.ci % 32 != 0 || a.M % 32 != 0 || a.ci <= 0 || a.M <= 0) return 0;
+    if (a.nw != (s2d ? 1 : 9) * a.ci || a.N != a.nw + 8) return 0;
     if (((a.x_stride | a.x_off | a.g_stride) & 7) != 0) return 0;
     if ((((uintptr_t)(a.x + a.x_off)) | (uintptr_t)a.g) & 15) return 0;
     if ((long long)a.nimg * a.H * a.W >= (1LL << 31)) return 0;
