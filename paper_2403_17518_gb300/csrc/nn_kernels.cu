@@ -233,32 +233,31 @@ __global__ void __launch_bounds__(128) igemm_fprop_kernel(FpropArgs P) {
 
 // Split-k reduction of the fprop partials (fixed split order) with the
 // epilogue of igemm_fprop_kernel.
-// Block (32, ny): 32 consecutive outputs, thread (x, y) summing the splits
-// z = y, y + ny, ... in order; the ny group sums are added in y order.
+// Sum over the splits z = 0 .. splits-1 of p[z * stride], in split order;
+// loads are issued eight at a time so that their latencies overlap (the
+// additions keep the order, so the result is that of the plain loop).
+__device__ __forceinline__ float split_sum(const float *__restrict__ p, int splits, long long stride) {
+    float s = 0.f;
+    int z = 0;
+    for (; z + 8 <= splits; z += 8) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = p[(long long)(z + k) * stride];
+#pragma unroll
+        for (int k = 0; k < 8; k++) s += v[k];
+    }
+    for (; z < splits; z++) s += p[(long long)z * stride];
+    return s;
+}
+
+// One thread per output (grid-stride), the splits summed in order.
 template <int EPI>
 __global__ void fprop_reduce_kernel(FpropArgs P, int splits) {
-    __shared__ float red[8][32];
     const long long MN = (long long)P.M * P.N;
     const int HWo = P.Ho * P.Wo;
-    const long long idx = blockIdx.x * 32LL + threadIdx.x;
-    const int ty = threadIdx.y, ny = blockDim.y;
-    float s = 0.f;
-    if (idx < MN) {
-        int z = ty;
-        for (; z + 7 * ny < splits; z += 8 * ny) {
-            float u[8];
-#pragma unroll
-            for (int k = 0; k < 8; k++) u[k] = P.part[(long long)(z + k * ny) * MN + idx];
-#pragma unroll
-            for (int k = 0; k < 8; k++) s += u[k];
-        }
-        for (; z < splits; z += ny) s += P.part[(long long)z * MN + idx];
-    }
-    red[ty][threadIdx.x] = s;
-    __syncthreads();
-    if (ty == 0 && idx < MN) {
-        float v = 0.f;
-        for (int y = 0; y < ny; y++) v += red[y][threadIdx.x];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < MN;
+         idx += (long long)gridDim.x * blockDim.x) {
+        float v = split_sum(P.part + idx, splits, MN);
         const int m = (int)(idx / P.N), n = (int)(idx - (long long)m * P.N);
         if (EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) {
             v += P.bias[n];
@@ -476,48 +475,29 @@ __global__ void __launch_bounds__(128) igemm_wgrad_kernel(WgradArgs P) {
         }
 }
 
-// Reduction of the weight-gradient split-k partials (fixed order): block
-// (32, ny) takes 32 consecutive outputs; thread (x, y) sums the splits
-// z = y, y + ny, ... in order (loads eight at a time), and the ny partial
-// sums are added in y order.  The weight gradient goes out in the parameter
-// layout (conv: [co][tap][ci] = C[co][n]; transposed conv: [co][a][b][ci] =
-// C[(a*2+b)*Co + co][ci]), the bias column (n = nw) to db (transposed conv:
-// summed over the four sub-pixel rows ab * co_n + m of output channel m).
+// Sum of the weight-gradient split partials in split order (one thread per
+// output); writes the weight gradient in the parameter layout (conv:
+// [co][tap][ci] = C[co][n]; transposed conv: [co][a][b][ci] =
+// C[(a*2+b)*Co + co][ci]) and the bias gradient from the bias column
+// (transposed conv: summed over the four (a, b) rows).
 __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, int M, int N, int nw, int mode,
                                     int co_n, float *__restrict__ dw, float *__restrict__ db) {
-    __shared__ float red[8][32];
-    const long long MN = (long long)M * N;
-    const long long idx = blockIdx.x * 32LL + threadIdx.x;
-    const int ty = threadIdx.y, ny = blockDim.y;
-    const bool in = idx < MN;
-    const int m = in ? (int)(idx / N) : 0, n = in ? (int)(idx - (long long)m * N) : 0;
-    float s = 0.f;
-    if (in && n <= nw) {
-        if (n == nw && mode != WG_CONV) {
-            if (m < co_n)
-                for (int ab = 0; ab < 4; ab++)
-                    for (int z = ty; z < splits; z += ny) s += part[(long long)z * MN + (long long)(ab * co_n + m) * N + n];
-        } else {
-            int z = ty;
-            for (; z + 7 * ny < splits; z += 8 * ny) {
-                float v[8];
-#pragma unroll
-                for (int k = 0; k < 8; k++) v[k] = part[(long long)(z + k * ny) * MN + idx];
-#pragma unroll
-                for (int k = 0; k < 8; k++) s += v[k];
-            }
-            for (; z < splits; z += ny) s += part[(long long)z * MN + idx];
-        }
-    }
-    red[ty][threadIdx.x] = s;
-    __syncthreads();
-    if (ty != 0 || !in || n > nw) return;
-    float t = 0.f;
-    for (int y = 0; y < ny; y++) t += red[y][threadIdx.x];
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)M * N) return;
+    const int m = (int)(idx / N), n = (int)(idx - (long long)m * N);
+    if (n > nw) return;
     if (n == nw) {
-        if (mode == WG_CONV || m < co_n) db[m] = t;
+        if (mode == WG_CONV) {
+            db[m] = split_sum(part + idx, splits, (long long)M * N);
+        } else if (m < co_n) {  // one thread per co sums the rows (ab*co_n + m)
+            float s = 0.f;
+            for (int ab = 0; ab < 4; ab++)
+                for (int z = 0; z < splits; z++) s += part[(long long)z * M * N + (long long)(ab * co_n + m) * N + n];
+            db[m] = s;
+        }
         return;
     }
+    const float s = split_sum(part + idx, splits, (long long)M * N);
     long long o;
     if (mode == WG_CONV) {
         o = (long long)m * nw + n;
@@ -525,7 +505,7 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int splits, 
         const int ab = m / co_n, co = m - ab * co_n;
         o = ((long long)co * 4 + ab) * nw + n;
     }
-    dw[o] = t;
+    dw[o] = s;
 }
 
 // One warp per channel: lane l sums the partials l, l+32, ..., then a
@@ -1063,34 +1043,52 @@ __global__ void absmax_finish_kernel(const unsigned *mx, float *scale_out) {
 // one real channel (channel 0 of xin, the others zero):
 //   dW[co][t] = sum_p G[p][co] x[p + shift(t)],   db[co] = sum_p G[p][co],
 // a reduction over the pixels on CUDA cores (the tensor-core GEMM would
-// spend 72 of its 80 columns on the zero channels).  Block b takes a run
-// of pixels; lane = output channel (32 per pass), the 8 warps interleave
-// pixels; per-block sums [b][co][10] in a fixed order, then
-// first_wgrad_final_kernel sums the blocks in order.
+// spend 72 of its 80 columns on the zero channels).  A warp walks image rows
+// (row = img * H + h; rows warp, warp + warps, ...) with lane = output
+// channel (32 per pass), sliding the 3 x 3 input window along the row (three
+// new inputs per pixel, no index division); per-block sums [b][co][10] in a
+// fixed order, then first_wgrad_final_kernel sums the blocks.
 __global__ void __launch_bounds__(256) first_wgrad_kernel(const __nv_bfloat16 *__restrict__ g, int co_n,
                                                           const __nv_bfloat16 *__restrict__ xin, int cpad, int nimg,
-                                                          int H, int W, long long ppb, float *__restrict__ part) {
+                                                          int H, int W, float *__restrict__ part) {
     __shared__ float red[8][32][10];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long P = (long long)nimg * H * W;
-    const long long p0 = blockIdx.x * ppb, p1 = p0 + ppb < P ? p0 + ppb : P;
+    const int rows = nimg * H, nwarps = gridDim.x * 8;
+    auto xat = [&](int row, int hh, int ww) -> float {  // x at (hh, ww) of the row's image, zero outside
+        return hh >= 0 && hh < H && ww >= 0 && ww < W
+                   ? __bfloat162float(xin[((long long)(row - (row % H) + hh) * W + ww) * cpad])
+                   : 0.f;
+    };
     for (int cb = 0; cb < co_n; cb += 32) {
         const int co = cb + lane;
         const bool valid = co < co_n;
         float acc[10];
 #pragma unroll
         for (int k = 0; k < 10; k++) acc[k] = 0.f;
-        for (long long p = p0 + warp; p < p1; p += 8) {
-            const int w = (int)(p % W), h = (int)((p / W) % H);
-            const float gv = valid ? __bfloat162float(g[p * co_n + co]) : 0.f;
+        for (int row = blockIdx.x * 8 + warp; row < rows; row += nwarps) {
+            const int h = row % H;
+            float xw[3][3];  // rows h-1..h+1, columns w-1..w+1
 #pragma unroll
-            for (int t = 0; t < 9; t++) {
-                const int dh = t / 3 - 1, dw = t % 3 - 1;
-                const bool in = h + dh >= 0 && h + dh < H && w + dw >= 0 && w + dw < W;
-                const float xv = in ? __bfloat162float(xin[(p + (long long)dh * W + dw) * cpad]) : 0.f;
-                acc[t] += gv * xv;
+            for (int a = 0; a < 3; a++) {
+                xw[a][0] = 0.f;
+                xw[a][1] = xat(row, h + a - 1, 0);
+                xw[a][2] = xat(row, h + a - 1, 1);
             }
-            acc[9] += gv;
+            const __nv_bfloat16 *gr = g + (long long)row * W * co_n + co;
+            for (int w = 0; w < W; w++) {
+                const float gv = valid ? __bfloat162float(gr[(long long)w * co_n]) : 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int b = 0; b < 3; b++) acc[a * 3 + b] += gv * xw[a][b];
+                acc[9] += gv;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    xw[a][0] = xw[a][1];
+                    xw[a][1] = xw[a][2];
+                    xw[a][2] = xat(row, h + a - 1, w + 2);
+                }
+            }
         }
 #pragma unroll
         for (int k = 0; k < 10; k++) red[warp][lane][k] = acc[k];
@@ -1107,16 +1105,25 @@ __global__ void __launch_bounds__(256) first_wgrad_kernel(const __nv_bfloat16 *_
     }
 }
 
-// dw[co][9] and db[co] from the per-block sums (blocks in order).
+// dw[co][9] and db[co] from the per-block sums: block i = output (co, k);
+// thread t sums blocks t, t + 256, ... in order, then a fixed shared-memory
+// tree.
 __global__ void first_wgrad_final_kernel(const float *__restrict__ part, int nblk, int co_n, float *__restrict__ dw,
                                          float *__restrict__ db) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= co_n * 10) return;
-    const int co = i / 10, k = i - co * 10;
+    __shared__ float red[256];
+    const int i = blockIdx.x, co = i / 10, k = i - co * 10;
     float s = 0.f;
-    for (int b = 0; b < nblk; b++) s += part[((long long)b * co_n + co) * 10 + k];
-    if (k < 9) dw[co * 9 + k] = s;
-    else db[co] = s;
+    for (int b = threadIdx.x; b < nblk; b += 256) s += part[((long long)b * co_n + co) * 10 + k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (k < 9) dw[co * 9 + k] = red[0];
+        else db[co] = red[0];
+    }
 }
 
 // The first 3x3 convolution (one real input channel: channel 0 of xin) with
@@ -1132,32 +1139,30 @@ __global__ void __launch_bounds__(256) first_conv_kernel(const __nv_bfloat16 *__
     for (int i = threadIdx.x; i < co_n * 10; i += blockDim.x)
         sw[i] = i < co_n * 9 ? __bfloat162float(w[i]) : bias[i - co_n * 9];
     __syncthreads();
-    const int groups = co_n / 8;
-    const long long P = (long long)nimg * H * W;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P * groups;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long p = t / groups;
-        const int g = (int)(t - p * groups), c0 = 8 * g;
-        const int w0 = (int)(p % W), h0 = (int)((p / W) % H);
-        float xv[9];
+    // blockIdx.y: image row (img * H + h); x: (pixel of the row, channel group).
+    const int groups = co_n / 8, row = blockIdx.y, h0 = row % H;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w0 = t / groups, c0 = 8 * (t - w0 * groups);
+    if (w0 >= W) return;
+    const long long p = (long long)row * W + w0;
+    float xv[9];
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
-            const int dh = k / 3 - 1, dw = k % 3 - 1;
-            const bool in = h0 + dh >= 0 && h0 + dh < H && w0 + dw >= 0 && w0 + dw < W;
-            xv[k] = in ? __bfloat162float(xin[(p + (long long)dh * W + dw) * cpad]) : 0.f;
-        }
-        __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const float *wr = sw + (c0 + e) * 9;
-            float a = 0.f;
-#pragma unroll
-            for (int k = 0; k < 9; k++) a = fmaf(wr[k], xv[k], a);
-            a += sw[co_n * 9 + c0 + e];
-            o[e] = __float2bfloat16_rn(a > 0.f ? a : slope * a);
-        }
-        *reinterpret_cast<uint4 *>(y + p * ys + c0) = *reinterpret_cast<const uint4 *>(o);
+    for (int k = 0; k < 9; k++) {
+        const int dh = k / 3 - 1, dw = k % 3 - 1;
+        const bool in = h0 + dh >= 0 && h0 + dh < H && w0 + dw >= 0 && w0 + dw < W;
+        xv[k] = in ? __bfloat162float(xin[(p + (long long)dh * W + dw) * cpad]) : 0.f;
     }
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const float *wr = sw + (c0 + e) * 9;
+        float a = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; k++) a = fmaf(wr[k], xv[k], a);
+        a += sw[co_n * 9 + c0 + e];
+        o[e] = __float2bfloat16_rn(a > 0.f ? a : slope * a);
+    }
+    *reinterpret_cast<uint4 *>(y + p * ys + c0) = *reinterpret_cast<const uint4 *>(o);
 }
 
 __global__ void pad_first_w_kernel(const __nv_bfloat16 *__restrict__ w, int co, int cpad,
@@ -1358,14 +1363,13 @@ static void fprop_launch(const FpropArgs &a, cudaStream_t s) {
     igemm_fprop_kernel<BN, EPI><<<grid, 128, sm, s>>>(b);
     if (splits > 1) {
         const long long mn = (long long)a.M * a.N;
-        fprop_reduce_kernel<EPI><<<(int)((mn + 31) / 32), dim3(32, std::min(8, splits)), 0, s>>>(b, splits);
+        fprop_reduce_kernel<EPI><<<grid_for(mn), 256, 0, s>>>(b, splits);
     }
 }
 
 void launch_fprop_reduce(const FpropArgs &a, int epi, int splits, cudaStream_t s) {
-    // Output blocks of 32, split groups of up to 8 (see fprop_reduce_kernel).
-    const int g = (int)(((long long)a.M * a.N + 31) / 32);
-    const dim3 b(32, std::max(1, std::min(8, splits)));
+    const int g = grid_for((long long)a.M * a.N);
+    const int b = 256;
     switch (epi) {
     case EPI_BF16_LEAKY: fprop_reduce_kernel<EPI_BF16_LEAKY><<<g, b, 0, s>>>(a, splits); break;
     case EPI_BF16: fprop_reduce_kernel<EPI_BF16><<<g, b, 0, s>>>(a, splits); break;
@@ -1489,14 +1493,14 @@ int launch_wgrad(const WgradArgs &a, int splits, float *dw, float *db, cudaStrea
     const long long mn = (long long)a.M * a.N;
     const int tsp = launch_wgrad_tma(a, splits, s);
     if (tsp > 0) {  // partials with the bias column: weight and bias gradients in one reduction
-        wgrad_reduce_kernel<<<(int)((mn + 31) / 32), dim3(32, std::min(8, tsp)), 0, s>>>(a.part, tsp, a.M, a.N, a.nw,
-                                                                                           a.mode, a.co, dw, db);
+        wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, tsp, a.M, a.N, a.nw, a.mode, a.co, dw,
+                                                                     db);
         return 2;
     }
     if (wgrad_narrow(a.M)) wgrad_launch<1, 4>(a, splits, s);
     else wgrad_launch<2, 2>(a, splits, s);
-    wgrad_reduce_kernel<<<(int)((mn + 31) / 32), dim3(32, std::max(1, std::min(8, splits))), 0, s>>>(
-        a.part, splits, a.M, a.N, a.nw, a.mode, a.co, dw, db);
+    wgrad_reduce_kernel<<<(int)((mn + 255) / 256), 256, 0, s>>>(a.part, splits, a.M, a.N, a.nw, a.mode, a.co, dw,
+                                                                 db);
     return 2;
 }
 
@@ -1630,22 +1634,20 @@ void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const f
 }
 int launch_first_wgrad(const __nv_bfloat16 *g, int co, const __nv_bfloat16 *xin, int cpad, int nimg, int H, int W,
                        float *part, long long part_floats, float *dw, float *db, cudaStream_t s) {
-    const long long P = (long long)nimg * H * W;
-    int nblk = (int)std::min<long long>(152 * 4, (P + 255) / 256);
-    if (nblk < 1) nblk = 1;
+    const int rows = nimg * H;
+    int nblk = std::min(152 * 4, (rows + 7) / 8);
     if ((long long)nblk * co * 10 > part_floats) nblk = (int)(part_floats / (10LL * co));
     if (nblk < 1) return 0;
-    const long long ppb = (P + nblk - 1) / nblk;
-    first_wgrad_kernel<<<nblk, 256, 0, s>>>(g, co, xin, cpad, nimg, H, W, ppb, part);
-    first_wgrad_final_kernel<<<(co * 10 + 255) / 256, 256, 0, s>>>(part, nblk, co, dw, db);
+    first_wgrad_kernel<<<nblk, 256, 0, s>>>(g, co, xin, cpad, nimg, H, W, part);
+    first_wgrad_final_kernel<<<co * 10, 256, 0, s>>>(part, nblk, co, dw, db);
     return 2;
 }
 bool launch_first_conv(const __nv_bfloat16 *xin, int cpad, int nimg, int H, int W, const __nv_bfloat16 *w,
                        const float *bias, int co, float slope, __nv_bfloat16 *y, int ys, cudaStream_t s) {
     if (co % 8 != 0 || ys % 8 != 0 || ((uintptr_t)y & 15) != 0) return false;
-    const long long work = (long long)nimg * H * W * (co / 8);
-    first_conv_kernel<<<grid_for(work), 256, sizeof(float) * co * 10, s>>>(xin, cpad, nimg, H, W, w, bias, co, slope,
-                                                                          y, ys);
+    if ((long long)nimg * H > 65535) return false;
+    const dim3 grid((unsigned)(((long long)W * (co / 8) + 255) / 256), (unsigned)(nimg * H));
+    first_conv_kernel<<<grid, 256, sizeof(float) * co * 10, s>>>(xin, cpad, nimg, H, W, w, bias, co, slope, y, ys);
     return true;
 }
 void launch_pad_first_w(const __nv_bfloat16 *w, int co, int cpad, __nv_bfloat16 *wp, cudaStream_t s) {
