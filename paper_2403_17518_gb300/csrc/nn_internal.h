@@ -103,8 +103,12 @@ void launch_conv1x1_fwd(const __nv_bfloat16 *a, int C, long long P, const __nv_b
                         cudaStream_t s);
 void launch_mse(const float *out, const float *y, long long P, __nv_bfloat16 *g, double *partial, int nblocks,
                 cudaStream_t s);
-void launch_conv1x1_bwd(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long long P, int C, const __nv_bfloat16 *w,
-                        float *dA, float *part, int max_blocks, float *dw_db, cudaStream_t s);
+// Output layer backward fused with the LeakyReLU backward of its input a
+// (bf16 [P][C]): the next block's output gradient gn (bf16 [P][C]) and the
+// layer's weight and bias gradients (dw_db[0..C), dw_db[C]).
+void launch_conv1x1_bwd_leaky(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long long P, int C,
+                              const __nv_bfloat16 *w, float slope, __nv_bfloat16 *gn, float *part, int max_blocks,
+                              float *dw_db, cudaStream_t s);
 void launch_adam(float *theta, const float *grad, float *m, float *v, long long n, float lr, float b1, float b2,
                  float eps, int t, __nv_bfloat16 *shadow, cudaStream_t s);
 void launch_to_bf16(const float *x, long long n, __nv_bfloat16 *y, cudaStream_t s);

@@ -821,7 +821,17 @@ __global__ void conv1x1_fwd_kernel(const __nv_bfloat16 *__restrict__ a, int C, l
                                    float *__restrict__ out) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         float s = 0.f;
-        for (int c = 0; c < C; c++) s = fmaf(__bfloat162float(w[c]), __bfloat162float(a[p * C + c]), s);
+        if ((C & 7) == 0) {  // 16-byte loads of 8 channels (rows are 16-byte aligned when C is a multiple of 8)
+            const uint4 *row = reinterpret_cast<const uint4 *>(a + p * C);
+            for (int c8 = 0; c8 < C / 8; c8++) {
+                const uint4 q = row[c8];
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+                for (int e = 0; e < 8; e++) s = fmaf(__bfloat162float(w[8 * c8 + e]), __bfloat162float(h[e]), s);
+            }
+        } else {
+            for (int c = 0; c < C; c++) s = fmaf(__bfloat162float(w[c]), __bfloat162float(a[p * C + c]), s);
+        }
         out[p] = s + b[0];
     }
 }
@@ -847,33 +857,32 @@ __global__ void mse_kernel(const float *__restrict__ out, const float *__restric
     }
 }
 
-// Output layer backward: dW[c] = sum_p g[p] a[p][c] (per-block partials),
-// db = sum_p g[p], dA[p][c] = bf16(W[c]) g[p].
-__global__ void conv1x1_bwd_data_kernel(const __nv_bfloat16 *__restrict__ g, long long P, int C,
-                                        const __nv_bfloat16 *__restrict__ w, float *__restrict__ dA) {
-    const long long n = P * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long p = i / C;
-        const int c = (int)(i - p * C);
-        dA[i] = __bfloat162float(w[c]) * __bfloat162float(g[p]);
-    }
-}
-
-// part[blk][c] for c < C, part[blk][C] = sum g over the block's `rows`
-// pixels.  Threads (c, j): channel c (blockDim.x = C + 1 rounded up to 32)
-// over the pixels p0 + j, p0 + j + S, ... (S = blockDim.y streams); the
-// streams are then summed in order j = 0, 1, ... (deterministic).
-__global__ void conv1x1_wgrad_partial_kernel(const __nv_bfloat16 *__restrict__ g, const __nv_bfloat16 *__restrict__ a,
-                                             long long P, int C, int rows, float *__restrict__ part) {
+// Output layer (1x1 conv, C -> 1) backward fused with the activation
+// backward of its input: per pixel p, g = g_out[p] (bf16); the next block's
+// output gradient gn[p][c] = bf16(bf16(W[c]) g * leaky'(a[p][c])), and
+// per-block partial sums part[blk][c] = sum g a[p][c], part[blk][C] = sum g.
+// Threads (c, j): channel c (blockDim.x = C + 1 rounded up to 32) over the
+// pixels p0 + j, p0 + j + S, ... (S = blockDim.y streams), the streams then
+// summed in order j = 0, 1, ... (deterministic).
+__global__ void conv1x1_bwd_leaky_kernel(const __nv_bfloat16 *__restrict__ g, const __nv_bfloat16 *__restrict__ a,
+                                         long long P, int C, const __nv_bfloat16 *__restrict__ w, float slope,
+                                         __nv_bfloat16 *__restrict__ gn, int rows, float *__restrict__ part) {
     extern __shared__ float red[];  // [S][blockDim.x]
     const int c = threadIdx.x, j = threadIdx.y, S = blockDim.y;
     const long long p0 = (long long)blockIdx.x * rows;
     const long long p1 = p0 + rows < P ? p0 + rows : P;
+    const float wc = c < C ? __bfloat162float(w[c]) : 0.f;
     float s = 0.f;
     if (c <= C)
         for (long long p = p0 + j; p < p1; p += S) {
             const float gv = __bfloat162float(g[p]);
-            s += c < C ? gv * __bfloat162float(a[p * C + c]) : gv;
+            if (c < C) {
+                const float av = __bfloat162float(a[p * C + c]);
+                s += gv * av;
+                gn[p * C + c] = __float2bfloat16_rn(wc * gv * (av > 0.f ? 1.0f : slope));
+            } else {
+                s += gv;
+            }
         }
     red[j * blockDim.x + c] = s;
     __syncthreads();
@@ -1573,17 +1582,16 @@ void launch_mse(const float *out, const float *y, long long P, __nv_bfloat16 *g,
                 cudaStream_t s) {
     mse_kernel<<<nblocks, 256, 0, s>>>(out, y, P, g, partial);
 }
-void launch_conv1x1_bwd(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long long P, int C, const __nv_bfloat16 *w,
-                        float *dA, float *part, int max_blocks, float *dw_db, cudaStream_t s) {
-    conv1x1_bwd_data_kernel<<<grid_for(P * C), 256, 0, s>>>(g, P, C, w, dA);
+void launch_conv1x1_bwd_leaky(const __nv_bfloat16 *g, const __nv_bfloat16 *a, long long P, int C,
+                              const __nv_bfloat16 *w, float slope, __nv_bfloat16 *gn, float *part, int max_blocks,
+                              float *dw_db, cudaStream_t s) {
     int rows = (int)((P + max_blocks - 1) / max_blocks);
     if (rows < 64) rows = 64;
     const int nblk = (int)((P + rows - 1) / rows);
     const int cx = ((C + 1 + 31) / 32) * 32;
     const int streams = std::max(1, std::min(8, 1024 / cx));
-    conv1x1_wgrad_partial_kernel<<<nblk, dim3(cx, streams), sizeof(float) * cx * streams, s>>>(g, a, P, C, rows,
-                                                                                                 part);
-    // dw_db[0..C) = dW, dw_db[C] = db: reuse the bias-final reduction over C+1 columns.
+    conv1x1_bwd_leaky_kernel<<<nblk, dim3(cx, streams), sizeof(float) * cx * streams, s>>>(g, a, P, C, w, slope, gn,
+                                                                                             rows, part);
     bias_grad_final_kernel<<<((C + 1) * 32 + 255) / 256, 256, 0, s>>>(part, nblk, C + 1, dw_db);
 }
 void launch_adam(float *theta, const float *grad, float *m, float *v, long long n, float lr, float b1, float b2,

@@ -736,9 +736,12 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
     const LayerDesc &dout = N.L[layer_index_out(N)];
     // Keep g_out apart from gbuf, which the blocks reuse: stage it in dB.
     __nv_bfloat16 *gout = reinterpret_cast<__nv_bfloat16 *>(V.dB);
-    launch_conv1x1_bwd(gout, V.dec1[0], P0, C(0), N.w16 + dout.off, V.dA, N.red_part, RED_BLOCKS,
-                       N.grad + dout.off, s);
-    N.launches += 3;
+    // Its input gradient goes, with dec1[0]'s activation backward, straight
+    // into the next block's output gradient (gbuf).
+    before_gbuf_write(N, V.gbuf, s);
+    launch_conv1x1_bwd_leaky(gout, V.dec1[0], P0, C(0), N.w16 + dout.off, 0.2f, V.gbuf, N.red_part, RED_BLOCKS,
+                             N.grad + dout.off, s);
+    N.launches += 2;
     float *dA = V.dA, *dB = V.dB;
     for (int l = Lv; l >= 1; l--) {
         const int r = Lv - l;
@@ -750,8 +753,9 @@ void backward_impl(NetState &N, int n, int H, int W, cudaStream_t s) {
         fu.act = V.dec0[r];
         fu.stride = C(r);
         fu.g = V.gbuf2;
-        block_bwd(N, layer_index_up(N, l, 2), dA, V.dec1[r], C(r), 0, V.dec0[r], C(r), 0, C(r), n, Hr, Wr, nullptr, s,
-                  nullptr, fu);
+        const __nv_bfloat16 *g_top = l == Lv ? V.gbuf : nullptr;  // from the output layer's backward
+        block_bwd(N, layer_index_up(N, l, 2), g_top ? nullptr : dA, V.dec1[r], C(r), 0, V.dec0[r], C(r), 0, C(r), n,
+                  Hr, Wr, nullptr, s, g_top, fu);
         // up_l.0: output dec0, input cat (2C).
         block_bwd(N, layer_index_up(N, l, 1), nullptr, nullptr, 0, 0, V.cat[r], 2 * C(r), 0, 2 * C(r), n, Hr, Wr, dA,
                   s, V.gbuf2);
