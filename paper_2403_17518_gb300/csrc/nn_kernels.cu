@@ -691,18 +691,17 @@ __global__ void add_slice4_kernel(const float *__restrict__ src, int ss, int so,
 // (fine pixel (2h+a, 2w+b)) as the transposed conv's output gradient.
 __global__ void split_cat4_kernel(const float *__restrict__ src, int nimg, int H, int W, int C4,
                                   float4 *__restrict__ skip, Bf16x4 *__restrict__ up) {
-    const long long n = (long long)nimg * H * W * C4;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long p = i / C4;
-        const int c = (int)(i - p * C4);
-        const int w = (int)(p % W);
-        const long long r = p / W;
-        const int h = (int)(r % H);
-        const long long img = r / H;
-        const float *row = src + p * 8 * C4;
-        skip[i] = *reinterpret_cast<const float4 *>(row + 4 * c);
-        const long long q = ((img * (H / 2) + h / 2) * (W / 2) + w / 2) * 4 + (h & 1) * 2 + (w & 1);
-        up[q * C4 + c] = f4_to_bf4(*reinterpret_cast<const float4 *>(row + 4 * C4 + 4 * c));
+    const int rows = nimg * H;
+    for (int rw = blockIdx.y; rw < rows; rw += gridDim.y) {
+        const int img = rw / H, h = rw - img * H;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < W * C4; t += gridDim.x * blockDim.x) {
+            const int w = t / C4, c = t - w * C4;
+            const long long p = (long long)rw * W + w, i = p * C4 + c;
+            const float *row = src + p * 8 * C4;
+            skip[i] = *reinterpret_cast<const float4 *>(row + 4 * c);
+            const long long q = (((long long)img * (H / 2) + h / 2) * (W / 2) + w / 2) * 4 + (h & 1) * 2 + (w & 1);
+            up[q * C4 + c] = f4_to_bf4(*reinterpret_cast<const float4 *>(row + 4 * C4 + 4 * c));
+        }
     }
 }
 
@@ -730,16 +729,13 @@ __global__ void to_bf16_s2d_kernel(const float *__restrict__ x, int nimg, int H,
 __global__ void avgpool_bwd_leaky4_kernel(const float *__restrict__ dy, int nimg, int H, int W, int C4,
                                           const float4 *__restrict__ skip, const __nv_bfloat16 *__restrict__ act,
                                           int as, int ao, float slope, Bf16x4 *__restrict__ g) {
-    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
-    const long long n = (long long)nimg * H * W * C4;
+    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1, rows = nimg * H;
     const float4 *dy4 = reinterpret_cast<const float4 *>(dy);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C4);
-        const long long r0 = i / C4;
-        const int w = (int)(r0 % W);
-        const long long r1 = r0 / W;
-        const int h = (int)(r1 % H);
-        const long long img = r1 / H;
+    for (int rw = blockIdx.y; rw < rows; rw += gridDim.y)
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < W * C4; t += gridDim.x * blockDim.x) {
+        const long long img = rw / H;
+        const int h = rw - (int)img * H, w = t / C4, c = t - w * C4;
+        const long long r0 = (long long)rw * W + w, i = r0 * C4 + c;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int ho = (h > 0 ? h / 2 : 0); ho <= (h + 1) / 2 && ho < Ho; ho++) {
             if (2 * ho - 1 > h || 2 * ho + 1 < h) continue;
@@ -765,31 +761,30 @@ __global__ void avgpool_bwd_leaky4_kernel(const float *__restrict__ dy, int nimg
 
 __global__ void avgpool_fwd4_kernel(const __nv_bfloat16 *__restrict__ x, int xs, int xo, int nimg, int H, int W,
                                     int C4, Bf16x4 *__restrict__ y) {
-    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
-    const long long n = (long long)nimg * Ho * Wo * C4;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C4) * 4;
-        long long r = i / C4;
-        const int wo = (int)(r % Wo);
-        r /= Wo;
-        const int ho = (int)(r % Ho);
-        const long long img = r / Ho;
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int a = 0; a < 3; a++) {
-            const int h = 2 * ho + a - 1;
-            if (h < 0 || h >= H) continue;
-            for (int b = 0; b < 3; b++) {
-                const int w = 2 * wo + b - 1;
-                if (w < 0 || w >= W) continue;
-                const float4 v = bf4_to_f4(*reinterpret_cast<const Bf16x4 *>(x + ((img * H + h) * W + w) * xs + xo + c));
-                s.x += v.x;
-                s.y += v.y;
-                s.z += v.z;
-                s.w += v.w;
+    // Rows (img, ho) on blockIdx.y, (wo, channel quad) on x: no 64-bit index division.
+    const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1, rows = nimg * Ho;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int img = row / Ho, ho = row - img * Ho;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Wo * C4; t += gridDim.x * blockDim.x) {
+            const int wo = t / C4, c = (t - wo * C4) * 4;
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int a = 0; a < 3; a++) {
+                const int h = 2 * ho + a - 1;
+                if (h < 0 || h >= H) continue;
+                for (int b = 0; b < 3; b++) {
+                    const int w = 2 * wo + b - 1;
+                    if (w < 0 || w >= W) continue;
+                    const float4 v = bf4_to_f4(
+                        *reinterpret_cast<const Bf16x4 *>(x + (((long long)img * H + h) * W + w) * xs + xo + c));
+                    s.x += v.x;
+                    s.y += v.y;
+                    s.z += v.z;
+                    s.w += v.w;
+                }
             }
+            const float k = 1.0f / 9.0f;
+            y[(long long)row * Wo * C4 + t] = f4_to_bf4(make_float4(s.x * k, s.y * k, s.z * k, s.w * k));
         }
-        const float k = 1.0f / 9.0f;
-        y[i] = f4_to_bf4(make_float4(s.x * k, s.y * k, s.z * k, s.w * k));
     }
 }
 
@@ -1341,6 +1336,11 @@ __global__ void __launch_bounds__(128) conv3_halo_kernel(FpropArgs P, int bh_n, 
 // ===========================================================================
 // Host launchers
 // ===========================================================================
+// Grid of the row kernels: x over one row's elements (256 per block), y over
+// the rows (at most 65535; the kernels stride over the rest).
+static dim3 row_grid(int per_row, int rows) {
+    return dim3((unsigned)std::max(1, (per_row + 255) / 256), (unsigned)std::max(1, std::min(rows, 65535)));
+}
 static int grid_for(long long n, int block = 256) {
     long long g = (n + block - 1) / block;
     return (int)(g < 152 * 16 ? (g < 1 ? 1 : g) : 152 * 16);
@@ -1517,7 +1517,8 @@ void launch_avgpool_fwd(const __nv_bfloat16 *x, int xs, int xo, int nimg, int H,
                         cudaStream_t s) {
     const long long n = (long long)nimg * ((H - 1) / 2 + 1) * ((W - 1) / 2 + 1) * C;
     if (C % 4 == 0 && ((xs | xo) & 3) == 0 && (((uintptr_t)x | (uintptr_t)y) & 7) == 0)
-        avgpool_fwd4_kernel<<<grid_for(n / 4), 256, 0, s>>>(x, xs, xo, nimg, H, W, C / 4,
+        avgpool_fwd4_kernel<<<row_grid(((W - 1) / 2 + 1) * (C / 4), nimg * ((H - 1) / 2 + 1)), 256, 0, s>>>(
+            x, xs, xo, nimg, H, W, C / 4,
                                                             reinterpret_cast<Bf16x4 *>(y));
     else
         avgpool_fwd_kernel<<<grid_for(n), 256, 0, s>>>(x, xs, xo, nimg, H, W, C, y);
@@ -1534,7 +1535,8 @@ bool launch_split_cat(const float *src, int nimg, int H, int W, int C, float *sk
     if (C % 4 != 0 || (H | W) & 1 || (((uintptr_t)src | (uintptr_t)skip) & 15) != 0 || ((uintptr_t)up & 7) != 0)
         return false;
     const long long P = (long long)nimg * H * W;
-    split_cat4_kernel<<<grid_for(P * C / 4), 256, 0, s>>>(src, nimg, H, W, C / 4, reinterpret_cast<float4 *>(skip),
+    split_cat4_kernel<<<row_grid(W * (C / 4), nimg * H), 256, 0, s>>>(src, nimg, H, W, C / 4,
+                                                                      reinterpret_cast<float4 *>(skip),
                                                           reinterpret_cast<Bf16x4 *>(up));
     return true;
 }
@@ -1548,7 +1550,7 @@ bool launch_avgpool_bwd_leaky(const float *dy, int nimg, int H, int W, int C, co
         (((uintptr_t)act | (uintptr_t)g) & 7) != 0)
         return false;
     const long long n = (long long)nimg * H * W * C;
-    avgpool_bwd_leaky4_kernel<<<grid_for(n / 4), 256, 0, s>>>(dy, nimg, H, W, C / 4,
+    avgpool_bwd_leaky4_kernel<<<row_grid(W * (C / 4), nimg * H), 256, 0, s>>>(dy, nimg, H, W, C / 4,
                                                               reinterpret_cast<const float4 *>(skip), act, as, ao,
                                                               slope, reinterpret_cast<Bf16x4 *>(g));
     return true;
