@@ -1047,50 +1047,51 @@ __global__ void absmax_finish_kernel(const unsigned *mx, float *scale_out) {
 // one real channel (channel 0 of xin, the others zero):
 //   dW[co][t] = sum_p G[p][co] x[p + shift(t)],   db[co] = sum_p G[p][co],
 // a reduction over the pixels on CUDA cores (the tensor-core GEMM would
-// spend 72 of its 80 columns on the zero channels).  A warp walks image rows
-// (row = img * H + h; rows warp, warp + warps, ...) with lane = output
-// channel (32 per pass), sliding the 3 x 3 input window along the row (three
-// new inputs per pixel, no index division); per-block sums [b][co][10] in a
-// fixed order, then first_wgrad_final_kernel sums the blocks.
+// spend 72 of its 80 columns on the zero channels).  Lane = output channel
+// (32 per pass); a warp takes row segments of 32 pixels (row = img * H + h)
+// and walks each in chunks of 8 pixels whose output-gradient values and
+// 3 x 10 input window are all loaded before the chunk's sums (one memory
+// latency per chunk); per-block sums [b][co][10] in a fixed order, then
+// first_wgrad_final_kernel sums the blocks.
 __global__ void __launch_bounds__(256) first_wgrad_kernel(const __nv_bfloat16 *__restrict__ g, int co_n,
                                                           const __nv_bfloat16 *__restrict__ xin, int cpad, int nimg,
                                                           int H, int W, float *__restrict__ part) {
     __shared__ float red[8][32][10];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rows = nimg * H, nwarps = gridDim.x * 8;
-    auto xat = [&](int row, int hh, int ww) -> float {  // x at (hh, ww) of the row's image, zero outside
-        return hh >= 0 && hh < H && ww >= 0 && ww < W
-                   ? __bfloat162float(xin[((long long)(row - (row % H) + hh) * W + ww) * cpad])
-                   : 0.f;
-    };
+    const int segs = (W + 31) / 32, tasks = nimg * H * segs, nwarps = gridDim.x * 8;
     for (int cb = 0; cb < co_n; cb += 32) {
         const int co = cb + lane;
         const bool valid = co < co_n;
         float acc[10];
 #pragma unroll
         for (int k = 0; k < 10; k++) acc[k] = 0.f;
-        for (int row = blockIdx.x * 8 + warp; row < rows; row += nwarps) {
-            const int h = row % H;
-            float xw[3][3];  // rows h-1..h+1, columns w-1..w+1
+        for (int task = blockIdx.x * 8 + warp; task < tasks; task += nwarps) {
+            const int row = task / segs, ws = (task - row * segs) * 32;
+            const int h = row % H, we = min(W, ws + 32);
+            const long long rbase = (long long)(row - h) * W;  // first pixel of the row's image
+            for (int w0 = ws; w0 < we; w0 += 8) {
+                float gv[8], xc[3][10];
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                xw[a][0] = 0.f;
-                xw[a][1] = xat(row, h + a - 1, 0);
-                xw[a][2] = xat(row, h + a - 1, 1);
-            }
-            const __nv_bfloat16 *gr = g + (long long)row * W * co_n + co;
-            for (int w = 0; w < W; w++) {
-                const float gv = valid ? __bfloat162float(gr[(long long)w * co_n]) : 0.f;
-#pragma unroll
-                for (int a = 0; a < 3; a++)
-#pragma unroll
-                    for (int b = 0; b < 3; b++) acc[a * 3 + b] += gv * xw[a][b];
-                acc[9] += gv;
+                for (int e = 0; e < 8; e++)
+                    gv[e] = valid && w0 + e < we ? __bfloat162float(g[((long long)row * W + w0 + e) * co_n + co]) : 0.f;
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    xw[a][0] = xw[a][1];
-                    xw[a][1] = xw[a][2];
-                    xw[a][2] = xat(row, h + a - 1, w + 2);
+                    const int hh = h + a - 1;
+#pragma unroll
+                    for (int e = 0; e < 10; e++) {
+                        const int ww = w0 - 1 + e;
+                        xc[a][e] = hh >= 0 && hh < H && ww >= 0 && ww < W
+                                       ? __bfloat162float(xin[(rbase + (long long)hh * W + ww) * cpad])
+                                       : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+#pragma unroll
+                    for (int a = 0; a < 3; a++)
+#pragma unroll
+                        for (int b = 0; b < 3; b++) acc[a * 3 + b] += gv[e] * xc[a][e + b];
+                    acc[9] += gv[e];
                 }
             }
         }
@@ -1644,8 +1645,8 @@ void launch_crop_image(const float *src, int Hp, int Wp, int nz, int nx, const f
 }
 int launch_first_wgrad(const __nv_bfloat16 *g, int co, const __nv_bfloat16 *xin, int cpad, int nimg, int H, int W,
                        float *part, long long part_floats, float *dw, float *db, cudaStream_t s) {
-    const int rows = nimg * H;
-    int nblk = std::min(152 * 4, (rows + 7) / 8);
+    const long long tasks = (long long)nimg * H * ((W + 31) / 32);
+    int nblk = (int)std::min<long long>(152 * 8, (tasks + 7) / 8);
     if ((long long)nblk * co * 10 > part_floats) nblk = (int)(part_floats / (10LL * co));
     if (nblk < 1) return 0;
     first_wgrad_kernel<<<nblk, 256, 0, s>>>(g, co, xin, cpad, nimg, H, W, part);
