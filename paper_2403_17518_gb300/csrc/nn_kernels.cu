@@ -868,17 +868,28 @@ __global__ void conv1x1_bwd_leaky_kernel(const __nv_bfloat16 *__restrict__ g, co
     const long long p1 = p0 + rows < P ? p0 + rows : P;
     const float wc = c < C ? __bfloat162float(w[c]) : 0.f;
     float s = 0.f;
-    if (c <= C)
-        for (long long p = p0 + j; p < p1; p += S) {
-            const float gv = __bfloat162float(g[p]);
-            if (c < C) {
-                const float av = __bfloat162float(a[p * C + c]);
-                s += gv * av;
-                gn[p * C + c] = __float2bfloat16_rn(wc * gv * (av > 0.f ? 1.0f : slope));
-            } else {
-                s += gv;
+    if (c <= C) {
+        long long p = p0 + j;
+        for (; p + 7 * S < p1; p += 8 * S) {  // eight pixels' loads issued before their sums
+            float gv[8], av[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                gv[k] = __bfloat162float(g[p + k * S]);
+                av[k] = c < C ? __bfloat162float(a[(p + k * S) * C + c]) : 1.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                s += gv[k] * av[k];
+                if (c < C) gn[(p + k * S) * C + c] = __float2bfloat16_rn(wc * gv[k] * (av[k] > 0.f ? 1.0f : slope));
             }
         }
+        for (; p < p1; p += S) {
+            const float gv = __bfloat162float(g[p]);
+            const float av = c < C ? __bfloat162float(a[p * C + c]) : 1.f;
+            s += gv * av;
+            if (c < C) gn[p * C + c] = __float2bfloat16_rn(wc * gv * (av > 0.f ? 1.0f : slope));
+        }
+    }
     red[j * blockDim.x + c] = s;
     __syncthreads();
     if (j == 0 && c <= C) {
@@ -1074,16 +1085,16 @@ __global__ void __launch_bounds__(256) first_wgrad_kernel(const __nv_bfloat16 *_
 #pragma unroll
                 for (int e = 0; e < 8; e++)
                     gv[e] = valid && w0 + e < we ? __bfloat162float(g[((long long)row * W + w0 + e) * co_n + co]) : 0.f;
+                {  // lane l < 30 loads window element (l / 10, l % 10); shuffled to all lanes
+                    const int la = lane / 10, le = lane - 10 * la;
+                    const int hh = h + la - 1, ww = w0 - 1 + le;
+                    const float mine = lane < 30 && hh >= 0 && hh < H && ww >= 0 && ww < W
+                                           ? __bfloat162float(xin[(rbase + (long long)hh * W + ww) * cpad])
+                                           : 0.f;
 #pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    const int hh = h + a - 1;
+                    for (int a = 0; a < 3; a++)
 #pragma unroll
-                    for (int e = 0; e < 10; e++) {
-                        const int ww = w0 - 1 + e;
-                        xc[a][e] = hh >= 0 && hh < H && ww >= 0 && ww < W
-                                       ? __bfloat162float(xin[(rbase + (long long)hh * W + ww) * cpad])
-                                       : 0.f;
-                    }
+                        for (int e = 0; e < 10; e++) xc[a][e] = __shfl_sync(0xffffffffu, mine, a * 10 + e);
                 }
 #pragma unroll
                 for (int e = 0; e < 8; e++) {
