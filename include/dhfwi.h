@@ -307,7 +307,7 @@ const char *model_shots_static_error(void);
  * W[co][a][b][:] . x[h][w]) then bias; the 1x1 conv [Cout][Cin] then bias.
  * ------------------------------------------------------------------------ */
 typedef struct {
-    int base_channels;  /* channels of the input block (multiple of 8); 32 here, 128 in the paper */
+    int base_channels;  /* channels of the input block (multiple of 8, 8..256); 32 here, 128 in the paper */
     int levels;         /* down/up blocks (4 in the paper) */
     int patch;          /* square patch size (multiple of 2^levels); 0: full-image training, the
                            paper's choice (Section 2.4): the whole image, zero-padded at the bottom

@@ -859,7 +859,7 @@ __global__ void mse_kernel(const float *__restrict__ out, const float *__restric
 // Threads (c, j): channel c (blockDim.x = C + 1 rounded up to 32) over the
 // pixels p0 + j, p0 + j + S, ... (S = blockDim.y streams), the streams then
 // summed in order j = 0, 1, ... (deterministic).
-__global__ void conv1x1_bwd_leaky_kernel(const __nv_bfloat16 *__restrict__ g, const __nv_bfloat16 *__restrict__ a,
+__global__ void __launch_bounds__(512) conv1x1_bwd_leaky_kernel(const __nv_bfloat16 *__restrict__ g, const __nv_bfloat16 *__restrict__ a,
                                          long long P, int C, const __nv_bfloat16 *__restrict__ w, float slope,
                                          __nv_bfloat16 *__restrict__ gn, int rows, float *__restrict__ part) {
     extern __shared__ float red[];  // [S][blockDim.x]
@@ -1603,7 +1603,7 @@ void launch_conv1x1_bwd_leaky(const __nv_bfloat16 *g, const __nv_bfloat16 *a, lo
     if (rows < 64) rows = 64;
     const int nblk = (int)((P + rows - 1) / rows);
     const int cx = ((C + 1 + 31) / 32) * 32;
-    const int streams = std::max(1, std::min(8, 1024 / cx));
+    const int streams = std::max(1, std::min(8, 512 / cx));  // at most 512 threads (the kernel's bound)
     conv1x1_bwd_leaky_kernel<<<nblk, dim3(cx, streams), sizeof(float) * cx * streams, s>>>(g, a, P, C, w, slope, gn,
                                                                                              rows, part);
     bias_grad_final_kernel<<<((C + 1) * 32 + 255) / 256, 256, 0, s>>>(part, nblk, C + 1, dw_db);

@@ -1005,8 +1005,9 @@ int ensure_small(dhfwi_ctx *ctx, NetState &N) {
 
 int ensure_net(dhfwi_ctx *ctx, int base, int levels) {
     NetState *&net = ctx_net(ctx);
-    if (base < 8 || base % 8 != 0 || levels < 1 || levels > 6)
-        return fail(ctx, DHFWI_ERR_ARG, "network needs base_channels a multiple of 8 (>= 8) and 1 <= levels <= 6");
+    if (base < 8 || base > 256 || base % 8 != 0 || levels < 1 || levels > 6)
+        return fail(ctx, DHFWI_ERR_ARG,
+                    "network needs base_channels a multiple of 8 in [8, 256] and 1 <= levels <= 6");
     if (!net) net = new NetState();
     if (net->base != base || net->levels != levels || !net->theta) {
         drop_graphs(*net);
