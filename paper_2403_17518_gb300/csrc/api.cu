@@ -1020,7 +1020,6 @@ int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *w3, float *w4, floa
                 n += rc;
             }
         }
-        bool folded = false;  // the previous two-step launch injected this launch's first-step data
         for (int k = n1; k >= n0 + 1;) {
             b.nu = ncur;
             b.nun = nnxt;
@@ -1028,18 +1027,11 @@ int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *w3, float *w4, floa
             b.a = slot(k - 1);
             b.k = k;
             if (blocking_adj && k - 1 >= n0 + 1) {
-                // Steps k and k-1: the data of step k go into D_nu first, here
-                // for the shots the previous two-step launch did not cover
-                // (slots are sorted by record length: those with nt == k),
-                // or all of them after a one-step launch or at a segment's start.
-                const int s_hi = active_slots(P, k - 1), s_lo = folded ? active_slots(P, k) : 0;
-                const int r0 = P.rtiles_prefix[s_lo], nrt = P.rtiles_prefix[s_hi] - r0;
-                launch_adj_inject(b, (const int *)P.d_rtiles.p + r0, nrt, st);
+                // Steps k and k-1: the data of step k go into D_nu first.
+                const int nrt = P.rtiles_prefix[active_slots(P, k - 1)];
+                launch_adj_inject(b, (const int *)P.d_rtiles.p, nrt, st);
                 b.dd_out = dnxt_nu;
                 b.a2 = slot(k - 2);
-                // The next launch is a two-step launch of this segment: fold its injection.
-                b.inj_next = k - 3 >= n0 + 1 ? 1 : 0;
-                folded = b.inj_next != 0;
                 TileMaps M;
                 int rc = adj_pair_maps(ctx, b, &M);
                 if (rc) return rc;
@@ -1053,8 +1045,6 @@ int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *w3, float *w4, floa
             }
             b.dd_out = nullptr;
             b.a2 = nullptr;
-            b.inj_next = 0;
-            folded = false;
             int rc = adj_step(ctx, b, active_tiles(P, k - 1), ctx->launch[2], st);
             if (rc) return rc;
             ctx->stats.kernel_launches++;

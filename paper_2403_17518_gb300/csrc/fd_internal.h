@@ -140,12 +140,6 @@ struct AdjArgs {
     // goes to dd_out, nu^{k-1} to nun, a2 = a^{k-2}.
     float *dd_out;
     const float *a2;
-    // Two-step kernel: when set, the next launch is a two-step launch at k-2
-    // and this one adds the data of its first step, kappa r^{k-3}, to the
-    // stored D_nu^{k-1} at its tiles' receivers (what launch_adj_inject would
-    // do before that launch, same arithmetic), so that only the tiles of
-    // shots starting at step k-2 need the separate injection.
-    int inj_next = 0;
 };
 
 // Born joint step n: background u0 and scattered p advance together.

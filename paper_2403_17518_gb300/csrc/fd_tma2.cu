@@ -383,20 +383,6 @@ __device__ __forceinline__ void adj_pair_tile(const AdjArgs &A, const Fwd2Stage 
         *reinterpret_cast<f2 *>(A.nun + c) = nn;
         *reinterpret_cast<f2 *>(A.g + c) = g;
     }
-    // The next launch's first-step data (step k-2 takes r^{k-3}) into the
-    // stored D_nu^{k-1} at this tile's receivers, once the core's stores are
-    // done (the 256 workers; kappa of the stage is still this tile's).
-    if (A.inj_next && T.rec_end > T.rec_begin) {
-        asm volatile("bar.sync 1, 256;" ::: "memory");
-        const float *rk = A.r + T.doff + (long long)(k - 3) * T.nrec;
-        for (int e = T.rec_begin + tid; e < T.rec_end; e += 256)
-            if (e == T.rec_begin || A.c.recs[e - 1].cell != A.c.recs[e].cell) {
-                const int cell = A.c.recs[e].cell;
-                const int lz = cell / TX, lx = cell % TX;
-                float *d = A.dd_out + T.foff + (long long)(T.z0 + lz) * pitch + T.x0 + lx;
-                *d = fmaf(S.k[lz + HALO][lx + HALO], receiver_sum(A.c.recs, e, T.rec_end, rk), *d);
-            }
-    }
 }
 
 __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __grid_constant__ TileMaps M, int ntiles) {
