@@ -376,10 +376,14 @@ int deblur_train(dhfwi_ctx *ctx, const float *x_dev, const float *y_dev, int nz,
  *          bf16(convT(x) + b) for the transposed one (widened to float32);
  *        DHFWI_LAYER_DGRAD: [n][H][W][ci] = dL/dx for dL/dy = gy;
  *        DHFWI_LAYER_WGRAD: dL/dw (parameter layout) then dL/db [co].
- * ci and co are multiples of 8.  Unused pointers may be NULL.  Allocates its
- * temporaries and synchronises the stream. */
+ * ci and co are multiples of 8.  Kind DHFWI_LAYER_FIRST is the network's
+ * first 3x3 convolution, whose input has one channel (ci = 1; co a multiple
+ * of 8), on the CUDA-core kernels the network runs for it; FWD and WGRAD
+ * only.  Unused pointers may be NULL.  Allocates its temporaries and
+ * synchronises the stream. */
 #define DHFWI_LAYER_CONV3 0
 #define DHFWI_LAYER_CONVT 1
+#define DHFWI_LAYER_FIRST 2
 #define DHFWI_LAYER_FWD 0
 #define DHFWI_LAYER_DGRAD 1
 #define DHFWI_LAYER_WGRAD 2

@@ -1295,12 +1295,16 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
                  const float *w_dev, const float *b_dev, const float *gy_dev, float *out_dev, void *stream) {
     if (!ctx) return DHFWI_ERR_ARG;
     ctx_begin(ctx);
-    if (kind != DHFWI_LAYER_CONV3 && kind != DHFWI_LAYER_CONVT) return fail(ctx, DHFWI_ERR_ARG, "bad layer kind");
+    if (kind != DHFWI_LAYER_CONV3 && kind != DHFWI_LAYER_CONVT && kind != DHFWI_LAYER_FIRST)
+        return fail(ctx, DHFWI_ERR_ARG, "bad layer kind");
     if (op != DHFWI_LAYER_FWD && op != DHFWI_LAYER_DGRAD && op != DHFWI_LAYER_WGRAD)
         return fail(ctx, DHFWI_ERR_ARG, "bad layer operation");
-    if (n < 1 || H < 1 || W < 1 || ci < 8 || co < 8 || ci % 8 || co % 8)
+    const bool first = kind == DHFWI_LAYER_FIRST;
+    if (first && (ci != 1 || op == DHFWI_LAYER_DGRAD))
+        return fail(ctx, DHFWI_ERR_ARG, "the first layer has one input channel and no input gradient");
+    if (n < 1 || H < 1 || W < 1 || co < 8 || co % 8 || (!first && (ci < 8 || ci % 8)))
         return fail(ctx, DHFWI_ERR_ARG, "need n, H, W >= 1 and ci, co positive multiples of 8");
-    const bool conv = kind == DHFWI_LAYER_CONV3;
+    const bool conv = kind != DHFWI_LAYER_CONVT;
     const int taps = conv ? 9 : 4, Ho = conv ? H : 2 * H, Wo = conv ? W : 2 * W;
     const long long Pin = (long long)n * H * W, Pout = (long long)n * Ho * Wo;
     if (Pout * std::max(ci, co) >= (1LL << 31)) return fail(ctx, DHFWI_ERR_ARG, "layer too large");
@@ -1323,7 +1327,7 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
         void *ps[] = {x16, w16, wt16, g16, y16, ones, part, wg, err};
         for (void *p : ps) dev_free(p);
     };
-    if ((rc = dev_alloc(ctx, (void **)&x16, 2 * (size_t)Pin * ci)) ||
+    if ((rc = dev_alloc(ctx, (void **)&x16, 2 * (size_t)Pin * (first ? CPAD : ci))) ||
         (rc = dev_alloc(ctx, (void **)&w16, 2 * (size_t)nw)) || (rc = dev_alloc(ctx, (void **)&wt16, 2 * (size_t)nw)) ||
         (rc = dev_alloc(ctx, (void **)&g16, 2 * (size_t)Pout * co)) ||
         (rc = dev_alloc(ctx, (void **)&y16, 2 * (size_t)Pout * co)) || (rc = dev_alloc(ctx, (void **)&ones, 16)) ||
@@ -1341,121 +1345,143 @@ int deblur_layer(dhfwi_ctx *ctx, int kind, int op, int n, int H, int W, int ci, 
         return fail(ctx, DHFWI_ERR_CUDA, cudaGetErrorString(e));
     }
     long long launches = 0;
-    // Operands rounded to bf16 where the network rounds them.
-    if (x_dev) launch_to_bf16(x_dev, Pin * ci, x16, s), launches++;
-    if (w_dev) {
-        launch_to_bf16(w_dev, nw, w16, s);
-        if (!conv && op == DHFWI_LAYER_FWD) {  // the transposed conv's forward takes tap-major rows
-            TransposeJobs ct{};
-            ct.n = 1;
-            ct.off[0] = 0;
-            ct.co[0] = co;
-            ct.taps[0] = 4;
-            ct.ci[0] = ci;
-            launch_convt_tapmajor_batch(w16, wt16, ct, s);
-        } else {
-            launch_transpose_w(w16, co, taps, ci, wt16, s);
-        }
-        launches += 2;
-    }
-    // The transposed conv's output gradient in space-to-depth layout, as the
-    // network's backward pass keeps it.
-    if (gy_dev) {
-        if (conv) launch_to_bf16(gy_dev, Pout * co, g16, s);
-        else launch_to_bf16_s2d(gy_dev, n, H, W, co, g16, s);
-        launches++;
-    }
-    if (op == DHFWI_LAYER_FWD) {
-        FpropArgs a{};
-        a.src = x16;
-        a.src_stride = ci;
-        a.C = ci;
-        a.Hs = H;
-        a.Ws = W;
-        a.Ho = H;
-        a.Wo = W;
-        a.M = (int)Pin;
-        a.bt = w16;
-        a.bias = b_dev;
-        a.slope = 0.2f;
-        a.dst_bf16 = y16;
-        a.dst_stride = co;
-        a.part = part;
-        a.part_floats = fp_floats;
-        a.err = err;
-        a.scale = 1;
-        if (conv) {
-            a.ntaps = 9;
-            for (int t = 0; t < 9; t++) {
-                a.dh[t] = t / 3 - 1;
-                a.dw[t] = t % 3 - 1;
+    if (first) {  // the network's first layer: one input channel padded to CPAD, CUDA-core kernels
+        if (x_dev) launch_input_pack(x_dev, Pin, CPAD, x16, s), launches++;
+        if (w_dev) launch_to_bf16(w_dev, nw, w16, s), launches++;
+        if (op == DHFWI_LAYER_FWD) {
+            if (!launch_first_conv(x16, CPAD, n, H, W, w16, b_dev, co, 0.2f, y16, co, s)) {
+                cleanup();
+                return fail(ctx, DHFWI_ERR_ARG, "first layer: unsupported shape");
             }
-            a.N = co;
-            launch_fprop(a, EPI_BF16_LEAKY, s);
+            launch_bf16_to_f32(y16, Pout * co, out_dev, s);
+            launches += 2;
         } else {
-            a.ntaps = 1;
-            a.dh[0] = a.dw[0] = 0;
-            a.N = 4 * co;
-            a.bt = wt16;  // tap-major copy
-            launch_fprop(a, EPI_BF16_CONVT, s);
-        }
-        launch_bf16_to_f32(y16, Pout * co, out_dev, s);
-        launches += 3;
-    } else if (op == DHFWI_LAYER_DGRAD) {
-        FpropArgs a{};
-        a.src = g16;
-        a.src_stride = co;
-        a.C = co;
-        a.Hs = Ho;
-        a.Ws = Wo;
-        a.Ho = H;
-        a.Wo = W;
-        a.M = (int)Pin;
-        a.N = ci;
-        a.bt = wt16;
-        a.dst_f32 = out_dev;
-        a.dst_stride = ci;
-        a.part = part;
-        a.part_floats = fp_floats;
-        a.err = err;
-        if (conv) {
-            a.ntaps = 9;
-            a.scale = 1;
-            for (int t = 0; t < 9; t++) {
-                a.dh[t] = 1 - t / 3;
-                a.dw[t] = 1 - t % 3;
+            launch_to_bf16(gy_dev, Pout * co, g16, s);
+            const int k = launch_first_wgrad(g16, co, x16, CPAD, n, H, W, wg, wg_floats, out_dev, out_dev + nw, s);
+            if (!k) {
+                cleanup();
+                return fail(ctx, DHFWI_ERR_ARG, "first layer: scratch too small");
             }
-        } else {  // one tap over the 4 co space-to-depth channels of the coarse grid
-            a.src_stride = 4 * co;
-            a.C = 4 * co;
+            launches += 1 + k;
+        }
+    }
+    if (!first) {
+        // Operands rounded to bf16 where the network rounds them.
+        if (x_dev) launch_to_bf16(x_dev, Pin * ci, x16, s), launches++;
+        if (w_dev) {
+            launch_to_bf16(w_dev, nw, w16, s);
+            if (!conv && op == DHFWI_LAYER_FWD) {  // the transposed conv's forward takes tap-major rows
+                TransposeJobs ct{};
+                ct.n = 1;
+                ct.off[0] = 0;
+                ct.co[0] = co;
+                ct.taps[0] = 4;
+                ct.ci[0] = ci;
+                launch_convt_tapmajor_batch(w16, wt16, ct, s);
+            } else {
+                launch_transpose_w(w16, co, taps, ci, wt16, s);
+            }
+            launches += 2;
+        }
+        // The transposed conv's output gradient in space-to-depth layout, as the
+        // network's backward pass keeps it.
+        if (gy_dev) {
+            if (conv) launch_to_bf16(gy_dev, Pout * co, g16, s);
+            else launch_to_bf16_s2d(gy_dev, n, H, W, co, g16, s);
+            launches++;
+        }
+        if (op == DHFWI_LAYER_FWD) {
+            FpropArgs a{};
+            a.src = x16;
+            a.src_stride = ci;
+            a.C = ci;
             a.Hs = H;
             a.Ws = W;
-            a.ntaps = 1;
+            a.Ho = H;
+            a.Wo = W;
+            a.M = (int)Pin;
+            a.bt = w16;
+            a.bias = b_dev;
+            a.slope = 0.2f;
+            a.dst_bf16 = y16;
+            a.dst_stride = co;
+            a.part = part;
+            a.part_floats = fp_floats;
+            a.err = err;
             a.scale = 1;
-            a.dh[0] = a.dw[0] = 0;
+            if (conv) {
+                a.ntaps = 9;
+                for (int t = 0; t < 9; t++) {
+                    a.dh[t] = t / 3 - 1;
+                    a.dw[t] = t % 3 - 1;
+                }
+                a.N = co;
+                launch_fprop(a, EPI_BF16_LEAKY, s);
+            } else {
+                a.ntaps = 1;
+                a.dh[0] = a.dw[0] = 0;
+                a.N = 4 * co;
+                a.bt = wt16;  // tap-major copy
+                launch_fprop(a, EPI_BF16_CONVT, s);
+            }
+            launch_bf16_to_f32(y16, Pout * co, out_dev, s);
+            launches += 3;
+        } else if (op == DHFWI_LAYER_DGRAD) {
+            FpropArgs a{};
+            a.src = g16;
+            a.src_stride = co;
+            a.C = co;
+            a.Hs = Ho;
+            a.Ws = Wo;
+            a.Ho = H;
+            a.Wo = W;
+            a.M = (int)Pin;
+            a.N = ci;
+            a.bt = wt16;
+            a.dst_f32 = out_dev;
+            a.dst_stride = ci;
+            a.part = part;
+            a.part_floats = fp_floats;
+            a.err = err;
+            if (conv) {
+                a.ntaps = 9;
+                a.scale = 1;
+                for (int t = 0; t < 9; t++) {
+                    a.dh[t] = 1 - t / 3;
+                    a.dw[t] = 1 - t % 3;
+                }
+            } else {  // one tap over the 4 co space-to-depth channels of the coarse grid
+                a.src_stride = 4 * co;
+                a.C = 4 * co;
+                a.Hs = H;
+                a.Ws = W;
+                a.ntaps = 1;
+                a.scale = 1;
+                a.dh[0] = a.dw[0] = 0;
+            }
+            launch_fprop(a, EPI_F32, s);
+            launches += 2;
+        } else {
+            WgradArgs w{};
+            w.mode = conv ? WG_CONV : WG_CONVT;
+            w.g = g16;
+            w.g_stride = conv ? co : 4 * co;
+            w.g_s2d = !conv;
+            w.x = x16;
+            w.x_stride = ci;
+            w.nimg = n;
+            w.H = H;
+            w.W = W;
+            w.ci = ci;
+            w.co = co;
+            w.M = wM;
+            w.nw = conv ? 9 * ci : ci;
+            w.N = wN;
+            w.ones = ones;
+            w.part = wg;
+            w.err = err;
+            launches += launch_wgrad(w, splits, out_dev, out_dev + nw, s);
         }
-        launch_fprop(a, EPI_F32, s);
-        launches += 2;
-    } else {
-        WgradArgs w{};
-        w.mode = conv ? WG_CONV : WG_CONVT;
-        w.g = g16;
-        w.g_stride = conv ? co : 4 * co;
-        w.g_s2d = !conv;
-        w.x = x16;
-        w.x_stride = ci;
-        w.nimg = n;
-        w.H = H;
-        w.W = W;
-        w.ci = ci;
-        w.co = co;
-        w.M = wM;
-        w.nw = conv ? 9 * ci : ci;
-        w.N = wN;
-        w.ones = ones;
-        w.part = wg;
-        w.err = err;
-        launches += launch_wgrad(w, splits, out_dev, out_dev + nw, s);
     }
     e = cudaGetLastError();
     unsigned herr = 0;

@@ -265,12 +265,13 @@ class Context:
 
     def deblur_layer(self, kind: str, op: str, x=None, w=None, b=None, gy=None, n=1, H=1, W=1, ci=8, co=8,
                      stream=None) -> torch.Tensor:
-        """One network layer alone (kind "conv3" or "convT"; op "fwd", "dgrad"
-        or "wgrad"), NHWC float32 tensors; see deblur_layer in dhfwi.h."""
-        k = {"conv3": 0, "convT": 1}[kind]
+        """One network layer alone (kind "conv3", "convT" or "first", the
+        one-input-channel first convolution; op "fwd", "dgrad" or "wgrad"),
+        NHWC float32 tensors; see deblur_layer in dhfwi.h."""
+        k = {"conv3": 0, "convT": 1, "first": 2}[kind]
         o = {"fwd": 0, "dgrad": 1, "wgrad": 2}[op]
-        taps = 9 if k == 0 else 4
-        Ho, Wo = (H, W) if k == 0 else (2 * H, 2 * W)
+        taps = 4 if k == 1 else 9
+        Ho, Wo = (2 * H, 2 * W) if k == 1 else (H, W)
         shape = {0: (n, Ho, Wo, co), 1: (n, H, W, ci), 2: (taps * ci * co + co,)}[o]
         out = torch.empty(shape, dtype=torch.float32, device=self.device)
         ptr = lambda t, nm: self._dense(t, nm) if t is not None else None

@@ -144,3 +144,37 @@ def test_wgrad_mma_path(monkeypatch):
     layers the tcgen05 one takes by default."""
     monkeypatch.setenv("DHFWI_NN_WGRAD", "mma")
     _run(monkeypatch, "default", "conv3", (128, 128, 4, 8, 8), seed=3)
+
+
+# (co, n, H, W) of the first layer (one input channel).
+FIRST = [(32, 4, 128, 128), (16, 2, 20, 24), (128, 1, 30, 40)]
+
+
+@pytest.mark.parametrize("shape", FIRST, ids=lambda s: "x".join(map(str, s)))
+def test_first_layer_parity(shape):
+    """The first 3x3 convolution (one input channel, padded to 8 for the
+    GEMMs but run on CUDA cores): forward and weight / bias gradients within
+    1e-3 of the oracle's layer."""
+    import torch
+
+    co, n, H, W = shape
+    x, w, b, gy = _data(sum(shape), "conv3", 1, co, n, H, W)
+    from synth import tiny_case
+
+    ctx = gpu_ctx(tiny_case())
+    dev = lambda a: torch.as_tensor(a, device="cuda").contiguous()
+    errs = {}
+    for op in ("fwd", "wgrad"):
+        out = ctx.deblur_layer("first", op, x=dev(x), w=dev(w), b=dev(b), gy=dev(gy), n=n, H=H, W=W, ci=1, co=co)
+        got = out.cpu().numpy().astype(np.float64)
+        ref = _oracle("conv3", op, x, w, b, gy)
+        if op == "wgrad":
+            nw = w.size
+            errs["wgrad"] = rel_l2(got[:nw], ref[:nw])
+            errs["bgrad"] = rel_l2(got[nw:], ref[nw:])
+        else:
+            errs[op] = rel_l2(got.reshape(ref.shape), ref)
+    with pytest.raises(Exception):
+        ctx.deblur_layer("first", "dgrad", x=dev(x), w=dev(w), b=dev(b), gy=dev(gy), n=n, H=H, W=W, ci=1, co=co)
+    ctx.close()
+    assert all(e <= TOL for e in errs.values()), errs
