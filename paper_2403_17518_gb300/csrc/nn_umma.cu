@@ -1828,8 +1828,10 @@ int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s) {
     if (((a.x_stride | a.x_off | a.g_stride) & 7) != 0) return 0;
     if ((((uintptr_t)(a.x + a.x_off)) | (uintptr_t)a.g) & 15) return 0;
     if ((long long)a.nimg * a.H * a.W >= (1LL << 31)) return 0;
-    if (a.M % 256 == 0) return wgrad_tma_launch<256>(a, max_splits, s);
-    if (a.M % 128 == 0) return wgrad_tma_launch<128>(a, max_splits, s);
+    const char *nb = getenv("DHFWI_NN_WGRAD_NB");
+    const int nb_cap = nb ? atoi(nb) : 256;
+    if (a.M % 256 == 0 && nb_cap >= 256) return wgrad_tma_launch<256>(a, max_splits, s);
+    if (a.M % 128 == 0 && nb_cap >= 128) return wgrad_tma_launch<128>(a, max_splits, s);
     return wgrad_tma_launch<64>(a, max_splits, s);
 }
 
