@@ -906,7 +906,7 @@ bool graphs_on() {
 // The switches that change which kernels a pass launches.
 std::string gemm_switches() {
     static const char *names[] = {"DHFWI_NN_GEMM", "DHFWI_NN_WGRAD", "DHFWI_NN_CONV",   "DHFWI_NN_PATCH",
-                                  "DHFWI_NN_HALO", "DHFWI_NN_CONVT", "DHFWI_NN_OVERLAP", "DHFWI_NN_WGRAD_NB"};
+                                  "DHFWI_NN_HALO", "DHFWI_NN_CONVT", "DHFWI_NN_OVERLAP", "DHFWI_NN_WGRAD_NB", "DHFWI_NN_CONV_BN"};
     std::string k;
     for (const char *n : names) {
         const char *e = getenv(n);

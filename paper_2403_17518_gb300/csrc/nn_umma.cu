@@ -1476,13 +1476,16 @@ bool conv3_tma_dispatch(const FpropArgs &a, const ConvTile &G, cudaStream_t s) {
         if (a.N <= 128) return conv3_persistent_launch<128, 32, EPI>(a, G, s);
         return conv3_persistent_launch<256, 32, EPI>(a, G, s);
     }
+    // DHFWI_NN_CONV_BN=64|128 caps the N tile of the one-tile-per-CTA form.
+    const char *bn = getenv("DHFWI_NN_CONV_BN");
+    const int cap = bn ? atoi(bn) : 256;
     if (a.C % 64 == 0) {
-        if (a.N <= 64) return conv3_tma_launch<64, 64, EPI>(a, G, s);
-        if (a.N <= 128) return conv3_tma_launch<128, 64, EPI>(a, G, s);
+        if (a.N <= 64 || cap <= 64) return conv3_tma_launch<64, 64, EPI>(a, G, s);
+        if (a.N <= 128 || cap <= 128) return conv3_tma_launch<128, 64, EPI>(a, G, s);
         return conv3_tma_launch<256, 64, EPI>(a, G, s);
     }
-    if (a.N <= 64) return conv3_tma_launch<64, 32, EPI>(a, G, s);
-    if (a.N <= 128) return conv3_tma_launch<128, 32, EPI>(a, G, s);
+    if (a.N <= 64 || cap <= 64) return conv3_tma_launch<64, 32, EPI>(a, G, s);
+    if (a.N <= 128 || cap <= 128) return conv3_tma_launch<128, 32, EPI>(a, G, s);
     return conv3_tma_launch<256, 32, EPI>(a, G, s);
 }
 
