@@ -41,11 +41,14 @@ struct Plan {
     std::vector<int> tiles_prefix;     // tiles of the first m slots
     std::vector<int> rtiles;           // tiles with receivers, in tile order
     std::vector<int> rtiles_prefix;    // of those, the tiles of the first m slots
+    std::vector<TileRec> xrecs;        // receivers of each tile's grown region (StepCommon::xrecs)
+    std::vector<int> xrec_off;         // per tile, with a final end offset
+    bool xinj = false;                 // every grown region holds at most kInjCap entries
     long long pool_floats = 0;
     int pitch = 0;                     // row pitch of every window in a pool
     long long n_data = 0;
     long long cells_per_step_all = 0;  // padded cells of all shots
-    DevBuf d_shots, d_tiles, d_recs, d_slot_of, d_wav, d_infos, d_rtiles;
+    DevBuf d_shots, d_tiles, d_recs, d_slot_of, d_wav, d_infos, d_rtiles, d_xrecs, d_xrec_off;
 };
 
 }  // namespace
@@ -280,6 +283,9 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
     P.tiles_prefix.assign(ns + 1, 0);
     P.rtiles.clear();
     P.rtiles_prefix.assign(ns + 1, 0);
+    P.xrecs.clear();
+    P.xrec_off.clear();
+    P.xinj = true;
     // One row pitch for all windows: a pool is then a [slot][NZ][pitch] array
     // that a single 3-D tensor map describes.
     int pitch = POOL_ALIGN;
@@ -326,6 +332,33 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
                 for (const TileRec &e : bk) P.recs.push_back(e);
             }
         P.tiles_prefix[k + 1] = (int)P.tiles.size();
+        // Receivers of each tile's grown region ((TX + 2 HALO)^2 cells), by
+        // cell then receiver as the per-tile lists.
+        {
+            constexpr int EW = TX + 2 * HALO;
+            std::vector<std::vector<TileRec>> xb((size_t)ntz * ntx);
+            for (int r = 0; r < sd.nrec; r++) {
+                const int rz = G->rec_iz[G->rec_off[s] + r] + nb;
+                const int rx = G->rec_ix[G->rec_off[s] + r] - x0 + nb;
+                for (int tz = 0; tz < ntz; tz++) {
+                    const int ez = rz - (tz * TZ - HALO);
+                    if (ez < 0 || ez >= EW) continue;
+                    for (int tx = 0; tx < ntx; tx++) {
+                        const int ex = rx - (tx * TX - HALO);
+                        if (ex >= 0 && ex < EW) xb[(size_t)tz * ntx + tx].push_back(TileRec{ez * EW + ex, r});
+                    }
+                }
+            }
+            for (size_t t = 0; t < xb.size(); t++) {
+                std::vector<TileRec> &bk = xb[t];
+                std::sort(bk.begin(), bk.end(), [](const TileRec &a, const TileRec &b) {
+                    return a.cell < b.cell || (a.cell == b.cell && a.r < b.r);
+                });
+                P.xrec_off.push_back((int)P.xrecs.size());
+                if ((int)bk.size() > kInjCap) P.xinj = false;
+                for (const TileRec &e : bk) P.xrecs.push_back(e);
+            }
+        }
         for (int ti = P.tiles_prefix[k]; ti < P.tiles_prefix[k + 1]; ti++) {
             const int rb = P.tiles[ti].rec_begin;
             const int re = ti + 1 < (int)P.tiles.size() ? P.tiles[ti + 1].rec_begin : (int)P.recs.size();
@@ -333,6 +366,8 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
         }
         P.rtiles_prefix[k + 1] = (int)P.rtiles.size();
     }
+    P.xrec_off.push_back((int)P.xrecs.size());  // end of the last tile's list
+    if (P.xrecs.empty()) P.xrecs.push_back(TileRec{0, 0});  // (a valid device pointer)
     P.tiles.push_back(Tile{0, 0, 0, (int)P.recs.size()});  // sentinel
     P.infos.resize(P.tiles.size() - 1);
     for (size_t i = 0; i + 1 < P.tiles.size(); i++) {
@@ -376,6 +411,8 @@ int get_plan(dhfwi_ctx *ctx, const dhfwi_geom *G) {
     if ((rc = upload(ctx, P.d_wav, wav, "wavelets"))) return rc;
     if ((rc = upload(ctx, P.d_infos, P.infos, "tile descriptors"))) return rc;
     if ((rc = upload(ctx, P.d_rtiles, P.rtiles, "receiver tile list"))) return rc;
+    if ((rc = upload(ctx, P.d_xrecs, P.xrecs, "grown-region receiver table"))) return rc;
+    if ((rc = upload(ctx, P.d_xrec_off, P.xrec_off, "grown-region receiver offsets"))) return rc;
     P.hash = h;
     return DHFWI_OK;
 }
@@ -422,6 +459,10 @@ StepCommon common(dhfwi_ctx *ctx) {
     c.NZ = ctx->NZ;
     c.nb = ctx->g.nb;
     c.tflag = (unsigned *)ctx->status.p + TFLAG_WORD;
+    if (ctx->plan.xinj) {
+        c.xrecs = (const TileRec *)ctx->plan.d_xrecs.p;
+        c.xrec_off = (const int *)ctx->plan.d_xrec_off.p;
+    }
     return c;
 }
 
@@ -847,7 +888,8 @@ int tune_depth(dhfwi_ctx *ctx, cudaStream_t st, const float *one_step_ms, int re
                 b.g = F + 4 * pool;
                 b.r = (const float *)ctx->rtmp.p;
                 b.k = 2;
-                const int nrt = P.rtiles_prefix[active_slots(P, 1)];
+                b.inject_here = P.xinj ? 1 : 0;
+                const int nrt = P.xinj ? 0 : P.rtiles_prefix[active_slots(P, 1)];
                 launch_adj_inject(b, (const int *)P.d_rtiles.p, nrt, st);
                 if (!(rc = adj_pair_maps(ctx, b, &M))) launch_adj_pair(b, ntiles, M, st);
                 ctx->stats.kernel_launches += 1 + (nrt > 0);
@@ -1027,8 +1069,11 @@ int run_backward(dhfwi_ctx *ctx, float *w, float *w2, float *w3, float *w4, floa
             b.a = slot(k - 1);
             b.k = k;
             if (blocking_adj && k - 1 >= n0 + 1) {
-                // Steps k and k-1: the data of step k go into D_nu first.
-                const int nrt = P.rtiles_prefix[active_slots(P, k - 1)];
+                // Steps k and k-1: the data of step k go into D_nu first (in
+                // the kernel's staged tiles, or by the separate pass when a
+                // tile's grown region holds too many receivers).
+                b.inject_here = P.xinj ? 1 : 0;
+                const int nrt = P.xinj ? 0 : P.rtiles_prefix[active_slots(P, k - 1)];
                 launch_adj_inject(b, (const int *)P.d_rtiles.p, nrt, st);
                 b.dd_out = dnxt_nu;
                 b.a2 = slot(k - 2);
@@ -1231,7 +1276,7 @@ void dhfwi_destroy(dhfwi_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->kap, &ctx->dkap, &ctx->status, &ctx->partial, &ctx->fields,
                       &ctx->ck, &ctx->abuf, &ctx->hist, &ctx->dtmp, &ctx->rtmp, &ctx->plan.d_shots, &ctx->plan.d_tiles,
                       &ctx->plan.d_recs, &ctx->plan.d_slot_of, &ctx->plan.d_wav, &ctx->plan.d_infos,
-                      &ctx->plan.d_rtiles};
+                      &ctx->plan.d_rtiles, &ctx->plan.d_xrecs, &ctx->plan.d_xrec_off};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_partial) cudaFreeHost(ctx->h_partial);

@@ -83,7 +83,17 @@ struct StepCommon {
     int NZ;               // padded rows = nz + 2 nb
     int nb;
     unsigned *tflag;      // set to 1 by a TMA-staged kernel whose bounded wait ran out
+    // Receivers of each tile's grown region (the tile and its HALO ring, a
+    // (TX + 2 HALO)^2 square, cell = ez * (TX + 2 HALO) + ex), by cell then
+    // receiver: tile t's are xrecs[xrec_off[t] .. xrec_off[t + 1]).  The
+    // two-step adjoint applies the data injection of its first step to the
+    // staged D_nu from them (nullable: no such lists, separate injection).
+    const TileRec *xrecs = nullptr;
+    const int *xrec_off = nullptr;
 };
+// Most grown-region receiver entries the two-step adjoint's shared-memory
+// list holds; plans with more use the separate injection pass.
+constexpr int kInjCap = 256;
 
 // Tensor maps of one TMA-staged step launch (kernel parameters).  A field
 // pool is a 3-D float array [slot][NZ][pitch] (x = column, y = row, z =
@@ -137,9 +147,12 @@ struct AdjArgs {
     int k;
     // Two-step kernel only (steps k and k-1 in one launch): dd holds D_nu^{k+1}
     // with the data of step k already injected (launch_adj_inject), D_nu^{k-1}
-    // goes to dd_out, nu^{k-1} to nun, a2 = a^{k-2}.
+    // goes to dd_out, nu^{k-1} to nun, a2 = a^{k-2}.  With inject_here set
+    // the data of step k are not in dd: each tile adds them to its staged
+    // D_nu from c.xrecs (same arithmetic as launch_adj_inject).
     float *dd_out;
     const float *a2;
+    int inject_here = 0;
 };
 
 // Born joint step n: background u0 and scattered p advance together.

@@ -40,6 +40,19 @@ struct Fwd2Stage {
 constexpr unsigned kFwd2StageBytes = sizeof(UTile2) + 2 * sizeof(ETile);
 static_assert(sizeof(Fwd2Stage) == kFwd2StageBytes && sizeof(Fwd2Stage) % 128 == 0, "stage layout");
 constexpr size_t kFwd2Smem = sizeof(Fwd2Stage) + 2 * sizeof(ETile) + sizeof(PipeTail);
+// The two-step adjoint's list of its next tile's data injection (grown
+// region, step k): offset of the cell in the staged D_nu (-1: a further
+// receiver of the cell before, already summed), kappa there, summed data.
+struct InjEntry {
+    int off;
+    float kap, sum;
+};
+struct InjBuf {
+    int n, pad[3];
+    InjEntry e[kInjCap];
+};
+constexpr size_t kAdj2Smem = kFwd2Smem + sizeof(InjBuf);
+static_assert(kFwd2Smem % 16 == 0, "injection list alignment");
 // Thread layout: 288 threads.  Step n covers the 72 x 72 grown tile with
 // 36 column pairs x 8 blocks of R1 = 9 rows; step n+1 covers the 64 x 64
 // core with the first 256 threads, 32 column pairs x 8 blocks of R2 = 8 rows.
@@ -391,6 +404,7 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
     ETile &V = *reinterpret_cast<ETile *>(smem_raw + sizeof(Fwd2Stage));
     ETile &Dn = *reinterpret_cast<ETile *>(smem_raw + sizeof(Fwd2Stage) + sizeof(ETile));
     PipeTail *tail = reinterpret_cast<PipeTail *>(smem_raw + sizeof(Fwd2Stage) + 2 * sizeof(ETile));
+    InjBuf &IB = *reinterpret_cast<InjBuf *>(smem_raw + kFwd2Smem);
     const int tid = threadIdx.x + threadIdx.y * 32;
     const bool leader = tid == 0;
     const unsigned bar = smem_u32(&tail->bar[0]);
@@ -427,11 +441,39 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
         fence_proxy_async();
         tma_load_3d(smem_u32(&S.k), &M.m[2], co.w - HALO, co.y - HALO, mc, bar);
     };
+    // Data of step k injected here (inject_here): warp 8, which has no cells
+    // in the second step, lists the next tile's grown-region injection
+    // (kappa and the receivers' summed data, from global memory) while the
+    // other warps run that step; after the tile's stage lands every thread
+    // adds the list to the staged D_nu, D' = fmaf(kappa, sum, D) as the
+    // separate pass computes it.  Shots whose record ends before step k take
+    // none.
+    const bool inj = A.inject_here && A.c.xrec_off != nullptr;
+    auto build = [&](int t) {
+        const int lane = tid - 256;
+        const int xb = A.c.xrec_off[t], xe = A.c.xrec_off[t + 1];
+        const TileInfo &Tg = A.c.infos[t];
+        const bool has = Tg.nt > A.k - 1;
+        const float *rk = A.r + Tg.doff + (long long)(A.k - 1) * Tg.nrec;
+        for (int e = xb + lane; has && e < xe; e += 32) {
+            InjEntry en{-1, 0.f, 0.f};
+            if (e == xb || A.c.xrecs[e - 1].cell != A.c.xrecs[e].cell) {
+                const int cell = A.c.xrecs[e].cell, ez = cell / E, ex = cell % E;
+                en.off = cell;
+                en.kap = A.c.kap[(long long)Tg.mc * A.c.mstride + (long long)(Tg.z0 - HALO + ez) * A.c.pf + Tg.mx +
+                                 ex - HALO];
+                en.sum = receiver_sum(A.c.xrecs, e, xe, rk);
+            }
+            IB.e[e - xb] = en;
+        }
+        if (lane == 0) IB.n = has ? xe - xb : 0;
+    };
     if (leader) {
         issue_ud();
         issue_k();
         if (b + g < ntiles) fetch_coords(A.c.infos, b + g, co, mc);
     }
+    if (inj && tid >= 256) build(b);
     __syncthreads();
     unsigned phase = 0;
     for (int tix = b; tix < ntiles; tix += g) {
@@ -445,6 +487,15 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
             }
             return;
         }
+        if (inj) {
+            const int n = IB.n;  // uniform: written before the last barrier
+            float *dflat = &S.d[0][0];
+            for (int e = tid; e < n; e += NT2) {
+                const InjEntry en = IB.e[e];
+                if (en.off >= 0) dflat[en.off] = fmaf(en.kap, en.sum, dflat[en.off]);
+            }
+            if (n > 0) __syncthreads();
+        }
         const bool more = tix + g < ntiles;
         auto mid = [&]() {  // after a barrier: every thread is done with u and D_nu
             if (leader && more) issue_ud();
@@ -452,6 +503,7 @@ __global__ void __launch_bounds__(NT2, 2) adj_pair_kernel(AdjArgs A, const __gri
         const TileInfo &T = tail->desc[0];
         if (T.flags & TI_INTERIOR2) adj_pair_tile<true>(A, S, V, Dn, T, tid, mid);
         else adj_pair_tile<false>(A, S, V, Dn, T, tid, mid);
+        if (inj && tid >= 256 && more) build(tix + g);  // warp 8, during the other warps' second step
         __syncthreads();  // kappa, the descriptor, V and Dn are free
         if (leader && more) {
             issue_k();
@@ -483,11 +535,12 @@ __global__ void adj_inject_kernel(AdjArgs A, const int *__restrict__ rtiles) {
 }
 
 template <typename K, typename Args>
-void launch_pdl2(K kernel, int grid, const Args &a, const TileMaps &maps, int ntiles, cudaStream_t s) {
+void launch_pdl2(K kernel, int grid, const Args &a, const TileMaps &maps, int ntiles, cudaStream_t s,
+                 size_t smem = kFwd2Smem) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(32, NT2 / 32);
-    cfg.dynamicSmemBytes = kFwd2Smem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -497,10 +550,10 @@ void launch_pdl2(K kernel, int grid, const Args &a, const TileMaps &maps, int nt
     cudaLaunchKernelEx(&cfg, kernel, a, maps, ntiles);
 }
 
-int occupancy_of(const void *fn) {
+int occupancy_of(const void *fn, size_t smem = kFwd2Smem) {
     int n = 0;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwd2Smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NT2, kFwd2Smem);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NT2, smem);
     return n < 1 ? 1 : n;
 }
 
@@ -513,10 +566,10 @@ void launch_adj_pair(const AdjArgs &a, int ntiles, const TileMaps &maps, cudaStr
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        occ = occupancy_of((const void *)adj_pair_kernel);
+        occ = occupancy_of((const void *)adj_pair_kernel, kAdj2Smem);
     }
     const int cap = occ * sms;
-    launch_pdl2(adj_pair_kernel, ntiles < cap ? ntiles : cap, a, maps, ntiles, s);
+    launch_pdl2(adj_pair_kernel, ntiles < cap ? ntiles : cap, a, maps, ntiles, s, kAdj2Smem);
 }
 
 void launch_adj_inject(const AdjArgs &a, const int *rtiles, int nrtiles, cudaStream_t s) {
