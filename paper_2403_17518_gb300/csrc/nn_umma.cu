@@ -1831,16 +1831,17 @@ int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s) {
     if (((a.x_stride | a.x_off | a.g_stride) & 7) != 0) return 0;
     if ((((uintptr_t)(a.x + a.x_off)) | (uintptr_t)a.g) & 15) return 0;
     if ((long long)a.nimg * a.H * a.W >= (1LL << 31)) return 0;
-    // N tile: 64 output channels for the short reductions (fewer than 64
-    // blocks of 128 pixels, or fewer than 512 on layers of at most 256 output
-    // channels: more stages and CTAs in flight; the 128 x 128 patches' network
+    // N tile: 64 output channels for the short reductions of the narrower
+    // layers (fewer than 64 blocks of 128 pixels and at most 512 output
+    // channels, or fewer than 512 blocks and at most 256 channels: more
+    // stages and CTAs in flight; the 128 x 128 patches' network
     // trained at 247 against 232 TFLOP/s with 64 everywhere), else at most
     // 128 (the full-image paper-size network: 683 against 659 TFLOP/s with
     // 256 and 630-637 with 64 on its wide layers, which then re-read their
     // input too often); DHFWI_NN_WGRAD_NB=64|128|256 caps it instead.
     const char *nb = getenv("DHFWI_NN_WGRAD_NB");
     const long long npb = ((long long)a.nimg * a.H * a.W + 127) / 128;
-    const int nb_cap = nb ? atoi(nb) : (npb < 64 || (a.M <= 256 && npb < 512)) ? 64 : 128;
+    const int nb_cap = nb ? atoi(nb) : ((a.M <= 512 && npb < 64) || (a.M <= 256 && npb < 512)) ? 64 : 128;
     if (a.M % 256 == 0 && nb_cap >= 256) return wgrad_tma_launch<256>(a, max_splits, s);
     if (a.M % 128 == 0 && nb_cap >= 128) return wgrad_tma_launch<128>(a, max_splits, s);
     return wgrad_tma_launch<64>(a, max_splits, s);
