@@ -433,14 +433,42 @@ __device__ __forceinline__ void conv_tile_epilogue(const FpropArgs &P, const Con
 #pragma unroll 1
     for (int c0 = cbeg; c0 < cend; c0 += 16) {
         if (n0 + c0 >= P.N) break;  // uniform across the warp
+        const int nb = n0 + c0;
+        const bool full16 = nb + 16 <= P.N;
+        // The chunk's bias (bf16 epilogues) is requested before the TMEM
+        // load, 16 bytes at a time where aligned, so that the two overlap.
+        float bias16[16];
+        if ((EPI == EPI_BF16_LEAKY || EPI == EPI_BF16) && !P.part && valid) {
+            if (full16 && ((uintptr_t)(P.bias + nb) & 15) == 0) {
+#pragma unroll
+                for (int e = 0; e < 16; e += 4) {
+                    const float4 b4 = *reinterpret_cast<const float4 *>(P.bias + nb + e);
+                    bias16[e] = b4.x;
+                    bias16[e + 1] = b4.y;
+                    bias16[e + 2] = b4.z;
+                    bias16[e + 3] = b4.w;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; e++) bias16[e] = nb + e < P.N ? P.bias[nb + e] : 0.f;
+            }
+        }
+        // Likewise the activation the LeakyReLU backward reads (16-byte path).
+        __align__(16) __nv_bfloat16 act16[16];
+        const __nv_bfloat16 *ap = P.act + m * P.act_stride + P.act_off + nb;
+        __nv_bfloat16 *ob = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
+        const bool act_vec = EPI == EPI_BF16_LEAKYBWD && !P.part && valid && full16 &&
+                             (((uintptr_t)ap | (uintptr_t)ob) & 15) == 0;
+        if (act_vec) {
+            reinterpret_cast<uint4 *>(act16)[0] = reinterpret_cast<const uint4 *>(ap)[0];
+            reinterpret_cast<uint4 *>(act16)[1] = reinterpret_cast<const uint4 *>(ap)[1];
+        }
         float v[16];
         if (nk > 0) tmem_ld16(trow + c0, v);
         else
 #pragma unroll
             for (int e = 0; e < 16; e++) v[e] = 0.f;
         if (!valid) continue;
-        const int nb = n0 + c0;
-        const bool full16 = nb + 16 <= P.N;
         if (P.part) {  // split-k: raw partial sums
             float *out = P.part + (long long)split * P.M * P.N + m * P.N + nb;
             if (full16 && (P.N & 3) == 0) {
@@ -459,7 +487,7 @@ __device__ __forceinline__ void conv_tile_epilogue(const FpropArgs &P, const Con
             __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
             for (int e = 0; e < 16; e++) {
-                float x = v[e] + (nb + e < P.N ? P.bias[nb + e] : 0.f);
+                float x = v[e] + bias16[e];
                 if (EPI == EPI_BF16_LEAKY) x = x > 0.f ? x : P.slope * x;
                 h[e] = __float2bfloat16_rn(x);
             }
@@ -499,15 +527,12 @@ __device__ __forceinline__ void conv_tile_epilogue(const FpropArgs &P, const Con
                 }
             }
         } else if (EPI == EPI_BF16_LEAKYBWD) {
-            const __nv_bfloat16 *ap = P.act + m * P.act_stride + P.act_off + nb;
-            __nv_bfloat16 *o = P.dst_bf16 + m * P.dst_stride + P.dst_off + nb;
-            if (full16 && (((uintptr_t)ap | (uintptr_t)o) & 15) == 0) {  // 16-byte loads and stores
-                __align__(16) __nv_bfloat16 av[16], h[16];
-                reinterpret_cast<uint4 *>(av)[0] = reinterpret_cast<const uint4 *>(ap)[0];
-                reinterpret_cast<uint4 *>(av)[1] = reinterpret_cast<const uint4 *>(ap)[1];
+            __nv_bfloat16 *o = ob;
+            if (act_vec) {  // 16-byte loads (issued above) and stores
+                __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
                 for (int e = 0; e < 16; e++)
-                    h[e] = __float2bfloat16_rn(v[e] * (__bfloat162float(av[e]) > 0.f ? 1.0f : P.slope));
+                    h[e] = __float2bfloat16_rn(v[e] * (__bfloat162float(act16[e]) > 0.f ? 1.0f : P.slope));
                 reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
                 reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
             } else {
