@@ -175,8 +175,8 @@ def test_network_direction_that_raises_the_misfit_falls_back_to_the_gradient():
     hist, calls = _run("deblur", iters=1, bands=(12.0,), bad_network=True)
     r = hist[1]
     assert r["fallback"] and r["alpha"] > 0
-    # gradient 2 + Born pair 2 + failed line search 2 and its backtracking
-    # round 2 + gradient line search 2
+    # gradient 2 + Born pair 2 + failed line search 2, its backtracked
+    # trials 2 + gradient line search 2
     assert r["solves"] == 10 and calls["data_misfit"] == 6 and not r["stalled"]
 
 
