@@ -137,3 +137,65 @@ def test_edge_case_layout():
     assert {1, 2, 3} <= set(g.nt.tolist()) and any(n % 2 for n in g.nt.tolist() if n > 3)
     assert (g.win_x1 - g.win_x0).min() == 3
     assert any(g.src_ix[s] == g.win_x1[s] - 1 for s in range(g.n_shots))
+
+
+def _dense_case():
+    """Receivers on five rows of 71 consecutive cells: one tile's grown region
+    holds 355 receiver entries, more than the two-step adjoint's in-kernel
+    injection list takes, so the plan uses the separate injection pass."""
+    nz, nx, h, dt, nb, nt = 120, 160, 10.0, 1e-3, 20, 120
+    g = synth.rng(47)
+    v = synth.smooth_model(1800.0 + 400.0 * g.uniform(size=(nz, nx)), 1.5)
+    v0 = synth.smooth_model(v, 3.0)
+    shots = [
+        (3, 80, 120, 0, 160, [(z, x) for z in range(1, 6) for x in range(40, 111)]),
+        (2, 30, 117, 10, 100, [(1, x) for x in range(10, 100, 3)]),
+    ]
+    rec_iz, rec_ix, off = [], [], [0]
+    for s in shots:
+        rec_iz += [r[0] for r in s[5]]
+        rec_ix += [r[1] for r in s[5]]
+        off.append(off[-1] + len(s[5]))
+    geom = synth.Geometry(
+        src_iz=synth._i32([s[0] for s in shots]), src_ix=synth._i32([s[1] for s in shots]),
+        nt=synth._i32([s[2] for s in shots]), rec_off=synth._i32(off), rec_iz=synth._i32(rec_iz),
+        rec_ix=synth._i32(rec_ix), win_x0=synth._i32([s[3] for s in shots]),
+        win_x1=synth._i32([s[4] for s in shots]), wavelet=synth.ricker(20.0, dt, nt), wavelet_shared=True)
+    return synth.Case(nz, nx, h, dt, nb, v, v0, geom, name="dense")
+
+
+DENSE = _dense_case()
+
+
+def _run_dense(blocking, monkeypatch):
+    import torch
+
+    monkeypatch.setenv("DHFWI_TIME_BLOCK", "1" if blocking else "0")
+    c = DENSE
+    ctx = gpu_ctx(c)
+    geom = f32_geom(c.geom)
+    v, v0 = to_dev(f32(c.v_true)), to_dev(f32(c.v_init))
+    d = ctx.model_shots(v, geom)
+    d_obs = 0.5 * d
+    J, g = ctx.fwi_gradient(v0, geom, d_obs)
+    m = ctx.rtm_mig(v0, geom, d_obs)
+    ctx.close()
+    return {"d": to_host(d), "g": to_host(g), "m": to_host(m), "J": J}
+
+
+def test_dense_receivers_separate_injection(monkeypatch):
+    """The separate injection pass (too many receivers for the in-kernel
+    list): gradient and migration match the oracle, and the two-step kernels
+    the one-step ones bit for bit."""
+    c = DENSE
+    geom = f32_geom(c.geom)
+    d = oracle.model_shots(f32(c.v_true), geom, c.h, c.dt, c.nb)
+    d_obs = f32(0.5 * f32(d))
+    J, g, _ = oracle.fwi_gradient(f32(c.v_init), geom, d_obs, c.h, c.dt, c.nb)
+    m = oracle.rtm_mig(f32(c.v_init), geom, d_obs, c.h, c.dt, c.nb)
+    two = _run_dense(True, monkeypatch)
+    assert rel_l2(two["g"], g) <= TOL and rel_l2(two["m"], m) <= TOL
+    assert abs(two["J"] - J) <= TOL * abs(J)
+    one = _run_dense(False, monkeypatch)
+    for k in ("d", "g", "m"):
+        np.testing.assert_array_equal(two[k], one[k], err_msg=k)
