@@ -1837,8 +1837,9 @@ bool launch_conv3_tma(const FpropArgs &a, int epi, cudaStream_t s) {
 }
 
 // The tcgen05 weight gradient (the default; DHFWI_NN_WGRAD=mma or
-// DHFWI_NN_GEMM=mma keep the mma.sync one) for WG_CONV with ci and co
-// multiples of 32 and aligned operands.  Partials as igemm_wgrad_kernel's,
+// DHFWI_NN_GEMM=mma keep the mma.sync one) for WG_CONV, and WG_CONVT with a
+// space-to-depth output gradient, with ci and co multiples of 32 and aligned
+// operands.  Partials as igemm_wgrad_kernel's,
 // bias column the sum of G's column.  Returns the number of splits written (0: not
 // applicable, nothing launched).
 int launch_wgrad_tma(const WgradArgs &a, int max_splits, cudaStream_t s) {
