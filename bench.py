@@ -444,11 +444,15 @@ def run_forward_only(args, dist, ctx, case, geom, v0, d_out):
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     U = case.geom.cell_updates(case.nz, case.nb)
     st = ctx.stats()
+    peak, peak_kind = peaks()
+    alg = FWD_BYTES_PER_CELL * U / ms / 1e6
     if dist.rank == 0:
         print(json.dumps({"only": "fwd", "workload": case.name, "ms_per_pass": round(ms, 3),
                           "step_variants": st["step_variant"],
                           "gcell_per_s": round(U / ms / 1e6, 3), "launches_per_pass": st["kernel_launches"],
-                          "bytes_per_cell": 16, "effective_GBps": round(16 * U / ms / 1e6, 1)}), flush=True)
+                          "algorithmic_bytes_per_cell": FWD_BYTES_PER_CELL, "algorithmic_GBps": round(alg, 1),
+                          "frac": round(alg / peak, 4), "peak": peak, "peak_kind": f"{peak_kind} (hbm_gbs)",
+                          "summed_form_GBps": round(SUMMED_FWD_BYTES_PER_CELL * U / ms / 1e6, 1)}), flush=True)
 
 
 def run_gradient_only(args, dist, ctx, case, geom, v0, d_obs):
